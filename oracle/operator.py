@@ -1,0 +1,360 @@
+"""Semi-discrete ES operator on a curvilinear moving mesh (oracle; test infrastructure only).
+
+Sec. 3: the point values (JU)_i and J_i on a fixed uniform computational mesh
+xi evolve by eq. semi_U / semi_J, with the 2w-th order EC flux of
+eq. ECFlux_curv_2p / GCL_flux built from the two-point flux eq. ECfluxMM, the
+metrics of eq. SCLCoeff / VCLCoeff, and the ES flux of eq. HOstable.
+
+Array layout: a 1D field has shape (n1,), a 2D field (n2, n1); direction
+xi_1 is the LAST axis.  States carry a leading component axis (d + 2).
+Coordinates x have shape (d, ...), x[0] = x_1.
+
+Readings of points the paper leaves open (each listed in the design notes):
+  * ghost nodes: periodic = wrap (coordinates shifted by the period);
+    outflow = copy of the boundary state, coordinates and mesh velocity
+    extended by odd reflection about the boundary node (x_{-m} = 2 x_0 - x_m);
+  * the face normal n, its length L and the face J xi_t used in the
+    dissipation are arithmetic means of the two neighbouring node values;
+  * the rotation angle theta is taken with the quadrant of (n_1, n_2), i.e.
+    cos(theta) = n_1/L, sin(theta) = n_2/L;
+  * the sign switch Y compares [[W]]^WENO at face i+1/2 with the plain jump
+    W_{i+1} - W_i at the same face.
+"""
+from dataclasses import dataclass, field
+from fractions import Fraction
+
+import numpy as np
+
+from . import thermo
+from .ecflux import ec_flux, log_mean, mean
+from .weno import mr_weno5
+
+PERIODIC = "periodic"
+OUTFLOW = "outflow"
+
+
+# ---------------------------------------------------------------- parameters
+
+@dataclass
+class Scheme:
+    """Parameters of the scheme (Sec. 3 - Sec. 5)."""
+    gas: thermo.Gas
+    dim: int = 1
+    w: int = 3                                   # EC order 2w (eq. ECFlux_curv_2p)
+    weno_gammas: tuple = (0.005, 0.045, 0.95)    # (1-pt, 3-pt, 5-pt) linear weights (Sec. 5)
+    weno_eps: float = 1e-12
+    dissipation: bool = True                     # False: the EC scheme alone
+    bc: tuple = (PERIODIC,)                      # per direction xi_1, xi_2
+    dxi: tuple = (1.0,)                          # Delta xi_k
+    period: tuple = (1.0,)                       # period length of x_k for periodic directions
+
+
+def ec_alphas(w):
+    """alpha_{w,m} from sum_m m alpha = 1, sum_m m^(2s-1) alpha = 0, s = 2..w (Sec. 3.1, after eq. GCL_flux).
+
+    Solved exactly in rationals; for w = 3: (3/2, -3/10, 1/30).
+    """
+    A = [[Fraction(m) ** (2 * s - 1) for m in range(1, w + 1)] for s in range(1, w + 1)]
+    rhs = [Fraction(1)] + [Fraction(0)] * (w - 1)
+    n = w
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        rhs[col], rhs[piv] = rhs[piv], rhs[col]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                f = A[r][col] / A[col][col]
+                A[r] = [a - f * b for a, b in zip(A[r], A[col])]
+                rhs[r] = rhs[r] - f * rhs[col]
+    return [rhs[i] / A[i][i] for i in range(n)]
+
+
+# ------------------------------------------------------------------- ghosts
+
+def pad(a, g, axis, bc, shift=0.0, odd=False):
+    """Extend array a by g ghost nodes on both ends of `axis`.
+
+    periodic: wrap, adding -shift / +shift on the low / high side;
+    outflow : odd=False copies the boundary value, odd=True reflects
+              (a_{-m} = 2 a_0 - a_m, a_{N-1+m} = 2 a_{N-1} - a_{N-1-m}).
+    """
+    a = np.moveaxis(a, axis, -1)
+    n = a.shape[-1]
+    if bc == PERIODIC:
+        lo = a[..., n - g:] - shift
+        hi = a[..., :g] + shift
+    elif odd:
+        lo = 2.0 * a[..., :1] - a[..., g:0:-1]
+        hi = 2.0 * a[..., -1:] - a[..., -2:-2 - g:-1]
+    else:
+        lo = np.repeat(a[..., :1], g, axis=-1)
+        hi = np.repeat(a[..., -1:], g, axis=-1)
+    out = np.concatenate([lo, a, hi], axis=-1)
+    return np.moveaxis(out, -1, axis)
+
+
+def axis_of(k, dim):
+    """Array axis of direction xi_k (k = 0 is xi_1, the last axis)."""
+    return dim - 1 - k
+
+
+def pad_coords(sch, x, g):
+    """Coordinates with g ghosts in every direction (corners included)."""
+    out = x
+    for k in range(sch.dim):
+        comps = []
+        for c in range(sch.dim):
+            shift = sch.period[k] if (c == k and sch.bc[k] == PERIODIC) else 0.0
+            comps.append(pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], shift=shift, odd=True))
+        out = np.stack(comps)
+    return out
+
+
+def pad_velocity(sch, xdot, g):
+    """Mesh velocity with g ghosts: the linear part of the coordinate extension."""
+    out = xdot
+    for k in range(sch.dim):
+        out = np.stack([pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], odd=True)
+                        for c in range(sch.dim)])
+    return out
+
+
+# ------------------------------------------------------------------ metrics
+
+def central_difference(a, axis, w):
+    """delta_k[a]_i = 1/2 sum_m alpha_{w,m} (a_{i+m} - a_{i-m}) (Sec. 3.2, after eq. SCLCoeff).
+
+    Returns values for the nodes that have w neighbours on both sides.
+    """
+    al = ec_alphas(w)
+    a = np.moveaxis(a, axis, -1)
+    n = a.shape[-1]
+    out = np.zeros(a.shape[:-1] + (n - 2 * w,))
+    for m in range(1, w + 1):
+        out += 0.5 * float(al[m - 1]) * (a[..., w + m:n - w + m] - a[..., w - m:n - w - m])
+    return np.moveaxis(out, -1, axis)
+
+
+def node_jacobian(sch, x):
+    """J = det d(x)/d(xi) at the nodes from the same delta_k (initial J; eq. ConserLaw_curv)."""
+    w = sch.w
+    xp = pad_coords(sch, x, w)
+    if sch.dim == 1:
+        return central_difference(xp[0], 0, w) / sch.dxi[0]
+    dx = {}
+    for k in range(2):
+        ax = axis_of(k, 2)
+        for c in range(2):
+            dx[(c, k)] = _trim(central_difference(xp[c], ax, w), 1 - ax, w) / sch.dxi[k]
+    return dx[(0, 0)] * dx[(1, 1)] - dx[(0, 1)] * dx[(1, 0)]
+
+
+def _trim(a, axis, t):
+    """Drop t nodes from both ends of `axis`."""
+    if t == 0:
+        return a
+    a = np.moveaxis(a, axis, 0)[t:a.shape[axis] - t]
+    return np.moveaxis(a, 0, axis)
+
+
+def direction_metrics(sch, x, xdot, k, g=3):
+    """Node metrics of direction xi_k on the nodes of the k-lines with g ghosts along xi_k.
+
+    Returns (n, xt): n has shape (d, ...) = (J dxi_k/dx_1, ..., J dxi_k/dx_d) and
+    xt = J dxi_k/dt = -sum_j xdot_j J dxi_k/dx_j (eq. VCLCoeff).  The grid of
+    the result is the interior extended by g nodes along xi_k only.
+
+    2D (degenerate form of eq. SCLCoeff):
+      J dxi_1/dx = ( delta_2[x_2], -delta_2[x_1]) / dxi_2
+      J dxi_2/dx = (-delta_1[x_2],  delta_1[x_1]) / dxi_1
+    1D: J dxi/dx = 1.
+    """
+    dim = sch.dim
+    w = sch.w
+    xd = pad_velocity(sch, xdot, g)
+    if dim == 1:
+        n = np.ones((1,) + xd.shape[1:])
+        xt = -xd[0]
+        return n, xt
+    o = 1 - k                       # the other direction
+    oax = axis_of(o, 2)
+    ax = axis_of(k, 2)
+    P = max(g, w)
+    xp = pad_coords(sch, x, P)      # P ghosts along both directions
+    # derivative along xi_o; keep g ghosts along xi_k and none along xi_o
+    dxo = [_trim(_trim(central_difference(xp[c], oax, w), oax, P - w), ax, P - g) / sch.dxi[o]
+           for c in range(2)]
+    if k == 0:
+        n = np.stack([dxo[1], -dxo[0]])
+    else:
+        n = np.stack([-dxo[1], dxo[0]])
+    xdk = np.stack([_trim(xd[c], oax, g) for c in range(2)])
+    xt = -np.sum(xdk * n, axis=0)
+    return n, xt
+
+
+# ------------------------------------------------------------ eigen-system
+
+def rotate(vec, c, s, inverse=False):
+    """Apply T (or T^{-1} = T^T) to the momentum slots of a (4, ...) vector."""
+    out = vec.copy()
+    if inverse:
+        out[1] = c * vec[1] - s * vec[2]
+        out[2] = s * vec[1] + c * vec[2]
+    else:
+        out[1] = c * vec[1] + s * vec[2]
+        out[2] = -s * vec[1] + c * vec[2]
+    return out
+
+
+def face_state(gas, rho_l, v_l, p_l, rho_r, v_r, p_r):
+    """Averaged face state (Sec. 3.3): rho = {rho}^ln, v = {v}, p = {rho}^ln / {rho/p}^ln."""
+    rho = log_mean(rho_l, rho_r)
+    v = mean(v_l, v_r)
+    p = rho / log_mean(rho_l / p_l, rho_r / p_r)
+    return rho, v, p
+
+
+def scaled_eigenvectors(gas, rho, vn, vt, p):
+    """R = R~ S for the x_1-flux Jacobian at a (rotated) state (Sec. 3.3, eq. eigen).
+
+    Columns of R~ (general units): (1, v_n - c, [v_t], H - v_n c), (1, v_n, [v_t], H - c^2 rho/p_e),
+    [(0, 0, 1, v_t)], (1, v_n + c, [v_t], H + v_n c), with p_e = rho delta/(1 - b rho)
+    and H = (E + p)/rho.  S^2 = diag(rho T/(2c^2), R delta rho T^2/((R T - 2 a rho (1 - b rho)^2) c^2),
+    [rho T], rho T/(2 c^2)) -- the reduced-unit S of Sec. 3.3 in general units.
+    vt is None in 1D.  Returns (R, c) with R of shape (d+2, d+2, ...).
+    """
+    g = gas
+    T = thermo.temperature(g, rho, p)
+    c2 = thermo.sound_speed2(g, rho, T)
+    c = np.sqrt(c2)
+    v2 = vn**2 + (0.0 if vt is None else vt**2)
+    E = rho * thermo.internal_energy(g, rho, T) + 0.5 * rho * v2
+    H = (E + p) / rho
+    mid = H - c2 * (1.0 - g.b * rho) / g.delta
+    s_ac = rho * T / (2.0 * c2)
+    s_en = g.R * g.delta * rho * T**2 / ((g.R * T - 2.0 * g.a * rho * (1.0 - g.b * rho) ** 2) * c2)
+    one = np.ones_like(rho)
+    zero = np.zeros_like(rho)
+    if vt is None:
+        cols = [np.stack([one, vn - c, H - vn * c]),
+                np.stack([one, vn, mid]),
+                np.stack([one, vn + c, H + vn * c])]
+        scal = [s_ac, s_en, s_ac]
+    else:
+        cols = [np.stack([one, vn - c, vt, H - vn * c]),
+                np.stack([one, vn, vt, mid]),
+                np.stack([zero, zero, one, vt]),
+                np.stack([one, vn + c, vt, H + vn * c])]
+        scal = [s_ac, s_en, rho * T, s_ac]
+    R = np.stack([col * np.sqrt(sc) for col, sc in zip(cols, scal)], axis=1)
+    return R, c
+
+
+# ---------------------------------------------------------- direction flux
+
+def _line_view(a, ax):
+    """Move the xi_k axis of a (component-leading) field to the end."""
+    return np.moveaxis(a, 1 + ax, -1)
+
+
+def direction_fluxes(sch, U_pad, n, xt, V_pad):
+    """ES face fluxes of direction xi_k at the faces i+1/2, i = -1 .. N-1.
+
+    U_pad, V_pad: (d+2, ..., N+6) with the xi_k axis last, 3 ghosts each side;
+    n: (d, ..., N+6) node metrics J dxi_k/dx_j; xt: (..., N+6) node J dxi_k/dt.
+    Returns (F_U, F_J) with shapes (d+2, ..., N+1) and (..., N+1).
+    """
+    g = sch.gas
+    d = sch.dim
+    w = sch.w
+    al = [float(a) for a in ec_alphas(w)]
+    N = U_pad.shape[-1] - 6
+    rho, v, T, p = thermo.cons_to_prim(g, U_pad)
+
+    F_U = np.zeros(U_pad.shape[:-1] + (N + 1,))
+    F_J = np.zeros(xt.shape[:-1] + (N + 1,))
+    # face i+1/2 for i = -1..N-1 has padded index ip = i + 3 = 2 .. N+2
+    ip = np.arange(2, N + 3)
+    for m in range(1, w + 1):
+        for s in range(m):
+            lft = ip - s
+            rgt = ip - s + m
+            Ut, Ft = ec_flux(g, rho[..., lft], v[..., lft], T[..., lft],
+                             rho[..., rgt], v[..., rgt], T[..., rgt])
+            xt_m = mean(xt[..., lft], xt[..., rgt])
+            pair = xt_m * Ut
+            for j in range(d):
+                pair = pair + mean(n[j][..., lft], n[j][..., rgt]) * Ft[j]
+            F_U += al[m - 1] * pair
+            F_J += al[m - 1] * xt_m
+    if not sch.dissipation:
+        return F_U, F_J
+
+    # ---- ES dissipation, eq. HOstable
+    il, ir = ip, ip + 1
+    rho_f, v_f, p_f = face_state(g, rho[..., il], v[..., il], p[..., il],
+                                 rho[..., ir], v[..., ir], p[..., ir])
+    nf = np.stack([mean(n[j][..., il], n[j][..., ir]) for j in range(d)])
+    xtf = mean(xt[..., il], xt[..., ir])
+    L = np.sqrt(np.sum(nf**2, axis=0))
+    if d == 1:
+        cth, sth = nf[0] / L, None
+        vn = v_f[0] * cth
+        vt = None
+    else:
+        cth, sth = nf[0] / L, nf[1] / L
+        vn = cth * v_f[0] + sth * v_f[1]
+        vt = -sth * v_f[0] + cth * v_f[1]
+    R, c = scaled_eigenvectors(g, rho_f, vn, vt, p_f)
+    Lam = np.abs(xtf + L * vn) + L * c          # max_m |J xi_t + L lambda_m|
+
+    def project(j_off):
+        Vj = V_pad[..., ip + j_off]
+        TV = Vj if d == 1 else rotate(Vj, cth, sth)     # T = I in 1D
+        return np.einsum("ab...,a...->b...", R, TV)   # W = R^T (T V)
+
+    Wst = np.stack([project(o) for o in range(-2, 4)])      # nodes i-2 .. i+3
+    W_minus = mr_weno5(Wst[0:5], sch.weno_gammas, sch.weno_eps)
+    W_plus = mr_weno5(Wst[5:0:-1], sch.weno_gammas, sch.weno_eps)
+    jump_weno = W_plus - W_minus
+    jump = Wst[3] - Wst[2]
+    Y = (np.sign(jump_weno) * np.sign(jump) > 0).astype(np.float64)
+    incr = np.einsum("ab...,b...->a...", R, Y * jump_weno)  # R Y [[W]]
+    if d == 2:
+        incr = rotate(incr, cth, sth, inverse=True)
+    F_U = F_U - 0.5 * Lam * incr
+    return F_U, F_J
+
+
+def rhs(sch, JU, J, x, xdot):
+    """Right-hand sides of eq. semi_U and eq. semi_J: -sum_k (F_{k,+1/2} - F_{k,-1/2}) / dxi_k."""
+    g = sch.gas
+    d = sch.dim
+    U = JU / J
+    dU = np.zeros_like(JU)
+    dJ = np.zeros_like(J)
+    for k in range(d):
+        ax = axis_of(k, d)
+        U_pad = pad(U, 3, 1 + ax, sch.bc[k])
+        V_pad = thermo.entropy_variables(g, U_pad)
+        n, xt = direction_metrics(sch, x, xdot, k, 3)
+        FU, FJ = direction_fluxes(sch, _line_view(U_pad, ax), np.moveaxis(n, 1 + ax, -1),
+                                  np.moveaxis(xt, ax, -1), _line_view(V_pad, ax))
+        divU = (FU[..., 1:] - FU[..., :-1]) / sch.dxi[k]
+        divJ = (FJ[..., 1:] - FJ[..., :-1]) / sch.dxi[k]
+        dU -= np.moveaxis(divU, -1, 1 + ax)
+        dJ -= np.moveaxis(divJ, -1, ax)
+    return dU, dJ
+
+
+def entropy_rate(sch, JU, J, dU, dJ):
+    """Total entropy rate sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt) times the cell volume.
+
+    d(J eta)/dt = V . d(JU)/dt - phi dJ/dt (from eta(U) with U = JU/J and phi = V.U - eta).
+    """
+    U = JU / J
+    V = thermo.entropy_variables(sch.gas, U)
+    phi = thermo.potential(sch.gas, U)
+    vol = float(np.prod(sch.dxi))
+    return vol * float(np.sum(np.sum(V * dU, axis=0) - phi * dJ))

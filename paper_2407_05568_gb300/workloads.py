@@ -1,0 +1,160 @@
+"""Seeded synthetic inputs: primitive fields (rho, v, p), meshes and run settings.
+
+This module holds input recipes only -- no arithmetic of the numerical method.
+Both the CUDA path and the oracle receive the same arrays from here and each
+converts them to conservative variables with its own EOS.
+
+Recipes follow the paper's test problems (Sec. 5): sine waves (Examples 5.1,
+5.3), Riemann problems with the Table 5.1 states, and seeded four-quadrant /
+shock-tube states near the critical point for the larger runs.  Units: the
+reduced van der Waals units with a plain-pressure flux,
+a = 3, b = 1/3, R = 8/3, c_v = R/0.0125, where p = 8 rho T/(3 - rho) - 3 rho^2.
+"""
+import numpy as np
+
+UNITS_A = dict(a=3.0, b=1.0 / 3.0, R=8.0 / 3.0, cv=(8.0 / 3.0) / 0.0125)
+IDEAL_14 = dict(a=0.0, b=0.0, R=1.0, cv=1.0 / 0.4)
+
+# Table 5.1 (Example 5.2): (rho_l, v_l, p_l, rho_r, v_r, p_r)
+TABLE_5_1 = {
+    "RP1": (1.818, 0.0, 3.000, 0.275, 0.0, 0.575),
+    "RP2": (0.879, 0.0, 1.090, 0.562, 0.0, 0.885),
+    "RP3": (0.879, 0.0, 1.090, 0.275, 0.0, 0.575),
+}
+
+
+def _recipe_temperature(rho, p):
+    """Acceptance test of the sampling recipe in the units above (input filter only)."""
+    return (p + 3.0 * rho**2) * (3.0 - rho) / (8.0 * rho)
+
+
+def _recipe_ok(rho, p):
+    """Recipe acceptance region: T > 27/32 and 4T - rho (3 - rho)^2 > 0, 0 < rho < 3."""
+    T = _recipe_temperature(rho, p)
+    return (0.0 < rho < 3.0) and T > 27.0 / 32.0 and 4.0 * T - rho * (3.0 - rho) ** 2 > 0.0
+
+
+def _pair_ok(s1, s2):
+    """Recipe acceptance between two neighbouring states: 4{T} - {rho}(3 - {rho})^2 > 0."""
+    rm = 0.5 * (s1[0] + s2[0])
+    Tm = 0.5 * (_recipe_temperature(s1[0], s1[-1]) + _recipe_temperature(s2[0], s2[-1]))
+    return 4.0 * Tm - rm * (3.0 - rm) ** 2 > 0.0
+
+
+def uniform_nodes(n, lo, hi, periodic):
+    """Node coordinates and spacing: periodic -> n nodes on [lo, hi); else n nodes on [lo, hi]."""
+    if periodic:
+        d = (hi - lo) / n
+        return lo + d * np.arange(n), d
+    d = (hi - lo) / (n - 1)
+    return lo + d * np.arange(n), d
+
+
+def sine_1d(n=200, t_end=0.1, cfl=0.4):
+    """1D periodic density sine wave on a fixed uniform mesh (Example 5.1 setup, fixed mesh):
+    rho = 0.5 + 0.2 sin(2 pi x), v = 1, p = 1 on [0, 1); exact rho(x - t)."""
+    x, d = uniform_nodes(n, 0.0, 1.0, True)
+    return dict(gas=UNITS_A, dim=1, n=(n,), dxi=(d,), bc=("periodic",), period=(1.0,),
+                x=x[None].copy(), rho=0.5 + 0.2 * np.sin(2 * np.pi * x), v=np.ones((1, n)),
+                p=np.ones(n), t_end=t_end, cfl=cfl, moving=False)
+
+
+def sine_2d(n=1024, t_end=0.1, cfl=0.4):
+    """2D periodic sine wave (Example 5.3 setup): rho = 0.5 + 0.2 sin(2 pi (x + y)), v = (0.5, 0.5), p = 1."""
+    x1, d = uniform_nodes(n, 0.0, 1.0, True)
+    X, Yc = np.meshgrid(x1, x1)          # shape (n2, n1), X varies along the last axis
+    return dict(gas=UNITS_A, dim=2, n=(n, n), dxi=(d, d), bc=("periodic", "periodic"),
+                period=(1.0, 1.0), x=np.stack([X, Yc]),
+                rho=0.5 + 0.2 * np.sin(2 * np.pi * (X + Yc)),
+                v=np.stack([0.5 * np.ones_like(X), 0.5 * np.ones_like(X)]),
+                p=np.ones_like(X), t_end=t_end, cfl=cfl, moving=False)
+
+
+def quadrant_states(seed):
+    """Four seeded admissible states near the critical point:
+    rho in [0.4, 1.6], p in [0.6, 1.4], |v| <= 0.5 (uniform in the disc), rejection-sampled
+    for the recipe acceptance region and for every pair of neighbouring quadrants."""
+    rng = np.random.default_rng(seed)
+    while True:
+        st = []
+        while len(st) < 4:
+            rho = rng.uniform(0.4, 1.6)
+            p = rng.uniform(0.6, 1.4)
+            r = 0.5 * np.sqrt(rng.uniform())
+            th = rng.uniform(0.0, 2.0 * np.pi)
+            if _recipe_ok(rho, p):
+                st.append((rho, r * np.cos(th), r * np.sin(th), p))
+        # quadrants: 0 = (x>.5,y>.5), 1 = (x<.5,y>.5), 2 = (x<.5,y<.5), 3 = (x>.5,y<.5)
+        if all(_pair_ok(st[i], st[(i + 1) % 4]) for i in range(4)):
+            return st
+
+
+def riemann_2d(n=200, seed=0, t_end=0.2, cfl=0.4, moving=True):
+    """2D four-quadrant vdW Riemann problem on [0,1]^2 with outflow boundaries and an
+    adaptive moving mesh (monitor with rho and G, alpha = (1200, 1200, 1200), 5 filter
+    passes, 5 Jacobi sweeps)."""
+    x1, d = uniform_nodes(n, 0.0, 1.0, False)
+    X, Yc = np.meshgrid(x1, x1)
+    st = quadrant_states(seed)
+    q = np.where(X > 0.5, np.where(Yc > 0.5, 0, 3), np.where(Yc > 0.5, 1, 2))
+    tab = np.array(st)                    # (4, 4): rho, vx, vy, p
+    rho = tab[q, 0]
+    v = np.stack([tab[q, 1], tab[q, 2]])
+    p = tab[q, 3]
+    return dict(gas=UNITS_A, dim=2, n=(n, n), dxi=(d, d), bc=("outflow", "outflow"),
+                period=(1.0, 1.0), x=np.stack([X, Yc]), rho=rho, v=v, p=p,
+                t_end=t_end, cfl=cfl, moving=moving,
+                mesh=dict(monitor="vdw", alphas=(1200.0, 1200.0, 1200.0), kappa=2,
+                          filter_passes=5, sweeps=5, eps=0.0))
+
+
+def riemann_1d(name="RP1", n=100, moving=True, t_end=None, cfl=0.4):
+    """1D Riemann problem of Table 5.1 on [0, 1], interface at 0.5, outflow boundaries
+    (Example 5.2; the paper's final times are given in its reduced units)."""
+    rl, vl, pl, rr, vr, pr = TABLE_5_1[name]
+    x, d = uniform_nodes(n, 0.0, 1.0, False)
+    left = x < 0.5
+    alphas = (1200.0, 3000.0, 5000.0) if name in ("RP1", "RP2") else (1200.0, 1200.0, 1200.0)
+    return dict(gas=UNITS_A, dim=1, n=(n,), dxi=(d,), bc=("outflow",), period=(1.0,),
+                x=x[None].copy(), rho=np.where(left, rl, rr), v=np.where(left, vl, vr)[None],
+                p=np.where(left, pl, pr), t_end=0.1 if t_end is None else t_end, cfl=cfl,
+                moving=moving,
+                mesh=dict(monitor="vdw", alphas=alphas, kappa=2, filter_passes=5,
+                          sweeps=10, eps=0.0))
+
+
+def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0):
+    """Ideal-gas (gamma = 1.4) isentropic vortex on [0,10]^2, periodic, mean flow (1, 1)
+    (Shu 1998): dT = -(gamma-1) eps^2 e^(1-r^2) / (8 gamma pi^2),
+    dv = eps/(2 pi) e^((1-r^2)/2) (-ybar, xbar), rho = T^(1/(gamma-1)), p = rho T."""
+    gam = 1.4
+    x1, d = uniform_nodes(n, 0.0, 10.0, True)
+    X, Yc = np.meshgrid(x1, x1)
+    xb = X - 5.0
+    yb = Yc - 5.0
+    r2 = xb**2 + yb**2
+    T = 1.0 - (gam - 1.0) * eps_v**2 * np.exp(1.0 - r2) / (8.0 * gam * np.pi**2)
+    rho = T ** (1.0 / (gam - 1.0))
+    fac = eps_v / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
+    v = np.stack([1.0 - fac * yb, 1.0 + fac * xb])
+    return dict(gas=IDEAL_14, dim=2, n=(n, n), dxi=(d, d), bc=("periodic", "periodic"),
+                period=(10.0, 10.0), x=np.stack([X, Yc]), rho=rho, v=v, p=rho * T,
+                t_end=t_end, cfl=cfl, moving=False)
+
+
+def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345):
+    """Batched 1D shock tubes on [0, 1], interface at 0.5, outflow boundaries.
+    Lengths ~ U{lmin..lmax}; left/right states rho in [0.2, 2.5], p in [0.3, 2], v in [-1, 1],
+    rejection-sampled for the recipe acceptance region and between the two states."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(lmin, lmax + 1, size=nprob)
+    states = np.empty((nprob, 6))
+    for i in range(nprob):
+        while True:
+            rl, rr = rng.uniform(0.2, 2.5, 2)
+            pl, pr = rng.uniform(0.3, 2.0, 2)
+            vl, vr = rng.uniform(-1.0, 1.0, 2)
+            if _recipe_ok(rl, pl) and _recipe_ok(rr, pr) and _pair_ok((rl, pl), (rr, pr)):
+                break
+        states[i] = (rl, vl, pl, rr, vr, pr)
+    return dict(gas=UNITS_A, lengths=lengths, states=states)
