@@ -1,0 +1,344 @@
+"""Benchmark: cell-updates/s per RK stage of the ES van der Waals moving-mesh scheme on GB300.
+
+Workload (default): the 2D four-quadrant van der Waals Riemann problem on an
+adaptive moving mesh, 200 x 200 nodes, outflow boundaries, seeded states near
+the critical point, monitor with the fundamental derivative (alpha = 1200 x 3,
+5 filter passes, 5 Jacobi sweeps), SSP-RK3 at CFL 0.4, FP64.  One step = the
+whole hot path: CFL time step, mesh redistribution, three fused RK stages.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+The reference arm (--impl reference) times the plain FP64 CPU oracle on the
+same workload on the host cores.  Multi-GPU runs (torchrun) are independent
+replicas (the hot path has no cross-rank exchange here); value = all ranks'
+cell updates / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage"
+RESTART_EVERY = 40          # steps; the state restarts from t = 0 (outside the timed region)
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=200)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n):
+    from paper_2407_05568_gb300 import workloads as wl
+    w = wl.riemann_2d(n, seed=0)
+    w["t_end"] = 1e30        # steps are the unit of work; restarts keep the run on the t <= 0.2 solution
+    return w
+
+
+def config(n, precision, flush):
+    return {"workload": f"2D vdW four-quadrant Riemann problem, adaptive moving mesh, {n}x{n} nodes, "
+                        f"monitor with G, 5 filter passes, 5 Jacobi sweeps, SSP-RK3 CFL 0.4",
+            "nodes": n * n, "rk_stages_per_step": 3, "precision_form": precision,
+            "l2": flush, "restart_every_steps": RESTART_EVERY}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_state(w):
+    from oracle import operator as op
+    from oracle import stepper, thermo
+    g = thermo.Gas(**w["gas"])
+    sch = op.Scheme(gas=g, dim=w["dim"], bc=w["bc"], dxi=w["dxi"], period=w["period"])
+    J = op.node_jacobian(sch, w["x"])
+    JU = thermo.prim_to_cons(g, w["rho"], w["v"], w["p"]) * J
+    mc = stepper.MeshControl(moving=True, **w["mesh"])
+    return sch, mc, JU, J, w["x"].copy()
+
+
+def time_oracle(w, nsteps):
+    """Oracle steps from t = 0; returns (seconds, steps)."""
+    from oracle import stepper
+    sch, mc, JU, J, x = oracle_state(w)
+    t = 0.0
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        JU, J, x, t, _ = stepper.step(sch, mc, JU, J, x, t, 1e30, w["cfl"])
+    return time.perf_counter() - t0, nsteps
+
+
+def cpu_cores():
+    return 1   # numpy element-wise kernels run on one thread; no BLAS on this path
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.n)
+    nodes = args.n * args.n
+    time_oracle(w, max(0, min(args.warmup, 1)))
+    sec, k = time_oracle(w, args.steps)
+    value = nodes * 3 * k / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": config(args.n, "fp64", "host"),
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{k} full steps of the {args.n}x{args.n} workload from t = 0"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_05568_gb300 import build, es
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    w = workload(args.n)
+    nodes = args.n * args.n
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = es.es_create(es.make_params(w, precision=args.precision), stream)
+        x0 = torch.tensor(w["x"], dtype=torch.float64, device=dev)
+        J0 = torch.empty(w["x"].shape[1:], dtype=torch.float64, device=dev)
+        es.es_init_mesh(ctx, x0, J0)
+        JU0 = torch.empty((4,) + w["x"].shape[1:], dtype=torch.float64, device=dev)
+        es.es_prim_to_cons(ctx, torch.tensor(w["rho"], device=dev), torch.tensor(w["v"], device=dev),
+                           torch.tensor(w["p"], device=dev), J0, JU0)
+        JU, J, x = JU0.clone(), J0.clone(), x0.clone()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream.synchronize()
+
+    def restart():
+        with torch.cuda.stream(stream):
+            JU.copy_(JU0)
+            J.copy_(J0)
+            x.copy_(x0)
+        stream.synchronize()
+        es.es_set_time(ctx, 0.0)
+
+    restart()
+    done = 0
+    for _ in range(args.warmup):
+        es.es_steps(ctx, JU, J, x, 1, w["t_end"])
+        done += 1
+    stream.synchronize()
+    rc = es.es_check(ctx)
+    if rc:
+        raise RuntimeError(es.es_last_error(ctx))
+
+    # ---- device-timed region: K steps, L2 flushed before each (outside the events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launches
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            if done and done % RESTART_EVERY == 0:
+                restart()
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                starts[k].record(stream)
+            es.es_steps(ctx, JU, J, x, 1, w["t_end"])
+            ends[k].record(stream)
+            done += 1
+        torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    rc = es.es_check(ctx)
+    if rc:
+        raise RuntimeError(es.es_last_error(ctx))
+    value = world * nodes * 3 / (ms * 1e-3)
+
+    # ---- dominant kernel: the fused stage kernel, timed alone on the same stream
+    roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, args.precision)
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    hJU = np.ascontiguousarray(JU0.cpu().numpy())
+    hJ = np.ascontiguousarray(J0.cpu().numpy())
+    hx = np.ascontiguousarray(x0.cpu().numpy())
+    hJU, hJ, hx = (pin(a) for a in (hJU, hJ, hx))
+    es.es_set_time(ctx, 0.0)
+    es.es_run_host(ctx, hJU, hJ, hx, 1, w["t_end"])          # warm (captures the host-buffer graph)
+    e2e_t = []
+    for k in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        es.es_run_host(ctx, hJU, hJ, hx, 1, w["t_end"])
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    bytes_io = (hJU.nbytes + hJ.nbytes + hx.nbytes)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+                "data": "synthetic", "config": config(args.n, args.precision,
+                                                      "flushed before each timed step (512 MB write)"),
+                "roofline": roof, "clocks": clk.summary(), "gpu_launches": int(launches),
+                "e2e": {"value": world * nodes * 3 / e2e_s, "unit": "cell-updates/s",
+                        "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}}
+        if not args.no_cpu_baseline:
+            sec, k = time_oracle(w, 8)
+            line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),
+                                    "kind": "oracle",
+                                    "sample": f"{k} full steps of the same {args.n}x{args.n} workload from t = 0"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def pin(a):
+    import torch
+    t = torch.from_numpy(a).pin_memory()
+    return t.numpy()
+
+
+# Algorithmic FP64 operations per node and RK stage of the fused stage kernel
+# (+, -, *, / and sqrt/log each one operation; an FMA two), counted from the
+# formulas the kernel evaluates; derivation in the design notes.
+FLOPS_PER_NODE_STAGE_2D = None
+
+
+def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision):
+    """Average duration of the stage kernel (stage 2 form) over 20 launches on the bench stream."""
+    import torch
+    S1 = torch.empty_like(JU)
+    S1J = torch.empty_like(J)
+    xdot = torch.zeros_like(x)
+    dt = 1e-4
+    reps = 20
+    for _ in range(3):
+        es.es_rk_stage(ctx, 2, dt, JU, J, JU, J, x, xdot, S1, S1J)
+    st = torch.cuda.Event(enable_timing=True)
+    en = torch.cuda.Event(enable_timing=True)
+    st.record(stream)
+    for _ in range(reps):
+        es.es_rk_stage(ctx, 2, dt, JU, J, JU, J, x, xdot, S1, S1J)
+    en.record(stream)
+    en.synchronize()
+    ms = st.elapsed_time(en) / reps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    from paper_2407_05568_gb300 import perfmodel
+    flops = perfmodel.stage_flops(dim=2, nodes=nodes, precision=precision)
+    peak = perfmodel.fp64_peak_tflops(peaks) if precision == "fp64" else perfmodel.fp32_peak_tflops(peaks)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "stage_kernel_fp64<2,32,8>" if precision == "fp64" else "stage_kernel_mixed",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "launch_ms": ms, "flops_per_launch": flops,
+            "peak_source": "nominal FP64 rate of GB300 from the recipe (1.25 TFLOP/s); not in MEASURED_PEAKS.json"
+            if precision == "fp64" else "FP32 rate from SM count x 128 lanes x 2 x max clock"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,157 @@
+/*
+ * es_vdw.h -- C ABI of the GB300 (sm_103a) library for the high-order
+ * entropy-stable finite-difference scheme for the Euler equations with the
+ * van der Waals equation of state on an adaptive moving mesh
+ * (Li & Tang, arXiv:2407.05568).
+ *
+ * Data layout (all calls)
+ *   Node-centred fields on a logically rectangular n1 x n2 mesh (n2 = 1 in 1D),
+ *   structure of arrays, xi_1 fastest:  field[c][j][i] at c*n1*n2 + j*n1 + i.
+ *     JU : (dim + 2) components (rho, rho v_1, [rho v_2], E) times J, double
+ *     J  : 1 component, double
+ *     x  : dim components (x_1, [x_2]) of the node coordinates, double
+ *     xdot : dim components of the mesh velocity, double
+ *   The computational mesh is uniform with spacings dxi[k]; x(xi) maps it to
+ *   the physical mesh (Sec. 3, eq. transf).
+ *
+ * Pointers
+ *   Every array argument is a DEVICE pointer (cudaMalloc'd or a PyTorch
+ *   tensor's storage) owned by the caller, except where a name ends in _host.
+ *   The library never frees caller memory.  The context owns its scratch.
+ *
+ * Streams and errors
+ *   Calls are asynchronous on the context's stream.  The return value reports
+ *   argument and launch errors only (ES_OK = 0).  Errors found on the device
+ *   (an inadmissible state, a folded mesh) latch in a device word read by
+ *   es_check(), which synchronises the stream.  es_last_error() gives the text.
+ */
+#ifndef ES_VDW_H
+#define ES_VDW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ES_OK               0
+#define ES_ERR_ARG          1   /* bad argument (size, null pointer, unsupported option) */
+#define ES_ERR_CUDA         2   /* a CUDA runtime call failed */
+#define ES_ERR_INADMISSIBLE 3   /* eq. coefflimit / Theorem 3.1 violated at some node or face */
+#define ES_ERR_MESH         4   /* J <= 0 or the mesh folded */
+#define ES_ERR_TIMEOUT      5   /* a bounded device wait ran out */
+
+/* boundary conditions, per direction */
+#define ES_BC_PERIODIC 0        /* wrap; coordinates shifted by period[k] */
+#define ES_BC_OUTFLOW  1        /* state copied; coordinates reflected; boundary nodes fixed */
+
+/* arithmetic of the operator */
+#define ES_PREC_FP64   0        /* every step in double */
+#define ES_PREC_MIXED  1        /* flux / WENO / RK bulk in float, critical steps in double */
+
+/* monitor functions of Sec. 4 / Example 5.1 */
+#define ES_MONITOR_VDW    0     /* eq. van der Waalsmonitor: delta_1 = rho, delta_2 = G, plus |Delta G|^2 */
+#define ES_MONITOR_SMOOTH 1     /* eq. van der Waalssinmonitor: |grad rho| and |Delta rho| */
+
+typedef struct es_params {
+    /* van der Waals gas, Sec. 1 eq. vdWEOS: p = rho R T/(1 - b rho) - a rho^2, e = cv T - a rho.
+       a = b = 0 is the ideal gas. */
+    double a, b, R, cv;
+    int    dim;             /* 1 or 2 */
+    int    n1, n2;          /* nodes per direction; n2 = 1 when dim = 1; each >= 8 */
+    double dxi[2];          /* computational spacings Delta xi_k */
+    double period[2];       /* period of x_k along a periodic direction */
+    int    bc[2];           /* ES_BC_* per direction */
+    double weno_gamma[3];   /* MR-WENO5 linear weights (1-point, 3-point, 5-point), Sec. 5: (0.005, 0.045, 0.95) */
+    double weno_eps;        /* smoothness regulariser (paper silent; 1e-12) */
+    double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| <= sign_tol (|W_i| + |W_{i+1}|)
+                               is round-off of a zero jump and has sign 0 (1e-12 in FP64) */
+    int    dissipation;     /* 1: ES flux eq. HOstable; 0: the EC flux alone */
+    double cfl;             /* eq. cfl; 0.4 in 1D/2D */
+    double dt_fixed;        /* > 0: use this Delta t instead of eq. cfl (Example 5.1 uses CFL dxi^(5/3)) */
+    int    moving;          /* 1: adaptive moving mesh (Sec. 4) */
+    int    monitor;         /* ES_MONITOR_* */
+    int    kappa;           /* number of gradient terms of the vdW monitor (1: rho; 2: rho and G) */
+    double alpha[4];        /* monitor weights alpha_1 .. alpha_{kappa+1} */
+    int    filter_passes;   /* low-pass filter passes (Sec. 4) */
+    int    jacobi_sweeps;   /* mu: maximum Jacobi sweeps (Sec. 4) */
+    double jacobi_eps;      /* stop when max |x^[nu+1] - x^[nu]| < eps; 0 = exactly mu sweeps */
+    int    precision;       /* ES_PREC_* */
+} es_params;
+
+typedef struct es_ctx es_ctx;
+
+/* Create a context for one mesh size and parameter set on the current device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Allocates the
+ * scratch it needs (a few fields of the mesh size).  Returns ES_ERR_ARG for
+ * unsupported sizes or options. */
+int es_create(es_ctx** ctx, const es_params* p, void* stream);
+void es_destroy(es_ctx* ctx);
+
+/* Initial metric Jacobian J = det dx/dxi at the nodes, from the same 6th-order
+ * central differences delta_k used by the metrics (Sec. 3.2, eq. SCLCoeff).
+ * x: [dim][n2][n1] in, J: [n2][n1] out. */
+int es_init_mesh(es_ctx* ctx, const double* x, double* J);
+
+/* Conservative variables JU = J (rho, rho v, E) from primitive (rho, v, p)
+ * (Sec. 1, eq. ConserLaw2 with E = rho e + rho |v|^2/2, T from eq. vdWEOS).
+ * rho, p: [n2][n1]; v: [dim][n2][n1]; J: [n2][n1]; JU out: [dim+2][n2][n1]. */
+int es_prim_to_cons(es_ctx* ctx, const double* rho, const double* v, const double* p,
+                    const double* J, double* JU);
+
+/* Semi-discrete operator alone (eq. semi_U, eq. semi_J):
+ *   dJU = -sum_k (F_{k,+1/2} - F_{k,-1/2}) / dxi_k,  dJ likewise with the J xi_t fluxes,
+ * with the 6th-order EC flux (eq. ECFlux_curv_2p, GCL_flux), the metrics of the
+ * mesh x moving with velocity xdot (eq. SCLCoeff, VCLCoeff) and, when
+ * p->dissipation, the ES dissipation (eq. HOstable).  All device arrays. */
+int es_rhs(es_ctx* ctx, const double* JU, const double* J, const double* x, const double* xdot,
+           double* dJU, double* dJ);
+
+/* One SSP-RK3 stage (Shu-Osher form, stage = 1, 2, 3):
+ *   (JU, J)_out = a_s (JU, J)_n + b_s ((JU, J)_s + dt L(JU_s, J_s; x_s)),
+ * (a, b) = (0, 1), (3/4, 1/4), (1/3, 2/3); the operator is evaluated on the stage
+ * mesh x_s = xn + c_s dt xdot with c = (0, 1, 1/2).  JUn/Jn are read only at the
+ * node itself, so JU_out may alias JUn (but not JUs). */
+int es_rk_stage(es_ctx* ctx, int stage, double dt,
+                const double* JUn, const double* Jn, const double* JUs, const double* Js,
+                const double* xn, const double* xdot, double* JU_out, double* J_out);
+
+/* Time step of eq. cfl from the current mesh with zero mesh velocity; writes the host double. */
+int es_cfl_dt(es_ctx* ctx, const double* JU, const double* J, const double* x, double* dt_host);
+
+/* Mesh redistribution of Sec. 4 for a step of size dt: monitor (with G) ->
+ * filter passes -> Jacobi sweeps from xn -> limiter Delta_gamma -> mesh velocity
+ * xdot = Delta_gamma (x^[mu] - xn)/dt.  Writes xdot (device) and, if non-null,
+ * the sweeps taken and Delta_gamma (host; this synchronises the stream). */
+int es_mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, const double* xn,
+                         double dt, double* xdot, int* sweeps_host, double* gamma_host);
+
+/* Advance the caller's state (JU, J, x) in place by nsteps full steps
+ * (Delta t from eq. cfl or dt_fixed, clipped to t_end; mesh redistribution when
+ * moving; three RK stages; x += dt xdot).  The time t lives on the device:
+ * es_set_time / es_get_time move it.  Steps after t reaches t_end are no-ops.
+ * Launches a CUDA graph per step once the first step has been captured. */
+int es_steps(es_ctx* ctx, double* JU, double* J, double* x, int nsteps, double t_end);
+int es_set_time(es_ctx* ctx, double t);
+int es_get_time(es_ctx* ctx, double* t_host, double* last_dt_host);   /* synchronises */
+
+/* End-to-end form for callers holding HOST arrays: copies JU_host, J_host,
+ * x_host to context-owned device buffers, runs es_steps, copies them back and
+ * synchronises.  Same layouts as the device arrays. */
+int es_run_host(es_ctx* ctx, double* JU_host, double* J_host, double* x_host, int nsteps,
+                double t_end);
+
+/* Synchronise and return the latched device status (ES_OK or ES_ERR_*);
+ * clears it.  es_last_error writes a message (with the first failing node). */
+int es_check(es_ctx* ctx);
+int es_last_error(es_ctx* ctx, char* buf, int len);
+
+/* Number of kernel launches the library has issued (graph launches count
+ * their kernels), for launch accounting. */
+int64_t es_launch_count(es_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ES_VDW_H */

@@ -18,7 +18,10 @@ Readings of points the paper leaves open (each listed in the design notes):
   * the rotation angle theta is taken with the quadrant of (n_1, n_2), i.e.
     cos(theta) = n_1/L, sin(theta) = n_2/L;
   * the sign switch Y compares [[W]]^WENO at face i+1/2 with the plain jump
-    W_{i+1} - W_i at the same face.
+    W_{i+1} - W_i at the same face; a plain jump no larger than sign_tol
+    (1e-12) times |W_i| + |W_{i+1}| is round-off of an exactly zero jump and
+    has sign 0 (so Y = 0), which keeps the switch from turning on or off on
+    the last bits of equal states.
 """
 from dataclasses import dataclass, field
 from fractions import Fraction
@@ -43,6 +46,7 @@ class Scheme:
     w: int = 3                                   # EC order 2w (eq. ECFlux_curv_2p)
     weno_gammas: tuple = (0.005, 0.045, 0.95)    # (1-pt, 3-pt, 5-pt) linear weights (Sec. 5)
     weno_eps: float = 1e-12
+    sign_tol: float = 1e-12                      # |[[W]]| below this relative size counts as 0 in Y
     dissipation: bool = True                     # False: the EC scheme alone
     bc: tuple = (PERIODIC,)                      # per direction xi_1, xi_2
     dxi: tuple = (1.0,)                          # Delta xi_k
@@ -319,6 +323,8 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
     W_plus = mr_weno5(Wst[5:0:-1], sch.weno_gammas, sch.weno_eps)
     jump_weno = W_plus - W_minus
     jump = Wst[3] - Wst[2]
+    # a plain jump within round-off of its endpoints counts as zero (sign 0)
+    jump = np.where(np.abs(jump) <= sch.sign_tol * (np.abs(Wst[3]) + np.abs(Wst[2])), 0.0, jump)
     Y = (np.sign(jump_weno) * np.sign(jump) > 0).astype(np.float64)
     incr = np.einsum("ab...,b...->a...", R, Y * jump_weno)  # R Y [[W]]
     if d == 2:

@@ -1,0 +1,359 @@
+// es_aux.cu -- initialisation, time step, and mesh-redistribution kernels.
+//
+// Sec. 3.2: initial J from the metrics' central differences.
+// Sec. 5, eq. cfl: Delta t from the spectral radii (grid-wide max).
+// Sec. 4: monitor with G (eq. van der Waalsmonitor) or the smooth-test monitor
+// (eq. van der Waalssinmonitor), low-pass filter, Jacobi sweeps of the
+// discretised Winslow equation, movement limiter Delta_gamma, mesh velocity.
+#include <cuda_runtime.h>
+
+#include "es_aux.h"
+#include "es_device.cuh"
+
+namespace es {
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ double coord_at(const GridParams& g, const double* x, int gi, int gj, int comp) {
+    const size_t N = size_t(g.n1) * g.n2;
+    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0]);
+    GhostTerms tj;
+    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1]);
+    else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
+    double acc = 0.0;
+    for (int a = 0; a < ti.nterm; ++a)
+        for (int c = 0; c < tj.nterm; ++c)
+            acc += ti.w[a] * tj.w[c] * x[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
+    if (comp == 0) acc += ti.q * g.period[0];
+    if (comp == 1) acc += tj.q * g.period[1];
+    return acc;
+}
+
+// 6th-order central difference delta_k of coordinate `comp` at node (i, j), divided by dxi_k
+__device__ __forceinline__ double dcoord(const GridParams& g, const double* x, int i, int j, int comp, int k) {
+    double s = 0.0;
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        const double h = 0.5 * ec_alpha(m);
+        if (k == 0) s += h * (coord_at(g, x, i + m, j, comp) - coord_at(g, x, i - m, j, comp));
+        else s += h * (coord_at(g, x, i, j + m, comp) - coord_at(g, x, i, j - m, comp));
+    }
+    return s * g.inv_dxi[k];
+}
+
+__device__ __forceinline__ double block_reduce_max(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ double block_reduce_min(double v) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 1e300;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+// ------------------------------------------------------------ init
+__global__ void k_init_J(GridParams g, const double* x, double* J) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        if (g.dim == 1) {
+            J[id] = dcoord(g, x, i, 0, 0, 0);
+        } else {
+            const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
+            const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
+            J[id] = x1 * y2 - x2 * y1;
+        }
+    }
+}
+
+__global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const double* v, const double* p,
+                               const double* J, double* JU) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const double r = rho[id];
+        const double T = (p[id] + G.a * r * r) * (1.0 - G.b * r) / (G.R * r);
+        double ke = 0.0;
+        for (int k = 0; k < g.dim; ++k) ke += v[k * N + id] * v[k * N + id];
+        const double E = r * (G.cv * T - G.a * r) + 0.5 * r * ke;
+        const double Jv = J[id];
+        JU[id] = Jv * r;
+        for (int k = 0; k < g.dim; ++k) JU[(1 + k) * N + id] = Jv * r * v[k * N + id];
+        JU[(1 + g.dim) * N + id] = Jv * E;
+    }
+}
+
+// ------------------------------------------------------------ time step
+__global__ void k_reset(DevScalars* d) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int k = 0; k < 8; ++k) d->red[k] = 0ULL;
+        d->red[RED_GAMMA] = (unsigned long long)__double_as_longlong(1.0);
+        d->sweeps = 0;
+        d->conv = 0;
+    }
+}
+
+// eq. cfl: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), with zero mesh velocity
+__global__ void k_cfl(GridParams g, Gas G, const double* JU, const double* J, const double* x, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    double m = 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        const double iJ = 1.0 / J[id];
+        const double rho = JU[id] * iJ;
+        const double v1 = JU[N + id] * iJ / rho;
+        const double v2 = g.dim == 2 ? JU[2 * N + id] * iJ / rho : 0.0;
+        const double E = JU[(g.dim + 1) * N + id] * iJ;
+        const double T = (E / rho - 0.5 * (v1 * v1 + v2 * v2) + G.a * rho) / G.cv;
+        const double om = 1.0 - G.b * rho;
+        const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
+        const double c = sqrt(fmax(c2, 0.0));
+        double tot;
+        if (g.dim == 1) {
+            tot = (fabs(v1) + c) * iJ * g.inv_dxi[0];
+        } else {
+            const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
+            const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
+            const double a1 = y2, b1 = -x2;          // J dxi_1/dx
+            const double a2 = -y1, b2 = x1;          // J dxi_2/dx
+            tot = (fabs(a1 * v1 + b1 * v2) + sqrt(a1 * a1 + b1 * b1) * c) * iJ * g.inv_dxi[0] +
+                  (fabs(a2 * v1 + b2 * v2) + sqrt(a2 * a2 + b2 * b2) * c) * iJ * g.inv_dxi[1];
+        }
+        if (!(c2 > 0.0)) tot = 1e300;
+        m = fmax(m, tot);
+    }
+    m = block_reduce_max(m);
+    if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_CFL], m);
+}
+
+// Delta t = CFL / max (or the fixed step), clipped to t_end; 0 once t_end is reached
+__global__ void k_dt(DevScalars* d, double cfl, double dt_fixed) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double mx = __longlong_as_double((long long)d->red[RED_CFL]);
+        double dt = dt_fixed > 0.0 ? dt_fixed : cfl / mx;
+        const double left = d->t_end - d->t;
+        if (left <= 1e-14 * fmax(1.0, fabs(d->t_end))) dt = 0.0;
+        else if (dt > left) dt = left;
+        d->dt = dt;
+    }
+}
+
+__global__ void k_set_dt(DevScalars* d, double dt) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) d->dt = dt;
+}
+
+__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    const double dt = d->dt;
+    if (xdot != nullptr && dt != 0.0)
+        for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
+            x[id] += dt * xdot[id];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d->t += dt;
+        d->last_dt = dt;
+    }
+}
+
+// ------------------------------------------------------------ monitor (Sec. 4)
+// density and fundamental derivative G = nu^3 p_nunu|_s / (2 c^2) at the nodes
+__global__ void k_mon_fields(GridParams g, Gas G, const double* JU, const double* J, double* rhoF, double* GF) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const double iJ = 1.0 / J[id];
+        const double rho = JU[id] * iJ;
+        double ke = 0.0;
+        for (int k = 0; k < g.dim; ++k) {
+            const double v = JU[(1 + k) * N + id] * iJ / rho;
+            ke += v * v;
+        }
+        const double E = JU[(g.dim + 1) * N + id] * iJ;
+        const double T = (E / rho - 0.5 * ke + G.a * rho) / G.cv;
+        const double om = 1.0 - G.b * rho;
+        const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
+        const double pnn3 = (1.0 + G.delta) * (2.0 + G.delta) * G.R * T / (om * om * om) - 6.0 * G.a * rho;
+        rhoF[id] = rho;
+        GF[id] = pnn3 / (2.0 * c2);
+    }
+}
+
+__device__ __forceinline__ double field_at(const GridParams& g, const double* f, int i, int j) {
+    const int si = state_index(i, g.n1, g.bc[0]);
+    const int sj = g.dim == 2 ? state_index(j, g.n2, g.bc[1]) : 0;
+    return f[sj * g.n1 + si];
+}
+
+// raw monitor terms and their grid maxima
+__global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, const double* GF, double* t0,
+                            double* t1, double* t2, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        double gr = 0.0, gg = 0.0, lg = 0.0, lr = 0.0;
+        for (int k = 0; k < g.dim; ++k) {
+            const int di = k == 0, dj = k == 1;
+            const double h2 = g.inv_dxi[k];
+            const double rp = field_at(g, rhoF, i + di, j + dj), rm = field_at(g, rhoF, i - di, j - dj);
+            const double r0 = rhoF[id];
+            const double Gp = field_at(g, GF, i + di, j + dj), Gm = field_at(g, GF, i - di, j - dj);
+            const double G0 = GF[id];
+            const double a = (rp - rm) * 0.5 * h2, b = (Gp - Gm) * 0.5 * h2;
+            const double c = (Gp - 2.0 * G0 + Gm) * h2 * h2, e = (rp - 2.0 * r0 + rm) * h2 * h2;
+            gr += a * a;
+            gg += b * b;
+            lg += c * c;
+            lr += e * e;
+        }
+        double v0, v1, v2;
+        if (mp.kind == ES_MONITOR_SMOOTH) {
+            v0 = sqrt(gr);
+            v1 = 0.0;
+            v2 = sqrt(lr);
+        } else {
+            v0 = gr;
+            v1 = mp.kappa >= 2 ? gg : 0.0;
+            v2 = lg;
+        }
+        t0[id] = v0;
+        t1[id] = v1;
+        t2[id] = v2;
+        m0 = fmax(m0, v0);
+        m1 = fmax(m1, v1);
+        m2 = fmax(m2, v2);
+    }
+    m0 = block_reduce_max(m0);
+    m1 = block_reduce_max(m1);
+    m2 = block_reduce_max(m2);
+    if (threadIdx.x == 0) {
+        atomic_max_pos(&d->red[RED_MON0], m0);
+        atomic_max_pos(&d->red[RED_MON1], m1);
+        atomic_max_pos(&d->red[RED_MON2], m2);
+    }
+}
+
+__global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,
+                            const DevScalars* d, double* omega) {
+    const int N = g.n1 * g.n2;
+    const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
+    const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
+    const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
+    const double c0 = M0 > 0.0 ? mp.w0 / M0 : 0.0;
+    const double c1 = M1 > 0.0 ? mp.w1 / M1 : 0.0;
+    const double c2 = M2 > 0.0 ? mp.w2 / M2 : 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
+        omega[id] = sqrt(1.0 + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
+}
+
+// low-pass filter: omega_i <- sum_{j in {0,+-1}^d} (1/2)^(|j|_1 + d) omega_{i+j}
+__global__ void k_filter(GridParams g, const double* in, double* out) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        double s;
+        if (g.dim == 1) {
+            s = 0.25 * field_at(g, in, i - 1, 0) + 0.5 * in[id] + 0.25 * field_at(g, in, i + 1, 0);
+        } else {
+            s = 0.0;
+            for (int dj = -1; dj <= 1; ++dj) {
+                double row = 0.0;
+                for (int di = -1; di <= 1; ++di) {
+                    const double wgt = (di == 0 ? 0.5 : 0.25);
+                    row += wgt * field_at(g, in, i + di, j + dj);
+                }
+                s += (dj == 0 ? 0.5 : 0.25) * row;
+            }
+        }
+        out[id] = s;
+    }
+}
+
+// one Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0
+__global__ void k_jacobi(GridParams g, const double* omega, const double* xin, double* xout, DevScalars* d,
+                         int check) {
+    const int N = g.n1 * g.n2;
+    const bool skip = d->conv != 0;
+    double chg = 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        bool fixed = (g.bc[0] == ES_BC_OUTFLOW && (i == 0 || i == g.n1 - 1));
+        if (g.dim == 2) fixed = fixed || (g.bc[1] == ES_BC_OUTFLOW && (j == 0 || j == g.n2 - 1));
+        if (skip || fixed) {
+            for (int c = 0; c < g.dim; ++c) xout[c * N + id] = xin[c * N + id];
+            continue;
+        }
+        const double w0 = omega[id];
+        double den = 0.0, num[2] = {0.0, 0.0};
+        for (int k = 0; k < g.dim; ++k) {
+            const int di = k == 0, dj = k == 1;
+            const double ih2 = g.inv_dxi[k] * g.inv_dxi[k];
+            const double wp = 0.5 * (w0 + field_at(g, omega, i + di, j + dj)) * ih2;
+            const double wm = 0.5 * (w0 + field_at(g, omega, i - di, j - dj)) * ih2;
+            den += wp + wm;
+            for (int c = 0; c < g.dim; ++c)
+                num[c] += wp * coord_at(g, xin, i + di, j + dj, c) + wm * coord_at(g, xin, i - di, j - dj, c);
+        }
+        for (int c = 0; c < g.dim; ++c) {
+            const double xn = num[c] / den;
+            chg = fmax(chg, fabs(xn - xin[c * N + id]));
+            xout[c * N + id] = xn;
+        }
+    }
+    if (check) {
+        chg = block_reduce_max(chg);
+        if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_JAC], chg);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) atomicAdd(&d->sweeps, 1);
+}
+
+__global__ void k_jacobi_check(DevScalars* d, double eps) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double c = __longlong_as_double((long long)d->red[RED_JAC]);
+        if (d->conv == 0 && c < eps) d->conv = 1;
+        d->red[RED_JAC] = 0ULL;
+    }
+}
+
+// Delta_gamma: each node moves at most half of the spacing towards its neighbour (Sec. 4)
+__global__ void k_limiter(GridParams g, const double* xn, const double* xit, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    double m = 1.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        for (int k = 0; k < g.dim; ++k) {
+            const double dx = xit[k * N + id] - xn[k * N + id];
+            const int di = k == 0, dj = k == 1;
+            if (dx < 0.0) m = fmin(m, -(xn[k * N + id] - coord_at(g, xn, i - di, j - dj, k)) / (2.0 * dx));
+            else if (dx > 0.0) m = fmin(m, (coord_at(g, xn, i + di, j + dj, k) - xn[k * N + id]) / (2.0 * dx));
+        }
+    }
+    m = block_reduce_min(m);
+    if (threadIdx.x == 0) atomic_min_pos(&d->red[RED_GAMMA], m);
+}
+
+__global__ void k_velocity(GridParams g, const double* xn, const double* xit, DevScalars* d, double* xdot) {
+    const int N = g.n1 * g.n2;
+    const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
+    const double dt = d->dt;
+    const double f = dt > 0.0 ? gam / dt : 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
+        xdot[id] = f * (xit[id] - xn[id]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) d->gamma = gam;
+}
+
+}  // namespace es

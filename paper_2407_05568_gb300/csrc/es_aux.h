@@ -1,0 +1,54 @@
+// es_aux.h -- declarations of the auxiliary kernels (init, time step, mesh).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "es_device.cuh"
+
+namespace es {
+
+struct GridParams {
+    int dim;
+    int n1, n2;
+    int bc[2];
+    double inv_dxi[2];
+    double period[2];
+};
+
+struct MonitorParams {
+    int kind;            // ES_MONITOR_*
+    int kappa;
+    double w0, w1, w2;   // weights of the three monitor terms
+};
+
+enum { RED_CFL = 0, RED_MON0 = 1, RED_MON1 = 2, RED_MON2 = 3, RED_GAMMA = 4, RED_JAC = 5 };
+
+// Device-resident scalars of a run.
+struct DevScalars {
+    double t, dt, t_end, last_dt, gamma;
+    unsigned long long red[8];
+    int sweeps;
+    int conv;
+    DevStatus status;
+};
+
+__global__ void k_init_J(GridParams g, const double* x, double* J);
+__global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const double* v, const double* p,
+                               const double* J, double* JU);
+__global__ void k_reset(DevScalars* d);
+__global__ void k_cfl(GridParams g, Gas G, const double* JU, const double* J, const double* x, DevScalars* d);
+__global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
+__global__ void k_set_dt(DevScalars* d, double dt);
+__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
+__global__ void k_mon_fields(GridParams g, Gas G, const double* JU, const double* J, double* rhoF, double* GF);
+__global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, const double* GF, double* t0,
+                            double* t1, double* t2, DevScalars* d);
+__global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,
+                            const DevScalars* d, double* omega);
+__global__ void k_filter(GridParams g, const double* in, double* out);
+__global__ void k_jacobi(GridParams g, const double* omega, const double* xin, double* xout, DevScalars* d,
+                         int check);
+__global__ void k_jacobi_check(DevScalars* d, double eps);
+__global__ void k_limiter(GridParams g, const double* xn, const double* xit, DevScalars* d);
+__global__ void k_velocity(GridParams g, const double* xn, const double* xit, DevScalars* d, double* xdot);
+
+}  // namespace es

@@ -1,0 +1,221 @@
+"""ctypes binding of the C ABI in include/es_vdw.h (argument marshalling only).
+
+Every computation runs in ``libesvdw.so``; this module converts PyTorch CUDA
+tensors to device pointers and Python settings to ``es_params``.  It raises if
+the library is missing: there is no other code path.
+
+Functions keep the C names: ``es_create``, ``es_init_mesh``, ``es_prim_to_cons``,
+``es_rhs``, ``es_rk_stage``, ``es_cfl_dt``, ``es_mesh_redistribute``,
+``es_steps``, ``es_set_time``, ``es_get_time``, ``es_run_host``, ``es_check``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libesvdw.so")
+
+ES_OK, ES_ERR_ARG, ES_ERR_CUDA, ES_ERR_INADMISSIBLE, ES_ERR_MESH, ES_ERR_TIMEOUT = range(6)
+ES_BC = {"periodic": 0, "outflow": 1}
+ES_PREC = {"fp64": 0, "mixed": 1}
+ES_MONITOR = {"vdw": 0, "smooth": 1}
+
+
+class EsParams(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double), ("cv", ctypes.c_double),
+        ("dim", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
+        ("dxi", ctypes.c_double * 2), ("period", ctypes.c_double * 2), ("bc", ctypes.c_int * 2),
+        ("weno_gamma", ctypes.c_double * 3), ("weno_eps", ctypes.c_double), ("sign_tol", ctypes.c_double),
+        ("dissipation", ctypes.c_int), ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+        ("moving", ctypes.c_int), ("monitor", ctypes.c_int), ("kappa", ctypes.c_int),
+        ("alpha", ctypes.c_double * 4), ("filter_passes", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int),
+        ("jacobi_eps", ctypes.c_double), ("precision", ctypes.c_int),
+    ]
+
+
+class EsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"es error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libesvdw.so (built by paper_2407_05568_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2407_05568_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.es_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(EsParams), vp]
+        L.es_destroy.argtypes = [vp]
+        L.es_destroy.restype = None
+        L.es_init_mesh.argtypes = [vp, vp, vp]
+        L.es_prim_to_cons.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.es_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.es_rk_stage.argtypes = [vp, i, d, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.es_cfl_dt.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d)]
+        L.es_mesh_redistribute.argtypes = [vp, vp, vp, vp, d, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        L.es_steps.argtypes = [vp, vp, vp, vp, i, d]
+        L.es_set_time.argtypes = [vp, d]
+        L.es_get_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.es_run_host.argtypes = [vp, vp, vp, vp, i, d]
+        L.es_check.argtypes = [vp]
+        L.es_last_error.argtypes = [vp, ctypes.c_char_p, i]
+        L.es_launch_count.argtypes = [vp]
+        L.es_launch_count.restype = ctypes.c_int64
+        for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
+                     "es_mesh_redistribute", "es_steps", "es_set_time", "es_get_time", "es_run_host",
+                     "es_check", "es_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=1e-12):
+    """es_params from a workload description (see workloads.py)."""
+    p = EsParams()
+    g = w["gas"]
+    p.a, p.b, p.R, p.cv = g["a"], g["b"], g["R"], g["cv"]
+    p.dim = w["dim"]
+    p.n1 = w["n"][-1] if w["dim"] == 2 else w["n"][0]
+    p.n2 = w["n"][0] if w["dim"] == 2 else 1
+    for k in range(w["dim"]):
+        p.dxi[k] = w["dxi"][k]
+        p.period[k] = w["period"][k]
+        p.bc[k] = ES_BC[w["bc"][k]]
+    p.weno_gamma[:] = (0.005, 0.045, 0.95)
+    p.weno_eps = weno_eps
+    p.sign_tol = sign_tol
+    p.dissipation = int(dissipation)
+    p.cfl = w.get("cfl", 0.4)
+    p.dt_fixed = dt_fixed
+    p.moving = int(w.get("moving", False))
+    m = w.get("mesh", {})
+    p.monitor = ES_MONITOR[m.get("monitor", "vdw")]
+    p.kappa = m.get("kappa", 2)
+    al = list(m.get("alphas", (1200.0, 1200.0, 1200.0)))
+    for k, a in enumerate(al[:4]):
+        p.alpha[k] = a
+    p.filter_passes = m.get("filter_passes", 5)
+    p.jacobi_sweeps = m.get("sweeps", 5)
+    p.jacobi_eps = m.get("eps", 0.0)
+    p.precision = ES_PREC[precision]
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns an es_ctx*; destroyed with the object."""
+
+    def __init__(self, params, stream=None):
+        self.params = params
+        self._h = ctypes.c_void_p()
+        rc = lib().es_create(ctypes.byref(self._h), ctypes.byref(params), _stream_handle(stream))
+        if rc != ES_OK:
+            raise EsError(rc, "es_create rejected the parameters" if rc == ES_ERR_ARG else "es_create failed")
+
+    def _call(self, rc):
+        if rc != ES_OK:
+            buf = ctypes.create_string_buffer(256)
+            lib().es_last_error(self._h, buf, 256)
+            raise EsError(rc, buf.value.decode())
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.es_destroy(self._h)
+            self._h = None
+
+    @property
+    def launches(self):
+        return int(lib().es_launch_count(self._h))
+
+
+def es_create(params, stream=None):
+    return Context(params, stream)
+
+
+def es_init_mesh(ctx, x, J):
+    ctx._call(lib().es_init_mesh(ctx._h, _ptr(x), _ptr(J)))
+
+
+def es_prim_to_cons(ctx, rho, v, p, J, JU):
+    ctx._call(lib().es_prim_to_cons(ctx._h, _ptr(rho), _ptr(v), _ptr(p), _ptr(J), _ptr(JU)))
+
+
+def es_rhs(ctx, JU, J, x, xdot, dJU, dJ):
+    ctx._call(lib().es_rhs(ctx._h, _ptr(JU), _ptr(J), _ptr(x), _ptr(xdot), _ptr(dJU), _ptr(dJ)))
+
+
+def es_rk_stage(ctx, stage, dt, JUn, Jn, JUs, Js, xn, xdot, JU_out, J_out):
+    ctx._call(lib().es_rk_stage(ctx._h, stage, dt, _ptr(JUn), _ptr(Jn), _ptr(JUs), _ptr(Js), _ptr(xn),
+                                _ptr(xdot), _ptr(JU_out), _ptr(J_out)))
+
+
+def es_cfl_dt(ctx, JU, J, x):
+    dt = ctypes.c_double()
+    ctx._call(lib().es_cfl_dt(ctx._h, _ptr(JU), _ptr(J), _ptr(x), ctypes.byref(dt)))
+    return dt.value
+
+
+def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot):
+    sw = ctypes.c_int()
+    gam = ctypes.c_double()
+    ctx._call(lib().es_mesh_redistribute(ctx._h, _ptr(JU), _ptr(J), _ptr(xn), dt, _ptr(xdot),
+                                         ctypes.byref(sw), ctypes.byref(gam)))
+    return sw.value, gam.value
+
+
+def es_steps(ctx, JU, J, x, nsteps, t_end):
+    ctx._call(lib().es_steps(ctx._h, _ptr(JU), _ptr(J), _ptr(x), int(nsteps), float(t_end)))
+
+
+def es_set_time(ctx, t):
+    ctx._call(lib().es_set_time(ctx._h, float(t)))
+
+
+def es_get_time(ctx):
+    t = ctypes.c_double()
+    dt = ctypes.c_double()
+    ctx._call(lib().es_get_time(ctx._h, ctypes.byref(t), ctypes.byref(dt)))
+    return t.value, dt.value
+
+
+def es_run_host(ctx, JU, J, x, nsteps, t_end):
+    """JU, J, x: C-contiguous float64 numpy arrays (pinned or pageable host memory), updated in place."""
+    arrs = [JU, J, x]
+    for a in arrs:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+            raise ValueError("expected C-contiguous float64 arrays")
+    ptrs = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
+    ctx._call(lib().es_run_host(ctx._h, *ptrs, int(nsteps), float(t_end)))
+
+
+def es_check(ctx):
+    """Synchronise and return the latched device status (0 = ok)."""
+    return int(lib().es_check(ctx._h))
+
+
+def es_last_error(ctx):
+    buf = ctypes.create_string_buffer(256)
+    lib().es_last_error(ctx._h, buf, 256)
+    return buf.value.decode()

@@ -158,3 +158,35 @@ def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345):
                 break
         states[i] = (rl, vl, pl, rr, vr, pr)
     return dict(gas=UNITS_A, lengths=lengths, states=states)
+
+
+def wavy_mesh_2d(X, Y, amp=0.01):
+    """Smooth periodic perturbation of a uniform unit-square mesh (x(X+1, Y) = x + 1)."""
+    return np.stack([X + amp * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y),
+                     Y + amp * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)])
+
+
+def mesh_velocity_2d(X, Y, amp=0.05, fixed_edges=False):
+    """Smooth mesh-velocity field; zero on the boundary nodes when fixed_edges."""
+    xd = amp * np.stack([np.sin(2 * np.pi * (X + Y)), np.cos(2 * np.pi * (X - Y))])
+    if fixed_edges:
+        xd[:, [0, -1], :] = 0.0
+        xd[:, :, [0, -1]] = 0.0
+    return xd
+
+
+def smooth_state_2d(X, Y):
+    """Smooth periodic primitive fields (rho, v, p) for operator checks."""
+    rho = 0.6 + 0.2 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+    v = np.stack([0.3 + 0.1 * np.cos(2 * np.pi * Y), -0.2 + 0.1 * np.sin(2 * np.pi * X)])
+    p = 1.0 + 0.1 * np.sin(2 * np.pi * Y)
+    return rho, v, p
+
+
+def rough_state(shape, seed, dim):
+    """Seeded random admissible-looking primitive fields (rho, v, p) for stress checks."""
+    rng = np.random.default_rng(seed)
+    rho = 0.3 + 0.4 * rng.uniform(size=shape)
+    v = rng.uniform(-0.5, 0.5, (dim,) + shape)
+    p = 0.9 + 0.4 * rng.uniform(size=shape)
+    return rho, v, p
