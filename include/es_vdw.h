@@ -65,8 +65,9 @@ typedef struct es_params {
     int    bc[2];           /* ES_BC_* per direction */
     double weno_gamma[3];   /* MR-WENO5 linear weights (1-point, 3-point, 5-point), Sec. 5: (0.005, 0.045, 0.95) */
     double weno_eps;        /* smoothness regulariser (paper silent; 1e-12) */
-    double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| <= sign_tol (|W_i| + |W_{i+1}|)
-                               is round-off of a zero jump and has sign 0 (1e-12 in FP64) */
+    double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| no larger than sign_tol times
+                               sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|), the size of the terms forming
+                               it, is round-off of a zero jump and has sign 0 (1e-12 in FP64) */
     int    dissipation;     /* 1: ES flux eq. HOstable; 0: the EC flux alone */
     double cfl;             /* eq. cfl; 0.4 in 1D/2D */
     double dt_fixed;        /* > 0: use this Delta t instead of eq. cfl (Example 5.1 uses CFL dxi^(5/3)) */

@@ -19,7 +19,8 @@ Readings of points the paper leaves open (each listed in the design notes):
     cos(theta) = n_1/L, sin(theta) = n_2/L;
   * the sign switch Y compares [[W]]^WENO at face i+1/2 with the plain jump
     W_{i+1} - W_i at the same face; a plain jump no larger than sign_tol
-    (1e-12) times |W_i| + |W_{i+1}| is round-off of an exactly zero jump and
+    (1e-12) times the size of the terms that form it, sum_a |R_am|
+    (|(TV_i)_a| + |(TV_{i+1})_a|), is round-off of an exactly zero jump and
     has sign 0 (so Y = 0), which keeps the switch from turning on or off on
     the last bits of equal states.
 """
@@ -313,18 +314,20 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
     R, c = scaled_eigenvectors(g, rho_f, vn, vt, p_f)
     Lam = np.abs(xtf + L * vn) + L * c          # max_m |J xi_t + L lambda_m|
 
-    def project(j_off):
+    def rotated(j_off):
         Vj = V_pad[..., ip + j_off]
-        TV = Vj if d == 1 else rotate(Vj, cth, sth)     # T = I in 1D
-        return np.einsum("ab...,a...->b...", R, TV)   # W = R^T (T V)
+        return Vj if d == 1 else rotate(Vj, cth, sth)     # T V (T = I in 1D)
 
-    Wst = np.stack([project(o) for o in range(-2, 4)])      # nodes i-2 .. i+3
+    TV = [rotated(o) for o in range(-2, 4)]                 # nodes i-2 .. i+3
+    Wst = np.stack([np.einsum("ab...,a...->b...", R, tv) for tv in TV])   # W = R^T (T V)
     W_minus = mr_weno5(Wst[0:5], sch.weno_gammas, sch.weno_eps)
     W_plus = mr_weno5(Wst[5:0:-1], sch.weno_gammas, sch.weno_eps)
     jump_weno = W_plus - W_minus
     jump = Wst[3] - Wst[2]
-    # a plain jump within round-off of its endpoints counts as zero (sign 0)
-    jump = np.where(np.abs(jump) <= sch.sign_tol * (np.abs(Wst[3]) + np.abs(Wst[2])), 0.0, jump)
+    # a plain jump within round-off of the terms that form W_i and W_{i+1}
+    # (sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|)) is round-off of a zero jump: sign 0
+    scale = np.einsum("ab...,a...->b...", np.abs(R), np.abs(TV[2]) + np.abs(TV[3]))
+    jump = np.where(np.abs(jump) <= sch.sign_tol * scale, 0.0, jump)
     Y = (np.sign(jump_weno) * np.sign(jump) > 0).astype(np.float64)
     incr = np.einsum("ab...,b...->a...", R, Y * jump_weno)  # R Y [[W]]
     if d == 2:

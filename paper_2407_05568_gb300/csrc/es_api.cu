@@ -16,7 +16,9 @@ using namespace es;
 struct es_ctx {
     es_params p;
     int device;
-    cudaStream_t stream;
+    cudaStream_t stream;              // the caller's stream
+    cudaStream_t s_enq;               // stream the enqueue helpers launch on (capture stream while capturing)
+    cudaStream_t cap_stream;          // private stream for graph capture (the legacy stream cannot capture)
     GridParams g;
     Gas gas;
     Weno weno;
@@ -85,7 +87,7 @@ StageParams stage_params(es_ctx* c) {
 
 cudaError_t launch_stage(es_ctx* c, const StageParams& P) {
     count(c);
-    return c->p.precision == ES_PREC_MIXED ? launch_stage_mixed(P, c->stream) : launch_stage_fp64(P, c->stream);
+    return c->p.precision == ES_PREC_MIXED ? launch_stage_mixed(P, c->s_enq) : launch_stage_fp64(P, c->s_enq);
 }
 
 const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -95,7 +97,7 @@ const double RK_C[3] = {0.0, 1.0, 0.5};
 // monitor -> filter -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
 int enqueue_mesh(es_ctx* c, const double* JU, const double* J, const double* xn, double* xdot) {
     const int B = 256, G = c->grid1d;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = c->s_enq;
     k_mon_fields<<<G, B, 0, s>>>(c->g, c->gas, JU, J, c->rhoF, c->GF);
     k_mon_terms<<<G, B, 0, s>>>(c->g, c->mon, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->dev);
     k_mon_omega<<<G, B, 0, s>>>(c->g, c->mon, c->t0, c->t1, c->t2, c->dev, c->om0);
@@ -130,7 +132,7 @@ int enqueue_mesh(es_ctx* c, const double* JU, const double* J, const double* xn,
 
 int enqueue_step(es_ctx* c, double* JU, double* J, double* x) {
     const int B = 256, G = c->grid1d;
-    cudaStream_t s = c->stream;
+    cudaStream_t s = c->s_enq;
     k_reset<<<1, 32, 0, s>>>(c->dev);
     k_cfl<<<G, B, 0, s>>>(c->g, c->gas, JU, J, x, c->dev);
     k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
@@ -209,6 +211,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     if (!c) return ES_ERR_ARG;
     c->p = *p;
     c->stream = (cudaStream_t)stream;
+    c->s_enq = c->stream;
     CK(cudaGetDevice(&c->device), "cudaGetDevice");
     c->g.dim = p->dim;
     c->g.n1 = p->n1;
@@ -276,7 +279,9 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     ALLOC(c->dev, sizeof(DevScalars));
 #undef ALLOC
     {
-        cudaError_t e = cudaMallocHost((void**)&c->hpin, sizeof(DevScalars));
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaStreamCreate"); goto fail_out; }
+        e = cudaMallocHost((void**)&c->hpin, sizeof(DevScalars));
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaMallocHost"); goto fail_out; }
         e = cudaMemsetAsync(c->dev, 0, sizeof(DevScalars), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->xdot, 0, B * p->dim, c->stream);
@@ -296,6 +301,7 @@ fail_out:
 void es_destroy(es_ctx* c) {
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     double* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2,
                       c->om0, c->om1, c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx};
     for (double* b : bufs)
@@ -429,12 +435,14 @@ int es_steps(es_ctx* c, double* JU, double* J, double* x, int nsteps, double t_e
             c->gexec = nullptr;
         }
         cudaGraph_t graph;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         c->capturing = 1;
         c->capture_count = 0;
+        c->s_enq = c->cap_stream;
         int rc = enqueue_step(c, JU, J, x);
+        c->s_enq = c->stream;
         c->capturing = 0;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
         e = cudaGraphInstantiate(&c->gexec, graph, 0);

@@ -146,8 +146,11 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
     const double Lam = fabs(xtf + L * vn) + L * c;
     const double Hm = H - vn * c, Hp = H + vn * c;
 
-    // scaled entropy variables W = R^T (T V) at nodes l-2 .. l+3
+    // scaled entropy variables W = R^T (T V) at nodes l-2 .. l+3; aTV = |T V_i| + |T V_{i+1}|
     double W[6][DIM + 2];
+    double aTV[DIM + 2];
+#pragma unroll
+    for (int a = 0; a < DIM + 2; ++a) aTV[a] = 0.0;
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
         const int q = l + (o - 2) * step;
@@ -157,6 +160,11 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
             W[o][0] = sA * (V0 + (vn - c) * V1 + Hm * V2);
             W[o][1] = sE * (V0 + vn * V1 + mid * V2);
             W[o][2] = sA * (V0 + (vn + c) * V1 + Hp * V2);
+            if (o == 2 || o == 3) {
+                aTV[0] += fabs(V0);
+                aTV[1] += fabs(V1);
+                aTV[2] += fabs(V2);
+            }
         } else {
             const double a1 = S[F_W1 * NB + q], a2 = S[F_W2 * NB + q];
             const double V1 = cs * a1 + sn * a2, V2 = -sn * a1 + cs * a2, V3 = S[F_W3 * NB + q];
@@ -165,7 +173,26 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
             W[o][1] = sE * (base + vn * V1 + mid * V3);
             W[o][2] = sT * (V2 + vt * V3);
             W[o][3] = sA * (base + (vn + c) * V1 + Hp * V3);
+            if (o == 2 || o == 3) {
+                aTV[0] += fabs(V0);
+                aTV[1] += fabs(V1);
+                aTV[2] += fabs(V2);
+                aTV[3] += fabs(V3);
+            }
         }
+    }
+    // round-off size of each W_m: sum_a |R_am| aTV_a
+    double scl[DIM + 2];
+    if (DIM == 1) {
+        scl[0] = sA * (aTV[0] + fabs(vn - c) * aTV[1] + fabs(Hm) * aTV[2]);
+        scl[1] = sE * (aTV[0] + fabs(vn) * aTV[1] + fabs(mid) * aTV[2]);
+        scl[2] = sA * (aTV[0] + fabs(vn + c) * aTV[1] + fabs(Hp) * aTV[2]);
+    } else {
+        const double avt = fabs(vt);
+        scl[0] = sA * (aTV[0] + fabs(vn - c) * aTV[1] + avt * aTV[2] + fabs(Hm) * aTV[3]);
+        scl[1] = sE * (aTV[0] + fabs(vn) * aTV[1] + avt * aTV[2] + fabs(mid) * aTV[3]);
+        scl[2] = sT * (aTV[2] + avt * aTV[3]);
+        scl[3] = sA * (aTV[0] + fabs(vn + c) * aTV[1] + avt * aTV[2] + fabs(Hp) * aTV[3]);
     }
     double y[DIM + 2];
 #pragma unroll
@@ -174,7 +201,7 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
         const double wplu = mr_weno5(W[5][m], W[4][m], W[3][m], W[2][m], W[1][m], Wc);
         const double jw = wplu - wmin;
         double j = W[3][m] - W[2][m];
-        if (fabs(j) <= Wc.sign_tol * (fabs(W[3][m]) + fabs(W[2][m]))) j = 0.0;   // round-off of a zero jump
+        if (fabs(j) <= Wc.sign_tol * scl[m]) j = 0.0;     // round-off of a zero jump: sign 0
         const bool keep = (jw > 0.0 && j > 0.0) || (jw < 0.0 && j < 0.0);
         y[m] = keep ? jw : 0.0;
     }

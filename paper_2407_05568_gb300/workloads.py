@@ -28,10 +28,13 @@ def _recipe_temperature(rho, p):
     return (p + 3.0 * rho**2) * (3.0 - rho) / (8.0 * rho)
 
 
-def _recipe_ok(rho, p):
-    """Recipe acceptance region: T > 27/32 and 4T - rho (3 - rho)^2 > 0, 0 < rho < 3."""
+def _recipe_ok(rho, p, t_min=1.02):
+    """Recipe acceptance region: 0 < rho < 3 and a supercritical temperature T >= t_min
+    (T_c = 1).  Subcritical states can expand into the unstable region where
+    4T - rho (3 - rho)^2 < 0; the states near the critical point with G < 0 lie just
+    above T_c, so the recipe keeps them."""
     T = _recipe_temperature(rho, p)
-    return (0.0 < rho < 3.0) and T > 27.0 / 32.0 and 4.0 * T - rho * (3.0 - rho) ** 2 > 0.0
+    return (0.0 < rho < 3.0) and T >= t_min and 4.0 * T - rho * (3.0 - rho) ** 2 > 0.0
 
 
 def _pair_ok(s1, s2):
@@ -73,7 +76,8 @@ def sine_2d(n=1024, t_end=0.1, cfl=0.4):
 def quadrant_states(seed):
     """Four seeded admissible states near the critical point:
     rho in [0.4, 1.6], p in [0.6, 1.4], |v| <= 0.5 (uniform in the disc), rejection-sampled
-    for the recipe acceptance region and for every pair of neighbouring quadrants."""
+    for the recipe acceptance region (supercritical, T >= 1.02) and for every pair of
+    neighbouring quadrants."""
     rng = np.random.default_rng(seed)
     while True:
         st = []
