@@ -152,6 +152,38 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
  * their kernels), for launch accounting. */
 int64_t es_launch_count(es_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free SSP-RK3 step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (a host application
+ * that owns and budgets all device memory itself, code running while a memory
+ * pool is torn down or rebuilt, a process that must not allocate after its
+ * start-up).  It needs no es_ctx.
+ *
+ * Advances (JU, J) in place by one SSP-RK3 step of size dt of the FP64
+ * operator (the same three fused stage launches as es_rk_stage), on the mesh x
+ * moving with velocity xdot (nullable: fixed mesh); x itself is not updated.
+ * p must have precision ES_PREC_FP64; the time-step, mesh and graph fields of
+ * p are ignored.  All arrays are caller-owned device arrays as above.
+ *
+ * Scratch: the two intermediate stage states and the status word live in a
+ * __device__ array compiled into the library (about 5 MB, held on every GPU
+ * that loads the library until the process exits).  Meshes with more than
+ * ES_STATIC_MAX_NODES nodes are rejected with ES_ERR_ARG.  The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * The first call on a device looks up the scratch array's device address and
+ * sets the stage kernel's shared-memory attribute (with that device current);
+ * make that first call before any stream capture.  Every call then clears the
+ * status word, launches on `stream` and synchronises it to read the status
+ * back: the return value is ES_OK, ES_ERR_ARG, ES_ERR_CUDA, or a device status
+ * such as ES_ERR_INADMISSIBLE.  All calls share the one scratch array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (from two
+ * streams or two host threads) race on it and must be serialised by the
+ * caller. */
+#define ES_STATIC_MAX_NODES 65536
+int es_rk3_step_static(const es_params* p, double dt, double* JU, double* J, const double* x,
+                       const double* xdot, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

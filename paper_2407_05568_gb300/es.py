@@ -69,6 +69,8 @@ def lib():
         L.es_last_error.argtypes = [vp, ctypes.c_char_p, i]
         L.es_launch_count.argtypes = [vp]
         L.es_launch_count.restype = ctypes.c_int64
+        L.es_rk3_step_static.argtypes = [ctypes.POINTER(EsParams), d, vp, vp, vp, vp, vp]
+        L.es_rk3_step_static.restype = ctypes.c_int
         for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
                      "es_mesh_redistribute", "es_steps", "es_set_time", "es_get_time", "es_run_host",
                      "es_check", "es_last_error"):
@@ -213,6 +215,12 @@ def es_run_host(ctx, JU, J, x, nsteps, t_end):
 def es_check(ctx):
     """Synchronise and return the latched device status (0 = ok)."""
     return int(lib().es_check(ctx._h))
+
+
+def es_rk3_step_static(params, dt, JU, J, x, xdot=None, stream=None):
+    """Allocation-free SSP-RK3 step (see es_vdw.h); returns the status code (0 = ok)."""
+    return int(lib().es_rk3_step_static(ctypes.byref(params), float(dt), _ptr(JU), _ptr(J), _ptr(x),
+                                        _ptr(xdot), _stream_handle(stream)))
 
 
 def es_last_error(ctx):
