@@ -7,8 +7,10 @@
  * Data layout (all calls)
  *   Node-centred fields on a logically rectangular n1 x n2 mesh (n2 = 1 in 1D),
  *   structure of arrays, xi_1 fastest:  field[c][j][i] at c*n1*n2 + j*n1 + i.
- *     JU : (dim + 2) components (rho, rho v_1, [rho v_2], E) times J, double
- *     J  : 1 component, double
+ *     JU : (dim + 2) components (rho, rho v_1, [rho v_2], E) times J
+ *     J  : 1 component
+ *     JU, J (and dJU, dJ) hold double in ES_PREC_FP64 and float in ES_PREC_MIXED;
+ *     they are passed as void*.
  *     x  : dim components (x_1, [x_2]) of the node coordinates, double
  *     xdot : dim components of the mesh velocity, double
  *   The computational mesh is uniform with spacings dxi[k]; x(xi) maps it to
@@ -48,7 +50,10 @@ extern "C" {
 
 /* arithmetic of the operator */
 #define ES_PREC_FP64   0        /* every step in double */
-#define ES_PREC_MIXED  1        /* flux / WENO / RK bulk in float, critical steps in double */
+#define ES_PREC_MIXED  1        /* float state and per-stage arithmetic (entropy-variable jumps by the
+                                   paper's jump decomposition, mesh as an FP32 displacement); the
+                                   mesh redistribution and the mesh itself stay double.  Periodic
+                                   directions need period[k] = n_k dxi[k]. */
 
 /* monitor functions of Sec. 4 / Example 5.1 */
 #define ES_MONITOR_VDW    0     /* eq. van der Waalsmonitor: delta_1 = rho, delta_2 = G, plus |Delta G|^2 */
@@ -93,21 +98,21 @@ void es_destroy(es_ctx* ctx);
 /* Initial metric Jacobian J = det dx/dxi at the nodes, from the same 6th-order
  * central differences delta_k used by the metrics (Sec. 3.2, eq. SCLCoeff).
  * x: [dim][n2][n1] in, J: [n2][n1] out. */
-int es_init_mesh(es_ctx* ctx, const double* x, double* J);
+int es_init_mesh(es_ctx* ctx, const double* x, void* J);
 
 /* Conservative variables JU = J (rho, rho v, E) from primitive (rho, v, p)
  * (Sec. 1, eq. ConserLaw2 with E = rho e + rho |v|^2/2, T from eq. vdWEOS).
  * rho, p: [n2][n1]; v: [dim][n2][n1]; J: [n2][n1]; JU out: [dim+2][n2][n1]. */
 int es_prim_to_cons(es_ctx* ctx, const double* rho, const double* v, const double* p,
-                    const double* J, double* JU);
+                    const void* J, void* JU);
 
 /* Semi-discrete operator alone (eq. semi_U, eq. semi_J):
  *   dJU = -sum_k (F_{k,+1/2} - F_{k,-1/2}) / dxi_k,  dJ likewise with the J xi_t fluxes,
  * with the 6th-order EC flux (eq. ECFlux_curv_2p, GCL_flux), the metrics of the
  * mesh x moving with velocity xdot (eq. SCLCoeff, VCLCoeff) and, when
  * p->dissipation, the ES dissipation (eq. HOstable).  All device arrays. */
-int es_rhs(es_ctx* ctx, const double* JU, const double* J, const double* x, const double* xdot,
-           double* dJU, double* dJ);
+int es_rhs(es_ctx* ctx, const void* JU, const void* J, const double* x, const double* xdot,
+           void* dJU, void* dJ);
 
 /* One SSP-RK3 stage (Shu-Osher form, stage = 1, 2, 3):
  *   (JU, J)_out = a_s (JU, J)_n + b_s ((JU, J)_s + dt L(JU_s, J_s; x_s)),
@@ -115,17 +120,17 @@ int es_rhs(es_ctx* ctx, const double* JU, const double* J, const double* x, cons
  * mesh x_s = xn + c_s dt xdot with c = (0, 1, 1/2).  JUn/Jn are read only at the
  * node itself, so JU_out may alias JUn (but not JUs). */
 int es_rk_stage(es_ctx* ctx, int stage, double dt,
-                const double* JUn, const double* Jn, const double* JUs, const double* Js,
-                const double* xn, const double* xdot, double* JU_out, double* J_out);
+                const void* JUn, const void* Jn, const void* JUs, const void* Js,
+                const double* xn, const double* xdot, void* JU_out, void* J_out);
 
 /* Time step of eq. cfl from the current mesh with zero mesh velocity; writes the host double. */
-int es_cfl_dt(es_ctx* ctx, const double* JU, const double* J, const double* x, double* dt_host);
+int es_cfl_dt(es_ctx* ctx, const void* JU, const void* J, const double* x, double* dt_host);
 
 /* Mesh redistribution of Sec. 4 for a step of size dt: monitor (with G) ->
  * filter passes -> Jacobi sweeps from xn -> limiter Delta_gamma -> mesh velocity
  * xdot = Delta_gamma (x^[mu] - xn)/dt.  Writes xdot (device) and, if non-null,
  * the sweeps taken and Delta_gamma (host; this synchronises the stream). */
-int es_mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, const double* xn,
+int es_mesh_redistribute(es_ctx* ctx, const void* JU, const void* J, const double* xn,
                          double dt, double* xdot, int* sweeps_host, double* gamma_host);
 
 /* Advance the caller's state (JU, J, x) in place by nsteps full steps
@@ -133,14 +138,14 @@ int es_mesh_redistribute(es_ctx* ctx, const double* JU, const double* J, const d
  * moving; three RK stages; x += dt xdot).  The time t lives on the device:
  * es_set_time / es_get_time move it.  Steps after t reaches t_end are no-ops.
  * Launches a CUDA graph per step once the first step has been captured. */
-int es_steps(es_ctx* ctx, double* JU, double* J, double* x, int nsteps, double t_end);
+int es_steps(es_ctx* ctx, void* JU, void* J, double* x, int nsteps, double t_end);
 int es_set_time(es_ctx* ctx, double t);
 int es_get_time(es_ctx* ctx, double* t_host, double* last_dt_host);   /* synchronises */
 
 /* End-to-end form for callers holding HOST arrays: copies JU_host, J_host,
  * x_host to context-owned device buffers, runs es_steps, copies them back and
  * synchronises.  Same layouts as the device arrays. */
-int es_run_host(es_ctx* ctx, double* JU_host, double* J_host, double* x_host, int nsteps,
+int es_run_host(es_ctx* ctx, void* JU_host, void* J_host, double* x_host, int nsteps,
                 double t_end);
 
 /* Synchronise and return the latched device status (ES_OK or ES_ERR_*);

@@ -26,13 +26,17 @@ struct es_ctx {
     size_t N;
     int nc;
     int grid1d;
+    int mixed;                        // ES_PREC_MIXED: float state
+    size_t esz;                       // bytes per state element (8 or 4)
     // scratch (device)
-    double *S1, *S1J, *S2, *S2J;
+    void *S1, *S1J, *S2, *S2J;        // RK stage states in the state precision
+    float *fdisp, *fxd;               // mixed form: FP32 mesh displacement and velocity
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1;
     double *xa, *xb, *xdot;
     DevScalars* dev;
     DevScalars* hpin;                 // pinned host mirror
-    double *hJU, *hJ, *hx;            // device copies for es_run_host
+    void *hJU, *hJ;                   // device copies for es_run_host
+    double* hx;
     // graph cache
     cudaGraphExec_t gexec;
     const void* gkey[3];
@@ -85,6 +89,35 @@ StageParams stage_params(es_ctx* c) {
     return P;
 }
 
+// state pointers of a stage launch in the context's precision
+void set_state(es_ctx* c, StageParams& P, const void* JUn, const void* Jn, const void* JUs, const void* Js,
+               void* JUo, void* Jo) {
+    if (c->mixed) {
+        P.fJUn = (const float*)JUn;
+        P.fJn = (const float*)Jn;
+        P.fJUs = (const float*)JUs;
+        P.fJs = (const float*)Js;
+        P.fJUo = (float*)JUo;
+        P.fJo = (float*)Jo;
+    } else {
+        P.JUn = (const double*)JUn;
+        P.Jn = (const double*)Jn;
+        P.JUs = (const double*)JUs;
+        P.Js = (const double*)Js;
+        P.JUo = (double*)JUo;
+        P.Jo = (double*)Jo;
+    }
+}
+
+// mixed form: FP32 mesh displacement / velocity for the stage kernels
+void enqueue_mesh_f32(es_ctx* c, StageParams& P, const double* x, const double* xdot) {
+    if (!c->mixed) return;
+    k_mesh_f32<<<c->grid1d, 256, 0, c->s_enq>>>(c->g, x, xdot, c->fdisp, c->fxd);
+    count(c);
+    P.fdisp = c->fdisp;
+    P.fxdot = xdot ? c->fxd : nullptr;
+}
+
 cudaError_t launch_stage(es_ctx* c, const StageParams& P) {
     count(c);
     return c->p.precision == ES_PREC_MIXED ? launch_stage_mixed(P, c->s_enq) : launch_stage_fp64(P, c->s_enq);
@@ -95,10 +128,10 @@ const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 const double RK_C[3] = {0.0, 1.0, 0.5};
 
 // monitor -> filter -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
-int enqueue_mesh(es_ctx* c, const double* JU, const double* J, const double* xn, double* xdot) {
+int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
-    k_mon_fields<<<G, B, 0, s>>>(c->g, c->gas, JU, J, c->rhoF, c->GF);
+    launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s);
     k_mon_terms<<<G, B, 0, s>>>(c->g, c->mon, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->dev);
     k_mon_omega<<<G, B, 0, s>>>(c->g, c->mon, c->t0, c->t1, c->t2, c->dev, c->om0);
     count(c, 3);
@@ -130,13 +163,19 @@ int enqueue_mesh(es_ctx* c, const double* JU, const double* J, const double* xn,
     return ES_OK;
 }
 
-int enqueue_step(es_ctx* c, double* JU, double* J, double* x) {
+void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x) {
+    launch_cfl(c->g, c->gas, JU, J, x, c->dev, c->mixed, c->grid1d, c->s_enq);
+    count(c);
+}
+
+int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     k_reset<<<1, 32, 0, s>>>(c->dev);
-    k_cfl<<<G, B, 0, s>>>(c->g, c->gas, JU, J, x, c->dev);
+    count(c);
+    enqueue_cfl(c, JU, J, x);
     k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
-    count(c, 3);
+    count(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
@@ -149,20 +188,16 @@ int enqueue_step(es_ctx* c, double* JU, double* J, double* x) {
     P.dt_dev = &c->dev->dt;
     P.xn = x;
     P.xdot = xdot;
-    const double* srcU[3] = {JU, c->S1, c->S2};
-    const double* srcJ[3] = {J, c->S1J, c->S2J};
-    double* dstU[3] = {c->S1, c->S2, JU};
-    double* dstJ[3] = {c->S1J, c->S2J, J};
+    enqueue_mesh_f32(c, P, x, xdot);
+    const void* srcU[3] = {JU, c->S1, c->S2};
+    const void* srcJ[3] = {J, c->S1J, c->S2J};
+    void* dstU[3] = {c->S1, c->S2, JU};
+    void* dstJ[3] = {c->S1J, c->S2J, J};
     for (int st = 0; st < 3; ++st) {
         P.ca = RK_A[st];
         P.cb = RK_B[st];
         P.cst = RK_C[st];
-        P.JUn = JU;
-        P.Jn = J;
-        P.JUs = srcU[st];
-        P.Js = srcJ[st];
-        P.JUo = dstU[st];
-        P.Jo = dstJ[st];
+        set_state(c, P, JU, J, srcU[st], srcJ[st], dstU[st], dstJ[st]);
         e = launch_stage(c, P);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel");
     }
@@ -191,6 +226,12 @@ int check_params(const es_params* p) {
     if (!(p->sign_tol >= 0.0) || p->sign_tol > 1e-2) return 0;
     if (!(p->cfl > 0.0) && !(p->dt_fixed > 0.0)) return 0;
     if (p->precision != ES_PREC_FP64 && p->precision != ES_PREC_MIXED) return 0;
+    if (p->precision == ES_PREC_MIXED) {
+        // the FP32 displacement is periodic only when the period is n dxi
+        const int nn[2] = {p->n1, p->n2};
+        for (int k = 0; k < p->dim; ++k)
+            if (p->bc[k] == ES_BC_PERIODIC && fabs(p->period[k] - nn[k] * p->dxi[k]) > 1e-9 * p->period[k]) return 0;
+    }
     if (p->moving) {
         if (p->monitor != ES_MONITOR_VDW && p->monitor != ES_MONITOR_SMOOTH) return 0;
         if (p->monitor == ES_MONITOR_VDW && (p->kappa < 1 || p->kappa > 2)) return 0;
@@ -250,6 +291,8 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     }
     c->N = size_t(c->g.n1) * c->g.n2;
     c->nc = p->dim + 2;
+    c->mixed = p->precision == ES_PREC_MIXED;
+    c->esz = c->mixed ? sizeof(float) : sizeof(double);
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     const size_t blocks = (c->N + 255) / 256;
@@ -262,10 +305,14 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                         \
         if (e_ != cudaSuccess) { rc = cuda_fail(c, e_, "cudaMalloc"); goto fail_out; } \
     } while (0)
-    ALLOC(c->S1, B * c->nc);
-    ALLOC(c->S2, B * c->nc);
-    ALLOC(c->S1J, B);
-    ALLOC(c->S2J, B);
+    ALLOC(c->S1, c->esz * c->N * c->nc);
+    ALLOC(c->S2, c->esz * c->N * c->nc);
+    ALLOC(c->S1J, c->esz * c->N);
+    ALLOC(c->S2J, c->esz * c->N);
+    if (c->mixed) {
+        ALLOC(c->fdisp, sizeof(float) * c->N * p->dim);
+        ALLOC(c->fxd, sizeof(float) * c->N * p->dim);
+    }
     ALLOC(c->rhoF, B);
     ALLOC(c->GF, B);
     ALLOC(c->t0, B);
@@ -302,52 +349,46 @@ void es_destroy(es_ctx* c) {
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    double* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2,
-                      c->om0, c->om1, c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx};
-    for (double* b : bufs)
+    void* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->om0, c->om1,
+                    c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx, c->fdisp, c->fxd};
+    for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->dev) cudaFree(c->dev);
     if (c->hpin) cudaFreeHost(c->hpin);
     free(c);
 }
 
-int es_init_mesh(es_ctx* c, const double* x, double* J) {
+int es_init_mesh(es_ctx* c, const double* x, void* J) {
     if (!c || !x || !J) return fail(c, ES_ERR_ARG, "null argument");
-    k_init_J<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, J);
+    launch_init_J(c->g, x, J, c->mixed, c->grid1d, c->stream);
     count(c);
     CK(cudaGetLastError(), "k_init_J");
     return ES_OK;
 }
 
-int es_prim_to_cons(es_ctx* c, const double* rho, const double* v, const double* p, const double* J,
-                    double* JU) {
+int es_prim_to_cons(es_ctx* c, const double* rho, const double* v, const double* p, const void* J, void* JU) {
     if (!c || !rho || !v || !p || !J || !JU) return fail(c, ES_ERR_ARG, "null argument");
-    k_prim_to_cons<<<c->grid1d, 256, 0, c->stream>>>(c->g, c->gas, rho, v, p, J, JU);
+    launch_prim_to_cons(c->g, c->gas, rho, v, p, J, JU, c->mixed, c->grid1d, c->stream);
     count(c);
     CK(cudaGetLastError(), "k_prim_to_cons");
     return ES_OK;
 }
 
-int es_rhs(es_ctx* c, const double* JU, const double* J, const double* x, const double* xdot, double* dJU,
-           double* dJ) {
+int es_rhs(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot, void* dJU, void* dJ) {
     if (!c || !JU || !J || !x || !dJU || !dJ) return fail(c, ES_ERR_ARG, "null argument");
     StageParams P = stage_params(c);
     P.mode = 1;
     P.dt_host = 1.0;
-    P.JUn = JU;
-    P.Jn = J;
-    P.JUs = JU;
-    P.Js = J;
     P.xn = x;
     P.xdot = xdot;
-    P.JUo = dJU;
-    P.Jo = dJ;
+    enqueue_mesh_f32(c, P, x, xdot);
+    set_state(c, P, JU, J, JU, J, dJU, dJ);
     CK(launch_stage(c, P), "stage kernel");
     return ES_OK;
 }
 
-int es_rk_stage(es_ctx* c, int stage, double dt, const double* JUn, const double* Jn, const double* JUs,
-                const double* Js, const double* xn, const double* xdot, double* JU_out, double* J_out) {
+int es_rk_stage(es_ctx* c, int stage, double dt, const void* JUn, const void* Jn, const void* JUs,
+                const void* Js, const double* xn, const double* xdot, void* JU_out, void* J_out) {
     if (!c || stage < 1 || stage > 3 || !JUn || !Jn || !JUs || !Js || !xn || !JU_out || !J_out)
         return fail(c, ES_ERR_ARG, "bad argument");
     if (JU_out == JUs || J_out == Js) return fail(c, ES_ERR_ARG, "output aliases the stage input");
@@ -356,23 +397,19 @@ int es_rk_stage(es_ctx* c, int stage, double dt, const double* JUn, const double
     P.cb = RK_B[stage - 1];
     P.cst = RK_C[stage - 1];
     P.dt_host = dt;
-    P.JUn = JUn;
-    P.Jn = Jn;
-    P.JUs = JUs;
-    P.Js = Js;
     P.xn = xn;
     P.xdot = xdot;
-    P.JUo = JU_out;
-    P.Jo = J_out;
+    enqueue_mesh_f32(c, P, xn, xdot);
+    set_state(c, P, JUn, Jn, JUs, Js, JU_out, J_out);
     CK(launch_stage(c, P), "stage kernel");
     return ES_OK;
 }
 
-int es_cfl_dt(es_ctx* c, const double* JU, const double* J, const double* x, double* dt_host) {
+int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, double* dt_host) {
     if (!c || !JU || !J || !x || !dt_host) return fail(c, ES_ERR_ARG, "null argument");
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
-    k_cfl<<<c->grid1d, 256, 0, c->stream>>>(c->g, c->gas, JU, J, x, c->dev);
-    count(c, 2);
+    count(c);
+    enqueue_cfl(c, JU, J, x);
     CK(cudaGetLastError(), "k_cfl");
     CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -382,7 +419,7 @@ int es_cfl_dt(es_ctx* c, const double* JU, const double* J, const double* x, dou
     return ES_OK;
 }
 
-int es_mesh_redistribute(es_ctx* c, const double* JU, const double* J, const double* xn, double dt,
+int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double* xn, double dt,
                          double* xdot, int* sweeps_host, double* gamma_host) {
     if (!c || !JU || !J || !xn || !xdot || !(dt > 0.0)) return fail(c, ES_ERR_ARG, "bad argument");
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
@@ -419,7 +456,7 @@ int es_get_time(es_ctx* c, double* t_host, double* last_dt_host) {
     return ES_OK;
 }
 
-int es_steps(es_ctx* c, double* JU, double* J, double* x, int nsteps, double t_end) {
+int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) {
     if (!c || !JU || !J || !x || nsteps < 0) return fail(c, ES_ERR_ARG, "bad argument");
     if (nsteps == 0) return ES_OK;
     // t_end lives on the device; write it with a tiny copy (ordered on the stream)
@@ -458,22 +495,23 @@ int es_steps(es_ctx* c, double* JU, double* J, double* x, int nsteps, double t_e
     return ES_OK;
 }
 
-int es_run_host(es_ctx* c, double* JU_host, double* J_host, double* x_host, int nsteps, double t_end) {
+int es_run_host(es_ctx* c, void* JU_host, void* J_host, double* x_host, int nsteps, double t_end) {
     if (!c || !JU_host || !J_host || !x_host) return fail(c, ES_ERR_ARG, "null argument");
-    const size_t B = sizeof(double) * c->N;
+    const size_t SB = c->esz * c->N;
+    const size_t XB = sizeof(double) * c->N * c->p.dim;
     if (!c->hJU) {
-        CK(cudaMalloc((void**)&c->hJU, B * c->nc), "cudaMalloc");
-        CK(cudaMalloc((void**)&c->hJ, B), "cudaMalloc");
-        CK(cudaMalloc((void**)&c->hx, B * c->p.dim), "cudaMalloc");
+        CK(cudaMalloc(&c->hJU, SB * c->nc), "cudaMalloc");
+        CK(cudaMalloc(&c->hJ, SB), "cudaMalloc");
+        CK(cudaMalloc((void**)&c->hx, XB), "cudaMalloc");
     }
-    CK(cudaMemcpyAsync(c->hJU, JU_host, B * c->nc, cudaMemcpyHostToDevice, c->stream), "h2d");
-    CK(cudaMemcpyAsync(c->hJ, J_host, B, cudaMemcpyHostToDevice, c->stream), "h2d");
-    CK(cudaMemcpyAsync(c->hx, x_host, B * c->p.dim, cudaMemcpyHostToDevice, c->stream), "h2d");
+    CK(cudaMemcpyAsync(c->hJU, JU_host, SB * c->nc, cudaMemcpyHostToDevice, c->stream), "h2d");
+    CK(cudaMemcpyAsync(c->hJ, J_host, SB, cudaMemcpyHostToDevice, c->stream), "h2d");
+    CK(cudaMemcpyAsync(c->hx, x_host, XB, cudaMemcpyHostToDevice, c->stream), "h2d");
     int rc = es_steps(c, c->hJU, c->hJ, c->hx, nsteps, t_end);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(JU_host, c->hJU, B * c->nc, cudaMemcpyDeviceToHost, c->stream), "d2h");
-    CK(cudaMemcpyAsync(J_host, c->hJ, B, cudaMemcpyDeviceToHost, c->stream), "d2h");
-    CK(cudaMemcpyAsync(x_host, c->hx, B * c->p.dim, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    CK(cudaMemcpyAsync(JU_host, c->hJU, SB * c->nc, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    CK(cudaMemcpyAsync(J_host, c->hJ, SB, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    CK(cudaMemcpyAsync(x_host, c->hx, XB, cudaMemcpyDeviceToHost, c->stream), "d2h");
     CK(cudaStreamSynchronize(c->stream), "sync");
     return ES_OK;
 }

@@ -69,22 +69,24 @@ __device__ __forceinline__ double block_reduce_min(double v) {
 }
 
 // ------------------------------------------------------------ init
-__global__ void k_init_J(GridParams g, const double* x, double* J) {
+template <class TS>
+__global__ void k_init_J(GridParams g, const double* x, TS* J) {
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         if (g.dim == 1) {
-            J[id] = dcoord(g, x, i, 0, 0, 0);
+            J[id] = TS(dcoord(g, x, i, 0, 0, 0));
         } else {
             const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
             const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
-            J[id] = x1 * y2 - x2 * y1;
+            J[id] = TS(x1 * y2 - x2 * y1);
         }
     }
 }
 
+template <class TS>
 __global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const double* v, const double* p,
-                               const double* J, double* JU) {
+                               const TS* J, TS* JU) {
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const double r = rho[id];
@@ -92,10 +94,10 @@ __global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const dou
         double ke = 0.0;
         for (int k = 0; k < g.dim; ++k) ke += v[k * N + id] * v[k * N + id];
         const double E = r * (G.cv * T - G.a * r) + 0.5 * r * ke;
-        const double Jv = J[id];
-        JU[id] = Jv * r;
-        for (int k = 0; k < g.dim; ++k) JU[(1 + k) * N + id] = Jv * r * v[k * N + id];
-        JU[(1 + g.dim) * N + id] = Jv * E;
+        const double Jv = double(J[id]);
+        JU[id] = TS(Jv * r);
+        for (int k = 0; k < g.dim; ++k) JU[(1 + k) * N + id] = TS(Jv * r * v[k * N + id]);
+        JU[(1 + g.dim) * N + id] = TS(Jv * E);
     }
 }
 
@@ -110,16 +112,17 @@ __global__ void k_reset(DevScalars* d) {
 }
 
 // eq. cfl: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), with zero mesh velocity
-__global__ void k_cfl(GridParams g, Gas G, const double* JU, const double* J, const double* x, DevScalars* d) {
+template <class TS>
+__global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const double* x, DevScalars* d) {
     const int N = g.n1 * g.n2;
     double m = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        const double iJ = 1.0 / J[id];
-        const double rho = JU[id] * iJ;
-        const double v1 = JU[N + id] * iJ / rho;
-        const double v2 = g.dim == 2 ? JU[2 * N + id] * iJ / rho : 0.0;
-        const double E = JU[(g.dim + 1) * N + id] * iJ;
+        const double iJ = 1.0 / double(J[id]);
+        const double rho = double(JU[id]) * iJ;
+        const double v1 = double(JU[N + id]) * iJ / rho;
+        const double v2 = g.dim == 2 ? double(JU[2 * N + id]) * iJ / rho : 0.0;
+        const double E = double(JU[(g.dim + 1) * N + id]) * iJ;
         const double T = (E / rho - 0.5 * (v1 * v1 + v2 * v2) + G.a * rho) / G.cv;
         const double om = 1.0 - G.b * rho;
         const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
@@ -172,17 +175,18 @@ __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalar
 
 // ------------------------------------------------------------ monitor (Sec. 4)
 // density and fundamental derivative G = nu^3 p_nunu|_s / (2 c^2) at the nodes
-__global__ void k_mon_fields(GridParams g, Gas G, const double* JU, const double* J, double* rhoF, double* GF) {
+template <class TS>
+__global__ void k_mon_fields(GridParams g, Gas G, const TS* JU, const TS* J, double* rhoF, double* GF) {
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const double iJ = 1.0 / J[id];
-        const double rho = JU[id] * iJ;
+        const double iJ = 1.0 / double(J[id]);
+        const double rho = double(JU[id]) * iJ;
         double ke = 0.0;
         for (int k = 0; k < g.dim; ++k) {
-            const double v = JU[(1 + k) * N + id] * iJ / rho;
+            const double v = double(JU[(1 + k) * N + id]) * iJ / rho;
             ke += v * v;
         }
-        const double E = JU[(g.dim + 1) * N + id] * iJ;
+        const double E = double(JU[(g.dim + 1) * N + id]) * iJ;
         const double T = (E / rho - 0.5 * ke + G.a * rho) / G.cv;
         const double om = 1.0 - G.b * rho;
         const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
@@ -354,6 +358,47 @@ __global__ void k_velocity(GridParams g, const double* xn, const double* xit, De
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
         xdot[id] = f * (xit[id] - xn[id]);
     if (blockIdx.x == 0 && threadIdx.x == 0) d->gamma = gam;
+}
+
+// Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)
+// and FP32 mesh velocity, once per step (the base is linear in the node index,
+// so delta_k of it is exactly dxi_k e_k)
+__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd) {
+    const int N = g.n1 * g.n2;
+    const double x00 = x[0];
+    const double y00 = g.dim == 2 ? x[N] : 0.0;
+    const double dxi1 = 1.0 / g.inv_dxi[0];
+    const double dxi2 = g.dim == 2 ? 1.0 / g.inv_dxi[1] : 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        disp[id] = float(x[id] - (x00 + i * dxi1));
+        if (g.dim == 2) disp[N + id] = float(x[N + id] - (y00 + j * dxi2));
+        for (int k = 0; k < g.dim; ++k) fxd[k * N + id] = xdot ? float(xdot[k * N + id]) : 0.0f;
+    }
+}
+
+// launchers of the kernels templated on the state type (float in the mixed form)
+void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int grid, cudaStream_t s) {
+    if (f32) k_init_J<float><<<grid, 256, 0, s>>>(g, x, (float*)J);
+    else k_init_J<double><<<grid, 256, 0, s>>>(g, x, (double*)J);
+}
+
+void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
+                         const void* J, void* JU, bool f32, int grid, cudaStream_t s) {
+    if (f32) k_prim_to_cons<float><<<grid, 256, 0, s>>>(g, G, rho, v, p, (const float*)J, (float*)JU);
+    else k_prim_to_cons<double><<<grid, 256, 0, s>>>(g, G, rho, v, p, (const double*)J, (double*)JU);
+}
+
+void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x, DevScalars* d,
+                bool f32, int grid, cudaStream_t s) {
+    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, d);
+    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, d);
+}
+
+void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,
+                       bool f32, int grid, cudaStream_t s) {
+    if (f32) k_mon_fields<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, rhoF, GF);
+    else k_mon_fields<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, rhoF, GF);
 }
 
 }  // namespace es

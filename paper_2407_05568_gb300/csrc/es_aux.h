@@ -31,15 +31,19 @@ struct DevScalars {
     DevStatus status;
 };
 
-__global__ void k_init_J(GridParams g, const double* x, double* J);
-__global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const double* v, const double* p,
-                               const double* J, double* JU);
+// kernels templated on the state type are launched through these (f32: float state)
+void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int grid, cudaStream_t s);
+void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
+                         const void* J, void* JU, bool f32, int grid, cudaStream_t s);
+void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x, DevScalars* d,
+                bool f32, int grid, cudaStream_t s);
+void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,
+                       bool f32, int grid, cudaStream_t s);
 __global__ void k_reset(DevScalars* d);
-__global__ void k_cfl(GridParams g, Gas G, const double* JU, const double* J, const double* x, DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
 __global__ void k_set_dt(DevScalars* d, double dt);
 __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
-__global__ void k_mon_fields(GridParams g, Gas G, const double* JU, const double* J, double* rhoF, double* GF);
+__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd);
 __global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, const double* GF, double* t0,
                             double* t1, double* t2, DevScalars* d);
 __global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,

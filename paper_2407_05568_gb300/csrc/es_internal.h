@@ -32,6 +32,15 @@ struct StageParams {
     double* Jo;
     int mode;                     // 0: RK combination; 1: write the right-hand sides
     DevStatus* status;
+    // mixed form: float state and float mesh displacement / velocity
+    const float* fJUn;
+    const float* fJn;
+    const float* fJUs;
+    const float* fJs;
+    float* fJUo;
+    float* fJo;
+    const float* fdisp;           // x - (x_00 + i dxi_1, y_00 + j dxi_2), [dim][n2][n1]
+    const float* fxdot;           // mesh velocity, [dim][n2][n1] (nullable)
 };
 
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s);

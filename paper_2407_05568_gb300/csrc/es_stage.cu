@@ -28,7 +28,7 @@ enum Field {
     F_COUNT
 };
 
-template <int DIM, int BX, int BY>
+template <int DIM, int BX, int BY, int NT>
 struct Tile {
     static constexpr int GX = BX + 6;
     static constexpr int GY = DIM == 2 ? BY + 6 : 1;
@@ -44,7 +44,9 @@ struct Tile {
     static constexpr int NF = NF1 > NF2 ? NF1 : NF2;
     static constexpr int PAIR_DOUBLES = (NP * NC > 4 * NB) ? NP * NC : 4 * NB;   // also holds coords
     static constexpr size_t SMEM = sizeof(double) * (size_t(F_COUNT) * NB + PAIR_DOUBLES + NF * (NC + 1));
-    static constexpr int THREADS = BX * (DIM == 2 ? BY : 1);
+    // one thread per face of the larger direction, so each face phase is one pass
+    static constexpr int THREADS = NT;
+    static_assert(NT >= BX * (DIM == 2 ? BY : 1) && NT % 32 == 0, "threads cover the tile");
 };
 
 // --------------------------------------------------------------- pair flux
@@ -311,10 +313,10 @@ __device__ __forceinline__ void stage_coords(const StageParams& P, int gi, int g
     }
 }
 
-template <int DIM, int BX, int BY>
-__global__ void __launch_bounds__(Tile<DIM, BX, BY>::THREADS, 1)
+template <int DIM, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT, 1)
 stage_kernel_fp64(StageParams P) {
-    using TL = Tile<DIM, BX, BY>;
+    using TL = Tile<DIM, BX, BY, NT>;
     constexpr int GX = TL::GX, GY = TL::GY, NB = TL::NB, NC = TL::NC;
     extern __shared__ double smem[];
     double* S = smem;                                   // F_COUNT * NB
@@ -458,7 +460,7 @@ stage_kernel_fp64(StageParams P) {
         }
         __syncthreads();
         // ---- E: divergence at the interior node (tx, ty)
-        {
+        if (tid < BX * (DIM == 2 ? BY : 1)) {
             const int line = k == 0 ? ty : tx;
             const int pos = k == 0 ? tx : ty;
             const int fm = line * (LB + 1) + pos;           // face pos - 1/2
@@ -471,7 +473,7 @@ stage_kernel_fp64(StageParams P) {
 
     // ---- F: Shu-Osher combination (or the bare right-hand side)
     const int gi = i0 + tx, gj = j0 + ty;
-    if (gi < P.n1 && (DIM == 1 || gj < P.n2)) {
+    if (tid < BX * (DIM == 2 ? BY : 1) && gi < P.n1 && (DIM == 1 || gj < P.n2)) {
         const size_t N = size_t(P.n1) * P.n2;
         const size_t idx = size_t(DIM == 2 ? gj : 0) * P.n1 + gi;
         if (P.mode == 1) {
@@ -491,28 +493,30 @@ stage_kernel_fp64(StageParams P) {
 }
 
 // ----------------------------------------------------------------- launch
-template <int DIM, int BX, int BY>
+template <int DIM, int BX, int BY, int NT>
 static cudaError_t prepare_tile() {
-    return cudaFuncSetAttribute(stage_kernel_fp64<DIM, BX, BY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(Tile<DIM, BX, BY>::SMEM));
+    return cudaFuncSetAttribute(stage_kernel_fp64<DIM, BX, BY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(Tile<DIM, BX, BY, NT>::SMEM));
 }
 
-template <int DIM, int BX, int BY>
+template <int DIM, int BX, int BY, int NT>
 static cudaError_t launch_tile(const StageParams& P, cudaStream_t s) {
-    using TL = Tile<DIM, BX, BY>;
+    using TL = Tile<DIM, BX, BY, NT>;
     const int ntx = (P.n1 + BX - 1) / BX;
     const int nty = DIM == 2 ? (P.n2 + BY - 1) / BY : 1;
-    stage_kernel_fp64<DIM, BX, BY><<<ntx * nty, TL::THREADS, TL::SMEM, s>>>(P);
+    stage_kernel_fp64<DIM, BX, BY, NT><<<ntx * nty, NT, TL::SMEM, s>>>(P);
     return cudaGetLastError();
 }
 
+// 2D: 32 x 8 nodes, 288 threads (= the 32 x 9 faces of xi_2); 1D: 254 nodes,
+// 256 threads (255 faces, 768 pairs = three passes)
 cudaError_t stage_prepare_fp64(int dim) {
-    return dim == 1 ? prepare_tile<1, 256, 1>() : prepare_tile<2, 32, 8>();
+    return dim == 1 ? prepare_tile<1, 254, 1, 256>() : prepare_tile<2, 32, 8, 288>();
 }
 
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s) {
-    if (P.dim == 1) return launch_tile<1, 256, 1>(P, s);
-    return launch_tile<2, 32, 8>(P, s);
+    if (P.dim == 1) return launch_tile<1, 254, 1, 256>(P, s);
+    return launch_tile<2, 32, 8, 288>(P, s);
 }
 
 }  // namespace es

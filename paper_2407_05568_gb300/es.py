@@ -79,7 +79,7 @@ def lib():
     return _lib
 
 
-def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=1e-12):
+def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=None):
     """es_params from a workload description (see workloads.py)."""
     p = EsParams()
     g = w["gas"]
@@ -93,7 +93,9 @@ def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e
         p.bc[k] = ES_BC[w["bc"][k]]
     p.weno_gamma[:] = (0.005, 0.045, 0.95)
     p.weno_eps = weno_eps
-    p.sign_tol = sign_tol
+    # round-off size of a zero plain jump: FP64 rounding, or the FP32 rounding of the
+    # entropy-variable jumps (whose c_v-sized terms cancel in W)
+    p.sign_tol = sign_tol if sign_tol is not None else (1e-12 if precision == "fp64" else 1e-5)
     p.dissipation = int(dissipation)
     p.cfl = w.get("cfl", 0.4)
     p.dt_fixed = dt_fixed
@@ -111,11 +113,13 @@ def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e
     return p
 
 
-def _ptr(t):
+def _ptr(t, dtype=None):
     if t is None:
         return None
     if not (t.is_cuda and t.dtype.is_floating_point and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA float tensor")
+    if dtype is not None and str(t.dtype) != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -131,6 +135,7 @@ class Context:
 
     def __init__(self, params, stream=None):
         self.params = params
+        self.state_dtype = "torch.float32" if params.precision == ES_PREC["mixed"] else "torch.float64"
         self._h = ctypes.c_void_p()
         rc = lib().es_create(ctypes.byref(self._h), ctypes.byref(params), _stream_handle(stream))
         if rc != ES_OK:
@@ -156,39 +161,49 @@ def es_create(params, stream=None):
     return Context(params, stream)
 
 
+F64 = "torch.float64"
+
+
 def es_init_mesh(ctx, x, J):
-    ctx._call(lib().es_init_mesh(ctx._h, _ptr(x), _ptr(J)))
+    ctx._call(lib().es_init_mesh(ctx._h, _ptr(x, F64), _ptr(J, ctx.state_dtype)))
 
 
 def es_prim_to_cons(ctx, rho, v, p, J, JU):
-    ctx._call(lib().es_prim_to_cons(ctx._h, _ptr(rho), _ptr(v), _ptr(p), _ptr(J), _ptr(JU)))
+    S = ctx.state_dtype
+    ctx._call(lib().es_prim_to_cons(ctx._h, _ptr(rho, F64), _ptr(v, F64), _ptr(p, F64), _ptr(J, S), _ptr(JU, S)))
 
 
 def es_rhs(ctx, JU, J, x, xdot, dJU, dJ):
-    ctx._call(lib().es_rhs(ctx._h, _ptr(JU), _ptr(J), _ptr(x), _ptr(xdot), _ptr(dJU), _ptr(dJ)))
+    S = ctx.state_dtype
+    ctx._call(lib().es_rhs(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), _ptr(xdot, F64), _ptr(dJU, S),
+                           _ptr(dJ, S)))
 
 
 def es_rk_stage(ctx, stage, dt, JUn, Jn, JUs, Js, xn, xdot, JU_out, J_out):
-    ctx._call(lib().es_rk_stage(ctx._h, stage, dt, _ptr(JUn), _ptr(Jn), _ptr(JUs), _ptr(Js), _ptr(xn),
-                                _ptr(xdot), _ptr(JU_out), _ptr(J_out)))
+    S = ctx.state_dtype
+    ctx._call(lib().es_rk_stage(ctx._h, stage, dt, _ptr(JUn, S), _ptr(Jn, S), _ptr(JUs, S), _ptr(Js, S),
+                                _ptr(xn, F64), _ptr(xdot, F64), _ptr(JU_out, S), _ptr(J_out, S)))
 
 
 def es_cfl_dt(ctx, JU, J, x):
+    S = ctx.state_dtype
     dt = ctypes.c_double()
-    ctx._call(lib().es_cfl_dt(ctx._h, _ptr(JU), _ptr(J), _ptr(x), ctypes.byref(dt)))
+    ctx._call(lib().es_cfl_dt(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(dt)))
     return dt.value
 
 
 def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot):
+    S = ctx.state_dtype
     sw = ctypes.c_int()
     gam = ctypes.c_double()
-    ctx._call(lib().es_mesh_redistribute(ctx._h, _ptr(JU), _ptr(J), _ptr(xn), dt, _ptr(xdot),
+    ctx._call(lib().es_mesh_redistribute(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(xn, F64), dt, _ptr(xdot, F64),
                                          ctypes.byref(sw), ctypes.byref(gam)))
     return sw.value, gam.value
 
 
 def es_steps(ctx, JU, J, x, nsteps, t_end):
-    ctx._call(lib().es_steps(ctx._h, _ptr(JU), _ptr(J), _ptr(x), int(nsteps), float(t_end)))
+    S = ctx.state_dtype
+    ctx._call(lib().es_steps(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), int(nsteps), float(t_end)))
 
 
 def es_set_time(ctx, t):
@@ -203,11 +218,12 @@ def es_get_time(ctx):
 
 
 def es_run_host(ctx, JU, J, x, nsteps, t_end):
-    """JU, J, x: C-contiguous float64 numpy arrays (pinned or pageable host memory), updated in place."""
+    """JU, J (state precision) and x (float64): C-contiguous numpy arrays in host memory, updated in place."""
     arrs = [JU, J, x]
-    for a in arrs:
-        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
-            raise ValueError("expected C-contiguous float64 arrays")
+    sdt = np.float32 if ctx.state_dtype == "torch.float32" else np.float64
+    for a, dt in zip(arrs, (sdt, sdt, np.float64)):
+        if not (isinstance(a, np.ndarray) and a.dtype == dt and a.flags.c_contiguous):
+            raise ValueError("expected C-contiguous arrays of the state precision (x: float64)")
     ptrs = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
     ctx._call(lib().es_run_host(ctx._h, *ptrs, int(nsteps), float(t_end)))
 

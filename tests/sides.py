@@ -28,13 +28,14 @@ def gpu_setup(w, precision="fp64", dissipation=True, x=None, dt_fixed=0.0):
     p = es.make_params(w, precision=precision, dissipation=dissipation, dt_fixed=dt_fixed)
     ctx = es.es_create(p)
     x = w["x"] if x is None else x
+    sdt = torch.float32 if precision == "mixed" else torch.float64
     xt = torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
-    J = torch.empty(x.shape[1:], dtype=torch.float64, device=dev)
+    J = torch.empty(x.shape[1:], dtype=sdt, device=dev)
     es.es_init_mesh(ctx, xt, J)
     rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
     v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
     pr = torch.tensor(w["p"], dtype=torch.float64, device=dev)
-    JU = torch.empty((w["dim"] + 2,) + x.shape[1:], dtype=torch.float64, device=dev)
+    JU = torch.empty((w["dim"] + 2,) + x.shape[1:], dtype=sdt, device=dev)
     es.es_prim_to_cons(ctx, rho, v, pr, J, JU)
     return ctx, JU, J, xt
 
@@ -47,4 +48,4 @@ def rel_l1(a, b):
 
 
 def to_np(t):
-    return t.detach().cpu().numpy()
+    return t.detach().cpu().double().numpy()

@@ -1,0 +1,114 @@
+"""The mixed-precision form (FP32 state and stage arithmetic) against the FP64 oracle.
+
+Bar: <= 1e-5 relative L1 against the oracle at the final time on smooth
+problems, with the design order of the scheme preserved above the FP32 floor.
+On discontinuous data the sign switch Y takes some decisions differently in
+FP32 (a plain jump within FP32 round-off counts as zero), so the bound there
+is 1e-4 after a few steps.
+"""
+import numpy as np
+import pytest
+
+from oracle import operator as op
+from oracle import stepper
+from paper_2407_05568_gb300 import workloads as wl
+
+from sides import gpu_setup, oracle_setup, rel_l1, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_05568_gb300 import build
+    build.build()
+
+
+def _wavy(n=40):
+    w = wl.sine_2d(n)
+    X, Y = w["x"]
+    w["x"] = wl.wavy_mesh_2d(X, Y)
+    w["rho"], w["v"], w["p"] = wl.smooth_state_2d(X, Y)
+    w["xdot"] = wl.mesh_velocity_2d(X, Y)
+    return w
+
+
+@pytest.mark.parametrize("case", ["sine1d", "sine2d", "wavy", "vortex"])
+def test_mixed_rhs_vs_oracle(case):
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = {"sine1d": lambda: wl.sine_1d(200), "sine2d": lambda: wl.sine_2d(48), "wavy": _wavy,
+         "vortex": lambda: wl.isentropic_vortex(48)}[case]()
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    xd = w.get("xdot", np.zeros_like(w["x"]))
+    dU_o, dJ_o = op.rhs(sch, JU_o, J_o, x, xd)
+    xdt = torch.tensor(np.ascontiguousarray(xd), dtype=torch.float64, device="cuda")
+    dU = torch.empty_like(JU)
+    dJ = torch.empty_like(J)
+    es.es_rhs(ctx, JU, J, xt, xdt, dU, dJ)
+    assert es.es_check(ctx) == 0
+    scale = np.abs(JU_o).sum() / min(w["dxi"])
+    err = np.abs(to_np(dU) - dU_o).sum() / scale
+    assert err < 2e-6, err
+
+
+def _run_both(w, t_end, dt_fixed=None):
+    from paper_2407_05568_gb300 import es
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    JU_o, J_o, x_o, n = stepper.run(sch, mc, JU_o, J_o, x_o, t_end, w["cfl"], dt_fixed=dt_fixed)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed", dt_fixed=dt_fixed or 0.0)
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, n + 2, t_end)
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    t, _ = es.es_get_time(ctx)
+    assert t == pytest.approx(t_end, rel=1e-12)
+    return JU_o, J_o, x_o, to_np(JU), to_np(J), to_np(xt)
+
+
+@pytest.mark.parametrize("case", ["sine1d", "sine2d", "vortex"])
+def test_mixed_final_time_vs_oracle(case):
+    """Relative L1 of (JU, J) against the FP64 oracle at the final time <= 1e-5."""
+    w, t_end = {"sine1d": (wl.sine_1d(200), 0.1), "sine2d": (wl.sine_2d(40), 0.05),
+                "vortex": (wl.isentropic_vortex(32), 0.5)}[case]
+    JU_o, J_o, x_o, JU, J, x = _run_both(w, t_end)
+    assert rel_l1(JU, JU_o) < 1e-5, rel_l1(JU, JU_o)
+    assert rel_l1(J, J_o) < 1e-6
+
+
+def test_mixed_riemann_moving_mesh_few_steps():
+    """The 2D vdW Riemann problem on the moving mesh, 3 steps (discontinuous data)."""
+    w = wl.riemann_2d(64, seed=5)
+    from paper_2407_05568_gb300 import es
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    t = 0.0
+    for _ in range(3):
+        JU_o, J_o, x_o, t, _ = stepper.step(sch, mc, JU_o, J_o, x_o, t, w["t_end"], w["cfl"])
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, 3, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    assert rel_l1(to_np(JU), JU_o) < 1e-4, rel_l1(to_np(JU), JU_o)
+    assert rel_l1(to_np(xt), x_o) < 1e-5
+
+
+def test_mixed_design_order_1d():
+    """Example 5.1 setup (fixed mesh, dt = 0.4 dxi^(5/3)): the mixed form keeps ~5th order."""
+    from paper_2407_05568_gb300 import es
+    errs = []
+    for n in (20, 40, 80):
+        w = wl.sine_1d(n, t_end=0.05)
+        dt = 0.4 * w["dxi"][0] ** (5.0 / 3.0)
+        ctx, JU, J, xt = gpu_setup(w, precision="mixed", dt_fixed=dt)
+        es.es_set_time(ctx, 0.0)
+        es.es_steps(ctx, JU, J, xt, int(np.ceil(w["t_end"] / dt)) + 2, w["t_end"])
+        assert es.es_check(ctx) == 0
+        rho = to_np(JU)[0] / to_np(J)
+        ex = 0.5 + 0.2 * np.sin(2 * np.pi * (w["x"][0] - w["t_end"]))
+        errs.append(np.abs(rho - ex).mean())
+    order = np.log2(errs[-2] / errs[-1])
+    assert order > 4.5, errs
