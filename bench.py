@@ -189,9 +189,9 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         ctx = es.es_create(es.make_params(w, precision=args.precision), stream)
         x0 = torch.tensor(w["x"], dtype=torch.float64, device=dev)
-        J0 = torch.empty(w["x"].shape[1:], dtype=torch.float64, device=dev)
+        J0 = es.state_empty(ctx, w["x"].shape[1:], dev)
         es.es_init_mesh(ctx, x0, J0)
-        JU0 = torch.empty((4,) + w["x"].shape[1:], dtype=torch.float64, device=dev)
+        JU0 = es.state_empty(ctx, (4,) + w["x"].shape[1:], dev)
         es.es_prim_to_cons(ctx, torch.tensor(w["rho"], device=dev), torch.tensor(w["v"], device=dev),
                            torch.tensor(w["p"], device=dev), J0, JU0)
         JU, J, x = JU0.clone(), J0.clone(), x0.clone()

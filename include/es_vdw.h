@@ -9,8 +9,10 @@
  *   structure of arrays, xi_1 fastest:  field[c][j][i] at c*n1*n2 + j*n1 + i.
  *     JU : (dim + 2) components (rho, rho v_1, [rho v_2], E) times J
  *     J  : 1 component
- *     JU, J (and dJU, dJ) hold double in ES_PREC_FP64 and float in ES_PREC_MIXED;
- *     they are passed as void*.
+ *     JU, J (and dJU, dJ) hold double in ES_PREC_FP64.  In ES_PREC_MIXED they
+ *     hold compensated float pairs in two planes: [2][dim+2][n2][n1] for JU and
+ *     [2][n2][n1] for J, value = hi plane + lo plane (a 48-bit significand in
+ *     8 bytes, like a double).  They are passed as void*.
  *     x  : dim components (x_1, [x_2]) of the node coordinates, double
  *     xdot : dim components of the mesh velocity, double
  *   The computational mesh is uniform with spacings dxi[k]; x(xi) maps it to
@@ -50,10 +52,11 @@ extern "C" {
 
 /* arithmetic of the operator */
 #define ES_PREC_FP64   0        /* every step in double */
-#define ES_PREC_MIXED  1        /* float state and per-stage arithmetic (entropy-variable jumps by the
-                                   paper's jump decomposition, mesh as an FP32 displacement); the
-                                   mesh redistribution and the mesh itself stay double.  Periodic
-                                   directions need period[k] = n_k dxi[k]. */
+#define ES_PREC_MIXED  1        /* per-stage arithmetic on the FP32 pipe: the state and the primitive
+                                   variables in double-float (hi + lo float pairs), fluxes and WENO in
+                                   float, entropy-variable jumps by the paper's jump decomposition, the
+                                   mesh as an FP32 displacement; the mesh redistribution and the mesh
+                                   itself stay double.  Periodic directions need period[k] = n_k dxi[k]. */
 
 /* monitor functions of Sec. 4 / Example 5.1 */
 #define ES_MONITOR_VDW    0     /* eq. van der Waalsmonitor: delta_1 = rho, delta_2 = G, plus |Delta G|^2 */
@@ -72,7 +75,8 @@ typedef struct es_params {
     double weno_eps;        /* smoothness regulariser (paper silent; 1e-12) */
     double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| no larger than sign_tol times
                                sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|), the size of the terms forming
-                               it, is round-off of a zero jump and has sign 0 (1e-12 in FP64) */
+                               it, is round-off of a zero jump and has sign 0 (Y = 0): 1e-12 in
+                               ES_PREC_FP64, 4e-7 (a few FP32 roundings) in ES_PREC_MIXED */
     int    dissipation;     /* 1: ES flux eq. HOstable; 0: the EC flux alone */
     double cfl;             /* eq. cfl; 0.4 in 1D/2D */
     double dt_fixed;        /* > 0: use this Delta t instead of eq. cfl (Example 5.1 uses CFL dxi^(5/3)) */

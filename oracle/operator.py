@@ -22,7 +22,8 @@ Readings of points the paper leaves open (each listed in the design notes):
     (1e-12) times the size of the terms that form it, sum_a |R_am|
     (|(TV_i)_a| + |(TV_{i+1})_a|), is round-off of an exactly zero jump and
     has sign 0 (so Y = 0), which keeps the switch from turning on or off on
-    the last bits of equal states.
+    the last bits of equal states; Y = 0 adds no entropy, so the flux stays
+    entropy stable.
 """
 from dataclasses import dataclass, field
 from fractions import Fraction

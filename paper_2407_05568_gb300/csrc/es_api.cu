@@ -292,7 +292,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->N = size_t(c->g.n1) * c->g.n2;
     c->nc = p->dim + 2;
     c->mixed = p->precision == ES_PREC_MIXED;
-    c->esz = c->mixed ? sizeof(float) : sizeof(double);
+    c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     const size_t blocks = (c->N + 255) / 256;

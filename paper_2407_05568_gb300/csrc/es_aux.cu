@@ -68,6 +68,19 @@ __device__ __forceinline__ double block_reduce_min(double v) {
     return v;
 }
 
+// state element access: double arrays, or the mixed form's (hi, lo) float planes
+// (value = hi + lo, the lo plane `plane` elements after the hi plane)
+__device__ __forceinline__ double ld_state(const double* a, size_t, size_t i) { return a[i]; }
+__device__ __forceinline__ double ld_state(const float* a, size_t plane, size_t i) {
+    return double(a[i]) + double(a[plane + i]);
+}
+__device__ __forceinline__ void st_state(double* a, size_t, size_t i, double v) { a[i] = v; }
+__device__ __forceinline__ void st_state(float* a, size_t plane, size_t i, double v) {
+    const float hi = float(v);
+    a[i] = hi;
+    a[plane + i] = float(v - double(hi));
+}
+
 // ------------------------------------------------------------ init
 template <class TS>
 __global__ void k_init_J(GridParams g, const double* x, TS* J) {
@@ -75,11 +88,11 @@ __global__ void k_init_J(GridParams g, const double* x, TS* J) {
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         if (g.dim == 1) {
-            J[id] = TS(dcoord(g, x, i, 0, 0, 0));
+            st_state(J, N, id, dcoord(g, x, i, 0, 0, 0));
         } else {
             const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
             const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
-            J[id] = TS(x1 * y2 - x2 * y1);
+            st_state(J, N, id, x1 * y2 - x2 * y1);
         }
     }
 }
@@ -94,10 +107,11 @@ __global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const dou
         double ke = 0.0;
         for (int k = 0; k < g.dim; ++k) ke += v[k * N + id] * v[k * N + id];
         const double E = r * (G.cv * T - G.a * r) + 0.5 * r * ke;
-        const double Jv = double(J[id]);
-        JU[id] = TS(Jv * r);
-        for (int k = 0; k < g.dim; ++k) JU[(1 + k) * N + id] = TS(Jv * r * v[k * N + id]);
-        JU[(1 + g.dim) * N + id] = TS(Jv * E);
+        const double Jv = ld_state(J, N, id);
+        const size_t P = size_t(g.dim + 2) * N;
+        st_state(JU, P, id, Jv * r);
+        for (int k = 0; k < g.dim; ++k) st_state(JU, P, (1 + k) * N + id, Jv * r * v[k * N + id]);
+        st_state(JU, P, (1 + g.dim) * N + id, Jv * E);
     }
 }
 
@@ -118,11 +132,12 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
     double m = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        const double iJ = 1.0 / double(J[id]);
-        const double rho = double(JU[id]) * iJ;
-        const double v1 = double(JU[N + id]) * iJ / rho;
-        const double v2 = g.dim == 2 ? double(JU[2 * N + id]) * iJ / rho : 0.0;
-        const double E = double(JU[(g.dim + 1) * N + id]) * iJ;
+        const size_t P = size_t(g.dim + 2) * N;
+        const double iJ = 1.0 / ld_state(J, N, id);
+        const double rho = ld_state(JU, P, id) * iJ;
+        const double v1 = ld_state(JU, P, N + id) * iJ / rho;
+        const double v2 = g.dim == 2 ? ld_state(JU, P, 2 * N + id) * iJ / rho : 0.0;
+        const double E = ld_state(JU, P, (g.dim + 1) * N + id) * iJ;
         const double T = (E / rho - 0.5 * (v1 * v1 + v2 * v2) + G.a * rho) / G.cv;
         const double om = 1.0 - G.b * rho;
         const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
@@ -179,14 +194,15 @@ template <class TS>
 __global__ void k_mon_fields(GridParams g, Gas G, const TS* JU, const TS* J, double* rhoF, double* GF) {
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const double iJ = 1.0 / double(J[id]);
-        const double rho = double(JU[id]) * iJ;
+        const size_t P = size_t(g.dim + 2) * N;
+        const double iJ = 1.0 / ld_state(J, N, id);
+        const double rho = ld_state(JU, P, id) * iJ;
         double ke = 0.0;
         for (int k = 0; k < g.dim; ++k) {
-            const double v = double(JU[(1 + k) * N + id]) * iJ / rho;
+            const double v = ld_state(JU, P, (1 + k) * N + id) * iJ / rho;
             ke += v * v;
         }
-        const double E = double(JU[(g.dim + 1) * N + id]) * iJ;
+        const double E = ld_state(JU, P, (g.dim + 1) * N + id) * iJ;
         const double T = (E / rho - 0.5 * ke + G.a * rho) / G.cv;
         const double om = 1.0 - G.b * rho;
         const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;

@@ -2,8 +2,14 @@
 //
 // GB300 runs FP32 about 70 times faster than FP64 (2 FP64 FMA lanes per SM per
 // clock), and an FP64 -> FP32 conversion costs as much as an FP64 FMA.  This
-// form therefore keeps the per-stage work entirely in FP32:
-//   * the state JU, J is stored in FP32 (the context's stage buffers too);
+// form therefore keeps the per-stage work entirely on the FP32 pipe:
+//   * the state JU, J is stored as compensated pairs of floats (hi, lo), value
+//     hi + lo with a 48-bit significand, in two planes [2][...] (hi plane first);
+//     the primitive state (rho, v, T) and the RK combination are evaluated in
+//     double-float arithmetic (error-free sums and products built from FP32
+//     FMA), so the jumps of rho, v and T between neighbouring nodes keep their
+//     digits even where they are far below the FP32 resolution of the values
+//     (near smooth extrema); everything else is plain FP32 on the hi parts;
 //   * the mesh enters as an FP32 displacement d = x - (x_00 + i dxi_1, y_00 + j dxi_2)
 //     and an FP32 mesh velocity, converted from the FP64 mesh once per step, so
 //     the metric differences delta_k[x] = dxi_k e_k + delta_k[d] lose no digits;
@@ -29,6 +35,7 @@ namespace {
 
 enum FieldF {
     G_RHO, G_V1, G_V2, G_T, G_IT, G_OM, G_IOM, G_G, G_RT, G_VT1, G_VT2, G_V2T, G_RV1, G_RV2, G_RP,
+    G_RHOL, G_V1L, G_V2L, G_TL,   // low parts of rho, v, T (double-float)
     G_N1X, G_N1Y, G_XT1, G_N2X, G_N2Y, G_XT2,
     G_COUNT
 };
@@ -51,18 +58,59 @@ struct TileF {
 };
 
 struct GasF {
-    float a, b, R, cv, delta, Rb;
+    float a, b, R, cv, delta, Rb, icv;
 };
 
 struct WenoF {
     float g1, g2, g3, g12, ig22, ig3, eps, sign_tol;
 };
 
+// ---- double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + x.lo + y.lo);
+}
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    df s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, s.lo + x.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df x, float y) {
+    const float p = x.hi * y;
+    const float e = fmaf(x.hi, y, -p) + x.lo * y;
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_recip(df y) {
+    const float q1 = 1.0f / y.hi;
+    // r = 1 - q1 y, exactly enough: fma gives the low part of q1 y.hi
+    const float r = fmaf(-q1, y.hi, 1.0f) - q1 * y.lo;
+    return fast_two_sum(q1, r * q1);
+}
+__device__ __forceinline__ float df_diff(df a, df b) {            // (a - b) rounded to float
+    return (a.hi - b.hi) + (a.lo - b.lo);
+}
+
 // reciprocal logarithmic mean 1/{a}^ln from the relative jump f = (a_l - a_r)/(a_l + a_r):
 // [[ln a]] = ln((1 + f)/(1 - f)) = 2 artanh(f); series of artanh(f)/f for |f| < 0.05
-__device__ __forceinline__ float inv_log_mean_f(float al, float ar) {
+__device__ __forceinline__ float inv_log_mean_j(float al, float ar, float d) {
+    // d = a_l - a_r, passed in when known to more digits than al - ar
     const float s = al + ar;
-    const float d = al - ar;
     const float is = 1.0f / s;
     const float f = d * is;
     if (fabsf(f) < 0.05f) {
@@ -72,6 +120,8 @@ __device__ __forceinline__ float inv_log_mean_f(float al, float ar) {
     }
     return log1pf(2.0f * f / (1.0f - f)) / d;
 }
+
+__device__ __forceinline__ float inv_log_mean_f(float al, float ar) { return inv_log_mean_j(al, ar, al - ar); }
 
 __device__ __forceinline__ float mr_weno5_f(float wm2, float wm1, float w0, float wp1, float wp2, const WenoF& c) {
     const float q2 = (-wm1 + 5.0f * w0 + 2.0f * wp1) * (1.0f / 6.0f);
@@ -109,13 +159,14 @@ __device__ __forceinline__ void pair_flux_f(const float* S, int NB, int l, int r
     const float rho_m = 0.5f * (rl + rr);
     const float T_m = 0.5f * (Tl + Tr);
     const float iT_m = 0.5f * (S[G_IT * NB + l] + S[G_IT * NB + r]);
-    const float ilr = inv_log_mean_f(rl, rr);
-    const float ilT = inv_log_mean_f(Tl, Tr);
+    const float drho = (rl - rr) + (S[G_RHOL * NB + l] - S[G_RHOL * NB + r]);
+    const float ilr = inv_log_mean_j(rl, rr, drho);
+    const float ilT = inv_log_mean_j(Tl, Tr, (Tl - Tr) + (S[G_TL * NB + l] - S[G_TL * NB + r]));
     const float Pinv = S[G_IOM * NB + l] * S[G_IOM * NB + r];
     const float iTa = 1.0f / T_m;
     const float coef = G.Rb * Pinv - G.a * iTa;
     float D = G.R * ilr + coef - G.a * iTa;
-    if (G.b > 0.0f) D += G.Rb * inv_log_mean_f(S[G_OM * NB + l], S[G_OM * NB + r]);
+    if (G.b > 0.0f) D += G.Rb * inv_log_mean_j(S[G_OM * NB + l], S[G_OM * NB + r], -G.b * drho);
     const float iD = 1.0f / D;
     const float g_m = 0.5f * (S[G_G * NB + l] + S[G_G * NB + r]);
     const float rT_m = 0.5f * (S[G_RT * NB + l] + S[G_RT * NB + r]);
@@ -157,20 +208,22 @@ template <int DIM>
 __device__ __forceinline__ void entropy_jump(const float* S, int NB, int i, int j, const GasF& G, float* dV) {
     const float ri = S[G_RHO * NB + i], rj = S[G_RHO * NB + j];
     const float Ti = S[G_T * NB + i], Tj = S[G_T * NB + j];
-    const float dr = rj - ri, dT = Tj - Ti;
+    // jumps from the double-float node values: exact hi difference plus lo difference
+    const float dr = (rj - ri) + (S[G_RHOL * NB + j] - S[G_RHOL * NB + i]);
+    const float dT = (Tj - Ti) + (S[G_TL * NB + j] - S[G_TL * NB + i]);
     const float iTa = 2.0f / (Ti + Tj);
-    float crho = G.R * inv_log_mean_f(ri, rj) + G.Rb * S[G_IOM * NB + i] * S[G_IOM * NB + j] - 2.0f * G.a * iTa;
-    if (G.b > 0.0f) crho += G.Rb * inv_log_mean_f(S[G_OM * NB + i], S[G_OM * NB + j]);
+    float crho = G.R * inv_log_mean_j(ri, rj, -dr) + G.Rb * S[G_IOM * NB + i] * S[G_IOM * NB + j] - 2.0f * G.a * iTa;
+    if (G.b > 0.0f) crho += G.Rb * inv_log_mean_j(S[G_OM * NB + i], S[G_OM * NB + j], G.b * dr);
     const float rT = 0.5f * (S[G_RT * NB + i] + S[G_RT * NB + j]);
     const float v2T = 0.5f * (S[G_V2T * NB + i] + S[G_V2T * NB + j]);
-    const float cT = -G.cv * inv_log_mean_f(Ti, Tj) + (2.0f * G.a * rT + 0.5f * v2T) * iTa;
+    const float cT = -G.cv * inv_log_mean_j(Ti, Tj, -dT) + (2.0f * G.a * rT + 0.5f * v2T) * iTa;
     const float v1i = S[G_V1 * NB + i], v1j = S[G_V1 * NB + j];
-    const float dv1 = v1j - v1i;
+    const float dv1 = (v1j - v1i) + (S[G_V1L * NB + j] - S[G_V1L * NB + i]);
     float kin = 0.5f * (v1i + v1j) * dv1;
     dV[1] = (dv1 - 0.5f * (S[G_VT1 * NB + i] + S[G_VT1 * NB + j]) * dT) * iTa;
     if (DIM == 2) {
         const float v2i = S[G_V2 * NB + i], v2j = S[G_V2 * NB + j];
-        const float dv2 = v2j - v2i;
+        const float dv2 = (v2j - v2i) + (S[G_V2L * NB + j] - S[G_V2L * NB + i]);
         kin += 0.5f * (v2i + v2j) * dv2;
         dV[2] = (dv2 - 0.5f * (S[G_VT2 * NB + i] + S[G_VT2 * NB + j]) * dT) * iTa;
     }
@@ -306,37 +359,47 @@ __device__ __forceinline__ void load_node_f(float* S, int NB, int b, const Stage
     const int sj = DIM == 2 ? state_index(gj, P.n2, P.bc[1]) : 0;
     const int idx = sj * P.n1 + si;
     const size_t N = size_t(P.n1) * P.n2;
-    const float iJ = 1.0f / P.fJs[idx];
-    const float rho = P.fJUs[idx] * iJ;
-    const float m1 = P.fJUs[N + idx] * iJ;
-    const float m2 = DIM == 2 ? P.fJUs[2 * N + idx] * iJ : 0.0f;
-    const float E = P.fJUs[(DIM + 1) * N + idx] * iJ;
-    const float irho = 1.0f / rho;
-    const float v1 = m1 * irho, v2 = m2 * irho;
-    const float ke = 0.5f * (v1 * v1 + v2 * v2);
-    const float T = (E * irho - ke + G.a * rho) / G.cv;
-    const float om = 1.0f - G.b * rho;
+    const size_t LO = size_t(DIM + 2) * N;                  // offset of the lo plane of JU
+    // primitive state in double-float arithmetic
+    const df iJ = df_recip({P.fJs[idx], P.fJs[N + idx]});
+    const df rho = df_mul({P.fJUs[idx], P.fJUs[LO + idx]}, iJ);
+    const df m1 = df_mul({P.fJUs[N + idx], P.fJUs[LO + N + idx]}, iJ);
+    const df m2 = DIM == 2 ? df_mul({P.fJUs[2 * N + idx], P.fJUs[LO + 2 * N + idx]}, iJ) : df{0.0f, 0.0f};
+    const df E = df_mul({P.fJUs[(DIM + 1) * N + idx], P.fJUs[LO + (DIM + 1) * N + idx]}, iJ);
+    const df irho = df_recip(rho);
+    const df v1 = df_mul(m1, irho);
+    const df v2 = DIM == 2 ? df_mul(m2, irho) : df{0.0f, 0.0f};
+    const df ke = df_mul_f(df_add(df_mul(v1, v1), df_mul(v2, v2)), 0.5f);
+    // T = (E/rho - |v|^2/2 + a rho) / cv
+    const df e = df_add(df_mul(E, irho), {-ke.hi, -ke.lo});
+    const df Td = df_mul_f(df_add(e, df_mul_f(rho, G.a)), G.icv);
+    const float r = rho.hi, T = Td.hi;
+    const float om = 1.0f - G.b * r;
     const float iom = 1.0f / om;
-    const float p = rho * G.R * T * iom - G.a * rho * rho;
+    const float p = r * G.R * T * iom - G.a * r * r;
     const float iT = 1.0f / T;
-    if (!(rho > 0.0f) || !(om > 0.0f) || !(T > 0.0f) || !(p > 0.0f) ||
-        !(G.R * T - 2.0f * G.a * rho * om * om > 0.0f))
+    if (!(r > 0.0f) || !(om > 0.0f) || !(T > 0.0f) || !(p > 0.0f) ||
+        !(G.R * T - 2.0f * G.a * r * om * om > 0.0f))
         raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
-    S[G_RHO * NB + b] = rho;
-    S[G_V1 * NB + b] = v1;
-    S[G_V2 * NB + b] = v2;
+    S[G_RHO * NB + b] = r;
+    S[G_RHOL * NB + b] = rho.lo;
+    S[G_V1 * NB + b] = v1.hi;
+    S[G_V1L * NB + b] = v1.lo;
+    S[G_V2 * NB + b] = v2.hi;
+    S[G_V2L * NB + b] = v2.lo;
     S[G_T * NB + b] = T;
+    S[G_TL * NB + b] = Td.lo;
     S[G_IT * NB + b] = iT;
     S[G_OM * NB + b] = om;
     S[G_IOM * NB + b] = iom;
-    S[G_G * NB + b] = G.R * iom - G.a * rho * iT;
-    S[G_RT * NB + b] = rho * iT;
-    S[G_VT1 * NB + b] = v1 * iT;
-    S[G_VT2 * NB + b] = v2 * iT;
-    S[G_V2T * NB + b] = 2.0f * ke * iT;
-    S[G_RV1 * NB + b] = m1;
-    S[G_RV2 * NB + b] = m2;
-    S[G_RP * NB + b] = rho / p;
+    S[G_G * NB + b] = G.R * iom - G.a * r * iT;
+    S[G_RT * NB + b] = r * iT;
+    S[G_VT1 * NB + b] = v1.hi * iT;
+    S[G_VT2 * NB + b] = v2.hi * iT;
+    S[G_V2T * NB + b] = 2.0f * ke.hi * iT;
+    S[G_RV1 * NB + b] = m1.hi;
+    S[G_RV2 * NB + b] = m2.hi;
+    S[G_RP * NB + b] = r / p;
 }
 
 // FP32 displacement and mesh velocity at a possibly-ghost node: periodic wrap
@@ -390,6 +453,7 @@ __global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
     G.cv = float(P.gas.cv);
     G.delta = float(P.gas.delta);
     G.Rb = float(P.gas.R * P.gas.b);
+    G.icv = float(1.0 / P.gas.cv);
     WenoF Wc;
     Wc.g1 = float(P.weno.g1);
     Wc.g2 = float(P.weno.g2);
@@ -538,18 +602,34 @@ __global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
     if (tid < BX * (DIM == 2 ? BY : 1) && gi < P.n1 && (DIM == 1 || gj < P.n2)) {
         const size_t N = size_t(P.n1) * P.n2;
         const size_t idx = size_t(DIM == 2 ? gj : 0) * P.n1 + gi;
-        const float ca = float(P.ca), cb = float(P.cb);
+        const size_t LO = size_t(NC) * N;
         if (P.mode == 1) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) P.fJUo[c * N + idx] = acc[c];
+            for (int c = 0; c < NC; ++c) {
+                P.fJUo[c * N + idx] = acc[c];
+                P.fJUo[LO + c * N + idx] = 0.0f;
+            }
             P.fJo[idx] = acc[NC];
+            P.fJo[N + idx] = 0.0f;
         } else {
+            // a_s U^n + b_s (U^s + dt L) in double-float (a_s, b_s are 0, 1, 3/4, 1/4, 1/3, 2/3)
+            const float ca = float(P.ca), cb = float(P.cb);
+            const float ca_lo = float(P.ca - double(ca)), cb_lo = float(P.cb - double(cb));
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                P.fJUo[c * N + idx] = ca * P.fJUn[c * N + idx] + cb * (P.fJUs[c * N + idx] + dt * acc[c]);
-            const float Jnew = ca * P.fJn[idx] + cb * (P.fJs[idx] + dt * acc[NC]);
-            P.fJo[idx] = Jnew;
-            if (!(Jnew > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(idx));
+            for (int c = 0; c <= NC; ++c) {
+                const float* un = c < NC ? P.fJUn + c * N : P.fJn;
+                const float* us = c < NC ? P.fJUs + c * N : P.fJs;
+                float* uo = c < NC ? P.fJUo + c * N : P.fJo;
+                const size_t lo = c < NC ? LO : N;
+                const df Un = {un[idx], un[lo + idx]};
+                const df Us = {us[idx], us[lo + idx]};
+                const df inc = df_add_f(Us, dt * acc[c]);
+                df outv = df_mul(inc, {cb, cb_lo});
+                if (P.ca != 0.0) outv = df_add(outv, df_mul(Un, {ca, ca_lo}));
+                uo[idx] = outv.hi;
+                uo[lo + idx] = outv.lo;
+                if (c == NC && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(idx));
+            }
         }
     }
 }

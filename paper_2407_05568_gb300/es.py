@@ -93,9 +93,10 @@ def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e
         p.bc[k] = ES_BC[w["bc"][k]]
     p.weno_gamma[:] = (0.005, 0.045, 0.95)
     p.weno_eps = weno_eps
-    # round-off size of a zero plain jump: FP64 rounding, or the FP32 rounding of the
-    # entropy-variable jumps (whose c_v-sized terms cancel in W)
-    p.sign_tol = sign_tol if sign_tol is not None else (1e-12 if precision == "fp64" else 1e-5)
+    # round-off size of a zero plain jump, relative to the terms forming it: FP64
+    # rounding, or a few FP32 roundings (the acoustic jumps of an entropy wave cancel
+    # to 1e-7 of their terms near smooth extrema, below what FP32 resolves)
+    p.sign_tol = sign_tol if sign_tol is not None else (1e-12 if precision == "fp64" else 4e-7)
     p.dissipation = int(dissipation)
     p.cfl = w.get("cfl", 0.4)
     p.dt_fixed = dt_fixed
@@ -159,6 +160,15 @@ class Context:
 
 def es_create(params, stream=None):
     return Context(params, stream)
+
+
+def state_empty(ctx, shape, device):
+    """An uninitialised state array of the context's precision: float64 of `shape`, or in
+    the mixed form the (hi, lo) float32 planes of shape (2, *shape)."""
+    import torch
+    if ctx.state_dtype == "torch.float32":
+        return torch.empty((2,) + tuple(shape), dtype=torch.float32, device=device)
+    return torch.empty(tuple(shape), dtype=torch.float64, device=device)
 
 
 F64 = "torch.float64"

@@ -28,14 +28,13 @@ def gpu_setup(w, precision="fp64", dissipation=True, x=None, dt_fixed=0.0):
     p = es.make_params(w, precision=precision, dissipation=dissipation, dt_fixed=dt_fixed)
     ctx = es.es_create(p)
     x = w["x"] if x is None else x
-    sdt = torch.float32 if precision == "mixed" else torch.float64
     xt = torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=dev)
-    J = torch.empty(x.shape[1:], dtype=sdt, device=dev)
+    J = es.state_empty(ctx, x.shape[1:], dev)
     es.es_init_mesh(ctx, xt, J)
     rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
     v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
     pr = torch.tensor(w["p"], dtype=torch.float64, device=dev)
-    JU = torch.empty((w["dim"] + 2,) + x.shape[1:], dtype=sdt, device=dev)
+    JU = es.state_empty(ctx, (w["dim"] + 2,) + x.shape[1:], dev)
     es.es_prim_to_cons(ctx, rho, v, pr, J, JU)
     return ctx, JU, J, xt
 
@@ -48,4 +47,13 @@ def rel_l1(a, b):
 
 
 def to_np(t):
-    return t.detach().cpu().double().numpy()
+    """float64 numpy values of a state tensor (mixed form: hi plane + lo plane)."""
+    a = t.detach().cpu()
+    if a.dtype == torch_float32():
+        return a[0].double().numpy() + a[1].double().numpy()
+    return a.double().numpy()
+
+
+def torch_float32():
+    import torch
+    return torch.float32

@@ -1,10 +1,11 @@
-"""The mixed-precision form (FP32 state and stage arithmetic) against the FP64 oracle.
+"""The mixed-precision form (stage arithmetic on the FP32 pipe) against the FP64 oracle.
 
 Bar: <= 1e-5 relative L1 against the oracle at the final time on smooth
 problems, with the design order of the scheme preserved above the FP32 floor.
-On discontinuous data the sign switch Y takes some decisions differently in
-FP32 (a plain jump within FP32 round-off counts as zero), so the bound there
-is 1e-4 after a few steps.
+The operator itself agrees to 2e-6 of the flux scale sum|JU|/dxi (1e-6 for the
+EC part alone).  On discontinuous data the sign switch Y takes some decisions
+differently in FP32 (a plain jump within a few FP32 roundings of its terms
+counts as zero), so the bound there is 1e-4 after a few steps.
 """
 import numpy as np
 import pytest
@@ -36,15 +37,16 @@ def _wavy(n=40):
     return w
 
 
+@pytest.mark.parametrize("dissipation", [False, True])
 @pytest.mark.parametrize("case", ["sine1d", "sine2d", "wavy", "vortex"])
-def test_mixed_rhs_vs_oracle(case):
+def test_mixed_rhs_vs_oracle(case, dissipation):
     import torch
 
     from paper_2407_05568_gb300 import es
-    w = {"sine1d": lambda: wl.sine_1d(200), "sine2d": lambda: wl.sine_2d(48), "wavy": _wavy,
-         "vortex": lambda: wl.isentropic_vortex(48)}[case]()
-    sch, mc, JU_o, J_o, x = oracle_setup(w)
-    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    w = {"sine1d": lambda: wl.sine_1d(200), "sine2d": lambda: wl.sine_2d(96), "wavy": lambda: _wavy(64),
+         "vortex": lambda: wl.isentropic_vortex(64)}[case]()
+    sch, mc, JU_o, J_o, x = oracle_setup(w, dissipation=dissipation)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed", dissipation=dissipation)
     xd = w.get("xdot", np.zeros_like(w["x"]))
     dU_o, dJ_o = op.rhs(sch, JU_o, J_o, x, xd)
     xdt = torch.tensor(np.ascontiguousarray(xd), dtype=torch.float64, device="cuda")
@@ -54,7 +56,7 @@ def test_mixed_rhs_vs_oracle(case):
     assert es.es_check(ctx) == 0
     scale = np.abs(JU_o).sum() / min(w["dxi"])
     err = np.abs(to_np(dU) - dU_o).sum() / scale
-    assert err < 2e-6, err
+    assert err < (2e-6 if dissipation else 1e-6), err
 
 
 def _run_both(w, t_end, dt_fixed=None):
@@ -73,8 +75,8 @@ def _run_both(w, t_end, dt_fixed=None):
 @pytest.mark.parametrize("case", ["sine1d", "sine2d", "vortex"])
 def test_mixed_final_time_vs_oracle(case):
     """Relative L1 of (JU, J) against the FP64 oracle at the final time <= 1e-5."""
-    w, t_end = {"sine1d": (wl.sine_1d(200), 0.1), "sine2d": (wl.sine_2d(40), 0.05),
-                "vortex": (wl.isentropic_vortex(32), 0.5)}[case]
+    w, t_end = {"sine1d": (wl.sine_1d(200), 0.1), "sine2d": (wl.sine_2d(96), 0.05),
+                "vortex": (wl.isentropic_vortex(64), 0.5)}[case]
     JU_o, J_o, x_o, JU, J, x = _run_both(w, t_end)
     assert rel_l1(JU, JU_o) < 1e-5, rel_l1(JU, JU_o)
     assert rel_l1(J, J_o) < 1e-6
