@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
     return ap.parse_args()
 
 
@@ -172,22 +173,16 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-def run_gpu(args):
+def measure_form(args, precision, dev, stream, world):
+    """Time K steps of one arithmetic form; returns a dict of the measurements."""
     import torch
     import torch.distributed as dist
 
-    from paper_2407_05568_gb300 import build, es
-    rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
+    from paper_2407_05568_gb300 import es
     w = workload(args.n)
     nodes = args.n * args.n
-    stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
-        ctx = es.es_create(es.make_params(w, precision=args.precision), stream)
+        ctx = es.es_create(es.make_params(w, precision=precision), stream)
         x0 = torch.tensor(w["x"], dtype=torch.float64, device=dev)
         J0 = es.state_empty(ctx, w["x"].shape[1:], dev)
         es.es_init_mesh(ctx, x0, J0)
@@ -212,19 +207,17 @@ def run_gpu(args):
         es.es_steps(ctx, JU, J, x, 1, w["t_end"])
         done += 1
     stream.synchronize()
-    rc = es.es_check(ctx)
-    if rc:
+    if es.es_check(ctx):
         raise RuntimeError(es.es_last_error(ctx))
 
-    # ---- device-timed region: K steps, L2 flushed before each (outside the events)
+    # device-timed region: K steps, L2 flushed before each (outside the events)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_ms = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev.index) as clk:
         for k in range(args.steps):
             if done and done % RESTART_EVERY == 0:
                 restart()
@@ -238,47 +231,73 @@ def run_gpu(args):
     launches = ctx.launches - launches0
     if world > 1:
         dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    rc = es.es_check(ctx)
-    if rc:
+    if es.es_check(ctx):
         raise RuntimeError(es.es_last_error(ctx))
-    value = world * nodes * 3 / (ms * 1e-3)
+    roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision)
 
-    # ---- dominant kernel: the fused stage kernel, timed alone on the same stream
-    roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, args.precision)
-
-    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
-    hJU = np.ascontiguousarray(JU0.cpu().numpy())
-    hJ = np.ascontiguousarray(J0.cpu().numpy())
-    hx = np.ascontiguousarray(x0.cpu().numpy())
-    hJU, hJ, hx = (pin(a) for a in (hJU, hJ, hx))
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hJU, hJ, hx = (pin(np.ascontiguousarray(t.cpu().numpy())) for t in (JU0, J0, x0))
     es.es_set_time(ctx, 0.0)
     es.es_run_host(ctx, hJU, hJ, hx, 1, w["t_end"])          # warm (captures the host-buffer graph)
     e2e_t = []
-    for k in range(max(3, args.steps // 2)):
+    for _ in range(max(3, args.steps // 2)):
         t0 = time.perf_counter()
         es.es_run_host(ctx, hJU, hJ, hx, 1, w["t_end"])
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_t)
-    bytes_io = (hJU.nbytes + hJ.nbytes + hx.nbytes)
+    # the state after the same number of steps from t = 0, for the error between forms
+    restart()
+    es.es_steps(ctx, JU, J, x, min(args.steps, RESTART_EVERY), w["t_end"])
+    stream.synchronize()
+    state = JU.double() if precision == "fp64" else (JU[0].double() + JU[1].double())
+    return dict(ms=ms, value=world * nodes * 3 / (ms * 1e-3), roof=roof, clocks=clk.summary(),
+                launches=int(launches), e2e=world * nodes * 3 / statistics.median(e2e_t),
+                io_bytes=hJU.nbytes + hJ.nbytes + hx.nbytes, state=state.cpu().numpy())
 
-    line = None
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_05568_gb300 import build
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    stream = torch.cuda.Stream(device=dev)
+    nodes = args.n * args.n
+    main_form = measure_form(args, args.precision, dev, stream, world)
+    other = None
+    if not args.no_chosen and args.precision == "fp64":
+        other = measure_form(args, "mixed", dev, stream, world)
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        m = main_form
+        line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic", "config": config(args.n, args.precision,
                                                       "flushed before each timed step (512 MB write)"),
-                "roofline": roof, "clocks": clk.summary(), "gpu_launches": int(launches),
-                "e2e": {"value": world * nodes * 3 / e2e_s, "unit": "cell-updates/s",
-                        "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}}
+                "roofline": m["roof"], "clocks": m["clocks"], "gpu_launches": m["launches"],
+                "e2e": {"value": m["e2e"], "unit": "cell-updates/s", "h2d_bytes_per_step": m["io_bytes"],
+                        "d2h_bytes_per_step": m["io_bytes"]}}
+        if other is not None:
+            ref = m["state"]
+            diff = float(np.abs(other["state"] - ref).sum() / np.abs(ref).sum())
+            line["chosen"] = {"form": "mixed (FP32 pipe, compensated-float state)", "value": other["value"],
+                              "unit": "cell-updates/s", "ms_per_step": other["ms"],
+                              "speedup_vs_fp64": other["value"] / m["value"],
+                              "rel_l1_vs_fp64_same_steps": diff,
+                              "steps_compared": min(args.steps, RESTART_EVERY),
+                              "roofline": other["roof"], "gpu_launches": other["launches"],
+                              "e2e": {"value": other["e2e"], "unit": "cell-updates/s"}}
         if not args.no_cpu_baseline:
-            sec, k = time_oracle(w, 8)
+            sec, k = time_oracle(workload(args.n), 8)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),
                                     "kind": "oracle",
                                     "sample": f"{k} full steps of the same {args.n}x{args.n} workload from t = 0"}

@@ -120,7 +120,12 @@ void enqueue_mesh_f32(es_ctx* c, StageParams& P, const double* x, const double* 
 
 cudaError_t launch_stage(es_ctx* c, const StageParams& P) {
     count(c);
-    return c->p.precision == ES_PREC_MIXED ? launch_stage_mixed(P, c->s_enq) : launch_stage_fp64(P, c->s_enq);
+    if (c->mixed) {
+        StageParams Q = P;
+        set_float_params(Q);
+        return launch_stage_mixed(Q, c->s_enq);
+    }
+    return launch_stage_fp64(P, c->s_enq);
 }
 
 const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};

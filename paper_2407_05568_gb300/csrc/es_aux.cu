@@ -15,6 +15,8 @@ namespace es {
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ double coord_at(const GridParams& g, const double* x, int gi, int gj, int comp) {
     const size_t N = size_t(g.n1) * g.n2;
+    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))   // interior: a plain load
+        return x[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
     const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0]);
     GhostTerms tj;
     if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1]);

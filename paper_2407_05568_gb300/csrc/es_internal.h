@@ -41,7 +41,33 @@ struct StageParams {
     float* fJo;
     const float* fdisp;           // x - (x_00 + i dxi_1, y_00 + j dxi_2), [dim][n2][n1]
     const float* fxdot;           // mesh velocity, [dim][n2][n1] (nullable)
+    // float copies of the constants (GB300 converts double -> float at FP64 speed)
+    float fgas[7];                // a, b, R, cv, delta, R b, 1/cv
+    float fweno[8];               // g1, g2, g3, g12, ig22, ig3, eps, sign_tol
+    float finv_dxi[2];
+    float fca, fcb, fca_lo, fcb_lo, fcst;
 };
+
+// fill the float copies of the constants of a stage launch
+inline void set_float_params(StageParams& P) {
+    P.fgas[0] = float(P.gas.a);
+    P.fgas[1] = float(P.gas.b);
+    P.fgas[2] = float(P.gas.R);
+    P.fgas[3] = float(P.gas.cv);
+    P.fgas[4] = float(P.gas.delta);
+    P.fgas[5] = float(P.gas.R * P.gas.b);
+    P.fgas[6] = float(1.0 / P.gas.cv);
+    const double w[8] = {P.weno.g1, P.weno.g2, P.weno.g3, P.weno.g12, P.weno.ig22, P.weno.ig3, P.weno.eps,
+                         P.weno.sign_tol};
+    for (int k = 0; k < 8; ++k) P.fweno[k] = float(w[k]);
+    P.finv_dxi[0] = float(P.inv_dxi[0]);
+    P.finv_dxi[1] = float(P.inv_dxi[1]);
+    P.fca = float(P.ca);
+    P.fcb = float(P.cb);
+    P.fca_lo = float(P.ca - double(P.fca));
+    P.fcb_lo = float(P.cb - double(P.fcb));
+    P.fcst = float(P.cst);
+}
 
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s);
 cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s);

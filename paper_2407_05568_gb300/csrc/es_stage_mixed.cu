@@ -445,25 +445,25 @@ __global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
     const double dtd = P.dt_dev ? *P.dt_dev : P.dt_host;
     if (P.mode == 0 && dtd == 0.0) return;
     const float dt = float(dtd);
-    const float cdt = float(P.cst) * dt;
+    const float cdt = P.fcst * dt;
     GasF G;
-    G.a = float(P.gas.a);
-    G.b = float(P.gas.b);
-    G.R = float(P.gas.R);
-    G.cv = float(P.gas.cv);
-    G.delta = float(P.gas.delta);
-    G.Rb = float(P.gas.R * P.gas.b);
-    G.icv = float(1.0 / P.gas.cv);
+    G.a = P.fgas[0];
+    G.b = P.fgas[1];
+    G.R = P.fgas[2];
+    G.cv = P.fgas[3];
+    G.delta = P.fgas[4];
+    G.Rb = P.fgas[5];
+    G.icv = P.fgas[6];
     WenoF Wc;
-    Wc.g1 = float(P.weno.g1);
-    Wc.g2 = float(P.weno.g2);
-    Wc.g3 = float(P.weno.g3);
-    Wc.g12 = float(P.weno.g12);
-    Wc.ig22 = float(P.weno.ig22);
-    Wc.ig3 = float(P.weno.ig3);
-    Wc.eps = float(P.weno.eps);
-    Wc.sign_tol = float(P.weno.sign_tol);
-    const float idx1 = float(P.inv_dxi[0]), idx2 = float(P.inv_dxi[1]);
+    Wc.g1 = P.fweno[0];
+    Wc.g2 = P.fweno[1];
+    Wc.g3 = P.fweno[2];
+    Wc.g12 = P.fweno[3];
+    Wc.ig22 = P.fweno[4];
+    Wc.ig3 = P.fweno[5];
+    Wc.eps = P.fweno[6];
+    Wc.sign_tol = P.fweno[7];
+    const float idx1 = P.finv_dxi[0], idx2 = P.finv_dxi[1];
 
     float* XS = PB;
     float* XD = PB + 2 * NB;
@@ -613,8 +613,8 @@ __global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
             P.fJo[N + idx] = 0.0f;
         } else {
             // a_s U^n + b_s (U^s + dt L) in double-float (a_s, b_s are 0, 1, 3/4, 1/4, 1/3, 2/3)
-            const float ca = float(P.ca), cb = float(P.cb);
-            const float ca_lo = float(P.ca - double(ca)), cb_lo = float(P.cb - double(cb));
+            const float ca = P.fca, cb = P.fcb;
+            const float ca_lo = P.fca_lo, cb_lo = P.fcb_lo;
 #pragma unroll
             for (int c = 0; c <= NC; ++c) {
                 const float* un = c < NC ? P.fJUn + c * N : P.fJn;
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
                 const df Us = {us[idx], us[lo + idx]};
                 const df inc = df_add_f(Us, dt * acc[c]);
                 df outv = df_mul(inc, {cb, cb_lo});
-                if (P.ca != 0.0) outv = df_add(outv, df_mul(Un, {ca, ca_lo}));
+                if (ca != 0.0f) outv = df_add(outv, df_mul(Un, {ca, ca_lo}));
                 uo[idx] = outv.hi;
                 uo[lo + idx] = outv.lo;
                 if (c == NC && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(idx));
