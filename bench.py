@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -259,6 +261,39 @@ def measure_form(args, precision, dev, stream, world):
                 io_bytes=hJU.nbytes + hJ.nbytes + hx.nbytes, state=state.cpu().numpy())
 
 
+def measure_batch(args, dev, stream):
+    """The batched form: 4096 1D vdW shock tubes, lengths U{200..8000}, moving mesh, one persistent
+    launch per K steps (mixed arithmetic).  The packed state (~2 GB) is larger than L2."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    from paper_2407_05568_gb300 import workloads as wl
+    batch = wl.shock_tube_batch(nprob=args.batch_problems)
+    b = es.es_batch_create(es.batch_params(batch["gas"]), batch["lengths"], stream)
+    with torch.cuda.stream(stream):
+        rho, v, p = (torch.tensor(a, dtype=torch.float64, device=dev) for a in wl.batch_fields(batch))
+        es.es_batch_set_prim(b, rho, v, p)
+    es.es_batch_steps(b, args.batch_steps, 1e30)          # warm-up launch (captures the graph)
+    if es.es_batch_check(b):
+        raise RuntimeError("batched form: device status")
+    st = torch.cuda.Event(enable_timing=True)
+    en = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    st.record(stream)
+    es.es_batch_steps(b, args.batch_steps, 1e30)
+    en.record(stream)
+    en.synchronize()
+    if es.es_batch_check(b):
+        raise RuntimeError("batched form: device status")
+    ms = st.elapsed_time(en)
+    cells = b.ntot * 3 * args.batch_steps
+    return {"workload": f"{b.nprob} independent 1D vdW shock tubes, lengths U{{200..8000}} "
+                        f"({b.ntot} nodes), moving mesh, one persistent launch per {args.batch_steps} steps",
+            "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_launch": ms,
+            "steps_per_launch": args.batch_steps, "nodes": b.ntot, "dtype": "f32",
+            "l2": "state (2 GB) larger than L2"}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -276,6 +311,9 @@ def run_gpu(args):
     other = None
     if not args.no_chosen and args.precision == "fp64":
         other = measure_form(args, "mixed", dev, stream, world)
+    batched = None
+    if args.batch_problems > 0 and rank == 0:
+        batched = measure_batch(args, dev, stream)
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -296,6 +334,8 @@ def run_gpu(args):
                               "steps_compared": min(args.steps, RESTART_EVERY),
                               "roofline": other["roof"], "gpu_launches": other["launches"],
                               "e2e": {"value": other["e2e"], "unit": "cell-updates/s"}}
+        if batched is not None:
+            line["batched"] = batched
         if not args.no_cpu_baseline:
             sec, k = time_oracle(workload(args.n), 8)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),

@@ -162,6 +162,33 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
 int64_t es_launch_count(es_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Batched form: many independent 1D problems (shock tubes on [0, 1], outflow
+ * boundaries, uniform initial mesh x_i = i/(L_p - 1)) advanced together by one
+ * persistent kernel replayed from a CUDA graph.  Each CTA takes a whole problem
+ * from a work queue (longest first) and runs its full steps -- its own CFL time
+ * step (eq. cfl), its own mesh redistribution (Sec. 4) and the three SSP-RK3
+ * stages of the fused operator -- with no waits on other CTAs.  Arithmetic is the
+ * mixed form (FP32 pipe, double-float state); the mesh is kept as an FP32
+ * displacement from the uniform mesh.  Packed layout: node i of problem p is
+ * element off_p + i, off_p = sum of the earlier lengths; ntot = sum of lengths. */
+typedef struct es_batch es_batch;
+
+/* p: gas, WENO, CFL and mesh parameters; p->dim must be 1 and p->precision
+ * ES_PREC_MIXED (n1, n2, dxi, period and bc are ignored).  lengths_host: nodes of
+ * each problem (>= 8).  Allocates the packed state and scratch. */
+int es_batch_create(es_batch** b, const es_params* p, int nprob, const int* lengths_host, void* stream);
+void es_batch_destroy(es_batch* b);
+int64_t es_batch_nodes(es_batch* b);
+/* Initial primitive state of every node (device arrays of ntot doubles). */
+int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const double* p);
+/* Advance every problem by nsteps full steps (each clipped to t_end). */
+int es_batch_steps(es_batch* b, int nsteps, double t_end);
+/* State as doubles: JU [3][ntot], J [ntot], x [ntot]; t [nprob] (nullable).  Device arrays. */
+int es_batch_get(es_batch* b, double* JU, double* J, double* x, double* t);
+int es_batch_check(es_batch* b);                      /* synchronises; latched device status */
+int es_batch_last_error(es_batch* b, char* buf, int len);
+
+/* ---------------------------------------------------------------------------
  * Allocation-free SSP-RK3 step.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc (a host application
  * that owns and budgets all device memory itself, code running while a memory

@@ -1,0 +1,515 @@
+// es_batch.cu -- many independent 1D problems in one persistent launch (mixed form).
+//
+// Each CTA takes a whole problem from an atomic work queue (problems ordered
+// longest first) and advances it by `nsteps` full steps -- its own CFL time
+// step (eq. cfl), its own mesh redistribution (Sec. 4: monitor with G, low-pass
+// filter, Jacobi sweeps, limiter, mesh velocity) and the three SSP-RK3 stages,
+// each stage a loop over 254-node chunks of the fused operator -- using only
+// __syncthreads between phases.  No CTA ever waits for another, so there is no
+// grid-wide synchronisation and no spin-wait.  The state of all problems is
+// packed component-major: value c of node i of problem p at c * ntot + off_p + i.
+//
+// The mesh of a 1D problem on [0, 1] with L nodes is stored as the FP32
+// displacement d_i = x_i - i/(L - 1) from the uniform computational mesh; the
+// Jacobi sweeps and the limiter work on d directly (the uniform part cancels
+// exactly), so the whole per-step pipeline runs on the FP32 pipe.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "es_batch.h"
+#include "es_mixed_device.cuh"
+
+namespace es {
+
+using namespace mixed;
+
+namespace {
+
+constexpr int BT = 256;                       // threads per CTA
+constexpr int BXC = 254;                      // nodes per stage chunk
+using TB = TileF<1, BXC, 1, BT>;
+
+__device__ __forceinline__ float block_max_f(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = red[0];
+    for (int w = 1; w < BT / 32; ++w) r = fmaxf(r, red[w]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ float block_min_f(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = red[0];
+    for (int w = 1; w < BT / 32; ++w) r = fminf(r, red[w]);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int clampi(int i, int L) { return i < 0 ? 0 : (i >= L ? L - 1 : i); }
+
+__global__ void __launch_bounds__(BT, 2) batch_kernel(BatchParams B) {
+    extern __shared__ float smemf[];
+    __shared__ float red[BT / 32];
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const GasF G = gas_f(B.tmpl);
+    const WenoF W = weno_f(B.tmpl);
+    const size_t ntot = B.ntot;
+    const float RK_A[3] = {0.0f, 0.75f, 1.0f / 3.0f};
+    const float RK_B[3] = {1.0f, 0.25f, 2.0f / 3.0f};
+    const float RK_C[3] = {0.0f, 1.0f, 0.5f};
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(B.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= B.nprob) break;
+        const int p = B.order[item];
+        const int L = B.lengths[p];
+        const size_t off = size_t(B.offsets[p]);
+        const float dxi = 1.0f / float(L - 1);
+        const float idxi = float(L - 1);
+        float* d = B.disp + off;
+        float* xd = B.xdot + off;
+        float* rhoF = B.work + off;
+        float* GF = B.work + ntot + off;
+        float* t0 = B.work + 2 * ntot + off;
+        float* t1 = B.work + 3 * ntot + off;
+        float* t2 = B.work + 4 * ntot + off;
+        float* om0 = B.work + 5 * ntot + off;
+        float* om1 = B.work + 6 * ntot + off;
+        float* da = B.work + 7 * ntot + off;
+        float* db = B.work + 8 * ntot + off;
+        double t = B.tprob[p];
+
+        for (int step = 0; step < B.nsteps; ++step) {
+            // ---- time step, eq. cfl: dt = CFL / max (|v| + c) / (J dxi)
+            float m = 0.0f;
+            for (int i = tid; i < L; i += BT) {
+                const float iJ = 1.0f / B.J[off + i];
+                const float rho = B.JU[off + i] * iJ;
+                const float v = B.JU[ntot + off + i] * iJ / rho;
+                const float E = B.JU[2 * ntot + off + i] * iJ;
+                const float T = (E / rho - 0.5f * v * v + G.a * rho) * G.icv;
+                const float om = 1.0f - G.b * rho;
+                const float c2 = (1.0f + G.delta) * G.R * T / (om * om) - 2.0f * G.a * rho;
+                const float lam = (fabsf(v) + sqrtf(fmaxf(c2, 0.0f))) * iJ * idxi;
+                m = fmaxf(m, c2 > 0.0f ? lam : 3.0e38f);
+                rhoF[i] = rho;
+                // fundamental derivative G = nu^3 p_nunu|_s / (2 c^2)
+                GF[i] = ((1.0f + G.delta) * (2.0f + G.delta) * G.R * T / (om * om * om) - 6.0f * G.a * rho) /
+                        (2.0f * c2);
+            }
+            m = block_max_f(m, red);
+            double dt = double(B.cfl) / double(m);
+            const double left = B.t_end - t;
+            if (left <= 1e-14 * fmax(1.0, fabs(B.t_end))) break;
+            if (dt > left) dt = left;
+            const float dtf = float(dt);
+
+            // ---- mesh redistribution (Sec. 4) on the displacement
+            if (B.moving) {
+                float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+                for (int i = tid; i < L; i += BT) {
+                    const int ip = clampi(i + 1, L), im = clampi(i - 1, L);
+                    const float gr = 0.5f * (rhoF[ip] - rhoF[im]) * idxi;
+                    const float gg = 0.5f * (GF[ip] - GF[im]) * idxi;
+                    const float lg = (GF[ip] - 2.0f * GF[i] + GF[im]) * idxi * idxi;
+                    const float a0 = gr * gr, a1 = B.kappa >= 2 ? gg * gg : 0.0f, a2 = lg * lg;
+                    t0[i] = a0;
+                    t1[i] = a1;
+                    t2[i] = a2;
+                    m0 = fmaxf(m0, a0);
+                    m1 = fmaxf(m1, a1);
+                    m2 = fmaxf(m2, a2);
+                }
+                m0 = block_max_f(m0, red);
+                m1 = block_max_f(m1, red);
+                m2 = block_max_f(m2, red);
+                const float c0 = m0 > 0.0f ? B.w0 / m0 : 0.0f;
+                const float c1 = m1 > 0.0f ? B.w1 / m1 : 0.0f;
+                const float c2 = m2 > 0.0f ? B.w2 / m2 : 0.0f;
+                for (int i = tid; i < L; i += BT) om0[i] = sqrtf(1.0f + c0 * t0[i] + c1 * t1[i] + c2 * t2[i]);
+                __syncthreads();
+                float* om = om0;
+                float* ot = om1;
+                for (int f = 0; f < B.filter_passes; ++f) {
+                    for (int i = tid; i < L; i += BT)
+                        ot[i] = 0.25f * om[clampi(i - 1, L)] + 0.5f * om[i] + 0.25f * om[clampi(i + 1, L)];
+                    __syncthreads();
+                    float* tmp = om; om = ot; ot = tmp;
+                }
+                // Jacobi sweeps: x_i = (w+ x_{i+1} + w- x_{i-1})/(w+ + w-), with x = i dxi + d
+                const float* din = d;
+                float* dout = da;
+                for (int k = 0; k < B.sweeps; ++k) {
+                    for (int i = tid; i < L; i += BT) {
+                        if (i == 0 || i == L - 1) {
+                            dout[i] = din[i];
+                        } else {
+                            const float wp = 0.5f * (om[i] + om[i + 1]), wm = 0.5f * (om[i] + om[i - 1]);
+                            dout[i] = (wp * (dxi + din[i + 1]) + wm * (din[i - 1] - dxi)) / (wp + wm);
+                        }
+                    }
+                    __syncthreads();
+                    din = dout;
+                    dout = (dout == da) ? db : da;
+                }
+                // limiter: each node moves at most half of its spacing towards its neighbour
+                float g = 1.0f;
+                for (int i = tid; i < L; i += BT) {
+                    const float del = din[i] - d[i];
+                    if (del < 0.0f && i > 0) g = fminf(g, -(dxi + d[i] - d[i - 1]) / (2.0f * del));
+                    else if (del > 0.0f && i < L - 1) g = fminf(g, (dxi + d[i + 1] - d[i]) / (2.0f * del));
+                }
+                g = block_min_f(g, red);
+                const float fv = g / dtf;
+                for (int i = tid; i < L; i += BT) xd[i] = fv * (din[i] - d[i]);
+                __syncthreads();
+            }
+
+            // ---- three fused RK stages, each a loop over 254-node chunks
+            StageParams P = B.tmpl;
+            P.n1 = L;
+            P.n2 = 1;
+            P.inv_dxi[0] = double(idxi);
+            P.finv_dxi[0] = idxi;
+            P.fcs = ntot;
+            P.fps = 3 * ntot;
+            P.fpsJ = ntot;
+            P.fdisp = d;
+            P.fxdot = B.moving ? xd : nullptr;
+            P.mode = 0;
+            for (int st = 0; st < 3; ++st) {
+                P.fca = RK_A[st];
+                P.fcb = RK_B[st];
+                P.fca_lo = st == 2 ? float(1.0 / 3.0 - double(RK_A[2])) : 0.0f;
+                P.fcb_lo = st == 2 ? float(2.0 / 3.0 - double(RK_B[2])) : 0.0f;
+                P.fcst = RK_C[st];
+                P.fJUn = B.JU + off;
+                P.fJn = B.J + off;
+                P.fJUs = (st == 0 ? B.JU : (st == 1 ? B.S1 : B.S2)) + off;
+                P.fJs = (st == 0 ? B.J : (st == 1 ? B.S1J : B.S2J)) + off;
+                P.fJUo = (st == 0 ? B.S1 : (st == 1 ? B.S2 : B.JU)) + off;
+                P.fJo = (st == 0 ? B.S1J : (st == 1 ? B.S2J : B.J)) + off;
+                for (int c0 = 0; c0 < L; c0 += BXC) {
+                    stage_tile_mixed<1, BXC, 1, BT>(smemf, P, c0, 0, dtf, G, W);
+                    __syncthreads();
+                }
+            }
+            if (B.moving)
+                for (int i = tid; i < L; i += BT) d[i] += dtf * xd[i];
+            __syncthreads();
+            t += dt;
+        }
+        if (tid == 0) B.tprob[p] = t;
+    }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes() { return TB::SMEM; }
+
+cudaError_t batch_prepare() {
+    return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TB::SMEM));
+}
+
+cudaError_t batch_launch(const BatchParams& B, int grid, cudaStream_t s) {
+    batch_kernel<<<grid, BT, TB::SMEM, s>>>(B);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel, BT, TB::SMEM);
+    return nb;
+}
+
+// per-problem elementwise kernels (one CTA per problem)
+__global__ void k_batch_set(BatchParams B, Gas Gd, const double* rho, const double* v, const double* pr) {
+    const int p = blockIdx.x;
+    const int L = B.lengths[p];
+    const size_t off = size_t(B.offsets[p]);
+    const size_t n = B.ntot;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const size_t id = off + i;
+        const double r = rho[id], u = v[id];
+        const double T = (pr[id] + Gd.a * r * r) * (1.0 - Gd.b * r) / (Gd.R * r);
+        const double E = r * (Gd.cv * T - Gd.a * r) + 0.5 * r * u * u;
+        const double vals[3] = {r, r * u, E};            // J = 1 on the uniform initial mesh
+        for (int c = 0; c < 3; ++c) {
+            const float hi = float(vals[c]);
+            B.JU[c * n + id] = hi;
+            B.JU[3 * n + c * n + id] = float(vals[c] - double(hi));
+        }
+        B.J[id] = 1.0f;
+        B.J[n + id] = 0.0f;
+        B.disp[id] = 0.0f;
+        B.xdot[id] = 0.0f;
+    }
+    if (threadIdx.x == 0) B.tprob[p] = 0.0;
+}
+
+__global__ void k_batch_get(BatchParams B, double* JU, double* J, double* x, double* t) {
+    const int p = blockIdx.x;
+    const int L = B.lengths[p];
+    const size_t off = size_t(B.offsets[p]);
+    const size_t n = B.ntot;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const size_t id = off + i;
+        for (int c = 0; c < 3; ++c) JU[c * n + id] = double(B.JU[c * n + id]) + double(B.JU[3 * n + c * n + id]);
+        J[id] = double(B.J[id]) + double(B.J[n + id]);
+        x[id] = double(i) / double(L - 1) + double(B.disp[id]);
+    }
+    if (threadIdx.x == 0 && t) t[p] = B.tprob[p];
+}
+
+}  // namespace es
+
+// ------------------------------------------------------------------ C ABI
+using namespace es;
+
+struct es_batch {
+    es_params p;
+    cudaStream_t stream, cap_stream;
+    BatchParams B;
+    int* d_order;
+    int* d_lengths;
+    long long* d_offsets;
+    float* state;
+    float* work;
+    double* tprob;
+    int* queue;
+    DevStatus* status;
+    int grid;
+    cudaGraphExec_t gexec;
+    int g_nsteps;
+    double g_tend;
+    char msg[256];
+};
+
+namespace {
+
+int bfail(es_batch* b, cudaError_t e, const char* where) {
+    if (b) snprintf(b->msg, sizeof(b->msg), "%s: %s", where, cudaGetErrorString(e));
+    return ES_ERR_CUDA;
+}
+
+#define BCK(call, where)                               \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return bfail(b, e_, where); \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int es_batch_create(es_batch** out, const es_params* p, int nprob, const int* lengths_host, void* stream) {
+    if (!out || !p || !lengths_host || nprob <= 0) return ES_ERR_ARG;
+    *out = nullptr;
+    if (p->dim != 1 || p->precision != ES_PREC_MIXED || !(p->cfl > 0.0) || !(p->R > 0.0) || !(p->cv > 0.0) ||
+        !(p->weno_eps > 0.0) || p->filter_passes < 0 || p->jacobi_sweeps < 0 || p->jacobi_sweeps > 100000 ||
+        (p->moving && (p->monitor != ES_MONITOR_VDW || p->kappa < 1 || p->kappa > 2)))
+        return ES_ERR_ARG;
+    long long ntot = 0;
+    for (int k = 0; k < nprob; ++k) {
+        if (lengths_host[k] < 8 || lengths_host[k] > (1 << 24)) return ES_ERR_ARG;
+        ntot += lengths_host[k];
+    }
+    if (ntot > (1LL << 31)) return ES_ERR_ARG;
+    es_batch* b = (es_batch*)calloc(1, sizeof(es_batch));
+    if (!b) return ES_ERR_ARG;
+    b->p = *p;
+    b->stream = (cudaStream_t)stream;
+    // host-side queue order: longest problems first (a greedy longest-processing-time schedule)
+    int* order = (int*)malloc(sizeof(int) * nprob);
+    long long* offs = (long long*)malloc(sizeof(long long) * nprob);
+    long long acc = 0;
+    for (int k = 0; k < nprob; ++k) {
+        order[k] = k;
+        offs[k] = acc;
+        acc += lengths_host[k];
+    }
+    for (int a = 1; a < nprob; ++a) {                   // insertion sort by length, descending
+        int v = order[a], j = a - 1;
+        while (j >= 0 && lengths_host[order[j]] < lengths_host[v]) { order[j + 1] = order[j]; --j; }
+        order[j + 1] = v;
+    }
+    const size_t n = size_t(ntot);
+    int rc = ES_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMalloc((void**)&b->d_order, sizeof(int) * nprob))) break;
+        if ((e = cudaMalloc((void**)&b->d_lengths, sizeof(int) * nprob))) break;
+        if ((e = cudaMalloc((void**)&b->d_offsets, sizeof(long long) * nprob))) break;
+        // state planes: JU 6n, J 2n, S1 6n, S1J 2n, S2 6n, S2J 2n, disp n, xdot n
+        if ((e = cudaMalloc((void**)&b->state, sizeof(float) * n * 26))) break;
+        if ((e = cudaMalloc((void**)&b->work, sizeof(float) * n * 9))) break;
+        if ((e = cudaMalloc((void**)&b->tprob, sizeof(double) * nprob))) break;
+        if ((e = cudaMalloc((void**)&b->queue, sizeof(int)))) break;
+        if ((e = cudaMalloc((void**)&b->status, sizeof(DevStatus)))) break;
+        if ((e = cudaMemcpy(b->d_order, order, sizeof(int) * nprob, cudaMemcpyHostToDevice))) break;
+        if ((e = cudaMemcpy(b->d_lengths, lengths_host, sizeof(int) * nprob, cudaMemcpyHostToDevice))) break;
+        if ((e = cudaMemcpy(b->d_offsets, offs, sizeof(long long) * nprob, cudaMemcpyHostToDevice))) break;
+        if ((e = cudaMemset(b->status, 0, sizeof(DevStatus)))) break;
+        if ((e = cudaMemset(b->tprob, 0, sizeof(double) * nprob))) break;
+        if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking))) break;
+        if ((e = batch_prepare())) break;
+    } while (0);
+    free(order);
+    free(offs);
+    if (e != cudaSuccess) {
+        rc = bfail(b, e, "es_batch_create");
+        es_batch_destroy(b);
+        return rc;
+    }
+    BatchParams& B = b->B;
+    B.nprob = nprob;
+    B.order = b->d_order;
+    B.lengths = b->d_lengths;
+    B.offsets = b->d_offsets;
+    B.ntot = n;
+    B.JU = b->state;
+    B.J = b->state + 6 * n;
+    B.S1 = b->state + 8 * n;
+    B.S1J = b->state + 14 * n;
+    B.S2 = b->state + 16 * n;
+    B.S2J = b->state + 22 * n;
+    B.disp = b->state + 24 * n;
+    B.xdot = b->state + 25 * n;
+    B.work = b->work;
+    B.tprob = b->tprob;
+    B.queue = b->queue;
+    B.cfl = float(p->cfl);
+    B.moving = p->moving;
+    B.kappa = p->kappa;
+    B.w0 = float(p->alpha[0]);
+    B.w1 = float(p->kappa >= 2 ? p->alpha[1] : 0.0);
+    B.w2 = float(p->alpha[p->kappa]);
+    B.filter_passes = p->filter_passes;
+    B.sweeps = p->jacobi_sweeps;
+    StageParams& P = B.tmpl;
+    memset(&P, 0, sizeof(P));
+    P.dim = 1;
+    P.bc[0] = ES_BC_OUTFLOW;
+    P.bc[1] = ES_BC_PERIODIC;
+    P.gas.a = p->a;
+    P.gas.b = p->b;
+    P.gas.R = p->R;
+    P.gas.cv = p->cv;
+    P.gas.delta = p->R / p->cv;
+    const double g1 = p->weno_gamma[0], g2 = p->weno_gamma[1], g3 = p->weno_gamma[2], gs = g1 + g2 + g3;
+    P.weno.g1 = g1 / gs;
+    P.weno.g2 = g2 / gs;
+    P.weno.g3 = g3 / gs;
+    P.weno.g12 = g1 / (g1 + g2);
+    P.weno.ig22 = (g1 + g2) / g2;
+    P.weno.ig3 = gs / g3;
+    P.weno.eps = p->weno_eps;
+    P.weno.sign_tol = p->sign_tol;
+    P.diss = p->dissipation;
+    P.status = b->status;
+    P.n1 = 8;
+    P.n2 = 1;
+    P.fcs = n;                                         // the kernel sets the per-problem fields
+    set_float_params(P);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = batch_blocks_per_sm();
+    b->grid = nsm * (per_sm > 0 ? per_sm : 1);
+    if (b->grid > nprob) b->grid = nprob;
+    *out = b;
+    return ES_OK;
+}
+
+void es_batch_destroy(es_batch* b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    void* bufs[] = {b->d_order, b->d_lengths, b->d_offsets, b->state, b->work, b->tprob, b->queue, b->status};
+    for (void* q : bufs)
+        if (q) cudaFree(q);
+    free(b);
+}
+
+int64_t es_batch_nodes(es_batch* b) { return b ? (int64_t)b->B.ntot : 0; }
+
+int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const double* pr) {
+    if (!b || !rho || !v || !pr) return ES_ERR_ARG;
+    Gas Gd;
+    Gd.a = b->p.a;
+    Gd.b = b->p.b;
+    Gd.R = b->p.R;
+    Gd.cv = b->p.cv;
+    Gd.delta = b->p.R / b->p.cv;
+    k_batch_set<<<b->B.nprob, 256, 0, b->stream>>>(b->B, Gd, rho, v, pr);
+    BCK(cudaGetLastError(), "k_batch_set");
+    return ES_OK;
+}
+
+int es_batch_steps(es_batch* b, int nsteps, double t_end) {
+    if (!b || nsteps < 0) return ES_ERR_ARG;
+    if (nsteps == 0) return ES_OK;
+    if (!b->gexec || b->g_nsteps != nsteps || b->g_tend != t_end) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        BatchParams B = b->B;
+        B.nsteps = nsteps;
+        B.t_end = t_end;
+        cudaGraph_t graph;
+        BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e1 = cudaMemsetAsync(b->queue, 0, sizeof(int), b->cap_stream);
+        cudaError_t e2 = batch_launch(B, b->grid, b->cap_stream);
+        cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (e1 != cudaSuccess) return bfail(b, e1, "memset");
+        if (e2 != cudaSuccess) return bfail(b, e2, "batch kernel");
+        if (e3 != cudaSuccess) return bfail(b, e3, "end capture");
+        cudaError_t e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return bfail(b, e, "instantiate");
+        b->g_nsteps = nsteps;
+        b->g_tend = t_end;
+    }
+    BCK(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
+    return ES_OK;
+}
+
+int es_batch_get(es_batch* b, double* JU, double* J, double* x, double* t) {
+    if (!b || !JU || !J || !x) return ES_ERR_ARG;
+    k_batch_get<<<b->B.nprob, 256, 0, b->stream>>>(b->B, JU, J, x, t);
+    BCK(cudaGetLastError(), "k_batch_get");
+    return ES_OK;
+}
+
+int es_batch_check(es_batch* b) {
+    if (!b) return ES_ERR_ARG;
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    DevStatus h = {0, 0};
+    BCK(cudaMemcpy(&h, b->status, sizeof(h), cudaMemcpyDeviceToHost), "status");
+    if (h.code) {
+        snprintf(b->msg, sizeof(b->msg), "device status %d at node %d", h.code, h.index);
+        DevStatus z = {0, 0};
+        BCK(cudaMemcpy(b->status, &z, sizeof(z), cudaMemcpyHostToDevice), "clear status");
+    }
+    return h.code;
+}
+
+int es_batch_last_error(es_batch* b, char* buf, int len) {
+    if (!b || !buf || len <= 0) return ES_ERR_ARG;
+    snprintf(buf, len, "%s", b->msg);
+    return ES_OK;
+}
+
+}  // extern "C"

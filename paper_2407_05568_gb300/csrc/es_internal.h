@@ -46,6 +46,9 @@ struct StageParams {
     float fweno[8];               // g1, g2, g3, g12, ig22, ig3, eps, sign_tol
     float finv_dxi[2];
     float fca, fcb, fca_lo, fcb_lo, fcst;
+    // mixed form strides: component stride, JU lo-plane offset, J lo-plane offset
+    // (0: the contiguous layout of one mesh, n1 n2, (dim + 2) n1 n2 and n1 n2)
+    size_t fcs, fps, fpsJ;
 };
 
 // fill the float copies of the constants of a stage launch
@@ -67,6 +70,12 @@ inline void set_float_params(StageParams& P) {
     P.fca_lo = float(P.ca - double(P.fca));
     P.fcb_lo = float(P.cb - double(P.fcb));
     P.fcst = float(P.cst);
+    const size_t N = size_t(P.n1) * P.n2;
+    if (P.fcs == 0) {
+        P.fcs = N;
+        P.fps = size_t(P.dim + 2) * N;
+        P.fpsJ = N;
+    }
 }
 
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s);

@@ -71,6 +71,19 @@ def lib():
         L.es_launch_count.restype = ctypes.c_int64
         L.es_rk3_step_static.argtypes = [ctypes.POINTER(EsParams), d, vp, vp, vp, vp, vp]
         L.es_rk3_step_static.restype = ctypes.c_int
+        L.es_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(EsParams), i, ctypes.POINTER(i), vp]
+        L.es_batch_destroy.argtypes = [vp]
+        L.es_batch_destroy.restype = None
+        L.es_batch_nodes.argtypes = [vp]
+        L.es_batch_nodes.restype = ctypes.c_int64
+        L.es_batch_set_prim.argtypes = [vp, vp, vp, vp]
+        L.es_batch_steps.argtypes = [vp, i, d]
+        L.es_batch_get.argtypes = [vp, vp, vp, vp, vp]
+        L.es_batch_check.argtypes = [vp]
+        L.es_batch_last_error.argtypes = [vp, ctypes.c_char_p, i]
+        for name in ("es_batch_create", "es_batch_set_prim", "es_batch_steps", "es_batch_get", "es_batch_check",
+                     "es_batch_last_error"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
                      "es_mesh_redistribute", "es_steps", "es_set_time", "es_get_time", "es_run_host",
                      "es_check", "es_last_error"):
@@ -247,6 +260,61 @@ def es_rk3_step_static(params, dt, JU, J, x, xdot=None, stream=None):
     """Allocation-free SSP-RK3 step (see es_vdw.h); returns the status code (0 = ok)."""
     return int(lib().es_rk3_step_static(ctypes.byref(params), float(dt), _ptr(JU), _ptr(J), _ptr(x),
                                         _ptr(xdot), _stream_handle(stream)))
+
+
+class Batch:
+    """Owns an es_batch* (many 1D problems advanced by one persistent launch)."""
+
+    def __init__(self, params, lengths, stream=None):
+        self.lengths = np.ascontiguousarray(np.asarray(lengths, dtype=np.int32))
+        self.nprob = int(self.lengths.size)
+        self._h = ctypes.c_void_p()
+        arr = self.lengths.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        rc = lib().es_batch_create(ctypes.byref(self._h), ctypes.byref(params), self.nprob, arr,
+                                   _stream_handle(stream))
+        if rc != ES_OK:
+            raise EsError(rc, "es_batch_create rejected the parameters")
+        self.ntot = int(lib().es_batch_nodes(self._h))
+        self.offsets = np.concatenate([[0], np.cumsum(self.lengths)[:-1]]).astype(np.int64)
+
+    def _call(self, rc):
+        if rc != ES_OK:
+            buf = ctypes.create_string_buffer(256)
+            lib().es_batch_last_error(self._h, buf, 256)
+            raise EsError(rc, buf.value.decode())
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.es_batch_destroy(self._h)
+            self._h = None
+
+
+def es_batch_create(params, lengths, stream=None):
+    return Batch(params, lengths, stream)
+
+
+def es_batch_set_prim(b, rho, v, p):
+    b._call(lib().es_batch_set_prim(b._h, _ptr(rho, F64), _ptr(v, F64), _ptr(p, F64)))
+
+
+def es_batch_steps(b, nsteps, t_end):
+    b._call(lib().es_batch_steps(b._h, int(nsteps), float(t_end)))
+
+
+def es_batch_get(b, JU, J, x, t=None):
+    b._call(lib().es_batch_get(b._h, _ptr(JU, F64), _ptr(J, F64), _ptr(x, F64), _ptr(t, F64)))
+
+
+def es_batch_check(b):
+    return int(lib().es_batch_check(b._h))
+
+
+def batch_params(gas, cfl=0.4, alphas=(1200.0, 1200.0, 1200.0), kappa=2, filter_passes=5, sweeps=5,
+                 moving=True, sign_tol=4e-7):
+    """es_params for es_batch_create: 1D, mixed form, vdW monitor (Sec. 4)."""
+    w = dict(gas=gas, dim=1, n=(8,), dxi=(1.0,), bc=("outflow",), period=(1.0,), cfl=cfl, moving=moving,
+             mesh=dict(monitor="vdw", alphas=alphas, kappa=kappa, filter_passes=filter_passes, sweeps=sweeps))
+    return make_params(w, precision="mixed", sign_tol=sign_tol)
 
 
 def es_last_error(ctx):

@@ -146,12 +146,15 @@ def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0):
                 t_end=t_end, cfl=cfl, moving=False)
 
 
-def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345):
+def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345, lengths=None):
     """Batched 1D shock tubes on [0, 1], interface at 0.5, outflow boundaries.
-    Lengths ~ U{lmin..lmax}; left/right states rho in [0.2, 2.5], p in [0.3, 2], v in [-1, 1],
-    rejection-sampled for the recipe acceptance region and between the two states."""
+    Lengths ~ U{lmin..lmax} (or given); left/right states rho in [0.2, 2.5], p in [0.3, 2],
+    v in [-1, 1], rejection-sampled for the recipe acceptance region and between the two states."""
     rng = np.random.default_rng(seed)
-    lengths = rng.integers(lmin, lmax + 1, size=nprob)
+    if lengths is None:
+        lengths = rng.integers(lmin, lmax + 1, size=nprob)
+    lengths = np.asarray(lengths)
+    nprob = lengths.size
     states = np.empty((nprob, 6))
     for i in range(nprob):
         while True:
@@ -162,6 +165,34 @@ def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345):
                 break
         states[i] = (rl, vl, pl, rr, vr, pr)
     return dict(gas=UNITS_A, lengths=lengths, states=states)
+
+
+def batch_fields(batch):
+    """Packed initial fields (rho, v, p) of a shock-tube batch: node i of problem k sits at
+    off_k + i with x_i = i/(L_k - 1); the left state holds for x < 0.5."""
+    L = batch["lengths"]
+    rho, v, p = [], [], []
+    for k in range(L.size):
+        x = np.arange(L[k]) / (L[k] - 1)
+        left = x < 0.5
+        rl, vl, pl, rr, vr, pr = batch["states"][k]
+        rho.append(np.where(left, rl, rr))
+        v.append(np.where(left, vl, vr))
+        p.append(np.where(left, pl, pr))
+    return np.concatenate(rho), np.concatenate(v), np.concatenate(p)
+
+
+def batch_problem(batch, k, mesh_sweeps=5):
+    """Problem k of a batch as a 1D workload (for a per-problem check)."""
+    L = int(batch["lengths"][k])
+    x, d = uniform_nodes(L, 0.0, 1.0, False)
+    rl, vl, pl, rr, vr, pr = batch["states"][k]
+    left = x < 0.5
+    return dict(gas=batch["gas"], dim=1, n=(L,), dxi=(d,), bc=("outflow",), period=(1.0,), x=x[None].copy(),
+                rho=np.where(left, rl, rr), v=np.where(left, vl, vr)[None], p=np.where(left, pl, pr),
+                t_end=1e30, cfl=0.4, moving=True,
+                mesh=dict(monitor="vdw", alphas=(1200.0, 1200.0, 1200.0), kappa=2, filter_passes=5,
+                          sweeps=mesh_sweeps, eps=0.0))
 
 
 def wavy_mesh_2d(X, Y, amp=0.01):

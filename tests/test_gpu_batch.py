@@ -1,0 +1,74 @@
+"""The batched persistent form (many 1D shock tubes, one launch) against the oracle, problem by problem."""
+import numpy as np
+import pytest
+
+from oracle import stepper
+from paper_2407_05568_gb300 import workloads as wl
+
+from sides import oracle_setup, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_05568_gb300 import build
+    build.build()
+
+
+def _run_batch(batch, nsteps):
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    dev = torch.device("cuda:0")
+    b = es.es_batch_create(es.batch_params(batch["gas"]), batch["lengths"])
+    rho, v, p = (torch.tensor(a, dtype=torch.float64, device=dev) for a in wl.batch_fields(batch))
+    es.es_batch_set_prim(b, rho, v, p)
+    es.es_batch_steps(b, nsteps, 1e30)
+    assert es.es_batch_check(b) == 0
+    JU = torch.empty((3, b.ntot), dtype=torch.float64, device=dev)
+    J = torch.empty(b.ntot, dtype=torch.float64, device=dev)
+    x = torch.empty(b.ntot, dtype=torch.float64, device=dev)
+    t = torch.empty(b.nprob, dtype=torch.float64, device=dev)
+    es.es_batch_get(b, JU, J, x, t)
+    assert es.es_batch_check(b) == 0
+    return b, JU.cpu().numpy(), J.cpu().numpy(), x.cpu().numpy(), t.cpu().numpy()
+
+
+def test_batch_matches_oracle_per_problem():
+    """Ragged lengths (one to five 254-node chunks, and a short tube) after 3 steps."""
+    batch = wl.shock_tube_batch(lengths=[37, 200, 257, 600, 1023, 64], seed=7)
+    nsteps = 3
+    b, JU, J, x, t = _run_batch(batch, nsteps)
+    for k in range(b.nprob):
+        w = wl.batch_problem(batch, k)
+        sch, mc, JUo, Jo, xo = oracle_setup(w)
+        to = 0.0
+        for _ in range(nsteps):
+            JUo, Jo, xo, to, _ = stepper.step(sch, mc, JUo, Jo, xo, to, 1e30, 0.4)
+        sl = slice(b.offsets[k], b.offsets[k] + b.lengths[k])
+        assert abs(t[k] - to) <= 1e-5 * to
+        assert rel_l1(JU[:, sl], JUo) < 1e-4, (k, rel_l1(JU[:, sl], JUo))
+        assert rel_l1(x[sl], xo[0]) < 1e-6
+        assert rel_l1(J[sl], Jo) < 1e-5
+
+
+def test_batch_problems_are_independent():
+    """A problem's result does not depend on which other problems share the launch."""
+    batch = wl.shock_tube_batch(lengths=[300, 900, 120, 500], seed=9)
+    b, JU, J, x, t = _run_batch(batch, 2)
+    sub = dict(batch, lengths=batch["lengths"][[1, 3]], states=batch["states"][[1, 3]])
+    b2, JU2, J2, x2, t2 = _run_batch(sub, 2)
+    for kk, k in enumerate([1, 3]):
+        a = slice(b.offsets[k], b.offsets[k] + b.lengths[k])
+        c = slice(b2.offsets[kk], b2.offsets[kk] + b2.lengths[kk])
+        assert np.array_equal(JU[:, a], JU2[:, c]) and np.array_equal(x[a], x2[c])
+
+
+def test_batch_rejects_bad_lengths():
+    from paper_2407_05568_gb300 import es
+    with pytest.raises(es.EsError):
+        es.es_batch_create(es.batch_params(wl.UNITS_A), [5, 100])
