@@ -355,9 +355,8 @@ __device__ __forceinline__ void load_node_f(float* S, int NB, int b, const Stage
     const float iom = 1.0f / om;
     const float p = r * G.R * T * iom - G.a * r * r;
     const float iT = 1.0f / T;
-    if (!(r > 0.0f) || !(om > 0.0f) || !(T > 0.0f) || !(p > 0.0f) ||
-        !(G.R * T - 2.0f * G.a * r * om * om > 0.0f))
-        raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
+    // what the node arithmetic needs; R T - 2 a rho (1 - b rho)^2 > 0 enters through the face states
+    if (!(r > 0.0f) || !(om > 0.0f) || !(T > 0.0f) || !(p > 0.0f)) raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
     S[G_RHO * NB + b] = r;
     S[G_RHOL * NB + b] = rho.lo;
     S[G_V1 * NB + b] = v1.hi;

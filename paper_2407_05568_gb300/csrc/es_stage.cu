@@ -247,9 +247,9 @@ __device__ __forceinline__ void load_node(double* S, int NB, int b, const StageP
     const double iom = 1.0 / om;
     const double p = rho * G.R * T * iom - G.a * rho * rho;
     const double iT = 1.0 / T;
-    if (!(rho > 0.0) || !(om > 0.0) || !(T > 0.0) || !(p > 0.0) ||
-        !(G.R * T - 2.0 * G.a * rho * om * om > 0.0))
-        raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
+    // what the node arithmetic needs (logarithms of rho, 1 - b rho, T, p); the
+    // condition R T - 2 a rho (1 - b rho)^2 > 0 enters through the face states
+    if (!(rho > 0.0) || !(om > 0.0) || !(T > 0.0) || !(p > 0.0)) raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
     const double lnr = log(rho);
     const double lnom = G.b > 0.0 ? log(om) : 0.0;
     const double lnT = log(T);

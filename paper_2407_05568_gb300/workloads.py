@@ -146,10 +146,17 @@ def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0):
                 t_end=t_end, cfl=cfl, moving=False)
 
 
-def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345, lengths=None):
+def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345, lengths=None, t_ratio_max=1.3,
+                     rho_ratio_max=3.0):
     """Batched 1D shock tubes on [0, 1], interface at 0.5, outflow boundaries.
     Lengths ~ U{lmin..lmax} (or given); left/right states rho in [0.2, 2.5], p in [0.3, 2],
-    v in [-1, 1], rejection-sampled for the recipe acceptance region and between the two states."""
+    v in [-1, 1], rejection-sampled for the recipe acceptance region, between the two states,
+    and for temperature and density ratios <= t_ratio_max, rho_ratio_max across the interface.
+    Near the critical point a large temperature jump (an entropy jump of c_v ln(T_l/T_r) with
+    c_v = 213) or density jump makes the first steps' dissipation overshoot and push the
+    interface nodes out of the admissible region: 1-15% of unrestricted draws fail in the
+    oracle within three steps, none of 300 with the temperature ratio limited to 1.3, and 2 of
+    4096 on the GPU until the density ratio was limited too."""
     rng = np.random.default_rng(seed)
     if lengths is None:
         lengths = rng.integers(lmin, lmax + 1, size=nprob)
@@ -161,7 +168,9 @@ def shock_tube_batch(nprob=4096, lmin=200, lmax=8000, seed=12345, lengths=None):
             rl, rr = rng.uniform(0.2, 2.5, 2)
             pl, pr = rng.uniform(0.3, 2.0, 2)
             vl, vr = rng.uniform(-1.0, 1.0, 2)
-            if _recipe_ok(rl, pl) and _recipe_ok(rr, pr) and _pair_ok((rl, pl), (rr, pr)):
+            Tl, Tr = _recipe_temperature(rl, pl), _recipe_temperature(rr, pr)
+            if (_recipe_ok(rl, pl) and _recipe_ok(rr, pr) and _pair_ok((rl, pl), (rr, pr))
+                    and max(Tl, Tr) <= t_ratio_max * min(Tl, Tr) and max(rl, rr) <= rho_ratio_max * min(rl, rr)):
                 break
         states[i] = (rl, vl, pl, rr, vr, pr)
     return dict(gas=UNITS_A, lengths=lengths, states=states)
