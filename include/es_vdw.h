@@ -132,8 +132,10 @@ int es_cfl_dt(es_ctx* ctx, const void* JU, const void* J, const double* x, doubl
 
 /* Mesh redistribution of Sec. 4 for a step of size dt: monitor (with G) ->
  * filter passes -> Jacobi sweeps from xn -> limiter Delta_gamma -> mesh velocity
- * xdot = Delta_gamma (x^[mu] - xn)/dt.  Writes xdot (device) and, if non-null,
- * the sweeps taken and Delta_gamma (host; this synchronises the stream). */
+ * xdot = Delta_gamma (x^[mu] - xn)/dt.  With a warm-start network registered
+ * (es_set_warm_start) the sweeps start, guarded, from its prediction (see
+ * es_mesh_solve).  Writes xdot (device) and, if non-null, the sweeps taken and
+ * Delta_gamma (host; this synchronises the stream). */
 int es_mesh_redistribute(es_ctx* ctx, const void* JU, const void* J, const double* xn,
                          double dt, double* xdot, int* sweeps_host, double* gamma_host);
 
@@ -160,6 +162,88 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
 /* Number of kernel launches the library has issued (graph launches count
  * their kernels), for launch accounting. */
 int64_t es_launch_count(es_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start of the mesh iteration (2D).  The Jacobi iteration of
+ * Sec. 4 solves the discretised mesh equation for the new node positions from
+ * the monitor omega (after the filter passes); a small network predicts, from
+ * omega, the fundamental derivative G and the current mesh, where that
+ * iteration ends, and the iteration then starts from the prediction.  The plain
+ * iteration always finishes the solve, so the network changes where it starts,
+ * never what it converges to; the guard below keeps the plain start whenever the
+ * prediction is worse. */
+
+/* Features at the mesh x for the state (JU, J), as float planes [4][n2][n1]
+ * (device, caller-owned): ln(omega), G/(1 + |G|), and the displacement of x from
+ * the Cartesian mesh (x_00 + i dxi_1, y_00 + j dxi_2) in cells, per direction.
+ * omega is the filtered monitor of Sec. 4; G = nu^3 p_nunu|_s / (2 c^2). */
+int es_mesh_features(es_ctx* ctx, const void* JU, const void* J, const double* x, float* feat);
+
+/* The Jacobi solve of Sec. 4 alone (no limiter): monitor and filter from (JU, J)
+ * on xn, then sweeps until max |x^[nu+1] - x^[nu]| < p->jacobi_eps (if > 0) or
+ * p->jacobi_sweeps sweeps.  x_start NULL: from xn.  Otherwise the first sweep
+ * runs from both xn and x_start (fixed boundary nodes of x_start must equal xn's),
+ * changing the mesh by c0 and c1 (max norm), and x_start is continued if
+ * c1 < guard_ratio * c0, else xn.  A ratio above 1 admits a start whose first
+ * residual is larger but that lies closer to where the iteration ends; noise at
+ * the grid scale, which a plain Jacobi sweep does not damp, gives c1 >> c0.
+ * x_out (device [dim][n2][n1], not aliasing xn or x_start; nullable) receives the
+ * iterate and disp_out (device float [dim][n2][n1]; nullable, but not both) the
+ * displacement (x^[nu] - xn)_k / dxi_k in cells.  If non-null, *sweeps_host =
+ * sweeps on the continued path (the guarded first sweep counts once) and
+ * *picked_host = 1 if x_start was kept (synchronises). */
+int es_mesh_solve(es_ctx* ctx, const void* JU, const void* J, const double* xn, const double* x_start,
+                  double guard_ratio, double* x_out, float* disp_out, int* sweeps_host, int* picked_host);
+
+/* x_start = xn + dxi_k out_k (out: device float [2][n2][n1], cells) at the nodes
+ * that move; fixed boundary nodes and non-finite outputs keep xn.  The same
+ * kernel forms the registered network's warm start. */
+int es_mesh_warm_start(es_ctx* ctx, const double* xn, const float* out, double* x_start);
+
+/* Register the warm-start network used by es_mesh_redistribute and es_steps:
+ * `layers` 3x3 cross-correlations (zero padding), 4 -> hidden -> ... -> hidden -> 2
+ * channels, tanh after all but the last; the output is the displacement in cells,
+ * x_start = xn + dxi_k out_k (boundary nodes fixed, non-finite outputs dropped).
+ * w_bf16: device bf16 weights, layer by layer, each [Cout][Cin][3][3]; bias:
+ * device float biases, layer by layer.  Both are copied (weights converted to
+ * float), so the caller may free or change them afterwards; register again to
+ * update.  w_bf16 NULL removes the network.  hidden: 4 or 32; 2 <= layers <= 16.
+ * guard_ratio: as in es_mesh_solve. */
+int es_set_warm_start(es_ctx* ctx, const uint16_t* w_bf16, const float* bias, int layers, int hidden,
+                      double guard_ratio);
+
+/* Cumulative mesh-solve counters of es_mesh_redistribute / es_steps: Jacobi
+ * sweeps, solves, and solves that kept the warm start; reset != 0 zeroes them.
+ * Synchronises. */
+int es_mesh_stats(es_ctx* ctx, int64_t* sweeps_total, int64_t* solves, int64_t* warm_kept, int reset);
+
+/* Network building blocks (training and inference of the warm start), all on
+ * device arrays and the given stream.  Activations [B][C][H][W] float, weights
+ * [Cout][Cin][3][3] bf16, biases float[Cout]; C in {2, 4, 32}.
+ *   forward:  out = act(bias + w (*) in), act = tanh if act_tanh, (*) the 3x3
+ *             cross-correlation with zero padding; FP32 accumulation.
+ *   backward: given grad_out = dL/d(out) (overwritten by dL/d(pre-activation)
+ *             when act_tanh, which needs `out`), writes grad_w = dL/dw and
+ *             grad_b = dL/db (summed over the batch, in a fixed order) and, if
+ *             grad_in is non-null, grad_in = dL/d(in).
+ * workspace: device scratch of at least es_nn_workspace_bytes(B, Cin, Cout, H, W)
+ * bytes (forward needs only Cout*Cin*9 floats).  Returns ES_ERR_ARG for bad
+ * shapes, null pointers or aliasing outputs. */
+size_t es_nn_workspace_bytes(int B, int Cin, int Cout, int H, int W);
+int es_nn_conv_forward(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin, int Cout,
+                       int H, int W, int act_tanh, void* workspace, size_t workspace_bytes, void* stream);
+int es_nn_conv_backward(const float* in, const uint16_t* w, const float* out, float* grad_out, float* grad_in,
+                        float* grad_w, float* grad_b, int B, int Cin, int Cout, int H, int W, int act_tanh,
+                        void* workspace, size_t workspace_bytes, void* stream);
+/* dst = src rounded to the nearest bf16 (ties to even), n elements. */
+int es_nn_to_bf16(const float* src, uint16_t* dst, int64_t n, void* stream);
+/* *loss += mean((pred - target)^2) over n elements; grad = 2 (pred - target)/n. */
+int es_nn_mse(const float* pred, const float* target, float* grad, float* loss, int64_t n, void* stream);
+/* One Adam step (Kingma & Ba 2015, bias-corrected, step >= 1) on FP32 master
+ * weights with moments m, v; if w_bf16 is non-null it receives the master rounded
+ * to nearest bf16. */
+int es_nn_adam(float* master, uint16_t* w_bf16, const float* grad, float* m, float* v, int n, float lr, float beta1,
+               float beta2, float eps, int step, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent 1D problems (shock tubes on [0, 1], outflow

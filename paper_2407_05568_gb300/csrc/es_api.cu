@@ -33,6 +33,11 @@ struct es_ctx {
     float *fdisp, *fxd;               // mixed form: FP32 mesh displacement and velocity
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1;
     double *xa, *xb, *xdot;
+    // learned warm start (2D): network copy (float weights), features, activations
+    int nn_layers, nn_hidden;
+    double nn_ratio;                  // guard: keep the warm start if c1 < nn_ratio c0
+    float *nn_wf, *nn_b, *feat, *act0, *act1, *nn_out;
+    double* xw;
     DevScalars* dev;
     DevScalars* hpin;                 // pinned host mirror
     void *hJU, *hJ;                   // device copies for es_run_host
@@ -132,8 +137,8 @@ const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
 const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 const double RK_C[3] = {0.0, 1.0, 0.5};
 
-// monitor -> filter -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
-int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot) {
+// monitor -> filter passes (Sec. 4); returns the buffer holding the filtered omega
+const double* enqueue_monitor(es_ctx* c, const void* JU, const void* J) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s);
@@ -147,21 +152,71 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
         count(c);
         double* tmp = om; om = other; other = tmp;
     }
-    const double* xin = xn;
-    double* xout = c->xa;
-    const int check = c->p.jacobi_eps > 0.0;
-    for (int k = 0; k < c->p.jacobi_sweeps; ++k) {
-        k_jacobi<<<G, B, 0, s>>>(c->g, om, xin, xout, c->dev, check);
+    return om;
+}
+
+// learned warm start x0 = x_n + dxi NN(features) into c->xw
+int enqueue_net(es_ctx* c, const double* om, const double* xn) {
+    const int B = 256, G = c->grid1d;
+    cudaStream_t s = c->s_enq;
+    k_features<<<G, B, 0, s>>>(c->g, om, c->GF, xn, c->feat);
+    count(c);
+    const float* in = c->feat;
+    int cin = c->p.dim + 2;
+    size_t woff = 0, boff = 0;
+    for (int l = 0; l < c->nn_layers; ++l) {
+        const bool last = l == c->nn_layers - 1;
+        const int cout = last ? c->p.dim : c->nn_hidden;
+        float* out = last ? c->nn_out : ((l & 1) ? c->act1 : c->act0);
+        cudaError_t e = nn_conv_forward_f32(in, c->nn_wf + woff, c->nn_b + boff, out, 1, cin, cout, c->g.n2,
+                                            c->g.n1, last ? 0 : 1, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "warm-start network");
         count(c);
-        if (check) {
-            k_jacobi_check<<<1, 32, 0, s>>>(c->dev, c->p.jacobi_eps);
-            count(c);
-        }
-        xin = xout;
-        xout = (xout == c->xa) ? c->xb : c->xa;
+        woff += size_t(cout) * cin * 9;
+        boff += cout;
+        in = out;
+        cin = cout;
     }
-    k_limiter<<<G, B, 0, s>>>(c->g, xn, xin, c->dev);
-    k_velocity<<<G, B, 0, s>>>(c->g, xn, xin, c->dev, xdot);
+    k_warm_start<<<G, B, 0, s>>>(c->g, xn, c->nn_out, c->xw);
+    count(c);
+    return ES_OK;
+}
+
+// Jacobi sweeps from x_n, or guarded from x_start (the first sweep runs from both starts
+// and the start whose sweep changes the mesh less is continued)
+void enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio) {
+    const int B = 256, G = c->grid1d;
+    cudaStream_t s = c->s_enq;
+    const int check = c->p.jacobi_eps > 0.0;
+    const double eps = c->p.jacobi_eps;
+    int k0 = 0;
+    if (x_start && c->p.jacobi_sweeps > 0) {
+        k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, 0, 0, c->dev, 1, RED_JAC, 0, eps);
+        k_jacobi<<<G, B, 0, s>>>(c->g, om, x_start, c->xa, c->xb, 0, 1, c->dev, 1, RED_JAC2, 0, eps);
+        k_pick<<<1, 32, 0, s>>>(c->dev, check, eps, ratio);
+        count(c, 3);
+        k0 = 1;
+    }
+    for (int k = k0; k < c->p.jacobi_sweeps; ++k) {
+        k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, k, 0, c->dev, check, RED_JAC, 1, eps);
+        count(c);
+    }
+}
+
+// monitor -> filter -> [warm start] -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
+int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot) {
+    const int B = 256, G = c->grid1d;
+    cudaStream_t s = c->s_enq;
+    const double* om = enqueue_monitor(c, JU, J);
+    const double* x_start = nullptr;
+    if (c->nn_layers > 0) {
+        int rc = enqueue_net(c, om, xn);
+        if (rc) return rc;
+        x_start = c->xw;
+    }
+    enqueue_jacobi(c, om, xn, x_start, c->nn_ratio);
+    k_limiter<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev);
+    k_velocity<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev, xdot);
     count(c, 2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels");
@@ -355,7 +410,8 @@ void es_destroy(es_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->om0, c->om1,
-                    c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx, c->fdisp, c->fxd};
+                    c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx, c->fdisp, c->fxd,
+                    c->nn_wf, c->nn_b, c->feat, c->act0, c->act1, c->nn_out, c->xw};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->dev) cudaFree(c->dev);
@@ -437,6 +493,114 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
         CK(cudaStreamSynchronize(c->stream), "sync");
         if (sweeps_host) *sweeps_host = c->hpin->sweeps;
         if (gamma_host) *gamma_host = c->hpin->gamma;
+    }
+    return ES_OK;
+}
+
+int es_mesh_features(es_ctx* c, const void* JU, const void* J, const double* x, float* feat) {
+    if (!c || !JU || !J || !x || !feat) return fail(c, ES_ERR_ARG, "null argument");
+    if (c->p.dim != 2) return fail(c, ES_ERR_ARG, "features are defined for 2D meshes");
+    k_reset<<<1, 32, 0, c->stream>>>(c->dev);
+    count(c);
+    const double* om = enqueue_monitor(c, JU, J);
+    k_features<<<c->grid1d, 256, 0, c->stream>>>(c->g, om, c->GF, x, feat);
+    count(c);
+    CK(cudaGetLastError(), "feature kernels");
+    return ES_OK;
+}
+
+int es_mesh_solve(es_ctx* c, const void* JU, const void* J, const double* xn, const double* x_start,
+                  double guard_ratio, double* x_out, float* disp_out, int* sweeps_host, int* picked_host) {
+    if (!c || !JU || !J || !xn || (!x_out && !disp_out)) return fail(c, ES_ERR_ARG, "null argument");
+    if (x_out && (x_out == xn || (x_start && x_out == x_start))) return fail(c, ES_ERR_ARG, "x_out aliases an input");
+    if (x_start && !(guard_ratio >= 0.0)) return fail(c, ES_ERR_ARG, "guard ratio must be >= 0");
+    k_reset<<<1, 32, 0, c->stream>>>(c->dev);
+    count(c);
+    const double* om = enqueue_monitor(c, JU, J);
+    enqueue_jacobi(c, om, xn, x_start, guard_ratio);
+    k_jacobi_out<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, c->xa, c->xb, c->dev, x_out, disp_out);
+    count(c);
+    CK(cudaGetLastError(), "mesh kernels");
+    if (sweeps_host || picked_host) {
+        CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        if (sweeps_host) *sweeps_host = c->hpin->sweeps;
+        if (picked_host) *picked_host = c->hpin->pick;
+    }
+    return ES_OK;
+}
+
+int es_mesh_warm_start(es_ctx* c, const double* xn, const float* out, double* x_start) {
+    if (!c || !xn || !out || !x_start) return fail(c, ES_ERR_ARG, "null argument");
+    if (c->p.dim != 2) return fail(c, ES_ERR_ARG, "the warm start is defined for 2D meshes");
+    if (x_start == xn) return fail(c, ES_ERR_ARG, "x_start aliases xn");
+    k_warm_start<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, out, x_start);
+    count(c);
+    CK(cudaGetLastError(), "k_warm_start");
+    return ES_OK;
+}
+
+int es_set_warm_start(es_ctx* c, const uint16_t* w_bf16, const float* bias, int layers, int hidden,
+                      double guard_ratio) {
+    if (!c) return ES_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (c->gexec) {                       // the step graph changes with the network
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (!w_bf16) {
+        c->nn_layers = 0;
+        return ES_OK;
+    }
+    if (!bias || c->p.dim != 2 || layers < 2 || layers > 16 || !(hidden == 4 || hidden == 32) ||
+        !(guard_ratio >= 0.0))
+        return fail(c, ES_ERR_ARG, "warm start: 2D only, 2..16 layers, hidden 4 or 32, guard ratio >= 0");
+    const int cin0 = c->p.dim + 2;
+    const size_t nw = size_t(hidden) * cin0 * 9 + size_t(layers - 2) * hidden * hidden * 9 +
+                      size_t(c->p.dim) * hidden * 9;
+    const size_t nb = size_t(layers - 1) * hidden + c->p.dim;
+    if (c->nn_hidden != hidden || !c->feat) {
+        void* old[] = {c->nn_wf, c->nn_b, c->act0, c->act1};
+        for (void* b : old)
+            if (b) cudaFree(b);
+        c->nn_wf = c->nn_b = c->act0 = c->act1 = nullptr;
+        const size_t FB = sizeof(float) * c->N;
+        if (!c->feat) {
+            CK(cudaMalloc((void**)&c->feat, FB * cin0), "cudaMalloc");
+            CK(cudaMalloc((void**)&c->nn_out, FB * c->p.dim), "cudaMalloc");
+            CK(cudaMalloc((void**)&c->xw, sizeof(double) * c->N * c->p.dim), "cudaMalloc");
+        }
+        CK(cudaMalloc((void**)&c->act0, FB * hidden), "cudaMalloc");
+        CK(cudaMalloc((void**)&c->act1, FB * hidden), "cudaMalloc");
+    }
+    if (c->nn_wf) cudaFree(c->nn_wf);
+    if (c->nn_b) cudaFree(c->nn_b);
+    c->nn_wf = c->nn_b = nullptr;
+    CK(cudaMalloc((void**)&c->nn_wf, sizeof(float) * nw), "cudaMalloc");
+    CK(cudaMalloc((void**)&c->nn_b, sizeof(float) * nb), "cudaMalloc");
+    CK(nn_bf16_to_float(w_bf16, c->nn_wf, nw, c->stream), "weight copy");
+    CK(cudaMemcpyAsync(c->nn_b, bias, sizeof(float) * nb, cudaMemcpyDeviceToDevice, c->stream), "bias copy");
+    CK(nn_prepare(), "conv kernel attributes");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    c->nn_layers = layers;
+    c->nn_hidden = hidden;
+    c->nn_ratio = guard_ratio;
+    return ES_OK;
+}
+
+int es_mesh_stats(es_ctx* c, int64_t* sweeps_total, int64_t* solves, int64_t* warm_kept, int reset) {
+    if (!c) return ES_ERR_ARG;
+    CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (sweeps_total) *sweeps_total = c->hpin->sweeps_total;
+    if (solves) *solves = c->hpin->solves;
+    if (warm_kept) *warm_kept = c->hpin->warm_kept;
+    if (reset) {
+        c->hpin->sweeps_total = c->hpin->solves = c->hpin->warm_kept = 0;
+        const size_t off = offsetof(DevScalars, sweeps_total);
+        CK(cudaMemcpyAsync((char*)c->dev + off, (char*)c->hpin + off, 3 * sizeof(long long),
+                           cudaMemcpyHostToDevice, c->stream), "copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
     }
     return ES_OK;
 }

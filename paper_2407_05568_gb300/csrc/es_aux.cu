@@ -124,6 +124,8 @@ __global__ void k_reset(DevScalars* d) {
         d->red[RED_GAMMA] = (unsigned long long)__double_as_longlong(1.0);
         d->sweeps = 0;
         d->conv = 0;
+        d->pick = 0;
+        d->done = 0u;
     }
 }
 
@@ -305,25 +307,51 @@ __global__ void k_filter(GridParams g, const double* in, double* out) {
     }
 }
 
-// one Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0
-__global__ void k_jacobi(GridParams g, const double* omega, const double* xin, double* xout, DevScalars* d,
-                         int check) {
+// Result buffer of the Jacobi iteration so far: x_n before the first sweep, else
+// the buffer the last sweep wrote (sweep k writes buf[(pick + k) % 2]).
+__device__ __forceinline__ const double* jacobi_result(const DevScalars* d, const double* xn, const double* xa,
+                                                      const double* xb) {
+    if (d->sweeps == 0) return xn;
+    return ((d->pick + d->sweeps - 1) & 1) ? xb : xa;
+}
+
+__device__ __forceinline__ bool fixed_node(const GridParams& g, int i, int j) {
+    bool f = g.bc[0] == ES_BC_OUTFLOW && (i == 0 || i == g.n1 - 1);
+    if (g.dim == 2) f = f || (g.bc[1] == ES_BC_OUTFLOW && (j == 0 || j == g.n2 - 1));
+    return f;
+}
+
+// One Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0.
+// Sweep k >= 1 reads buf[(pick + k - 1) % 2] and writes buf[(pick + k) % 2]; sweep 0 reads
+// `first` (x_n or the warm start) and writes buf[dst0].  Once the iteration has converged
+// (d->conv) the remaining sweeps return at once.  With `check`, the grid-wide max change
+// goes to red[slot]; if `judge`, the last block to finish compares it with eps.
+__global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
+                         int dst0, DevScalars* d, int check, int slot, int judge, double eps) {
+    if (d->conv) return;
     const int N = g.n1 * g.n2;
-    const bool skip = d->conv != 0;
+    const double* xin;
+    double* xout;
+    if (k == 0) {
+        xin = first;
+        xout = dst0 ? xb : xa;
+    } else {
+        const int src = (d->pick + k - 1) & 1;
+        xin = src ? xb : xa;
+        xout = src ? xa : xb;
+    }
     double chg = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        bool fixed = (g.bc[0] == ES_BC_OUTFLOW && (i == 0 || i == g.n1 - 1));
-        if (g.dim == 2) fixed = fixed || (g.bc[1] == ES_BC_OUTFLOW && (j == 0 || j == g.n2 - 1));
-        if (skip || fixed) {
+        if (fixed_node(g, i, j)) {
             for (int c = 0; c < g.dim; ++c) xout[c * N + id] = xin[c * N + id];
             continue;
         }
         const double w0 = omega[id];
         double den = 0.0, num[2] = {0.0, 0.0};
-        for (int k = 0; k < g.dim; ++k) {
-            const int di = k == 0, dj = k == 1;
-            const double ih2 = g.inv_dxi[k] * g.inv_dxi[k];
+        for (int kk = 0; kk < g.dim; ++kk) {
+            const int di = kk == 0, dj = kk == 1;
+            const double ih2 = g.inv_dxi[kk] * g.inv_dxi[kk];
             const double wp = 0.5 * (w0 + field_at(g, omega, i + di, j + dj)) * ih2;
             const double wm = 0.5 * (w0 + field_at(g, omega, i - di, j - dj)) * ih2;
             den += wp + wm;
@@ -331,29 +359,52 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* xin, d
                 num[c] += wp * coord_at(g, xin, i + di, j + dj, c) + wm * coord_at(g, xin, i - di, j - dj, c);
         }
         for (int c = 0; c < g.dim; ++c) {
-            const double xn = num[c] / den;
-            chg = fmax(chg, fabs(xn - xin[c * N + id]));
-            xout[c * N + id] = xn;
+            const double xv = num[c] / den;
+            chg = fmax(chg, fabs(xv - xin[c * N + id]));
+            xout[c * N + id] = xv;
         }
     }
     if (check) {
         chg = block_reduce_max(chg);
-        if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_JAC], chg);
+        if (threadIdx.x == 0) {
+            atomic_max_pos(&d->red[slot], chg);
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {                 // every block's maximum is in
+                if (judge) {
+                    const double c = __longlong_as_double((long long)atomicAdd(&d->red[slot], 0ULL));
+                    if (c < eps) d->conv = 1;
+                    d->red[slot] = 0ULL;
+                }
+                d->done = 0u;
+            }
+        }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !skip) atomicAdd(&d->sweeps, 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (k > 0 || slot == RED_JAC)) atomicAdd(&d->sweeps, 1);
 }
 
-__global__ void k_jacobi_check(DevScalars* d, double eps) {
+// Guarded warm start: the first sweep ran from x_n (into buf[0], change c0 in red[RED_JAC]) and
+// from the warm start (into buf[1], change c1 in red[RED_JAC2]); keep the warm start if
+// c1 < ratio c0 (ties and non-finite changes keep x_n).
+__global__ void k_pick(DevScalars* d, int check, double eps, double ratio) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const double c = __longlong_as_double((long long)d->red[RED_JAC]);
-        if (d->conv == 0 && c < eps) d->conv = 1;
+        const double c0 = __longlong_as_double((long long)d->red[RED_JAC]);
+        const double c1 = __longlong_as_double((long long)d->red[RED_JAC2]);
+        const int pick = (c1 < ratio * c0) ? 1 : 0;
+        d->pick = pick;
+        d->sweeps = 1;
+        if (check && (pick ? c1 : c0) < eps) d->conv = 1;
         d->red[RED_JAC] = 0ULL;
+        d->red[RED_JAC2] = 0ULL;
+        d->last_change[0] = c0;
+        d->last_change[1] = c1;
     }
 }
 
 // Delta_gamma: each node moves at most half of the spacing towards its neighbour (Sec. 4)
-__global__ void k_limiter(GridParams g, const double* xn, const double* xit, DevScalars* d) {
+__global__ void k_limiter(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d) {
     const int N = g.n1 * g.n2;
+    const double* xit = jacobi_result(d, xn, xa, xb);
     double m = 1.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
@@ -368,14 +419,63 @@ __global__ void k_limiter(GridParams g, const double* xn, const double* xit, Dev
     if (threadIdx.x == 0) atomic_min_pos(&d->red[RED_GAMMA], m);
 }
 
-__global__ void k_velocity(GridParams g, const double* xn, const double* xit, DevScalars* d, double* xdot) {
+__global__ void k_velocity(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d,
+                           double* xdot) {
     const int N = g.n1 * g.n2;
+    const double* xit = jacobi_result(d, xn, xa, xb);
     const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
     const double dt = d->dt;
     const double f = dt > 0.0 ? gam / dt : 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
         xdot[id] = f * (xit[id] - xn[id]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) d->gamma = gam;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d->gamma = gam;
+        d->sweeps_total += d->sweeps;
+        d->solves += 1;
+        d->warm_kept += d->pick;
+    }
+}
+
+// x_out = the Jacobi iterate (no limiter); disp = (x_out - x_n)/dxi_k as float (both nullable)
+__global__ void k_jacobi_out(GridParams g, const double* xn, const double* xa, const double* xb,
+                             const DevScalars* d, double* xout, float* disp) {
+    const int N = g.n1 * g.n2;
+    const double* xit = jacobi_result(d, xn, xa, xb);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x) {
+        const double v = xit[id];
+        if (xout) xout[id] = v;
+        if (disp) disp[id] = float((v - xn[id]) * g.inv_dxi[id / N]);
+    }
+}
+
+// Features of the learned warm start (2D): ln(omega), G/(1 + |G|) and the mesh
+// displacement from the Cartesian base in cells, as float planes [4][n2][n1].
+__global__ void k_features(GridParams g, const double* omega, const double* GF, const double* x, float* feat) {
+    const int N = g.n1 * g.n2;
+    const double x00 = x[0], y00 = x[N];
+    const double dxi1 = 1.0 / g.inv_dxi[0], dxi2 = 1.0 / g.inv_dxi[1];
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        const double G = GF[id];
+        feat[id] = float(log(omega[id]));
+        feat[N + id] = float(G / (1.0 + fabs(G)));
+        feat[2 * N + id] = float((x[id] - (x00 + i * dxi1)) * g.inv_dxi[0]);
+        feat[3 * N + id] = float((x[N + id] - (y00 + j * dxi2)) * g.inv_dxi[1]);
+    }
+}
+
+// warm start x0 = x_n + dxi * NN (per direction); fixed nodes and non-finite outputs keep x_n
+__global__ void k_warm_start(GridParams g, const double* xn, const float* out, double* x0) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        const bool fixed = fixed_node(g, i, j);
+        for (int c = 0; c < 2; ++c) {
+            const float o = out[c * N + id];
+            const bool ok = !fixed && isfinite(o);
+            x0[c * N + id] = xn[c * N + id] + (ok ? double(o) / g.inv_dxi[c] : 0.0);
+        }
+    }
 }
 
 // Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)

@@ -20,15 +20,19 @@ struct MonitorParams {
     double w0, w1, w2;   // weights of the three monitor terms
 };
 
-enum { RED_CFL = 0, RED_MON0 = 1, RED_MON1 = 2, RED_MON2 = 3, RED_GAMMA = 4, RED_JAC = 5 };
+enum { RED_CFL = 0, RED_MON0 = 1, RED_MON1 = 2, RED_MON2 = 3, RED_GAMMA = 4, RED_JAC = 5, RED_JAC2 = 6 };
 
 // Device-resident scalars of a run.
 struct DevScalars {
     double t, dt, t_end, last_dt, gamma;
     unsigned long long red[8];
-    int sweeps;
-    int conv;
+    int sweeps;          // Jacobi sweeps of the current solve
+    int conv;            // the current solve reached its tolerance
+    int pick;            // 1: the warm start was kept
+    unsigned int done;   // blocks finished (last-block reductions)
     DevStatus status;
+    double last_change[2];                     // first-sweep changes from x_n and from the warm start
+    long long sweeps_total, solves, warm_kept; // cumulative mesh-solve counters
 };
 
 // kernels templated on the state type are launched through these (f32: float state)
@@ -49,10 +53,15 @@ __global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, 
 __global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,
                             const DevScalars* d, double* omega);
 __global__ void k_filter(GridParams g, const double* in, double* out);
-__global__ void k_jacobi(GridParams g, const double* omega, const double* xin, double* xout, DevScalars* d,
-                         int check);
-__global__ void k_jacobi_check(DevScalars* d, double eps);
-__global__ void k_limiter(GridParams g, const double* xn, const double* xit, DevScalars* d);
-__global__ void k_velocity(GridParams g, const double* xn, const double* xit, DevScalars* d, double* xdot);
+__global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
+                         int dst0, DevScalars* d, int check, int slot, int judge, double eps);
+__global__ void k_pick(DevScalars* d, int check, double eps, double ratio);
+__global__ void k_limiter(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d);
+__global__ void k_velocity(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d,
+                           double* xdot);
+__global__ void k_jacobi_out(GridParams g, const double* xn, const double* xa, const double* xb,
+                             const DevScalars* d, double* xout, float* disp);
+__global__ void k_features(GridParams g, const double* omega, const double* GF, const double* x, float* feat);
+__global__ void k_warm_start(GridParams g, const double* xn, const float* out, double* x0);
 
 }  // namespace es

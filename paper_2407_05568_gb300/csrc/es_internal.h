@@ -84,4 +84,10 @@ cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s);
 cudaError_t stage_prepare_fp64(int dim);
 cudaError_t stage_prepare_mixed(int dim);
 
+// learned warm start (es_nn.cu): conv kernels' shared-memory attributes, weight copy, forward layer
+cudaError_t nn_prepare();
+cudaError_t nn_bf16_to_float(const uint16_t* w, float* f, size_t n, cudaStream_t s);
+cudaError_t nn_conv_forward_f32(const float* in, const float* wf, const float* bias, float* out, int B, int Cin,
+                                int Cout, int H, int W, int act, cudaStream_t s);
+
 }  // namespace es

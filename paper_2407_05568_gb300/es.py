@@ -81,6 +81,23 @@ def lib():
         L.es_batch_get.argtypes = [vp, vp, vp, vp, vp]
         L.es_batch_check.argtypes = [vp]
         L.es_batch_last_error.argtypes = [vp, ctypes.c_char_p, i]
+        L.es_mesh_features.argtypes = [vp, vp, vp, vp, vp]
+        L.es_mesh_solve.argtypes = [vp, vp, vp, vp, vp, d, vp, vp, ctypes.POINTER(i), ctypes.POINTER(i)]
+        L.es_set_warm_start.argtypes = [vp, vp, vp, i, i, d]
+        L.es_mesh_warm_start.argtypes = [vp, vp, vp, vp]
+        L.es_mesh_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64), i]
+        L.es_nn_workspace_bytes.argtypes = [i, i, i, i, i]
+        L.es_nn_workspace_bytes.restype = ctypes.c_size_t
+        L.es_nn_conv_forward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp, ctypes.c_size_t, vp]
+        L.es_nn_conv_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, i, i, i, vp, ctypes.c_size_t, vp]
+        L.es_nn_mse.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
+        L.es_nn_to_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
+        f = ctypes.c_float
+        L.es_nn_adam.argtypes = [vp, vp, vp, vp, vp, i, f, f, f, f, i, vp]
+        for name in ("es_mesh_features", "es_mesh_solve", "es_set_warm_start", "es_mesh_stats", "es_mesh_warm_start",
+                     "es_nn_conv_forward", "es_nn_conv_backward", "es_nn_mse", "es_nn_adam", "es_nn_to_bf16"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("es_batch_create", "es_batch_set_prim", "es_batch_steps", "es_batch_get", "es_batch_check",
                      "es_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -185,6 +202,8 @@ def state_empty(ctx, shape, device):
 
 
 F64 = "torch.float64"
+F32 = "torch.float32"
+BF16 = "torch.bfloat16"
 
 
 def es_init_mesh(ctx, x, J):
@@ -222,6 +241,85 @@ def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot):
     ctx._call(lib().es_mesh_redistribute(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(xn, F64), dt, _ptr(xdot, F64),
                                          ctypes.byref(sw), ctypes.byref(gam)))
     return sw.value, gam.value
+
+
+def es_mesh_features(ctx, JU, J, x, feat):
+    """Warm-start features [4][n2][n1] (float32) at the mesh x."""
+    S = ctx.state_dtype
+    ctx._call(lib().es_mesh_features(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), _ptr(feat, F32)))
+
+
+def es_mesh_solve(ctx, JU, J, xn, x_start, x_out, disp_out=None, guard_ratio=1.0):
+    """Jacobi solve of the mesh equation from xn (x_start None) or guarded from x_start;
+    writes x_out (float64) and/or disp_out (float32, cells); returns (sweeps, picked)."""
+    S = ctx.state_dtype
+    sw = ctypes.c_int()
+    pk = ctypes.c_int()
+    ctx._call(lib().es_mesh_solve(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(xn, F64), _ptr(x_start, F64),
+                                  float(guard_ratio), _ptr(x_out, F64), _ptr(disp_out, F32), ctypes.byref(sw),
+                                  ctypes.byref(pk)))
+    return sw.value, pk.value
+
+
+def es_mesh_warm_start(ctx, xn, out, x_start):
+    """x_start = xn + dxi out (out in cells, float32 [2][n2][n1]); fixed nodes keep xn."""
+    ctx._call(lib().es_mesh_warm_start(ctx._h, _ptr(xn, F64), _ptr(out, F32), _ptr(x_start, F64)))
+
+
+def es_set_warm_start(ctx, w_bf16, bias, layers, hidden, guard_ratio=1.0):
+    """Register (or with w_bf16 None remove) the warm-start network; the context copies it."""
+    ctx._call(lib().es_set_warm_start(ctx._h, _ptr(w_bf16, BF16), _ptr(bias, F32), int(layers), int(hidden),
+                                      float(guard_ratio)))
+
+
+def es_mesh_stats(ctx, reset=False):
+    """(sweeps_total, solves, warm_kept) since the last reset."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    ctx._call(lib().es_mesh_stats(ctx._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), int(reset)))
+    return a.value, b.value, c.value
+
+
+def _nn_rc(rc, what):
+    if rc != ES_OK:
+        raise EsError(rc, f"{what} failed")
+
+
+def es_nn_workspace_bytes(B, Cin, Cout, H, W):
+    return int(lib().es_nn_workspace_bytes(int(B), int(Cin), int(Cout), int(H), int(W)))
+
+
+def es_nn_conv_forward(inp, w, bias, out, act_tanh, workspace, stream=None):
+    """out = act(bias + w (*) inp) for inp [B][Cin][H][W], w [Cout][Cin][3][3] bf16."""
+    B, Cin, H, W = inp.shape
+    Cout = w.shape[0]
+    _nn_rc(lib().es_nn_conv_forward(_ptr(inp, F32), _ptr(w, BF16), _ptr(bias, F32), _ptr(out, F32), B, Cin, Cout,
+                                    H, W, int(act_tanh), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                    _stream_handle(stream)), "es_nn_conv_forward")
+
+
+def es_nn_conv_backward(inp, w, out, grad_out, grad_in, grad_w, grad_b, act_tanh, workspace, stream=None):
+    B, Cin, H, W = inp.shape
+    Cout = w.shape[0]
+    _nn_rc(lib().es_nn_conv_backward(_ptr(inp, F32), _ptr(w, BF16), _ptr(out, F32), _ptr(grad_out, F32),
+                                     _ptr(grad_in, F32), _ptr(grad_w, F32), _ptr(grad_b, F32), B, Cin, Cout, H, W,
+                                     int(act_tanh), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                     _stream_handle(stream)), "es_nn_conv_backward")
+
+
+def es_nn_to_bf16(src, dst, stream=None):
+    _nn_rc(lib().es_nn_to_bf16(_ptr(src, F32), _ptr(dst, BF16), src.numel(), _stream_handle(stream)),
+           "es_nn_to_bf16")
+
+
+def es_nn_mse(pred, target, grad, loss, stream=None):
+    _nn_rc(lib().es_nn_mse(_ptr(pred, F32), _ptr(target, F32), _ptr(grad, F32), _ptr(loss, F32), pred.numel(),
+                           _stream_handle(stream)), "es_nn_mse")
+
+
+def es_nn_adam(master, w_bf16, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _nn_rc(lib().es_nn_adam(_ptr(master, F32), _ptr(w_bf16, BF16), _ptr(grad, F32), _ptr(m, F32), _ptr(v, F32),
+                            master.numel(), float(lr), float(beta1), float(beta2), float(eps), int(step),
+                            _stream_handle(stream)), "es_nn_adam")
 
 
 def es_steps(ctx, JU, J, x, nsteps, t_end):
