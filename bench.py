@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--learned", action="store_true",
+                    help="also train and evaluate the learned warm start (512^2, about 3 minutes)")
+    ap.add_argument("--learned-n", type=int, default=512)
+    ap.add_argument("--learned-seeds", type=int, default=20, help="plain runs; the last two are held out")
+    ap.add_argument("--learned-steps", type=int, default=100)
+    ap.add_argument("--learned-epochs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -294,6 +300,59 @@ def measure_batch(args, dev, stream):
             "l2": "state (2 GB) larger than L2"}
 
 
+def measure_learned(args, dev):
+    """The learned warm start on the 2D vdW Riemann problem: snapshots of plain runs (Jacobi to
+    max change < 0.02 cells, at most 300 sweeps), training, and the plain against the
+    warm-started solve on held-out seeds (same states, then two full runs)."""
+    import time
+
+    import torch
+
+    from paper_2407_05568_gb300 import learned
+    n, eps, mu = args.learned_n, 0.02, 300
+    seeds = list(range(100, 100 + args.learned_seeds))
+    train_seeds, test_seeds = seeds[:-2], seeds[-2:]
+    t0 = time.perf_counter()
+    feats, tgts, sw = learned.snapshots(train_seeds, n, args.learned_steps, eps, mu, device=dev)
+    torch.cuda.synchronize()
+    t_snap = time.perf_counter() - t0
+    net = learned.WarmStartNet(hidden=32, layers=4, seed=0, in_scale=learned.feature_scale(feats), device=dev)
+    t0 = time.perf_counter()
+    hist = learned.train(net, feats, tgts, epochs=args.learned_epochs, batch=4, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    iters = args.learned_epochs * (feats.shape[0] // 4)
+    del feats, tgts
+    torch.cuda.empty_cache()
+    # inference time of the network alone (four conv launches on one n x n image)
+    x = torch.zeros((1, 4, n, n), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        net.forward(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        net.forward(x)
+    e1.record()
+    torch.cuda.synchronize()
+    t_inf = e0.elapsed_time(e1) / 20
+    cmp = learned.compare_solves(net, test_seeds, n, args.learned_steps, eps, mu, device=dev)
+    run = learned.compare_runs(net, test_seeds[0], n, args.learned_steps, eps, mu, device=dev)
+    return {"workload": f"2D vdW Riemann problem {n}x{n}, moving mesh, Jacobi to max change < {eps} cells "
+                        f"(at most {mu} sweeps); network 4 conv3x3 layers, 32 channels, bf16 weights",
+            "snapshots": int(len(sw)), "train_seeds": f"{train_seeds[0]}..{train_seeds[-1]}",
+            "test_seeds": test_seeds, "steps_per_seed": args.learned_steps,
+            "snapshot_seconds": t_snap, "train_seconds": t_train, "train_iterations": iters,
+            "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+            "guard_ratio": learned.GUARD_RATIO,
+            "same_states": {"sweeps_plain": float(cmp["sweeps_plain"].mean()),
+                            "sweeps_warm": float(cmp["sweeps_warm"].mean()),
+                            "sweeps_saved_frac": float(1 - cmp["sweeps_warm"].mean() / cmp["sweeps_plain"].mean()),
+                            "warm_kept_frac": float(cmp["picked"].mean()),
+                            "mesh_dev_cells_max": float(cmp["dev_cells"].max()),
+                            "mesh_dev_cells_mean": float(cmp["dev_cells"].mean())},
+            "full_runs": run, "nn_inference_ms": t_inf}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -314,6 +373,7 @@ def run_gpu(args):
     batched = None
     if args.batch_problems > 0 and rank == 0:
         batched = measure_batch(args, dev, stream)
+    learned_res = measure_learned(args, dev) if args.learned and rank == 0 else None
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -336,6 +396,8 @@ def run_gpu(args):
                               "e2e": {"value": other["e2e"], "unit": "cell-updates/s"}}
         if batched is not None:
             line["batched"] = batched
+        if learned_res is not None:
+            line["learned"] = learned_res
         if not args.no_cpu_baseline:
             sec, k = time_oracle(workload(args.n), 8)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),
