@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="also run the precision-form sweep: 2D sine 1024^2 and the vortex 64^2..1024^2, both forms")
     ap.add_argument("--learned", action="store_true",
                     help="also train and evaluate the learned warm start (512^2, about 3 minutes)")
     ap.add_argument("--learned-n", type=int, default=512)
@@ -279,6 +281,7 @@ def measure_batch(args, dev, stream):
     with torch.cuda.stream(stream):
         rho, v, p = (torch.tensor(a, dtype=torch.float64, device=dev) for a in wl.batch_fields(batch))
         es.es_batch_set_prim(b, rho, v, p)
+    bt, probe_ms = es.es_batch_autotune(b)                # CTA shape: one probe step per shape
     es.es_batch_steps(b, args.batch_steps, 1e30)          # warm-up launch (captures the graph)
     if es.es_batch_check(b):
         raise RuntimeError("batched form: device status")
@@ -297,7 +300,68 @@ def measure_batch(args, dev, stream):
                         f"({b.ntot} nodes), moving mesh, one persistent launch per {args.batch_steps} steps",
             "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_launch": ms,
             "steps_per_launch": args.batch_steps, "nodes": b.ntot, "dtype": "f32",
+            "autotune": {"threads_per_cta": bt, "probe_ms_128_256_512": probe_ms},
             "l2": "state (2 GB) larger than L2"}
+
+
+def run_to_end(w, precision, dev):
+    """Advance a workload to its t_end with es_steps (graph replays); returns the density at the end
+    (float64 numpy), the steps taken and the device time."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    ctx, JU, J, x = es.setup_workload(w, precision, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 0
+    es.es_steps(ctx, JU, J, x, 1, w["t_end"])        # capture the step graph
+    steps += 1
+    torch.cuda.synchronize()
+    ms = 0.0
+    t, dt = es.es_get_time(ctx)
+    while t < w["t_end"] * (1 - 1e-14):
+        k = max(1, min(200, int((w["t_end"] - t) / max(dt, 1e-300)) + 1))
+        e0.record()
+        es.es_steps(ctx, JU, J, x, k, w["t_end"])
+        e1.record()
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        steps += k
+        t, dt = es.es_get_time(ctx)
+    if es.es_check(ctx):
+        raise RuntimeError(es.es_last_error(ctx))
+    if JU.dtype == torch.float64:
+        rho = (JU[0] / J).cpu().numpy()
+    else:
+        rho = ((JU[0, 0].double() + JU[1, 0].double()) / (J[0].double() + J[1].double())).cpu().numpy()
+    return rho, steps, ms
+
+
+def measure_precision_sweep(args, dev):
+    """The precision form against the plain FP64 form: L1(rho) against the exact solution and
+    against the FP64 run, and throughput, on the 2D sine wave (1024^2, t = 0.1) and the ideal-gas
+    isentropic vortex (64^2 .. 1024^2, t = 1)."""
+    from paper_2407_05568_gb300 import workloads as wl
+    out = []
+    cases = [("sine2d", 1024)] + [("vortex", n) for n in (64, 128, 256, 512, 1024)]
+    for name, n in cases:
+        w = wl.sine_2d(n) if name == "sine2d" else wl.isentropic_vortex(n)
+        X, Y = w["x"]
+        t = w["t_end"]
+        exact = (0.5 + 0.2 * np.sin(2 * np.pi * (X + Y - t))) if name == "sine2d" else wl.vortex_density(X, Y, t)
+        row = {"case": name, "n": n, "t_end": t}
+        res = {}
+        for prec in ("fp64", "mixed"):
+            rho, steps, ms = run_to_end(w, prec, dev)
+            res[prec] = rho
+            row[prec] = {"l1_vs_exact": float(np.abs(rho - exact).mean()), "steps": steps,
+                         "cell_updates_per_s": n * n * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None}
+        row["mixed_rel_l1_vs_fp64"] = float(np.abs(res["mixed"] - res["fp64"]).sum() / np.abs(res["fp64"]).sum())
+        out.append(row)
+    vort = [r for r in out if r["case"] == "vortex"]
+    for a, b in zip(vort, vort[1:]):
+        for prec in ("fp64", "mixed"):
+            b[prec]["order_vs_previous"] = float(np.log2(a[prec]["l1_vs_exact"] / b[prec]["l1_vs_exact"]))
+    return out
 
 
 def measure_learned(args, dev):
@@ -374,6 +438,7 @@ def run_gpu(args):
     if args.batch_problems > 0 and rank == 0:
         batched = measure_batch(args, dev, stream)
     learned_res = measure_learned(args, dev) if args.learned and rank == 0 else None
+    sweep_res = measure_precision_sweep(args, dev) if args.precision_sweep and rank == 0 else None
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -398,6 +463,8 @@ def run_gpu(args):
             line["batched"] = batched
         if learned_res is not None:
             line["learned"] = learned_res
+        if sweep_res is not None:
+            line["precision_sweep"] = sweep_res
         if not args.no_cpu_baseline:
             sec, k = time_oracle(workload(args.n), 8)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),

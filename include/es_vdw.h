@@ -267,6 +267,13 @@ int64_t es_batch_nodes(es_batch* b);
 int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const double* p);
 /* Advance every problem by nsteps full steps (each clipped to t_end). */
 int es_batch_steps(es_batch* b, int nsteps, double t_end);
+/* Autotuner of the CTA shape: runs one step of every shape the library has
+ * (128, 256 or 512 threads per CTA, stage chunks of threads - 2 nodes; the grid
+ * is SMs x resident CTAs of that shape) from the current state, restores the
+ * state, and keeps the fastest for the following es_batch_steps.  Writes the
+ * chosen threads per CTA and, if ms_host is non-null, the three probe times
+ * (ms).  Needs a temporary copy of the state (26 floats per node).  Synchronises. */
+int es_batch_autotune(es_batch* b, int* bt_host, double* ms_host);
 /* State as doubles: JU [3][ntot], J [ntot], x [ntot]; t [nprob] (nullable).  Device arrays. */
 int es_batch_get(es_batch* b, double* JU, double* J, double* x, double* t);
 int es_batch_check(es_batch* b);                      /* synchronises; latched device status */

@@ -28,16 +28,20 @@ using namespace mixed;
 
 namespace {
 
-constexpr int BT = 256;                       // threads per CTA
-constexpr int BXC = 254;                      // nodes per stage chunk
-using TB = TileF<1, BXC, 1, BT>;
+// CTA shapes the autotuner chooses from: BT threads, chunks of BT - 2 nodes per stage tile
+template <int BT>
+struct BatchShape {
+    static constexpr int BXC = BT - 2;
+    using TB = TileF<1, BXC, 1, BT>;
+    static constexpr int MIN_BLOCKS = BT >= 512 ? 1 : 512 / BT;
+};
 
 __device__ __forceinline__ float block_max_f(float v, float* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float r = red[0];
-    for (int w = 1; w < BT / 32; ++w) r = fmaxf(r, red[w]);
+    for (int w = 1; w < int(blockDim.x) / 32; ++w) r = fmaxf(r, red[w]);
     __syncthreads();
     return r;
 }
@@ -47,14 +51,16 @@ __device__ __forceinline__ float block_min_f(float v, float* red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float r = red[0];
-    for (int w = 1; w < BT / 32; ++w) r = fminf(r, red[w]);
+    for (int w = 1; w < int(blockDim.x) / 32; ++w) r = fminf(r, red[w]);
     __syncthreads();
     return r;
 }
 
 __device__ __forceinline__ int clampi(int i, int L) { return i < 0 ? 0 : (i >= L ? L - 1 : i); }
 
-__global__ void __launch_bounds__(BT, 2) batch_kernel(BatchParams B) {
+template <int BT>
+__global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(BatchParams B) {
+    constexpr int BXC = BatchShape<BT>::BXC;
     extern __shared__ float smemf[];
     __shared__ float red[BT / 32];
     __shared__ int s_item;
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(BT, 2) batch_kernel(BatchParams B) {
                 __syncthreads();
             }
 
-            // ---- three fused RK stages, each a loop over 254-node chunks
+            // ---- three fused RK stages, each a loop over BXC-node chunks
             StageParams P = B.tmpl;
             P.n1 = L;
             P.n2 = 1;
@@ -214,23 +220,46 @@ __global__ void __launch_bounds__(BT, 2) batch_kernel(BatchParams B) {
     }
 }
 
-}  // namespace
-
-size_t batch_smem_bytes() { return TB::SMEM; }
-
-cudaError_t batch_prepare() {
-    return cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TB::SMEM));
+template <int BT>
+cudaError_t prepare_shape() {
+    return cudaFuncSetAttribute(batch_kernel<BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(BatchShape<BT>::TB::SMEM));
 }
 
-cudaError_t batch_launch(const BatchParams& B, int grid, cudaStream_t s) {
-    batch_kernel<<<grid, BT, TB::SMEM, s>>>(B);
+template <int BT>
+int blocks_per_sm_shape() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<BT>, BT, BatchShape<BT>::TB::SMEM);
+    return nb;
+}
+
+}  // namespace
+
+const int BATCH_SHAPES[BATCH_NSHAPES] = {128, 256, 512};
+
+size_t batch_smem_bytes(int bt) {
+    return bt == 128 ? BatchShape<128>::TB::SMEM : bt == 512 ? BatchShape<512>::TB::SMEM : BatchShape<256>::TB::SMEM;
+}
+
+cudaError_t batch_prepare() {
+    cudaError_t e = prepare_shape<128>();
+    if (e == cudaSuccess) e = prepare_shape<256>();
+    if (e == cudaSuccess) e = prepare_shape<512>();
+    return e;
+}
+
+cudaError_t batch_launch(const BatchParams& B, int grid, int bt, cudaStream_t s) {
+    switch (bt) {
+        case 128: batch_kernel<128><<<grid, 128, BatchShape<128>::TB::SMEM, s>>>(B); break;
+        case 512: batch_kernel<512><<<grid, 512, BatchShape<512>::TB::SMEM, s>>>(B); break;
+        case 256: batch_kernel<256><<<grid, 256, BatchShape<256>::TB::SMEM, s>>>(B); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm() {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel, BT, TB::SMEM);
-    return nb;
+int batch_blocks_per_sm(int bt) {
+    return bt == 128 ? blocks_per_sm_shape<128>() : bt == 512 ? blocks_per_sm_shape<512>() : blocks_per_sm_shape<256>();
 }
 
 // per-problem elementwise kernels (one CTA per problem)
@@ -290,6 +319,8 @@ struct es_batch {
     int* queue;
     DevStatus* status;
     int grid;
+    int bt;                           // threads per CTA (the CTA shape)
+    int nsm;
     cudaGraphExec_t gexec;
     int g_nsteps;
     double g_tend;
@@ -308,6 +339,18 @@ int bfail(es_batch* b, cudaError_t e, const char* where) {
         cudaError_t e_ = (call);                       \
         if (e_ != cudaSuccess) return bfail(b, e_, where); \
     } while (0)
+
+// CTA shape and the persistent grid: SMs x resident CTAs of that shape, at most one per problem
+void set_shape(es_batch* b, int bt) {
+    b->bt = bt;
+    const int per_sm = batch_blocks_per_sm(bt);
+    b->grid = b->nsm * (per_sm > 0 ? per_sm : 1);
+    if (b->grid > b->B.nprob) b->grid = b->B.nprob;
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+}
 
 }  // namespace
 
@@ -425,9 +468,8 @@ int es_batch_create(es_batch** out, const es_params* p, int nprob, const int* le
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = batch_blocks_per_sm();
-    b->grid = nsm * (per_sm > 0 ? per_sm : 1);
-    if (b->grid > nprob) b->grid = nprob;
+    b->nsm = nsm;
+    set_shape(b, 256);
     *out = b;
     return ES_OK;
 }
@@ -471,7 +513,7 @@ int es_batch_steps(es_batch* b, int nsteps, double t_end) {
         cudaGraph_t graph;
         BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t e1 = cudaMemsetAsync(b->queue, 0, sizeof(int), b->cap_stream);
-        cudaError_t e2 = batch_launch(B, b->grid, b->cap_stream);
+        cudaError_t e2 = batch_launch(B, b->grid, b->bt, b->cap_stream);
         cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &graph);
         if (e1 != cudaSuccess) return bfail(b, e1, "memset");
         if (e2 != cudaSuccess) return bfail(b, e2, "batch kernel");
@@ -483,6 +525,56 @@ int es_batch_steps(es_batch* b, int nsteps, double t_end) {
         b->g_tend = t_end;
     }
     BCK(cudaGraphLaunch(b->gexec, b->stream), "graph launch");
+    return ES_OK;
+}
+
+int es_batch_autotune(es_batch* b, int* bt_host, double* ms_host) {
+    if (!b) return ES_ERR_ARG;
+    const size_t sbytes = sizeof(float) * b->B.ntot * 26, tbytes = sizeof(double) * b->B.nprob;
+    char* save = nullptr;
+    BCK(cudaMalloc((void**)&save, sbytes + tbytes), "cudaMalloc");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save, b->state, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save + sbytes, b->tprob, tbytes, cudaMemcpyDeviceToDevice, b->stream);
+    BatchParams B = b->B;
+    B.nsteps = 1;
+    B.t_end = 1e300;
+    int best = 256;
+    float best_ms = 3.0e38f;
+    for (int k = 0; k < BATCH_NSHAPES && e == cudaSuccess; ++k) {
+        const int bt = BATCH_SHAPES[k];
+        const int per_sm = batch_blocks_per_sm(bt);
+        int grid = b->nsm * (per_sm > 0 ? per_sm : 1);
+        if (grid > b->B.nprob) grid = b->B.nprob;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run loads the kernel
+            e = cudaMemcpyAsync(b->state, save, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->tprob, save + sbytes, tbytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = batch_launch(B, grid, bt, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms_host) ms_host[k] = ms;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = bt;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->state, save, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->tprob, save + sbytes, tbytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (e != cudaSuccess) return bfail(b, e, "autotune");
+    set_shape(b, best);
+    if (bt_host) *bt_host = best;
     return ES_OK;
 }
 

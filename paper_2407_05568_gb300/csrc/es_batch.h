@@ -35,9 +35,12 @@ struct BatchParams {
     StageParams tmpl;             // gas, WENO and the float constants of the stage kernel
 };
 
+// CTA shapes (threads per CTA) of the batched kernel; the autotuner times each
+constexpr int BATCH_NSHAPES = 3;
+extern const int BATCH_SHAPES[BATCH_NSHAPES];
 cudaError_t batch_prepare();
-cudaError_t batch_launch(const BatchParams& B, int grid, cudaStream_t s);
-int batch_blocks_per_sm();
-size_t batch_smem_bytes();
+cudaError_t batch_launch(const BatchParams& B, int grid, int bt, cudaStream_t s);
+int batch_blocks_per_sm(int bt);
+size_t batch_smem_bytes(int bt);
 
 }  // namespace es

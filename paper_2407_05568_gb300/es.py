@@ -78,6 +78,7 @@ def lib():
         L.es_batch_nodes.restype = ctypes.c_int64
         L.es_batch_set_prim.argtypes = [vp, vp, vp, vp]
         L.es_batch_steps.argtypes = [vp, i, d]
+        L.es_batch_autotune.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         L.es_batch_get.argtypes = [vp, vp, vp, vp, vp]
         L.es_batch_check.argtypes = [vp]
         L.es_batch_last_error.argtypes = [vp, ctypes.c_char_p, i]
@@ -99,6 +100,7 @@ def lib():
                      "es_nn_conv_forward", "es_nn_conv_backward", "es_nn_mse", "es_nn_adam", "es_nn_to_bf16"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("es_batch_create", "es_batch_set_prim", "es_batch_steps", "es_batch_get", "es_batch_check",
+                     "es_batch_autotune",
                      "es_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
@@ -399,6 +401,15 @@ def es_batch_steps(b, nsteps, t_end):
     b._call(lib().es_batch_steps(b._h, int(nsteps), float(t_end)))
 
 
+def es_batch_autotune(b):
+    """Time one step of each CTA shape from the current state (restored afterwards) and keep
+    the fastest; returns (threads per CTA, [probe ms for 128, 256, 512])."""
+    bt = ctypes.c_int()
+    ms = (ctypes.c_double * 3)()
+    b._call(lib().es_batch_autotune(b._h, ctypes.byref(bt), ms))
+    return bt.value, list(ms)
+
+
 def es_batch_get(b, JU, J, x, t=None):
     b._call(lib().es_batch_get(b._h, _ptr(JU, F64), _ptr(J, F64), _ptr(x, F64), _ptr(t, F64)))
 
@@ -419,3 +430,21 @@ def es_last_error(ctx):
     buf = ctypes.create_string_buffer(256)
     lib().es_last_error(ctx._h, buf, 256)
     return buf.value.decode()
+
+
+def setup_workload(w, precision="fp64", device="cuda", dissipation=True):
+    """Context and device state (JU, J, x) of a workload description (workloads.py): J from
+    the mesh, JU from the primitive fields, time 0."""
+    import torch
+    dev = torch.device(device)
+    ctx = es_create(make_params(w, precision=precision, dissipation=dissipation))
+    x = torch.tensor(np.ascontiguousarray(w["x"]), dtype=torch.float64, device=dev)
+    J = state_empty(ctx, w["x"].shape[1:], dev)
+    es_init_mesh(ctx, x, J)
+    rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
+    v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
+    p = torch.tensor(w["p"], dtype=torch.float64, device=dev)
+    JU = state_empty(ctx, (w["dim"] + 2,) + w["x"].shape[1:], dev)
+    es_prim_to_cons(ctx, rho, v, p, J, JU)
+    es_set_time(ctx, 0.0)
+    return ctx, JU, J, x

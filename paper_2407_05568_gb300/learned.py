@@ -150,19 +150,7 @@ def riemann_workload(n, seed, eps_cells, mu_max):
 
 def setup(w, precision="fp64", device="cuda"):
     """Context and device state (JU, J, x) of a workload description."""
-    torch = _torch()
-    dev = torch.device(device)
-    ctx = es.es_create(es.make_params(w, precision=precision))
-    x = torch.tensor(np.ascontiguousarray(w["x"]), dtype=torch.float64, device=dev)
-    J = es.state_empty(ctx, w["x"].shape[1:], dev)
-    es.es_init_mesh(ctx, x, J)
-    rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
-    v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
-    p = torch.tensor(w["p"], dtype=torch.float64, device=dev)
-    JU = es.state_empty(ctx, (w["dim"] + 2,) + w["x"].shape[1:], dev)
-    es.es_prim_to_cons(ctx, rho, v, p, J, JU)
-    es.es_set_time(ctx, 0.0)
-    return ctx, JU, J, x
+    return es.setup_workload(w, precision, device)
 
 
 def snapshots(seeds, n, steps, eps_cells, mu_max, every=1, precision="fp64", device="cuda"):

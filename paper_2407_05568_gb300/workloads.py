@@ -127,6 +127,17 @@ def riemann_1d(name="RP1", n=100, moving=True, t_end=None, cfl=0.4):
                           sweeps=10, eps=0.0))
 
 
+def vortex_density(X, Y, t=0.0, eps_v=5.0, period=10.0, center=5.0):
+    """Density of the isentropic vortex (gamma = 1.4) carried by the mean flow (1, 1) to time t:
+    the initial field at (x - t, y - t), wrapped into the periodic box."""
+    gam = 1.4
+    xb = (X - t - center + 0.5 * period) % period - 0.5 * period
+    yb = (Y - t - center + 0.5 * period) % period - 0.5 * period
+    r2 = xb * xb + yb * yb
+    T = 1.0 - (gam - 1.0) * eps_v ** 2 * np.exp(1.0 - r2) / (8.0 * gam * np.pi ** 2)
+    return T ** (1.0 / (gam - 1.0))
+
+
 def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0):
     """Ideal-gas (gamma = 1.4) isentropic vortex on [0,10]^2, periodic, mean flow (1, 1)
     (Shu 1998): dT = -(gamma-1) eps^2 e^(1-r^2) / (8 gamma pi^2),

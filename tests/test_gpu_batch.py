@@ -72,3 +72,34 @@ def test_batch_rejects_bad_lengths():
     from paper_2407_05568_gb300 import es
     with pytest.raises(es.EsError):
         es.es_batch_create(es.batch_params(wl.UNITS_A), [5, 100])
+
+
+def test_autotune_restores_state_and_shapes_agree():
+    """The autotuner leaves the state as it found it, and every CTA shape gives the same
+    step bit for bit (per-node arithmetic does not depend on the chunking; the reductions are maxima)."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    dev = torch.device("cuda:0")
+    batch = wl.shock_tube_batch(lengths=[37, 200, 257, 600, 1023, 64, 513, 130], seed=7)
+    res = {}
+    for tune in (False, True):
+        b = es.es_batch_create(es.batch_params(batch["gas"]), batch["lengths"])
+        rho, v, p = (torch.tensor(a, dtype=torch.float64, device=dev) for a in wl.batch_fields(batch))
+        es.es_batch_set_prim(b, rho, v, p)
+        es.es_batch_steps(b, 2, 1e30)
+        JU0 = torch.empty((3, b.ntot), dtype=torch.float64, device=dev)
+        J0 = torch.empty(b.ntot, dtype=torch.float64, device=dev)
+        x0 = torch.empty(b.ntot, dtype=torch.float64, device=dev)
+        es.es_batch_get(b, JU0, J0, x0)
+        if tune:
+            bt, ms = es.es_batch_autotune(b)
+            assert bt in (128, 256, 512) and all(m > 0 for m in ms)
+            JU1, J1, x1 = torch.empty_like(JU0), torch.empty_like(J0), torch.empty_like(x0)
+            es.es_batch_get(b, JU1, J1, x1)
+            assert torch.equal(JU0, JU1) and torch.equal(J0, J1) and torch.equal(x0, x1)
+        es.es_batch_steps(b, 3, 1e30)
+        assert es.es_batch_check(b) == 0
+        es.es_batch_get(b, JU0, J0, x0)
+        res[tune] = (JU0.cpu(), x0.cpu())
+    assert torch.equal(res[False][0], res[True][0]) and torch.equal(res[False][1], res[True][1])
