@@ -212,6 +212,7 @@ def measure_form(args, precision, dev, stream, world):
         es.es_set_time(ctx, 0.0)
 
     restart()
+    tile, tile_ms = es.es_autotune(ctx, JU, J, x)        # stage tile shape for this problem size
     done = 0
     for _ in range(args.warmup):
         es.es_steps(ctx, JU, J, x, 1, w["t_end"])
@@ -248,7 +249,8 @@ def measure_form(args, precision, dev, stream, world):
         ms = float(t.item())
     if es.es_check(ctx):
         raise RuntimeError(es.es_last_error(ctx))
-    roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision)
+    roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile)
+    roof["autotune_ms_per_shape"] = tile_ms
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hJU, hJ, hx = (pin(np.ascontiguousarray(t.cpu().numpy())) for t in (JU0, J0, x0))
@@ -488,7 +490,10 @@ def pin(a):
 FLOPS_PER_NODE_STAGE_2D = None
 
 
-def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision):
+TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16)}, "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8)}}
+
+
+def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
     """Average duration of the stage kernel (stage 2 form) over 20 launches on the bench stream."""
     import torch
     S1 = torch.empty_like(JU)
@@ -515,7 +520,9 @@ def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision):
     flops = perfmodel.stage_flops(dim=2, nodes=nodes, precision=precision)
     peak = perfmodel.fp64_peak_tflops(peaks) if precision == "fp64" else perfmodel.fp32_peak_tflops(peaks)
     achieved = flops / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": "stage_kernel_fp64<2,32,8>" if precision == "fp64" else "stage_kernel_mixed",
+    bx, by = TILES[precision][tile]
+    kname = ("stage_kernel_fp64" if precision == "fp64" else "stage_kernel_mixed") + f"<2,{bx},{by}>"
+    return {"bound": "alu", "kernel": kname, "tile": f"{bx}x{by}",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "launch_ms": ms, "flops_per_launch": flops,
             "peak_source": "nominal FP64 rate of GB300 from the recipe (1.25 TFLOP/s); not in MEASURED_PEAKS.json"

@@ -88,7 +88,12 @@ typedef struct es_params {
     int    jacobi_sweeps;   /* mu: maximum Jacobi sweeps (Sec. 4) */
     double jacobi_eps;      /* stop when max |x^[nu+1] - x^[nu]| < eps; 0 = exactly mu sweeps */
     int    precision;       /* ES_PREC_* */
+    int    tile;            /* 2D stage tile shape: 0 = chosen by es_autotune (run by the first es_steps
+                               if not called before); k = 1 .. ES_NTILES: shape k of the precision's
+                               table (FP64: 32x8, 25x11, 16x16 nodes; mixed: 32x8, 25x6, 20x8) */
 } es_params;
+
+#define ES_NTILES 3
 
 typedef struct es_ctx es_ctx;
 
@@ -158,6 +163,15 @@ int es_run_host(es_ctx* ctx, void* JU_host, void* J_host, double* x_host, int ns
  * clears it.  es_last_error writes a message (with the first failing node). */
 int es_check(es_ctx* ctx);
 int es_last_error(es_ctx* ctx, char* buf, int len);
+
+/* Stage-kernel autotuner (2D): times one launch of the operator (es_rhs into the
+ * context's scratch) for every tile shape on the caller's state and mesh and keeps
+ * the fastest for all later launches.  The shapes change only how nodes are
+ * grouped into CTAs (how many tiles make a wave on the SMs, how much halo each
+ * tile recomputes), never a result: every shape gives the same bits.  Writes the
+ * chosen shape (1 .. ES_NTILES) and, if ms_host is non-null, the ES_NTILES probe
+ * times in ms.  1D contexts have one shape (returns 1).  Synchronises. */
+int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host);
 
 /* Number of kernel launches the library has issued (graph launches count
  * their kernels), for launch accounting. */

@@ -27,6 +27,8 @@ struct es_ctx {
     int nc;
     int grid1d;
     int mixed;                        // ES_PREC_MIXED: float state
+    int tile;                         // 2D stage tile shape (0-based); tuned: chosen by es_autotune or fixed
+    int tuned;
     size_t esz;                       // bytes per state element (8 or 4)
     // scratch (device)
     void *S1, *S1J, *S2, *S2J;        // RK stage states in the state precision
@@ -91,6 +93,7 @@ StageParams stage_params(es_ctx* c) {
     P.weno = c->weno;
     P.diss = c->p.dissipation;
     P.status = &c->dev->status;
+    P.tile = c->tile;
     return P;
 }
 
@@ -286,6 +289,7 @@ int check_params(const es_params* p) {
     if (!(p->sign_tol >= 0.0) || p->sign_tol > 1e-2) return 0;
     if (!(p->cfl > 0.0) && !(p->dt_fixed > 0.0)) return 0;
     if (p->precision != ES_PREC_FP64 && p->precision != ES_PREC_MIXED) return 0;
+    if (p->tile < 0 || p->tile > ES_NTILES) return 0;
     if (p->precision == ES_PREC_MIXED) {
         // the FP32 displacement is periodic only when the period is n dxi
         const int nn[2] = {p->n1, p->n2};
@@ -352,6 +356,8 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->N = size_t(c->g.n1) * c->g.n2;
     c->nc = p->dim + 2;
     c->mixed = p->precision == ES_PREC_MIXED;
+    c->tile = p->tile > 0 ? p->tile - 1 : 0;
+    c->tuned = p->tile > 0 || p->dim == 1;
     c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -634,6 +640,10 @@ int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) 
     CK(cudaMemcpyAsync(&c->dev->t_end, &c->hpin->t_end, sizeof(double), cudaMemcpyHostToDevice, c->stream),
        "copy t_end");
     CK(cudaStreamSynchronize(c->stream), "sync");
+    if (!c->tuned) {
+        int rc = es_autotune(c, JU, J, x, nullptr, nullptr);
+        if (rc) return rc;
+    }
     const void* key[3] = {JU, J, x};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
         if (c->gexec) {
@@ -682,6 +692,65 @@ int es_run_host(es_ctx* c, void* JU_host, void* J_host, double* x_host, int nste
     CK(cudaMemcpyAsync(J_host, c->hJ, SB, cudaMemcpyDeviceToHost, c->stream), "d2h");
     CK(cudaMemcpyAsync(x_host, c->hx, XB, cudaMemcpyDeviceToHost, c->stream), "d2h");
     CK(cudaStreamSynchronize(c->stream), "sync");
+    return ES_OK;
+}
+
+int es_autotune(es_ctx* c, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host) {
+    if (!c || !JU || !J || !x) return fail(c, ES_ERR_ARG, "null argument");
+    if (c->p.dim == 1) {
+        c->tuned = 1;
+        if (tile_host) *tile_host = 1;
+        return ES_OK;
+    }
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, e, "event");
+    }
+    int best = 0;
+    float best_ms = 3.0e38f;
+    const int saved = c->tile;
+    for (int k = 0; k < ES_NTILES && e == cudaSuccess; ++k) {
+        c->tile = k;
+        StageParams P = stage_params(c);
+        P.mode = 1;
+        P.dt_host = 1.0;
+        P.xn = x;
+        P.xdot = nullptr;
+        enqueue_mesh_f32(c, P, x, nullptr);
+        set_state(c, P, JU, J, JU, J, c->S1, c->S1J);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // the first launch loads the kernel
+            e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess) e = launch_stage(c, P);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;
+        }
+        if (ms_host) ms_host[k] = ms / 2;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        c->tile = saved;
+        return cuda_fail(c, e, "autotune");
+    }
+    c->tile = best;
+    c->tuned = 1;
+    if (c->gexec) {                        // the step graph holds the old shape
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (tile_host) *tile_host = best + 1;
     return ES_OK;
 }
 

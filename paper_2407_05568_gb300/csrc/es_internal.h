@@ -31,6 +31,7 @@ struct StageParams {
     double* JUo;
     double* Jo;
     int mode;                     // 0: RK combination; 1: write the right-hand sides
+    int tile;                     // 2D tile shape: index into the precision's shape table
     DevStatus* status;
     // mixed form: float state and float mesh displacement / velocity
     const float* fJUn;
@@ -80,6 +81,10 @@ inline void set_float_params(StageParams& P) {
 
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s);
 cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s);
+// 2D tile shapes of the stage kernels (nodes BX x BY, NT threads >= the faces of either direction);
+// the autotuner times each on the caller's problem
+constexpr int STAGE_NTILES = 3;
+void stage_tile_shape(bool mixed, int k, int* bx, int* by, int* nt);
 // set the kernels' shared-memory attributes (call outside any stream capture)
 cudaError_t stage_prepare_fp64(int dim);
 cudaError_t stage_prepare_mixed(int dim);

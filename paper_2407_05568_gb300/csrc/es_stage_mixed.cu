@@ -61,13 +61,23 @@ cudaError_t launch_tile_f(const StageParams& P, cudaStream_t s) {
 
 }  // namespace
 
+// 2D shapes: 32 x 8 nodes with 288 threads, 25 x 6 with 192 (175 faces; 8 x 34 = 272 tiles fill
+// 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces)
 cudaError_t stage_prepare_mixed(int dim) {
-    return dim == 1 ? prepare_tile_f<1, 254, 1, 256>() : prepare_tile_f<2, 32, 8, 288>();
+    if (dim == 1) return prepare_tile_f<1, 254, 1, 256>();
+    cudaError_t e = prepare_tile_f<2, 32, 8, 288>();
+    if (e == cudaSuccess) e = prepare_tile_f<2, 25, 6, 192>();
+    if (e == cudaSuccess) e = prepare_tile_f<2, 20, 8, 192>();
+    return e;
 }
 
 cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s) {
     if (P.dim == 1) return launch_tile_f<1, 254, 1, 256>(P, s);
-    return launch_tile_f<2, 32, 8, 288>(P, s);
+    switch (P.tile) {
+        case 1: return launch_tile_f<2, 25, 6, 192>(P, s);
+        case 2: return launch_tile_f<2, 20, 8, 192>(P, s);
+        default: return launch_tile_f<2, 32, 8, 288>(P, s);
+    }
 }
 
 }  // namespace es

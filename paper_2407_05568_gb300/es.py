@@ -31,7 +31,7 @@ class EsParams(ctypes.Structure):
         ("dissipation", ctypes.c_int), ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
         ("moving", ctypes.c_int), ("monitor", ctypes.c_int), ("kappa", ctypes.c_int),
         ("alpha", ctypes.c_double * 4), ("filter_passes", ctypes.c_int), ("jacobi_sweeps", ctypes.c_int),
-        ("jacobi_eps", ctypes.c_double), ("precision", ctypes.c_int),
+        ("jacobi_eps", ctypes.c_double), ("precision", ctypes.c_int), ("tile", ctypes.c_int),
     ]
 
 
@@ -67,6 +67,8 @@ def lib():
         L.es_run_host.argtypes = [vp, vp, vp, vp, i, d]
         L.es_check.argtypes = [vp]
         L.es_last_error.argtypes = [vp, ctypes.c_char_p, i]
+        L.es_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        L.es_autotune.restype = ctypes.c_int
         L.es_launch_count.argtypes = [vp]
         L.es_launch_count.restype = ctypes.c_int64
         L.es_rk3_step_static.argtypes = [ctypes.POINTER(EsParams), d, vp, vp, vp, vp, vp]
@@ -111,7 +113,7 @@ def lib():
     return _lib
 
 
-def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=None):
+def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=None, tile=0):
     """es_params from a workload description (see workloads.py)."""
     p = EsParams()
     g = w["gas"]
@@ -143,6 +145,7 @@ def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e
     p.jacobi_sweeps = m.get("sweeps", 5)
     p.jacobi_eps = m.get("eps", 0.0)
     p.precision = ES_PREC[precision]
+    p.tile = int(tile)
     return p
 
 
@@ -349,6 +352,15 @@ def es_run_host(ctx, JU, J, x, nsteps, t_end):
             raise ValueError("expected C-contiguous arrays of the state precision (x: float64)")
     ptrs = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
     ctx._call(lib().es_run_host(ctx._h, *ptrs, int(nsteps), float(t_end)))
+
+
+def es_autotune(ctx, JU, J, x):
+    """Time the stage kernel's tile shapes on this state; returns (chosen shape 1..3, [ms per shape])."""
+    S = ctx.state_dtype
+    k = ctypes.c_int()
+    ms = (ctypes.c_double * 3)()
+    ctx._call(lib().es_autotune(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(k), ms))
+    return k.value, list(ms)
 
 
 def es_check(ctx):

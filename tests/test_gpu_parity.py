@@ -274,3 +274,30 @@ def test_bad_parameters_rejected():
     p.n1 = 4
     with pytest.raises(es.EsError):
         es.es_create(p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["riemann2d_ragged", "wavy_rough"])
+def test_tile_shapes_agree_bitwise(case, precision):
+    """Every 2D tile shape gives the same operator bit for bit (shapes only regroup nodes into
+    CTAs), and the autotuner picks one of them."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = CASES[case]()
+    xd = _xdot(w)
+    xdt = torch.tensor(np.ascontiguousarray(xd), dtype=torch.float64, device="cuda")
+    outs = []
+    for tile in (1, 2, 3):
+        from sides import gpu_setup as _gs
+        p_ctx, JU, J, xt = _gs(w, precision=precision)
+        ctx = es.es_create(es.make_params(w, precision=precision, tile=tile))
+        dU = torch.empty_like(JU)
+        dJ = torch.empty_like(J)
+        es.es_rhs(ctx, JU, J, xt, xdt, dU, dJ)
+        assert es.es_check(ctx) == 0
+        outs.append((dU.clone(), dJ.clone()))
+    for dU, dJ in outs[1:]:
+        assert torch.equal(dU, outs[0][0]) and torch.equal(dJ, outs[0][1])
+    k, ms = es.es_autotune(p_ctx, JU, J, xt)
+    assert k in (1, 2, 3) and all(m > 0 for m in ms)
