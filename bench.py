@@ -491,6 +491,10 @@ FLOPS_PER_NODE_STAGE_2D = None
 
 
 TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16)}, "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8)}}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
+# kernel (profiles/stage_fp64_riemann2d_200.md, profiles/stage_mixed_riemann2d_200.md); other
+# shapes and sizes were not captured
+TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3084544 + 0, "stage_kernel_mixed<2,20,8>": 2341888 + 0}
 
 
 def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
@@ -524,7 +528,8 @@ def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
     kname = ("stage_kernel_fp64" if precision == "fp64" else "stage_kernel_mixed") + f"<2,{bx},{by}>"
     return {"bound": "alu", "kernel": kname, "tile": f"{bx}x{by}",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "launch_ms": ms, "flops_per_launch": flops,
+            "traffic": TRAFFIC_200.get(kname) if nodes == 200 * 200 else None, "launch_ms": ms,
+            "flops_per_launch": flops,
             "peak_source": "nominal FP64 rate of GB300 from the recipe (1.25 TFLOP/s); not in MEASURED_PEAKS.json"
             if precision == "fp64" else "FP32 rate from SM count x 128 lanes x 2 x max clock"}
 
