@@ -56,6 +56,17 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, device):
+    """The largest of the ranks' values (the slowest rank's time); the value itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -242,11 +253,7 @@ def measure_form(args, precision, dev, stream, world):
     launches = ctx.launches - launches0
     if world > 1:
         dist.barrier()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, dev)
     if es.es_check(ctx):
         raise RuntimeError(es.es_last_error(ctx))
     roof = stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile)
@@ -492,8 +499,7 @@ FLOPS_PER_NODE_STAGE_2D = None
 
 TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16)}, "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
-# kernel (profiles/stage_fp64_riemann2d_200.md, profiles/stage_mixed_riemann2d_200.md); other
-# shapes and sizes were not captured
+# kernel as it is now; other shapes and sizes were not captured
 TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3084544 + 0, "stage_kernel_mixed<2,20,8>": 2341888 + 0}
 
 
