@@ -332,6 +332,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->gas.R = p->R;
     c->gas.cv = p->cv;
     c->gas.delta = p->R / p->cv;
+    gas_reciprocals(c->gas);
     const double g1 = p->weno_gamma[0], g2 = p->weno_gamma[1], g3 = p->weno_gamma[2];
     const double gs = g1 + g2 + g3;
     c->weno.g1 = g1 / gs;

@@ -450,6 +450,7 @@ int es_batch_create(es_batch** out, const es_params* p, int nprob, const int* le
     P.gas.R = p->R;
     P.gas.cv = p->cv;
     P.gas.delta = p->R / p->cv;
+    gas_reciprocals(P.gas);
     const double g1 = p->weno_gamma[0], g2 = p->weno_gamma[1], g3 = p->weno_gamma[2], gs = g1 + g2 + g3;
     P.weno.g1 = g1 / gs;
     P.weno.g2 = g2 / gs;
@@ -494,6 +495,7 @@ int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const dou
     Gd.R = b->p.R;
     Gd.cv = b->p.cv;
     Gd.delta = b->p.R / b->p.cv;
+    gas_reciprocals(Gd);
     k_batch_set<<<b->B.nprob, 256, 0, b->stream>>>(b->B, Gd, rho, v, pr);
     BCK(cudaGetLastError(), "k_batch_set");
     return ES_OK;

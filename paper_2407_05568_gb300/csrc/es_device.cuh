@@ -14,7 +14,13 @@ namespace es {
 // ----------------------------------------------------------------- constants
 struct Gas {
     double a, b, R, cv, delta;   // delta = R / cv
+    double iR, idelta;           // 1/R, 1/delta (set with the others)
 };
+
+inline void gas_reciprocals(Gas& g) {
+    g.iR = 1.0 / g.R;
+    g.idelta = 1.0 / g.delta;
+}
 
 // Sixth-order EC combination weights alpha_{3,m}, m = 1, 2, 3 (Sec. 3.1:
 // sum m alpha = 1, sum m^3 alpha = sum m^5 alpha = 0).
@@ -75,13 +81,11 @@ __device__ __forceinline__ double mr_weno5(double wm2, double wm1, double w0, do
     const double c1 = (34.0 * o1 - 5.0 * o2) * (1.0 / 24.0);
     const double c4 = (e2 - 4.0 * e1 + 3.0 * e0) * (1.0 / 12.0);
     const double c2 = (12.0 * e1 - 11.0 * e0 - e2) * 0.125;
-    // int_{-1/2}^{1/2} of (q')^2 + (q'')^2 + (q''')^2 + (q'''')^2, using
-    // int x^2 = 1/12, int x^4 = 1/80, int x^6 = 1/448
-    const double b3 = c1 * c1 + (4.0 * c2 * c2 + 6.0 * c1 * c3) * (1.0 / 12.0)
-                    + (9.0 * c3 * c3 + 16.0 * c2 * c4) * (1.0 / 80.0) + 16.0 * c4 * c4 * (1.0 / 448.0)
-                    + 4.0 * c2 * c2 + (36.0 * c3 * c3 + 48.0 * c2 * c4) * (1.0 / 12.0) + 144.0 * c4 * c4 * (1.0 / 80.0)
-                    + 36.0 * c3 * c3 + 48.0 * c4 * c4
-                    + 576.0 * c4 * c4;
+    // int_{-1/2}^{1/2} of (q')^2 + (q'')^2 + (q''')^2 + (q'''')^2 (int x^2 = 1/12, x^4 = 1/80,
+    // x^6 = 1/448), collected by monomial: c1^2 + c1 c3/2 + 13/3 c2^2 + 3129/80 c3^2
+    // + 21/5 c2 c4 + 87617/140 c4^2
+    const double b3 = c1 * (c1 + 0.5 * c3) + c2 * ((13.0 / 3.0) * c2 + 4.2 * c4) + (3129.0 / 80.0) * c3 * c3
+                    + (87617.0 / 140.0) * c4 * c4;
     const double t = 0.5 * (fabs(b3 - b1) + fabs(b3 - b2));
     const double tau = t * t;
     // w~_l = g_l (1 + tau/(beta_l + eps)); scaled by (d1 d2 d3) to need one division

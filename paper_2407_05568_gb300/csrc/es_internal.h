@@ -43,7 +43,7 @@ struct StageParams {
     const float* fdisp;           // x - (x_00 + i dxi_1, y_00 + j dxi_2), [dim][n2][n1]
     const float* fxdot;           // mesh velocity, [dim][n2][n1] (nullable)
     // float copies of the constants (GB300 converts double -> float at FP64 speed)
-    float fgas[7];                // a, b, R, cv, delta, R b, 1/cv
+    float fgas[9];                // a, b, R, cv, delta, R b, 1/cv, 1/R, 1/delta
     float fweno[8];               // g1, g2, g3, g12, ig22, ig3, eps, sign_tol
     float finv_dxi[2];
     float fca, fcb, fca_lo, fcb_lo, fcst;
@@ -61,6 +61,8 @@ inline void set_float_params(StageParams& P) {
     P.fgas[4] = float(P.gas.delta);
     P.fgas[5] = float(P.gas.R * P.gas.b);
     P.fgas[6] = float(1.0 / P.gas.cv);
+    P.fgas[7] = float(1.0 / P.gas.R);
+    P.fgas[8] = float(P.gas.cv / P.gas.R);
     const double w[8] = {P.weno.g1, P.weno.g2, P.weno.g3, P.weno.g12, P.weno.ig22, P.weno.ig3, P.weno.eps,
                          P.weno.sign_tol};
     for (int k = 0; k < 8; ++k) P.fweno[k] = float(w[k]);

@@ -35,7 +35,7 @@ struct TileF {
 };
 
 struct GasF {
-    float a, b, R, cv, delta, Rb, icv;
+    float a, b, R, cv, delta, Rb, icv, iR, idelta;
 };
 
 struct WenoF {
@@ -116,10 +116,8 @@ __device__ __forceinline__ float mr_weno5_f(float wm2, float wm1, float w0, floa
     const float c1 = (34.0f * o1 - 5.0f * o2) * (1.0f / 24.0f);
     const float c4 = (e2 - 4.0f * e1 + 3.0f * e0) * (1.0f / 12.0f);
     const float c2 = (12.0f * e1 - 11.0f * e0 - e2) * 0.125f;
-    const float b3 = c1 * c1 + (4.0f * c2 * c2 + 6.0f * c1 * c3) * (1.0f / 12.0f)
-                   + (9.0f * c3 * c3 + 16.0f * c2 * c4) * (1.0f / 80.0f) + 16.0f * c4 * c4 * (1.0f / 448.0f)
-                   + 4.0f * c2 * c2 + (36.0f * c3 * c3 + 48.0f * c2 * c4) * (1.0f / 12.0f)
-                   + 144.0f * c4 * c4 * (1.0f / 80.0f) + 36.0f * c3 * c3 + 48.0f * c4 * c4 + 576.0f * c4 * c4;
+    const float b3 = c1 * (c1 + 0.5f * c3) + c2 * ((13.0f / 3.0f) * c2 + 4.2f * c4) + (3129.0f / 80.0f) * c3 * c3
+                   + (87617.0f / 140.0f) * c4 * c4;
     const float t = 0.5f * (fabsf(b3 - b1) + fabsf(b3 - b2));
     const float tau = t * t;
     const float w1 = c.g1 * (1.0f + tau / (b1 + c.eps));
@@ -218,7 +216,7 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
     const float ilrp = inv_log_mean_f(S[G_RP * NB + l], S[G_RP * NB + r]);
     const float p = rho * ilrp;
     const float om = 1.0f - G.b * rho;
-    const float T = (p + G.a * rho * rho) * om * ilr / G.R;
+    const float T = (p + G.a * rho * rho) * om * ilr * G.iR;
     const float iom = 1.0f / om;
     const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
     const float dcrit = G.R * T - 2.0f * G.a * rho * om * om;
@@ -241,7 +239,7 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
     }
     const float E = rho * (G.cv * T - G.a * rho) + 0.5f * rho * (vn * vn + vt * vt);
     const float H = (E + p) * ilr;
-    const float mid = H - c2 * om / G.delta;
+    const float mid = H - c2 * om * G.idelta;
     const float ic2 = 1.0f / c2;
     const float sA = sqrtf(0.5f * rho * T * ic2);
     const float sE = sqrtf(G.R * G.delta * rho * T * T * ic2 / dcrit);
@@ -602,6 +600,8 @@ __device__ __forceinline__ GasF gas_f(const StageParams& P) {
     G.delta = P.fgas[4];
     G.Rb = P.fgas[5];
     G.icv = P.fgas[6];
+    G.iR = P.fgas[7];
+    G.idelta = P.fgas[8];
     return G;
 }
 

@@ -117,7 +117,7 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
     const double ilrp = inv_log_mean(S[F_RP * NB + l], S[F_RP * NB + r], S[F_LNRP * NB + l], S[F_LNRP * NB + r]);
     const double p = rho * ilrp;
     const double om = 1.0 - G.b * rho;
-    const double T = (p + G.a * rho * rho) * om * ilr / G.R;
+    const double T = (p + G.a * rho * rho) * om * ilr * G.iR;
     const double iom = 1.0 / om;
     const double c2 = (1.0 + G.delta) * G.R * T * iom * iom - 2.0 * G.a * rho;
     const double dcrit = G.R * T - 2.0 * G.a * rho * om * om;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
     }
     const double E = rho * (G.cv * T - G.a * rho) + 0.5 * rho * (vn * vn + vt * vt);
     const double H = (E + p) * ilr;
-    const double mid = H - c2 * om / G.delta;
+    const double mid = H - c2 * om * G.idelta;
     const double ic2 = 1.0 / c2;
     const double sA = sqrt(0.5 * rho * T * ic2);
     const double sE = sqrt(G.R * G.delta * rho * T * T * ic2 / dcrit);

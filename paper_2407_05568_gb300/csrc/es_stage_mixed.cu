@@ -35,7 +35,7 @@ namespace {
 using namespace mixed;
 
 template <int DIM, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT, 2) stage_kernel_mixed(StageParams P) {
+__global__ void __launch_bounds__(NT, NT <= 192 ? 3 : 2) stage_kernel_mixed(StageParams P) {
     extern __shared__ float smemf[];
     const int ntx = (P.n1 + BX - 1) / BX;
     const int i0 = (blockIdx.x % ntx) * BX;

@@ -106,6 +106,7 @@ extern "C" int es_rk3_step_static(const es_params* p, double dt, double* JU, dou
     P.gas.R = p->R;
     P.gas.cv = p->cv;
     P.gas.delta = p->R / p->cv;
+    gas_reciprocals(P.gas);
     const double g1 = p->weno_gamma[0], g2 = p->weno_gamma[1], g3 = p->weno_gamma[2];
     const double gs = g1 + g2 + g3;
     P.weno.g1 = g1 / gs;
