@@ -9,6 +9,7 @@
 
 #include "es_aux.h"
 #include "es_internal.h"
+#include "es_mesh_f32.h"
 #include "es_vdw.h"
 
 using namespace es;
@@ -226,6 +227,47 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
     return ES_OK;
 }
 
+// The mixed form runs the time step and the mesh redistribution on the FP32 displacement
+// (es_mesh_f32.cu) unless a warm-start network is registered (its features and guarded
+// sweeps are the FP64 kernels).
+bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
+
+// Sec. 4 on the FP32 pipe; c->fdisp must hold the displacement of x^n.  Writes c->fxd and xdot.
+int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot) {
+    const int B = 256, G = c->grid1d;
+    cudaStream_t s = c->s_enq;
+    const GasF32 gf = gas_f32(c->gas);
+    float* rho = (float*)c->rhoF;
+    float* Gf = (float*)c->GF;
+    float* t0 = (float*)c->t0;
+    float* t1 = (float*)c->t1;
+    float* t2 = (float*)c->t2;
+    float* om = (float*)c->om0;
+    float* other = (float*)c->om1;
+    float* da = (float*)c->xa;
+    float* db = (float*)c->xb;
+    k_mon_fields_f<<<G, B, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, rho, Gf);
+    k_mon_terms_f<<<G, B, 0, s>>>(c->g, c->mon, rho, Gf, t0, t1, t2, c->dev);
+    k_mon_omega_f<<<G, B, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, om);
+    count(c, 3);
+    for (int k = 0; k < c->p.filter_passes; ++k) {
+        k_filter_f<<<G, B, 0, s>>>(c->g, om, other);
+        count(c);
+        float* tmp = om; om = other; other = tmp;
+    }
+    const int check = c->p.jacobi_eps > 0.0;
+    for (int k = 0; k < c->p.jacobi_sweeps; ++k) {
+        k_jacobi_f<<<G, B, 0, s>>>(c->g, om, c->fdisp, da, db, k, c->dev, check, c->p.jacobi_eps);
+        count(c);
+    }
+    k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
+    k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot);
+    count(c, 2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels (FP32)");
+    return ES_OK;
+}
+
 void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x) {
     launch_cfl(c->g, c->gas, JU, J, x, c->dev, c->mixed, c->grid1d, c->s_enq);
     count(c);
@@ -236,14 +278,21 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     cudaStream_t s = c->s_enq;
     k_reset<<<1, 32, 0, s>>>(c->dev);
     count(c);
-    enqueue_cfl(c, JU, J, x);
+    const bool f32 = mesh_on_fp32(c);
+    if (f32) {
+        k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd);
+        k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, c->dev);
+        count(c, 2);
+    } else {
+        enqueue_cfl(c, JU, J, x);
+    }
     k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
     count(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
     if (c->p.moving) {
-        int rc = enqueue_mesh(c, JU, J, x, c->xdot);
+        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot) : enqueue_mesh(c, JU, J, x, c->xdot);
         if (rc) return rc;
         xdot = c->xdot;
     }
@@ -251,7 +300,12 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     P.dt_dev = &c->dev->dt;
     P.xn = x;
     P.xdot = xdot;
-    enqueue_mesh_f32(c, P, x, xdot);
+    if (f32) {
+        P.fdisp = c->fdisp;
+        P.fxdot = xdot ? c->fxd : nullptr;
+    } else {
+        enqueue_mesh_f32(c, P, x, xdot);
+    }
     const void* srcU[3] = {JU, c->S1, c->S2};
     const void* srcJ[3] = {J, c->S1J, c->S2J};
     void* dstU[3] = {c->S1, c->S2, JU};
@@ -477,7 +531,14 @@ int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, double*
     if (!c || !JU || !J || !x || !dt_host) return fail(c, ES_ERR_ARG, "null argument");
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
-    enqueue_cfl(c, JU, J, x);
+    if (mesh_on_fp32(c)) {
+        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, nullptr, c->fdisp, c->fxd);
+        k_cfl_f<<<c->grid1d, 256, 0, c->stream>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J,
+                                                   c->fdisp, c->dev);
+        count(c, 2);
+    } else {
+        enqueue_cfl(c, JU, J, x);
+    }
     CK(cudaGetLastError(), "k_cfl");
     CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -493,7 +554,14 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     k_set_dt<<<1, 32, 0, c->stream>>>(c->dev, dt);
     count(c, 2);
-    int rc = enqueue_mesh(c, JU, J, xn, xdot);
+    int rc;
+    if (mesh_on_fp32(c)) {
+        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
+        count(c);
+        rc = enqueue_mesh32(c, JU, J, xdot);
+    } else {
+        rc = enqueue_mesh(c, JU, J, xn, xdot);
+    }
     if (rc) return rc;
     if (sweeps_host || gamma_host) {
         CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");

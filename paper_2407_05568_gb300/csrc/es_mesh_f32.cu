@@ -1,0 +1,341 @@
+// es_mesh_f32.cu -- the time step and the mesh redistribution of the mixed form on
+// the FP32 pipe.
+//
+// The mixed form keeps the mesh as an FP32 displacement d = x - (x_00 + i dxi_1,
+// y_00 + j dxi_2) from the Cartesian mesh (the stage kernels read it).  Here the
+// CFL time step (eq. cfl), the monitor with G (eq. van der Waalsmonitor, or the
+// smooth-test monitor), the low-pass filter, the Jacobi sweeps, the limiter
+// Delta_gamma and the mesh velocity (Sec. 4) run on d in FP32: the Cartesian part
+// of x is linear in the node index, so a neighbour's coordinate is its
+// displacement plus +-dxi_k along its own direction, and its 6th-order difference
+// is exactly dxi_k e_k.  On GB300 FP64 issues at 1/64 of the FP32 rate, and
+// these kernels were a third of the mixed step at 200 x 200 in FP64.
+#include <cuda_runtime.h>
+
+#include "es_aux.h"
+#include "es_device.cuh"
+#include "es_mesh_f32.h"
+
+namespace es {
+
+namespace {
+
+__device__ __forceinline__ float block_max_f32(float v) {
+    __shared__ float sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0f;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ float block_min_f32(float v) {
+    __shared__ float sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 3.0e38f;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    return v;
+}
+
+// displacement at a node that may be a ghost: periodic wrap (d is periodic), outflow odd
+// reflection d_{-m} = 2 d_0 - d_m (the reflection of x, whose Cartesian part cancels)
+__device__ __forceinline__ float disp_at(const GridParams& g, const float* d, int gi, int gj, int comp) {
+    const size_t N = size_t(g.n1) * g.n2;
+    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))
+        return d[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
+    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0]);
+    GhostTerms tj;
+    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1]);
+    else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
+    float acc = 0.0f;
+    for (int a = 0; a < ti.nterm; ++a)
+        for (int c = 0; c < tj.nterm; ++c)
+            acc += float(ti.w[a] * tj.w[c]) * d[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
+    return acc;
+}
+
+__device__ __forceinline__ float field_at_f(const GridParams& g, const float* f, int i, int j) {
+    const int si = state_index(i, g.n1, g.bc[0]);
+    const int sj = g.dim == 2 ? state_index(j, g.n2, g.bc[1]) : 0;
+    return f[sj * g.n1 + si];
+}
+
+// d x_comp / d xi_k at (i, j) from the 6th-order central difference of the displacement
+__device__ __forceinline__ float dx_dxi(const GridParams& g, const float* d, int i, int j, int comp, int k,
+                                        float inv_dxi) {
+    float s = 0.0f;
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        const float h = 0.5f * float(ec_alpha(m));
+        if (k == 0) s += h * (disp_at(g, d, i + m, j, comp) - disp_at(g, d, i - m, j, comp));
+        else s += h * (disp_at(g, d, i, j + m, comp) - disp_at(g, d, i, j - m, comp));
+    }
+    return (comp == k ? 1.0f : 0.0f) + s * inv_dxi;
+}
+
+// value of a mixed-form state entry: hi plane + lo plane
+__device__ __forceinline__ float ld2(const float* a, size_t plane, size_t i) { return a[i] + a[plane + i]; }
+
+__device__ __forceinline__ bool fixed_node_f(const GridParams& g, int i, int j) {
+    bool f = g.bc[0] == ES_BC_OUTFLOW && (i == 0 || i == g.n1 - 1);
+    if (g.dim == 2) f = f || (g.bc[1] == ES_BC_OUTFLOW && (j == 0 || j == g.n2 - 1));
+    return f;
+}
+
+}  // namespace
+
+// eq. cfl on the FP32 pipe: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), zero mesh velocity
+__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    const size_t P = size_t(g.dim + 2) * N;
+    const float idx1 = float(g.inv_dxi[0]), idx2 = float(g.inv_dxi[1]);
+    float m = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        const float iJ = 1.0f / ld2(J, N, id);
+        const float rho = ld2(JU, P, id) * iJ;
+        const float irho = 1.0f / rho;
+        const float v1 = ld2(JU, P, N + id) * iJ * irho;
+        const float v2 = g.dim == 2 ? ld2(JU, P, 2 * N + id) * iJ * irho : 0.0f;
+        const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
+        const float T = (E * irho - 0.5f * (v1 * v1 + v2 * v2) + G.a * rho) * G.icv;
+        const float iom = 1.0f / (1.0f - G.b * rho);
+        const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
+        const float c = sqrtf(fmaxf(c2, 0.0f));
+        float tot;
+        if (g.dim == 1) {
+            tot = (fabsf(v1) + c) * iJ * idx1;
+        } else {
+            const float x1 = dx_dxi(g, disp, i, j, 0, 0, idx1), x2 = dx_dxi(g, disp, i, j, 0, 1, idx2);
+            const float y1 = dx_dxi(g, disp, i, j, 1, 0, idx1), y2 = dx_dxi(g, disp, i, j, 1, 1, idx2);
+            const float a1 = y2, b1 = -x2;        // J dxi_1/dx
+            const float a2 = -y1, b2 = x1;        // J dxi_2/dx
+            tot = (fabsf(a1 * v1 + b1 * v2) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
+                  (fabsf(a2 * v1 + b2 * v2) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
+        }
+        if (!(c2 > 0.0f)) tot = 3.0e38f;
+        m = fmaxf(m, tot);
+    }
+    m = block_max_f32(m);
+    if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_CFL], double(m));
+}
+
+// density and G = nu^3 p_nunu|_s / (2 c^2) at the nodes, then the raw monitor terms need
+// the neighbours: two kernels (as in the FP64 path)
+__global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF) {
+    const int N = g.n1 * g.n2;
+    const size_t P = size_t(g.dim + 2) * N;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const float iJ = 1.0f / ld2(J, N, id);
+        const float rho = ld2(JU, P, id) * iJ;
+        const float irho = 1.0f / rho;
+        float ke = 0.0f;
+        for (int k = 0; k < g.dim; ++k) {
+            const float v = ld2(JU, P, (1 + k) * N + id) * iJ * irho;
+            ke += v * v;
+        }
+        const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
+        const float T = (E * irho - 0.5f * ke + G.a * rho) * G.icv;
+        const float iom = 1.0f / (1.0f - G.b * rho);
+        const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
+        const float pnn3 = (1.0f + G.delta) * (2.0f + G.delta) * G.R * T * iom * iom * iom - 6.0f * G.a * rho;
+        rhoF[id] = rho;
+        GF[id] = pnn3 / (2.0f * c2);
+    }
+}
+
+__global__ void k_mon_terms_f(GridParams g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
+                              float* t2, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
+        for (int k = 0; k < g.dim; ++k) {
+            const int di = k == 0, dj = k == 1;
+            const float h = float(g.inv_dxi[k]);
+            const float rp = field_at_f(g, rhoF, i + di, j + dj), rm = field_at_f(g, rhoF, i - di, j - dj);
+            const float Gp = field_at_f(g, GF, i + di, j + dj), Gm = field_at_f(g, GF, i - di, j - dj);
+            const float r0 = rhoF[id], G0 = GF[id];
+            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
+            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
+            gr += a * a;
+            gg += b * b;
+            lg += c * c;
+            lr += e * e;
+        }
+        float v0, v1, v2;
+        if (mp.kind == ES_MONITOR_SMOOTH) {
+            v0 = sqrtf(gr);
+            v1 = 0.0f;
+            v2 = sqrtf(lr);
+        } else {
+            v0 = gr;
+            v1 = mp.kappa >= 2 ? gg : 0.0f;
+            v2 = lg;
+        }
+        t0[id] = v0;
+        t1[id] = v1;
+        t2[id] = v2;
+        m0 = fmaxf(m0, v0);
+        m1 = fmaxf(m1, v1);
+        m2 = fmaxf(m2, v2);
+    }
+    m0 = block_max_f32(m0);
+    m1 = block_max_f32(m1);
+    m2 = block_max_f32(m2);
+    if (threadIdx.x == 0) {
+        atomic_max_pos(&d->red[RED_MON0], double(m0));
+        atomic_max_pos(&d->red[RED_MON1], double(m1));
+        atomic_max_pos(&d->red[RED_MON2], double(m2));
+    }
+}
+
+__global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
+                              const DevScalars* d, float* omega) {
+    const int N = g.n1 * g.n2;
+    const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
+    const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
+    const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
+    const float c0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
+    const float c1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
+    const float c2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
+        omega[id] = sqrtf(1.0f + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
+}
+
+// low-pass filter: omega_i <- sum_{j in {0,+-1}^d} (1/2)^(|j|_1 + d) omega_{i+j}
+__global__ void k_filter_f(GridParams g, const float* in, float* out) {
+    const int N = g.n1 * g.n2;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        float s;
+        if (g.dim == 1) {
+            s = 0.25f * field_at_f(g, in, i - 1, 0) + 0.5f * in[id] + 0.25f * field_at_f(g, in, i + 1, 0);
+        } else {
+            s = 0.0f;
+            for (int dj = -1; dj <= 1; ++dj) {
+                float row = 0.0f;
+                for (int di = -1; di <= 1; ++di) row += (di == 0 ? 0.5f : 0.25f) * field_at_f(g, in, i + di, j + dj);
+                s += (dj == 0 ? 0.5f : 0.25f) * row;
+            }
+        }
+        out[id] = s;
+    }
+}
+
+// Jacobi sweep k on the displacement: sweep 0 reads d and writes buf[0]; sweep k reads
+// buf[(k-1)%2] and writes buf[k%2].  The coordinate of a neighbour along direction kk is
+// its displacement plus +-dxi_kk in component kk.  Tolerance check as in the FP64 path.
+__global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, float* da, float* db, int k,
+                           DevScalars* d, int check, double eps) {
+    if (d->conv) return;
+    const int N = g.n1 * g.n2;
+    const float* xin = k == 0 ? d0 : ((k - 1) & 1 ? db : da);
+    float* xout = (k & 1) ? db : da;
+    float chg = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        if (fixed_node_f(g, i, j)) {
+            for (int c = 0; c < g.dim; ++c) xout[c * N + id] = xin[c * N + id];
+            continue;
+        }
+        const float w0 = omega[id];
+        float den = 0.0f, num0 = 0.0f, num1 = 0.0f;
+        for (int kk = 0; kk < g.dim; ++kk) {
+            const int di = kk == 0, dj = kk == 1;
+            const float ih2 = float(g.inv_dxi[kk] * g.inv_dxi[kk]);
+            const float dx = float(1.0 / g.inv_dxi[kk]);
+            const float wp = 0.5f * (w0 + field_at_f(g, omega, i + di, j + dj)) * ih2;
+            const float wm = 0.5f * (w0 + field_at_f(g, omega, i - di, j - dj)) * ih2;
+            den += wp + wm;
+            const float sp = kk == 0 ? dx : 0.0f, sp1 = kk == 1 ? dx : 0.0f;
+            num0 += wp * (disp_at(g, xin, i + di, j + dj, 0) + sp) + wm * (disp_at(g, xin, i - di, j - dj, 0) - sp);
+            if (g.dim == 2)
+                num1 += wp * (disp_at(g, xin, i + di, j + dj, 1) + sp1) +
+                        wm * (disp_at(g, xin, i - di, j - dj, 1) - sp1);
+        }
+        const float idn = 1.0f / den;
+        const float n0 = num0 * idn;
+        chg = fmaxf(chg, fabsf(n0 - xin[id]));
+        xout[id] = n0;
+        if (g.dim == 2) {
+            const float n1 = num1 * idn;
+            chg = fmaxf(chg, fabsf(n1 - xin[N + id]));
+            xout[N + id] = n1;
+        }
+    }
+    if (check) {
+        chg = block_max_f32(chg);
+        if (threadIdx.x == 0) {
+            atomic_max_pos(&d->red[RED_JAC], double(chg));
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {
+                const double c = __longlong_as_double((long long)atomicAdd(&d->red[RED_JAC], 0ULL));
+                if (c < eps) d->conv = 1;
+                d->red[RED_JAC] = 0ULL;
+                d->done = 0u;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&d->sweeps, 1);
+}
+
+__device__ __forceinline__ const float* jacobi_result_f(const DevScalars* d, const float* d0, const float* da,
+                                                        const float* db) {
+    if (d->sweeps == 0) return d0;
+    return ((d->sweeps - 1) & 1) ? db : da;
+}
+
+// Delta_gamma on the displacement: the spacing to a neighbour along k is dxi_k + d_i - d_{i-1}
+__global__ void k_limiter_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d) {
+    const int N = g.n1 * g.n2;
+    const float* xit = jacobi_result_f(d, d0, da, db);
+    float m = 1.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const int i = id % g.n1, j = id / g.n1;
+        for (int k = 0; k < g.dim; ++k) {
+            const float dx = xit[k * N + id] - d0[k * N + id];
+            const int di = k == 0, dj = k == 1;
+            const float h = float(1.0 / g.inv_dxi[k]);
+            if (dx < 0.0f) m = fminf(m, -(h + d0[k * N + id] - disp_at(g, d0, i - di, j - dj, k)) / (2.0f * dx));
+            else if (dx > 0.0f) m = fminf(m, (h + disp_at(g, d0, i + di, j + dj, k) - d0[k * N + id]) / (2.0f * dx));
+        }
+    }
+    m = block_min_f32(m);
+    if (threadIdx.x == 0) atomic_min_pos(&d->red[RED_GAMMA], double(m));
+}
+
+// xdot = Delta_gamma (x^[mu] - x^n) / dt: float (for the stage kernels) and double (the API's array)
+__global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
+                             float* fxd, double* xdot) {
+    const int N = g.n1 * g.n2;
+    const float* xit = jacobi_result_f(d, d0, da, db);
+    const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
+    const double dt = d->dt;
+    const float f = dt > 0.0 ? float(gam / dt) : 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x) {
+        const float v = f * (xit[id] - d0[id]);
+        fxd[id] = v;
+        xdot[id] = double(v);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d->gamma = gam;
+        d->sweeps_total += d->sweeps;
+        d->solves += 1;
+    }
+}
+
+}  // namespace es

@@ -1,0 +1,39 @@
+// es_mesh_f32.h -- time step and mesh redistribution of the mixed form on the FP32 pipe.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "es_aux.h"
+
+namespace es {
+
+// float copies of the gas constants
+struct GasF32 {
+    float a, b, R, cv, delta, icv;
+};
+
+inline GasF32 gas_f32(const Gas& g) {
+    GasF32 f;
+    f.a = float(g.a);
+    f.b = float(g.b);
+    f.R = float(g.R);
+    f.cv = float(g.cv);
+    f.delta = float(g.delta);
+    f.icv = float(1.0 / g.cv);
+    return f;
+}
+
+// JU, J: the mixed form's (hi, lo) float planes; disp: the FP32 displacement [dim][N]
+__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, DevScalars* d);
+__global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
+__global__ void k_mon_terms_f(GridParams g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
+                              float* t2, DevScalars* d);
+__global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
+                              const DevScalars* d, float* omega);
+__global__ void k_filter_f(GridParams g, const float* in, float* out);
+__global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, float* da, float* db, int k,
+                           DevScalars* d, int check, double eps);
+__global__ void k_limiter_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d);
+__global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
+                             float* fxd, double* xdot);
+
+}  // namespace es

@@ -114,3 +114,33 @@ def test_mixed_design_order_1d():
         errs.append(np.abs(rho - ex).mean())
     order = np.log2(errs[-2] / errs[-1])
     assert order > 4.5, errs
+
+
+@pytest.mark.parametrize("case", ["riemann2d", "rp1d", "wavy_periodic"])
+def test_mixed_mesh_redistribution_fp32_vs_oracle(case):
+    """The mixed form's time step and mesh redistribution run on the FP32 displacement:
+    the same sweeps, Delta_gamma and mesh velocity as the FP64 oracle to FP32 rounding."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    if case == "riemann2d":
+        w = wl.riemann_2d(64, seed=5)
+    elif case == "rp1d":
+        w = wl.riemann_1d("RP1", n=300)
+    else:
+        w = _wavy(48)
+        w["moving"] = True
+        w["mesh"] = dict(monitor="vdw", alphas=(1200.0, 1200.0, 1200.0), kappa=2, filter_passes=5, sweeps=5,
+                         eps=0.0)
+        w["rho"], w["v"], w["p"] = wl.rough_state(w["x"].shape[1:], 11, 2)
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    dt = 0.004
+    xdot_o, sw_o, gam_o = stepper.redistribute(sch, mc, JU_o, J_o, x, dt)
+    xdot = torch.empty_like(xt)
+    sw, gam = es.es_mesh_redistribute(ctx, JU, J, xt, dt, xdot)
+    assert sw == sw_o
+    assert abs(gam - gam_o) <= 1e-5 * gam_o
+    assert np.abs(to_np(xdot) - xdot_o).max() <= 2e-5 * np.abs(xdot_o).max()
+    dt_o = stepper.cfl_dt(sch, JU_o, J_o, x, w.get("cfl", 0.4))
+    assert abs(es.es_cfl_dt(ctx, JU, J, xt) - dt_o) <= 1e-5 * dt_o
