@@ -375,14 +375,14 @@ def measure_precision_sweep(args, dev):
 
 def measure_learned(args, dev):
     """The learned warm start on the 2D vdW Riemann problem: snapshots of plain runs (Jacobi to
-    max change < 0.02 cells, at most 300 sweeps), training, and the plain against the
+    max change < 0.02 cells, at most 64 sweeps), training, and the plain against the
     warm-started solve on held-out seeds (same states, then two full runs)."""
     import time
 
     import torch
 
     from paper_2407_05568_gb300 import learned
-    n, eps, mu = args.learned_n, 0.02, 300
+    n, eps, mu = args.learned_n, 0.02, 64
     seeds = list(range(100, 100 + args.learned_seeds))
     train_seeds, test_seeds = seeds[:-2], seeds[-2:]
     t0 = time.perf_counter()
@@ -397,17 +397,20 @@ def measure_learned(args, dev):
     iters = args.learned_epochs * (feats.shape[0] // 4)
     del feats, tgts
     torch.cuda.empty_cache()
-    # inference time of the network alone (four conv launches on one n x n image)
+    # inference time of the network alone (four conv launches on one n x n image): the tensor-core
+    # path the solver uses, and the FP32 CUDA-core forward of the training path
     x = torch.zeros((1, 4, n, n), dtype=torch.float32, device=dev)
-    for _ in range(3):
-        net.forward(x)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(20):
-        net.forward(x)
-    e1.record()
-    torch.cuda.synchronize()
-    t_inf = e0.elapsed_time(e1) / 20
+    t_inf = {}
+    for name, fn in (("tensor_cores_bf16_inputs", net.infer), ("cuda_cores_fp32", net.forward)):
+        for _ in range(3):
+            fn(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            fn(x)
+        e1.record()
+        torch.cuda.synchronize()
+        t_inf[name] = e0.elapsed_time(e1) / 20
     cmp = learned.compare_solves(net, test_seeds, n, args.learned_steps, eps, mu, device=dev)
     run = learned.compare_runs(net, test_seeds[0], n, args.learned_steps, eps, mu, device=dev)
     return {"workload": f"2D vdW Riemann problem {n}x{n}, moving mesh, Jacobi to max change < {eps} cells "

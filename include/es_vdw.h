@@ -218,6 +218,7 @@ int es_mesh_warm_start(es_ctx* ctx, const double* xn, const float* out, double* 
  * `layers` 3x3 cross-correlations (zero padding), 4 -> hidden -> ... -> hidden -> 2
  * channels, tanh after all but the last; the output is the displacement in cells,
  * x_start = xn + dxi_k out_k (boundary nodes fixed, non-finite outputs dropped).
+ * The layers run as es_nn_conv_forward_bf16 (tensor cores, bf16 layer inputs).
  * w_bf16: device bf16 weights, layer by layer, each [Cout][Cin][3][3]; bias:
  * device float biases, layer by layer.  Both are copied (weights converted to
  * float), so the caller may free or change them afterwards; register again to
@@ -244,6 +245,11 @@ int es_mesh_stats(es_ctx* ctx, int64_t* sweeps_total, int64_t* solves, int64_t* 
  * bytes (forward needs only Cout*Cin*9 floats).  Returns ES_ERR_ARG for bad
  * shapes, null pointers or aliasing outputs. */
 size_t es_nn_workspace_bytes(int B, int Cin, int Cout, int H, int W);
+/* Forward layer on the tensor cores (the warm start's inference path): the same
+ * correlation with the layer input rounded to bf16 (round to nearest even), bf16
+ * weights, products accumulated in FP32 (mma m16n8k16), bias and tanh in FP32. */
+int es_nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
+                            int Cout, int H, int W, int act_tanh, void* stream);
 int es_nn_conv_forward(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin, int Cout,
                        int H, int W, int act_tanh, void* workspace, size_t workspace_bytes, void* stream);
 int es_nn_conv_backward(const float* in, const uint16_t* w, const float* out, float* grad_out, float* grad_in,

@@ -76,12 +76,14 @@ def conv3x3_backward(a, w, g):
     return gw, gb, ga
 
 
-def forward(ws, bs, a0):
-    """Activations [a^0, a^1, ..., output] of the network with layers (ws[l], bs[l])."""
+def forward(ws, bs, a0, bf16_inputs=False):
+    """Activations [a^0, a^1, ..., output] of the network with layers (ws[l], bs[l]); with
+    bf16_inputs each layer's input is first rounded to bf16 (a tensor-core layer's operand)."""
     acts = [np.asarray(a0, dtype=np.float64)]
     L = len(ws)
     for l in range(L):
-        z = conv3x3(acts[-1], ws[l], bs[l])
+        a = bf16_round(acts[-1]) if bf16_inputs else acts[-1]
+        z = conv3x3(a, ws[l], bs[l])
         acts.append(np.tanh(z) if l < L - 1 else z)
     return acts
 

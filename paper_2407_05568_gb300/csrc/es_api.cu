@@ -39,7 +39,8 @@ struct es_ctx {
     // learned warm start (2D): network copy (float weights), features, activations
     int nn_layers, nn_hidden;
     double nn_ratio;                  // guard: keep the warm start if c1 < nn_ratio c0
-    float *nn_wf, *nn_b, *feat, *act0, *act1, *nn_out;
+    uint16_t* nn_wbf;                 // bf16 weights (the context's copy)
+    float *nn_b, *feat, *act0, *act1, *nn_out;
     double* xw;
     DevScalars* dev;
     DevScalars* hpin;                 // pinned host mirror
@@ -172,8 +173,8 @@ int enqueue_net(es_ctx* c, const double* om, const double* xn) {
         const bool last = l == c->nn_layers - 1;
         const int cout = last ? c->p.dim : c->nn_hidden;
         float* out = last ? c->nn_out : ((l & 1) ? c->act1 : c->act0);
-        cudaError_t e = nn_conv_forward_f32(in, c->nn_wf + woff, c->nn_b + boff, out, 1, cin, cout, c->g.n2,
-                                            c->g.n1, last ? 0 : 1, s);
+        cudaError_t e = nn_conv_forward_bf16(in, c->nn_wbf + woff, c->nn_b + boff, out, 1, cin, cout, c->g.n2,
+                                             c->g.n1, last ? 0 : 1, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "warm-start network");
         count(c);
         woff += size_t(cout) * cin * 9;
@@ -472,7 +473,7 @@ void es_destroy(es_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     void* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->om0, c->om1,
                     c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx, c->fdisp, c->fxd,
-                    c->nn_wf, c->nn_b, c->feat, c->act0, c->act1, c->nn_out, c->xw};
+                    c->nn_wbf, c->nn_b, c->feat, c->act0, c->act1, c->nn_out, c->xw};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->dev) cudaFree(c->dev);
@@ -635,10 +636,10 @@ int es_set_warm_start(es_ctx* c, const uint16_t* w_bf16, const float* bias, int 
                       size_t(c->p.dim) * hidden * 9;
     const size_t nb = size_t(layers - 1) * hidden + c->p.dim;
     if (c->nn_hidden != hidden || !c->feat) {
-        void* old[] = {c->nn_wf, c->nn_b, c->act0, c->act1};
+        void* old[] = {c->nn_b, c->act0, c->act1};
         for (void* b : old)
             if (b) cudaFree(b);
-        c->nn_wf = c->nn_b = c->act0 = c->act1 = nullptr;
+        c->nn_b = c->act0 = c->act1 = nullptr;
         const size_t FB = sizeof(float) * c->N;
         if (!c->feat) {
             CK(cudaMalloc((void**)&c->feat, FB * cin0), "cudaMalloc");
@@ -648,12 +649,13 @@ int es_set_warm_start(es_ctx* c, const uint16_t* w_bf16, const float* bias, int 
         CK(cudaMalloc((void**)&c->act0, FB * hidden), "cudaMalloc");
         CK(cudaMalloc((void**)&c->act1, FB * hidden), "cudaMalloc");
     }
-    if (c->nn_wf) cudaFree(c->nn_wf);
+    if (c->nn_wbf) cudaFree(c->nn_wbf);
     if (c->nn_b) cudaFree(c->nn_b);
-    c->nn_wf = c->nn_b = nullptr;
-    CK(cudaMalloc((void**)&c->nn_wf, sizeof(float) * nw), "cudaMalloc");
+    c->nn_wbf = nullptr;
+    c->nn_b = nullptr;
+    CK(cudaMalloc((void**)&c->nn_wbf, sizeof(uint16_t) * nw), "cudaMalloc");
     CK(cudaMalloc((void**)&c->nn_b, sizeof(float) * nb), "cudaMalloc");
-    CK(nn_bf16_to_float(w_bf16, c->nn_wf, nw, c->stream), "weight copy");
+    CK(cudaMemcpyAsync(c->nn_wbf, w_bf16, sizeof(uint16_t) * nw, cudaMemcpyDeviceToDevice, c->stream), "weight copy");
     CK(cudaMemcpyAsync(c->nn_b, bias, sizeof(float) * nb, cudaMemcpyDeviceToDevice, c->stream), "bias copy");
     CK(nn_prepare(), "conv kernel attributes");
     CK(cudaStreamSynchronize(c->stream), "sync");

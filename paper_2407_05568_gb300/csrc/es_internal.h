@@ -96,5 +96,7 @@ cudaError_t nn_prepare();
 cudaError_t nn_bf16_to_float(const uint16_t* w, float* f, size_t n, cudaStream_t s);
 cudaError_t nn_conv_forward_f32(const float* in, const float* wf, const float* bias, float* out, int B, int Cin,
                                 int Cout, int H, int W, int act, cudaStream_t s);
+cudaError_t nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
+                                 int Cout, int H, int W, int act, cudaStream_t s);
 
 }  // namespace es

@@ -209,6 +209,115 @@ __global__ void k_adam(float* master, __nv_bfloat16* wb, const float* grad, floa
     }
 }
 
+// ---- tensor-core forward (inference): implicit GEMM on mma.sync.m16n8k16 (bf16 in, FP32 accumulate).
+// A CTA of 4 warps computes a 16 x 16 pixel tile; warp w owns output rows 4w .. 4w+3 (one m16 tile
+// per row, rows of the m16 tile = the 16 pixels of that row), all NPAD output channels (NPAD/8 n8
+// tiles).  GEMM: M = pixels, N = Cout, K = 9 Cin ordered k = tap * Cin + ci (padded to 16).  The
+// input tile with its halo is staged as bf16 pairs [pixel][ci/2] and the weights as bf16 pairs
+// [n][k/2]; the row strides are padded so that the fragment loads of a warp hit 32 distinct banks.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int CIN, int NPAD>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(const float* __restrict__ in,
+                                                    const __nv_bfloat16* __restrict__ w,
+                                                    const float* __restrict__ bias, float* __restrict__ out,
+                                                    int Cout, int H, int W, int act) {
+    constexpr int K = 9 * CIN;
+    constexpr int KP = (K + 15) / 16 * 16;
+    constexpr int KSW = KP / 2 + 4;                       // words per weight row
+    constexpr int PSW = CIN / 2 + (CIN >= 32 ? 4 : 1);    // words per staged pixel
+    constexpr int NT = NPAD / 8;
+    __shared__ uint32_t ws[NPAD * KSW];
+    __shared__ uint32_t xs[HALO * HALO * PSW];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, b = blockIdx.z;
+    const size_t HW = size_t(H) * W;
+    for (int idx = tid; idx < NPAD * (KP / 2); idx += 128) {
+        const int n = idx / (KP / 2), k0 = 2 * (idx % (KP / 2));
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int k = k0 + e;
+            v[e] = (n < Cout && k < K) ? __bfloat162float(w[(n * CIN + k % CIN) * 9 + k / CIN]) : 0.0f;
+        }
+        ws[n * KSW + k0 / 2] = pack_bf16(v[0], v[1]);
+    }
+    const float* inb = in + size_t(b) * CIN * HW;
+    for (int idx = tid; idx < HALO * HALO * (CIN / 2); idx += 128) {
+        const int p = idx % (HALO * HALO), cw = idx / (HALO * HALO);
+        const int yy = y0 - 1 + p / HALO, xx = x0 - 1 + p % HALO;
+        float v0 = 0.0f, v1 = 0.0f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const size_t o = size_t(yy) * W + xx;
+            v0 = inb[(2 * cw) * HW + o];
+            v1 = inb[(2 * cw + 1) * HW + o];
+        }
+        xs[p * PSW + cw] = pack_bf16(v0, v1);
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    float acc[4][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll 2
+    for (int s = 0; s < KP / 16; ++s) {
+        uint32_t bf[NT][2];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int n = nt * 8 + g;
+            bf[nt][0] = ws[n * KSW + s * 8 + t];
+            bf[nt][1] = ws[n * KSW + s * 8 + 4 + t];
+        }
+        const int klo = s * 16 + 2 * t, khi = klo + 8;
+        const bool vlo = klo < K, vhi = khi < K;
+        const int tlo = klo / CIN, clo = (klo % CIN) / 2, thi = khi / CIN, chi = (khi % CIN) / 2;
+        const int olo = (tlo / 3) * HALO + tlo % 3, ohi = (thi / 3) * HALO + thi % 3;
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt) {
+            const int row = (warp * 4 + mt) * HALO;           // output row of this m16 tile, box coordinates
+            uint32_t af[4];
+            af[0] = vlo ? xs[(row + olo + g) * PSW + clo] : 0u;
+            af[1] = vlo ? xs[(row + olo + g + 8) * PSW + clo] : 0u;
+            af[2] = vhi ? xs[(row + ohi + g) * PSW + chi] : 0u;
+            af[3] = vhi ? xs[(row + ohi + g + 8) * PSW + chi] : 0u;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(acc[mt][nt], af, bf[nt]);
+        }
+    }
+    float* ob = out + size_t(b) * Cout * HW;
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        const int y = y0 + warp * 4 + mt;
+        if (y >= H) continue;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = x0 + g + (e >= 2 ? 8 : 0);
+                const int co = nt * 8 + 2 * t + (e & 1);
+                if (co < Cout && x < W) {
+                    const float v = acc[mt][nt][e] + bias[co];
+                    ob[co * HW + size_t(y) * W + x] = act ? tanhf(v) : v;
+                }
+            }
+    }
+}
+
 int grid_for(size_t n) {
     const size_t g = (n + 255) / 256;
     return int(g < 4096 ? (g > 0 ? g : 1) : 4096);
@@ -269,6 +378,28 @@ cudaError_t nn_bf16_to_float(const uint16_t* w, float* f, size_t n, cudaStream_t
     return cudaGetLastError();
 }
 
+cudaError_t nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
+                                 int Cout, int H, int W, int act, cudaStream_t s) {
+    const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
+    dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
+    if (Cout <= 8) {
+        switch (Cin) {
+            case 2: k_conv_fwd_tc<2, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 4: k_conv_fwd_tc<4, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 32: k_conv_fwd_tc<32, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (Cin) {
+            case 2: k_conv_fwd_tc<2, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 4: k_conv_fwd_tc<4, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 32: k_conv_fwd_tc<32, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t nn_conv_forward_f32(const float* in, const float* wf, const float* bias, float* out, int B, int Cin,
                                 int Cout, int H, int W, int act, cudaStream_t s) {
     switch (Cout) {
@@ -305,6 +436,14 @@ int es_nn_conv_forward(const float* in, const uint16_t* w, const float* bias, fl
     if (nn_bf16_to_float(w, wf, size_t(Cout) * Cin * 9, s) != cudaSuccess) return ES_ERR_CUDA;
     return nn_conv_forward_f32(in, wf, bias, out, B, Cin, Cout, H, W, act_tanh, s) == cudaSuccess ? ES_OK
                                                                                                 : ES_ERR_CUDA;
+}
+
+int es_nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
+                            int Cout, int H, int W, int act_tanh, void* stream) {
+    if (!in || !w || !bias || !out || !shape_ok(B, Cin, Cout, H, W) || in == out) return ES_ERR_ARG;
+    return nn_conv_forward_bf16(in, w, bias, out, B, Cin, Cout, H, W, act_tanh, (cudaStream_t)stream) == cudaSuccess
+               ? ES_OK
+               : ES_ERR_CUDA;
 }
 
 int es_nn_conv_backward(const float* in, const uint16_t* w, const float* out, float* grad_out, float* grad_in,

@@ -95,11 +95,13 @@ def lib():
         L.es_nn_conv_forward.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp, ctypes.c_size_t, vp]
         L.es_nn_conv_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, i, i, i, i, vp, ctypes.c_size_t, vp]
         L.es_nn_mse.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
+        L.es_nn_conv_forward_bf16.argtypes = [vp, vp, vp, vp, i, i, i, i, i, i, vp]
         L.es_nn_to_bf16.argtypes = [vp, vp, ctypes.c_int64, vp]
         f = ctypes.c_float
         L.es_nn_adam.argtypes = [vp, vp, vp, vp, vp, i, f, f, f, f, i, vp]
         for name in ("es_mesh_features", "es_mesh_solve", "es_set_warm_start", "es_mesh_stats", "es_mesh_warm_start",
-                     "es_nn_conv_forward", "es_nn_conv_backward", "es_nn_mse", "es_nn_adam", "es_nn_to_bf16"):
+                     "es_nn_conv_forward", "es_nn_conv_backward", "es_nn_mse", "es_nn_adam", "es_nn_to_bf16",
+                     "es_nn_conv_forward_bf16"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("es_batch_create", "es_batch_set_prim", "es_batch_steps", "es_batch_get", "es_batch_check",
                      "es_batch_autotune",
@@ -300,6 +302,14 @@ def es_nn_conv_forward(inp, w, bias, out, act_tanh, workspace, stream=None):
     _nn_rc(lib().es_nn_conv_forward(_ptr(inp, F32), _ptr(w, BF16), _ptr(bias, F32), _ptr(out, F32), B, Cin, Cout,
                                     H, W, int(act_tanh), _ptr(workspace), workspace.numel() * workspace.element_size(),
                                     _stream_handle(stream)), "es_nn_conv_forward")
+
+
+def es_nn_conv_forward_bf16(inp, w, bias, out, act_tanh, stream=None):
+    """The same layer on the tensor cores: input rounded to bf16, FP32 accumulation."""
+    B, Cin, H, W = inp.shape
+    Cout = w.shape[0]
+    _nn_rc(lib().es_nn_conv_forward_bf16(_ptr(inp, F32), _ptr(w, BF16), _ptr(bias, F32), _ptr(out, F32), B, Cin,
+                                         Cout, H, W, int(act_tanh), _stream_handle(stream)), "es_nn_conv_forward_bf16")
 
 
 def es_nn_conv_backward(inp, w, out, grad_out, grad_in, grad_w, grad_b, act_tanh, workspace, stream=None):

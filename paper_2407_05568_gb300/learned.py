@@ -116,6 +116,16 @@ class WarmStartNet:
                                   l < self.layers - 1, ws)
         return acts[-1]
 
+    def infer(self, x):
+        """The inference path the context uses: every layer on the tensor cores (bf16 layer inputs)."""
+        B, _, H, W = x.shape
+        acts, _, _, _ = self._buffers(B, H, W)
+        acts[0] = x
+        for l in range(self.layers):
+            es.es_nn_conv_forward_bf16(acts[l], self.layer(l, self.wb), self.layer(l, self.b, "b"), acts[l + 1],
+                                       l < self.layers - 1)
+        return acts[-1]
+
     def train_step(self, x, y, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         """One Adam step on the MSE of forward(x) against y; returns the loss tensor (device)."""
         B, _, H, W = x.shape
@@ -220,7 +230,7 @@ def compare_solves(net, seeds, n, steps, eps_cells, mu_max, precision="fp64", de
         xs = torch.empty_like(x)
         for s in range(steps):
             es.es_mesh_features(ctx, JU, J, x, feat[0])
-            o = net.forward(feat)
+            o = net.infer(feat)
             es.es_mesh_warm_start(ctx, x, o[0], xs)
             sp, _ = es.es_mesh_solve(ctx, JU, J, x, None, xp)
             sw, pk = es.es_mesh_solve(ctx, JU, J, x, xs, xw, guard_ratio=guard_ratio)

@@ -62,6 +62,26 @@ def test_conv_forward_vs_oracle(cin, cout, act):
     assert np.abs(_np(out) - ref).max() <= 2e-5 * scale
 
 
+@pytest.mark.parametrize("cin,cout,act", [(4, 32, True), (32, 32, True), (32, 2, False), (2, 4, False)])
+def test_conv_forward_tensor_cores_vs_oracle(cin, cout, act):
+    """The inference layer on the tensor cores: the correlation of the bf16-rounded input with bf16
+    weights, FP32 accumulation (several 16 x 16 tiles and ragged tails, batch of 2)."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    rng = np.random.default_rng(30 + cin + cout)
+    B, H, W = 2, 37, 50
+    a = rng.standard_normal((B, cin, H, W)).astype(np.float32)
+    w, wt = _bf16_weights(rng, (cout, cin, 3, 3), 1.0 / np.sqrt(9 * cin))
+    b = rng.standard_normal(cout).astype(np.float32) * 0.1
+    out = torch.empty((B, cout, H, W), dtype=torch.float32, device="cuda")
+    es.es_nn_conv_forward_bf16(_t(a), wt, _t(b), out, act)
+    torch.cuda.synchronize()
+    z = convnet.conv3x3(convnet.bf16_round(a), w, b.astype(np.float64))
+    ref = np.tanh(z) if act else z
+    assert np.abs(_np(out) - ref).max() <= 2e-5 * np.abs(z).max()
+
+
 @pytest.mark.parametrize("cin,cout,act", [(4, 32, True), (32, 32, True), (32, 2, False)])
 def test_conv_backward_vs_oracle(cin, cout, act):
     import torch
@@ -237,7 +257,7 @@ def test_redistribute_with_registered_network_vs_oracle():
     xdot = torch.empty_like(xt)
     sw, gam = es.es_mesh_redistribute(ctx, JU, J, xt, dt, xdot)
     f = warmstart.features(sch, mc, JU_o, J_o, x)
-    out = convnet.forward(ws, [b.astype(np.float64) for b in bs], f[None])[-1][0]
+    out = convnet.forward(ws, [b.astype(np.float64) for b in bs], f[None], bf16_inputs=True)[-1][0]
     xs = warmstart.warm_start(sch, x, out)
     xo, ko, po = warmstart.solve(sch, mc, JU_o, J_o, x, xs, guard_ratio=1.0)
     assert po == 0                                       # an untrained network's start is refused

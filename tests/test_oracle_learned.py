@@ -248,3 +248,17 @@ def test_guard_ratio_admits_a_larger_first_residual():
     ref, _ = mesh.jacobi(sch, xs, om, 6)
     assert (p1, p4, k4) == (0, 1, 6)
     assert np.array_equal(x4, ref)
+
+
+def test_forward_bf16_inputs_rounds_each_layer_input():
+    """With bf16_inputs the first layer sees the bf16-rounded features (a value between two bf16
+    neighbours moves to one of them) and the rest of the definition is unchanged."""
+    rng = np.random.default_rng(13)
+    ws, bs = _net(rng, hidden=3, layers=2)
+    a0 = (1.0 + 2.0 ** -9) * np.ones((1, 4, 3, 3))          # halfway-below: rounds to 1.0
+    plain = convnet.forward(ws, bs, a0)
+    rounded = convnet.forward(ws, bs, a0, bf16_inputs=True)
+    ref = convnet.forward(ws, bs, np.ones((1, 4, 3, 3)))
+    assert np.array_equal(rounded[1], convnet.forward(ws, bs, convnet.bf16_round(a0))[1])
+    assert np.array_equal(rounded[1], ref[1])
+    assert not np.array_equal(plain[1], ref[1])
