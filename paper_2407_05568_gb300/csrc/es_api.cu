@@ -249,17 +249,32 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot) {
     float* db = (float*)c->xb;
     k_mon_fields_f<<<G, B, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, rho, Gf);
     k_mon_terms_f<<<G, B, 0, s>>>(c->g, c->mon, rho, Gf, t0, t1, t2, c->dev);
-    k_mon_omega_f<<<G, B, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, om);
-    count(c, 3);
-    for (int k = 0; k < c->p.filter_passes; ++k) {
-        k_filter_f<<<G, B, 0, s>>>(c->g, om, other);
+    count(c, 2);
+    // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
+    const bool fuse = c->p.dim == 2;
+    const dim3 tiles((c->g.n1 + 31) / 32, (c->g.n2 + 15) / 16);
+    if (fuse && c->p.filter_passes >= 1 && c->p.filter_passes <= 8) {
+        k_omega_filter_f<<<tiles, 256, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, c->p.filter_passes, om);
         count(c);
-        float* tmp = om; om = other; other = tmp;
+    } else {
+        k_mon_omega_f<<<G, B, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, om);
+        count(c);
+        for (int k = 0; k < c->p.filter_passes; ++k) {
+            k_filter_f<<<G, B, 0, s>>>(c->g, om, other);
+            count(c);
+            float* tmp = om; om = other; other = tmp;
+        }
     }
     const int check = c->p.jacobi_eps > 0.0;
-    for (int k = 0; k < c->p.jacobi_sweeps; ++k) {
-        k_jacobi_f<<<G, B, 0, s>>>(c->g, om, c->fdisp, da, db, k, c->dev, check, c->p.jacobi_eps);
+    const int mu = c->p.jacobi_sweeps;
+    if (fuse && !check && mu >= 1 && mu <= 8) {
+        k_jacobi_multi_f<<<tiles, 256, 0, s>>>(c->g, om, c->fdisp, ((mu - 1) & 1) ? db : da, mu, c->dev);
         count(c);
+    } else {
+        for (int k = 0; k < mu; ++k) {
+            k_jacobi_f<<<G, B, 0, s>>>(c->g, om, c->fdisp, da, db, k, c->dev, check, c->p.jacobi_eps);
+            count(c);
+        }
     }
     k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
     k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot);

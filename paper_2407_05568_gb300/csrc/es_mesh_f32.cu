@@ -339,3 +339,141 @@ __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, con
 }
 
 }  // namespace es
+
+namespace es {
+
+// ---------------------------------------------------------------- fused passes (2D)
+// omega + s filter passes, and mu Jacobi sweeps without a tolerance, each in one launch: a CTA
+// owns a 32 x 16 tile and recomputes a halo of s (or mu) nodes in shared memory, so a pass
+// needs no grid-wide step.  Ghost nodes follow the unfused kernels: periodic halos hold the
+// wrapped nodes (and evolve with them); an outflow ghost of the filter is reset to its clamped
+// boundary node after every pass; outflow boundary nodes of the mesh do not move, so the sweeps
+// never read beyond them.  The arithmetic per node is that of k_mon_omega_f, k_filter_f and
+// k_jacobi_f, in the same order.
+constexpr int FT_X = 32, FT_Y = 16, FT_HMAX = 8;
+constexpr int FT_W = FT_X + 2 * FT_HMAX, FT_H = FT_Y + 2 * FT_HMAX;
+
+__global__ void __launch_bounds__(256) k_omega_filter_f(GridParams g, MonitorParams mp, const float* t0,
+                                                        const float* t1, const float* t2, const DevScalars* d,
+                                                        int passes, float* out) {
+    __shared__ float A[FT_W * FT_H], B[FT_W * FT_H];
+    const int h = passes, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
+    const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
+    const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
+    const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
+    const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
+    const float c0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
+    const float c1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
+    const float c2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+        const int sx = idx % TW, sy = idx / TW;
+        const int si = state_index(x0 + sx, g.n1, g.bc[0]), sj = state_index(y0 + sy, g.n2, g.bc[1]);
+        const int id = sj * g.n1 + si;
+        A[idx] = sqrtf(1.0f + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
+    }
+    __syncthreads();
+    float* cur = A;
+    float* nxt = B;
+    for (int p = 1; p <= h; ++p) {
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+            const int sx = idx % TW, sy = idx / TW;
+            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
+            float s = 0.0f;
+            for (int dj = -1; dj <= 1; ++dj) {
+                float row = 0.0f;
+                for (int di = -1; di <= 1; ++di) row += (di == 0 ? 0.5f : 0.25f) * cur[(sy + dj) * TW + sx + di];
+                s += (dj == 0 ? 0.5f : 0.25f) * row;
+            }
+            nxt[idx] = s;
+        }
+        __syncthreads();
+        // outflow ghosts take the new value of their clamped boundary node
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+            const int sx = idx % TW, sy = idx / TW;
+            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
+            const int gi = x0 + sx, gj = y0 + sy;
+            int cx = sx, cy = sy;
+            if (g.bc[0] == ES_BC_OUTFLOW) cx += (gi < 0 ? -gi : (gi >= g.n1 ? g.n1 - 1 - gi : 0));
+            if (g.bc[1] == ES_BC_OUTFLOW) cy += (gj < 0 ? -gj : (gj >= g.n2 ? g.n2 - 1 - gj : 0));
+            if (cx != sx || cy != sy) nxt[idx] = nxt[cy * TW + cx];
+        }
+        __syncthreads();
+        float* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
+        const int ix = idx % FT_X, iy = idx / FT_X;
+        const int gi = x0 + h + ix, gj = y0 + h + iy;
+        if (gi < g.n1 && gj < g.n2) out[gj * g.n1 + gi] = cur[(h + iy) * TW + h + ix];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const float* omega, const float* d0,
+                                                        float* dout, int sweeps, DevScalars* dv) {
+    __shared__ float Wm[FT_W * FT_H];
+    __shared__ float X[2][2][FT_W * FT_H];          // [buffer][component]
+    const int h = sweeps, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
+    const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
+    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+        const int sx = idx % TW, sy = idx / TW;
+        const int gi = x0 + sx, gj = y0 + sy;
+        Wm[idx] = field_at_f(g, omega, gi, gj);
+        X[0][0][idx] = disp_at(g, d0, gi, gj, 0);
+        X[0][1][idx] = disp_at(g, d0, gi, gj, 1);
+    }
+    __syncthreads();
+    const float ih2x = float(g.inv_dxi[0] * g.inv_dxi[0]), ih2y = float(g.inv_dxi[1] * g.inv_dxi[1]);
+    const float dxx = float(1.0 / g.inv_dxi[0]), dxy = float(1.0 / g.inv_dxi[1]);
+    int b = 0;
+    for (int p = 1; p <= h; ++p) {
+        const float* c0 = X[b][0];
+        const float* c1 = X[b][1];
+        float* n0 = X[b ^ 1][0];
+        float* n1 = X[b ^ 1][1];
+        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
+            const int sx = idx % TW, sy = idx / TW;
+            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
+            const int gi = x0 + sx, gj = y0 + sy;
+            const bool outside = (g.bc[0] == ES_BC_OUTFLOW && (gi < 0 || gi >= g.n1)) ||
+                                 (g.bc[1] == ES_BC_OUTFLOW && (gj < 0 || gj >= g.n2));
+            if (outside || fixed_node_f(g, gi, gj)) {
+                n0[idx] = c0[idx];
+                n1[idx] = c1[idx];
+                continue;
+            }
+            const float w0 = Wm[idx];
+            float den = 0.0f, num0 = 0.0f, num1 = 0.0f;
+            {   // direction 1
+                const float wp = 0.5f * (w0 + Wm[idx + 1]) * ih2x;
+                const float wm = 0.5f * (w0 + Wm[idx - 1]) * ih2x;
+                den += wp + wm;
+                num0 += wp * (c0[idx + 1] + dxx) + wm * (c0[idx - 1] - dxx);
+                num1 += wp * (c1[idx + 1] + 0.0f) + wm * (c1[idx - 1] - 0.0f);
+            }
+            {   // direction 2
+                const float wp = 0.5f * (w0 + Wm[idx + TW]) * ih2y;
+                const float wm = 0.5f * (w0 + Wm[idx - TW]) * ih2y;
+                den += wp + wm;
+                num0 += wp * (c0[idx + TW] + 0.0f) + wm * (c0[idx - TW] - 0.0f);
+                num1 += wp * (c1[idx + TW] + dxy) + wm * (c1[idx - TW] - dxy);
+            }
+            const float idn = 1.0f / den;
+            n0[idx] = num0 * idn;
+            n1[idx] = num1 * idn;
+        }
+        __syncthreads();
+        b ^= 1;
+    }
+    const size_t N = size_t(g.n1) * g.n2;
+    for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
+        const int ix = idx % FT_X, iy = idx / FT_X;
+        const int gi = x0 + h + ix, gj = y0 + h + iy;
+        if (gi < g.n1 && gj < g.n2) {
+            const int s = (h + iy) * TW + h + ix;
+            dout[size_t(gj) * g.n1 + gi] = X[b][0][s];
+            dout[N + size_t(gj) * g.n1 + gi] = X[b][1][s];
+        }
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&dv->sweeps, sweeps);
+}
+
+}  // namespace es

@@ -33,6 +33,11 @@ __global__ void k_filter_f(GridParams g, const float* in, float* out);
 __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, float* da, float* db, int k,
                            DevScalars* d, int check, double eps);
 __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d);
+// fused 2D passes (32 x 16 tiles, halo = the pass count <= FT_HMAX = 8)
+__global__ void k_omega_filter_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
+                                 const DevScalars* d, int passes, float* out);
+__global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
+                                 DevScalars* dv);
 __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
                              float* fxd, double* xdot);
 

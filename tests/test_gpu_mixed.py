@@ -144,3 +144,29 @@ def test_mixed_mesh_redistribution_fp32_vs_oracle(case):
     assert np.abs(to_np(xdot) - xdot_o).max() <= 2e-5 * np.abs(xdot_o).max()
     dt_o = stepper.cfl_dt(sch, JU_o, J_o, x, w.get("cfl", 0.4))
     assert abs(es.es_cfl_dt(ctx, JU, J, xt) - dt_o) <= 1e-5 * dt_o
+
+
+@pytest.mark.parametrize("case", ["riemann2d", "wavy_periodic"])
+def test_mixed_fused_sweeps_match_per_sweep_kernels(case):
+    """The fused multi-sweep Jacobi kernel (no tolerance) and the per-sweep kernels (forced by a
+    tolerance that is never met) give the same mesh velocity to FP32 rounding."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = wl.riemann_2d(70, seed=5) if case == "riemann2d" else _wavy(48)
+    if case == "wavy_periodic":
+        w["moving"] = True
+        w["mesh"] = dict(monitor="vdw", alphas=(1200.0, 1200.0, 1200.0), kappa=2, filter_passes=5, sweeps=5,
+                         eps=0.0)
+        w["rho"], w["v"], w["p"] = wl.rough_state(w["x"].shape[1:], 11, 2)
+    out = []
+    for eps in (0.0, 1e-300):
+        w["mesh"] = dict(w["mesh"], sweeps=6, eps=eps)
+        ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+        xdot = torch.empty_like(xt)
+        sw, gam = es.es_mesh_redistribute(ctx, JU, J, xt, 0.004, xdot)
+        assert sw == 6
+        out.append((to_np(xdot), gam))
+    scale = np.abs(out[1][0]).max()
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-6 * scale
+    assert abs(out[0][1] - out[1][1]) <= 1e-6 * out[1][1]
