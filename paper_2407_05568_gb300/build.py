@@ -19,6 +19,12 @@ LIB = os.path.join(HERE, "libesvdw.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# The mixed form's FP32 arithmetic (its stage kernel, the batched kernel and its mesh kernels) uses
+# the fast single-precision division and square root (within 2 ulp); its accuracy model is FP32
+# rounding with double-float state and jumps, whose reciprocal is Newton-corrected.  FP64 code
+# is not affected by these flags.
+PER_FILE = {name: ["-prec-div=false", "-prec-sqrt=false"]
+            for name in ("es_stage_mixed.cu", "es_batch.cu", "es_mesh_f32.cu")}
 
 
 def nvcc():
@@ -34,7 +40,8 @@ def sources():
 
 def _compile(src, verbose=False):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), "-I", INCLUDE, "-I", CSRC, "-c", src,
+           "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
