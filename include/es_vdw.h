@@ -173,6 +173,11 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
  * times in ms.  1D contexts have one shape (returns 1).  Synchronises. */
 int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host);
 
+/* Self-test of the library's FP64 quotient and reciprocal (the stage kernel divides with
+ * them: a Newton-Raphson-refined hardware reciprocal and a Markstein quotient correction):
+ * q[i] = a[i] / b[i], r[i] = 1 / b[i] for device arrays of n doubles, on `stream`. */
+int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream);
+
 /* Number of kernel launches the library has issued (graph launches count
  * their kernels), for launch accounting. */
 int64_t es_launch_count(es_ctx* ctx);

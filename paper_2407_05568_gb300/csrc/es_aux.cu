@@ -520,3 +520,19 @@ void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const 
 }
 
 }  // namespace es
+
+namespace es {
+__global__ void k_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        q[i] = div_nr(a[i], b[i]);
+        r[i] = rcp_nr(b[i]);
+    }
+}
+}  // namespace es
+
+extern "C" int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream) {
+    if (!a || !b || !q || !r || n <= 0) return ES_ERR_ARG;
+    const int64_t blocks = (n + 255) / 256;
+    es::k_selftest_division<<<int(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(a, b, q, r, n);
+    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}

@@ -14,12 +14,31 @@ namespace es {
 // ----------------------------------------------------------------- constants
 struct Gas {
     double a, b, R, cv, delta;   // delta = R / cv
-    double iR, idelta;           // 1/R, 1/delta (set with the others)
+    double iR, idelta, icv;      // 1/R, 1/delta, 1/cv (set with the others)
 };
 
 inline void gas_reciprocals(Gas& g) {
     g.iR = 1.0 / g.R;
     g.idelta = 1.0 / g.delta;
+    g.icv = 1.0 / g.cv;
+}
+
+// Reciprocal and quotient for finite, normal, nonzero divisors (all the kernels' divisors are
+// positive physical quantities or sums of them): the hardware's approximate reciprocal refined by
+// two Newton-Raphson steps, y <- y + y (1 - b y), each of which squares the relative error, and
+// for the quotient one correction q <- q + y (a - b q) (Markstein, IBM J. Res. Develop. 34(1),
+// 1990).  Checked against IEEE division on the GPU (es_selftest_division).
+__device__ __forceinline__ double rcp_nr(double b) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
+    y = fma(y, fma(-b, y, 1.0), y);
+    y = fma(y, fma(-b, y, 1.0), y);
+    return y;
+}
+__device__ __forceinline__ double div_nr(double a, double b) {
+    const double y = rcp_nr(b);
+    const double q = a * y;
+    return fma(fma(-b, q, a), y, q);
 }
 
 // Sixth-order EC combination weights alpha_{3,m}, m = 1, 2, 3 (Sec. 3.1:
@@ -37,13 +56,13 @@ __device__ __forceinline__ double inv_log_mean(double al, double ar, double lnl,
     const double s = al + ar;
     const double d = al - ar;
     if (fabs(d) < 1e-2 * s) {
-        const double is = 1.0 / s;
+        const double is = rcp_nr(s);
         const double f = d * is;
         const double u = f * f;
         const double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0 + u * (1.0 / 9.0 + u * (1.0 / 11.0)))));
         return 2.0 * F * is;
     }
-    return (lnl - lnr) / d;
+    return div_nr(lnl - lnr, d);
 }
 
 // --------------------------------------------------------- MR-WENO5 (Sec. 3.3)
@@ -93,7 +112,7 @@ __device__ __forceinline__ double mr_weno5(double wm2, double wm1, double w0, do
     const double n1 = c.g1 * (d1 + tau) * (d2 * d3);
     const double n2 = c.g2 * (d2 + tau) * (d1 * d3);
     const double n3 = c.g3 * (d3 + tau) * (d1 * d2);
-    return (n1 * p1 + n2 * p2 + n3 * p3) / (n1 + n2 + n3);
+    return div_nr(n1 * p1 + n2 * p2 + n3 * p3, n1 + n2 + n3);
 }
 
 // --------------------------------------------------------- index helpers

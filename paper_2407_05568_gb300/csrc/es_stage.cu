@@ -66,12 +66,12 @@ __device__ __forceinline__ void pair_flux(const double* S, int NB, int l, int r,
     const double ilr = inv_log_mean(rl, rr, S[F_LNR * NB + l], S[F_LNR * NB + r]);
     const double ilT = inv_log_mean(Tl, Tr, S[F_LNT * NB + l], S[F_LNT * NB + r]);
     const double Pinv = S[F_IOM * NB + l] * S[F_IOM * NB + r];
-    const double iTa = 1.0 / T_m;
+    const double iTa = rcp_nr(T_m);
     const double coef = G.R * G.b * Pinv - G.a * iTa;
     double D = G.R * ilr + coef - G.a * iTa;
     if (G.b > 0.0)
         D += G.R * G.b * inv_log_mean(S[F_OM * NB + l], S[F_OM * NB + r], S[F_LNOM * NB + l], S[F_LNOM * NB + r]);
-    const double iD = 1.0 / D;
+    const double iD = rcp_nr(D);
     const double g_m = 0.5 * (S[F_G * NB + l] + S[F_G * NB + r]);
     const double rT_m = 0.5 * (S[F_RT * NB + l] + S[F_RT * NB + r]);
     const double v2T_m = 0.5 * (S[F_V2T * NB + l] + S[F_V2T * NB + r]);
@@ -87,7 +87,7 @@ __device__ __forceinline__ void pair_flux(const double* S, int NB, int l, int r,
         const double sv = vT1 * vm1;
         out[0] = Q1;
         out[1] = vm1 * Q1 + nx * P;
-        out[2] = (G.a * rT_m * (xt * rho_m + nx * rv1) + (sv - B0) * Q1 + P * nx * vT1) / iT_m;
+        out[2] = div_nr(G.a * rT_m * (xt * rho_m + nx * rv1) + (sv - B0) * Q1 + P * nx * vT1, iT_m);
     } else {
         const double vm2 = 0.5 * (S[F_V2 * NB + l] + S[F_V2 * NB + r]);
         const double vT2 = 0.5 * (S[F_VT2 * NB + l] + S[F_VT2 * NB + r]);
@@ -98,7 +98,8 @@ __device__ __forceinline__ void pair_flux(const double* S, int NB, int l, int r,
         out[0] = Q1;
         out[1] = vm1 * Q1 + nx * P;
         out[2] = vm2 * Q1 + ny * P;
-        out[3] = (G.a * rT_m * (xt * rho_m + nx * rv1 + ny * rv2) + (sv - B0) * Q1 + P * (nx * vT1 + ny * vT2)) / iT_m;
+        out[3] = div_nr(G.a * rT_m * (xt * rho_m + nx * rv1 + ny * rv2) + (sv - B0) * Q1 + P * (nx * vT1 + ny * vT2),
+                        iT_m);
     }
 }
 
@@ -113,12 +114,12 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
                                                  DevStatus* st, int gidx) {
     const int r = l + step;
     const double ilr = inv_log_mean(S[F_RHO * NB + l], S[F_RHO * NB + r], S[F_LNR * NB + l], S[F_LNR * NB + r]);
-    const double rho = 1.0 / ilr;
+    const double rho = rcp_nr(ilr);
     const double ilrp = inv_log_mean(S[F_RP * NB + l], S[F_RP * NB + r], S[F_LNRP * NB + l], S[F_LNRP * NB + r]);
     const double p = rho * ilrp;
     const double om = 1.0 - G.b * rho;
     const double T = (p + G.a * rho * rho) * om * ilr * G.iR;
-    const double iom = 1.0 / om;
+    const double iom = rcp_nr(om);
     const double c2 = (1.0 + G.delta) * G.R * T * iom * iom - 2.0 * G.a * rho;
     const double dcrit = G.R * T - 2.0 * G.a * rho * om * om;
     if (!(c2 > 0.0) || !(dcrit > 0.0) || !(om > 0.0)) raise_error(st, ES_ERR_INADMISSIBLE, gidx);
@@ -128,7 +129,7 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
     if (DIM == 2) {
         const double vm2 = 0.5 * (S[F_V2 * NB + l] + S[F_V2 * NB + r]);
         L = sqrt(nx * nx + ny * ny);
-        const double iL = 1.0 / L;
+        const double iL = rcp_nr(L);
         cs = nx * iL;
         sn = ny * iL;
         vn = cs * vm1 + sn * vm2;
@@ -141,9 +142,9 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
     const double E = rho * (G.cv * T - G.a * rho) + 0.5 * rho * (vn * vn + vt * vt);
     const double H = (E + p) * ilr;
     const double mid = H - c2 * om * G.idelta;
-    const double ic2 = 1.0 / c2;
+    const double ic2 = rcp_nr(c2);
     const double sA = sqrt(0.5 * rho * T * ic2);
-    const double sE = sqrt(G.R * G.delta * rho * T * T * ic2 / dcrit);
+    const double sE = sqrt(div_nr(G.R * G.delta * rho * T * T * ic2, dcrit));
     const double sT = sqrt(rho * T);
     const double Lam = fabs(xtf + L * vn) + L * c;
     const double Hm = H - vn * c, Hp = H + vn * c;
@@ -234,19 +235,19 @@ __device__ __forceinline__ void load_node(double* S, int NB, int b, const StageP
     const int sj = DIM == 2 ? state_index(gj, P.n2, P.bc[1]) : 0;
     const int idx = sj * P.n1 + si;
     const size_t N = size_t(P.n1) * P.n2;
-    const double iJ = 1.0 / P.Js[idx];
+    const double iJ = rcp_nr(P.Js[idx]);
     const double rho = P.JUs[idx] * iJ;
     const double m1 = P.JUs[N + idx] * iJ;
     const double m2 = DIM == 2 ? P.JUs[2 * N + idx] * iJ : 0.0;
     const double E = P.JUs[(DIM + 1) * N + idx] * iJ;
-    const double irho = 1.0 / rho;
+    const double irho = rcp_nr(rho);
     const double v1 = m1 * irho, v2 = m2 * irho;
     const double ke = 0.5 * (v1 * v1 + v2 * v2);
-    const double T = (E * irho - ke + G.a * rho) / G.cv;
+    const double T = (E * irho - ke + G.a * rho) * G.icv;
     const double om = 1.0 - G.b * rho;
-    const double iom = 1.0 / om;
+    const double iom = rcp_nr(om);
     const double p = rho * G.R * T * iom - G.a * rho * rho;
-    const double iT = 1.0 / T;
+    const double iT = rcp_nr(T);
     // what the node arithmetic needs (logarithms of rho, 1 - b rho, T, p); the
     // condition R T - 2 a rho (1 - b rho)^2 > 0 enters through the face states
     if (!(rho > 0.0) || !(om > 0.0) || !(T > 0.0) || !(p > 0.0)) raise_error(P.status, ES_ERR_INADMISSIBLE, idx);
@@ -271,7 +272,7 @@ __device__ __forceinline__ void load_node(double* S, int NB, int b, const StageP
     S[F_LNR * NB + b] = lnr;
     S[F_LNOM * NB + b] = lnom;
     S[F_LNT * NB + b] = lnT;
-    S[F_RP * NB + b] = rho / p;
+    S[F_RP * NB + b] = div_nr(rho, p);
     S[F_LNRP * NB + b] = lnr - lnp;
     // entropy variables V = ((e + p/rho)/T - s - |v|^2/(2T), v/T, -1/T), s = cv ln T + R ln((1 - b rho)/rho)
     const double s = G.cv * lnT + G.R * (lnom - lnr);

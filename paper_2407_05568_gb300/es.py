@@ -68,6 +68,8 @@ def lib():
         L.es_check.argtypes = [vp]
         L.es_last_error.argtypes = [vp, ctypes.c_char_p, i]
         L.es_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        L.es_selftest_division.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
+        L.es_selftest_division.restype = ctypes.c_int
         L.es_autotune.restype = ctypes.c_int
         L.es_launch_count.argtypes = [vp]
         L.es_launch_count.restype = ctypes.c_int64
@@ -371,6 +373,12 @@ def es_autotune(ctx, JU, J, x):
     ms = (ctypes.c_double * 3)()
     ctx._call(lib().es_autotune(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(k), ms))
     return k.value, list(ms)
+
+
+def es_selftest_division(a, b, q, r, stream=None):
+    """q = a / b and r = 1 / b with the library's FP64 division (float64 device arrays)."""
+    _nn_rc(lib().es_selftest_division(_ptr(a, F64), _ptr(b, F64), _ptr(q, F64), _ptr(r, F64), a.numel(),
+                                      _stream_handle(stream)), "es_selftest_division")
 
 
 def es_check(ctx):

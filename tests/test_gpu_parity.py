@@ -301,3 +301,25 @@ def test_tile_shapes_agree_bitwise(case, precision):
         assert torch.equal(dU, outs[0][0]) and torch.equal(dJ, outs[0][1])
     k, ms = es.es_autotune(p_ctx, JU, J, xt)
     assert k in (1, 2, 3) and all(m > 0 for m in ms)
+
+
+def test_fp64_division_within_an_ulp_of_ieee():
+    """The stage kernel's quotient and reciprocal (Newton-Raphson refined reciprocal, Markstein
+    correction) against IEEE division, over magnitudes from 1e-12 to 1e12 and both signs."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    rng = np.random.default_rng(99)
+    n = 1 << 20
+    a = rng.standard_normal(n) * 10.0 ** rng.uniform(-12, 12, n)
+    b = rng.standard_normal(n) * 10.0 ** rng.uniform(-12, 12, n)
+    b[:8] = [1.0, -1.0, 3.0, 0.1, 1e-300 * 1e292, 7.0, 2.0 ** 52, 1.0 / 3.0]
+    ta = torch.tensor(a, device="cuda")
+    tb = torch.tensor(b, device="cuda")
+    q = torch.empty_like(ta)
+    r = torch.empty_like(ta)
+    es.es_selftest_division(ta, tb, q, r)
+    torch.cuda.synchronize()
+    qn, rn = q.cpu().numpy(), r.cpu().numpy()
+    assert np.all(np.abs(qn - a / b) <= np.spacing(np.abs(a / b)))
+    assert np.all(np.abs(rn - 1.0 / b) <= np.spacing(np.abs(1.0 / b)))
