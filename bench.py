@@ -49,6 +49,8 @@ def parse():
                     help="also run the precision-form sweep: 2D sine 1024^2 and the vortex 64^2..1024^2, both forms")
     ap.add_argument("--learned", action="store_true",
                     help="also train and evaluate the learned warm start (512^2, about 3 minutes)")
+    ap.add_argument("--nn-inference", type=int, default=0,
+                    help="also time the warm-start network's inference on one n x n image (0: skip)")
     ap.add_argument("--learned-n", type=int, default=512)
     ap.add_argument("--learned-seeds", type=int, default=20, help="plain runs; the last two are held out")
     ap.add_argument("--learned-steps", type=int, default=100)
@@ -429,6 +431,30 @@ def measure_learned(args, dev):
             "full_runs": run, "nn_inference_ms": t_inf}
 
 
+def measure_nn_inference(n, dev):
+    """The warm-start network (4 conv3x3 layers, 32 channels, seeded weights) on one n x n feature
+    image: tensor-core path and FP32 CUDA-core path, CUDA events over 20 inferences."""
+    import torch
+
+    from paper_2407_05568_gb300 import learned
+    net = learned.WarmStartNet(hidden=32, layers=4, seed=0, device=dev)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((1, 4, n, n), generator=g).to(dev)
+    res = {"n": n, "flops_per_inference": 2 * 9 * (4 * 32 + 32 * 32 * 2 + 32 * 2) * n * n}
+    for name, fn in (("tensor_cores_bf16_inputs", net.infer), ("cuda_cores_fp32", net.forward)):
+        for _ in range(3):
+            fn(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            fn(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        res[name] = {"ms": ms, "tflops": res["flops_per_inference"] / (ms * 1e-3) / 1e12}
+    return res
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -451,6 +477,7 @@ def run_gpu(args):
         batched = measure_batch(args, dev, stream)
     learned_res = measure_learned(args, dev) if args.learned and rank == 0 else None
     sweep_res = measure_precision_sweep(args, dev) if args.precision_sweep and rank == 0 else None
+    nn_res = measure_nn_inference(args.nn_inference, dev) if args.nn_inference > 0 and rank == 0 else None
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -477,8 +504,10 @@ def run_gpu(args):
             line["learned"] = learned_res
         if sweep_res is not None:
             line["precision_sweep"] = sweep_res
+        if nn_res is not None:
+            line["nn_inference"] = nn_res
         if not args.no_cpu_baseline:
-            sec, k = time_oracle(workload(args.n), 8)
+            sec, k = time_oracle(workload(args.n), 24)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),
                                     "kind": "oracle",
                                     "sample": f"{k} full steps of the same {args.n}x{args.n} workload from t = 0"}
@@ -502,8 +531,8 @@ FLOPS_PER_NODE_STAGE_2D = None
 
 TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16)}, "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
-# kernel as it is now (none since the last kernel change); other shapes and sizes were not captured
-TRAFFIC_200 = {}
+# kernel as it is now; other shapes and sizes were not captured
+TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3051520 + 0, "stage_kernel_mixed<2,20,8>": 2323968 + 0}
 
 
 def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
