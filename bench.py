@@ -377,14 +377,14 @@ def measure_precision_sweep(args, dev):
 
 def measure_learned(args, dev):
     """The learned warm start on the 2D vdW Riemann problem: snapshots of plain runs (Jacobi to
-    max change < 0.02 cells, at most 64 sweeps), training, and the plain against the
+    max change < 0.02 cells, at most 300 sweeps), training, and the plain against the
     warm-started solve on held-out seeds (same states, then two full runs)."""
     import time
 
     import torch
 
     from paper_2407_05568_gb300 import learned
-    n, eps, mu = args.learned_n, 0.02, 64
+    n, eps, mu = args.learned_n, 0.02, 300
     seeds = list(range(100, 100 + args.learned_seeds))
     train_seeds, test_seeds = seeds[:-2], seeds[-2:]
     t0 = time.perf_counter()

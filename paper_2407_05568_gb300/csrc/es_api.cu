@@ -20,6 +20,7 @@ struct es_ctx {
     cudaStream_t stream;              // the caller's stream
     cudaStream_t s_enq;               // stream the enqueue helpers launch on (capture stream while capturing)
     cudaStream_t cap_stream;          // private stream for graph capture (the legacy stream cannot capture)
+    cudaStream_t body_stream;         // captures the body of a graph while-loop
     GridParams g;
     Gas gas;
     Weno weno;
@@ -52,6 +53,7 @@ struct es_ctx {
     int graph_kernels;
     int capturing;
     int capture_count;
+    int loop_failed;                  // a graph while-loop could not be built (unrolled sweeps used)
     int64_t launches;
     char msg[256];
 };
@@ -173,8 +175,9 @@ int enqueue_net(es_ctx* c, const double* om, const double* xn) {
         const bool last = l == c->nn_layers - 1;
         const int cout = last ? c->p.dim : c->nn_hidden;
         float* out = last ? c->nn_out : ((l & 1) ? c->act1 : c->act0);
-        cudaError_t e = nn_conv_forward_bf16(in, c->nn_wbf + woff, c->nn_b + boff, out, 1, cin, cout, c->g.n2,
-                                             c->g.n1, last ? 0 : 1, s);
+        // layer inputs after the first and outputs before the last stay bf16 [H][W][C]
+        cudaError_t e = nn_conv_forward_bf16_fmt(in, l > 0, c->nn_wbf + woff, c->nn_b + boff, out, !last, 1, cin,
+                                                 cout, c->g.n2, c->g.n1, last ? 0 : 1, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "warm-start network");
         count(c);
         woff += size_t(cout) * cin * 9;
@@ -185,6 +188,41 @@ int enqueue_net(es_ctx* c, const double* om, const double* xn) {
     k_warm_start<<<G, B, 0, s>>>(c->g, xn, c->nn_out, c->xw);
     count(c);
     return ES_OK;
+}
+
+// While-loop node in the step graph being captured on c->s_enq; its body (one k_jacobi_loop
+// launch) is captured on c->body_stream.  Each pass of the loop runs one sweep; the kernel sets
+// the loop condition.
+int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t graph;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    if (cudaStreamGetCaptureInfo(c->s_enq, &st, nullptr, &graph, &deps, &edges, &ndeps) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+        return ES_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) return ES_ERR_CUDA;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, deps, edges, ndeps, &cp) != cudaSuccess) return ES_ERR_CUDA;
+    if (cudaStreamUpdateCaptureDependencies(c->s_enq, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+        cudaSuccess)
+        return ES_ERR_CUDA;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return ES_ERR_CUDA;
+    k_jacobi_loop<<<c->grid1d, 256, 0, c->body_stream>>>(c->g, om, xn, c->xa, c->xb, c->dev, c->p.jacobi_eps,
+                                                         c->p.jacobi_sweeps, h);
+    count(c);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->body_stream, &out);
+    return e == cudaSuccess ? ES_OK : ES_ERR_CUDA;
 }
 
 // Jacobi sweeps from x_n, or guarded from x_start (the first sweep runs from both starts
@@ -201,6 +239,11 @@ void enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double*
         k_pick<<<1, 32, 0, s>>>(c->dev, check, eps, ratio);
         count(c, 3);
         k0 = 1;
+    }
+    if (check && c->capturing && c->p.jacobi_sweeps > k0) {
+        // the remaining sweeps as a while-loop node: no launches after convergence
+        if (enqueue_sweep_loop(c, om, xn) == ES_OK) return;
+        c->loop_failed = 1;
     }
     for (int k = k0; k < c->p.jacobi_sweeps; ++k) {
         k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, k, 0, c->dev, check, RED_JAC, 1, eps);
@@ -464,6 +507,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
 #undef ALLOC
     {
         cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaStreamCreate"); goto fail_out; }
         e = cudaMallocHost((void**)&c->hpin, sizeof(DevScalars));
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaMallocHost"); goto fail_out; }
@@ -486,6 +530,7 @@ void es_destroy(es_ctx* c) {
     if (!c) return;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->body_stream) cudaStreamDestroy(c->body_stream);
     void* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->om0, c->om1,
                     c->xa, c->xb, c->xdot, c->hJU, c->hJ, c->hx, c->fdisp, c->fxd,
                     c->nn_wbf, c->nn_b, c->feat, c->act0, c->act1, c->nn_out, c->xw};

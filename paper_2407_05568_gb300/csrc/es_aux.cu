@@ -321,25 +321,11 @@ __device__ __forceinline__ bool fixed_node(const GridParams& g, int i, int j) {
     return f;
 }
 
-// One Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0.
-// Sweep k >= 1 reads buf[(pick + k - 1) % 2] and writes buf[(pick + k) % 2]; sweep 0 reads
-// `first` (x_n or the warm start) and writes buf[dst0].  Once the iteration has converged
-// (d->conv) the remaining sweeps return at once.  With `check`, the grid-wide max change
-// goes to red[slot]; if `judge`, the last block to finish compares it with eps.
-__global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
-                         int dst0, DevScalars* d, int check, int slot, int judge, double eps) {
-    if (d->conv) return;
+// One Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0
+// from xin into xout; returns this thread's max change
+__device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double* omega, const double* xin,
+                                              double* xout) {
     const int N = g.n1 * g.n2;
-    const double* xin;
-    double* xout;
-    if (k == 0) {
-        xin = first;
-        xout = dst0 ? xb : xa;
-    } else {
-        const int src = (d->pick + k - 1) & 1;
-        xin = src ? xb : xa;
-        xout = src ? xa : xb;
-    }
     double chg = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
@@ -364,6 +350,27 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* first,
             xout[c * N + id] = xv;
         }
     }
+    return chg;
+}
+
+// Sweep k of the iteration.  Sweep k >= 1 reads buf[(pick + k - 1) % 2] and writes
+// buf[(pick + k) % 2]; sweep 0 reads `first` (x_n or the warm start) and writes buf[dst0].  Once
+// the iteration has converged (d->conv) the remaining sweeps return at once.  With `check`, the
+// grid-wide max change goes to red[slot]; if `judge`, the last block to finish compares it with eps.
+__global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
+                         int dst0, DevScalars* d, int check, int slot, int judge, double eps) {
+    if (d->conv) return;
+    const double* xin;
+    double* xout;
+    if (k == 0) {
+        xin = first;
+        xout = dst0 ? xb : xa;
+    } else {
+        const int src = (d->pick + k - 1) & 1;
+        xin = src ? xb : xa;
+        xout = src ? xa : xb;
+    }
+    double chg = jacobi_sweep(g, omega, xin, xout);
     if (check) {
         chg = block_reduce_max(chg);
         if (threadIdx.x == 0) {
@@ -381,6 +388,42 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* first,
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (k > 0 || slot == RED_JAC)) atomicAdd(&d->sweeps, 1);
+}
+
+// The body of a graph while-loop over the sweeps with a tolerance: sweep k = d->sweeps (the
+// same buffers as k_jacobi), and the last block to finish judges the change, counts the sweep
+// and sets the loop's condition: another sweep while not converged and fewer than mu sweeps.
+__global__ void k_jacobi_loop(GridParams g, const double* omega, const double* xn, double* xa, double* xb,
+                              DevScalars* d, double eps, int mu, cudaGraphConditionalHandle h) {
+    if (d->conv || d->sweeps >= mu) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const int k = d->sweeps;
+    const double* xin;
+    double* xout;
+    if (k == 0) {
+        xin = xn;
+        xout = xa;
+    } else {
+        const int src = (d->pick + k - 1) & 1;
+        xin = src ? xb : xa;
+        xout = src ? xa : xb;
+    }
+    double chg = block_reduce_max(jacobi_sweep(g, omega, xin, xout));
+    if (threadIdx.x == 0) {
+        atomic_max_pos(&d->red[RED_JAC], chg);
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&d->done, 1u);
+        if (ticket == gridDim.x - 1) {
+            const double c = __longlong_as_double((long long)atomicAdd(&d->red[RED_JAC], 0ULL));
+            if (c < eps) d->conv = 1;
+            d->red[RED_JAC] = 0ULL;
+            d->done = 0u;
+            d->sweeps = k + 1;
+            cudaGraphSetConditional(h, (d->conv == 0 && k + 1 < mu) ? 1u : 0u);
+        }
+    }
 }
 
 // Guarded warm start: the first sweep ran from x_n (into buf[0], change c0 in red[RED_JAC]) and

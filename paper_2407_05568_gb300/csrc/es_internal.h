@@ -98,5 +98,8 @@ cudaError_t nn_conv_forward_f32(const float* in, const float* wf, const float* b
                                 int Cout, int H, int W, int act, cudaStream_t s);
 cudaError_t nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
                                  int Cout, int H, int W, int act, cudaStream_t s);
+// the same layer with bf16 [B][H][W][C] input and/or output (the context's inference buffers)
+cudaError_t nn_conv_forward_bf16_fmt(const void* in, bool in_nhwc, const uint16_t* w, const float* bias, void* out,
+                                     bool out_nhwc, int B, int Cin, int Cout, int H, int W, int act, cudaStream_t s);
 
 }  // namespace es

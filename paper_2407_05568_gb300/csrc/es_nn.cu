@@ -228,10 +228,13 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, cons
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int CIN, int NPAD>
-__global__ void __launch_bounds__(128) k_conv_fwd_tc(const float* __restrict__ in,
+// IN_NHWC / OUT_NHWC: the layer input / output as bf16 [B][H][W][C] (the context's inference
+// buffers between layers: what the next layer's staging would round to anyway) instead of FP32
+// [B][C][H][W].  The results are the same either way.
+template <int CIN, int NPAD, bool IN_NHWC, bool OUT_NHWC>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(const void* __restrict__ in_,
                                                     const __nv_bfloat16* __restrict__ w,
-                                                    const float* __restrict__ bias, float* __restrict__ out,
+                                                    const float* __restrict__ bias, void* __restrict__ out_,
                                                     int Cout, int H, int W, int act) {
     constexpr int K = 9 * CIN;
     constexpr int KP = (K + 15) / 16 * 16;
@@ -253,17 +256,36 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const float* __restrict__ i
         }
         ws[n * KSW + k0 / 2] = pack_bf16(v[0], v[1]);
     }
-    const float* inb = in + size_t(b) * CIN * HW;
-    for (int idx = tid; idx < HALO * HALO * (CIN / 2); idx += 128) {
-        const int p = idx % (HALO * HALO), cw = idx / (HALO * HALO);
-        const int yy = y0 - 1 + p / HALO, xx = x0 - 1 + p % HALO;
-        float v0 = 0.0f, v1 = 0.0f;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            const size_t o = size_t(yy) * W + xx;
-            v0 = inb[(2 * cw) * HW + o];
-            v1 = inb[(2 * cw + 1) * HW + o];
+    if (IN_NHWC) {
+        // CIN/2 words per pixel, copied 4 words (16 bytes) at a time when CIN is a multiple of 8
+        const uint32_t* inb = reinterpret_cast<const uint32_t*>(in_) + size_t(b) * HW * (CIN / 2);
+        constexpr int VW = (CIN % 8 == 0) ? 4 : 1;
+        for (int idx = tid; idx < HALO * HALO * (CIN / 2 / VW); idx += 128) {
+            const int p = idx / (CIN / 2 / VW), q = idx % (CIN / 2 / VW);
+            const int yy = y0 - 1 + p / HALO, xx = x0 - 1 + p % HALO;
+            const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+            const size_t o = (size_t(yy) * W + xx) * (CIN / 2) + q * VW;
+            if (VW == 4) {
+                const uint4 v = ok ? *reinterpret_cast<const uint4*>(inb + o) : make_uint4(0u, 0u, 0u, 0u);
+                uint32_t* d = xs + p * PSW + q * 4;
+                d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+            } else {
+                xs[p * PSW + q] = ok ? inb[o] : 0u;
+            }
         }
-        xs[p * PSW + cw] = pack_bf16(v0, v1);
+    } else {
+        const float* inb = reinterpret_cast<const float*>(in_) + size_t(b) * CIN * HW;
+        for (int idx = tid; idx < HALO * HALO * (CIN / 2); idx += 128) {
+            const int p = idx % (HALO * HALO), cw = idx / (HALO * HALO);
+            const int yy = y0 - 1 + p / HALO, xx = x0 - 1 + p % HALO;
+            float v0 = 0.0f, v1 = 0.0f;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const size_t o = size_t(yy) * W + xx;
+                v0 = inb[(2 * cw) * HW + o];
+                v1 = inb[(2 * cw + 1) * HW + o];
+            }
+            xs[p * PSW + cw] = pack_bf16(v0, v1);
+        }
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
@@ -299,22 +321,42 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const float* __restrict__ i
             for (int nt = 0; nt < NT; ++nt) mma_bf16_16816(acc[mt][nt], af, bf[nt]);
         }
     }
-    float* ob = out + size_t(b) * Cout * HW;
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
         const int y = y0 + warp * 4 + mt;
         if (y >= H) continue;
+        if (OUT_NHWC) {
+            // channel pairs (co, co + 1) as one bf16x2 word; Cout is even here
+            uint32_t* ob = reinterpret_cast<uint32_t*>(out_) + size_t(b) * HW * (Cout / 2);
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
+            for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int x = x0 + g + (e >= 2 ? 8 : 0);
-                const int co = nt * 8 + 2 * t + (e & 1);
-                if (co < Cout && x < W) {
-                    const float v = acc[mt][nt][e] + bias[co];
-                    ob[co * HW + size_t(y) * W + x] = act ? tanhf(v) : v;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int x = x0 + g + hh * 8;
+                    const int co = nt * 8 + 2 * t;
+                    if (co < Cout && x < W) {
+                        float v0 = acc[mt][nt][2 * hh] + bias[co], v1 = acc[mt][nt][2 * hh + 1] + bias[co + 1];
+                        if (act) {
+                            v0 = tanhf(v0);
+                            v1 = tanhf(v1);
+                        }
+                        ob[(size_t(y) * W + x) * (Cout / 2) + co / 2] = pack_bf16(v0, v1);
+                    }
                 }
-            }
+        } else {
+            float* ob = reinterpret_cast<float*>(out_) + size_t(b) * Cout * HW;
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int x = x0 + g + (e >= 2 ? 8 : 0);
+                    const int co = nt * 8 + 2 * t + (e & 1);
+                    if (co < Cout && x < W) {
+                        const float v = acc[mt][nt][e] + bias[co];
+                        ob[co * HW + size_t(y) * W + x] = act ? tanhf(v) : v;
+                    }
+                }
+        }
     }
 }
 
@@ -378,26 +420,44 @@ cudaError_t nn_bf16_to_float(const uint16_t* w, float* f, size_t n, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
-                                 int Cout, int H, int W, int act, cudaStream_t s) {
-    const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
+template <bool IN_NHWC, bool OUT_NHWC>
+cudaError_t conv_tc_launch(const void* in, const __nv_bfloat16* wb, const float* bias, void* out, int B, int Cin,
+                           int Cout, int H, int W, int act, cudaStream_t s) {
     dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS, B);
+#define ES_TC(CI, NP) k_conv_fwd_tc<CI, NP, IN_NHWC, OUT_NHWC><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act)
     if (Cout <= 8) {
         switch (Cin) {
-            case 2: k_conv_fwd_tc<2, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
-            case 4: k_conv_fwd_tc<4, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
-            case 32: k_conv_fwd_tc<32, 8><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 2: ES_TC(2, 8); break;
+            case 4: ES_TC(4, 8); break;
+            case 32: ES_TC(32, 8); break;
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (Cin) {
-            case 2: k_conv_fwd_tc<2, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
-            case 4: k_conv_fwd_tc<4, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
-            case 32: k_conv_fwd_tc<32, 32><<<grid, 128, 0, s>>>(in, wb, bias, out, Cout, H, W, act); break;
+            case 2: ES_TC(2, 32); break;
+            case 4: ES_TC(4, 32); break;
+            case 32: ES_TC(32, 32); break;
             default: return cudaErrorInvalidValue;
         }
     }
+#undef ES_TC
     return cudaGetLastError();
+}
+
+cudaError_t nn_conv_forward_bf16(const float* in, const uint16_t* w, const float* bias, float* out, int B, int Cin,
+                                 int Cout, int H, int W, int act, cudaStream_t s) {
+    return conv_tc_launch<false, false>(in, (const __nv_bfloat16*)w, bias, out, B, Cin, Cout, H, W, act, s);
+}
+
+cudaError_t nn_conv_forward_bf16_fmt(const void* in, bool in_nhwc, const uint16_t* w, const float* bias, void* out,
+                                     bool out_nhwc, int B, int Cin, int Cout, int H, int W, int act, cudaStream_t s) {
+    const __nv_bfloat16* wb = (const __nv_bfloat16*)w;
+    if (out_nhwc && (Cout & 1)) return cudaErrorInvalidValue;
+    if (in_nhwc)
+        return out_nhwc ? conv_tc_launch<true, true>(in, wb, bias, out, B, Cin, Cout, H, W, act, s)
+                        : conv_tc_launch<true, false>(in, wb, bias, out, B, Cin, Cout, H, W, act, s);
+    return out_nhwc ? conv_tc_launch<false, true>(in, wb, bias, out, B, Cin, Cout, H, W, act, s)
+                    : conv_tc_launch<false, false>(in, wb, bias, out, B, Cin, Cout, H, W, act, s);
 }
 
 cudaError_t nn_conv_forward_f32(const float* in, const float* wf, const float* bias, float* out, int B, int Cin,

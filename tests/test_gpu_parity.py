@@ -323,3 +323,26 @@ def test_fp64_division_within_an_ulp_of_ieee():
     qn, rn = q.cpu().numpy(), r.cpu().numpy()
     assert np.all(np.abs(qn - a / b) <= np.spacing(np.abs(a / b)))
     assert np.all(np.abs(rn - 1.0 / b) <= np.spacing(np.abs(1.0 / b)))
+
+
+def test_step_parity_jacobi_tolerance_graph_loop():
+    """Jacobi to a tolerance inside the step graph (a while-loop node: one sweep per pass, the
+    kernel ends the loop): two steps against the oracle, the same sweep counts."""
+    from paper_2407_05568_gb300 import es
+    w = _ragged_riemann()
+    w["mesh"] = dict(w["mesh"], sweeps=40, eps=0.08 * w["dxi"][0])     # 24 and 23 sweeps: ends by tolerance
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w)
+    t = 0.0
+    sweeps_o = 0
+    for _ in range(2):
+        JU_o, J_o, x_o, t, info = stepper.step(sch, mc, JU_o, J_o, x_o, t, w["t_end"], w["cfl"])
+        sweeps_o += info["sweeps"]
+    es.es_set_time(ctx, 0.0)
+    es.es_mesh_stats(ctx, reset=True)
+    es.es_steps(ctx, JU, J, xt, 2, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    sw, solves, _ = es.es_mesh_stats(ctx)
+    assert solves == 2 and sw == sweeps_o and sw < 80
+    assert rel_l1(to_np(JU), JU_o) < 2e-12
+    assert rel_l1(to_np(xt), x_o) < 2e-12
