@@ -529,7 +529,8 @@ def pin(a):
 FLOPS_PER_NODE_STAGE_2D = None
 
 
-TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16)}, "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8)}}
+TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12)},
+         "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
 # kernel as it is now; other shapes and sizes were not captured
 TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3051520 + 0, "stage_kernel_mixed<2,20,8>": 2323968 + 0}
