@@ -381,6 +381,16 @@ __device__ __forceinline__ void load_node_f(float* S, int NB, int b, const Stage
 template <int DIM>
 __device__ __forceinline__ void stage_disp(const StageParams& P, int gi, int gj, float cdt, float* ds, float* xd) {
     const size_t N = P.fcs;
+    if (gi >= 0 && gi < P.n1 && (DIM == 1 || (gj >= 0 && gj < P.n2))) {     // interior: plain loads
+        const size_t id = size_t(DIM == 2 ? gj : 0) * P.n1 + gi;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float xdk = P.fxdot ? P.fxdot[k * N + id] : 0.0f;
+            ds[k] = P.fdisp[k * N + id] + cdt * xdk;
+            xd[k] = xdk;
+        }
+        return;
+    }
     const GhostTerms ti = ghost_terms(gi, P.n1, P.bc[0]);
     GhostTerms tj;
     if (DIM == 2) tj = ghost_terms(gj, P.n2, P.bc[1]);
@@ -481,7 +491,9 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
     for (int c = 0; c <= NC; ++c) acc[c] = 0.0f;
     const int tx = tid % BX, ty = tid / BX;
 
-#pragma unroll 1
+    // both directions unrolled: line lengths and strides are constants, so the index
+    // divisions below compile to multiplications
+#pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const int nlines = k == 0 ? (DIM == 2 ? BY : 1) : BX;
         const int LB = k == 0 ? BX : BY;
