@@ -137,14 +137,16 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         const size_t P = size_t(g.dim + 2) * N;
-        const double iJ = 1.0 / ld_state(J, N, id);
+        const double iJ = rcp_nr(ld_state(J, N, id));
         const double rho = ld_state(JU, P, id) * iJ;
-        const double v1 = ld_state(JU, P, N + id) * iJ / rho;
-        const double v2 = g.dim == 2 ? ld_state(JU, P, 2 * N + id) * iJ / rho : 0.0;
+        const double irho = rcp_nr(rho);
+        const double v1 = ld_state(JU, P, N + id) * iJ * irho;
+        const double v2 = g.dim == 2 ? ld_state(JU, P, 2 * N + id) * iJ * irho : 0.0;
         const double E = ld_state(JU, P, (g.dim + 1) * N + id) * iJ;
-        const double T = (E / rho - 0.5 * (v1 * v1 + v2 * v2) + G.a * rho) / G.cv;
+        const double T = (E * irho - 0.5 * (v1 * v1 + v2 * v2) + G.a * rho) * G.icv;
         const double om = 1.0 - G.b * rho;
-        const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
+        const double iom = rcp_nr(om);
+        const double c2 = (1.0 + G.delta) * G.R * T * (iom * iom) - 2.0 * G.a * rho;
         const double c = sqrt(fmax(c2, 0.0));
         double tot;
         if (g.dim == 1) {
@@ -199,20 +201,22 @@ __global__ void k_mon_fields(GridParams g, Gas G, const TS* JU, const TS* J, dou
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const size_t P = size_t(g.dim + 2) * N;
-        const double iJ = 1.0 / ld_state(J, N, id);
+        const double iJ = rcp_nr(ld_state(J, N, id));
         const double rho = ld_state(JU, P, id) * iJ;
+        const double irho = rcp_nr(rho);
         double ke = 0.0;
         for (int k = 0; k < g.dim; ++k) {
-            const double v = ld_state(JU, P, (1 + k) * N + id) * iJ / rho;
+            const double v = ld_state(JU, P, (1 + k) * N + id) * iJ * irho;
             ke += v * v;
         }
         const double E = ld_state(JU, P, (g.dim + 1) * N + id) * iJ;
-        const double T = (E / rho - 0.5 * ke + G.a * rho) / G.cv;
+        const double T = (E * irho - 0.5 * ke + G.a * rho) * G.icv;
         const double om = 1.0 - G.b * rho;
-        const double c2 = (1.0 + G.delta) * G.R * T / (om * om) - 2.0 * G.a * rho;
-        const double pnn3 = (1.0 + G.delta) * (2.0 + G.delta) * G.R * T / (om * om * om) - 6.0 * G.a * rho;
+        const double iom = rcp_nr(om);
+        const double c2 = (1.0 + G.delta) * G.R * T * (iom * iom) - 2.0 * G.a * rho;
+        const double pnn3 = (1.0 + G.delta) * (2.0 + G.delta) * G.R * T * (iom * iom * iom) - 6.0 * G.a * rho;
         rhoF[id] = rho;
-        GF[id] = pnn3 / (2.0 * c2);
+        GF[id] = div_nr(pnn3, 2.0 * c2);
     }
 }
 
@@ -344,8 +348,9 @@ __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double
             for (int c = 0; c < g.dim; ++c)
                 num[c] += wp * coord_at(g, xin, i + di, j + dj, c) + wm * coord_at(g, xin, i - di, j - dj, c);
         }
+        const double iden = rcp_nr(den);
         for (int c = 0; c < g.dim; ++c) {
-            const double xv = num[c] / den;
+            const double xv = num[c] * iden;
             chg = fmax(chg, fabs(xv - xin[c * N + id]));
             xout[c * N + id] = xv;
         }
@@ -454,8 +459,8 @@ __global__ void k_limiter(GridParams g, const double* xn, const double* xa, cons
         for (int k = 0; k < g.dim; ++k) {
             const double dx = xit[k * N + id] - xn[k * N + id];
             const int di = k == 0, dj = k == 1;
-            if (dx < 0.0) m = fmin(m, -(xn[k * N + id] - coord_at(g, xn, i - di, j - dj, k)) / (2.0 * dx));
-            else if (dx > 0.0) m = fmin(m, (coord_at(g, xn, i + di, j + dj, k) - xn[k * N + id]) / (2.0 * dx));
+            if (dx < 0.0) m = fmin(m, div_nr(-(xn[k * N + id] - coord_at(g, xn, i - di, j - dj, k)), 2.0 * dx));
+            else if (dx > 0.0) m = fmin(m, div_nr(coord_at(g, xn, i + di, j + dj, k) - xn[k * N + id], 2.0 * dx));
         }
     }
     m = block_reduce_min(m);
