@@ -192,7 +192,11 @@ int enqueue_net(es_ctx* c, const double* om, const double* xn) {
 
 // While-loop node in the step graph being captured on c->s_enq; its body (one k_jacobi_loop
 // launch) is captured on c->body_stream.  Each pass of the loop runs one sweep; the kernel sets
-// the loop condition.
+// the loop condition (to 0 once converged or after mu sweeps, so the loop always ends).
+// Returns LOOP_OK, LOOP_UNTOUCHED (nothing added: the caller may unroll the sweeps instead) or
+// LOOP_BROKEN (a node was added but its body could not be built: the capture must be abandoned,
+// since a while-node without the kernel that clears its condition would never end).
+enum { LOOP_OK = 0, LOOP_UNTOUCHED = 1, LOOP_BROKEN = 2 };
 int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
     cudaStreamCaptureStatus st;
     cudaGraph_t graph;
@@ -201,33 +205,39 @@ int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
     size_t ndeps = 0;
     if (cudaStreamGetCaptureInfo(c->s_enq, &st, nullptr, &graph, &deps, &edges, &ndeps) != cudaSuccess ||
         st != cudaStreamCaptureStatusActive)
-        return ES_ERR_CUDA;
+        return LOOP_UNTOUCHED;
     cudaGraphConditionalHandle h;
-    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) return ES_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return LOOP_UNTOUCHED;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    if (cudaGraphAddNode(&node, graph, deps, edges, ndeps, &cp) != cudaSuccess) return ES_ERR_CUDA;
+    if (cudaGraphAddNode(&node, graph, deps, edges, ndeps, &cp) != cudaSuccess) return LOOP_UNTOUCHED;
     if (cudaStreamUpdateCaptureDependencies(c->s_enq, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
         cudaSuccess)
-        return ES_ERR_CUDA;
+        return LOOP_BROKEN;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     if (cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
-        return ES_ERR_CUDA;
+        return LOOP_BROKEN;
     k_jacobi_loop<<<c->grid1d, 256, 0, c->body_stream>>>(c->g, om, xn, c->xa, c->xb, c->dev, c->p.jacobi_eps,
                                                          c->p.jacobi_sweeps, h);
+    const cudaError_t el = cudaGetLastError();
     count(c);
     cudaGraph_t out = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->body_stream, &out);
-    return e == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+    size_t nodes = 0;
+    if (el != cudaSuccess || e != cudaSuccess || cudaGraphGetNodes(body, nullptr, &nodes) != cudaSuccess ||
+        nodes != 1)
+        return LOOP_BROKEN;
+    return LOOP_OK;
 }
 
 // Jacobi sweeps from x_n, or guarded from x_start (the first sweep runs from both starts
 // and the start whose sweep changes the mesh less is continued)
-void enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio) {
+int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const int check = c->p.jacobi_eps > 0.0;
@@ -242,13 +252,16 @@ void enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double*
     }
     if (check && c->capturing && c->p.jacobi_sweeps > k0) {
         // the remaining sweeps as a while-loop node: no launches after convergence
-        if (enqueue_sweep_loop(c, om, xn) == ES_OK) return;
+        const int r = enqueue_sweep_loop(c, om, xn);
+        if (r == LOOP_OK) return ES_OK;
+        if (r == LOOP_BROKEN) return fail(c, ES_ERR_CUDA, "graph while-loop of the Jacobi sweeps");
         c->loop_failed = 1;
     }
     for (int k = k0; k < c->p.jacobi_sweeps; ++k) {
         k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, k, 0, c->dev, check, RED_JAC, 1, eps);
         count(c);
     }
+    return ES_OK;
 }
 
 // monitor -> filter -> [warm start] -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
@@ -262,7 +275,8 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
         if (rc) return rc;
         x_start = c->xw;
     }
-    enqueue_jacobi(c, om, xn, x_start, c->nn_ratio);
+    int rc = enqueue_jacobi(c, om, xn, x_start, c->nn_ratio);
+    if (rc) return rc;
     k_limiter<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev);
     k_velocity<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev, xdot);
     count(c, 2);
@@ -653,7 +667,8 @@ int es_mesh_solve(es_ctx* c, const void* JU, const void* J, const double* xn, co
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
     const double* om = enqueue_monitor(c, JU, J);
-    enqueue_jacobi(c, om, xn, x_start, guard_ratio);
+    const int rj = enqueue_jacobi(c, om, xn, x_start, guard_ratio);
+    if (rj) return rj;
     k_jacobi_out<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, c->xa, c->xb, c->dev, x_out, disp_out);
     count(c);
     CK(cudaGetLastError(), "mesh kernels");
@@ -790,7 +805,10 @@ int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) 
         c->s_enq = c->stream;
         c->capturing = 0;
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (rc) return rc;
+        if (rc) {
+            if (e == cudaSuccess && graph) cudaGraphDestroy(graph);    // never instantiated
+            return rc;
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
         e = cudaGraphInstantiate(&c->gexec, graph, 0);
         cudaGraphDestroy(graph);
