@@ -30,7 +30,13 @@ struct TileF {
     static constexpr int NF2 = DIM == 2 ? BX * (BY + 1) : 0;
     static constexpr int NF = NF1 > NF2 ? NF1 : NF2;
     static constexpr int PAIR_FLOATS = (NP * NC > 4 * NB) ? NP * NC : 4 * NB;
-    static constexpr size_t SMEM = sizeof(float) * (size_t(G_COUNT) * NB + PAIR_FLOATS + NF * (NC + 1));
+    // entropy-variable jumps between neighbours along each line (box positions q, q + 1), shared
+    // by the faces whose stencils contain them
+    static constexpr int NJ1 = (DIM == 2 ? BY : 1) * (BX + 5);
+    static constexpr int NJ2 = DIM == 2 ? BX * (BY + 5) : 0;
+    static constexpr int NJ = NJ1 > NJ2 ? NJ1 : NJ2;
+    static constexpr size_t SMEM =
+        sizeof(float) * (size_t(G_COUNT) * NB + PAIR_FLOATS + NF * (NC + 1) + size_t(NJ) * NC);
     static_assert(NT >= BX * (DIM == 2 ? BY : 1) && NT % 32 == 0, "threads cover the tile");
 };
 
@@ -209,7 +215,7 @@ __device__ __forceinline__ void entropy_jump(const float* S, int NB, int i, int 
 template <int DIM>
 __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l, int step, float nx, float ny,
                                                    float xtf, const GasF& G, const WenoF& Wc, float* out,
-                                                   DevStatus* st) {
+                                                   DevStatus* st, const float* JB, int NJ, int jq) {
     const int r = l + step;
     const float ilr = inv_log_mean_f(S[G_RHO * NB + l], S[G_RHO * NB + r]);
     const float rho = 1.0f / ilr;
@@ -247,18 +253,39 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
     const float Lam = fabsf(xtf + L * vn) + L * c;
     const float Hm = H - vn * c, Hp = H + vn * c;
 
-    // W_j - W_l = R^T T (V_j - V_l) at nodes l-2 .. l+3 (zero at l itself)
+    // W_j - W_l = R^T T (V_j - V_l) at nodes l-2 .. l+3 (zero at l itself); V_j - V_l is the sum
+    // of the neighbour jumps between them (JB[c][jq + q] = V_{q+1} - V_q along the line, the
+    // face's left node at jq + 0)
     float W[6][DIM + 2];
     float aTV[DIM + 2];
+    float cum[DIM + 2];
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) {
+        W[2][m] = 0.0f;
+        cum[m] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 3; o < 6; ++o)
+#pragma unroll
+        for (int m = 0; m < DIM + 2; ++m) {
+            cum[m] += JB[m * NJ + jq + (o - 3)];
+            W[o][m] = cum[m];
+        }
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) cum[m] = 0.0f;
+#pragma unroll
+    for (int o = 1; o >= 0; --o)
+#pragma unroll
+        for (int m = 0; m < DIM + 2; ++m) {
+            cum[m] -= JB[m * NJ + jq + (o - 2)];
+            W[o][m] = cum[m];
+        }
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
-        if (o == 2) {
-#pragma unroll
-            for (int m = 0; m < DIM + 2; ++m) W[o][m] = 0.0f;
-            continue;
-        }
+        if (o == 2) continue;
         float dV[DIM + 2];
-        entropy_jump<DIM>(S, NB, l, l + (o - 2) * step, G, dV);
+#pragma unroll
+        for (int m = 0; m < DIM + 2; ++m) dV[m] = W[o][m];
         if (DIM == 1) {
             const float V0 = dV[0], V1 = cs * dV[1], V2 = dV[2];
             W[o][0] = sA * (V0 + (vn - c) * V1 + Hm * V2);
@@ -428,6 +455,7 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
     float* S = smemf;
     float* PB = smemf + G_COUNT * NB;
     float* FB = PB + TL::PAIR_FLOATS;
+    float* JB = FB + TL::NF * (NC + 1);
     const int tid = threadIdx.x;
     const float cdt = P.fcst * dt;
     const float idx1 = P.finv_dxi[0], idx2 = P.finv_dxi[1];
@@ -518,6 +546,18 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
 #pragma unroll
             for (int c = 0; c < NC; ++c) PB[c * TL::NP + t] = f[c];
         }
+        if (P.diss) {
+            // neighbour jumps V_{q+1} - V_q, q = 0 .. LB+4 along each line (eq. jumpV)
+            for (int t = tid; t < nlines * (LB + 5); t += NT) {
+                const int line = t / (LB + 5), q = t % (LB + 5);
+                const int base = k == 0 ? (DIM == 2 ? (3 + line) * GX : 0) : 3 + line;
+                const int l = base + q * step;
+                float dV[NC];
+                entropy_jump<DIM>(S, NB, l, l + step, G, dV);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) JB[c * TL::NJ + t] = dV[c];
+            }
+        }
         __syncthreads();
         for (int t = tid; t < nlines * (LB + 1); t += NT) {
             const int line = t / (LB + 1), f = t % (LB + 1);
@@ -546,7 +586,8 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
                 const float ny = 0.5f * (S[fNy * NB + l] + S[fNy * NB + l + step]);
                 const float xtf = 0.5f * (S[fXT * NB + l] + S[fXT * NB + l + step]);
                 float d[NC];
-                face_dissipation_f<DIM>(S, NB, l, step, nx, ny, xtf, G, Wc, d, P.status);
+                face_dissipation_f<DIM>(S, NB, l, step, nx, ny, xtf, G, Wc, d, P.status, JB, TL::NJ,
+                                        line * (LB + 5) + q);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) F[c] += d[c];
             }
