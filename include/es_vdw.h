@@ -55,8 +55,10 @@ extern "C" {
 #define ES_PREC_MIXED  1        /* per-stage arithmetic on the FP32 pipe: the state and the primitive
                                    variables in double-float (hi + lo float pairs), fluxes and WENO in
                                    float, entropy-variable jumps by the paper's jump decomposition, the
-                                   mesh as an FP32 displacement; the mesh redistribution and the mesh
-                                   itself stay double.  Periodic directions need period[k] = n_k dxi[k]. */
+                                   mesh as an FP32 displacement from the Cartesian mesh; the CFL step and
+                                   the mesh redistribution also run on that displacement in float (with a
+                                   warm-start network registered they use the double kernels); the mesh x
+                                   itself stays double.  Periodic directions need period[k] = n_k dxi[k]. */
 
 /* monitor functions of Sec. 4 / Example 5.1 */
 #define ES_MONITOR_VDW    0     /* eq. van der Waalsmonitor: delta_1 = rho, delta_2 = G, plus |Delta G|^2 */
@@ -169,14 +171,17 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
  * context's scratch) for every tile shape on the caller's state and mesh and keeps
  * the fastest for all later launches.  The shapes change only how nodes are
  * grouped into CTAs (how many tiles make a wave on the SMs, how much halo each
- * tile recomputes), never a result: every shape gives the same bits.  Writes the
+ * tile recomputes): in ES_PREC_FP64 every shape gives the same bits, in
+ * ES_PREC_MIXED the same values to FP32 rounding.  Writes the
  * chosen shape (1 .. ES_NTILES) and, if ms_host is non-null, the ES_NTILES probe
  * times in ms.  1D contexts have one shape (returns 1).  Synchronises. */
 int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host);
 
 /* Self-test of the library's FP64 quotient and reciprocal (the stage kernel divides with
  * them: a Newton-Raphson-refined hardware reciprocal and a Markstein quotient correction):
- * q[i] = a[i] / b[i], r[i] = 1 / b[i] for device arrays of n doubles, on `stream`. */
+ * q[i] = a[i] / b[i], r[i] = 1 / b[i] for device arrays of n doubles, on `stream`
+ * (asynchronous; ES_ERR_ARG for null arrays or n <= 0, ES_ERR_CUDA if the launch fails).
+ * Divisors must be finite, normal and nonzero. */
 int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream);
 
 /* Number of kernel launches the library has issued (graph launches count
