@@ -311,7 +311,7 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot) {
     const bool fuse = c->p.dim == 2;
     const dim3 tiles((c->g.n1 + 31) / 32, (c->g.n2 + 15) / 16);
     if (fuse && c->p.filter_passes >= 1 && c->p.filter_passes <= 8) {
-        k_omega_filter_f<<<tiles, 256, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, c->p.filter_passes, om);
+        launch_omega_filter(c->g, c->mon, t0, t1, t2, c->dev, c->p.filter_passes, om, s);
         count(c);
     } else {
         k_mon_omega_f<<<G, B, 0, s>>>(c->g, c->mon, t0, t1, t2, c->dev, om);

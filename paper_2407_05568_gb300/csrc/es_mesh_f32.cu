@@ -353,36 +353,38 @@ namespace es {
 constexpr int FT_X = 32, FT_Y = 16, FT_HMAX = 8;
 constexpr int FT_W = FT_X + 2 * FT_HMAX, FT_H = FT_Y + 2 * FT_HMAX;
 
-__global__ void __launch_bounds__(256) k_omega_filter_f(GridParams g, MonitorParams mp, const float* t0,
-                                                        const float* t1, const float* t2, const DevScalars* d,
-                                                        int passes, float* out) {
-    __shared__ float A[FT_W * FT_H], B[FT_W * FT_H];
+// (templated on the value type; the FP64 form keeps one pass per launch: in FP64 the halo
+// recomputation costs more than the launches it saves)
+template <class T>
+__global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorParams mp, const T* t0, const T* t1,
+                                                        const T* t2, const DevScalars* d, int passes, T* out) {
+    __shared__ T A[FT_W * FT_H], B[FT_W * FT_H];
     const int h = passes, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
     const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
     const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
     const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
     const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
-    const float c0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
-    const float c1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
-    const float c2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    const T c0 = M0 > 0.0 ? T(mp.w0 / M0) : T(0);
+    const T c1 = M1 > 0.0 ? T(mp.w1 / M1) : T(0);
+    const T c2 = M2 > 0.0 ? T(mp.w2 / M2) : T(0);
     for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
         const int sx = idx % TW, sy = idx / TW;
         const int si = state_index(x0 + sx, g.n1, g.bc[0]), sj = state_index(y0 + sy, g.n2, g.bc[1]);
         const int id = sj * g.n1 + si;
-        A[idx] = sqrtf(1.0f + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
+        A[idx] = sqrt(T(1) + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
     }
     __syncthreads();
-    float* cur = A;
-    float* nxt = B;
+    T* cur = A;
+    T* nxt = B;
     for (int p = 1; p <= h; ++p) {
         for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
             const int sx = idx % TW, sy = idx / TW;
             if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
-            float s = 0.0f;
+            T s = T(0);
             for (int dj = -1; dj <= 1; ++dj) {
-                float row = 0.0f;
-                for (int di = -1; di <= 1; ++di) row += (di == 0 ? 0.5f : 0.25f) * cur[(sy + dj) * TW + sx + di];
-                s += (dj == 0 ? 0.5f : 0.25f) * row;
+                T row = T(0);
+                for (int di = -1; di <= 1; ++di) row += (di == 0 ? T(0.5) : T(0.25)) * cur[(sy + dj) * TW + sx + di];
+                s += (dj == 0 ? T(0.5) : T(0.25)) * row;
             }
             nxt[idx] = s;
         }
@@ -398,13 +400,25 @@ __global__ void __launch_bounds__(256) k_omega_filter_f(GridParams g, MonitorPar
             if (cx != sx || cy != sy) nxt[idx] = nxt[cy * TW + cx];
         }
         __syncthreads();
-        float* tmp = cur; cur = nxt; nxt = tmp;
+        T* tmp = cur; cur = nxt; nxt = tmp;
     }
     for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
         const int ix = idx % FT_X, iy = idx / FT_X;
         const int gi = x0 + h + ix, gj = y0 + h + iy;
         if (gi < g.n1 && gj < g.n2) out[gj * g.n1 + gi] = cur[(h + iy) * TW + h + ix];
     }
+}
+
+// launchers (the kernel template is instantiated here): 32 x 16 tiles, 256 threads
+template <class T>
+static void launch_omega_filter_t(const GridParams& g, const MonitorParams& mp, const T* t0, const T* t1,
+                                  const T* t2, const DevScalars* d, int passes, T* out, cudaStream_t s) {
+    const dim3 tiles((g.n1 + FT_X - 1) / FT_X, (g.n2 + FT_Y - 1) / FT_Y);
+    k_omega_filter_t<T><<<tiles, 256, 0, s>>>(g, mp, t0, t1, t2, d, passes, out);
+}
+void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const float* t0, const float* t1,
+                         const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s) {
+    launch_omega_filter_t(g, mp, t0, t1, t2, d, passes, out, s);
 }
 
 __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const float* omega, const float* d0,

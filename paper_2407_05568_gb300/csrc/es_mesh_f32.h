@@ -34,8 +34,9 @@ __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, fl
                            DevScalars* d, int check, double eps);
 __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d);
 // fused 2D passes (32 x 16 tiles, halo = the pass count <= FT_HMAX = 8)
-__global__ void k_omega_filter_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
-                                 const DevScalars* d, int passes, float* out);
+// omega and its low-pass filter passes fused per 32 x 16 tile (2D, 1 <= passes <= FT_HMAX = 8)
+void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const float* t0, const float* t1,
+                         const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s);
 __global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
                                  DevScalars* dv);
 __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
