@@ -317,11 +317,12 @@ def measure_batch(args, dev, stream):
 
 def run_to_end(w, precision, dev):
     """Advance a workload to its t_end with es_steps (graph replays); returns the density at the end
-    (float64 numpy), the steps taken and the device time."""
+    (float64 numpy), the steps taken, the device time and the autotuned tile shape."""
     import torch
 
     from paper_2407_05568_gb300 import es
     ctx, JU, J, x = es.setup_workload(w, precision, dev)
+    tile, _ = es.es_autotune(ctx, JU, J, x)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = 0
     es.es_steps(ctx, JU, J, x, 1, w["t_end"])        # capture the step graph
@@ -344,7 +345,7 @@ def run_to_end(w, precision, dev):
         rho = (JU[0] / J).cpu().numpy()
     else:
         rho = ((JU[0, 0].double() + JU[1, 0].double()) / (J[0].double() + J[1].double())).cpu().numpy()
-    return rho, steps, ms
+    return rho, steps, ms, tile
 
 
 def measure_precision_sweep(args, dev):
@@ -362,10 +363,12 @@ def measure_precision_sweep(args, dev):
         row = {"case": name, "n": n, "t_end": t}
         res = {}
         for prec in ("fp64", "mixed"):
-            rho, steps, ms = run_to_end(w, prec, dev)
+            rho, steps, ms, tile = run_to_end(w, prec, dev)
             res[prec] = rho
+            bx, by = TILES[prec][tile]
             row[prec] = {"l1_vs_exact": float(np.abs(rho - exact).mean()), "steps": steps,
-                         "cell_updates_per_s": n * n * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None}
+                         "cell_updates_per_s": n * n * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None,
+                         "tile": f"{bx}x{by}"}
         row["mixed_rel_l1_vs_fp64"] = float(np.abs(res["mixed"] - res["fp64"]).sum() / np.abs(res["fp64"]).sum())
         out.append(row)
     vort = [r for r in out if r["case"] == "vortex"]
@@ -529,8 +532,8 @@ def pin(a):
 FLOPS_PER_NODE_STAGE_2D = None
 
 
-TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12)},
-         "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16)}}
+TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12), 5: (20, 10)},
+         "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16), 5: (16, 8)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
 # kernel as it is now; other shapes and sizes were not captured
 TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3051520 + 0, "stage_kernel_mixed<2,20,8>": 2323968 + 0}

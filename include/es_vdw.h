@@ -92,11 +92,11 @@ typedef struct es_params {
     int    precision;       /* ES_PREC_* */
     int    tile;            /* 2D stage tile shape: 0 = chosen by es_autotune (run by the first es_steps
                                if not called before); k = 1 .. ES_NTILES: shape k of the precision's
-                               table (FP64: 32x8, 25x11, 16x16, 32x12 nodes; mixed: 32x8, 25x6, 20x8,
-                               32x16) */
+                               table (FP64: 32x8, 25x11, 16x16, 32x12, 20x10 nodes; mixed: 32x8, 25x6,
+                               20x8, 32x16, 16x8) */
 } es_params;
 
-#define ES_NTILES 4
+#define ES_NTILES 5
 
 typedef struct es_ctx es_ctx;
 

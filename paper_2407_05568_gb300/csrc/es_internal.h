@@ -85,7 +85,7 @@ cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s);
 cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s);
 // 2D tile shapes of the stage kernels (nodes BX x BY, NT threads >= the faces of either direction);
 // the autotuner times each on the caller's problem
-constexpr int STAGE_NTILES = 4;
+constexpr int STAGE_NTILES = 5;
 void stage_tile_shape(bool mixed, int k, int* bx, int* by, int* nt);
 // set the kernels' shared-memory attributes (call outside any stream capture)
 cudaError_t stage_prepare_fp64(int dim);

@@ -511,13 +511,14 @@ static cudaError_t launch_tile(const StageParams& P, cudaStream_t s) {
 
 // 2D shapes: 32 x 8 nodes with 288 threads (= the 32 x 9 faces of xi_2), 25 x 11 with 320
 // (25 x 12 = 300 faces; 8 x 19 = 152 tiles cover 200 x 200 in one wave on 152 SMs), 16 x 16
-// with 288 (272 faces), 32 x 12 with 416 (416 faces; less halo per node).  1D: 254 nodes, 256 threads (255 faces, 768 pairs = three passes).
+// with 288 (272 faces), 32 x 12 with 416 (416 faces; less halo per node), 20 x 10 with 224.  1D: 254 nodes, 256 threads (255 faces, 768 pairs = three passes).
 cudaError_t stage_prepare_fp64(int dim) {
     if (dim == 1) return prepare_tile<1, 254, 1, 256>();
     cudaError_t e = prepare_tile<2, 32, 8, 288>();
     if (e == cudaSuccess) e = prepare_tile<2, 25, 11, 320>();
     if (e == cudaSuccess) e = prepare_tile<2, 16, 16, 288>();
     if (e == cudaSuccess) e = prepare_tile<2, 32, 12, 416>();
+    if (e == cudaSuccess) e = prepare_tile<2, 20, 10, 224>();
     return e;
 }
 
@@ -527,13 +528,15 @@ cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s) {
         case 1: return launch_tile<2, 25, 11, 320>(P, s);
         case 2: return launch_tile<2, 16, 16, 288>(P, s);
         case 3: return launch_tile<2, 32, 12, 416>(P, s);
+        case 4: return launch_tile<2, 20, 10, 224>(P, s);
         default: return launch_tile<2, 32, 8, 288>(P, s);
     }
 }
 
 void stage_tile_shape(bool mixed, int k, int* bx, int* by, int* nt) {
-    static const int fp64[STAGE_NTILES][3] = {{32, 8, 288}, {25, 11, 320}, {16, 16, 288}, {32, 12, 416}};
-    static const int f32[STAGE_NTILES][3] = {{32, 8, 288}, {25, 6, 192}, {20, 8, 192}, {32, 16, 544}};
+    static const int fp64[STAGE_NTILES][3] = {{32, 8, 288}, {25, 11, 320}, {16, 16, 288}, {32, 12, 416},
+                                              {20, 10, 224}};
+    static const int f32[STAGE_NTILES][3] = {{32, 8, 288}, {25, 6, 192}, {20, 8, 192}, {32, 16, 544}, {16, 8, 160}};
     const int(*t)[3] = mixed ? f32 : fp64;
     *bx = t[k][0];
     *by = t[k][1];

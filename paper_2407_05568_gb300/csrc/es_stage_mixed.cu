@@ -63,13 +63,15 @@ cudaError_t launch_tile_f(const StageParams& P, cudaStream_t s) {
 
 // 2D shapes: 32 x 8 nodes with 288 threads, 25 x 6 with 192 (175 faces; 8 x 34 = 272 tiles fill
 // 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces), 32 x 16 with 544
-// (544 faces; less halo per node for large meshes, one CTA per SM)
+// (544 faces; less halo per node for large meshes, one CTA per SM), 16 x 8 with 160 (more CTAs
+// for small meshes)
 cudaError_t stage_prepare_mixed(int dim) {
     if (dim == 1) return prepare_tile_f<1, 254, 1, 256>();
     cudaError_t e = prepare_tile_f<2, 32, 8, 288>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 25, 6, 192>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 20, 8, 192>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 32, 16, 544>();
+    if (e == cudaSuccess) e = prepare_tile_f<2, 16, 8, 160>();
     return e;
 }
 
@@ -79,6 +81,7 @@ cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s) {
         case 1: return launch_tile_f<2, 25, 6, 192>(P, s);
         case 2: return launch_tile_f<2, 20, 8, 192>(P, s);
         case 3: return launch_tile_f<2, 32, 16, 544>(P, s);
+        case 4: return launch_tile_f<2, 16, 8, 160>(P, s);
         default: return launch_tile_f<2, 32, 8, 288>(P, s);
     }
 }

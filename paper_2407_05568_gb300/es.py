@@ -367,10 +367,10 @@ def es_run_host(ctx, JU, J, x, nsteps, t_end):
 
 
 def es_autotune(ctx, JU, J, x):
-    """Time the stage kernel's tile shapes on this state; returns (chosen shape 1..4, [ms per shape])."""
+    """Time the stage kernel's tile shapes on this state; returns (chosen shape 1..5, [ms per shape])."""
     S = ctx.state_dtype
     k = ctypes.c_int()
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 5)()
     ctx._call(lib().es_autotune(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(k), ms))
     return k.value, list(ms)
 

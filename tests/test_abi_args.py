@@ -22,7 +22,7 @@ def _params(**over):
     return p
 
 
-@pytest.mark.parametrize("field,value", [("dim", 3), ("n1", 4), ("n2", 0), ("precision", 7), ("tile", 5),
+@pytest.mark.parametrize("field,value", [("dim", 3), ("n1", 4), ("n2", 0), ("precision", 7), ("tile", 6),
                                          ("tile", -1), ("cfl", 0.0), ("sign_tol", 0.5), ("kappa", 3),
                                          ("jacobi_sweeps", -1), ("R", 0.0), ("weno_eps", 0.0)])
 def test_create_rejects_bad_params(L, field, value):
