@@ -315,13 +315,13 @@ def measure_batch(args, dev, stream):
             "l2": "state (2 GB) larger than L2"}
 
 
-def run_to_end(w, precision, dev):
+def run_to_end(w, precision, dev, dt_fixed=0.0):
     """Advance a workload to its t_end with es_steps (graph replays); returns the density at the end
     (float64 numpy), the steps taken, the device time and the autotuned tile shape."""
     import torch
 
     from paper_2407_05568_gb300 import es
-    ctx, JU, J, x = es.setup_workload(w, precision, dev)
+    ctx, JU, J, x = es.setup_workload(w, precision, dev, dt_fixed=dt_fixed)
     tile, _ = es.es_autotune(ctx, JU, J, x)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = 0
@@ -331,7 +331,7 @@ def run_to_end(w, precision, dev):
     ms = 0.0
     t, dt = es.es_get_time(ctx)
     while t < w["t_end"] * (1 - 1e-14):
-        k = max(1, min(200, int((w["t_end"] - t) / max(dt, 1e-300)) + 1))
+        k = max(1, min(2000, int((w["t_end"] - t) / max(dt, 1e-300)) + 1))
         e0.record()
         es.es_steps(ctx, JU, J, x, k, w["t_end"])
         e1.record()
@@ -348,34 +348,71 @@ def run_to_end(w, precision, dev):
     return rho, steps, ms, tile
 
 
+def matched_error(rows, levels=(1e-4, 1e-5, 1e-6, 1e-7, 1e-8)):
+    """Per target level of L1(rho) against the exact solution and per form, the smallest grid of
+    a sweep that meets it, with its time to solution and throughput (None: no grid meets it)."""
+    out = []
+    for lv in levels:
+        row = {"l1_level": lv}
+        for prec in ("fp64", "mixed"):
+            ok = [r for r in rows if r[prec]["l1_vs_exact"] <= lv]
+            if not ok:
+                row[prec] = None
+                continue
+            r = min(ok, key=lambda r: r["n"])
+            row[prec] = {"n": r["n"], "time_to_solution_ms": r[prec]["ms"],
+                         "cell_updates_per_s": r[prec]["cell_updates_per_s"]}
+        if row["fp64"] and row["mixed"]:
+            row["time_ratio_fp64_over_mixed"] = row["fp64"]["time_to_solution_ms"] / row["mixed"]["time_to_solution_ms"]
+        out.append(row)
+    return out
+
+
 def measure_precision_sweep(args, dev):
     """The precision form against the plain FP64 form: L1(rho) against the exact solution and
-    against the FP64 run, and throughput, on the 2D sine wave (1024^2, t = 0.1) and the ideal-gas
-    isentropic vortex (64^2 .. 1024^2, t = 1)."""
+    against the FP64 run, throughput and time to solution, on the 1D sine wave (50 .. 1600 nodes,
+    fixed mesh, dt = 0.4 dxi^(5/3), t = 0.1), the 2D sine wave (1024^2, t = 0.1) and the
+    ideal-gas isentropic vortex (64^2 .. 1024^2, t = 1); then, per sweep, the smallest grid of
+    each form that meets each error level (matched error)."""
     from paper_2407_05568_gb300 import workloads as wl
     out = []
-    cases = [("sine2d", 1024)] + [("vortex", n) for n in (64, 128, 256, 512, 1024)]
+    cases = ([("sine1d", n) for n in (50, 100, 200, 400, 800, 1600)] + [("sine2d", 1024)]
+             + [("vortex", n) for n in (64, 128, 256, 512, 1024)])
     for name, n in cases:
-        w = wl.sine_2d(n) if name == "sine2d" else wl.isentropic_vortex(n)
-        X, Y = w["x"]
-        t = w["t_end"]
-        exact = (0.5 + 0.2 * np.sin(2 * np.pi * (X + Y - t))) if name == "sine2d" else wl.vortex_density(X, Y, t)
-        row = {"case": name, "n": n, "t_end": t}
+        dt_fixed = 0.0
+        if name == "sine1d":
+            w = wl.sine_1d(n)
+            dt_fixed = 0.4 * w["dxi"][0] ** (5.0 / 3.0)
+            X = w["x"][0]
+            exact = 0.5 + 0.2 * np.sin(2 * np.pi * (X - w["t_end"]))
+        elif name == "sine2d":
+            w = wl.sine_2d(n)
+            X, Y = w["x"]
+            exact = 0.5 + 0.2 * np.sin(2 * np.pi * (X + Y - w["t_end"]))
+        else:
+            w = wl.isentropic_vortex(n)
+            X, Y = w["x"]
+            exact = wl.vortex_density(X, Y, w["t_end"])
+        nodes = int(np.prod(w["x"].shape[1:]))
+        row = {"case": name, "n": n, "t_end": w["t_end"]}
         res = {}
         for prec in ("fp64", "mixed"):
-            rho, steps, ms, tile = run_to_end(w, prec, dev)
+            rho, steps, ms, tile = run_to_end(w, prec, dev, dt_fixed=dt_fixed)
             res[prec] = rho
-            bx, by = TILES[prec][tile]
-            row[prec] = {"l1_vs_exact": float(np.abs(rho - exact).mean()), "steps": steps,
-                         "cell_updates_per_s": n * n * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None,
+            bx, by = TILES[prec][tile] if w["dim"] == 2 else (254, 1)
+            row[prec] = {"l1_vs_exact": float(np.abs(rho - exact).mean()), "steps": steps, "ms": ms,
+                         "cell_updates_per_s": nodes * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None,
                          "tile": f"{bx}x{by}"}
         row["mixed_rel_l1_vs_fp64"] = float(np.abs(res["mixed"] - res["fp64"]).sum() / np.abs(res["fp64"]).sum())
         out.append(row)
-    vort = [r for r in out if r["case"] == "vortex"]
-    for a, b in zip(vort, vort[1:]):
-        for prec in ("fp64", "mixed"):
-            b[prec]["order_vs_previous"] = float(np.log2(a[prec]["l1_vs_exact"] / b[prec]["l1_vs_exact"]))
-    return out
+    matched = {}
+    for case in ("sine1d", "vortex"):
+        rows = [r for r in out if r["case"] == case]
+        for a, b in zip(rows, rows[1:]):
+            for prec in ("fp64", "mixed"):
+                b[prec]["order_vs_previous"] = float(np.log2(a[prec]["l1_vs_exact"] / b[prec]["l1_vs_exact"]))
+        matched[case] = matched_error(rows)
+    return {"runs": out, "matched_error": matched}
 
 
 def measure_learned(args, dev):

@@ -79,6 +79,15 @@ def low_pass(omega, dim, bc):
             nb = omega if s == 0 else _shift(omega, 0, 1, bc, s)
             out += 0.5 ** (abs(s) + 1) * nb
         return out
+    if dim == 3:
+        for s3 in (-1, 0, 1):
+            pl = omega if s3 == 0 else _shift(omega, 2, 3, bc, s3)
+            for s2 in (-1, 0, 1):
+                row = pl if s2 == 0 else _shift(pl, 1, 3, bc, s2)
+                for s1 in (-1, 0, 1):
+                    nb = row if s1 == 0 else _shift(row, 0, 3, bc, s1)
+                    out += 0.5 ** (abs(s1) + abs(s2) + abs(s3) + 3) * nb
+        return out
     for s2 in (-1, 0, 1):
         row = omega if s2 == 0 else _shift(omega, 1, 2, bc, s2)
         for s1 in (-1, 0, 1):

@@ -5,8 +5,8 @@ xi evolve by eq. semi_U / semi_J, with the 2w-th order EC flux of
 eq. ECFlux_curv_2p / GCL_flux built from the two-point flux eq. ECfluxMM, the
 metrics of eq. SCLCoeff / VCLCoeff, and the ES flux of eq. HOstable.
 
-Array layout: a 1D field has shape (n1,), a 2D field (n2, n1); direction
-xi_1 is the LAST axis.  States carry a leading component axis (d + 2).
+Array layout: a 1D field has shape (n1,), a 2D field (n2, n1), a 3D field
+(n3, n2, n1); direction xi_1 is the LAST axis.  States carry a leading component axis (d + 2).
 Coordinates x have shape (d, ...), x[0] = x_1.
 
 Readings of points the paper leaves open (each listed in the design notes):
@@ -16,7 +16,9 @@ Readings of points the paper leaves open (each listed in the design notes):
   * the face normal n, its length L and the face J xi_t used in the
     dissipation are arithmetic means of the two neighbouring node values;
   * the rotation angle theta is taken with the quadrant of (n_1, n_2), i.e.
-    cos(theta) = n_1/L, sin(theta) = n_2/L;
+    cos(theta) = n_1/L, sin(theta) = n_2/L; in 3D theta = atan2(n_2, n_1)
+    (0 when n_1 = n_2 = 0) and phi = atan2(n_3, sqrt(n_1^2 + n_2^2)), so the
+    first row of T is n/L;
   * the sign switch Y compares [[W]]^WENO at face i+1/2 with the plain jump
     W_{i+1} - W_i at the same face; a plain jump no larger than sign_tol
     (1e-12) times the size of the terms that form it, sum_a |R_am|
@@ -147,6 +149,19 @@ def node_jacobian(sch, x):
     xp = pad_coords(sch, x, w)
     if sch.dim == 1:
         return central_difference(xp[0], 0, w) / sch.dxi[0]
+    if sch.dim == 3:
+        D = np.empty((3, 3) + x.shape[1:])          # D[c, k] = delta_k[x_c] / dxi_k
+        for k in range(3):
+            ax = axis_of(k, 3)
+            for c in range(3):
+                a = central_difference(xp[c], ax, w)
+                for o in range(3):
+                    if o != ax:
+                        a = _trim(a, o, w)
+                D[c, k] = a / sch.dxi[k]
+        return (D[0, 0] * (D[1, 1] * D[2, 2] - D[1, 2] * D[2, 1])
+                - D[0, 1] * (D[1, 0] * D[2, 2] - D[1, 2] * D[2, 0])
+                + D[0, 2] * (D[1, 0] * D[2, 1] - D[1, 1] * D[2, 0]))
     dx = {}
     for k in range(2):
         ax = axis_of(k, 2)
@@ -177,6 +192,8 @@ def direction_metrics(sch, x, xdot, k, g=3):
     """
     dim = sch.dim
     w = sch.w
+    if dim == 3:
+        return direction_metrics_3d(sch, x, xdot, k, g)
     xd = pad_velocity(sch, xdot, g)
     if dim == 1:
         n = np.ones((1,) + xd.shape[1:])
@@ -199,6 +216,55 @@ def direction_metrics(sch, x, xdot, k, g=3):
     return n, xt
 
 
+def _central_same(a, axis, w):
+    """delta_k[a] on the same grid as a, NaN on the w nodes at each end that lack neighbours."""
+    out = np.full(a.shape, np.nan)
+    d = central_difference(a, axis, w)
+    idx = [slice(None)] * a.ndim
+    idx[axis] = slice(w, a.shape[axis] - w)
+    out[tuple(idx)] = d
+    return out
+
+
+def direction_metrics_3d(sch, x, xdot, k, g=3):
+    """3D node metrics of direction xi_k by eq. SCLCoeff and eq. VCLCoeff.
+
+    With (k, l, m) and (j, p, q) cyclic permutations of (1, 2, 3):
+      J dxi_k/dx_j = (delta_m[delta_l[x_p] x_q] - delta_l[delta_m[x_p] x_q]) / (dxi_l dxi_m),
+    the conservative form of (x_p)_{xi_l} (x_q)_{xi_m} - (x_p)_{xi_m} (x_q)_{xi_l}; the
+    difference operators commute, so sum_k delta_k[J dxi_k/dx_j] = 0 (the discrete SCL).
+    Grid of the result: the interior extended by g nodes along xi_k only.
+    """
+    w = sch.w
+    P = max(g, w)                   # ghosts of the padded coordinates (each difference runs along
+    xp = pad_coords(sch, x, P)      # one axis, so w ghosts along it suffice)
+    l, m = (k + 1) % 3, (k + 2) % 3
+    al, am = axis_of(l, 3), axis_of(m, 3)
+    n = []
+    for j in range(3):
+        pj, qj = (j + 1) % 3, (j + 2) % 3
+        t1 = _central_same(_central_same(xp[pj], al, w) * xp[qj], am, w)
+        t2 = _central_same(_central_same(xp[pj], am, w) * xp[qj], al, w)
+        n.append((t1 - t2) / (sch.dxi[l] * sch.dxi[m]))
+    n = np.stack(n)
+    # keep g ghosts along xi_k, none along the other two directions
+    sl = [slice(None)] * 4
+    for d in range(3):
+        ax = axis_of(d, 3)
+        keep = g if d == k else 0
+        sl[1 + ax] = slice(P - keep, n.shape[1 + ax] - (P - keep))
+    n = n[tuple(sl)]
+    assert not np.isnan(n).any()
+    xd = pad_velocity(sch, xdot, g)
+    sl = [slice(None)] * 4
+    for d in range(3):
+        ax = axis_of(d, 3)
+        sl[1 + ax] = slice(None) if d == k else slice(g, xd.shape[1 + ax] - g)
+    xd = xd[tuple(sl)]
+    xt = -np.sum(xd * n, axis=0)
+    return n, xt
+
+
 # ------------------------------------------------------------ eigen-system
 
 def rotate(vec, c, s, inverse=False):
@@ -210,6 +276,38 @@ def rotate(vec, c, s, inverse=False):
     else:
         out[1] = c * vec[1] + s * vec[2]
         out[2] = -s * vec[1] + c * vec[2]
+    return out
+
+
+def frame_3d(nf):
+    """Rows of the momentum block of T in 3D (Sec. 3.3): with theta = atan2(n_2, n_1) and
+    phi = atan2(n_3, sqrt(n_1^2 + n_2^2)) (theta = 0 when n_1 = n_2 = 0),
+      e_n  = ( cos phi cos theta,  cos phi sin theta, sin phi) = n/L,
+      e_t1 = (-sin theta,          cos theta,         0),
+      e_t2 = (-sin phi cos theta, -sin phi sin theta, cos phi)."""
+    L = np.sqrt(np.sum(nf**2, axis=0))
+    r12 = np.sqrt(nf[0] ** 2 + nf[1] ** 2)
+    flat = r12 == 0.0
+    safe = np.where(flat, 1.0, r12)
+    ct = np.where(flat, 1.0, nf[0] / safe)
+    st = np.where(flat, 0.0, nf[1] / safe)
+    cp = r12 / L
+    sp = nf[2] / L
+    zero = np.zeros_like(L)
+    e_n = np.stack([cp * ct, cp * st, sp])
+    e_t1 = np.stack([-st, ct, zero])
+    e_t2 = np.stack([-sp * ct, -sp * st, cp])
+    return L, np.stack([e_n, e_t1, e_t2])
+
+
+def rotate_3d(vec, frame, inverse=False):
+    """Apply T (or T^T) to the momentum slots 1..3 of a (5, ...) vector; frame from frame_3d."""
+    out = vec.copy()
+    mom = vec[1:4]
+    if inverse:
+        out[1:4] = np.einsum("rc...,r...->c...", frame, mom)
+    else:
+        out[1:4] = np.einsum("rc...,c...->r...", frame, mom)
     return out
 
 
@@ -228,8 +326,12 @@ def scaled_eigenvectors(gas, rho, vn, vt, p):
     [(0, 0, 1, v_t)], (1, v_n + c, [v_t], H + v_n c), with p_e = rho delta/(1 - b rho)
     and H = (E + p)/rho.  S^2 = diag(rho T/(2c^2), R delta rho T^2/((R T - 2 a rho (1 - b rho)^2) c^2),
     [rho T], rho T/(2 c^2)) -- the reduced-unit S of Sec. 3.3 in general units.
-    vt is None in 1D.  Returns (R, c) with R of shape (d+2, d+2, ...).
+    vt is None in 1D, an array in 2D and a pair (vt1, vt2) in 3D, where the two tangential
+    columns are (0, 0, 1, 0, vt1) and (0, 0, 0, 1, vt2), each scaled by sqrt(rho T).
+    Returns (R, c) with R of shape (d+2, d+2, ...).
     """
+    if isinstance(vt, (tuple, list)):
+        return _scaled_eigenvectors_3d(gas, rho, vn, vt[0], vt[1], p)
     g = gas
     T = thermo.temperature(g, rho, p)
     c2 = thermo.sound_speed2(g, rho, T)
@@ -253,6 +355,28 @@ def scaled_eigenvectors(gas, rho, vn, vt, p):
                 np.stack([zero, zero, one, vt]),
                 np.stack([one, vn + c, vt, H + vn * c])]
         scal = [s_ac, s_en, rho * T, s_ac]
+    R = np.stack([col * np.sqrt(sc) for col, sc in zip(cols, scal)], axis=1)
+    return R, c
+
+
+def _scaled_eigenvectors_3d(g, rho, vn, vt1, vt2, p):
+    """The 3D R = R~ S of Sec. 3.3 (eq. eigen) at a rotated state."""
+    T = thermo.temperature(g, rho, p)
+    c2 = thermo.sound_speed2(g, rho, T)
+    c = np.sqrt(c2)
+    E = rho * thermo.internal_energy(g, rho, T) + 0.5 * rho * (vn**2 + vt1**2 + vt2**2)
+    H = (E + p) / rho
+    mid = H - c2 * (1.0 - g.b * rho) / g.delta
+    s_ac = rho * T / (2.0 * c2)
+    s_en = g.R * g.delta * rho * T**2 / ((g.R * T - 2.0 * g.a * rho * (1.0 - g.b * rho) ** 2) * c2)
+    one = np.ones_like(rho)
+    zero = np.zeros_like(rho)
+    cols = [np.stack([one, vn - c, vt1, vt2, H - vn * c]),
+            np.stack([one, vn, vt1, vt2, mid]),
+            np.stack([zero, zero, one, zero, vt1]),
+            np.stack([zero, zero, zero, one, vt2]),
+            np.stack([one, vn + c, vt1, vt2, H + vn * c])]
+    scal = [s_ac, s_en, rho * T, rho * T, s_ac]
     R = np.stack([col * np.sqrt(sc) for col, sc in zip(cols, scal)], axis=1)
     return R, c
 
@@ -308,15 +432,21 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
         cth, sth = nf[0] / L, None
         vn = v_f[0] * cth
         vt = None
-    else:
+    elif d == 2:
         cth, sth = nf[0] / L, nf[1] / L
         vn = cth * v_f[0] + sth * v_f[1]
         vt = -sth * v_f[0] + cth * v_f[1]
+    else:
+        L, frame = frame_3d(nf)
+        vr = np.einsum("rc...,c...->r...", frame, v_f)
+        vn, vt = vr[0], (vr[1], vr[2])
     R, c = scaled_eigenvectors(g, rho_f, vn, vt, p_f)
     Lam = np.abs(xtf + L * vn) + L * c          # max_m |J xi_t + L lambda_m|
 
     def rotated(j_off):
         Vj = V_pad[..., ip + j_off]
+        if d == 3:
+            return rotate_3d(Vj, frame)
         return Vj if d == 1 else rotate(Vj, cth, sth)     # T V (T = I in 1D)
 
     TV = [rotated(o) for o in range(-2, 4)]                 # nodes i-2 .. i+3
@@ -333,6 +463,8 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
     incr = np.einsum("ab...,b...->a...", R, Y * jump_weno)  # R Y [[W]]
     if d == 2:
         incr = rotate(incr, cth, sth, inverse=True)
+    elif d == 3:
+        incr = rotate_3d(incr, frame, inverse=True)
     F_U = F_U - 0.5 * Lam * incr
     return F_U, F_J
 

@@ -462,12 +462,12 @@ def es_last_error(ctx):
     return buf.value.decode()
 
 
-def setup_workload(w, precision="fp64", device="cuda", dissipation=True):
+def setup_workload(w, precision="fp64", device="cuda", dissipation=True, dt_fixed=0.0):
     """Context and device state (JU, J, x) of a workload description (workloads.py): J from
-    the mesh, JU from the primitive fields, time 0."""
+    the mesh, JU from the primitive fields, time 0.  dt_fixed > 0 replaces the CFL step."""
     import torch
     dev = torch.device(device)
-    ctx = es_create(make_params(w, precision=precision, dissipation=dissipation))
+    ctx = es_create(make_params(w, precision=precision, dissipation=dissipation, dt_fixed=dt_fixed))
     x = torch.tensor(np.ascontiguousarray(w["x"]), dtype=torch.float64, device=dev)
     J = state_empty(ctx, w["x"].shape[1:], dev)
     es_init_mesh(ctx, x, J)

@@ -73,6 +73,38 @@ def sine_2d(n=1024, t_end=0.1, cfl=0.4):
                 p=np.ones_like(X), t_end=t_end, cfl=cfl, moving=False)
 
 
+def sine_3d(n=64, t_end=0.1, cfl=0.4, moving=False):
+    """3D periodic sine wave (Example 5.6 setup): rho = 0.5 + 0.2 sin(2 pi (x_1 + x_2 + x_3)),
+    v = (0.3, 0.3, 0.3), p = 1 on [0, 1)^3; exact rho at (x - 0.3 t).  MM: the monitor of
+    Example 5.1 (alpha = (20, 15), 20 filter passes), 10 Jacobi sweeps; MR-WENO linear weights
+    1/3 each."""
+    x1, d = uniform_nodes(n, 0.0, 1.0, True)
+    Z, Yc, X = np.meshgrid(x1, x1, x1, indexing="ij")      # shape (n3, n2, n1), x_1 along the last axis
+    return dict(gas=UNITS_A, dim=3, n=(n, n, n), dxi=(d, d, d), bc=("periodic",) * 3,
+                period=(1.0, 1.0, 1.0), x=np.stack([X, Yc, Z]),
+                rho=0.5 + 0.2 * np.sin(2 * np.pi * (X + Yc + Z)),
+                v=np.stack([0.3 * np.ones_like(X)] * 3), p=np.ones_like(X), t_end=t_end, cfl=cfl,
+                moving=moving, weno_gammas=(1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0),
+                mesh=dict(monitor="smooth", alphas=(20.0, 15.0), kappa=2, filter_passes=20, sweeps=10,
+                          eps=0.0))
+
+
+def spherical_shock_3d(n=64, t_end=0.1, cfl=0.4, moving=True):
+    """3D spherically symmetric shock tube (Example 5.7 setup): the RP1 states of Table 5.1,
+    (1.818, 0, 3.0) inside r < 0.5 and (0.275, 0, 0.575) outside, on [0, 1]^3 with outflow
+    boundaries; MM monitor with rho and G, alpha = (1200, 1200, 0), 5 filter passes,
+    10 Jacobi sweeps."""
+    x1, d = uniform_nodes(n, 0.0, 1.0, False)
+    Z, Yc, X = np.meshgrid(x1, x1, x1, indexing="ij")
+    inside = X**2 + Yc**2 + Z**2 < 0.25
+    return dict(gas=UNITS_A, dim=3, n=(n, n, n), dxi=(d, d, d), bc=("outflow",) * 3,
+                period=(1.0, 1.0, 1.0), x=np.stack([X, Yc, Z]),
+                rho=np.where(inside, 1.818, 0.275), v=np.zeros((3,) + X.shape),
+                p=np.where(inside, 3.0, 0.575), t_end=t_end, cfl=cfl, moving=moving,
+                mesh=dict(monitor="vdw", alphas=(1200.0, 1200.0, 0.0), kappa=2, filter_passes=5,
+                          sweeps=10, eps=0.0))
+
+
 def quadrant_states(seed):
     """Four seeded admissible states near the critical point:
     rho in [0.4, 1.6], p in [0.6, 1.4], |v| <= 0.5 (uniform in the disc), rejection-sampled

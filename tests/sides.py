@@ -12,7 +12,7 @@ from oracle import stepper, thermo
 def oracle_setup(w, dissipation=True, x=None):
     g = thermo.Gas(**w["gas"])
     sch = op.Scheme(gas=g, dim=w["dim"], bc=tuple(w["bc"]), dxi=tuple(w["dxi"]), period=tuple(w["period"]),
-                    dissipation=dissipation)
+                    dissipation=dissipation, weno_gammas=tuple(w.get("weno_gammas", (0.005, 0.045, 0.95))))
     x = w["x"] if x is None else x
     J = op.node_jacobian(sch, x)
     JU = thermo.prim_to_cons(g, w["rho"], w["v"], w["p"]) * J
