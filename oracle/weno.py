@@ -124,8 +124,12 @@ def mr_weno5(w, gammas=(0.005, 0.045, 0.95), eps=1e-12):
     p2 = (q2 - g12 * p1) / g22
     p3 = (q3 - g1 * p1 - g2 * p2) / g3
     beta1 = np.minimum((w[2] - w[1]) ** 2, (w[3] - w[2]) ** 2)
-    beta2 = np.einsum("a...,ab,b...->...", w[1:4], _B2, w[1:4])
-    beta3 = np.einsum("a...,ab,b...->...", w, _B3, w)
+    # beta integrates squared derivatives of the polynomial, so it ignores a constant added to
+    # the data (B 1 = 0): the forms are evaluated on w - w_i, which keeps rounding of |w|^2-sized
+    # terms out of indicators that can be far smaller (data with a large mean and a small variation)
+    d = w - w[2]
+    beta2 = np.einsum("a...,ab,b...->...", d[1:4], _B2, d[1:4])
+    beta3 = np.einsum("a...,ab,b...->...", d, _B3, d)
     tau = (0.5 * (np.abs(beta3 - beta1) + np.abs(beta3 - beta2))) ** 2
     wt1 = g1 * (1.0 + tau / (beta1 + eps))
     wt2 = g2 * (1.0 + tau / (beta2 + eps))

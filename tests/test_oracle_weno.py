@@ -75,3 +75,19 @@ def test_discontinuity_picks_smooth_stencil():
     w = np.array([1.0, 1.0, 1.0, 0.0, 0.0])
     r = weno.mr_weno5(w)
     assert 0.0 <= r <= 1.0 + 1e-12
+
+
+def test_shift_equivariance_on_small_variations():
+    """Adding a constant C to the data adds C to the reconstruction: the smoothness indicators
+    integrate derivatives, which ignore C, and every candidate reproduces constants.  With a large
+    mean and a variation near the indicator regulariser this holds only if the indicators are not
+    formed from |w|^2-sized terms."""
+    rng = np.random.default_rng(8)
+    base = 1e-6 * np.cumsum(rng.standard_normal((5, 400)), axis=0)
+    for C in (8.47, -250.0, 3.0e3):
+        for g in ((0.005, 0.045, 0.95), (1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0)):
+            r0 = weno.mr_weno5(base, g, 1e-12)
+            r1 = weno.mr_weno5(base + C, g, 1e-12)
+            # the shifted data themselves are rounded to the spacing of C
+            tol = 1e-3 * np.abs(base).max() + 64 * np.spacing(abs(C))
+            assert np.abs((r1 - C) - r0).max() < tol, (C, g)
