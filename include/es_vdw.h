@@ -6,17 +6,28 @@
  *
  * Data layout (all calls)
  *   Node-centred fields on a logically rectangular n1 x n2 mesh (n2 = 1 in 1D),
- *   structure of arrays, xi_1 fastest:  field[c][j][i] at c*n1*n2 + j*n1 + i.
- *     JU : (dim + 2) components (rho, rho v_1, [rho v_2], E) times J
+ *   structure of arrays, xi_1 fastest:  field[c][j][i] at c*n1*n2 + j*n1 + i;
+ *   in 3D an n1 x n2 x n3 mesh, field[c][k][j][i] at ((c*n3 + k)*n2 + j)*n1 + i.
+ *     JU : (dim + 2) components (rho, rho v_1, [rho v_2, [rho v_3]], E) times J
  *     J  : 1 component
  *     JU, J (and dJU, dJ) hold double in ES_PREC_FP64.  In ES_PREC_MIXED they
  *     hold compensated float pairs in two planes: [2][dim+2][n2][n1] for JU and
  *     [2][n2][n1] for J, value = hi plane + lo plane (a 48-bit significand in
  *     8 bytes, like a double).  They are passed as void*.
- *     x  : dim components (x_1, [x_2]) of the node coordinates, double
+ *     x  : dim components (x_1, [x_2, [x_3]]) of the node coordinates, double
  *     xdot : dim components of the mesh velocity, double
  *   The computational mesh is uniform with spacings dxi[k]; x(xi) maps it to
  *   the physical mesh (Sec. 3, eq. transf).
+ *
+ * Three dimensions (dim = 3)
+ *   The operator, the SSP-RK3 stages and the mesh redistribution in their 3D form:
+ *   the cross-form metrics of Sec. 3.2 (eq. SCLCoeff), the theta/phi rotation of
+ *   Sec. 3.3 and the 27-point filter of Sec. 4.  ES_PREC_FP64 only.  es_create,
+ *   es_init_mesh, es_prim_to_cons, es_rhs, es_rk_stage, es_cfl_dt,
+ *   es_mesh_redistribute, es_steps, es_run_host, es_autotune (a no-op) and the
+ *   time and status calls accept a 3D context; es_mesh_features, es_mesh_solve,
+ *   es_mesh_warm_start and es_set_warm_start return ES_ERR_ARG for it.  A 3D
+ *   context holds about 66 n1 n2 n3 + 12 (n1+6)(n2+6)(n3+6) doubles of scratch.
  *
  * Pointers
  *   Every array argument is a DEVICE pointer (cudaMalloc'd or a PyTorch
@@ -68,11 +79,12 @@ typedef struct es_params {
     /* van der Waals gas, Sec. 1 eq. vdWEOS: p = rho R T/(1 - b rho) - a rho^2, e = cv T - a rho.
        a = b = 0 is the ideal gas. */
     double a, b, R, cv;
-    int    dim;             /* 1 or 2 */
-    int    n1, n2;          /* nodes per direction; n2 = 1 when dim = 1; each >= 8 */
-    double dxi[2];          /* computational spacings Delta xi_k */
-    double period[2];       /* period of x_k along a periodic direction */
-    int    bc[2];           /* ES_BC_* per direction */
+    int    dim;             /* 1, 2 or 3 */
+    int    n1, n2, n3;      /* nodes per direction, each >= 8 in use; n2 = 1 when dim = 1; n3 = 0 or 1
+                               when dim < 3 */
+    double dxi[3];          /* computational spacings Delta xi_k */
+    double period[3];       /* period of x_k along a periodic direction */
+    int    bc[3];           /* ES_BC_* per direction */
     double weno_gamma[3];   /* MR-WENO5 linear weights (1-point, 3-point, 5-point), Sec. 5: (0.005, 0.045, 0.95) */
     double weno_eps;        /* smoothness regulariser (paper silent; 1e-12) */
     double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| no larger than sign_tol times

@@ -1,0 +1,64 @@
+// es_3d.h -- the three-dimensional FP64 path: metrics, node fields, direction-split flux
+// kernels and the mesh redistribution on an n1 x n2 x n3 mesh ([comp][n3][n2][n1], xi_1 fastest).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "es_aux.h"
+#include "es_device.cuh"
+
+namespace es {
+
+struct Grid3 {
+    int n[3];
+    int bc[3];
+    double inv_dxi[3];
+    double period[3];
+};
+
+// the context's 3D scratch (device) and settings
+struct Ctx3 {
+    Grid3 g;
+    Gas gas;
+    Weno weno;
+    MonitorParams mon;
+    int diss;
+    int filter_passes, sweeps;
+    double eps;
+    int grid;                 // blocks of the grid-stride kernels
+    size_t N;                 // nodes
+    size_t NE;                // nodes of the grid extended by 3 ghosts in every direction
+    size_t NKk[3];            // nodes of direction k's metric grid (3 ghosts along xi_k only)
+    double* XE;               // stage coordinates on the extended grid [3][NE]
+    double* D;                // delta_l[x_p] on the extended grid [9][NE] (valid where xi_l is interior)
+    double* NK[3];            // J dxi_k/dx_j on direction k's metric grid [3][NKk]
+    double* NF;               // node fields of the stage state [F3_COUNT][N]
+    double* RH;               // right-hand sides accumulated over the directions [6][N]
+    // mesh scratch (the context's buffers)
+    double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1, *xa, *xb;
+};
+
+// arguments of one operator evaluation / RK stage
+struct Stage3 {
+    const double *JUn, *Jn, *JUs, *Js;
+    const double *xn, *xdot;  // mesh at t^n and its velocity (xdot nullable)
+    double *JUo, *Jo;
+    double ca, cb, cst;       // Shu-Osher coefficients and the stage time fraction
+    double dt_host;
+    const double* dt_dev;     // device dt (nullptr: dt_host)
+    int mode;                 // 0: RK combination; 1: right-hand sides into (JUo, Jo)
+    int reuse;                // the metrics and node fields of (xn, JUs, Js) are in the buffers
+};
+
+cudaError_t d3_alloc(Ctx3* d);
+void d3_free(Ctx3* d);
+cudaError_t d3_prepare();
+// each returns the number of kernels it launched (negative: a launch failed, *err set)
+int d3_init_J(const Ctx3* d, const double* x, double* J, cudaStream_t s, cudaError_t* err);
+int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
+int d3_cfl(Ctx3* d, const double* JU, const double* J, const double* x, DevScalars* dv, cudaStream_t s,
+           cudaError_t* err);
+int d3_mesh(Ctx3* d, const double* JU, const double* J, const double* xn, double* xdot, DevScalars* dv,
+            cudaStream_t s, cudaError_t* err);
+
+}  // namespace es

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "es_3d.h"
 #include "es_aux.h"
 #include "es_internal.h"
 #include "es_mesh_f32.h"
@@ -55,6 +56,7 @@ struct es_ctx {
     int capture_count;
     int loop_failed;                  // a graph while-loop could not be built (unrolled sweeps used)
     int64_t launches;
+    Ctx3* d3;                         // the 3D path's scratch and settings (dim = 3)
     char msg[256];
 };
 
@@ -346,7 +348,62 @@ void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x) {
     count(c);
 }
 
+// one 3D step: CFL (its metrics and node fields serve stage 1), mesh, three stages, advance
+int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
+    cudaStream_t s = c->s_enq;
+    cudaError_t e;
+    k_reset<<<1, 32, 0, s>>>(c->dev);
+    count(c);
+    int n = d3_cfl(c->d3, JU, J, x, c->dev, s, &e);
+    if (n < 0) return cuda_fail(c, e, "3D time-step kernels");
+    count(c, n);
+    k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
+    count(c);
+    const double* xdot = nullptr;
+    if (c->p.moving) {
+        n = d3_mesh(c->d3, JU, J, x, c->xdot, c->dev, s, &e);
+        if (n < 0) return cuda_fail(c, e, "3D mesh kernels");
+        count(c, n);
+        xdot = c->xdot;
+    }
+    double* S1 = (double*)c->S1;
+    double* S2 = (double*)c->S2;
+    double* S1J = (double*)c->S1J;
+    double* S2J = (double*)c->S2J;
+    const double* srcU[3] = {JU, S1, S2};
+    const double* srcJ[3] = {J, S1J, S2J};
+    double* dstU[3] = {S1, S2, JU};
+    double* dstJ[3] = {S1J, S2J, J};
+    for (int st = 0; st < 3; ++st) {
+        Stage3 a;
+        a.JUn = JU;
+        a.Jn = J;
+        a.JUs = srcU[st];
+        a.Js = srcJ[st];
+        a.xn = x;
+        a.xdot = xdot;
+        a.JUo = dstU[st];
+        a.Jo = dstJ[st];
+        a.ca = RK_A[st];
+        a.cb = RK_B[st];
+        a.cst = RK_C[st];
+        a.dt_host = 0.0;
+        a.dt_dev = &c->dev->dt;
+        a.mode = 0;
+        a.reuse = st == 0;                 // x_s = x^n and (JU, J)_s = (JU, J)^n: the CFL's buffers
+        n = d3_stage(c->d3, a, &c->dev->status, s, &e);
+        if (n < 0) return cuda_fail(c, e, "3D stage kernels");
+        count(c, n);
+    }
+    k_advance<<<c->grid1d, 256, 0, s>>>(c->g, x, xdot, c->dev);
+    count(c);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance kernel");
+    return ES_OK;
+}
+
 int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
+    if (c->p.dim == 3) return enqueue_step3(c, (double*)JU, (double*)J, x);
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     k_reset<<<1, 32, 0, s>>>(c->dev);
@@ -400,11 +457,14 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
 
 int check_params(const es_params* p) {
     if (!p) return 0;
-    if (p->dim != 1 && p->dim != 2) return 0;
+    if (p->dim < 1 || p->dim > 3) return 0;
     if (p->n1 < 8) return 0;
     if (p->dim == 1 && p->n2 != 1) return 0;
-    if (p->dim == 2 && p->n2 < 8) return 0;
-    if ((long long)p->n1 * p->n2 > (1LL << 30)) return 0;
+    if (p->dim >= 2 && p->n2 < 8) return 0;
+    if (p->dim < 3 && p->n3 != 0 && p->n3 != 1) return 0;
+    if (p->dim == 3 && (p->n3 < 8 || p->precision != ES_PREC_FP64)) return 0;
+    const long long n3 = p->dim == 3 ? p->n3 : 1;
+    if ((long long)p->n1 * p->n2 * n3 > (1LL << 30)) return 0;
     for (int k = 0; k < p->dim; ++k) {
         if (!(p->dxi[k] > 0.0)) return 0;
         if (p->bc[k] != ES_BC_PERIODIC && p->bc[k] != ES_BC_OUTFLOW) return 0;
@@ -481,11 +541,18 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         c->mon.w1 = p->kappa >= 2 ? p->alpha[1] : 0.0;
         c->mon.w2 = p->alpha[p->kappa];
     }
+    if (p->dim == 3) {
+        // the 1D/2D elementwise kernels see the 3D mesh as N nodes in a row
+        c->g.n1 = p->n1 * p->n2 * p->n3;
+        c->g.n2 = 1;
+        c->g.bc[0] = c->g.bc[1] = ES_BC_PERIODIC;
+        c->g.inv_dxi[0] = c->g.inv_dxi[1] = 1.0;
+    }
     c->N = size_t(c->g.n1) * c->g.n2;
     c->nc = p->dim + 2;
     c->mixed = p->precision == ES_PREC_MIXED;
     c->tile = p->tile > 0 ? p->tile - 1 : 0;
-    c->tuned = p->tile > 0 || p->dim == 1;
+    c->tuned = p->tile > 0 || p->dim != 2;
     c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -530,8 +597,40 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "init"); goto fail_out; }
         // warm the stage kernel once so its shared-memory attribute is set outside any capture
-        e = p->precision == ES_PREC_MIXED ? stage_prepare_mixed(p->dim) : stage_prepare_fp64(p->dim);
+        if (p->dim == 3) e = d3_prepare();
+        else e = p->precision == ES_PREC_MIXED ? stage_prepare_mixed(p->dim) : stage_prepare_fp64(p->dim);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "stage kernel attributes"); goto fail_out; }
+    }
+    if (p->dim == 3) {
+        c->d3 = (Ctx3*)calloc(1, sizeof(Ctx3));
+        if (!c->d3) { rc = fail(c, ES_ERR_ARG, "out of host memory"); goto fail_out; }
+        Ctx3* d = c->d3;
+        const int nn[3] = {p->n1, p->n2, p->n3};
+        for (int k = 0; k < 3; ++k) {
+            d->g.n[k] = nn[k];
+            d->g.bc[k] = p->bc[k];
+            d->g.inv_dxi[k] = 1.0 / p->dxi[k];
+            d->g.period[k] = p->period[k];
+        }
+        d->gas = c->gas;
+        d->weno = c->weno;
+        d->mon = c->mon;
+        d->diss = p->dissipation;
+        d->filter_passes = p->filter_passes;
+        d->sweeps = p->jacobi_sweeps;
+        d->eps = p->jacobi_eps;
+        d->grid = c->grid1d;
+        d->rhoF = c->rhoF;
+        d->GF = c->GF;
+        d->t0 = c->t0;
+        d->t1 = c->t1;
+        d->t2 = c->t2;
+        d->om0 = c->om0;
+        d->om1 = c->om1;
+        d->xa = c->xa;
+        d->xb = c->xb;
+        cudaError_t e = d3_alloc(d);
+        if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaMalloc (3D scratch)"); goto fail_out; }
     }
     *out = c;
     return ES_OK;
@@ -552,11 +651,21 @@ void es_destroy(es_ctx* c) {
         if (b) cudaFree(b);
     if (c->dev) cudaFree(c->dev);
     if (c->hpin) cudaFreeHost(c->hpin);
+    if (c->d3) {
+        d3_free(c->d3);
+        free(c->d3);
+    }
     free(c);
 }
 
 int es_init_mesh(es_ctx* c, const double* x, void* J) {
     if (!c || !x || !J) return fail(c, ES_ERR_ARG, "null argument");
+    if (c->d3) {
+        cudaError_t e;
+        if (d3_init_J(c->d3, x, (double*)J, c->stream, &e) < 0) return cuda_fail(c, e, "k3_init_J");
+        count(c);
+        return ES_OK;
+    }
     launch_init_J(c->g, x, J, c->mixed, c->grid1d, c->stream);
     count(c);
     CK(cudaGetLastError(), "k_init_J");
@@ -573,6 +682,22 @@ int es_prim_to_cons(es_ctx* c, const double* rho, const double* v, const double*
 
 int es_rhs(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot, void* dJU, void* dJ) {
     if (!c || !JU || !J || !x || !dJU || !dJ) return fail(c, ES_ERR_ARG, "null argument");
+    if (c->d3) {
+        Stage3 a = {};
+        a.JUn = a.JUs = (const double*)JU;
+        a.Jn = a.Js = (const double*)J;
+        a.xn = x;
+        a.xdot = xdot;
+        a.JUo = (double*)dJU;
+        a.Jo = (double*)dJ;
+        a.dt_host = 1.0;
+        a.mode = 1;
+        cudaError_t e;
+        const int n = d3_stage(c->d3, a, &c->dev->status, c->stream, &e);
+        if (n < 0) return cuda_fail(c, e, "3D stage kernels");
+        count(c, n);
+        return ES_OK;
+    }
     StageParams P = stage_params(c);
     P.mode = 1;
     P.dt_host = 1.0;
@@ -589,6 +714,27 @@ int es_rk_stage(es_ctx* c, int stage, double dt, const void* JUn, const void* Jn
     if (!c || stage < 1 || stage > 3 || !JUn || !Jn || !JUs || !Js || !xn || !JU_out || !J_out)
         return fail(c, ES_ERR_ARG, "bad argument");
     if (JU_out == JUs || J_out == Js) return fail(c, ES_ERR_ARG, "output aliases the stage input");
+    if (c->d3) {
+        Stage3 a = {};
+        a.JUn = (const double*)JUn;
+        a.Jn = (const double*)Jn;
+        a.JUs = (const double*)JUs;
+        a.Js = (const double*)Js;
+        a.xn = xn;
+        a.xdot = xdot;
+        a.JUo = (double*)JU_out;
+        a.Jo = (double*)J_out;
+        a.ca = RK_A[stage - 1];
+        a.cb = RK_B[stage - 1];
+        a.cst = RK_C[stage - 1];
+        a.dt_host = dt;
+        a.mode = 0;
+        cudaError_t e;
+        const int n = d3_stage(c->d3, a, &c->dev->status, c->stream, &e);
+        if (n < 0) return cuda_fail(c, e, "3D stage kernels");
+        count(c, n);
+        return ES_OK;
+    }
     StageParams P = stage_params(c);
     P.ca = RK_A[stage - 1];
     P.cb = RK_B[stage - 1];
@@ -606,7 +752,12 @@ int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, double*
     if (!c || !JU || !J || !x || !dt_host) return fail(c, ES_ERR_ARG, "null argument");
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
-    if (mesh_on_fp32(c)) {
+    if (c->d3) {
+        cudaError_t e;
+        const int n = d3_cfl(c->d3, (const double*)JU, (const double*)J, x, c->dev, c->stream, &e);
+        if (n < 0) return cuda_fail(c, e, "3D time-step kernels");
+        count(c, n);
+    } else if (mesh_on_fp32(c)) {
         k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, nullptr, c->fdisp, c->fxd);
         k_cfl_f<<<c->grid1d, 256, 0, c->stream>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J,
                                                    c->fdisp, c->dev);
@@ -630,7 +781,13 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
     k_set_dt<<<1, 32, 0, c->stream>>>(c->dev, dt);
     count(c, 2);
     int rc;
-    if (mesh_on_fp32(c)) {
+    if (c->d3) {
+        cudaError_t e;
+        const int n = d3_mesh(c->d3, (const double*)JU, (const double*)J, xn, xdot, c->dev, c->stream, &e);
+        if (n < 0) return cuda_fail(c, e, "3D mesh kernels");
+        count(c, n);
+        rc = ES_OK;
+    } else if (mesh_on_fp32(c)) {
         k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
         count(c);
         rc = enqueue_mesh32(c, JU, J, xdot);
@@ -664,6 +821,7 @@ int es_mesh_solve(es_ctx* c, const void* JU, const void* J, const double* xn, co
     if (!c || !JU || !J || !xn || (!x_out && !disp_out)) return fail(c, ES_ERR_ARG, "null argument");
     if (x_out && (x_out == xn || (x_start && x_out == x_start))) return fail(c, ES_ERR_ARG, "x_out aliases an input");
     if (x_start && !(guard_ratio >= 0.0)) return fail(c, ES_ERR_ARG, "guard ratio must be >= 0");
+    if (c->d3) return fail(c, ES_ERR_ARG, "es_mesh_solve is defined for 1D and 2D meshes");
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
     const double* om = enqueue_monitor(c, JU, J);
@@ -846,7 +1004,7 @@ int es_run_host(es_ctx* c, void* JU_host, void* J_host, double* x_host, int nste
 
 int es_autotune(es_ctx* c, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host) {
     if (!c || !JU || !J || !x) return fail(c, ES_ERR_ARG, "null argument");
-    if (c->p.dim == 1) {
+    if (c->p.dim != 2) {                 // one stage shape in 1D and 3D
         c->tuned = 1;
         if (tile_host) *tile_host = 1;
         return ES_OK;

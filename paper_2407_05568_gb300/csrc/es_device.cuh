@@ -93,13 +93,15 @@ __device__ __forceinline__ double mr_weno5(double wm2, double wm1, double w0, do
     const double b2 = (13.0 / 12.0) * s2a * s2a + 0.25 * s2b * s2b;
     // beta_3: coefficients c1..c4 of the quartic q(x) = sum c_k x^k (unit cell
     // centred at 0) whose cell averages are w_{-2..2}; odd part from
-    // o1 = (w1 - w-1)/2, o2 = (w2 - w-2)/2, even part from e0, e1, e2.
+    // o1 = (w1 - w-1)/2, o2 = (w2 - w-2)/2, even part from the means of w_{+-1} and
+    // w_{+-2} relative to w0 (beta ignores a constant added to the data, so everything is
+    // formed from differences: no rounding of |w|-sized terms in small indicators)
     const double o1 = 0.5 * (wp1 - wm1), o2 = 0.5 * (wp2 - wm2);
-    const double e0 = w0, e1 = 0.5 * (wp1 + wm1), e2 = 0.5 * (wp2 + wm2);
+    const double a1 = 0.5 * ((wp1 - w0) + (wm1 - w0)), a2 = 0.5 * ((wp2 - w0) + (wm2 - w0));
     const double c3 = (o2 - 2.0 * o1) * (1.0 / 6.0);
     const double c1 = (34.0 * o1 - 5.0 * o2) * (1.0 / 24.0);
-    const double c4 = (e2 - 4.0 * e1 + 3.0 * e0) * (1.0 / 12.0);
-    const double c2 = (12.0 * e1 - 11.0 * e0 - e2) * 0.125;
+    const double c4 = (a2 - 4.0 * a1) * (1.0 / 12.0);
+    const double c2 = (12.0 * a1 - a2) * 0.125;
     // int_{-1/2}^{1/2} of (q')^2 + (q'')^2 + (q''')^2 + (q'''')^2 (int x^2 = 1/12, x^4 = 1/80,
     // x^6 = 1/448), collected by monomial: c1^2 + c1 c3/2 + 13/3 c2^2 + 3129/80 c3^2
     // + 21/5 c2 c4 + 87617/140 c4^2

@@ -117,11 +117,12 @@ __device__ __forceinline__ float mr_weno5_f(float wm2, float wm1, float w0, floa
     const float s2a = wm1 - 2.0f * w0 + wp1, s2b = wp1 - wm1;
     const float b2 = (13.0f / 12.0f) * s2a * s2a + 0.25f * s2b * s2b;
     const float o1 = 0.5f * (wp1 - wm1), o2 = 0.5f * (wp2 - wm2);
-    const float e0 = w0, e1 = 0.5f * (wp1 + wm1), e2 = 0.5f * (wp2 + wm2);
+    // even part relative to w0 (beta ignores a constant added to the data)
+    const float a1 = 0.5f * ((wp1 - w0) + (wm1 - w0)), a2 = 0.5f * ((wp2 - w0) + (wm2 - w0));
     const float c3 = (o2 - 2.0f * o1) * (1.0f / 6.0f);
     const float c1 = (34.0f * o1 - 5.0f * o2) * (1.0f / 24.0f);
-    const float c4 = (e2 - 4.0f * e1 + 3.0f * e0) * (1.0f / 12.0f);
-    const float c2 = (12.0f * e1 - 11.0f * e0 - e2) * 0.125f;
+    const float c4 = (a2 - 4.0f * a1) * (1.0f / 12.0f);
+    const float c2 = (12.0f * a1 - a2) * 0.125f;
     const float b3 = c1 * (c1 + 0.5f * c3) + c2 * ((13.0f / 3.0f) * c2 + 4.2f * c4) + (3129.0f / 80.0f) * c3 * c3
                    + (87617.0f / 140.0f) * c4 * c4;
     const float t = 0.5f * (fabsf(b3 - b1) + fabsf(b3 - b2));

@@ -25,8 +25,8 @@ ES_MONITOR = {"vdw": 0, "smooth": 1}
 class EsParams(ctypes.Structure):
     _fields_ = [
         ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double), ("cv", ctypes.c_double),
-        ("dim", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int),
-        ("dxi", ctypes.c_double * 2), ("period", ctypes.c_double * 2), ("bc", ctypes.c_int * 2),
+        ("dim", ctypes.c_int), ("n1", ctypes.c_int), ("n2", ctypes.c_int), ("n3", ctypes.c_int),
+        ("dxi", ctypes.c_double * 3), ("period", ctypes.c_double * 3), ("bc", ctypes.c_int * 3),
         ("weno_gamma", ctypes.c_double * 3), ("weno_eps", ctypes.c_double), ("sign_tol", ctypes.c_double),
         ("dissipation", ctypes.c_int), ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
         ("moving", ctypes.c_int), ("monitor", ctypes.c_int), ("kappa", ctypes.c_int),
@@ -123,13 +123,15 @@ def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e
     g = w["gas"]
     p.a, p.b, p.R, p.cv = g["a"], g["b"], g["R"], g["cv"]
     p.dim = w["dim"]
-    p.n1 = w["n"][-1] if w["dim"] == 2 else w["n"][0]
-    p.n2 = w["n"][0] if w["dim"] == 2 else 1
+    n = tuple(w["n"])[::-1]                     # workloads list sizes slowest axis first
+    p.n1 = n[0]
+    p.n2 = n[1] if w["dim"] >= 2 else 1
+    p.n3 = n[2] if w["dim"] == 3 else 1
     for k in range(w["dim"]):
         p.dxi[k] = w["dxi"][k]
         p.period[k] = w["period"][k]
         p.bc[k] = ES_BC[w["bc"][k]]
-    p.weno_gamma[:] = (0.005, 0.045, 0.95)
+    p.weno_gamma[:] = tuple(w.get("weno_gammas", (0.005, 0.045, 0.95)))
     p.weno_eps = weno_eps
     # round-off size of a zero plain jump, relative to the terms forming it: FP64
     # rounding, or a few FP32 roundings (the acoustic jumps of an entropy wave cancel
