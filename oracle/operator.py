@@ -24,8 +24,10 @@ Readings of points the paper leaves open (each listed in the design notes):
     (1e-12) times the size of the terms that form it, sum_a |R_am|
     (|(TV_i)_a| + |(TV_{i+1})_a|), is round-off of an exactly zero jump and
     has sign 0 (so Y = 0), which keeps the switch from turning on or off on
-    the last bits of equal states; Y = 0 adds no entropy, so the flux stays
-    entropy stable.
+    the last bits of equal states; for the tangential waves the v_t entry of
+    R counts as |v_t| + c there (round-off in a velocity follows the flow's
+    velocity scale, also where v_t itself is zero); Y = 0 adds no entropy, so
+    the flux stays entropy stable.
 """
 from dataclasses import dataclass, field
 from fractions import Fraction
@@ -456,8 +458,13 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
     jump_weno = W_plus - W_minus
     jump = Wst[3] - Wst[2]
     # a plain jump within round-off of the terms that form W_i and W_{i+1}
-    # (sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|)) is round-off of a zero jump: sign 0
-    scale = np.einsum("ab...,a...->b...", np.abs(R), np.abs(TV[2]) + np.abs(TV[3]))
+    # (sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|)) is round-off of a zero jump: sign 0; for a
+    # tangential wave the velocity's round-off follows the flow's velocity scale |v_t| + c, so its
+    # v_t entry counts as |v_t| + c (a zero tangential velocity is otherwise judged by its own noise)
+    aTV = np.abs(TV[2]) + np.abs(TV[3])
+    scale = np.einsum("ab...,a...->b...", np.abs(R), aTV)
+    for m in range(2, d + 1):
+        scale[m] = scale[m] + np.abs(R[m, m]) * c * aTV[-1]
     jump = np.where(np.abs(jump) <= sch.sign_tol * scale, 0.0, jump)
     Y = (np.sign(jump_weno) * np.sign(jump) > 0).astype(np.float64)
     incr = np.einsum("ab...,b...->a...", R, Y * jump_weno)  # R Y [[W]]

@@ -353,3 +353,28 @@ def test_moving_mesh_step_3d_keeps_free_stream_and_conserves():
     assert np.abs(x1 - w["x"]).max() > 1e-6
     assert np.allclose(JU1.sum(axis=(1, 2, 3)), JU.sum(axis=(1, 2, 3)), rtol=1e-13, atol=1e-13)
     assert np.isclose(J1.sum(), J.sum(), rtol=1e-13)
+
+
+def test_sign_switch_ignores_velocity_noise_where_v_t_is_zero():
+    """Where the exact tangential velocity is zero, velocity noise at the level of rounding (1e-18)
+    must not turn on the tangential waves' dissipation: the dead zone of Y counts the tangential
+    entry of R as |v_t| + c (round-off in a velocity follows the flow's velocity scale)."""
+    n = 14
+    X, Y, Z, d = _grid(n, periodic=False)
+    sch = _scheme3(d, bc="outflow")
+    g = sch.gas
+    inside = X**2 + Y**2 + Z**2 < 0.25
+    U0 = thermo.prim_to_cons(g, np.where(inside, 1.2, 0.6), np.zeros((3,) + X.shape), np.where(inside, 1.8, 1.0))
+    x = np.stack([X, Y, Z])
+    J = op.node_jacobian(sch, x)
+    # one stage: the flow starts at the sphere, the far field keeps v = 0 exactly
+    dt = 0.5 * stepper.cfl_dt(sch, U0 * J, J, x, 0.4)
+    JU1, J1 = stepper.rk_stage(sch, 0, dt, U0 * J, J, U0 * J, J, x, np.zeros_like(x))
+    still = np.all(JU1[1:4] == 0.0, axis=0)
+    assert still.any() and not still.all()
+    rng = np.random.default_rng(1)
+    JUn = JU1.copy()
+    JUn[1:4] += np.where(still, 1e-18 * rng.standard_normal((3,) + X.shape), 0.0)
+    dU, _ = op.rhs(sch, JU1, J1, x, np.zeros_like(x))
+    dUn, _ = op.rhs(sch, JUn, J1, x, np.zeros_like(x))
+    assert np.abs(dUn - dU).max() < 1e-12 * np.abs(dU).max()
