@@ -344,8 +344,9 @@ __device__ __forceinline__ void face_dissipation3(const double* S, int NB, int l
     double scl[5];
     scl[0] = sA * (common + fabs(vn - c) * aTV[1] + fabs(Hm) * aTV[4]);
     scl[1] = sE * (common + fabs(vn) * aTV[1] + fabs(mid) * aTV[4]);
-    scl[2] = sT * (aTV[2] + avt1 * aTV[4]);
-    scl[3] = sT * (aTV[3] + avt2 * aTV[4]);
+    // tangential waves: round-off in a velocity follows the flow's velocity scale |v_t| + c
+    scl[2] = sT * (aTV[2] + (avt1 + c) * aTV[4]);
+    scl[3] = sT * (aTV[3] + (avt2 + c) * aTV[4]);
     scl[4] = sA * (common + fabs(vn + c) * aTV[1] + fabs(Hp) * aTV[4]);
     double y[5];
 #pragma unroll

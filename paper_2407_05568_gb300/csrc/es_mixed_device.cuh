@@ -322,7 +322,7 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
         const float avt = fabsf(vt);
         scl[0] = sA * (aTV[0] + fabsf(vn - c) * aTV[1] + avt * aTV[2] + fabsf(Hm) * aTV[3]);
         scl[1] = sE * (aTV[0] + fabsf(vn) * aTV[1] + avt * aTV[2] + fabsf(mid) * aTV[3]);
-        scl[2] = sT * (aTV[2] + avt * aTV[3]);
+        scl[2] = sT * (aTV[2] + (avt + c) * aTV[3]);     // velocity round-off scales with |v_t| + c
         scl[3] = sA * (aTV[0] + fabsf(vn + c) * aTV[1] + avt * aTV[2] + fabsf(Hp) * aTV[3]);
     }
     float y[DIM + 2];

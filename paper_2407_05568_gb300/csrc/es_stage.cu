@@ -194,7 +194,7 @@ __device__ __forceinline__ void face_dissipation(const double* S, int NB, int l,
         const double avt = fabs(vt);
         scl[0] = sA * (aTV[0] + fabs(vn - c) * aTV[1] + avt * aTV[2] + fabs(Hm) * aTV[3]);
         scl[1] = sE * (aTV[0] + fabs(vn) * aTV[1] + avt * aTV[2] + fabs(mid) * aTV[3]);
-        scl[2] = sT * (aTV[2] + avt * aTV[3]);
+        scl[2] = sT * (aTV[2] + (avt + c) * aTV[3]);     // velocity round-off scales with |v_t| + c
         scl[3] = sA * (aTV[0] + fabs(vn + c) * aTV[1] + avt * aTV[2] + fabs(Hp) * aTV[3]);
     }
     double y[DIM + 2];
