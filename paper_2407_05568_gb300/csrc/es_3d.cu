@@ -70,6 +70,11 @@ __device__ __forceinline__ double field3(const Grid3& g, const double* f, int i1
                   state_index(i3, g.n[2], g.bc[2]))];
 }
 
+// node at least `m` nodes inside the mesh in every direction (its stencil needs no ghost rule)
+__device__ __forceinline__ bool inside3(const Grid3& g, int i1, int i2, int i3, int m) {
+    return i1 >= m && i1 < g.n[0] - m && i2 >= m && i2 < g.n[1] - m && i3 >= m && i3 < g.n[2] - m;
+}
+
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -109,6 +114,11 @@ __global__ void k3_coords(Grid3 g, const double* xn, const double* xdot, double 
     for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
         const int e1 = int(e % E1), e2 = int((e / E1) % E2), e3 = int(e / (size_t(E1) * E2));
         const int i1 = e1 - 3, i2 = e2 - 3, i3 = e3 - 3;
+        if (inside3(g, i1, i2, i3, 0)) {
+            const size_t id = idx3(g, i1, i2, i3);
+            for (int c = 0; c < 3; ++c) XE[c * NE + e] = xdot ? xn[c * N + id] + cdt * xdot[c * N + id] : xn[c * N + id];
+            continue;
+        }
         for (int c = 0; c < 3; ++c)
             XE[c * NE + e] = ghost_value3(g, xn + c * N, xdot ? xdot + c * N : nullptr, cdt, i1, i2, i3, c);
     }
@@ -121,6 +131,7 @@ __global__ void k3_deriv(Grid3 g, const double* XE, double* D) {
     const size_t st[3] = {1, size_t(E1), size_t(E1) * E2};
     for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
         const int ee[3] = {int(e % E1), int((e / E1) % E2), int(e / (size_t(E1) * E2))};
+#pragma unroll
         for (int l = 0; l < 3; ++l) {
             const bool ok = ee[l] >= 3 && ee[l] < g.n[l] + 3;
             for (int p = 0; p < 3; ++p) {
@@ -140,7 +151,6 @@ __global__ void k3_deriv(Grid3 g, const double* XE, double* D) {
 __global__ void k3_metric(Grid3 g, int k, const double* XE, const double* D, double* NKo) {
     const int E1 = g.n[0] + 6, E2 = g.n[1] + 6;
     const size_t NE = size_t(E1) * E2 * (g.n[2] + 6);
-    const size_t st[3] = {1, size_t(E1), size_t(E1) * E2};
     int m1 = g.n[0], m2 = g.n[1], m3 = g.n[2];
     if (k == 0) m1 += 6;
     else if (k == 1) m2 += 6;
@@ -148,6 +158,8 @@ __global__ void k3_metric(Grid3 g, int k, const double* XE, const double* D, dou
     const size_t M = size_t(m1) * m2 * m3;
     const int l = (k + 1) % 3, m = (k + 2) % 3;
     const double scale = g.inv_dxi[l] * g.inv_dxi[m];
+    const size_t stl = l == 0 ? 1 : (l == 1 ? size_t(E1) : size_t(E1) * E2);
+    const size_t stm = m == 0 ? 1 : (m == 1 ? size_t(E1) : size_t(E1) * E2);
     for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < M; t += size_t(gridDim.x) * blockDim.x) {
         const int a1 = int(t % m1), a2 = int((t / m1) % m2), a3 = int(t / (size_t(m1) * m2));
         // extended-grid position: the metric grid already carries the 3 ghosts along xi_k
@@ -161,7 +173,7 @@ __global__ void k3_metric(Grid3 g, int k, const double* XE, const double* D, dou
 #pragma unroll
             for (int a = 1; a <= 3; ++a) {
                 const double h = 0.5 * ec_alpha(a);
-                const size_t sm = a * st[m], sl = a * st[l];
+                const size_t sm = a * stm, sl = a * stl;
                 A += h * (Dl[e + sm] * Xq[e + sm] - Dl[e - sm] * Xq[e - sm]);
                 B += h * (Dm[e + sl] * Xq[e + sl] - Dm[e - sl] * Xq[e - sl]);
             }
@@ -402,7 +414,7 @@ struct Pencil {
 };
 
 template <int K, int LB, int W, int NT>
-__global__ void __launch_bounds__(NT, 1) k3_dir(Dir3Params P) {
+__global__ void __launch_bounds__(NT, W >= 16 ? 1 : 2) k3_dir(Dir3Params P) {
     using PC = Pencil<LB, W>;
     constexpr int LS = PC::LS, NB = PC::NB, NP = PC::NP, NFc = PC::NF;
     extern __shared__ double smem[];
@@ -572,23 +584,35 @@ __global__ void __launch_bounds__(NT, 1) k3_dir(Dir3Params P) {
     }
 }
 
-// pencil shape: 16 nodes along xi_K by 16 lines, 288 threads (one per face of a pass)
-constexpr int P3_LB = 16, P3_W = 16, P3_NT = 288;
-
-template <int K>
-static cudaError_t dir_prepare() {
-    return cudaFuncSetAttribute(k3_dir<K, P3_LB, P3_W, P3_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(Pencil<P3_LB, P3_W>::SMEM));
+// pencil shapes: 16 nodes along xi_K by 16 lines with 288 threads (one per face of a pass, one CTA
+// per SM by shared memory), or by 8 lines with 160 threads (two CTAs per SM: one CTA's loads overlap
+// the other's arithmetic)
+template <int K, int LB, int W, int NT>
+static cudaError_t dir_prepare_shape() {
+    return cudaFuncSetAttribute(k3_dir<K, LB, W, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(Pencil<LB, W>::SMEM));
 }
 
 template <int K>
-static cudaError_t dir_launch(const Dir3Params& P, cudaStream_t s) {
+static cudaError_t dir_prepare() {
+    cudaError_t e = dir_prepare_shape<K, 16, 16, 288>();
+    if (e == cudaSuccess) e = dir_prepare_shape<K, 16, 8, 160>();
+    return e;
+}
+
+template <int K, int LB, int W, int NT>
+static cudaError_t dir_launch_shape(const Dir3Params& P, cudaStream_t s) {
     const Grid3& g = P.g;
     const int nA = K == 0 ? g.n[1] : g.n[0];
     const int nB = K == 2 ? g.n[1] : g.n[2];
-    const long long blocks = (long long)((g.n[K] + P3_LB - 1) / P3_LB) * ((nA + P3_W - 1) / P3_W) * nB;
-    k3_dir<K, P3_LB, P3_W, P3_NT><<<unsigned(blocks), P3_NT, Pencil<P3_LB, P3_W>::SMEM, s>>>(P);
+    const long long blocks = (long long)((g.n[K] + LB - 1) / LB) * ((nA + W - 1) / W) * nB;
+    k3_dir<K, LB, W, NT><<<unsigned(blocks), NT, Pencil<LB, W>::SMEM, s>>>(P);
     return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t dir_launch(const Dir3Params& P, int shape, cudaStream_t s) {
+    return shape == 1 ? dir_launch_shape<K, 16, 8, 160>(P, s) : dir_launch_shape<K, 16, 16, 288>(P, s);
 }
 
 // ================================================================ CFL (eq. cfl), zero mesh velocity
@@ -654,13 +678,15 @@ __global__ void k3_mon_terms(Grid3 g, MonitorParams mp, const double* rhoF, cons
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int i1 = int(id % g.n[0]), i2 = int((id / g.n[0]) % g.n[1]), i3 = int(id / (size_t(g.n[0]) * g.n[1]));
         double gr = 0.0, gg = 0.0, lg = 0.0, lr = 0.0;
+        const bool in = inside3(g, i1, i2, i3, 1);
+        const size_t stride[3] = {1, size_t(g.n[0]), size_t(g.n[0]) * g.n[1]};
         for (int k = 0; k < 3; ++k) {
             const int d1 = k == 0, d2 = k == 1, d3 = k == 2;
             const double h = g.inv_dxi[k];
-            const double rp = field3(g, rhoF, i1 + d1, i2 + d2, i3 + d3);
-            const double rm = field3(g, rhoF, i1 - d1, i2 - d2, i3 - d3);
-            const double Gp = field3(g, GF, i1 + d1, i2 + d2, i3 + d3);
-            const double Gm = field3(g, GF, i1 - d1, i2 - d2, i3 - d3);
+            const double rp = in ? rhoF[id + stride[k]] : field3(g, rhoF, i1 + d1, i2 + d2, i3 + d3);
+            const double rm = in ? rhoF[id - stride[k]] : field3(g, rhoF, i1 - d1, i2 - d2, i3 - d3);
+            const double Gp = in ? GF[id + stride[k]] : field3(g, GF, i1 + d1, i2 + d2, i3 + d3);
+            const double Gm = in ? GF[id - stride[k]] : field3(g, GF, i1 - d1, i2 - d2, i3 - d3);
             const double r0 = rhoF[id], G0 = GF[id];
             const double a = (rp - rm) * 0.5 * h, bb = (Gp - Gm) * 0.5 * h;
             const double c = (Gp - 2.0 * G0 + Gm) * h * h, e = (rp - 2.0 * r0 + rm) * h * h;
@@ -701,13 +727,16 @@ __global__ void k3_filter(Grid3 g, const double* in, double* out) {
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int i1 = int(id % g.n[0]), i2 = int((id / g.n[0]) % g.n[1]), i3 = int(id / (size_t(g.n[0]) * g.n[1]));
+        const bool fast = inside3(g, i1, i2, i3, 1);
+        const long long s2 = g.n[0], s3 = (long long)g.n[0] * g.n[1];
         double s = 0.0;
         for (int d3 = -1; d3 <= 1; ++d3) {
             double pl = 0.0;
             for (int d2 = -1; d2 <= 1; ++d2) {
                 double row = 0.0;
                 for (int d1 = -1; d1 <= 1; ++d1)
-                    row += (d1 == 0 ? 0.5 : 0.25) * field3(g, in, i1 + d1, i2 + d2, i3 + d3);
+                    row += (d1 == 0 ? 0.5 : 0.25) *
+                           (fast ? in[(long long)id + d1 + d2 * s2 + d3 * s3] : field3(g, in, i1 + d1, i2 + d2, i3 + d3));
                 pl += (d2 == 0 ? 0.5 : 0.25) * row;
             }
             s += (d3 == 0 ? 0.5 : 0.25) * pl;
@@ -735,24 +764,33 @@ __global__ void k3_jacobi(Grid3 g, const double* omega, const double* xn, double
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int ii[3] = {int(id % g.n[0]), int((id / g.n[0]) % g.n[1]), int(id / (size_t(g.n[0]) * g.n[1]))};
         if (fixed3(g, ii)) {
+#pragma unroll
             for (int c = 0; c < 3; ++c) xout[c * N + id] = xin[c * N + id];
             continue;
         }
         const double w0 = omega[id];
         double den = 0.0, num[3] = {0.0, 0.0, 0.0};
+        const bool fast = inside3(g, ii[0], ii[1], ii[2], 1);
+        const size_t stride[3] = {1, size_t(g.n[0]), size_t(g.n[0]) * g.n[1]};
+#pragma unroll
         for (int kk = 0; kk < 3; ++kk) {
             int p[3] = {ii[0], ii[1], ii[2]}, q[3] = {ii[0], ii[1], ii[2]};
             p[kk] += 1;
             q[kk] -= 1;
             const double ih2 = g.inv_dxi[kk] * g.inv_dxi[kk];
-            const double wp = 0.5 * (w0 + field3(g, omega, p[0], p[1], p[2])) * ih2;
-            const double wm = 0.5 * (w0 + field3(g, omega, q[0], q[1], q[2])) * ih2;
+            const size_t ip = id + stride[kk], iq = id - stride[kk];
+            const double wp = 0.5 * (w0 + (fast ? omega[ip] : field3(g, omega, p[0], p[1], p[2]))) * ih2;
+            const double wm = 0.5 * (w0 + (fast ? omega[iq] : field3(g, omega, q[0], q[1], q[2]))) * ih2;
             den += wp + wm;
-            for (int c = 0; c < 3; ++c)
-                num[c] += wp * ghost_value3(g, xin + c * N, nullptr, 0.0, p[0], p[1], p[2], c) +
-                          wm * ghost_value3(g, xin + c * N, nullptr, 0.0, q[0], q[1], q[2], c);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double xp = fast ? xin[c * N + ip] : ghost_value3(g, xin + c * N, nullptr, 0.0, p[0], p[1], p[2], c);
+                const double xq = fast ? xin[c * N + iq] : ghost_value3(g, xin + c * N, nullptr, 0.0, q[0], q[1], q[2], c);
+                num[c] += wp * xp + wm * xq;
+            }
         }
         const double iden = rcp_nr(den);
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double xv = num[c] * iden;
             chg = fmax(chg, fabs(xv - xin[c * N + id]));
@@ -783,6 +821,7 @@ __global__ void k3_limiter(Grid3 g, const double* xn, const double* xa, const do
     double m = 1.0;
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int ii[3] = {int(id % g.n[0]), int((id / g.n[0]) % g.n[1]), int(id / (size_t(g.n[0]) * g.n[1]))};
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double dx = xit[k * N + id] - xn[k * N + id];
             int p[3] = {ii[0], ii[1], ii[2]};
@@ -877,7 +916,7 @@ int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_
         P.NK = d->NK[k];
         P.first = k == 0;
         P.last = k == 2;
-        e = k == 0 ? dir_launch<0>(P, s) : (k == 1 ? dir_launch<1>(P, s) : dir_launch<2>(P, s));
+        e = k == 0 ? dir_launch<0>(P, d->shape, s) : (k == 1 ? dir_launch<1>(P, d->shape, s) : dir_launch<2>(P, d->shape, s));
         ++n;
     }
     *err = e;

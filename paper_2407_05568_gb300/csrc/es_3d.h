@@ -26,6 +26,7 @@ struct Ctx3 {
     int filter_passes, sweeps;
     double eps;
     int grid;                 // blocks of the grid-stride kernels
+    int shape;                // pencil shape of the direction kernels: 0 = 16 x 16 lines, 1 = 16 x 8
     size_t N;                 // nodes
     size_t NE;                // nodes of the grid extended by 3 ghosts in every direction
     size_t NKk[3];            // nodes of direction k's metric grid (3 ghosts along xi_k only)

@@ -620,6 +620,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;
         d->grid = c->grid1d;
+        d->shape = p->tile == 2 ? 1 : 0;
         d->rhoF = c->rhoF;
         d->GF = c->GF;
         d->t0 = c->t0;
