@@ -75,6 +75,38 @@ __device__ __forceinline__ bool inside3(const Grid3& g, int i1, int i2, int i3, 
     return i1 >= m && i1 < g.n[0] - m && i2 >= m && i2 < g.n[1] - m && i3 >= m && i3 < g.n[2] - m;
 }
 
+// stride of direction k in a [n3][n2][n1] field
+__device__ __forceinline__ size_t stride3(const Grid3& g, int k) {
+    return k == 0 ? 1 : (k == 1 ? size_t(g.n[0]) : size_t(g.n[0]) * g.n[1]);
+}
+
+// index of the node at offset s (|s| = 1) along direction k from in-mesh node id (position i_k),
+// ghosts by copy / wrap: the neighbour can leave the mesh along k only
+__device__ __forceinline__ size_t nb_index(const Grid3& g, size_t id, int ik, int k, int s) {
+    const int n = g.n[k];
+    int j = ik + s;
+    if (j < 0 || j >= n) j = g.bc[k] == ES_BC_PERIODIC ? (j < 0 ? j + n : j - n) : ik;
+    return id + (long long)(j - ik) * (long long)stride3(g, k);
+}
+
+// coordinate component `comp` of that neighbour: wrap with the period shift, or odd reflection
+// about the boundary node (2 x_b - x_{b -+ 1}), the one-direction case of the ghost rule
+__device__ __forceinline__ double nb_coord(const Grid3& g, const double* f, size_t id, int ik, int k, int s,
+                                           int comp) {
+    const int n = g.n[k];
+    const int j = ik + s;
+    const long long st = (long long)stride3(g, k);
+    if (j >= 0 && j < n) return f[id + (long long)s * st];
+    if (g.bc[k] == ES_BC_PERIODIC) {
+        const int r = j < 0 ? j + n : j - n;
+        double v = f[id + (long long)(r - ik) * st];
+        if (comp == k) v += (j < 0 ? -1.0 : 1.0) * g.period[k];
+        return v;
+    }
+    const int b = j < 0 ? 0 : n - 1, m = j < 0 ? 1 : n - 2;
+    return 2.0 * f[id + (long long)(b - ik) * st] - f[id + (long long)(m - ik) * st];
+}
+
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -678,15 +710,13 @@ __global__ void k3_mon_terms(Grid3 g, MonitorParams mp, const double* rhoF, cons
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int i1 = int(id % g.n[0]), i2 = int((id / g.n[0]) % g.n[1]), i3 = int(id / (size_t(g.n[0]) * g.n[1]));
         double gr = 0.0, gg = 0.0, lg = 0.0, lr = 0.0;
-        const bool in = inside3(g, i1, i2, i3, 1);
-        const size_t stride[3] = {1, size_t(g.n[0]), size_t(g.n[0]) * g.n[1]};
+        const int ii[3] = {i1, i2, i3};
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int d1 = k == 0, d2 = k == 1, d3 = k == 2;
             const double h = g.inv_dxi[k];
-            const double rp = in ? rhoF[id + stride[k]] : field3(g, rhoF, i1 + d1, i2 + d2, i3 + d3);
-            const double rm = in ? rhoF[id - stride[k]] : field3(g, rhoF, i1 - d1, i2 - d2, i3 - d3);
-            const double Gp = in ? GF[id + stride[k]] : field3(g, GF, i1 + d1, i2 + d2, i3 + d3);
-            const double Gm = in ? GF[id - stride[k]] : field3(g, GF, i1 - d1, i2 - d2, i3 - d3);
+            const size_t ip = nb_index(g, id, ii[k], k, 1), im = nb_index(g, id, ii[k], k, -1);
+            const double rp = rhoF[ip], rm = rhoF[im];
+            const double Gp = GF[ip], Gm = GF[im];
             const double r0 = rhoF[id], G0 = GF[id];
             const double a = (rp - rm) * 0.5 * h, bb = (Gp - Gm) * 0.5 * h;
             const double c = (Gp - 2.0 * G0 + Gm) * h * h, e = (rp - 2.0 * r0 + rm) * h * h;
@@ -727,19 +757,27 @@ __global__ void k3_filter(Grid3 g, const double* in, double* out) {
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int i1 = int(id % g.n[0]), i2 = int((id / g.n[0]) % g.n[1]), i3 = int(id / (size_t(g.n[0]) * g.n[1]));
-        const bool fast = inside3(g, i1, i2, i3, 1);
-        const long long s2 = g.n[0], s3 = (long long)g.n[0] * g.n[1];
+        // offsets of the neighbours along each direction (ghosts by copy / wrap, per direction)
+        long long o1[3], o2[3], o3[3];
+        o1[1] = o2[1] = o3[1] = 0;
+        o1[0] = (long long)nb_index(g, id, i1, 0, -1) - (long long)id;
+        o1[2] = (long long)nb_index(g, id, i1, 0, 1) - (long long)id;
+        o2[0] = (long long)nb_index(g, id, i2, 1, -1) - (long long)id;
+        o2[2] = (long long)nb_index(g, id, i2, 1, 1) - (long long)id;
+        o3[0] = (long long)nb_index(g, id, i3, 2, -1) - (long long)id;
+        o3[2] = (long long)nb_index(g, id, i3, 2, 1) - (long long)id;
         double s = 0.0;
-        for (int d3 = -1; d3 <= 1; ++d3) {
+#pragma unroll
+        for (int d3 = 0; d3 < 3; ++d3) {
             double pl = 0.0;
-            for (int d2 = -1; d2 <= 1; ++d2) {
+#pragma unroll
+            for (int d2 = 0; d2 < 3; ++d2) {
                 double row = 0.0;
-                for (int d1 = -1; d1 <= 1; ++d1)
-                    row += (d1 == 0 ? 0.5 : 0.25) *
-                           (fast ? in[(long long)id + d1 + d2 * s2 + d3 * s3] : field3(g, in, i1 + d1, i2 + d2, i3 + d3));
-                pl += (d2 == 0 ? 0.5 : 0.25) * row;
+#pragma unroll
+                for (int d1 = 0; d1 < 3; ++d1) row += (d1 == 1 ? 0.5 : 0.25) * in[(long long)id + o1[d1] + o2[d2] + o3[d3]];
+                pl += (d2 == 1 ? 0.5 : 0.25) * row;
             }
-            s += (d3 == 0 ? 0.5 : 0.25) * pl;
+            s += (d3 == 1 ? 0.5 : 0.25) * pl;
         }
         out[id] = s;
     }
@@ -770,22 +808,16 @@ __global__ void k3_jacobi(Grid3 g, const double* omega, const double* xn, double
         }
         const double w0 = omega[id];
         double den = 0.0, num[3] = {0.0, 0.0, 0.0};
-        const bool fast = inside3(g, ii[0], ii[1], ii[2], 1);
-        const size_t stride[3] = {1, size_t(g.n[0]), size_t(g.n[0]) * g.n[1]};
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) {
-            int p[3] = {ii[0], ii[1], ii[2]}, q[3] = {ii[0], ii[1], ii[2]};
-            p[kk] += 1;
-            q[kk] -= 1;
             const double ih2 = g.inv_dxi[kk] * g.inv_dxi[kk];
-            const size_t ip = id + stride[kk], iq = id - stride[kk];
-            const double wp = 0.5 * (w0 + (fast ? omega[ip] : field3(g, omega, p[0], p[1], p[2]))) * ih2;
-            const double wm = 0.5 * (w0 + (fast ? omega[iq] : field3(g, omega, q[0], q[1], q[2]))) * ih2;
+            const double wp = 0.5 * (w0 + omega[nb_index(g, id, ii[kk], kk, 1)]) * ih2;
+            const double wm = 0.5 * (w0 + omega[nb_index(g, id, ii[kk], kk, -1)]) * ih2;
             den += wp + wm;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double xp = fast ? xin[c * N + ip] : ghost_value3(g, xin + c * N, nullptr, 0.0, p[0], p[1], p[2], c);
-                const double xq = fast ? xin[c * N + iq] : ghost_value3(g, xin + c * N, nullptr, 0.0, q[0], q[1], q[2], c);
+                const double xp = nb_coord(g, xin + c * N, id, ii[kk], kk, 1, c);
+                const double xq = nb_coord(g, xin + c * N, id, ii[kk], kk, -1, c);
                 num[c] += wp * xp + wm * xq;
             }
         }
@@ -824,16 +856,10 @@ __global__ void k3_limiter(Grid3 g, const double* xn, const double* xa, const do
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const double dx = xit[k * N + id] - xn[k * N + id];
-            int p[3] = {ii[0], ii[1], ii[2]};
-            if (dx < 0.0) {
-                p[k] -= 1;
-                m = fmin(m, div_nr(-(xn[k * N + id] - ghost_value3(g, xn + k * N, nullptr, 0.0, p[0], p[1], p[2], k)),
-                                   2.0 * dx));
-            } else if (dx > 0.0) {
-                p[k] += 1;
-                m = fmin(m, div_nr(ghost_value3(g, xn + k * N, nullptr, 0.0, p[0], p[1], p[2], k) - xn[k * N + id],
-                                   2.0 * dx));
-            }
+            if (dx < 0.0)
+                m = fmin(m, div_nr(-(xn[k * N + id] - nb_coord(g, xn + k * N, id, ii[k], k, -1, k)), 2.0 * dx));
+            else if (dx > 0.0)
+                m = fmin(m, div_nr(nb_coord(g, xn + k * N, id, ii[k], k, 1, k) - xn[k * N + id], 2.0 * dx));
         }
     }
     m = block_min(m);
