@@ -552,7 +552,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->nc = p->dim + 2;
     c->mixed = p->precision == ES_PREC_MIXED;
     c->tile = p->tile > 0 ? p->tile - 1 : 0;
-    c->tuned = p->tile > 0 || p->dim != 2;
+    c->tuned = p->tile > 0 || p->dim == 1;
     c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
@@ -620,7 +620,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;
         d->grid = c->grid1d;
-        d->shape = p->tile == 2 ? 1 : 0;
+        d->shape = p->tile == 2 ? 1 : 0;           // tile 0: chosen by es_autotune
         d->rhoF = c->rhoF;
         d->GF = c->GF;
         d->t0 = c->t0;
@@ -1003,13 +1003,74 @@ int es_run_host(es_ctx* c, void* JU_host, void* J_host, double* x_host, int nste
     return ES_OK;
 }
 
+// 3D: time the operator (metrics, node fields, three direction launches) with each pencil shape
+static int autotune3(es_ctx* c, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host) {
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, e, "event");
+    }
+    Stage3 a = {};
+    a.JUn = a.JUs = (const double*)JU;
+    a.Jn = a.Js = (const double*)J;
+    a.xn = x;
+    a.JUo = (double*)c->S1;
+    a.Jo = (double*)c->S1J;
+    a.dt_host = 1.0;
+    a.mode = 1;
+    const int saved = c->d3->shape;
+    int best = 0;
+    float best_ms = 3.0e38f;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        c->d3->shape = k;
+        float ms = 0.0f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // the first evaluation loads the kernels
+            e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess) {
+                cudaError_t el;
+                const int n = d3_stage(c->d3, a, &c->dev->status, c->stream, &el);
+                if (n < 0) e = el;
+                else count(c, n);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms += t;
+        }
+        if (ms_host) ms_host[k] = ms / 2;
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        c->d3->shape = saved;
+        return cuda_fail(c, e, "autotune");
+    }
+    c->d3->shape = best;
+    c->tuned = 1;
+    if (c->gexec) {                        // the step graph holds the old shape
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (tile_host) *tile_host = best + 1;
+    return ES_OK;
+}
+
 int es_autotune(es_ctx* c, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host) {
     if (!c || !JU || !J || !x) return fail(c, ES_ERR_ARG, "null argument");
-    if (c->p.dim != 2) {                 // one stage shape in 1D and 3D
+    if (c->p.dim == 1) {                 // one stage shape in 1D
         c->tuned = 1;
         if (tile_host) *tile_host = 1;
         return ES_OK;
     }
+    if (c->d3) return autotune3(c, JU, J, x, tile_host, ms_host);
     CK(cudaStreamSynchronize(c->stream), "sync");
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");

@@ -258,3 +258,31 @@ def test_3d_rejections():
     ctx, JU, J, xt = gpu_setup(w)
     with pytest.raises(es.EsError):
         es.es_mesh_solve(ctx, JU, J, xt, None, xt.clone())
+
+
+def test_pencil_shapes_agree_bitwise_and_autotune():
+    """The two pencil shapes of the 3D direction kernels group faces differently but evaluate each
+    face the same way: identical bits; the autotuner picks one of them."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = CASES["wavy_periodic_rough"]()
+    outs = []
+    for tile in (1, 2):
+        p = es.make_params(w, tile=tile)
+        ctx = es.es_create(p)
+        xt = torch.tensor(w["x"], dtype=torch.float64, device="cuda")
+        J = torch.empty(w["x"].shape[1:], dtype=torch.float64, device="cuda")
+        es.es_init_mesh(ctx, xt, J)
+        JU = torch.empty((5,) + w["x"].shape[1:], dtype=torch.float64, device="cuda")
+        es.es_prim_to_cons(ctx, torch.tensor(w["rho"], device="cuda"), torch.tensor(w["v"], device="cuda"),
+                           torch.tensor(w["p"], device="cuda"), J, JU)
+        xd = torch.tensor(np.ascontiguousarray(_xdot(w)), dtype=torch.float64, device="cuda")
+        dU, dJ = torch.empty_like(JU), torch.empty_like(J)
+        es.es_rhs(ctx, JU, J, xt, xd, dU, dJ)
+        assert es.es_check(ctx) == 0
+        outs.append((dU.cpu().numpy(), dJ.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ctx, JU, J, xt = gpu_setup(w)
+    k, ms = es.es_autotune(ctx, JU, J, xt)
+    assert k in (1, 2) and ms[0] > 0 and ms[1] > 0
