@@ -10,15 +10,16 @@ Readings of points the paper leaves open:
   * gradients and second derivatives of the monitor use second-order central
     differences on the computational mesh (the order of Sec. 4's mesh
     equation); a term whose normalising maximum is 0 is dropped;
-  * monitor and filter ghosts: periodic = wrap, outflow = copy;
+  * monitor and filter ghosts: periodic = wrap, outflow = copy, wall / symmetry = mirror;
   * at most mu sweeps are taken; with eps > 0 the sweeps stop as soon as
     max |x^[nu+1] - x^[nu]| < eps;
-  * nodes on an outflow boundary stay fixed; periodic boundary nodes move;
+  * nodes on an outflow boundary stay fixed; nodes on a wall or symmetry plane slide along it
+    (their normal coordinate stays); periodic boundary nodes move;
   * Delta_gamma = min(1, the bounds of Sec. 4 over all nodes and directions).
 """
 import numpy as np
 
-from .operator import OUTFLOW, PERIODIC, axis_of, pad, pad_coords
+from .operator import PERIODIC, axis_of, mirrored, pad, pad_coords
 
 
 def _shift(a, k, dim, bc, s):
@@ -97,16 +98,19 @@ def low_pass(omega, dim, bc):
 
 
 def _fixed_mask(shape, dim, bc):
-    """True on nodes of outflow boundaries (they do not move)."""
-    fixed = np.zeros(shape, dtype=bool)
+    """Per coordinate component, True where it does not move: every component on an outflow
+    boundary, the normal component on a wall or symmetry plane (its nodes slide along it)."""
+    fixed = np.zeros((dim,) + tuple(shape), dtype=bool)
     for k in range(dim):
-        if bc[k] == OUTFLOW:
-            ax = axis_of(k, dim)
+        if bc[k] == PERIODIC:
+            continue
+        ax = axis_of(k, dim)
+        for end, mir in zip((0, -1), mirrored(bc[k])):
             idx = [slice(None)] * dim
-            idx[ax] = 0
-            fixed[tuple(idx)] = True
-            idx[ax] = -1
-            fixed[tuple(idx)] = True
+            idx[ax] = end
+            comps = [k] if mir else list(range(dim))
+            for c in comps:
+                fixed[c][tuple(idx)] = True
     return fixed
 
 
@@ -139,7 +143,7 @@ def jacobi(sch, x0, omega, mu, eps=0.0):
                 hi[ax] = slice(2, 2 + n)
                 lo[ax] = slice(0, n)
                 num += (wp[k] * xp[c][tuple(hi)] + wm[k] * xp[c][tuple(lo)]) / sch.dxi[k] ** 2
-            new[c] = np.where(fixed, x[c], num / den)
+            new[c] = np.where(fixed[c], x[c], num / den)
         change = float(np.max(np.abs(new - x)))
         x = new
         taken += 1

@@ -13,6 +13,9 @@ Readings of points the paper leaves open (each listed in the design notes):
   * ghost nodes: periodic = wrap (coordinates shifted by the period);
     outflow = copy of the boundary state, coordinates and mesh velocity
     extended by odd reflection about the boundary node (x_{-m} = 2 x_0 - x_m);
+    wall / symmetry plane = the mirror image about the boundary node: the state
+    mirrored with the normal momentum negated, coordinates and mesh velocity
+    mirrored along the plane and oddly reflected across it;
   * the face normal n, its length L and the face J xi_t used in the
     dissipation are arithmetic means of the two neighbouring node values;
   * the rotation angle theta is taken with the quadrant of (n_1, n_2), i.e.
@@ -40,6 +43,8 @@ from .weno import mr_weno5
 
 PERIODIC = "periodic"
 OUTFLOW = "outflow"
+REFLECT = "reflect"            # reflective wall at both ends of the direction
+SYMMETRY_LO = "symmetry_lo"    # symmetry plane at the low end, outflow at the high end
 
 
 # ---------------------------------------------------------------- parameters
@@ -54,7 +59,7 @@ class Scheme:
     weno_eps: float = 1e-12
     sign_tol: float = 1e-12                      # |[[W]]| below this relative size counts as 0 in Y
     dissipation: bool = True                     # False: the EC scheme alone
-    bc: tuple = (PERIODIC,)                      # per direction xi_1, xi_2
+    bc: tuple = (PERIODIC,)                      # per direction xi_1, xi_2, xi_3
     dxi: tuple = (1.0,)                          # Delta xi_k
     period: tuple = (1.0,)                       # period length of x_k for periodic directions
 
@@ -81,26 +86,56 @@ def ec_alphas(w):
 
 # ------------------------------------------------------------------- ghosts
 
-def pad(a, g, axis, bc, shift=0.0, odd=False):
+def mirrored(bc):
+    """(low end, high end) of a direction that mirror the state about the boundary node."""
+    return (bc in (REFLECT, SYMMETRY_LO), bc == REFLECT)
+
+
+def pad(a, g, axis, bc, shift=0.0, odd=False, tangential=False):
     """Extend array a by g ghost nodes on both ends of `axis`.
 
     periodic: wrap, adding -shift / +shift on the low / high side;
-    outflow : odd=False copies the boundary value, odd=True reflects
-              (a_{-m} = 2 a_0 - a_m, a_{N-1+m} = 2 a_{N-1} - a_{N-1-m}).
+    outflow end: odd=True (coordinates, mesh velocity) reflects oddly about the boundary node
+                 (a_{-m} = 2 a_0 - a_m, a_{N-1+m} = 2 a_{N-1} - a_{N-1-m}); odd=False (state,
+                 monitor fields) copies the boundary value;
+    wall / symmetry end: the mirror image about the boundary node: a_{-m} = a_m for the state and
+                 for coordinate / velocity components along the plane (tangential=True), odd
+                 reflection for the component normal to it.
     """
     a = np.moveaxis(a, axis, -1)
     n = a.shape[-1]
     if bc == PERIODIC:
         lo = a[..., n - g:] - shift
         hi = a[..., :g] + shift
-    elif odd:
-        lo = 2.0 * a[..., :1] - a[..., g:0:-1]
-        hi = 2.0 * a[..., -1:] - a[..., -2:-2 - g:-1]
     else:
-        lo = np.repeat(a[..., :1], g, axis=-1)
-        hi = np.repeat(a[..., -1:], g, axis=-1)
+        mlo, mhi = mirrored(bc)
+        odd_lo = odd and not (mlo and tangential)
+        odd_hi = odd and not (mhi and tangential)
+        if odd_lo:
+            lo = 2.0 * a[..., :1] - a[..., g:0:-1]
+        else:
+            lo = a[..., g:0:-1] if mlo else np.repeat(a[..., :1], g, axis=-1)
+        if odd_hi:
+            hi = 2.0 * a[..., -1:] - a[..., -2:-2 - g:-1]
+        else:
+            hi = a[..., -2:-2 - g:-1] if mhi else np.repeat(a[..., -1:], g, axis=-1)
     out = np.concatenate([lo, a, hi], axis=-1)
     return np.moveaxis(out, -1, axis)
+
+
+def pad_state(U, g, k, dim, bc):
+    """State with g ghosts along direction k: pad() per component, and at a mirroring end the
+    momentum normal to it (component 1 + k) changes sign (a wall or symmetry plane)."""
+    ax = axis_of(k, dim)
+    out = pad(U, g, 1 + ax, bc)
+    mlo, mhi = mirrored(bc)
+    if mlo or mhi:
+        mom = np.moveaxis(out[1 + k], ax, -1)
+        if mlo:
+            mom[..., :g] *= -1.0
+        if mhi:
+            mom[..., -g:] *= -1.0
+    return out
 
 
 def axis_of(k, dim):
@@ -115,7 +150,7 @@ def pad_coords(sch, x, g):
         comps = []
         for c in range(sch.dim):
             shift = sch.period[k] if (c == k and sch.bc[k] == PERIODIC) else 0.0
-            comps.append(pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], shift=shift, odd=True))
+            comps.append(pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], shift=shift, odd=True, tangential=c != k))
         out = np.stack(comps)
     return out
 
@@ -124,7 +159,7 @@ def pad_velocity(sch, xdot, g):
     """Mesh velocity with g ghosts: the linear part of the coordinate extension."""
     out = xdot
     for k in range(sch.dim):
-        out = np.stack([pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], odd=True)
+        out = np.stack([pad(out[c], g, axis_of(k, sch.dim), sch.bc[k], odd=True, tangential=c != k)
                         for c in range(sch.dim)])
     return out
 
@@ -485,7 +520,7 @@ def rhs(sch, JU, J, x, xdot):
     dJ = np.zeros_like(J)
     for k in range(d):
         ax = axis_of(k, d)
-        U_pad = pad(U, 3, 1 + ax, sch.bc[k])
+        U_pad = pad_state(U, 3, k, d, sch.bc[k])
         V_pad = thermo.entropy_variables(g, U_pad)
         n, xt = direction_metrics(sch, x, xdot, k, 3)
         FU, FJ = direction_fluxes(sch, _line_view(U_pad, ax), np.moveaxis(n, 1 + ax, -1),

@@ -9,7 +9,7 @@ continued, and what features a network sees:
     fundamental derivative G of Sec. 1, and the displacement of x^n from the
     Cartesian mesh (x_00 + i dxi_1, y_00 + j dxi_2) in cells;
   * warm start from a network output o (cells): x_s = x^n + dxi_k o_k at nodes
-    that move, x^n at fixed (outflow-boundary) nodes and where o is not finite;
+    that move, x^n at fixed (boundary) coordinates and where o is not finite;
   * guarded solve: the first sweep runs from x^n and from x_s, changing the mesh
     by c0 and c1 (max norm); x_s is continued if c1 < kappa c0 (kappa = the
     guard ratio), else x^n; the sweeps then stop as in ``mesh.jacobi`` (eps, at
@@ -52,11 +52,11 @@ def features(sch, mc, JU, J, x):
 
 
 def warm_start(sch, xn, out):
-    """x_s = x^n + dxi_k out_k at moving nodes; fixed nodes and non-finite outputs keep x^n."""
+    """x_s = x^n + dxi_k out_k at moving nodes; fixed coordinates and non-finite outputs keep x^n."""
     fixed = mesh._fixed_mask(xn.shape[1:], sch.dim, sch.bc)
     xs = xn.copy()
     for k in range(sch.dim):
-        ok = ~fixed & np.isfinite(out[k])
+        ok = ~fixed[k] & np.isfinite(out[k])
         xs[k] = np.where(ok, xn[k] + sch.dxi[k] * np.where(ok, out[k], 0.0), xn[k])
     return xs
 

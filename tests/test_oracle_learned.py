@@ -200,10 +200,11 @@ def test_warm_start_keeps_fixed_nodes_and_drops_nonfinite():
     out = np.full(x.shape, 0.25)
     out[0, 5, 5] = np.nan
     xs = warmstart.warm_start(sch, x, out)
-    fixed = mesh._fixed_mask(x.shape[1:], 2, sch.bc)
-    assert np.array_equal(xs[:, fixed], x[:, fixed])
+    fixed = mesh._fixed_mask(x.shape[1:], 2, sch.bc)          # per component (outflow: all of them)
+    for c in range(2):
+        assert np.array_equal(xs[c][fixed[c]], x[c][fixed[c]])
     assert xs[0, 5, 5] == x[0, 5, 5]
-    inner = ~fixed
+    inner = ~fixed[0]
     inner[5, 5] = False
     assert np.allclose((xs[0] - x[0])[inner], 0.25 * sch.dxi[0], rtol=1e-12)
 
