@@ -47,9 +47,10 @@ __device__ __forceinline__ size_t eidx(const Grid3& g, int e1, int e2, int e3) {
 // `comp` (-1: none)
 __device__ __forceinline__ double ghost_value3(const Grid3& g, const double* f, const double* f2, double c2,
                                                int i1, int i2, int i3, int comp) {
-    const GhostTerms t1 = ghost_terms(i1, g.n[0], g.bc[0]);
-    const GhostTerms t2 = ghost_terms(i2, g.n[1], g.bc[1]);
-    const GhostTerms t3 = ghost_terms(i3, g.n[2], g.bc[2]);
+    // a coordinate / velocity component other than direction d lies along that direction's planes
+    const GhostTerms t1 = ghost_terms(i1, g.n[0], g.bc[0], comp != 0);
+    const GhostTerms t2 = ghost_terms(i2, g.n[1], g.bc[1], comp != 1);
+    const GhostTerms t3 = ghost_terms(i3, g.n[2], g.bc[2], comp != 2);
     double acc = 0.0;
     for (int c = 0; c < t3.nterm; ++c)
         for (int b = 0; b < t2.nterm; ++b)
@@ -83,9 +84,7 @@ __device__ __forceinline__ size_t stride3(const Grid3& g, int k) {
 // index of the node at offset s (|s| = 1) along direction k from in-mesh node id (position i_k),
 // ghosts by copy / wrap: the neighbour can leave the mesh along k only
 __device__ __forceinline__ size_t nb_index(const Grid3& g, size_t id, int ik, int k, int s) {
-    const int n = g.n[k];
-    int j = ik + s;
-    if (j < 0 || j >= n) j = g.bc[k] == ES_BC_PERIODIC ? (j < 0 ? j + n : j - n) : ik;
+    const int j = state_index(ik + s, g.n[k], g.bc[k]);
     return id + (long long)(j - ik) * (long long)stride3(g, k);
 }
 
@@ -104,6 +103,7 @@ __device__ __forceinline__ double nb_coord(const Grid3& g, const double* f, size
         return v;
     }
     const int b = j < 0 ? 0 : n - 1, m = j < 0 ? 1 : n - 2;
+    if (comp != k && end_mirrored(g.bc[k], j < 0)) return f[id + (long long)(m - ik) * st];
     return 2.0 * f[id + (long long)(b - ik) * st] - f[id + (long long)(m - ik) * st];
 }
 
@@ -490,6 +490,11 @@ __global__ void __launch_bounds__(NT, W >= 16 ? 1 : 2) k3_dir(Dir3Params P) {
         const int bx = line * LS + q;
 #pragma unroll 1
         for (int f = 0; f < F3_COUNT; ++f) S[f * NB + bx] = P.NF[f * N + id];
+        if ((s < 0 || s >= nk) && end_mirrored(g.bc[K], s < 0)) {     // wall / symmetry ghost
+            S[(G_V1 + K) * NB + bx] = -S[(G_V1 + K) * NB + bx];
+            S[(G_VT1 + K) * NB + bx] = -S[(G_VT1 + K) * NB + bx];
+            S[(G_RV1 + K) * NB + bx] = -S[(G_RV1 + K) * NB + bx];
+        }
         // metrics: the metric grid holds s in [-3, n_K + 3); the tail of a ragged pencil is clamped
         int se = s + 3;
         se = se < 0 ? 0 : (se > nk + 5 ? nk + 5 : se);
@@ -503,17 +508,19 @@ __global__ void __launch_bounds__(NT, W >= 16 ? 1 : 2) k3_dir(Dir3Params P) {
         S[G_NZ * NB + bx] = nz;
         double xt = 0.0;
         if (P.xdot) {
-            // mesh velocity at the node: odd reflection / wrap along xi_K (no period shift)
-            const GhostTerms tk = ghost_terms(s, nk, g.bc[K]);
+            // mesh velocity at the node: wrap, odd reflection, or at a wall / symmetry end the
+            // mirror image (components along the plane mirrored, the normal one reflected)
             double xd[3] = {0.0, 0.0, 0.0};
-            for (int u = 0; u < tk.nterm; ++u) {
-                int k1 = i1, k2 = i2, k3 = i3;
-                if (K == 0) k1 = tk.idx[u];
-                else if (K == 1) k2 = tk.idx[u];
-                else k3 = tk.idx[u];
-                const size_t iu = idx3(g, k1, k2, k3);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) xd[c] += tk.w[u] * P.xdot[c * N + iu];
+            for (int c = 0; c < 3; ++c) {
+                const GhostTerms tk = ghost_terms(s, nk, g.bc[K], c != K);
+                for (int u = 0; u < tk.nterm; ++u) {
+                    int k1 = i1, k2 = i2, k3 = i3;
+                    if (K == 0) k1 = tk.idx[u];
+                    else if (K == 1) k2 = tk.idx[u];
+                    else k3 = tk.idx[u];
+                    xd[c] += tk.w[u] * P.xdot[c * N + idx3(g, k1, k2, k3)];
+                }
             }
             xt = -(xd[0] * nx + xd[1] * ny + xd[2] * nz);
         }
@@ -783,9 +790,18 @@ __global__ void k3_filter(Grid3 g, const double* in, double* out) {
     }
 }
 
-__device__ __forceinline__ bool fixed3(const Grid3& g, const int* ii) {
+// Coordinate component c of a boundary node that does not move: every component on an outflow
+// end, the normal one on a wall or symmetry end (the node slides along the plane).
+__device__ __forceinline__ bool fixed3(const Grid3& g, const int* ii, int c) {
     bool f = false;
-    for (int k = 0; k < 3; ++k) f = f || (g.bc[k] == ES_BC_OUTFLOW && (ii[k] == 0 || ii[k] == g.n[k] - 1));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (g.bc[k] == ES_BC_PERIODIC) continue;
+        const bool lo = ii[k] == 0, hi = ii[k] == g.n[k] - 1;
+        if (!lo && !hi) continue;
+        const bool mir = end_mirrored(g.bc[k], lo);
+        f = f || !mir || c == k;
+    }
     return f;
 }
 
@@ -801,11 +817,6 @@ __global__ void k3_jacobi(Grid3 g, const double* omega, const double* xn, double
     double chg = 0.0;
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
         const int ii[3] = {int(id % g.n[0]), int((id / g.n[0]) % g.n[1]), int(id / (size_t(g.n[0]) * g.n[1]))};
-        if (fixed3(g, ii)) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) xout[c * N + id] = xin[c * N + id];
-            continue;
-        }
         const double w0 = omega[id];
         double den = 0.0, num[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -824,7 +835,7 @@ __global__ void k3_jacobi(Grid3 g, const double* omega, const double* xn, double
         const double iden = rcp_nr(den);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double xv = num[c] * iden;
+            const double xv = fixed3(g, ii, c) ? xin[c * N + id] : num[c] * iden;
             chg = fmax(chg, fabs(xv - xin[c * N + id]));
             xout[c * N + id] = xv;
         }

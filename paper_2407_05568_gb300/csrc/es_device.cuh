@@ -134,7 +134,14 @@ struct GhostTerms {
     int q;         // period count (periodic only)
 };
 
-__device__ __forceinline__ GhostTerms ghost_terms(int i, int n, int bc) {
+// Walls and symmetry planes: the end of a direction that mirrors the mesh and the state.
+__device__ __forceinline__ bool end_mirrored(int bc, bool lo) {
+    return bc == ES_BC_REFLECT || (bc == ES_BC_SYMMETRY_LO && lo);
+}
+
+// `tangential`: a coordinate or mesh-velocity component along the boundary plane, which a
+// mirroring end mirrors (value of the mirror node) instead of reflecting oddly.
+__device__ __forceinline__ GhostTerms ghost_terms(int i, int n, int bc, bool tangential = false) {
     GhostTerms g;
     g.q = 0;
     if (i >= 0 && i < n) {
@@ -148,15 +155,24 @@ __device__ __forceinline__ GhostTerms ghost_terms(int i, int n, int bc) {
         // occur in the unused tail of a ragged tile and must stay in bounds
         int m = i < 0 ? -i : 2 * (n - 1) - i;
         m = m < 0 ? 0 : (m > n - 1 ? n - 1 : m);
-        g.idx[0] = i < 0 ? 0 : n - 1; g.w[0] = 2.0; g.idx[1] = m; g.w[1] = -1.0; g.nterm = 2;
+        if (tangential && end_mirrored(bc, i < 0)) {
+            g.idx[0] = m; g.w[0] = 1.0; g.nterm = 1;
+        } else {
+            g.idx[0] = i < 0 ? 0 : n - 1; g.w[0] = 2.0; g.idx[1] = m; g.w[1] = -1.0; g.nterm = 2;
+        }
     }
     return g;
 }
 
-// State index for ghosts: periodic wrap, outflow copy of the boundary node.
+// State index for ghosts: periodic wrap, outflow copy of the boundary node, mirror node at a
+// wall or symmetry end (the caller negates the normal momentum there).
 __device__ __forceinline__ int state_index(int i, int n, int bc) {
     if (i >= 0 && i < n) return i;
     if (bc == ES_BC_PERIODIC) return wrap_index(i, n);
+    if (end_mirrored(bc, i < 0)) {
+        int m = i < 0 ? -i : 2 * (n - 1) - i;
+        return m < 0 ? 0 : (m > n - 1 ? n - 1 : m);
+    }
     return i < 0 ? 0 : n - 1;
 }
 

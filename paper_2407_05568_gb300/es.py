@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libesvdw.so")
 
 ES_OK, ES_ERR_ARG, ES_ERR_CUDA, ES_ERR_INADMISSIBLE, ES_ERR_MESH, ES_ERR_TIMEOUT = range(6)
-ES_BC = {"periodic": 0, "outflow": 1}
+ES_BC = {"periodic": 0, "outflow": 1, "reflect": 2, "symmetry_lo": 3}
 ES_PREC = {"fp64": 0, "mixed": 1}
 ES_MONITOR = {"vdw": 0, "smooth": 1}
 

@@ -91,13 +91,13 @@ def sine_3d(n=64, t_end=0.1, cfl=0.4, moving=False):
 
 def spherical_shock_3d(n=64, t_end=0.1, cfl=0.4, moving=True):
     """3D spherically symmetric shock tube (Example 5.7 setup): the RP1 states of Table 5.1,
-    (1.818, 0, 3.0) inside r < 0.5 and (0.275, 0, 0.575) outside, on [0, 1]^3 with outflow
-    boundaries; MM monitor with rho and G, alpha = (1200, 1200, 0), 5 filter passes,
-    10 Jacobi sweeps."""
+    (1.818, 0, 3.0) inside r < 0.5 and (0.275, 0, 0.575) outside, on the octant [0, 1]^3 with
+    symmetry planes through the centre (x_k = 0) and outflow at x_k = 1; MM monitor with rho and
+    G, alpha = (1200, 1200, 0), 5 filter passes, 10 Jacobi sweeps."""
     x1, d = uniform_nodes(n, 0.0, 1.0, False)
     Z, Yc, X = np.meshgrid(x1, x1, x1, indexing="ij")
     inside = X**2 + Yc**2 + Z**2 < 0.25
-    return dict(gas=UNITS_A, dim=3, n=(n, n, n), dxi=(d, d, d), bc=("outflow",) * 3,
+    return dict(gas=UNITS_A, dim=3, n=(n, n, n), dxi=(d, d, d), bc=("symmetry_lo",) * 3,
                 period=(1.0, 1.0, 1.0), x=np.stack([X, Yc, Z]),
                 rho=np.where(inside, 1.818, 0.275), v=np.zeros((3,) + X.shape),
                 p=np.where(inside, 3.0, 0.575), t_end=t_end, cfl=cfl, moving=moving,

@@ -2,8 +2,9 @@
 
 Meshes have three different sizes (so a swapped axis shows), more nodes along xi_1 than one
 pencil (16) holds and ragged pencils in every direction; periodic wavy meshes with a
-mesh velocity, and the spherical shock tube geometry of Example 5.7 with outflow boundaries
-and the moving mesh.  Bar: 1e-12 relative per step, as in 1D/2D.
+mesh velocity, outflow boundaries, walls, and the spherical shock tube geometry of Example 5.7
+with symmetry planes through the centre and the moving mesh.  Bar: 1e-12 relative per step, as in
+1D/2D.
 """
 import numpy as np
 import pytest
@@ -69,7 +70,8 @@ CASES = {
     "wavy_periodic_smooth": lambda: _box(20, 18, 17, True, amp=0.01),
     "wavy_periodic_rough": lambda: _box(19, 22, 12, True, amp=0.01, seed=4),
     "outflow_rough": lambda: _box(18, 12, 21, False, amp=0.0, seed=9),
-    "shock_ragged": lambda: _shock(19, 17, 21),
+    "shock_ragged": lambda: _shock(19, 17, 21),          # symmetry planes at x_k = 0, outflow at 1
+    "walls_rough": lambda: dict(_box(17, 20, 19, False, amp=0.0, seed=13), bc=("reflect",) * 3),
 }
 
 
@@ -112,7 +114,7 @@ def test_rhs_parity_3d(case, dissipation):
     assert np.abs(dU_o).sum() > 1e-6 * scale * min(w["dxi"])
 
 
-@pytest.mark.parametrize("case", ["wavy_periodic_rough", "shock_ragged"])
+@pytest.mark.parametrize("case", ["wavy_periodic_rough", "shock_ragged", "walls_rough"])
 def test_rk_stage_parity_3d(case):
     import torch
 
@@ -157,7 +159,7 @@ def _moving(w, monitor="vdw"):
 
 
 @pytest.mark.parametrize("case,monitor", [("shock_ragged", "vdw"), ("wavy_periodic_smooth", "smooth"),
-                                          ("outflow_rough", "vdw")])
+                                          ("outflow_rough", "vdw"), ("walls_rough", "vdw")])
 def test_mesh_redistribution_parity_3d(case, monitor):
     import torch
 
@@ -176,7 +178,7 @@ def test_mesh_redistribution_parity_3d(case, monitor):
 
 
 @pytest.mark.parametrize("case,monitor,nsteps", [("shock_ragged", "vdw", 2), ("wavy_periodic_smooth", "smooth", 2),
-                                                 ("wavy_periodic_rough", None, 1)])
+                                                 ("wavy_periodic_rough", None, 1), ("walls_rough", "vdw", 1)])
 def test_step_parity_3d(case, monitor, nsteps):
     """Full steps through es_steps (CFL, mesh redistribution, three stages; a CUDA graph)."""
     from paper_2407_05568_gb300 import es
