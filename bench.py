@@ -370,8 +370,9 @@ def measure_three_d(args, dev, stream):
             "precision_form": "fp64", "value": nodes * 3 / (ms * 1e-3), "unit": "cell-updates/s",
             "ms_per_step": ms, "steps": K, "gpu_launches_per_step": launches,
             "operator_ms": ms_rhs, "operator_cell_updates_per_s": nodes / (ms_rhs * 1e-3),
-            "pencil": {1: "16 nodes x 16 lines", 2: "16 nodes x 8 lines"}[shape],
-            "autotune_ms_per_shape": list(shape_ms[:2]),
+            "pencil": {1: "16 nodes x 16 lines", 2: "16 nodes x 8 lines", 3: "16 nodes x 4 lines",
+                       4: "32 nodes x 4 lines"}[shape],
+            "autotune_ms_per_shape": list(shape_ms[:4]),
             "l2": f"working set {nodes * 8 * 66 / 1e9:.1f} GB (larger than L2); no flush"}
 
 

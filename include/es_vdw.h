@@ -24,7 +24,7 @@
  *   the cross-form metrics of Sec. 3.2 (eq. SCLCoeff), the theta/phi rotation of
  *   Sec. 3.3 and the 27-point filter of Sec. 4.  ES_PREC_FP64 only.  es_create,
  *   es_init_mesh, es_prim_to_cons, es_rhs, es_rk_stage, es_cfl_dt,
- *   es_mesh_redistribute, es_steps, es_run_host, es_autotune (two pencil shapes) and the
+ *   es_mesh_redistribute, es_steps, es_run_host, es_autotune (four pencil shapes) and the
  *   time and status calls accept a 3D context; es_mesh_features, es_mesh_solve,
  *   es_mesh_warm_start and es_set_warm_start return ES_ERR_ARG for it.  A 3D
  *   context holds about 66 n1 n2 n3 + 12 (n1+6)(n2+6)(n3+6) doubles of scratch.
@@ -111,7 +111,8 @@ typedef struct es_params {
     int    tile;            /* stage tile shape: 0 = chosen by es_autotune (run by the first es_steps
                                if not called before); k = 1 .. ES_NTILES: shape k of the precision's
                                2D table (FP64: 32x8, 25x11, 16x16, 32x12, 20x10 nodes; mixed: 32x8, 25x6,
-                               20x8, 32x16, 16x8); in 3D 1 = pencils of 16 nodes x 16 lines, 2 = 16 x 8 */
+                               20x8, 32x16, 16x8); in 3D the direction kernels' pencils: 1 = 16 nodes
+                               x 16 lines, 2 = 16 x 8, 3 = 16 x 4, 4 = 32 x 4 */
 } es_params;
 
 #define ES_NTILES 5
@@ -192,8 +193,7 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
  * tile recomputes): in ES_PREC_FP64 every shape gives the same bits, in
  * ES_PREC_MIXED the same values to FP32 rounding.  Writes the
  * chosen shape (1 .. ES_NTILES) and, if ms_host is non-null, the probe times in ms
- * (ES_NTILES of them in 2D; 2 in 3D, whose direction kernels have two pencil shapes,
- * 16 nodes x 16 lines and 16 x 8).  1D contexts have one shape (returns 1).
+ * (ES_NTILES of them in 2D; 4 in 3D, the pencil shapes of its direction kernels).  1D contexts have one shape (returns 1).
  * Synchronises. */
 int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host);
 

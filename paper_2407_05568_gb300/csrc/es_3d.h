@@ -26,7 +26,7 @@ struct Ctx3 {
     int filter_passes, sweeps;
     double eps;
     int grid;                 // blocks of the grid-stride kernels
-    int shape;                // pencil shape of the direction kernels: 0 = 16 x 16 lines, 1 = 16 x 8
+    int shape;                // pencil shape of the direction kernels (D3_NSHAPES of them, see es_3d.cu)
     size_t N;                 // nodes
     size_t NE;                // nodes of the grid extended by 3 ghosts in every direction
     size_t NKk[3];            // nodes of direction k's metric grid (3 ghosts along xi_k only)
@@ -51,6 +51,7 @@ struct Stage3 {
     int reuse;                // the metrics and node fields of (xn, JUs, Js) are in the buffers
 };
 
+constexpr int D3_NSHAPES = 4;
 cudaError_t d3_alloc(Ctx3* d);
 void d3_free(Ctx3* d);
 cudaError_t d3_prepare();

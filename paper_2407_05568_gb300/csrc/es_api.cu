@@ -462,7 +462,7 @@ int check_params(const es_params* p) {
     if (p->dim == 1 && p->n2 != 1) return 0;
     if (p->dim >= 2 && p->n2 < 8) return 0;
     if (p->dim < 3 && p->n3 != 0 && p->n3 != 1) return 0;
-    if (p->dim == 3 && (p->n3 < 8 || p->precision != ES_PREC_FP64)) return 0;
+    if (p->dim == 3 && (p->n3 < 8 || p->precision != ES_PREC_FP64 || p->tile > D3_NSHAPES)) return 0;
     const long long n3 = p->dim == 3 ? p->n3 : 1;
     if ((long long)p->n1 * p->n2 * n3 > (1LL << 30)) return 0;
     for (int k = 0; k < p->dim; ++k) {
@@ -621,7 +621,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;
         d->grid = c->grid1d;
-        d->shape = p->tile == 2 ? 1 : 0;           // tile 0: chosen by es_autotune
+        d->shape = p->tile >= 1 && p->tile <= D3_NSHAPES ? p->tile - 1 : 0;   // tile 0: chosen by es_autotune
         d->rhoF = c->rhoF;
         d->GF = c->GF;
         d->t0 = c->t0;
@@ -1025,7 +1025,7 @@ static int autotune3(es_ctx* c, const void* JU, const void* J, const double* x, 
     const int saved = c->d3->shape;
     int best = 0;
     float best_ms = 3.0e38f;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    for (int k = 0; k < D3_NSHAPES && e == cudaSuccess; ++k) {
         c->d3->shape = k;
         float ms = 0.0f;
         for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {   // the first evaluation loads the kernels
