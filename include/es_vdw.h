@@ -60,12 +60,12 @@ extern "C" {
 /* boundary conditions, per direction */
 #define ES_BC_PERIODIC 0        /* wrap; coordinates shifted by period[k] */
 #define ES_BC_OUTFLOW  1        /* state copied; coordinates reflected; boundary nodes fixed */
-#define ES_BC_REFLECT  2        /* wall at both ends (3D contexts only): the mirror image about the
+#define ES_BC_REFLECT  2        /* wall at both ends (ES_PREC_FP64 only): the mirror image about the
                                    boundary node -- state mirrored with the normal momentum negated,
                                    coordinates and mesh velocity mirrored along the wall and reflected
                                    across it; boundary nodes slide along the wall */
 #define ES_BC_SYMMETRY_LO 3     /* symmetry plane at the low end as ES_BC_REFLECT, outflow at the high
-                                   end (3D contexts only; e.g. an octant of a spherical problem) */
+                                   end (ES_PREC_FP64 only; e.g. an octant of a spherical problem) */
 
 /* arithmetic of the operator */
 #define ES_PREC_FP64   0        /* every step in double */

@@ -468,7 +468,8 @@ int check_params(const es_params* p) {
     for (int k = 0; k < p->dim; ++k) {
         if (!(p->dxi[k] > 0.0)) return 0;
         const bool mirror = p->bc[k] == ES_BC_REFLECT || p->bc[k] == ES_BC_SYMMETRY_LO;
-        if (p->bc[k] != ES_BC_PERIODIC && p->bc[k] != ES_BC_OUTFLOW && !(mirror && p->dim == 3)) return 0;
+        if (p->bc[k] != ES_BC_PERIODIC && p->bc[k] != ES_BC_OUTFLOW && !(mirror && p->precision == ES_PREC_FP64))
+            return 0;
         if (p->bc[k] == ES_BC_PERIODIC && !(p->period[k] > 0.0)) return 0;
     }
     if (!(p->R > 0.0) || !(p->cv > 0.0) || !(p->a >= 0.0) || !(p->b >= 0.0)) return 0;

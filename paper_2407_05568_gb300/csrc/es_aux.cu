@@ -17,9 +17,9 @@ __device__ __forceinline__ double coord_at(const GridParams& g, const double* x,
     const size_t N = size_t(g.n1) * g.n2;
     if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))   // interior: a plain load
         return x[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
-    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0]);
+    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0], comp != 0);
     GhostTerms tj;
-    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1]);
+    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1], comp != 1);
     else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
     double acc = 0.0;
     for (int a = 0; a < ti.nterm; ++a)
@@ -319,9 +319,13 @@ __device__ __forceinline__ const double* jacobi_result(const DevScalars* d, cons
     return ((d->pick + d->sweeps - 1) & 1) ? xb : xa;
 }
 
-__device__ __forceinline__ bool fixed_node(const GridParams& g, int i, int j) {
-    bool f = g.bc[0] == ES_BC_OUTFLOW && (i == 0 || i == g.n1 - 1);
-    if (g.dim == 2) f = f || (g.bc[1] == ES_BC_OUTFLOW && (j == 0 || j == g.n2 - 1));
+// Coordinate component c of a boundary node that does not move: every component on an outflow end,
+// the normal one on a wall or symmetry end (the node slides along it).
+__device__ __forceinline__ bool fixed_comp(const GridParams& g, int i, int j, int c) {
+    bool f = false;
+    if (g.bc[0] != ES_BC_PERIODIC && (i == 0 || i == g.n1 - 1)) f = !end_mirrored(g.bc[0], i == 0) || c == 0;
+    if (g.dim == 2 && g.bc[1] != ES_BC_PERIODIC && (j == 0 || j == g.n2 - 1))
+        f = f || !end_mirrored(g.bc[1], j == 0) || c == 1;
     return f;
 }
 
@@ -333,10 +337,6 @@ __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double
     double chg = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        if (fixed_node(g, i, j)) {
-            for (int c = 0; c < g.dim; ++c) xout[c * N + id] = xin[c * N + id];
-            continue;
-        }
         const double w0 = omega[id];
         double den = 0.0, num[2] = {0.0, 0.0};
         for (int kk = 0; kk < g.dim; ++kk) {
@@ -350,7 +350,7 @@ __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double
         }
         const double iden = rcp_nr(den);
         for (int c = 0; c < g.dim; ++c) {
-            const double xv = num[c] * iden;
+            const double xv = fixed_comp(g, i, j, c) ? xin[c * N + id] : num[c] * iden;
             chg = fmax(chg, fabs(xv - xin[c * N + id]));
             xout[c * N + id] = xv;
         }
@@ -517,10 +517,9 @@ __global__ void k_warm_start(GridParams g, const double* xn, const float* out, d
     const int N = g.n1 * g.n2;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        const bool fixed = fixed_node(g, i, j);
         for (int c = 0; c < 2; ++c) {
             const float o = out[c * N + id];
-            const bool ok = !fixed && isfinite(o);
+            const bool ok = !fixed_comp(g, i, j, c) && isfinite(o);
             x0[c * N + id] = xn[c * N + id] + (ok ? double(o) / g.inv_dxi[c] : 0.0);
         }
     }

@@ -237,8 +237,11 @@ __device__ __forceinline__ void load_node(double* S, int NB, int b, const StageP
     const size_t N = size_t(P.n1) * P.n2;
     const double iJ = rcp_nr(P.Js[idx]);
     const double rho = P.JUs[idx] * iJ;
-    const double m1 = P.JUs[N + idx] * iJ;
-    const double m2 = DIM == 2 ? P.JUs[2 * N + idx] * iJ : 0.0;
+    // at a wall or symmetry end the ghost is the mirror node with the normal momentum negated
+    const double f1 = (gi < 0 || gi >= P.n1) && end_mirrored(P.bc[0], gi < 0) ? -1.0 : 1.0;
+    const double f2 = DIM == 2 && (gj < 0 || gj >= P.n2) && end_mirrored(P.bc[1], gj < 0) ? -1.0 : 1.0;
+    const double m1 = f1 * (P.JUs[N + idx] * iJ);
+    const double m2 = DIM == 2 ? f2 * (P.JUs[2 * N + idx] * iJ) : 0.0;
     const double E = P.JUs[(DIM + 1) * N + idx] * iJ;
     const double irho = rcp_nr(rho);
     const double v1 = m1 * irho, v2 = m2 * irho;
@@ -291,26 +294,24 @@ template <int DIM>
 __device__ __forceinline__ void stage_coords(const StageParams& P, int gi, int gj, double cdt, double* xs,
                                              double* xd) {
     const size_t N = size_t(P.n1) * P.n2;
-    const GhostTerms ti = ghost_terms(gi, P.n1, P.bc[0]);
-    GhostTerms tj;
-    if (DIM == 2) tj = ghost_terms(gj, P.n2, P.bc[1]);
-    else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
-    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-    for (int a = 0; a < ti.nterm; ++a)
-        for (int c = 0; c < tj.nterm; ++c) {
-            const double w = ti.w[a] * tj.w[c];
-            const size_t id = size_t(tj.idx[c]) * P.n1 + ti.idx[a];
-            for (int k = 0; k < DIM; ++k) {
+    // per component k: a wall or symmetry end mirrors the components along it (tangential) and
+    // reflects the normal one; the other ends treat every component alike
+    for (int k = 0; k < DIM; ++k) {
+        const GhostTerms ti = ghost_terms(gi, P.n1, P.bc[0], k != 0);
+        GhostTerms tj;
+        if (DIM == 2) tj = ghost_terms(gj, P.n2, P.bc[1], k != 1);
+        else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
+        double as = 0.0, ad = 0.0;
+        for (int a = 0; a < ti.nterm; ++a)
+            for (int c = 0; c < tj.nterm; ++c) {
+                const double w = ti.w[a] * tj.w[c];
+                const size_t id = size_t(tj.idx[c]) * P.n1 + ti.idx[a];
                 const double xdk = P.xdot ? P.xdot[k * N + id] : 0.0;
-                acc[0][k] += w * (P.xn[k * N + id] + cdt * xdk);
-                acc[1][k] += w * xdk;
+                as += w * (P.xn[k * N + id] + cdt * xdk);
+                ad += w * xdk;
             }
-        }
-    xs[0] = acc[0][0] + ti.q * P.period[0];
-    xd[0] = acc[1][0];
-    if (DIM == 2) {
-        xs[1] = acc[0][1] + tj.q * P.period[1];
-        xd[1] = acc[1][1];
+        xs[k] = as + (k == 0 ? ti.q * P.period[0] : tj.q * P.period[1]);
+        xd[k] = ad;
     }
 }
 

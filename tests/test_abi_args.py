@@ -32,6 +32,13 @@ def test_create_rejects_bad_params(L, field, value):
     assert not h.value
 
 
+def test_create_rejects_walls_in_the_mixed_form(L):
+    p = es.make_params(wl.sine_2d(16), precision="mixed")
+    p.bc[0] = es.ES_BC["reflect"]
+    h = ctypes.c_void_p()
+    assert L.es_create(ctypes.byref(h), ctypes.byref(p), None) == es.ES_ERR_ARG
+
+
 def test_create_rejects_mixed_period_mismatch(L):
     w = wl.sine_2d(16)
     p = es.make_params(w, precision="mixed")
