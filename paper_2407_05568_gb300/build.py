@@ -24,7 +24,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 # rounding with double-float state and jumps, whose reciprocal is Newton-corrected.  FP64 code
 # is not affected by these flags.
 PER_FILE = {name: ["-prec-div=false", "-prec-sqrt=false"]
-            for name in ("es_stage_mixed.cu", "es_batch.cu", "es_mesh_f32.cu")}
+            for name in ("es_stage_mixed.cu", "es_batch.cu", "es_mesh_f32.cu", "es_3d_mixed.cu")}
 
 
 def nvcc():

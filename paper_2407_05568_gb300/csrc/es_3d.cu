@@ -912,10 +912,16 @@ cudaError_t d3_prepare() {
     return e;
 }
 
-int d3_init_J(const Ctx3* d, const double* x, double* J, cudaStream_t s, cudaError_t* err) {
-    k3_init_J<<<d->grid, 256, 0, s>>>(d->g, x, J);
+int d3_init_J(const Ctx3* d, const double* x, void* J, cudaStream_t s, cudaError_t* err) {
+    int n = 1;
+    if (d->mixed) {                                   // FP64 J into the scratch, then split
+        k3_init_J<<<d->grid, 256, 0, s>>>(d->g, x, d->RH);
+        n += d3f_init_J(const_cast<Ctx3*>(d), d->RH, J, s);
+    } else {
+        k3_init_J<<<d->grid, 256, 0, s>>>(d->g, x, (double*)J);
+    }
     *err = cudaGetLastError();
-    return *err == cudaSuccess ? 1 : -1;
+    return *err == cudaSuccess ? n : -1;
 }
 
 // metrics of x_s = xn + cst dt xdot for the three directions
@@ -932,8 +938,15 @@ int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_
     int n = 0;
     if (!a.reuse) {
         n += enqueue_metrics(d, a.xn, a.xdot, a.cst, a.dt_dev, a.dt_host, s);
-        k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, a.JUs, a.Js, d->NF, st);
-        ++n;
+        if (d->mixed) n += d3f_nodes(d, a.JUs, a.Js, st, s);
+        else {
+            k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const double*)a.JUs, (const double*)a.Js, d->NF, st);
+            ++n;
+        }
+    }
+    if (d->mixed) {
+        const int m = d3f_directions(d, a, st, s, err);
+        return m < 0 ? -1 : n + m;
     }
     Dir3Params P;
     P.g = d->g;
@@ -948,12 +961,12 @@ int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_
     P.cb = a.cb;
     P.dt_host = a.dt_host;
     P.dt_dev = a.dt_dev;
-    P.JUn = a.JUn;
-    P.Jn = a.Jn;
-    P.JUs = a.JUs;
-    P.Js = a.Js;
-    P.JUo = a.JUo;
-    P.Jo = a.Jo;
+    P.JUn = (const double*)a.JUn;
+    P.Jn = (const double*)a.Jn;
+    P.JUs = (const double*)a.JUs;
+    P.Js = (const double*)a.Js;
+    P.JUo = (double*)a.JUo;
+    P.Jo = (double*)a.Jo;
     P.status = st;
     cudaError_t e = cudaGetLastError();
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
@@ -967,17 +980,22 @@ int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_
     return e == cudaSuccess ? n : -1;
 }
 
-int d3_cfl(Ctx3* d, const double* JU, const double* J, const double* x, DevScalars* dv, cudaStream_t s,
+int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* dv, cudaStream_t s,
            cudaError_t* err) {
     int n = enqueue_metrics(d, x, nullptr, 0.0, nullptr, 0.0, s);
-    k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, JU, J, d->NF, &dv->status);
-    k3_cfl<<<d->grid, 256, 0, s>>>(d->g, d->gas, d->NF, J, d->NK[0], d->NK[1], d->NK[2], dv);
-    n += 2;
+    if (d->mixed) {
+        n += d3f_nodes(d, JU, J, &dv->status, s);
+        n += d3f_cfl(d, J, dv, s);
+    } else {
+        k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const double*)JU, (const double*)J, d->NF, &dv->status);
+        k3_cfl<<<d->grid, 256, 0, s>>>(d->g, d->gas, d->NF, (const double*)J, d->NK[0], d->NK[1], d->NK[2], dv);
+        n += 2;
+    }
     *err = cudaGetLastError();
     return *err == cudaSuccess ? n : -1;
 }
 
-int d3_mesh(Ctx3* d, const double* JU, const double* J, const double* xn, double* xdot, DevScalars* dv,
+int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
             cudaStream_t s, cudaError_t* err) {
     const int G = d->grid;
     // the elementwise kernels of the 1D/2D path see the 3D mesh as N nodes in a row
@@ -989,7 +1007,7 @@ int d3_mesh(Ctx3* d, const double* JU, const double* J, const double* xn, double
     flat.inv_dxi[0] = flat.inv_dxi[1] = 1.0;
     flat.period[0] = flat.period[1] = 0.0;
     int n = 0;
-    launch_mon_fields(flat, d->gas, JU, J, d->rhoF, d->GF, false, G, s);
+    launch_mon_fields(flat, d->gas, JU, J, d->rhoF, d->GF, d->mixed != 0, G, s);
     k3_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, d->rhoF, d->GF, d->t0, d->t1, d->t2, dv);
     k_mon_omega<<<G, 256, 0, s>>>(flat, d->mon, d->t0, d->t1, d->t2, dv, d->om0);
     n += 3;

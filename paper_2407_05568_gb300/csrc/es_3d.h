@@ -23,6 +23,7 @@ struct Ctx3 {
     Weno weno;
     MonitorParams mon;
     int diss;
+    int mixed;                // ES_PREC_MIXED: double-float state, FP32 direction kernels (es_3d_mixed.cu)
     int filter_passes, sweeps;
     double eps;
     int grid;                 // blocks of the grid-stride kernels
@@ -33,17 +34,17 @@ struct Ctx3 {
     double* XE;               // stage coordinates on the extended grid [3][NE]
     double* D;                // delta_l[x_p] on the extended grid [9][NE] (valid where xi_l is interior)
     double* NK[3];            // J dxi_k/dx_j on direction k's metric grid [3][NKk]
-    double* NF;               // node fields of the stage state [F3_COUNT][N]
-    double* RH;               // right-hand sides accumulated over the directions [6][N]
+    double* NF;               // node fields of the stage state [F3_COUNT][N] (mixed: float fields)
+    double* RH;               // right-hand sides accumulated over the directions [6][N] (mixed: float)
     // mesh scratch (the context's buffers)
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1, *xa, *xb;
 };
 
 // arguments of one operator evaluation / RK stage
 struct Stage3 {
-    const double *JUn, *Jn, *JUs, *Js;
+    const void *JUn, *Jn, *JUs, *Js;    // double, or the mixed form's double-float planes
     const double *xn, *xdot;  // mesh at t^n and its velocity (xdot nullable)
-    double *JUo, *Jo;
+    void *JUo, *Jo;
     double ca, cb, cst;       // Shu-Osher coefficients and the stage time fraction
     double dt_host;
     const double* dt_dev;     // device dt (nullptr: dt_host)
@@ -56,11 +57,17 @@ cudaError_t d3_alloc(Ctx3* d);
 void d3_free(Ctx3* d);
 cudaError_t d3_prepare();
 // each returns the number of kernels it launched (negative: a launch failed, *err set)
-int d3_init_J(const Ctx3* d, const double* x, double* J, cudaStream_t s, cudaError_t* err);
+int d3_init_J(const Ctx3* d, const double* x, void* J, cudaStream_t s, cudaError_t* err);
 int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
-int d3_cfl(Ctx3* d, const double* JU, const double* J, const double* x, DevScalars* dv, cudaStream_t s,
+int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* dv, cudaStream_t s,
            cudaError_t* err);
-int d3_mesh(Ctx3* d, const double* JU, const double* J, const double* xn, double* xdot, DevScalars* dv,
+int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
             cudaStream_t s, cudaError_t* err);
+// the mixed form's kernels (es_3d_mixed.cu)
+cudaError_t d3f_prepare();
+int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s);
+int d3f_cfl(Ctx3* d, const void* J, DevScalars* dv, cudaStream_t s);
+int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);
+int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
 
 }  // namespace es

@@ -1,0 +1,675 @@
+// es_3d_mixed.cu -- the mixed-precision form of the 3D path: the direction kernels on the FP32 pipe.
+//
+// As in the 1D/2D mixed form, the state is kept as double-float pairs (hi + lo float planes), the
+// primitive state rho, v, T of every node carries a low part so that jumps between neighbours
+// keep their digits, the two-point fluxes and MR-WENO5 run in float, and the dissipation works on
+// entropy-variable jumps from the jump decomposition of Sec. 3.1 (eq. jumpV) shared by the faces
+// of a line.  What is cheap per node stays FP64: the node fields are computed once per node in
+// double and stored as floats (with the low parts), and the metrics are the FP64 cross-form
+// metrics of es_3d.cu rounded to float at load.  The right-hand sides are accumulated over the
+// three directions in float and the Shu-Osher combination is done in double-float.
+#include <cuda_runtime.h>
+
+#include "es_3d.h"
+#include "es_device.cuh"
+#include "es_internal.h"
+#include "es_mixed_device.cuh"
+
+namespace es {
+namespace mixed3 {
+
+using mixed::df;
+using mixed::df_add;
+using mixed::df_add_f;
+using mixed::df_mul;
+using mixed::GasF;
+using mixed::inv_log_mean_f;
+using mixed::inv_log_mean_j;
+using mixed::mr_weno5_f;
+using mixed::WenoF;
+
+// float node fields (global planes and shared-memory slots)
+enum FieldM {
+    M_RHO, M_V1, M_V2, M_V3, M_T, M_IT, M_OM, M_IOM, M_G, M_RT, M_VT1, M_VT2, M_VT3, M_V2T,
+    M_RV1, M_RV2, M_RV3, M_RP, M_RHOL, M_V1L, M_V2L, M_V3L, M_TL,
+    MF_COUNT,
+    M_NX = MF_COUNT, M_NY, M_NZ, M_XT,
+    MS_COUNT
+};
+static_assert(MF_COUNT <= 23, "the float node fields reuse the FP64 node-field buffer");
+
+__device__ __forceinline__ size_t idx3(const Grid3& g, int i1, int i2, int i3) {
+    return (size_t(i3) * g.n[1] + i2) * g.n[0] + i1;
+}
+
+// ---------------------------------------------------------------- node fields
+// From the double-float state (JU: hi plane [5][N] then lo plane; J: hi then lo) in FP64, stored
+// as floats with the low parts of rho, v, T.
+__global__ void k3_nodes_f(Grid3 g, Gas G, const float* JU, const float* J, float* NF, DevStatus* st) {
+    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
+    const size_t LO = 5 * N;
+    for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
+        const double iJ = 1.0 / (double(J[id]) + double(J[N + id]));
+        double u[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) u[c] = (double(JU[c * N + id]) + double(JU[LO + c * N + id])) * iJ;
+        const double rho = u[0];
+        const double irho = 1.0 / rho;
+        const double v1 = u[1] * irho, v2 = u[2] * irho, v3 = u[3] * irho;
+        const double ke = 0.5 * (v1 * v1 + v2 * v2 + v3 * v3);
+        const double T = (u[4] * irho - ke + G.a * rho) * G.icv;
+        const float r = float(rho), Tf = float(T);
+        const float om = 1.0f - float(G.b) * r;
+        const float iom = 1.0f / om;
+        const float iT = 1.0f / Tf;
+        const float p = r * float(G.R) * Tf * iom - float(G.a) * r * r;
+        if (!(r > 0.0f) || !(om > 0.0f) || !(Tf > 0.0f) || !(p > 0.0f)) raise_error(st, ES_ERR_INADMISSIBLE, int(id));
+        NF[M_RHO * N + id] = r;
+        NF[M_RHOL * N + id] = float(rho - double(r));
+        NF[M_T * N + id] = Tf;
+        NF[M_TL * N + id] = float(T - double(Tf));
+        const double vv[3] = {v1, v2, v3};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float vh = float(vv[c]);
+            NF[(M_V1 + c) * N + id] = vh;
+            NF[(M_V1L + c) * N + id] = float(vv[c] - double(vh));
+            NF[(M_VT1 + c) * N + id] = vh * iT;
+            NF[(M_RV1 + c) * N + id] = float(u[1 + c]);
+        }
+        NF[M_IT * N + id] = iT;
+        NF[M_OM * N + id] = om;
+        NF[M_IOM * N + id] = iom;
+        NF[M_G * N + id] = float(G.R) * iom - float(G.a) * r * iT;
+        NF[M_RT * N + id] = r * iT;
+        NF[M_V2T * N + id] = float(2.0 * ke) * iT;
+        NF[M_RP * N + id] = r / p;
+    }
+}
+
+// ---------------------------------------------------------------- pair flux
+__device__ __forceinline__ void pair_flux3_f(const float* S, int NB, int l, int r, float nx, float ny, float nz,
+                                             float xt, const GasF& G, float* out) {
+    const float rl = S[M_RHO * NB + l], rr = S[M_RHO * NB + r];
+    const float Tl = S[M_T * NB + l], Tr = S[M_T * NB + r];
+    const float rho_m = 0.5f * (rl + rr);
+    const float T_m = 0.5f * (Tl + Tr);
+    const float iT_m = 0.5f * (S[M_IT * NB + l] + S[M_IT * NB + r]);
+    const float drho = (rl - rr) + (S[M_RHOL * NB + l] - S[M_RHOL * NB + r]);
+    const float ilr = inv_log_mean_j(rl, rr, drho);
+    const float ilT = inv_log_mean_j(Tl, Tr, (Tl - Tr) + (S[M_TL * NB + l] - S[M_TL * NB + r]));
+    const float Pinv = S[M_IOM * NB + l] * S[M_IOM * NB + r];
+    const float iTa = 1.0f / T_m;
+    const float coef = G.Rb * Pinv - G.a * iTa;
+    float D = G.R * ilr + coef - G.a * iTa;
+    if (G.b > 0.0f) D += G.Rb * inv_log_mean_j(S[M_OM * NB + l], S[M_OM * NB + r], -G.b * drho);
+    const float iD = 1.0f / D;
+    const float g_m = 0.5f * (S[M_G * NB + l] + S[M_G * NB + r]);
+    const float rT_m = 0.5f * (S[M_RT * NB + l] + S[M_RT * NB + r]);
+    const float v2T_m = 0.5f * (S[M_V2T * NB + l] + S[M_V2T * NB + r]);
+    float vm[3], vT[3], rv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        vm[c] = 0.5f * (S[(M_V1 + c) * NB + l] + S[(M_V1 + c) * NB + r]);
+        vT[c] = 0.5f * (S[(M_VT1 + c) * NB + l] + S[(M_VT1 + c) * NB + r]);
+        rv[c] = 0.5f * (S[(M_RV1 + c) * NB + l] + S[(M_RV1 + c) * NB + r]);
+    }
+    const float U1 = (rho_m * coef + g_m) * iD;
+    const float F11 = (rv[0] * coef + g_m * vm[0]) * iD;
+    const float F21 = (rv[1] * coef + g_m * vm[1]) * iD;
+    const float F31 = (rv[2] * coef + g_m * vm[2]) * iD;
+    const float P = rho_m * T_m * g_m;
+    const float B0 = 0.5f * v2T_m - G.cv * T_m * ilT + 2.0f * G.a * rT_m;
+    const float Q1 = xt * U1 + nx * F11 + ny * F21 + nz * F31;
+    const float sv = vT[0] * vm[0] + vT[1] * vm[1] + vT[2] * vm[2];
+    out[0] = Q1;
+    out[1] = vm[0] * Q1 + nx * P;
+    out[2] = vm[1] * Q1 + ny * P;
+    out[3] = vm[2] * Q1 + nz * P;
+    out[4] = (G.a * rT_m * (xt * rho_m + nx * rv[0] + ny * rv[1] + nz * rv[2]) + (sv - B0) * Q1 +
+              P * (nx * vT[0] + ny * vT[1] + nz * vT[2])) /
+             iT_m;
+}
+
+// entropy-variable jump V_j - V_i by eq. jumpV in general units (the 2D form of the mixed
+// kernels with three velocity components)
+__device__ __forceinline__ void entropy_jump3_f(const float* S, int NB, int i, int j, const GasF& G, float* dV) {
+    const float ri = S[M_RHO * NB + i], rj = S[M_RHO * NB + j];
+    const float Ti = S[M_T * NB + i], Tj = S[M_T * NB + j];
+    const float dr = (rj - ri) + (S[M_RHOL * NB + j] - S[M_RHOL * NB + i]);
+    const float dT = (Tj - Ti) + (S[M_TL * NB + j] - S[M_TL * NB + i]);
+    const float iTa = 2.0f / (Ti + Tj);
+    float crho = G.R * inv_log_mean_j(ri, rj, -dr) + G.Rb * S[M_IOM * NB + i] * S[M_IOM * NB + j] - 2.0f * G.a * iTa;
+    if (G.b > 0.0f) crho += G.Rb * inv_log_mean_j(S[M_OM * NB + i], S[M_OM * NB + j], G.b * dr);
+    const float rT = 0.5f * (S[M_RT * NB + i] + S[M_RT * NB + j]);
+    const float v2T = 0.5f * (S[M_V2T * NB + i] + S[M_V2T * NB + j]);
+    const float cT = -G.cv * inv_log_mean_j(Ti, Tj, -dT) + (2.0f * G.a * rT + 0.5f * v2T) * iTa;
+    float kin = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float vi = S[(M_V1 + c) * NB + i], vj = S[(M_V1 + c) * NB + j];
+        const float dv = (vj - vi) + (S[(M_V1L + c) * NB + j] - S[(M_V1L + c) * NB + i]);
+        kin += 0.5f * (vi + vj) * dv;
+        dV[1 + c] = (dv - 0.5f * (S[(M_VT1 + c) * NB + i] + S[(M_VT1 + c) * NB + j]) * dT) * iTa;
+    }
+    dV[0] = dr * crho + dT * cT - kin * iTa;
+    dV[4] = dT * S[M_IT * NB + i] * S[M_IT * NB + j];
+}
+
+// -1/2 Lambda T^{-1} R Y [[W]]^WENO at the face between l and l+1 with the 3D frame (as in the FP64
+// 3D kernel), W measured from node l through the shared neighbour jumps JB (line offset jq)
+__device__ __forceinline__ void face_dissipation3_f(const float* S, int NB, int l, float nx, float ny, float nz,
+                                                    float xtf, const GasF& G, const WenoF& Wc, float* out,
+                                                    DevStatus* st, const float* JB, int NJ, int jq) {
+    const int r = l + 1;
+    const float ilr = inv_log_mean_f(S[M_RHO * NB + l], S[M_RHO * NB + r]);
+    const float rho = 1.0f / ilr;
+    const float ilrp = inv_log_mean_f(S[M_RP * NB + l], S[M_RP * NB + r]);
+    const float p = rho * ilrp;
+    const float om = 1.0f - G.b * rho;
+    const float T = (p + G.a * rho * rho) * om * ilr * G.iR;
+    const float iom = 1.0f / om;
+    const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
+    const float dcrit = G.R * T - 2.0f * G.a * rho * om * om;
+    if (!(c2 > 0.0f) || !(dcrit > 0.0f) || !(om > 0.0f)) raise_error(st, ES_ERR_INADMISSIBLE, 0);
+    const float c = sqrtf(c2);
+    const float vm1 = 0.5f * (S[M_V1 * NB + l] + S[M_V1 * NB + r]);
+    const float vm2 = 0.5f * (S[M_V2 * NB + l] + S[M_V2 * NB + r]);
+    const float vm3 = 0.5f * (S[M_V3 * NB + l] + S[M_V3 * NB + r]);
+    const float L = sqrtf(nx * nx + ny * ny + nz * nz);
+    const float r12 = sqrtf(nx * nx + ny * ny);
+    float ct = 1.0f, sn = 0.0f;
+    if (r12 > 0.0f) {
+        const float ir = 1.0f / r12;
+        ct = nx * ir;
+        sn = ny * ir;
+    }
+    const float iL = 1.0f / L;
+    const float cp = r12 * iL, sp = nz * iL;
+    const float en[3] = {cp * ct, cp * sn, sp};
+    const float et1[3] = {-sn, ct, 0.0f};
+    const float et2[3] = {-sp * ct, -sp * sn, cp};
+    const float vn = en[0] * vm1 + en[1] * vm2 + en[2] * vm3;
+    const float vt1 = et1[0] * vm1 + et1[1] * vm2;
+    const float vt2 = et2[0] * vm1 + et2[1] * vm2 + et2[2] * vm3;
+    const float E = rho * (G.cv * T - G.a * rho) + 0.5f * rho * (vn * vn + vt1 * vt1 + vt2 * vt2);
+    const float H = (E + p) * ilr;
+    const float mid = H - c2 * om * G.idelta;
+    const float ic2 = 1.0f / c2;
+    const float sA = sqrtf(0.5f * rho * T * ic2);
+    const float sE = sqrtf(G.R * G.delta * rho * T * T * ic2 / dcrit);
+    const float sT = sqrtf(rho * T);
+    const float Lam = fabsf(xtf + L * vn) + L * c;
+    const float Hm = H - vn * c, Hp = H + vn * c;
+
+    // V_j - V_l at nodes l-2 .. l+3 from the neighbour jumps (zero at l)
+    float W[6][5];
+    float cum[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        W[2][m] = 0.0f;
+        cum[m] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 3; o < 6; ++o)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cum[m] += JB[m * NJ + jq + (o - 3)];
+            W[o][m] = cum[m];
+        }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) cum[m] = 0.0f;
+#pragma unroll
+    for (int o = 1; o >= 0; --o)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cum[m] -= JB[m * NJ + jq + (o - 2)];
+            W[o][m] = cum[m];
+        }
+    float aTV[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        if (o == 2) continue;
+        const float V0 = W[o][0], V4 = W[o][4];
+        const float a1 = W[o][1], a2 = W[o][2], a3 = W[o][3];
+        const float V1 = en[0] * a1 + en[1] * a2 + en[2] * a3;
+        const float V2 = et1[0] * a1 + et1[1] * a2;
+        const float V3 = et2[0] * a1 + et2[1] * a2 + et2[2] * a3;
+        const float base = V0 + vt1 * V2 + vt2 * V3;
+        W[o][0] = sA * (base + (vn - c) * V1 + Hm * V4);
+        W[o][1] = sE * (base + vn * V1 + mid * V4);
+        W[o][2] = sT * (V2 + vt1 * V4);
+        W[o][3] = sT * (V3 + vt2 * V4);
+        W[o][4] = sA * (base + (vn + c) * V1 + Hp * V4);
+        if (o == 3) {
+            aTV[0] = fabsf(V0);
+            aTV[1] = fabsf(V1);
+            aTV[2] = fabsf(V2);
+            aTV[3] = fabsf(V3);
+            aTV[4] = fabsf(V4);
+        }
+    }
+    const float avt1 = fabsf(vt1), avt2 = fabsf(vt2);
+    const float common = aTV[0] + avt1 * aTV[2] + avt2 * aTV[3];
+    float scl[5];
+    scl[0] = sA * (common + fabsf(vn - c) * aTV[1] + fabsf(Hm) * aTV[4]);
+    scl[1] = sE * (common + fabsf(vn) * aTV[1] + fabsf(mid) * aTV[4]);
+    scl[2] = sT * (aTV[2] + (avt1 + c) * aTV[4]);
+    scl[3] = sT * (aTV[3] + (avt2 + c) * aTV[4]);
+    scl[4] = sA * (common + fabsf(vn + c) * aTV[1] + fabsf(Hp) * aTV[4]);
+    float y[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const float wmin = mr_weno5_f(W[0][m], W[1][m], W[2][m], W[3][m], W[4][m], Wc);
+        const float wplu = mr_weno5_f(W[5][m], W[4][m], W[3][m], W[2][m], W[1][m], Wc);
+        const float jw = wplu - wmin;
+        float j = W[3][m];
+        if (fabsf(j) <= Wc.sign_tol * scl[m]) j = 0.0f;
+        const bool keep = (jw > 0.0f && j > 0.0f) || (jw < 0.0f && j < 0.0f);
+        y[m] = keep ? jw : 0.0f;
+    }
+    const float h = -0.5f * Lam;
+    const float y0 = sA * y[0], y1 = sE * y[1], y2 = sT * y[2], y3 = sT * y[3], y4 = sA * y[4];
+    const float i0 = y0 + y1 + y4;
+    const float i1 = (vn - c) * y0 + vn * y1 + (vn + c) * y4;
+    const float i2 = vt1 * i0 + y2;
+    const float i3 = vt2 * i0 + y3;
+    const float i4 = Hm * y0 + mid * y1 + vt1 * y2 + vt2 * y3 + Hp * y4;
+    out[0] = h * i0;
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) out[1 + c3] = h * (en[c3] * i1 + et1[c3] * i2 + et2[c3] * i3);
+    out[4] = h * i4;
+}
+
+struct Dir3FParams {
+    Grid3 g;
+    GasF gas;
+    WenoF weno;
+    int diss;
+    const float* NF;          // float node fields [MF_COUNT][N]
+    const double* NK;         // metrics of this direction [3][M]
+    const double* xdot;       // nullable
+    float* RH;                // accumulated right-hand sides [6][N] (float)
+    int first, last;
+    int mode;
+    float ca, cb, ca_lo, cb_lo;
+    double dt_host;
+    const double* dt_dev;
+    const float *JUn, *Jn, *JUs, *Js;   // double-float planes
+    float *JUo, *Jo;
+    DevStatus* status;
+};
+
+template <int LB, int W>
+struct PencilF {
+    static constexpr int LS = (LB + 6) | 1;
+    static constexpr int NB = W * LS;
+    static constexpr int PL = 3 * LB + 6;
+    static constexpr int NP = W * PL;
+    static constexpr int NF = W * (LB + 1);
+    static constexpr int NJ = W * (LB + 5);
+    static constexpr size_t SMEM = sizeof(float) * (size_t(MS_COUNT) * NB + 5 * NP + 6 * NF + 5 * NJ);
+};
+
+template <int K, int LB, int W, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k3_dir_f(Dir3FParams P) {
+    using PC = PencilF<LB, W>;
+    constexpr int LS = PC::LS, NB = PC::NB, NP = PC::NP, NFc = PC::NF, NJ = PC::NJ;
+    extern __shared__ float smf[];
+    float* S = smf;
+    float* PB = S + MS_COUNT * NB;
+    float* FB = PB + 5 * NP;
+    float* JB = FB + 6 * NFc;
+    const Grid3& g = P.g;
+    const int tid = threadIdx.x;
+    const int nk = g.n[K];
+    const int nA = K == 0 ? g.n[1] : g.n[0];
+    const int nB = K == 2 ? g.n[1] : g.n[2];
+    const int nseg = (nk + LB - 1) / LB;
+    const int ngA = (nA + W - 1) / W;
+    const int seg = blockIdx.x % nseg;
+    const int grp = blockIdx.x / nseg;
+    const int a0 = (grp % ngA) * W;
+    const int b = grp / ngA;
+    if (b >= nB) return;
+    const int s0 = seg * LB;
+    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
+    const double dtd = P.dt_dev ? *P.dt_dev : P.dt_host;
+    if (P.mode == 0 && P.dt_dev && dtd == 0.0) return;   // finished run
+    const float dt = float(dtd);
+    const int M1 = g.n[0] + (K == 0 ? 6 : 0), M2 = g.n[1] + (K == 1 ? 6 : 0), M3 = g.n[2] + (K == 2 ? 6 : 0);
+    const size_t M = size_t(M1) * M2 * M3;
+    const GasF& G = P.gas;
+
+    // ---- A: node fields and metrics of the pencils
+    for (int t = tid; t < W * (LB + 6); t += NT) {
+        int line, q;
+        if (K == 0) { line = t / (LB + 6); q = t % (LB + 6); }
+        else { q = t / W; line = t % W; }
+        int a = a0 + line;
+        if (a > nA - 1) a = nA - 1;
+        const int s = s0 + q - 3;
+        const int ss = state_index(s, nk, g.bc[K]);
+        int i1, i2, i3, j1, j2, j3;
+        if (K == 0) { i1 = ss; i2 = a; i3 = b; }
+        else if (K == 1) { i1 = a; i2 = ss; i3 = b; }
+        else { i1 = a; i2 = b; i3 = ss; }
+        const size_t id = idx3(g, i1, i2, i3);
+        const int bx = line * LS + q;
+#pragma unroll 1
+        for (int f = 0; f < MF_COUNT; ++f) S[f * NB + bx] = P.NF[f * N + id];
+        int se = s + 3;
+        se = se < 0 ? 0 : (se > nk + 5 ? nk + 5 : se);
+        if (K == 0) { j1 = se; j2 = a; j3 = b; }
+        else if (K == 1) { j1 = a; j2 = se; j3 = b; }
+        else { j1 = a; j2 = b; j3 = se; }
+        const size_t mi = (size_t(j3) * M2 + j2) * M1 + j1;
+        const double nx = P.NK[mi], ny = P.NK[M + mi], nz = P.NK[2 * M + mi];
+        S[M_NX * NB + bx] = float(nx);
+        S[M_NY * NB + bx] = float(ny);
+        S[M_NZ * NB + bx] = float(nz);
+        double xt = 0.0;
+        if (P.xdot) {
+            double xd[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const GhostTerms tk = ghost_terms(s, nk, g.bc[K], c != K);
+                for (int u = 0; u < tk.nterm; ++u) {
+                    int k1 = i1, k2 = i2, k3 = i3;
+                    if (K == 0) k1 = tk.idx[u];
+                    else if (K == 1) k2 = tk.idx[u];
+                    else k3 = tk.idx[u];
+                    xd[c] += tk.w[u] * P.xdot[c * N + idx3(g, k1, k2, k3)];
+                }
+            }
+            xt = -(xd[0] * nx + xd[1] * ny + xd[2] * nz);
+        }
+        S[M_XT * NB + bx] = float(xt);
+    }
+    __syncthreads();
+
+    // ---- C: pair fluxes, and B: neighbour jumps V_{q+1} - V_q, q = 0 .. LB+4 (eq. jumpV)
+    for (int t = tid; t < NP; t += NT) {
+        const int line = t / PC::PL, kk = t % PC::PL;
+        int m, q;
+        if (kk < LB + 1) { m = 1; q = 2 + kk; }
+        else if (kk < 2 * LB + 3) { m = 2; q = 1 + (kk - LB - 1); }
+        else { m = 3; q = kk - 2 * LB - 3; }
+        const int l = line * LS + q, r = l + m;
+        const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + r]);
+        const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + r]);
+        const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + r]);
+        const float xt = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + r]);
+        float f[5];
+        pair_flux3_f(S, NB, l, r, nx, ny, nz, xt, G, f);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) PB[c * NP + t] = f[c];
+    }
+    if (P.diss) {
+        for (int t = tid; t < NJ; t += NT) {
+            const int line = t / (LB + 5), q = t % (LB + 5);
+            const int l = line * LS + q;
+            float dV[5];
+            entropy_jump3_f(S, NB, l, l + 1, G, dV);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) JB[c * NJ + t] = dV[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- D: face fluxes
+    for (int t = tid; t < NFc; t += NT) {
+        const int line = t / (LB + 1), f = t % (LB + 1);
+        const int q = 2 + f;
+        const int pbase = line * PC::PL;
+        const int base = line * LS;
+        float F[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float FJ = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) {
+            const int off = m == 1 ? 0 : (m == 2 ? LB + 1 : 2 * LB + 3);
+            const float al = float(ec_alpha(m));
+            for (int s = 0; s < m; ++s) {
+                const int qq = q - s;
+                const int pi = pbase + off + (qq - (3 - m));
+#pragma unroll
+                for (int c = 0; c < 5; ++c) F[c] += al * PB[c * NP + pi];
+                FJ += al * 0.5f * (S[M_XT * NB + base + qq] + S[M_XT * NB + base + qq + m]);
+            }
+        }
+        if (P.diss) {
+            const int l = base + q;
+            const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + l + 1]);
+            const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + l + 1]);
+            const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + l + 1]);
+            const float xtf = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + l + 1]);
+            float d[5];
+            face_dissipation3_f(S, NB, l, nx, ny, nz, xtf, G, P.weno, d, P.status, JB, NJ, line * (LB + 5) + q);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) F[c] += d[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) FB[c * NFc + t] = F[c];
+        FB[5 * NFc + t] = FJ;
+    }
+    __syncthreads();
+
+    // ---- E: divergence, accumulated in float; the last direction writes double-float results
+    const float inv = float(g.inv_dxi[K]);
+    for (int t = tid; t < W * LB; t += NT) {
+        int line, pos;
+        if (K == 0) { line = t / LB; pos = t % LB; }
+        else { pos = t / W; line = t % W; }
+        const int a = a0 + line, s = s0 + pos;
+        if (a >= nA || s >= nk) continue;
+        int i1, i2, i3;
+        if (K == 0) { i1 = s; i2 = a; i3 = b; }
+        else if (K == 1) { i1 = a; i2 = s; i3 = b; }
+        else { i1 = a; i2 = b; i3 = s; }
+        const size_t id = idx3(g, i1, i2, i3);
+        const int fm = line * (LB + 1) + pos;
+        float acc[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            acc[c] = -(FB[c * NFc + fm + 1] - FB[c * NFc + fm]) * inv;
+            if (!P.first) acc[c] += P.RH[c * N + id];
+        }
+        if (!P.last) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) P.RH[c * N + id] = acc[c];
+        } else if (P.mode == 1) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                P.JUo[c * N + id] = acc[c];
+                P.JUo[5 * N + c * N + id] = 0.0f;
+            }
+            P.Jo[id] = acc[5];
+            P.Jo[N + id] = 0.0f;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const float* un = c < 5 ? P.JUn + c * N : P.Jn;
+                const float* us = c < 5 ? P.JUs + c * N : P.Js;
+                float* uo = c < 5 ? P.JUo + c * N : P.Jo;
+                const size_t lo = c < 5 ? 5 * N : N;
+                const df Un = {un[id], un[lo + id]};
+                const df Us = {us[id], us[lo + id]};
+                const df inc = df_add_f(Us, dt * acc[c]);
+                df outv = df_mul(inc, {P.cb, P.cb_lo});
+                if (P.ca != 0.0f) outv = df_add(outv, df_mul(Un, {P.ca, P.ca_lo}));
+                uo[id] = outv.hi;
+                uo[lo + id] = outv.lo;
+                if (c == 5 && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(id));
+            }
+        }
+    }
+}
+
+template <int K, int LB, int W, int NT, int MINB>
+static cudaError_t prep_shape() {
+    return cudaFuncSetAttribute(k3_dir_f<K, LB, W, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(PencilF<LB, W>::SMEM));
+}
+
+template <int K, int LB, int W, int NT, int MINB>
+static cudaError_t launch_shape(const Dir3FParams& P, cudaStream_t s) {
+    const Grid3& g = P.g;
+    const int nA = K == 0 ? g.n[1] : g.n[0];
+    const int nB = K == 2 ? g.n[1] : g.n[2];
+    const long long blocks = (long long)((g.n[K] + LB - 1) / LB) * ((nA + W - 1) / W) * nB;
+    k3_dir_f<K, LB, W, NT, MINB><<<unsigned(blocks), NT, PencilF<LB, W>::SMEM, s>>>(P);
+    return cudaGetLastError();
+}
+
+// pencil shapes of the float kernels: 16 x 16 lines / 288 threads (two CTAs per SM), 32 x 8 / 288,
+// 16 x 8 / 160 (three per SM), 32 x 4 / 160
+template <int K>
+static cudaError_t prep_dir() {
+    cudaError_t e = prep_shape<K, 16, 16, 288, 2>();
+    if (e == cudaSuccess) e = prep_shape<K, 32, 8, 288, 2>();
+    if (e == cudaSuccess) e = prep_shape<K, 16, 8, 160, 3>();
+    if (e == cudaSuccess) e = prep_shape<K, 32, 4, 160, 3>();
+    return e;
+}
+
+template <int K>
+static cudaError_t launch_dir(const Dir3FParams& P, int shape, cudaStream_t s) {
+    switch (shape) {
+        case 1: return launch_shape<K, 32, 8, 288, 2>(P, s);
+        case 2: return launch_shape<K, 16, 8, 160, 3>(P, s);
+        case 3: return launch_shape<K, 32, 4, 160, 3>(P, s);
+        default: return launch_shape<K, 16, 16, 288, 2>(P, s);
+    }
+}
+
+// CFL (eq. cfl) from the float node fields and the FP64 metrics, zero mesh velocity
+__global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const double* NK0, const double* NK1,
+                         const double* NK2, DevScalars* d) {
+    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
+    const size_t M[3] = {size_t(g.n[0] + 6) * g.n[1] * g.n[2], size_t(g.n[0]) * (g.n[1] + 6) * g.n[2],
+                         size_t(g.n[0]) * g.n[1] * (g.n[2] + 6)};
+    const double* NK[3] = {NK0, NK1, NK2};
+    const float a = float(Gd.a), R = float(Gd.R), delta = float(Gd.delta);
+    float mx = 0.0f;
+    for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
+        const int i1 = int(id % g.n[0]), i2 = int((id / g.n[0]) % g.n[1]), i3 = int(id / (size_t(g.n[0]) * g.n[1]));
+        const float rho = NF[M_RHO * N + id], T = NF[M_T * N + id], iom = NF[M_IOM * N + id];
+        const float v[3] = {NF[M_V1 * N + id], NF[M_V2 * N + id], NF[M_V3 * N + id]};
+        const float c2 = (1.0f + delta) * R * T * (iom * iom) - 2.0f * a * rho;
+        const float c = sqrtf(fmaxf(c2, 0.0f));
+        const float iJ = 1.0f / J[id];
+        float tot = 0.0f;
+        for (int k = 0; k < 3; ++k) {
+            const int m1 = g.n[0] + (k == 0 ? 6 : 0), m2 = g.n[1] + (k == 1 ? 6 : 0);
+            const size_t mi = (size_t(i3 + (k == 2 ? 3 : 0)) * m2 + i2 + (k == 1 ? 3 : 0)) * m1 + i1 + (k == 0 ? 3 : 0);
+            const float n0 = float(NK[k][mi]), n1 = float(NK[k][M[k] + mi]), n2 = float(NK[k][2 * M[k] + mi]);
+            tot += (fabsf(n0 * v[0] + n1 * v[1] + n2 * v[2]) + sqrtf(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
+                   float(g.inv_dxi[k]);
+        }
+        if (!(c2 > 0.0f)) tot = 3.0e38f;
+        mx = fmaxf(mx, tot);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(&d->red[RED_CFL], double(mx));
+}
+
+// J (FP64, from the FP64 kernel) into double-float planes
+__global__ void k3_split(const double* a, float* out, size_t n) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        const float hi = float(a[i]);
+        out[i] = hi;
+        out[n + i] = float(a[i] - double(hi));
+    }
+}
+
+}  // namespace mixed3
+
+using namespace mixed3;
+
+cudaError_t d3f_prepare() {
+    cudaError_t e = prep_dir<0>();
+    if (e == cudaSuccess) e = prep_dir<1>();
+    if (e == cudaSuccess) e = prep_dir<2>();
+    return e;
+}
+
+static GasF gasf(const Gas& g) {
+    GasF G;
+    G.a = float(g.a);
+    G.b = float(g.b);
+    G.R = float(g.R);
+    G.cv = float(g.cv);
+    G.delta = float(g.delta);
+    G.Rb = float(g.R * g.b);
+    G.icv = float(1.0 / g.cv);
+    G.iR = float(1.0 / g.R);
+    G.idelta = float(g.cv / g.R);
+    return G;
+}
+
+static WenoF wenof(const Weno& w) {
+    WenoF W;
+    W.g1 = float(w.g1);
+    W.g2 = float(w.g2);
+    W.g3 = float(w.g3);
+    W.g12 = float(w.g12);
+    W.ig22 = float(w.ig22);
+    W.ig3 = float(w.ig3);
+    W.eps = float(w.eps);
+    W.sign_tol = float(w.sign_tol);
+    return W;
+}
+
+int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s) {
+    k3_nodes_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)JU, (const float*)J, (float*)d->NF, st);
+    return 1;
+}
+
+int d3f_cfl(Ctx3* d, const void* J, DevScalars* dv, cudaStream_t s) {
+    k3_cfl_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)d->NF, (const float*)J, d->NK[0], d->NK[1],
+                                      d->NK[2], dv);
+    return 1;
+}
+
+int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s) {
+    k3_split<<<d->grid, 256, 0, s>>>(Jd, (float*)J, d->N);
+    return 1;
+}
+
+int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err) {
+    Dir3FParams P;
+    P.g = d->g;
+    P.gas = gasf(d->gas);
+    P.weno = wenof(d->weno);
+    P.diss = d->diss;
+    P.NF = (const float*)d->NF;
+    P.xdot = a.xdot;
+    P.RH = (float*)d->RH;
+    P.mode = a.mode;
+    P.ca = float(a.ca);
+    P.cb = float(a.cb);
+    P.ca_lo = float(a.ca - double(P.ca));
+    P.cb_lo = float(a.cb - double(P.cb));
+    P.dt_host = a.dt_host;
+    P.dt_dev = a.dt_dev;
+    P.JUn = (const float*)a.JUn;
+    P.Jn = (const float*)a.Jn;
+    P.JUs = (const float*)a.JUs;
+    P.Js = (const float*)a.Js;
+    P.JUo = (float*)a.JUo;
+    P.Jo = (float*)a.Jo;
+    P.status = st;
+    cudaError_t e = cudaGetLastError();
+    int n = 0;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        P.NK = d->NK[k];
+        P.first = k == 0;
+        P.last = k == 2;
+        e = k == 0 ? launch_dir<0>(P, d->shape, s) : (k == 1 ? launch_dir<1>(P, d->shape, s) : launch_dir<2>(P, d->shape, s));
+        ++n;
+    }
+    *err = e;
+    return e == cudaSuccess ? n : -1;
+}
+
+}  // namespace es

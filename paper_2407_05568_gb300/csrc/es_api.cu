@@ -462,7 +462,7 @@ int check_params(const es_params* p) {
     if (p->dim == 1 && p->n2 != 1) return 0;
     if (p->dim >= 2 && p->n2 < 8) return 0;
     if (p->dim < 3 && p->n3 != 0 && p->n3 != 1) return 0;
-    if (p->dim == 3 && (p->n3 < 8 || p->precision != ES_PREC_FP64 || p->tile > D3_NSHAPES)) return 0;
+    if (p->dim == 3 && (p->n3 < 8 || p->tile > D3_NSHAPES)) return 0;
     const long long n3 = p->dim == 3 ? p->n3 : 1;
     if ((long long)p->n1 * p->n2 * n3 > (1LL << 30)) return 0;
     for (int k = 0; k < p->dim; ++k) {
@@ -479,8 +479,8 @@ int check_params(const es_params* p) {
     if (!(p->cfl > 0.0) && !(p->dt_fixed > 0.0)) return 0;
     if (p->precision != ES_PREC_FP64 && p->precision != ES_PREC_MIXED) return 0;
     if (p->tile < 0 || p->tile > ES_NTILES) return 0;
-    if (p->precision == ES_PREC_MIXED) {
-        // the FP32 displacement is periodic only when the period is n dxi
+    if (p->precision == ES_PREC_MIXED && p->dim < 3) {
+        // the FP32 displacement (1D/2D) is periodic only when the period is n dxi
         const int nn[2] = {p->n1, p->n2};
         for (int k = 0; k < p->dim; ++k)
             if (p->bc[k] == ES_BC_PERIODIC && fabs(p->period[k] - nn[k] * p->dxi[k]) > 1e-9 * p->period[k]) return 0;
@@ -599,7 +599,10 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "init"); goto fail_out; }
         // warm the stage kernel once so its shared-memory attribute is set outside any capture
-        if (p->dim == 3) e = d3_prepare();
+        if (p->dim == 3) {
+            e = d3_prepare();
+            if (e == cudaSuccess && p->precision == ES_PREC_MIXED) e = d3f_prepare();
+        }
         else e = p->precision == ES_PREC_MIXED ? stage_prepare_mixed(p->dim) : stage_prepare_fp64(p->dim);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "stage kernel attributes"); goto fail_out; }
     }
@@ -618,6 +621,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->weno = c->weno;
         d->mon = c->mon;
         d->diss = p->dissipation;
+        d->mixed = c->mixed;
         d->filter_passes = p->filter_passes;
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;

@@ -249,14 +249,15 @@ def test_free_stream_3d_gpu_full_size():
 
 
 def test_3d_rejections():
-    """The mixed form and the 2D-only calls refuse a 3D context with ES_ERR_ARG."""
+    """Walls in the mixed form and the 2D-only calls refuse a 3D context with ES_ERR_ARG."""
     import ctypes
 
     from paper_2407_05568_gb300 import es
-    w = CASES["wavy_periodic_smooth"]()
+    w = CASES["walls_rough"]()
     p = es.make_params(w, precision="mixed")
     h = ctypes.c_void_p()
     assert es.lib().es_create(ctypes.byref(h), ctypes.byref(p), None) == es.ES_ERR_ARG
+    w = CASES["wavy_periodic_smooth"]()
     ctx, JU, J, xt = gpu_setup(w)
     with pytest.raises(es.EsError):
         es.es_mesh_solve(ctx, JU, J, xt, None, xt.clone())
@@ -289,3 +290,63 @@ def test_pencil_shapes_agree_bitwise_and_autotune():
     ctx, JU, J, xt = gpu_setup(w)
     k, ms = es.es_autotune(ctx, JU, J, xt)
     assert k in (1, 2, 3, 4) and all(m > 0 for m in ms[:4])
+
+
+# ------------------------------------------------------------------ mixed form
+@pytest.mark.parametrize("case", ["wavy_periodic_smooth", "wavy_periodic_rough", "outflow_rough", "shock_ragged"])
+def test_mixed_3d_rhs_against_oracle(case):
+    """The mixed form's 3D operator (FP32 direction kernels, double-float node values and jumps)
+    within 2e-6 of the flux scale of the FP64 oracle."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = CASES[case]()
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    xd = _xdot(w)
+    dU_o, dJ_o = op.rhs(sch, JU_o, J_o, x, xd)
+    dU, dJ = torch.empty_like(JU), torch.empty_like(J)
+    es.es_rhs(ctx, JU, J, xt, torch.tensor(np.ascontiguousarray(xd), device="cuda"), dU, dJ)
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    scale = np.abs(JU_o).sum() / min(w["dxi"])
+    err = np.abs(to_np(dU) - dU_o).sum() / scale
+    assert err < 2e-6, err
+    assert np.abs(to_np(dJ) - dJ_o).sum() / (np.abs(J_o).sum() / min(w["dxi"])) < 2e-6
+
+
+@pytest.mark.parametrize("case,monitor", [("wavy_periodic_smooth", "smooth"), ("shock_ragged", "vdw")])
+def test_mixed_3d_steps_against_oracle(case, monitor):
+    """Two full moving-mesh steps of the mixed form against the FP64 oracle: within 2e-6 (relative L1)."""
+    from paper_2407_05568_gb300 import es
+    w = _moving(CASES[case](), monitor)
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    t = 0.0
+    for _ in range(2):
+        JU_o, J_o, x_o, t, _ = stepper.step(sch, mc, JU_o, J_o, x_o, t, w["t_end"], w["cfl"])
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, 2, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    assert rel_l1(to_np(JU), JU_o) < 2e-6, rel_l1(to_np(JU), JU_o)
+    assert rel_l1(to_np(xt), x_o) < 1e-6
+
+
+def test_mixed_3d_sine_to_final_time_against_fp64():
+    """The 3D sine wave (Example 5.6 setup, fixed mesh) at 40^3 to t = 0.05: the mixed form stays within
+    1e-5 (relative L1) of the FP64 path, whose error against the exact solution it matches."""
+    from paper_2407_05568_gb300 import es
+    w = wl.sine_3d(40, t_end=0.05)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ctx, JU, J, xt = gpu_setup(w, precision=prec)
+        es.es_set_time(ctx, 0.0)
+        es.es_steps(ctx, JU, J, xt, 400, w["t_end"])
+        assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+        t, _ = es.es_get_time(ctx)
+        assert abs(t - w["t_end"]) < 1e-12
+        res[prec] = to_np(JU)[0] / to_np(J)
+    X, Y, Z = w["x"]
+    exact = 0.5 + 0.2 * np.sin(2 * np.pi * (X + Y + Z - 0.9 * w["t_end"]))
+    assert rel_l1(res["mixed"], res["fp64"]) < 1e-5
+    e64, e32 = np.abs(res["fp64"] - exact).mean(), np.abs(res["mixed"] - exact).mean()
+    assert e32 < 1.5 * e64 + 1e-6, (e64, e32)
