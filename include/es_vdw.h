@@ -111,8 +111,9 @@ typedef struct es_params {
     int    tile;            /* stage tile shape: 0 = chosen by es_autotune (run by the first es_steps
                                if not called before); k = 1 .. ES_NTILES: shape k of the precision's
                                2D table (FP64: 32x8, 25x11, 16x16, 32x12, 20x10 nodes; mixed: 32x8, 25x6,
-                               20x8, 32x16, 16x8); in 3D the direction kernels' pencils: 1 = 16 nodes
-                               x 16 lines, 2 = 16 x 8, 3 = 16 x 4, 4 = 32 x 4 */
+                               20x8, 32x16, 16x8); in 3D the direction kernels' pencils, FP64:
+                               1 = 16 nodes x 16 lines, 2 = 16 x 8, 3 = 16 x 4, 4 = 32 x 4; mixed:
+                               1 = 16 x 16, 2 = 32 x 8, 3 = 16 x 8, 4 = 32 x 4 */
 } es_params;
 
 #define ES_NTILES 5

@@ -464,19 +464,25 @@ def es_last_error(ctx):
     return buf.value.decode()
 
 
-def setup_workload(w, precision="fp64", device="cuda", dissipation=True, dt_fixed=0.0):
+def setup_workload(w, precision="fp64", device="cuda", dissipation=True, dt_fixed=0.0, stream=None):
     """Context and device state (JU, J, x) of a workload description (workloads.py): J from
-    the mesh, JU from the primitive fields, time 0.  dt_fixed > 0 replaces the CFL step."""
+    the mesh, JU from the primitive fields, time 0.  dt_fixed > 0 replaces the CFL step.
+    `stream` (a torch.cuda.Stream, or None for the current one) carries the context's work."""
+    import contextlib
+
     import torch
     dev = torch.device(device)
-    ctx = es_create(make_params(w, precision=precision, dissipation=dissipation, dt_fixed=dt_fixed))
-    x = torch.tensor(np.ascontiguousarray(w["x"]), dtype=torch.float64, device=dev)
-    J = state_empty(ctx, w["x"].shape[1:], dev)
-    es_init_mesh(ctx, x, J)
-    rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
-    v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
-    p = torch.tensor(w["p"], dtype=torch.float64, device=dev)
-    JU = state_empty(ctx, (w["dim"] + 2,) + w["x"].shape[1:], dev)
-    es_prim_to_cons(ctx, rho, v, p, J, JU)
+    ctx = es_create(make_params(w, precision=precision, dissipation=dissipation, dt_fixed=dt_fixed), stream)
+    with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+        x = torch.tensor(np.ascontiguousarray(w["x"]), dtype=torch.float64, device=dev)
+        J = state_empty(ctx, w["x"].shape[1:], dev)
+        es_init_mesh(ctx, x, J)
+        rho = torch.tensor(w["rho"], dtype=torch.float64, device=dev)
+        v = torch.tensor(np.ascontiguousarray(w["v"]), dtype=torch.float64, device=dev)
+        p = torch.tensor(w["p"], dtype=torch.float64, device=dev)
+        JU = state_empty(ctx, (w["dim"] + 2,) + w["x"].shape[1:], dev)
+        es_prim_to_cons(ctx, rho, v, p, J, JU)
+    if stream is not None:
+        stream.synchronize()
     es_set_time(ctx, 0.0)
     return ctx, JU, J, x
