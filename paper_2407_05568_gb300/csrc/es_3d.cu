@@ -997,6 +997,7 @@ int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* 
 
 int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
             cudaStream_t s, cudaError_t* err) {
+    if (d->mixed) return d3f_mesh(d, JU, J, xn, xdot, dv, s, err);       // FP32 pipe (es_3d_mixed.cu)
     const int G = d->grid;
     // the elementwise kernels of the 1D/2D path see the 3D mesh as N nodes in a row
     GridParams flat;
@@ -1007,7 +1008,7 @@ int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xd
     flat.inv_dxi[0] = flat.inv_dxi[1] = 1.0;
     flat.period[0] = flat.period[1] = 0.0;
     int n = 0;
-    launch_mon_fields(flat, d->gas, JU, J, d->rhoF, d->GF, d->mixed != 0, G, s);
+    launch_mon_fields(flat, d->gas, JU, J, d->rhoF, d->GF, false, G, s);
     k3_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, d->rhoF, d->GF, d->t0, d->t1, d->t2, dv);
     k_mon_omega<<<G, 256, 0, s>>>(flat, d->mon, d->t0, d->t1, d->t2, dv, d->om0);
     n += 3;

@@ -38,6 +38,7 @@ struct Ctx3 {
     double* RH;               // right-hand sides accumulated over the directions [6][N] (mixed: float)
     // mesh scratch (the context's buffers)
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1, *xa, *xb;
+    float* gc;                // mixed form: the sweeps' constant term g [3][N]
 };
 
 // arguments of one operator evaluation / RK stage
@@ -69,5 +70,7 @@ int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_
 int d3f_cfl(Ctx3* d, const void* J, DevScalars* dv, cudaStream_t s);
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);
 int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
+int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
+             cudaStream_t s, cudaError_t* err);
 
 }  // namespace es

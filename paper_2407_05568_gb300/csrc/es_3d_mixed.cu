@@ -13,6 +13,7 @@
 #include "es_3d.h"
 #include "es_device.cuh"
 #include "es_internal.h"
+#include "es_mesh_f32.h"
 #include "es_mixed_device.cuh"
 
 namespace es {
@@ -582,6 +583,290 @@ __global__ void k3_split(const double* a, float* out, size_t n) {
     }
 }
 
+
+// ---------------------------------------------------------------- mesh redistribution (Sec. 4)
+// On the FP32 pipe, with the Jacobi iteration written for the displacement delta = x - x^n from
+// the mesh at t^n.  omega is fixed during the sweeps, so x^[nu+1]_i = sum_nb a_nb x^[nu]_nb with
+// a_nb = w_nb / sum_nb w_nb becomes delta^[nu+1]_i = g_i + sum_nb a_nb delta^[nu]_nb, where
+// g_i = sum_nb a_nb (x^n_nb - x^n_i) is formed once per solve in FP64 from the FP64 mesh and
+// then rounded: the sweeps round only the displacement, which is small against the spacing.
+// The mixed form has periodic and outflow ends only; every node on an outflow end is fixed, so a
+// node that moves has its six neighbours in the mesh or across a periodic end, where delta wraps
+// (x shifts by the period, delta does not).
+
+__device__ __forceinline__ void split3(const Grid3& g, int id, int* ii) {
+    const int r = id / g.n[0];
+    ii[0] = id - r * g.n[0];
+    ii[2] = r / g.n[1];
+    ii[1] = r - ii[2] * g.n[1];
+}
+
+__device__ __forceinline__ int stride3i(const Grid3& g, int k) {
+    return k == 0 ? 1 : (k == 1 ? g.n[0] : g.n[0] * g.n[1]);
+}
+
+// neighbour at s = +-1 along k, ghosts by copy (outflow) or wrap (periodic)
+__device__ __forceinline__ int nb3(const Grid3& g, int id, int ik, int k, int s) {
+    const int j = state_index(ik + s, g.n[k], g.bc[k]);
+    return id + (j - ik) * stride3i(g, k);
+}
+
+__device__ __forceinline__ bool fixed_node3(const Grid3& g, const int* ii) {
+    bool f = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f = f || (g.bc[k] != ES_BC_PERIODIC && (ii[k] == 0 || ii[k] == g.n[k] - 1));
+    return f;
+}
+
+// x^n_comp at the neighbour s = +-1 along k minus x^n_comp at the node (FP64), for a node that
+// moves: the neighbour is in the mesh or across a periodic end
+__device__ __forceinline__ double xn_step(const Grid3& g, const double* f, int id, int ik, int k, int s, int comp) {
+    const int n = g.n[k], j = ik + s;
+    const int st = stride3i(g, k);
+    if (j >= 0 && j < n) return f[id + s * st] - f[id];
+    const int r = j < 0 ? j + n : j - n;
+    double v = f[id + (r - ik) * st] - f[id];
+    if (comp == k) v += (j < 0 ? -1.0 : 1.0) * g.period[k];
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_min_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// the raw monitor terms of eq. van der Waalsmonitor (or the smooth-test monitor) from the
+// float density and G: central first and second differences along each direction
+__global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
+                              float* t2, DevScalars* d) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        const float r0 = rhoF[id], G0 = GF[id];
+        float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float h = float(g.inv_dxi[k]);
+            const int ip = nb3(g, id, ii[k], k, 1), im = nb3(g, id, ii[k], k, -1);
+            const float rp = rhoF[ip], rm = rhoF[im], Gp = GF[ip], Gm = GF[im];
+            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
+            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
+            gr += a * a;
+            gg += b * b;
+            lg += c * c;
+            lr += e * e;
+        }
+        float v0, v1, v2;
+        if (mp.kind == ES_MONITOR_SMOOTH) {
+            v0 = sqrtf(gr);
+            v1 = 0.0f;
+            v2 = sqrtf(lr);
+        } else {
+            v0 = gr;
+            v1 = mp.kappa >= 2 ? gg : 0.0f;
+            v2 = lg;
+        }
+        t0[id] = v0;
+        t1[id] = v1;
+        t2[id] = v2;
+        m0 = fmaxf(m0, v0);
+        m1 = fmaxf(m1, v1);
+        m2 = fmaxf(m2, v2);
+    }
+    m0 = warp_max_f(m0);
+    m1 = warp_max_f(m1);
+    m2 = warp_max_f(m2);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&d->red[RED_MON0], double(m0));
+        atomic_max_pos(&d->red[RED_MON1], double(m1));
+        atomic_max_pos(&d->red[RED_MON2], double(m2));
+    }
+}
+
+// omega_i <- sum_{j in {0,+-1}^3} (1/2)^(|j|_1 + 3) omega_{i+j} (Sec. 4's low-pass filter)
+__global__ void k3f_filter(Grid3 g, const float* in, float* out) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        int o1[3], o2[3], o3[3];
+        o1[1] = o2[1] = o3[1] = 0;
+        o1[0] = nb3(g, id, ii[0], 0, -1) - id;
+        o1[2] = nb3(g, id, ii[0], 0, 1) - id;
+        o2[0] = nb3(g, id, ii[1], 1, -1) - id;
+        o2[2] = nb3(g, id, ii[1], 1, 1) - id;
+        o3[0] = nb3(g, id, ii[2], 2, -1) - id;
+        o3[2] = nb3(g, id, ii[2], 2, 1) - id;
+        float s = 0.0f;
+#pragma unroll
+        for (int d3 = 0; d3 < 3; ++d3) {
+            float pl = 0.0f;
+#pragma unroll
+            for (int d2 = 0; d2 < 3; ++d2) {
+                const int b = id + o2[d2] + o3[d3];
+                const float row = 0.25f * in[b + o1[0]] + 0.5f * in[b] + 0.25f * in[b + o1[2]];
+                pl += (d2 == 1 ? 0.5f : 0.25f) * row;
+            }
+            s += (d3 == 1 ? 0.5f : 0.25f) * pl;
+        }
+        out[id] = s;
+    }
+}
+
+// the sweep coefficients of every node: a_nb for the six neighbours ([6][N], order -xi_1, +xi_1,
+// -xi_2, ...) and g ([3][N]); zero at fixed nodes
+__global__ void k3f_coeffs(Grid3 g, const float* om, const double* xn, float* A, float* Gc) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        if (fixed_node3(g, ii)) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) A[m * P + id] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Gc[c * P + id] = 0.0f;
+            continue;
+        }
+        const float w0 = om[id];
+        float w[6], den = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float ih2 = float(g.inv_dxi[k] * g.inv_dxi[k]);
+            w[2 * k] = 0.5f * (w0 + om[nb3(g, id, ii[k], k, -1)]) * ih2;
+            w[2 * k + 1] = 0.5f * (w0 + om[nb3(g, id, ii[k], k, 1)]) * ih2;
+            den += w[2 * k] + w[2 * k + 1];
+        }
+        const float iden = 1.0f / den;
+        double gs[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float am = w[2 * k] * iden, ap = w[2 * k + 1] * iden;
+            A[(2 * k) * P + id] = am;
+            A[(2 * k + 1) * P + id] = ap;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                gs[c] += double(am) * xn_step(g, xn + size_t(c) * N, id, ii[k], k, -1, c) +
+                         double(ap) * xn_step(g, xn + size_t(c) * N, id, ii[k], k, 1, c);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Gc[c * P + id] = float(gs[c]);
+    }
+}
+
+// Jacobi sweep k on the displacement (sweep 0 starts from delta = 0 and writes da; sweep k reads
+// buf[(k - 1) % 2] and writes buf[k % 2]); with `check` the last block to finish compares the
+// grid's max change with eps and latches convergence, after which the remaining sweeps return
+__global__ void k3f_jacobi(Grid3 g, const float* A, const float* Gc, float* da, float* db, int k, DevScalars* d,
+                           int check, double eps) {
+    if (d->conv) return;
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    const float* din = k == 0 ? nullptr : (((k - 1) & 1) ? db : da);
+    float* dout = (k & 1) ? db : da;
+    float chg = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        if (fixed_node3(g, ii)) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dout[c * P + id] = 0.0f;
+            continue;
+        }
+        float v[3] = {Gc[id], Gc[P + id], Gc[2 * P + id]};
+        if (din) {
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const float am = A[(2 * kk) * P + id], ap = A[(2 * kk + 1) * P + id];
+                const int im = nb3(g, id, ii[kk], kk, -1), ip = nb3(g, id, ii[kk], kk, 1);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] += am * din[c * P + im] + ap * din[c * P + ip];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            chg = fmaxf(chg, fabsf(v[c] - (din ? din[c * P + id] : 0.0f)));
+            dout[c * P + id] = v[c];
+        }
+    }
+    if (check) {
+        chg = warp_max_f(chg);
+        __shared__ float sh[32];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) sh[w] = chg;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = 0.0f;
+            for (int i = 0; i < int(blockDim.x + 31) / 32; ++i) m = fmaxf(m, sh[i]);
+            atomic_max_pos(&d->red[RED_JAC], double(m));
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {
+                const double c = __longlong_as_double((long long)atomicAdd(&d->red[RED_JAC], 0ULL));
+                if (c < eps) d->conv = 1;
+                d->red[RED_JAC] = 0ULL;
+                d->done = 0u;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&d->sweeps, 1);
+}
+
+__device__ __forceinline__ const float* sweep_result(const DevScalars* d, const float* da, const float* db) {
+    if (d->sweeps == 0) return nullptr;
+    return ((d->sweeps - 1) & 1) ? db : da;
+}
+
+// Delta_gamma over all nodes and directions (Sec. 4): the spacing to the neighbour the node
+// moves towards, over twice its displacement along that direction
+__global__ void k3f_limiter(Grid3 g, const double* xn, const float* da, const float* db, DevScalars* d) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    const float* dl = sweep_result(d, da, db);
+    float m = 1.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; dl && id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        if (fixed_node3(g, ii)) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float dx = dl[k * P + id];
+            if (dx < 0.0f)
+                m = fminf(m, float(-xn_step(g, xn + size_t(k) * N, id, ii[k], k, -1, k)) / (-2.0f * dx));
+            else if (dx > 0.0f)
+                m = fminf(m, float(xn_step(g, xn + size_t(k) * N, id, ii[k], k, 1, k)) / (2.0f * dx));
+        }
+    }
+    m = warp_min_f(m);
+    if ((threadIdx.x & 31) == 0) atomic_min_pos(&d->red[RED_GAMMA], double(m));
+}
+
+// xdot = Delta_gamma delta^[mu] / dt (FP64, the API's array)
+__global__ void k3f_velocity(Grid3 g, const float* da, const float* db, DevScalars* d, double* xdot) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N);
+    const float* dl = sweep_result(d, da, db);
+    const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
+    const double dt = d->dt;
+    const double f = dt > 0.0 ? gam / dt : 0.0;
+    for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < 3 * P; id += size_t(gridDim.x) * blockDim.x)
+        xdot[id] = dl ? f * double(dl[id]) : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d->gamma = gam;
+        d->sweeps_total += d->sweeps;
+        d->solves += 1;
+    }
+}
+
 }  // namespace mixed3
 
 using namespace mixed3;
@@ -670,6 +955,52 @@ int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cuda
     }
     *err = e;
     return e == cudaSuccess ? n : -1;
+}
+
+int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
+             cudaStream_t s, cudaError_t* err) {
+    const int G = d->grid;
+    // the elementwise kernels of the 1D/2D mixed path see the 3D mesh as N nodes in a row
+    GridParams flat;
+    flat.dim = 3;
+    flat.n1 = int(d->N);
+    flat.n2 = 1;
+    flat.bc[0] = flat.bc[1] = ES_BC_PERIODIC;
+    flat.inv_dxi[0] = flat.inv_dxi[1] = 1.0;
+    flat.period[0] = flat.period[1] = 0.0;
+    float* rho = (float*)d->rhoF;
+    float* Gf = (float*)d->GF;
+    float* t0 = (float*)d->t0;
+    float* t1 = (float*)d->t1;
+    float* t2 = (float*)d->t2;
+    float* om = (float*)d->om0;
+    float* other = (float*)d->om1;
+    float* A = (float*)d->xa;                     // [6][N] floats in the [3][N] doubles
+    float* da = (float*)d->xb;                    // two [3][N] float displacements
+    float* db = da + 3 * d->N;               // (xb holds [3][N] doubles)
+    k_mon_fields_f<<<G, 256, 0, s>>>(flat, gas_f32(d->gas), (const float*)JU, (const float*)J, rho, Gf);
+    k3f_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, rho, Gf, t0, t1, t2, dv);
+    k_mon_omega_f<<<G, 256, 0, s>>>(flat, d->mon, t0, t1, t2, dv, om);
+    int n = 3;
+    for (int k = 0; k < d->filter_passes; ++k) {
+        k3f_filter<<<G, 256, 0, s>>>(d->g, om, other);
+        ++n;
+        float* t = om;
+        om = other;
+        other = t;
+    }
+    k3f_coeffs<<<G, 256, 0, s>>>(d->g, om, xn, A, d->gc);
+    ++n;
+    const int check = d->eps > 0.0;
+    for (int k = 0; k < d->sweeps; ++k) {
+        k3f_jacobi<<<G, 256, 0, s>>>(d->g, A, d->gc, da, db, k, dv, check, d->eps);
+        ++n;
+    }
+    k3f_limiter<<<G, 256, 0, s>>>(d->g, xn, da, db, dv);
+    k3f_velocity<<<G, 256, 0, s>>>(d->g, da, db, dv, xdot);
+    n += 2;
+    *err = cudaGetLastError();
+    return *err == cudaSuccess ? n : -1;
 }
 
 }  // namespace es

@@ -636,6 +636,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->om1 = c->om1;
         d->xa = c->xa;
         d->xb = c->xb;
+        d->gc = c->fdisp;                  // [3][N] floats, allocated for the mixed form
         cudaError_t e = d3_alloc(d);
         if (e != cudaSuccess) { rc = cuda_fail(c, e, "cudaMalloc (3D scratch)"); goto fail_out; }
     }

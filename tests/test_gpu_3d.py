@@ -338,6 +338,29 @@ def test_mixed_3d_steps_against_oracle(case, monitor):
     assert rel_l1(to_np(xt), x_o) < 1e-6
 
 
+@pytest.mark.parametrize("case,monitor,eps", [("shock_ragged", "vdw", 0.0), ("wavy_periodic_smooth", "smooth", 0.0),
+                                              ("outflow_rough", "vdw", 0.0), ("outflow_rough", "vdw", 1e30)])
+def test_mixed_3d_mesh_redistribution_against_oracle(case, monitor, eps):
+    """The mixed form's mesh redistribution (FP32 monitor, filter and sweeps on the displacement from
+    x^n): the same sweeps, Delta_gamma and mesh velocity as the FP64 oracle to FP32 rounding.  A
+    tolerance of 1e30 stops the iteration after its first sweep on both sides."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = _moving(_mixed_case(case), monitor)
+    w["mesh"]["eps"] = eps
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    dt = 0.002
+    xdot_o, sw_o, gam_o = stepper.redistribute(sch, mc, JU_o, J_o, x, dt)
+    xdot = torch.empty_like(xt)
+    sw, gam = es.es_mesh_redistribute(ctx, JU, J, xt, dt, xdot)
+    assert sw == sw_o == (1 if eps > 0 else w["mesh"]["sweeps"])
+    assert abs(gam - gam_o) <= 1e-5 * gam_o
+    assert np.abs(xdot_o).max() > 0.0
+    assert np.abs(to_np(xdot) - xdot_o).max() <= 2e-5 * np.abs(xdot_o).max()
+
+
 def test_mixed_3d_sine_to_final_time_against_fp64():
     """The 3D sine wave (Example 5.6 setup, fixed mesh) at 40^3 to t = 0.05: the mixed form stays within
     1e-5 (relative L1) of the FP64 path, whose error against the exact solution it matches."""
