@@ -488,8 +488,11 @@ __global__ void __launch_bounds__(NT, W >= 16 ? 1 : (NT <= 96 ? 3 : 2)) k3_dir(D
         else { i1 = a; i2 = b; i3 = ss; }
         const size_t id = idx3(g, i1, i2, i3);
         const int bx = line * LS + q;
-#pragma unroll 1
-        for (int f = 0; f < F3_COUNT; ++f) S[f * NB + bx] = P.NF[f * N + id];
+        double v[F3_COUNT];                                  // all loads in flight before the stores
+#pragma unroll
+        for (int f = 0; f < F3_COUNT; ++f) v[f] = P.NF[f * N + id];
+#pragma unroll
+        for (int f = 0; f < F3_COUNT; ++f) S[f * NB + bx] = v[f];
         if ((s < 0 || s >= nk) && end_mirrored(g.bc[K], s < 0)) {     // wall / symmetry ghost
             S[(G_V1 + K) * NB + bx] = -S[(G_V1 + K) * NB + bx];
             S[(G_VT1 + K) * NB + bx] = -S[(G_VT1 + K) * NB + bx];

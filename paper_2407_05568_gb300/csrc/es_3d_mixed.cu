@@ -357,8 +357,11 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(Dir3FParams P) {
         else { i1 = a; i2 = b; i3 = ss; }
         const size_t id = idx3(g, i1, i2, i3);
         const int bx = line * LS + q;
-#pragma unroll 1
-        for (int f = 0; f < MF_COUNT; ++f) S[f * NB + bx] = P.NF[f * N + id];
+        float v[MF_COUNT];                                   // all loads in flight before the stores
+#pragma unroll
+        for (int f = 0; f < MF_COUNT; ++f) v[f] = P.NF[f * N + id];
+#pragma unroll
+        for (int f = 0; f < MF_COUNT; ++f) S[f * NB + bx] = v[f];
         int se = s + 3;
         se = se < 0 ? 0 : (se > nk + 5 ? nk + 5 : se);
         if (K == 0) { j1 = se; j2 = a; j3 = b; }
