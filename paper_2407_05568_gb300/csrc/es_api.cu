@@ -293,12 +293,11 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
 bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
 
 // Sec. 4 on the FP32 pipe; c->fdisp must hold the displacement of x^n.  Writes c->fxd and xdot.
-int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot) {
+// with_dt: the monitor kernel also sets the step's dt from the CFL maximum (k_dt's work).
+int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool with_dt) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const GasF32 gf = gas_f32(c->gas);
-    float* rho = (float*)c->rhoF;
-    float* Gf = (float*)c->GF;
     float* t0 = (float*)c->t0;
     float* t1 = (float*)c->t1;
     float* t2 = (float*)c->t2;
@@ -306,9 +305,9 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot) {
     float* other = (float*)c->om1;
     float* da = (float*)c->xa;
     float* db = (float*)c->xb;
-    k_mon_fields_f<<<G, B, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, rho, Gf);
-    k_mon_terms_f<<<G, B, 0, s>>>(c->g, c->mon, rho, Gf, t0, t1, t2, c->dev);
-    count(c, 2);
+    k_mon_f<<<G, B, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0, t1, t2, c->dev, with_dt ? 1 : 0,
+                            c->p.cfl, c->p.dt_fixed);
+    count(c);
     // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
     const bool fuse = c->p.dim == 2;
     const dim3 tiles((c->g.n1 + 31) / 32, (c->g.n2 + 15) / 16);
@@ -406,23 +405,26 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     if (c->p.dim == 3) return enqueue_step3(c, (double*)JU, (double*)J, x);
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
-    k_reset<<<1, 32, 0, s>>>(c->dev);
-    count(c);
     const bool f32 = mesh_on_fp32(c);
-    if (f32) {
-        k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd);
+    if (f32) {      // the displacement kernel also resets the step's reductions (k_reset's work)
+        k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
         k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, c->dev);
         count(c, 2);
     } else {
+        k_reset<<<1, 32, 0, s>>>(c->dev);
+        count(c);
         enqueue_cfl(c, JU, J, x);
     }
-    k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
-    count(c);
+    const bool dt_in_mesh = f32 && c->p.moving;       // the FP32 monitor kernel sets dt
+    if (!dt_in_mesh) {
+        k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
+        count(c);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
     if (c->p.moving) {
-        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot) : enqueue_mesh(c, JU, J, x, c->xdot);
+        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true) : enqueue_mesh(c, JU, J, x, c->xdot);
         if (rc) return rc;
         xdot = c->xdot;
     }
@@ -798,7 +800,7 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
     } else if (mesh_on_fp32(c)) {
         k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
         count(c);
-        rc = enqueue_mesh32(c, JU, J, xdot);
+        rc = enqueue_mesh32(c, JU, J, xdot, false);
     } else {
         rc = enqueue_mesh(c, JU, J, xn, xdot);
     }

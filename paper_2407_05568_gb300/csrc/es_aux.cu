@@ -119,14 +119,7 @@ __global__ void k_prim_to_cons(GridParams g, Gas G, const double* rho, const dou
 
 // ------------------------------------------------------------ time step
 __global__ void k_reset(DevScalars* d) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        for (int k = 0; k < 8; ++k) d->red[k] = 0ULL;
-        d->red[RED_GAMMA] = (unsigned long long)__double_as_longlong(1.0);
-        d->sweeps = 0;
-        d->conv = 0;
-        d->pick = 0;
-        d->done = 0u;
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) reset_scalars(d);
 }
 
 // eq. cfl: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), with zero mesh velocity
@@ -168,14 +161,7 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
 
 // Delta t = CFL / max (or the fixed step), clipped to t_end; 0 once t_end is reached
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        const double mx = __longlong_as_double((long long)d->red[RED_CFL]);
-        double dt = dt_fixed > 0.0 ? dt_fixed : cfl / mx;
-        const double left = d->t_end - d->t;
-        if (left <= 1e-14 * fmax(1.0, fabs(d->t_end))) dt = 0.0;
-        else if (dt > left) dt = left;
-        d->dt = dt;
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
 }
 
 __global__ void k_set_dt(DevScalars* d, double dt) {
@@ -528,8 +514,10 @@ __global__ void k_warm_start(GridParams g, const double* xn, const float* out, d
 // Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)
 // and FP32 mesh velocity, once per step (the base is linear in the node index,
 // so delta_k of it is exactly dxi_k e_k)
-__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd) {
+__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd,
+                           DevScalars* rst) {
     const int N = g.n1 * g.n2;
+    if (rst && blockIdx.x == 0 && threadIdx.x == 0) reset_scalars(rst);
     const double x00 = x[0];
     const double y00 = g.dim == 2 ? x[N] : 0.0;
     const double dxi1 = 1.0 / g.inv_dxi[0];

@@ -35,6 +35,26 @@ struct DevScalars {
     long long sweeps_total, solves, warm_kept; // cumulative mesh-solve counters
 };
 
+// the per-step reset of the reductions and counters (k_reset), and the time step from the CFL
+// maximum clipped to the end time (k_dt); one thread runs each
+__device__ __forceinline__ void reset_scalars(DevScalars* d) {
+    for (int k = 0; k < 8; ++k) d->red[k] = 0ULL;
+    d->red[RED_GAMMA] = (unsigned long long)__double_as_longlong(1.0);
+    d->sweeps = 0;
+    d->conv = 0;
+    d->pick = 0;
+    d->done = 0u;
+}
+
+__device__ __forceinline__ void set_dt_from_cfl(DevScalars* d, double cfl, double dt_fixed) {
+    const double mx = __longlong_as_double((long long)d->red[RED_CFL]);
+    double dt = dt_fixed > 0.0 ? dt_fixed : cfl / mx;
+    const double left = d->t_end - d->t;
+    if (left <= 1e-14 * fmax(1.0, fabs(d->t_end))) dt = 0.0;
+    else if (dt > left) dt = left;
+    d->dt = dt;
+}
+
 // kernels templated on the state type are launched through these (f32: float state)
 void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int grid, cudaStream_t s);
 void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
@@ -47,7 +67,9 @@ __global__ void k_reset(DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
 __global__ void k_set_dt(DevScalars* d, double dt);
 __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
-__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd);
+// rst (nullable): also runs k_reset's work (the first kernel of a mixed-form step)
+__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd,
+                           DevScalars* rst = nullptr);
 __global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, const double* GF, double* t0,
                             double* t1, double* t2, DevScalars* d);
 __global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,

@@ -117,8 +117,28 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
         if (g.dim == 1) {
             tot = (fabsf(v1) + c) * iJ * idx1;
         } else {
-            const float x1 = dx_dxi(g, disp, i, j, 0, 0, idx1), x2 = dx_dxi(g, disp, i, j, 0, 1, idx2);
-            const float y1 = dx_dxi(g, disp, i, j, 1, 0, idx1), y2 = dx_dxi(g, disp, i, j, 1, 1, idx2);
+            float x1, x2, y1, y2;
+            if (i >= 3 && i < g.n1 - 3 && j >= 3 && j < g.n2 - 3) {
+                // interior: the 24 displacement loads have no ghost rule and are issued together
+                float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};      // d x/d xi_1, d x/d xi_2, d y/d xi_1, d y/d xi_2
+#pragma unroll
+                for (int m = 1; m <= 3; ++m) {
+                    const float h = 0.5f * float(ec_alpha(m));
+                    s[0] += h * (disp[id + m] - disp[id - m]);
+                    s[1] += h * (disp[id + m * g.n1] - disp[id - m * g.n1]);
+                    s[2] += h * (disp[N + id + m] - disp[N + id - m]);
+                    s[3] += h * (disp[N + id + m * g.n1] - disp[N + id - m * g.n1]);
+                }
+                x1 = 1.0f + s[0] * idx1;
+                x2 = s[1] * idx2;
+                y1 = s[2] * idx1;
+                y2 = 1.0f + s[3] * idx2;
+            } else {
+                x1 = dx_dxi(g, disp, i, j, 0, 0, idx1);
+                x2 = dx_dxi(g, disp, i, j, 0, 1, idx2);
+                y1 = dx_dxi(g, disp, i, j, 1, 0, idx1);
+                y2 = dx_dxi(g, disp, i, j, 1, 1, idx2);
+            }
             const float a1 = y2, b1 = -x2;        // J dxi_1/dx
             const float a2 = -y1, b2 = x1;        // J dxi_2/dx
             tot = (fabsf(a1 * v1 + b1 * v2) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
@@ -133,25 +153,86 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
 
 // density and G = nu^3 p_nunu|_s / (2 c^2) at the nodes, then the raw monitor terms need
 // the neighbours: two kernels (as in the FP64 path)
+__device__ __forceinline__ void mon_field_f(const GridParams& g, const GasF32& G, const float* JU, const float* J,
+                                            int N, size_t P, int id, float* rho_out, float* G_out) {
+    const float iJ = 1.0f / ld2(J, N, id);
+    const float rho = ld2(JU, P, id) * iJ;
+    const float irho = 1.0f / rho;
+    float ke = 0.0f;
+    for (int k = 0; k < g.dim; ++k) {
+        const float v = ld2(JU, P, (1 + k) * N + id) * iJ * irho;
+        ke += v * v;
+    }
+    const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
+    const float T = (E * irho - 0.5f * ke + G.a * rho) * G.icv;
+    const float iom = 1.0f / (1.0f - G.b * rho);
+    const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
+    const float pnn3 = (1.0f + G.delta) * (2.0f + G.delta) * G.R * T * iom * iom * iom - 6.0f * G.a * rho;
+    *rho_out = rho;
+    *G_out = pnn3 / (2.0f * c2);
+}
+
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
+        mon_field_f(g, G, JU, J, N, P, id, rhoF + id, GF + id);
+}
+
+// k_mon_fields_f and k_mon_terms_f in one pass: the density and G of the +-1 neighbours are
+// recomputed from their state (a few float operations against a launch and a round trip of two
+// fields).  With do_dt, thread 0 also sets the step's dt from the CFL maximum (k_dt's work:
+// the CFL kernel has finished when this one starts).
+__global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
+                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed) {
+    if (do_dt && blockIdx.x == 0 && threadIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
+    const int N = g.n1 * g.n2;
+    const size_t P = size_t(g.dim + 2) * N;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const float iJ = 1.0f / ld2(J, N, id);
-        const float rho = ld2(JU, P, id) * iJ;
-        const float irho = 1.0f / rho;
-        float ke = 0.0f;
+        const int i = id % g.n1, j = id / g.n1;
+        float r0, G0;
+        mon_field_f(g, G, JU, J, N, P, id, &r0, &G0);
+        float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
         for (int k = 0; k < g.dim; ++k) {
-            const float v = ld2(JU, P, (1 + k) * N + id) * iJ * irho;
-            ke += v * v;
+            const int di = k == 0, dj = k == 1;
+            const float h = float(g.inv_dxi[k]);
+            const int sp = (g.dim == 2 ? state_index(j + dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i + di, g.n1, g.bc[0]);
+            const int sm = (g.dim == 2 ? state_index(j - dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i - di, g.n1, g.bc[0]);
+            float rp, Gp, rm, Gm;
+            mon_field_f(g, G, JU, J, N, P, sp, &rp, &Gp);
+            mon_field_f(g, G, JU, J, N, P, sm, &rm, &Gm);
+            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
+            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
+            gr += a * a;
+            gg += b * b;
+            lg += c * c;
+            lr += e * e;
         }
-        const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
-        const float T = (E * irho - 0.5f * ke + G.a * rho) * G.icv;
-        const float iom = 1.0f / (1.0f - G.b * rho);
-        const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
-        const float pnn3 = (1.0f + G.delta) * (2.0f + G.delta) * G.R * T * iom * iom * iom - 6.0f * G.a * rho;
-        rhoF[id] = rho;
-        GF[id] = pnn3 / (2.0f * c2);
+        float v0, v1, v2;
+        if (mp.kind == ES_MONITOR_SMOOTH) {
+            v0 = sqrtf(gr);
+            v1 = 0.0f;
+            v2 = sqrtf(lr);
+        } else {
+            v0 = gr;
+            v1 = mp.kappa >= 2 ? gg : 0.0f;
+            v2 = lg;
+        }
+        t0[id] = v0;
+        t1[id] = v1;
+        t2[id] = v2;
+        m0 = fmaxf(m0, v0);
+        m1 = fmaxf(m1, v1);
+        m2 = fmaxf(m2, v2);
+    }
+    m0 = block_max_f32(m0);
+    m1 = block_max_f32(m1);
+    m2 = block_max_f32(m2);
+    if (threadIdx.x == 0) {
+        atomic_max_pos(&d->red[RED_MON0], double(m0));
+        atomic_max_pos(&d->red[RED_MON1], double(m1));
+        atomic_max_pos(&d->red[RED_MON2], double(m2));
     }
 }
 
@@ -353,6 +434,17 @@ namespace es {
 constexpr int FT_X = 32, FT_Y = 16, FT_HMAX = 8;
 constexpr int FT_W = FT_X + 2 * FT_HMAX, FT_H = FT_Y + 2 * FT_HMAX;
 
+// the (x, y) cell of a TW-wide tile one block stride further on (the strided loops below step
+// the cell without an integer division per iteration)
+__device__ __forceinline__ void next_cell(int& sx, int& sy, int2 sq, int TW) {
+    sx += sq.x;
+    sy += sq.y;
+    if (sx >= TW) {
+        sx -= TW;
+        ++sy;
+    }
+}
+
 // (templated on the value type; the FP64 form keeps one pass per launch: in FP64 the halo
 // recomputation costs more than the launches it saves)
 template <class T>
@@ -360,6 +452,7 @@ __global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorPar
                                                         const T* t2, const DevScalars* d, int passes, T* out) {
     __shared__ T A[FT_W * FT_H], B[FT_W * FT_H];
     const int h = passes, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
+    const int2 sq = make_int2(int(blockDim.x) % TW, int(blockDim.x) / TW);   // one stride in cells
     const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
     const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
     const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
@@ -367,8 +460,8 @@ __global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorPar
     const T c0 = M0 > 0.0 ? T(mp.w0 / M0) : T(0);
     const T c1 = M1 > 0.0 ? T(mp.w1 / M1) : T(0);
     const T c2 = M2 > 0.0 ? T(mp.w2 / M2) : T(0);
-    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-        const int sx = idx % TW, sy = idx / TW;
+    for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
+         idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
         const int si = state_index(x0 + sx, g.n1, g.bc[0]), sj = state_index(y0 + sy, g.n2, g.bc[1]);
         const int id = sj * g.n1 + si;
         A[idx] = sqrt(T(1) + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
@@ -377,8 +470,8 @@ __global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorPar
     T* cur = A;
     T* nxt = B;
     for (int p = 1; p <= h; ++p) {
-        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-            const int sx = idx % TW, sy = idx / TW;
+        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
+             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
             if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
             T s = T(0);
             for (int dj = -1; dj <= 1; ++dj) {
@@ -390,8 +483,8 @@ __global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorPar
         }
         __syncthreads();
         // outflow ghosts take the new value of their clamped boundary node
-        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-            const int sx = idx % TW, sy = idx / TW;
+        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
+             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
             if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
             const int gi = x0 + sx, gj = y0 + sy;
             int cx = sx, cy = sy;
@@ -426,9 +519,10 @@ __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const floa
     __shared__ float Wm[FT_W * FT_H];
     __shared__ float X[2][2][FT_W * FT_H];          // [buffer][component]
     const int h = sweeps, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
+    const int2 sq = make_int2(int(blockDim.x) % TW, int(blockDim.x) / TW);
     const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
-    for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-        const int sx = idx % TW, sy = idx / TW;
+    for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
+         idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
         const int gi = x0 + sx, gj = y0 + sy;
         Wm[idx] = field_at_f(g, omega, gi, gj);
         X[0][0][idx] = disp_at(g, d0, gi, gj, 0);
@@ -443,8 +537,8 @@ __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const floa
         const float* c1 = X[b][1];
         float* n0 = X[b ^ 1][0];
         float* n1 = X[b ^ 1][1];
-        for (int idx = threadIdx.x; idx < TW * TH; idx += blockDim.x) {
-            const int sx = idx % TW, sy = idx / TW;
+        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
+             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
             if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
             const int gi = x0 + sx, gj = y0 + sy;
             const bool outside = (g.bc[0] == ES_BC_OUTFLOW && (gi < 0 || gi >= g.n1)) ||

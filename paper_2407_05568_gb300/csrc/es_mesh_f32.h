@@ -25,6 +25,8 @@ inline GasF32 gas_f32(const Gas& g) {
 // JU, J: the mixed form's (hi, lo) float planes; disp: the FP32 displacement [dim][N]
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, DevScalars* d);
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
+__global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
+                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed);
 __global__ void k_mon_terms_f(GridParams g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
                               float* t2, DevScalars* d);
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
