@@ -156,16 +156,21 @@ __global__ void k3_coords(Grid3 g, const double* xn, const double* xdot, double 
     }
 }
 
-// D[3 l + p] = delta_l[x_p] (undivided) where the xi_l index is interior, 0 elsewhere
+// The products of eq. SCLCoeff's cross form, once per node: D[3 l + j] = delta_l[x_p] x_q with
+// p = (j + 1) % 3, q = (j + 2) % 3 (delta_l undivided; 0 where the xi_l index is not interior).
+// Each is differenced by two directions' metrics, which therefore read the same rounded value.
 __global__ void k3_deriv(Grid3 g, const double* XE, double* D) {
     const int E1 = g.n[0] + 6, E2 = g.n[1] + 6, E3 = g.n[2] + 6;
     const size_t NE = size_t(E1) * E2 * E3;
     const size_t st[3] = {1, size_t(E1), size_t(E1) * E2};
     for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
         const int ee[3] = {int(e % E1), int((e / E1) % E2), int(e / (size_t(E1) * E2))};
+        const double x[3] = {XE[e], XE[NE + e], XE[2 * NE + e]};
 #pragma unroll
         for (int l = 0; l < 3; ++l) {
             const bool ok = ee[l] >= 3 && ee[l] < g.n[l] + 3;
+            double dl[3];
+#pragma unroll
             for (int p = 0; p < 3; ++p) {
                 double s = 0.0;
                 if (ok) {
@@ -173,14 +178,16 @@ __global__ void k3_deriv(Grid3 g, const double* XE, double* D) {
                     for (int m = 1; m <= 3; ++m)
                         s += 0.5 * ec_alpha(m) * (XE[p * NE + e + m * st[l]] - XE[p * NE + e - m * st[l]]);
                 }
-                D[(3 * l + p) * NE + e] = s;
+                dl[p] = s;
             }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) D[(3 * l + j) * NE + e] = dl[(j + 1) % 3] * x[(j + 2) % 3];
         }
     }
 }
 
 // J dxi_k/dx_j on direction k's grid (n_k + 6 nodes along xi_k, interior across)
-__global__ void k3_metric(Grid3 g, int k, const double* XE, const double* D, double* NKo) {
+__global__ void k3_metric(Grid3 g, int k, const double* D, double* NKo) {
     const int E1 = g.n[0] + 6, E2 = g.n[1] + 6;
     const size_t NE = size_t(E1) * E2 * (g.n[2] + 6);
     int m1 = g.n[0], m2 = g.n[1], m3 = g.n[2];
@@ -197,17 +204,15 @@ __global__ void k3_metric(Grid3 g, int k, const double* XE, const double* D, dou
         // extended-grid position: the metric grid already carries the 3 ghosts along xi_k
         const size_t e = eidx(g, a1 + (k == 0 ? 0 : 3), a2 + (k == 1 ? 0 : 3), a3 + (k == 2 ? 0 : 3));
         for (int j = 0; j < 3; ++j) {
-            const int p = (j + 1) % 3, q = (j + 2) % 3;
-            const double* Dl = D + (3 * l + p) * NE;
-            const double* Dm = D + (3 * m + p) * NE;
-            const double* Xq = XE + q * NE;
+            const double* Pl = D + (3 * l + j) * NE;      // delta_l[x_p] x_q
+            const double* Pm = D + (3 * m + j) * NE;      // delta_m[x_p] x_q
             double A = 0.0, B = 0.0;
 #pragma unroll
             for (int a = 1; a <= 3; ++a) {
                 const double h = 0.5 * ec_alpha(a);
                 const size_t sm = a * stm, sl = a * stl;
-                A += h * (Dl[e + sm] * Xq[e + sm] - Dl[e - sm] * Xq[e - sm]);
-                B += h * (Dm[e + sl] * Xq[e + sl] - Dm[e - sl] * Xq[e - sl]);
+                A += h * (Pl[e + sm] - Pl[e - sm]);
+                B += h * (Pm[e + sl] - Pm[e - sl]);
             }
             NKo[j * M + t] = (A - B) * scale;
         }
@@ -933,7 +938,7 @@ static int enqueue_metrics(Ctx3* d, const double* xn, const double* xdot, double
     const int G = d->grid;
     k3_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, d->XE);
     k3_deriv<<<G, 256, 0, s>>>(d->g, d->XE, d->D);
-    for (int k = 0; k < 3; ++k) k3_metric<<<G, 256, 0, s>>>(d->g, k, d->XE, d->D, d->NK[k]);
+    for (int k = 0; k < 3; ++k) k3_metric<<<G, 256, 0, s>>>(d->g, k, d->D, d->NK[k]);
     return 5;
 }
 

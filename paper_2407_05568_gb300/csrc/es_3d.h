@@ -32,7 +32,7 @@ struct Ctx3 {
     size_t NE;                // nodes of the grid extended by 3 ghosts in every direction
     size_t NKk[3];            // nodes of direction k's metric grid (3 ghosts along xi_k only)
     double* XE;               // stage coordinates on the extended grid [3][NE]
-    double* D;                // delta_l[x_p] on the extended grid [9][NE] (valid where xi_l is interior)
+    double* D;                // cross-form products delta_l[x_p] x_q on the extended grid [9][NE] (k3_deriv)
     double* NK[3];            // J dxi_k/dx_j on direction k's metric grid [3][NKk]
     double* NF;               // node fields of the stage state [F3_COUNT][N] (mixed: float fields)
     double* RH;               // right-hand sides accumulated over the directions [6][N] (mixed: float)
