@@ -648,7 +648,6 @@ __device__ __forceinline__ float warp_min_f(float v) {
 __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
                               float* t2, DevScalars* d) {
     const int N = g.n[0] * g.n[1] * g.n[2];
-    const size_t P = size_t(N);
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         int ii[3];
@@ -697,7 +696,6 @@ __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, cons
 // omega_i <- sum_{j in {0,+-1}^3} (1/2)^(|j|_1 + 3) omega_{i+j} (Sec. 4's low-pass filter)
 __global__ void k3f_filter(Grid3 g, const float* in, float* out) {
     const int N = g.n[0] * g.n[1] * g.n[2];
-    const size_t P = size_t(N);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         int ii[3];
         split3(g, id, ii);
