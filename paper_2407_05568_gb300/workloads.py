@@ -159,6 +159,14 @@ def riemann_1d(name="RP1", n=100, moving=True, t_end=None, cfl=0.4):
                           sweeps=10, eps=0.0))
 
 
+def mm1(w):
+    """The MM1 counterpart of a moving-mesh workload (Sec. 5: the monitor without the fundamental
+    derivative, alpha_2 = alpha_3 = 0 in eq. van der Waalsmonitor)."""
+    m = dict(w["mesh"])
+    m["alphas"] = (m["alphas"][0], 0.0, 0.0)
+    return dict(w, mesh=m)
+
+
 def vortex_density(X, Y, t=0.0, eps_v=5.0, period=10.0, center=5.0):
     """Density of the isentropic vortex (gamma = 1.4) carried by the mean flow (1, 1) to time t:
     the initial field at (x - t, y - t), wrapped into the periodic box."""

@@ -116,7 +116,7 @@ def test_mixed_design_order_1d():
     assert order > 4.5, errs
 
 
-@pytest.mark.parametrize("case", ["riemann2d", "rp1d", "wavy_periodic"])
+@pytest.mark.parametrize("case", ["riemann2d", "rp1d", "wavy_periodic", "riemann2d_mm1"])
 def test_mixed_mesh_redistribution_fp32_vs_oracle(case):
     """The mixed form's time step and mesh redistribution run on the FP32 displacement:
     the same sweeps, Delta_gamma and mesh velocity as the FP64 oracle to FP32 rounding."""
@@ -125,6 +125,8 @@ def test_mixed_mesh_redistribution_fp32_vs_oracle(case):
     from paper_2407_05568_gb300 import es
     if case == "riemann2d":
         w = wl.riemann_2d(64, seed=5)
+    elif case == "riemann2d_mm1":                  # monitor without G (MM1)
+        w = wl.mm1(wl.riemann_2d(64, seed=5))
     elif case == "rp1d":
         w = wl.riemann_1d("RP1", n=300)
     else:

@@ -192,6 +192,14 @@ def test_step_parity_riemann2d_ragged():
     _one_step_compare(_ragged_riemann(), nsteps=2)
 
 
+@pytest.mark.parametrize("case", ["rp1d", "riemann2d_ragged"])
+def test_step_parity_mm1(case):
+    """The MM1 variant (monitor without G: alpha_2 = alpha_3 = 0) of Example 5.2's RP1 and of the 2D
+    Riemann problem: 3 and 2 full steps."""
+    w = wl.mm1(_rp1d(300) if case == "rp1d" else _ragged_riemann())
+    _one_step_compare(w, nsteps=3 if case == "rp1d" else 2)
+
+
 def test_step_parity_riemann2d_full_size():
     """The 200 x 200 moving-mesh vdW Riemann problem, in the launch configuration of the bench."""
     _one_step_compare(wl.riemann_2d(200, seed=5), nsteps=1)

@@ -280,6 +280,23 @@ def test_filter_preserves_constants_and_sums():
     assert np.isclose(mesh.low_pass(om1, 1, ("periodic",)).sum(), om1.sum(), rtol=1e-14)
 
 
+def test_mm1_monitor_sees_the_density_only():
+    """MM1 (Sec. 5: alpha_2 = alpha_3 = 0 in eq. van der Waalsmonitor): omega does not depend on G, and
+    on a piecewise-linear density with slopes s_1 < s_2 it is sqrt(1 + alpha_1 (s / s_2)^2) away from
+    the kink and the ends (second-order central differences are exact on linear data)."""
+    x, d = wl.uniform_nodes(41, 0.0, 1.0, False)
+    s1, s2 = 0.5, 2.0
+    rho = np.where(x < 0.5, 1.0 + s1 * (x - 0.5), 1.0 + s2 * (x - 0.5))
+    G = np.random.default_rng(7).uniform(-1.0, 1.0, x.shape)
+    alphas = wl.mm1(wl.riemann_1d("RP1", n=41))["mesh"]["alphas"]
+    assert alphas[1:] == (0.0, 0.0)
+    om = mesh.monitor_vdw([rho, G], G, alphas, 1, ("outflow",), (d,))
+    assert np.array_equal(om, mesh.monitor_vdw([rho, 0 * G], 0 * G, alphas, 1, ("outflow",), (d,)))
+    left, right = slice(1, 19), slice(22, 40)
+    assert np.allclose(om[left] ** 2 - 1.0, alphas[0] * (s1 / s2) ** 2, rtol=1e-12)
+    assert np.allclose(om[right] ** 2 - 1.0, alphas[0], rtol=1e-12)
+
+
 def test_uniform_monitor_fixed_point():
     """With omega = const the uniform mesh solves the discrete mesh equation (x unchanged)."""
     w = wl.riemann_2d(12, moving=True)
