@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-matched-error", action="store_true",
+                    help="skip the default matched-error comparison (1D sine 50..200, vortex 64^2..128^2, both forms)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="also run the precision-form sweep: 2D sine 1024^2 and the vortex 64^2..1024^2, both forms")
     ap.add_argument("--learned", action="store_true",
@@ -439,7 +441,11 @@ def matched_error(rows, levels=(1e-4, 1e-5, 1e-6, 1e-7, 1e-8)):
     return out
 
 
-def measure_precision_sweep(args, dev):
+# the default line's matched-error comparison: the smallest grids of the two accuracy sweeps
+QUICK_SWEEP = [("sine1d", 50), ("sine1d", 100), ("sine1d", 200), ("vortex", 64), ("vortex", 128)]
+
+
+def measure_precision_sweep(args, dev, cases=None):
     """The precision form against the plain FP64 form: L1(rho) against the exact solution and
     against the FP64 run, throughput and time to solution, on the 1D sine wave (50 .. 1600 nodes,
     fixed mesh, dt = 0.4 dxi^(5/3), t = 0.1), the 2D sine wave (1024^2, t = 0.1) and the
@@ -447,8 +453,9 @@ def measure_precision_sweep(args, dev):
     each form that meets each error level (matched error)."""
     from paper_2407_05568_gb300 import workloads as wl
     out = []
-    cases = ([("sine1d", n) for n in (50, 100, 200, 400, 800, 1600)] + [("sine2d", 1024)]
-             + [("vortex", n) for n in (64, 128, 256, 512, 1024)])
+    if cases is None:
+        cases = ([("sine1d", n) for n in (50, 100, 200, 400, 800, 1600)] + [("sine2d", 1024)]
+                 + [("vortex", n) for n in (64, 128, 256, 512, 1024)])
     for name, n in cases:
         dt_fixed = 0.0
         if name == "sine1d":
@@ -482,7 +489,8 @@ def measure_precision_sweep(args, dev):
         for a, b in zip(rows, rows[1:]):
             for prec in ("fp64", "mixed"):
                 b[prec]["order_vs_previous"] = float(np.log2(a[prec]["l1_vs_exact"] / b[prec]["l1_vs_exact"]))
-        matched[case] = matched_error(rows)
+        if rows:
+            matched[case] = matched_error(rows)
     return {"runs": out, "matched_error": matched}
 
 
@@ -589,6 +597,9 @@ def run_gpu(args):
     three_d = measure_three_d(args, dev, stream) if args.three_d > 0 and rank == 0 else None
     learned_res = measure_learned(args, dev) if args.learned and rank == 0 else None
     sweep_res = measure_precision_sweep(args, dev) if args.precision_sweep and rank == 0 else None
+    quick = None
+    if sweep_res is None and not args.no_matched_error and rank == 0:
+        quick = measure_precision_sweep(args, dev, QUICK_SWEEP)
     nn_res = measure_nn_inference(args.nn_inference, dev) if args.nn_inference > 0 and rank == 0 else None
     if rank == 0:
         m = main_form
@@ -618,6 +629,13 @@ def run_gpu(args):
             line["learned"] = learned_res
         if sweep_res is not None:
             line["precision_sweep"] = sweep_res
+            line["matched_error"] = sweep_res["matched_error"]
+        elif quick is not None:
+            # the metric's comparison at matched L1(rho) against the exact solution: per level, the
+            # smallest grid of each form that reaches it and its time to solution (to t_end)
+            line["matched_error"] = dict(quick["matched_error"],
+                                         cases="1D sine 50/100/200 nodes to t = 0.1 (dt = 0.4 dxi^(5/3)), "
+                                               "ideal-gas isentropic vortex 64^2/128^2 to t = 1, both forms")
         if nn_res is not None:
             line["nn_inference"] = nn_res
         if not args.no_cpu_baseline:
