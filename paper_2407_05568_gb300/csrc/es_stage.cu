@@ -516,7 +516,7 @@ static cudaError_t launch_tile(const StageParams& P, cudaStream_t s) {
 cudaError_t stage_prepare_fp64(int dim) {
     if (dim == 1) return prepare_tile<1, 254, 1, 256>();
     cudaError_t e = prepare_tile<2, 32, 8, 288>();
-    if (e == cudaSuccess) e = prepare_tile<2, 25, 11, 320>();
+    if (e == cudaSuccess) e = prepare_tile<2, 25, 11, 384>();
     if (e == cudaSuccess) e = prepare_tile<2, 16, 16, 288>();
     if (e == cudaSuccess) e = prepare_tile<2, 32, 12, 416>();
     if (e == cudaSuccess) e = prepare_tile<2, 20, 10, 224>();
@@ -526,7 +526,7 @@ cudaError_t stage_prepare_fp64(int dim) {
 cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s) {
     if (P.dim == 1) return launch_tile<1, 254, 1, 256>(P, s);
     switch (P.tile) {
-        case 1: return launch_tile<2, 25, 11, 320>(P, s);
+        case 1: return launch_tile<2, 25, 11, 384>(P, s);
         case 2: return launch_tile<2, 16, 16, 288>(P, s);
         case 3: return launch_tile<2, 32, 12, 416>(P, s);
         case 4: return launch_tile<2, 20, 10, 224>(P, s);
@@ -535,7 +535,7 @@ cudaError_t launch_stage_fp64(const StageParams& P, cudaStream_t s) {
 }
 
 void stage_tile_shape(bool mixed, int k, int* bx, int* by, int* nt) {
-    static const int fp64[STAGE_NTILES][3] = {{32, 8, 288}, {25, 11, 320}, {16, 16, 288}, {32, 12, 416},
+    static const int fp64[STAGE_NTILES][3] = {{32, 8, 288}, {25, 11, 384}, {16, 16, 288}, {32, 12, 416},
                                               {20, 10, 224}};
     static const int f32[STAGE_NTILES][3] = {{32, 8, 288}, {25, 6, 192}, {20, 8, 192}, {32, 16, 544}, {16, 8, 160}};
     const int(*t)[3] = mixed ? f32 : fp64;
