@@ -53,13 +53,17 @@ def uniform_nodes(n, lo, hi, periodic):
     return lo + d * np.arange(n), d
 
 
-def sine_1d(n=200, t_end=0.1, cfl=0.4):
-    """1D periodic density sine wave on a fixed uniform mesh (Example 5.1 setup, fixed mesh):
-    rho = 0.5 + 0.2 sin(2 pi x), v = 1, p = 1 on [0, 1); exact rho(x - t)."""
+def sine_1d(n=200, t_end=0.1, cfl=0.4, moving=False):
+    """1D periodic density sine wave (Example 5.1 setup): rho = 0.5 + 0.2 sin(2 pi x), v = 1, p = 1
+    on [0, 1); exact rho(x - t).  moving: Example 5.1's MM (the smooth-test monitor with
+    alpha = (20, 15), 20 filter passes, 10 Jacobi sweeps); otherwise the fixed uniform mesh."""
     x, d = uniform_nodes(n, 0.0, 1.0, True)
-    return dict(gas=UNITS_A, dim=1, n=(n,), dxi=(d,), bc=("periodic",), period=(1.0,),
-                x=x[None].copy(), rho=0.5 + 0.2 * np.sin(2 * np.pi * x), v=np.ones((1, n)),
-                p=np.ones(n), t_end=t_end, cfl=cfl, moving=False)
+    w = dict(gas=UNITS_A, dim=1, n=(n,), dxi=(d,), bc=("periodic",), period=(1.0,),
+             x=x[None].copy(), rho=0.5 + 0.2 * np.sin(2 * np.pi * x), v=np.ones((1, n)),
+             p=np.ones(n), t_end=t_end, cfl=cfl, moving=moving)
+    if moving:
+        w["mesh"] = dict(monitor="smooth", alphas=(20.0, 15.0), kappa=2, filter_passes=20, sweeps=10, eps=0.0)
+    return w
 
 
 def sine_2d(n=1024, t_end=0.1, cfl=0.4):

@@ -205,6 +205,29 @@ def test_step_parity_riemann2d_full_size():
     _one_step_compare(wl.riemann_2d(200, seed=5), nsteps=1)
 
 
+def test_design_order_1d_sine_moving_mesh_gpu():
+    """Example 5.1's MM on the GPU (smooth-test monitor, 20 filter passes, dt = CFL dxi^(5/3)): ~5th order
+    in rho at the moved nodes, and the run at 80 nodes equals the oracle's."""
+    from paper_2407_05568_gb300 import es
+    errs = []
+    for n in (20, 40, 80):
+        w = wl.sine_1d(n, t_end=0.05, moving=True)
+        dt = 0.4 * w["dxi"][0] ** (5.0 / 3.0)
+        ctx, JU, J, xt = gpu_setup(w, dt_fixed=dt)
+        es.es_set_time(ctx, 0.0)
+        es.es_steps(ctx, JU, J, xt, int(np.ceil(w["t_end"] / dt)) + 2, w["t_end"])
+        assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+        x = to_np(xt)
+        ex = 0.5 + 0.2 * np.sin(2 * np.pi * (x[0] - w["t_end"]))
+        errs.append(np.abs(to_np(JU)[0] / to_np(J) - ex).mean())
+    order = np.log2(errs[-2] / errs[-1])
+    assert order > 4.5, errs
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    JU_o, J_o, x_o, _ = stepper.run(sch, mc, JU_o, J_o, x_o, w["t_end"], 0.4, dt_fixed=dt)
+    assert rel_l1(to_np(JU), JU_o) < 1e-10
+    assert np.abs(x - x_o).max() < 1e-12
+
+
 def test_steps_stop_at_t_end():
     """Steps after t_end are no-ops; the last step is shortened to land on t_end."""
     from paper_2407_05568_gb300 import es

@@ -364,6 +364,24 @@ def test_design_order_1d_sine():
     assert order > 4.5, errs
 
 
+def test_design_order_1d_sine_moving_mesh():
+    """Example 5.1's MM (smooth-test monitor, alpha = (20, 15), 20 filter passes, dt = CFL dxi^(5/3)):
+    the error in rho at the moved nodes drops at ~5th order, as on the fixed mesh."""
+    errs = []
+    for n in (20, 40, 80):
+        w = wl.sine_1d(n, t_end=0.05, moving=True)
+        sch = _scheme(w)
+        J = op.node_jacobian(sch, w["x"])
+        JU = thermo.prim_to_cons(sch.gas, w["rho"], w["v"], w["p"]) * J
+        mc = stepper.MeshControl(moving=True, **w["mesh"])
+        JU, J, x, _ = stepper.run(sch, mc, JU, J, w["x"], w["t_end"], 0.4, dt_fixed=0.4 * w["dxi"][0] ** (5 / 3))
+        assert np.abs(x - w["x"]).max() > 1e-3 * w["dxi"][0]          # the mesh did move
+        ex = 0.5 + 0.2 * np.sin(2 * np.pi * (x[0] - w["t_end"]))
+        errs.append(np.abs(JU[0] / J - ex).mean())
+    order = np.log2(errs[-2] / errs[-1])
+    assert order > 4.5, errs
+
+
 def test_moving_mesh_step_runs_and_conserves():
     """One full MM step on the 1D sine (Example 5.1 monitor): mass is conserved on periodic data."""
     w = wl.sine_1d(40)
