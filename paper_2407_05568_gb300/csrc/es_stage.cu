@@ -42,9 +42,21 @@ struct Tile {
     static constexpr int NF1 = (DIM == 2 ? BY : 1) * (BX + 1);
     static constexpr int NF2 = DIM == 2 ? BX * (BY + 1) : 0;
     static constexpr int NF = NF1 > NF2 ? NF1 : NF2;
-    static constexpr int PAIR_DOUBLES = (NP * NC > 4 * NB) ? NP * NC : 4 * NB;   // also holds coords
-    static constexpr size_t SMEM = sizeof(double) * (size_t(F_COUNT) * NB + PAIR_DOUBLES + NF * (NC + 1));
-    // one thread per face of the larger direction, so each face phase is one pass
+    // Joint schedule (2D, when shared memory allows): the pairs of both directions in one phase
+    // and their faces in the next (two block barriers per stage instead of six, and the faces
+    // dealt to the warps as one pool of NF1 + NF2).  Otherwise pairs and faces go direction by
+    // direction.
+    static constexpr size_t FIELDS = sizeof(double) * size_t(F_COUNT) * NB;
+    static constexpr int PAIRJ = ((NP1 + NP2) * NC > 4 * NB) ? (NP1 + NP2) * NC : 4 * NB;
+    static constexpr size_t SMEM_JOINT = FIELDS + sizeof(double) * (size_t(PAIRJ) + size_t(NF1 + NF2) * (NC + 1));
+    static constexpr bool JOINT = DIM == 2 && SMEM_JOINT <= 227 * 1024;
+    // pair and face buffers: per-component strides and the offset of direction 2's entries
+    static constexpr int PS = JOINT ? NP1 + NP2 : NP;
+    static constexpr int FS = JOINT ? NF1 + NF2 : NF;
+    static constexpr int POFF2 = JOINT ? NP1 : 0;
+    static constexpr int FOFF2 = JOINT ? NF1 : 0;
+    static constexpr int PAIR_DOUBLES = JOINT ? PAIRJ : ((NP * NC > 4 * NB) ? NP * NC : 4 * NB);   // also holds coords
+    static constexpr size_t SMEM = FIELDS + sizeof(double) * (size_t(PAIR_DOUBLES) + size_t(FS) * (NC + 1));
     static constexpr int THREADS = NT;
     static_assert(NT >= BX * (DIM == 2 ? BY : 1) && NT % 32 == 0, "threads cover the tile");
 };
@@ -315,6 +327,88 @@ __device__ __forceinline__ void stage_coords(const StageParams& P, int gi, int g
     }
 }
 
+// geometry of direction k in the box: lines, interior nodes per line, pairs per line, node step
+// and the metric slots
+template <int DIM, int BX, int BY>
+struct DirGeo {
+    int k, nlines, LB, per_line, step, fN, fNy, fXT;
+    __device__ __forceinline__ explicit DirGeo(int kk) : k(kk) {
+        nlines = k == 0 ? (DIM == 2 ? BY : 1) : BX;
+        LB = k == 0 ? BX : BY;
+        per_line = 3 * LB + 6;
+        step = k == 0 ? 1 : BX + 6;
+        fN = k == 0 ? F_N1X : F_N2X;
+        fNy = k == 0 ? F_N1Y : F_N2Y;
+        fXT = k == 0 ? F_XT1 : F_XT2;
+    }
+    __device__ __forceinline__ int base(int line) const {
+        return k == 0 ? (DIM == 2 ? (3 + line) * (BX + 6) : 0) : 3 + line;
+    }
+};
+
+// ---- C: pair flux P_m(q) = F(U_q, U_{q+m}), q = 3-m .. LB+2, item t of direction d; stored at
+// PB[c * ps + out]
+template <int DIM, int BX, int BY>
+__device__ __forceinline__ void pair_item(const double* S, int NB, const DirGeo<DIM, BX, BY>& d, int t, const Gas& G,
+                                          double* PB, int ps, int out) {
+    const int line = t / d.per_line, kk = t % d.per_line;
+    int m, q;
+    if (kk < d.LB + 1) { m = 1; q = 2 + kk; }
+    else if (kk < 2 * d.LB + 3) { m = 2; q = 1 + (kk - d.LB - 1); }
+    else { m = 3; q = kk - 2 * d.LB - 3; }
+    const int l = d.base(line) + q * d.step, r = l + m * d.step;
+    const double nx = 0.5 * (S[d.fN * NB + l] + S[d.fN * NB + r]);
+    const double ny = 0.5 * (S[d.fNy * NB + l] + S[d.fNy * NB + r]);
+    const double xt = 0.5 * (S[d.fXT * NB + l] + S[d.fXT * NB + r]);
+    double f[DIM + 2];
+    pair_flux<DIM>(S, NB, l, r, nx, ny, xt, G, f);
+#pragma unroll
+    for (int c = 0; c < DIM + 2; ++c) PB[c * ps + out] = f[c];
+}
+
+// ---- D: face flux at q+1/2, q = 2 .. LB+2 (box coordinates), item t of direction d: the 6th-order
+// combination of the direction's pairs (which start at PB[c * ps + poff]) plus the dissipation;
+// stored at FB[c * fs + out]
+template <int DIM, int BX, int BY>
+__device__ __forceinline__ void face_item(const double* S, int NB, const DirGeo<DIM, BX, BY>& d, int t,
+                                          const StageParams& P, const double* PB, int ps, int poff, double* FB,
+                                          int fs, int out) {
+    constexpr int NC = DIM + 2;
+    const int line = t / (d.LB + 1), f = t % (d.LB + 1);
+    const int q = 2 + f;
+    const int pbase = poff + line * d.per_line;
+    double F[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) F[c] = 0.0;
+    double FJ = 0.0;
+    const int base = d.base(line);
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+        const int off = m == 1 ? 0 : (m == 2 ? d.LB + 1 : 2 * d.LB + 3);
+        const double al = ec_alpha(m);
+        for (int s = 0; s < m; ++s) {
+            const int qq = q - s;                       // left node of the pair
+            const int pi = pbase + off + (qq - (3 - m));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) F[c] += al * PB[c * ps + pi];
+            FJ += al * 0.5 * (S[d.fXT * NB + base + qq * d.step] + S[d.fXT * NB + base + (qq + m) * d.step]);
+        }
+    }
+    if (P.diss) {
+        const int l = base + q * d.step;
+        const double nx = 0.5 * (S[d.fN * NB + l] + S[d.fN * NB + l + d.step]);
+        const double ny = 0.5 * (S[d.fNy * NB + l] + S[d.fNy * NB + l + d.step]);
+        const double xtf = 0.5 * (S[d.fXT * NB + l] + S[d.fXT * NB + l + d.step]);
+        double dd[NC];
+        face_dissipation<DIM>(S, NB, l, d.step, nx, ny, xtf, P.gas, P.weno, dd, P.status, 0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) F[c] += dd[c];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) FB[c * fs + out] = F[c];
+    FB[NC * fs + out] = FJ;
+}
+
 template <int DIM, int BX, int BY, int NT>
 __global__ void __launch_bounds__(NT, 1)
 stage_kernel_fp64(StageParams P) {
@@ -323,7 +417,7 @@ stage_kernel_fp64(StageParams P) {
     extern __shared__ double smem[];
     double* S = smem;                                   // F_COUNT * NB
     double* PB = smem + F_COUNT * NB;                   // pair buffer (also the coordinates)
-    double* FB = PB + TL::PAIR_DOUBLES;                 // face buffer (NC + 1) * NF
+    double* FB = PB + TL::PAIR_DOUBLES;                 // face buffer (NC + 1) * FS
     const int tid = threadIdx.x;
     const int ntx = (P.n1 + BX - 1) / BX;
     const int i0 = (blockIdx.x % ntx) * BX;
@@ -396,81 +490,50 @@ stage_kernel_fp64(StageParams P) {
     for (int c = 0; c <= NC; ++c) acc[c] = 0.0;
     const int tx = tid % BX, ty = tid / BX;
 
+    // ---- C, D, E: pairs, faces and the divergence at the interior node (tx, ty)
+    if constexpr (TL::JOINT) {
+        // a warp may hold items of both directions: the direction is data (one code path), not a branch
+        for (int t = tid; t < TL::NP1 + TL::NP2; t += TL::THREADS) {
+            const bool two = t >= TL::NP1;
+            pair_item<DIM, BX, BY>(S, NB, DirGeo<DIM, BX, BY>(two ? 1 : 0), two ? t - TL::NP1 : t, G, PB, TL::PS, t);
+        }
+        __syncthreads();
+        for (int t = tid; t < TL::NF1 + TL::NF2; t += TL::THREADS) {
+            const bool two = t >= TL::NF1;
+            face_item<DIM, BX, BY>(S, NB, DirGeo<DIM, BX, BY>(two ? 1 : 0), two ? t - TL::NF1 : t, P, PB, TL::PS,
+                                   two ? TL::POFF2 : 0, FB, TL::FS, t);
+        }
+        __syncthreads();
+        if (tid < BX * BY) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int LB = k == 0 ? BX : BY;
+                const int fm = (k == 0 ? 0 : TL::FOFF2) + (k == 0 ? ty : tx) * (LB + 1) + (k == 0 ? tx : ty);
+                const double inv = P.inv_dxi[k];
+#pragma unroll
+                for (int c = 0; c <= NC; ++c) acc[c] -= (FB[c * TL::FS + fm + 1] - FB[c * TL::FS + fm]) * inv;
+            }
+        }
+    } else {
 #pragma unroll 1
-    for (int k = 0; k < DIM; ++k) {
-        // geometry of direction k: lines, line length in pairs/faces, node steps
-        const int nlines = k == 0 ? (DIM == 2 ? BY : 1) : BX;
-        const int LB = k == 0 ? BX : BY;              // interior nodes along the line
-        const int per_line = 3 * LB + 6;
-        const int step = k == 0 ? 1 : GX;
-        const int fN = k == 0 ? F_N1X : F_N2X;
-        const int fNy = k == 0 ? F_N1Y : F_N2Y;
-        const int fXT = k == 0 ? F_XT1 : F_XT2;
-        // ---- C: pair fluxes P_m(q) = F(U_q, U_{q+m}), q = 3-m .. LB+2 along the line
-        for (int t = tid; t < nlines * per_line; t += TL::THREADS) {
-            const int line = t / per_line, kk = t % per_line;
-            int m, q;
-            if (kk < LB + 1) { m = 1; q = 2 + kk; }
-            else if (kk < 2 * LB + 3) { m = 2; q = 1 + (kk - LB - 1); }
-            else { m = 3; q = kk - 2 * LB - 3; }
-            const int base = k == 0 ? (DIM == 2 ? (3 + line) * GX : 0) : 3 + line;
-            const int l = base + q * step, r = l + m * step;
-            const double nx = 0.5 * (S[fN * NB + l] + S[fN * NB + r]);
-            const double ny = 0.5 * (S[fNy * NB + l] + S[fNy * NB + r]);
-            const double xt = 0.5 * (S[fXT * NB + l] + S[fXT * NB + r]);
-            double f[NC];
-            pair_flux<DIM>(S, NB, l, r, nx, ny, xt, G, f);
+        for (int k = 0; k < DIM; ++k) {
+            const DirGeo<DIM, BX, BY> d(k);
+            for (int t = tid; t < d.nlines * d.per_line; t += TL::THREADS)
+                pair_item<DIM, BX, BY>(S, NB, d, t, G, PB, TL::PS, t);
+            __syncthreads();
+            for (int t = tid; t < d.nlines * (d.LB + 1); t += TL::THREADS)
+                face_item<DIM, BX, BY>(S, NB, d, t, P, PB, TL::PS, 0, FB, TL::FS, t);
+            __syncthreads();
+            if (tid < BX * (DIM == 2 ? BY : 1)) {
+                const int line = k == 0 ? ty : tx;
+                const int pos = k == 0 ? tx : ty;
+                const int fm = line * (d.LB + 1) + pos;           // face pos - 1/2
+                const double inv = P.inv_dxi[k];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) PB[c * TL::NP + t] = f[c];
-        }
-        __syncthreads();
-        // ---- D: face fluxes at q+1/2, q = 2 .. LB+2 (box coordinates)
-        for (int t = tid; t < nlines * (LB + 1); t += TL::THREADS) {
-            const int line = t / (LB + 1), f = t % (LB + 1);
-            const int q = 2 + f;
-            const int pbase = line * per_line;
-            double F[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) F[c] = 0.0;
-            double FJ = 0.0;
-            const int base = k == 0 ? (DIM == 2 ? (3 + line) * GX : 0) : 3 + line;
-#pragma unroll
-            for (int m = 1; m <= 3; ++m) {
-                const int off = m == 1 ? 0 : (m == 2 ? LB + 1 : 2 * LB + 3);
-                const double al = ec_alpha(m);
-                for (int s = 0; s < m; ++s) {
-                    const int qq = q - s;                       // left node of the pair
-                    const int pi = pbase + off + (qq - (3 - m));
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) F[c] += al * PB[c * TL::NP + pi];
-                    FJ += al * 0.5 * (S[fXT * NB + base + qq * step] + S[fXT * NB + base + (qq + m) * step]);
-                }
+                for (int c = 0; c <= NC; ++c) acc[c] -= (FB[c * TL::FS + fm + 1] - FB[c * TL::FS + fm]) * inv;
             }
-            if (P.diss) {
-                const int l = base + q * step;
-                const double nx = 0.5 * (S[fN * NB + l] + S[fN * NB + l + step]);
-                const double ny = 0.5 * (S[fNy * NB + l] + S[fNy * NB + l + step]);
-                const double xtf = 0.5 * (S[fXT * NB + l] + S[fXT * NB + l + step]);
-                double d[NC];
-                face_dissipation<DIM>(S, NB, l, step, nx, ny, xtf, G, P.weno, d, P.status, 0);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) F[c] += d[c];
-            }
-#pragma unroll
-            for (int c = 0; c < NC; ++c) FB[c * TL::NF + t] = F[c];
-            FB[NC * TL::NF + t] = FJ;
+            __syncthreads();
         }
-        __syncthreads();
-        // ---- E: divergence at the interior node (tx, ty)
-        if (tid < BX * (DIM == 2 ? BY : 1)) {
-            const int line = k == 0 ? ty : tx;
-            const int pos = k == 0 ? tx : ty;
-            const int fm = line * (LB + 1) + pos;           // face pos - 1/2
-            const double inv = P.inv_dxi[k];
-#pragma unroll
-            for (int c = 0; c <= NC; ++c) acc[c] -= (FB[c * TL::NF + fm + 1] - FB[c * TL::NF + fm]) * inv;
-        }
-        __syncthreads();
     }
 
     // ---- F: Shu-Osher combination (or the bare right-hand side)
@@ -510,7 +573,7 @@ static cudaError_t launch_tile(const StageParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// 2D shapes: 32 x 8 nodes with 288 threads (= the 32 x 9 faces of xi_2), 25 x 11 with 320
+// 2D shapes: 32 x 8 nodes with 288 threads (= the 32 x 9 faces of xi_2), 25 x 11 with 384
 // (25 x 12 = 300 faces; 8 x 19 = 152 tiles cover 200 x 200 in one wave on 152 SMs), 16 x 16
 // with 288 (272 faces), 32 x 12 with 416 (416 faces; less halo per node), 20 x 10 with 224.  1D: 254 nodes, 256 threads (255 faces, 768 pairs = three passes).
 cudaError_t stage_prepare_fp64(int dim) {
