@@ -665,7 +665,7 @@ TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12), 5: (20, 10)
          "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16), 5: (16, 8)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
 # kernel as it is now (a kernel changed since its capture has no entry); other sizes were not captured
-TRAFFIC_200 = {"stage_kernel_mixed<2,16,8>": 2343680 + 0}
+TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3032064 + 0, "stage_kernel_mixed<2,16,8>": 2343680 + 0}
 
 
 def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
