@@ -176,6 +176,12 @@ int es_steps(es_ctx* ctx, void* JU, void* J, double* x, int nsteps, double t_end
 int es_set_time(es_ctx* ctx, double t);
 int es_get_time(es_ctx* ctx, double* t_host, double* last_dt_host);   /* synchronises */
 
+/* One full step (Sec. 4's time step, mesh redistribution and the three SSP-RK3 stages of
+ * eq. semi_U / semi_J): es_steps with nsteps = 1.  If t_host or dt_host is non-null it
+ * synchronises and writes the time after the step and the step taken (0 once t_end is
+ * reached).  Errors as es_steps. */
+int es_step(es_ctx* ctx, void* JU, void* J, double* x, double t_end, double* t_host, double* dt_host);
+
 /* End-to-end form for callers holding HOST arrays: copies JU_host, J_host,
  * x_host to context-owned device buffers, runs es_steps, copies them back and
  * synchronises.  Same layouts as the device arrays. */

@@ -945,6 +945,12 @@ int es_get_time(es_ctx* c, double* t_host, double* last_dt_host) {
     return ES_OK;
 }
 
+int es_step(es_ctx* c, void* JU, void* J, double* x, double t_end, double* t_host, double* dt_host) {
+    const int rc = es_steps(c, JU, J, x, 1, t_end);
+    if (rc || (!t_host && !dt_host)) return rc;
+    return es_get_time(c, t_host, dt_host);
+}
+
 int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) {
     if (!c || !JU || !J || !x || nsteps < 0) return fail(c, ES_ERR_ARG, "bad argument");
     if (nsteps == 0) return ES_OK;

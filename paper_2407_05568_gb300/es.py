@@ -6,7 +6,7 @@ the library is missing: there is no other code path.
 
 Functions keep the C names: ``es_create``, ``es_init_mesh``, ``es_prim_to_cons``,
 ``es_rhs``, ``es_rk_stage``, ``es_cfl_dt``, ``es_mesh_redistribute``,
-``es_steps``, ``es_set_time``, ``es_get_time``, ``es_run_host``, ``es_check``.
+``es_step``, ``es_steps``, ``es_set_time``, ``es_get_time``, ``es_run_host``, ``es_check``.
 """
 import ctypes
 import os
@@ -62,6 +62,7 @@ def lib():
         L.es_cfl_dt.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d)]
         L.es_mesh_redistribute.argtypes = [vp, vp, vp, vp, d, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         L.es_steps.argtypes = [vp, vp, vp, vp, i, d]
+        L.es_step.argtypes = [vp, vp, vp, vp, d, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.es_set_time.argtypes = [vp, d]
         L.es_get_time.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.es_run_host.argtypes = [vp, vp, vp, vp, i, d]
@@ -110,7 +111,7 @@ def lib():
                      "es_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
-                     "es_mesh_redistribute", "es_steps", "es_set_time", "es_get_time", "es_run_host",
+                     "es_mesh_redistribute", "es_steps", "es_step", "es_set_time", "es_get_time", "es_run_host",
                      "es_check", "es_last_error"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -344,6 +345,16 @@ def es_nn_adam(master, w_bf16, grad, m, v, lr, beta1, beta2, eps, step, stream=N
 def es_steps(ctx, JU, J, x, nsteps, t_end):
     S = ctx.state_dtype
     ctx._call(lib().es_steps(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), int(nsteps), float(t_end)))
+
+
+def es_step(ctx, JU, J, x, t_end):
+    """One full step; returns (time after the step, step taken)."""
+    S = ctx.state_dtype
+    t = ctypes.c_double()
+    dt = ctypes.c_double()
+    ctx._call(lib().es_step(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), float(t_end), ctypes.byref(t),
+                            ctypes.byref(dt)))
+    return t.value, dt.value
 
 
 def es_set_time(ctx, t):

@@ -17,7 +17,7 @@ def test_library_exports_header_symbols():
     path = build.build()
     lib = ctypes.CDLL(path)
     names = _declared("es_vdw.h")
-    assert "es_step" not in names and "es_steps" in names
+    assert "es_step" in names and "es_steps" in names
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
 

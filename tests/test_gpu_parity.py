@@ -228,6 +228,22 @@ def test_design_order_1d_sine_moving_mesh_gpu():
     assert np.abs(x - x_o).max() < 1e-12
 
 
+def test_es_step_is_one_of_es_steps():
+    """es_step (one step, returning the time and the step taken) gives the bits of es_steps(1)."""
+    from paper_2407_05568_gb300 import es
+    w = _ragged_riemann()
+    ctx1, JU1, J1, x1 = gpu_setup(w)
+    ctx2, JU2, J2, x2 = gpu_setup(w)
+    es.es_set_time(ctx1, 0.0)
+    es.es_set_time(ctx2, 0.0)
+    for _ in range(2):
+        t, dt = es.es_step(ctx1, JU1, J1, x1, w["t_end"])
+        es.es_steps(ctx2, JU2, J2, x2, 1, w["t_end"])
+        assert (t, dt) == es.es_get_time(ctx2) and dt > 0.0
+    assert es.es_check(ctx1) == 0 and es.es_check(ctx2) == 0
+    assert np.array_equal(to_np(JU1), to_np(JU2)) and np.array_equal(to_np(x1), to_np(x2))
+
+
 def test_steps_stop_at_t_end():
     """Steps after t_end are no-ops; the last step is shortened to land on t_end."""
     from paper_2407_05568_gb300 import es
