@@ -4,9 +4,9 @@
 // primitive state rho, v, T of every node carries a low part so that jumps between neighbours
 // keep their digits, the two-point fluxes and MR-WENO5 run in float, and the dissipation works on
 // entropy-variable jumps from the jump decomposition of Sec. 3.1 (eq. jumpV) shared by the faces
-// of a line.  What is cheap per node stays FP64: the node fields are computed once per node in
-// double and stored as floats (with the low parts), and the metrics are the FP64 cross-form
-// metrics of es_3d.cu rounded to float at load.  The right-hand sides are accumulated over the
+// of a line.  The node fields are computed once per node in double-float arithmetic and stored
+// as floats (with the low parts), and the metrics are the FP64 cross-form metrics of es_3d.cu
+// rounded to float at load.  The right-hand sides are accumulated over the
 // three directions in float and the Shu-Osher combination is done in double-float.
 #include <cuda_runtime.h>
 
@@ -23,6 +23,8 @@ using mixed::df;
 using mixed::df_add;
 using mixed::df_add_f;
 using mixed::df_mul;
+using mixed::df_mul_f;
+using mixed::df_recip;
 using mixed::GasF;
 using mixed::inv_log_mean_f;
 using mixed::inv_log_mean_j;
@@ -44,47 +46,51 @@ __device__ __forceinline__ size_t idx3(const Grid3& g, int i1, int i2, int i3) {
 }
 
 // ---------------------------------------------------------------- node fields
-// From the double-float state (JU: hi plane [5][N] then lo plane; J: hi then lo) in FP64, stored
-// as floats with the low parts of rho, v, T.
-__global__ void k3_nodes_f(Grid3 g, Gas G, const float* JU, const float* J, float* NF, DevStatus* st) {
-    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
-    const size_t LO = 5 * N;
-    for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
-        const double iJ = 1.0 / (double(J[id]) + double(J[N + id]));
-        double u[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) u[c] = (double(JU[c * N + id]) + double(JU[LO + c * N + id])) * iJ;
-        const double rho = u[0];
-        const double irho = 1.0 / rho;
-        const double v1 = u[1] * irho, v2 = u[2] * irho, v3 = u[3] * irho;
-        const double ke = 0.5 * (v1 * v1 + v2 * v2 + v3 * v3);
-        const double T = (u[4] * irho - ke + G.a * rho) * G.icv;
-        const float r = float(rho), Tf = float(T);
-        const float om = 1.0f - float(G.b) * r;
-        const float iom = 1.0f / om;
-        const float iT = 1.0f / Tf;
-        const float p = r * float(G.R) * Tf * iom - float(G.a) * r * r;
-        if (!(r > 0.0f) || !(om > 0.0f) || !(Tf > 0.0f) || !(p > 0.0f)) raise_error(st, ES_ERR_INADMISSIBLE, int(id));
-        NF[M_RHO * N + id] = r;
-        NF[M_RHOL * N + id] = float(rho - double(r));
-        NF[M_T * N + id] = Tf;
-        NF[M_TL * N + id] = float(T - double(Tf));
-        const double vv[3] = {v1, v2, v3};
+// From the double-float state (JU: hi plane [5][N] then lo plane; J: hi then lo) in double-float
+// arithmetic on the FP32 pipe (as the 2D mixed tile does), stored as floats with the low parts of
+// rho, v, T.
+__global__ void k3_nodes_f(Grid3 g, GasF G, const float* JU, const float* J, float* NF, DevStatus* st) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    const size_t P = size_t(N), LO = 5 * P;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const df iJ = df_recip({J[id], J[P + id]});
+        const df rho = df_mul({JU[id], JU[LO + id]}, iJ);
+        const df E = df_mul({JU[4 * P + id], JU[LO + 4 * P + id]}, iJ);
+        const df irho = df_recip(rho);
+        df m[3], v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float vh = float(vv[c]);
-            NF[(M_V1 + c) * N + id] = vh;
-            NF[(M_V1L + c) * N + id] = float(vv[c] - double(vh));
-            NF[(M_VT1 + c) * N + id] = vh * iT;
-            NF[(M_RV1 + c) * N + id] = float(u[1 + c]);
+            m[c] = df_mul({JU[(1 + c) * P + id], JU[LO + (1 + c) * P + id]}, iJ);
+            v[c] = df_mul(m[c], irho);
         }
-        NF[M_IT * N + id] = iT;
-        NF[M_OM * N + id] = om;
-        NF[M_IOM * N + id] = iom;
-        NF[M_G * N + id] = float(G.R) * iom - float(G.a) * r * iT;
-        NF[M_RT * N + id] = r * iT;
-        NF[M_V2T * N + id] = float(2.0 * ke) * iT;
-        NF[M_RP * N + id] = r / p;
+        const df ke = df_mul_f(df_add(df_add(df_mul(v[0], v[0]), df_mul(v[1], v[1])), df_mul(v[2], v[2])), 0.5f);
+        // T = (E/rho - |v|^2/2 + a rho) / cv
+        const df e = df_add(df_mul(E, irho), {-ke.hi, -ke.lo});
+        const df Td = df_mul_f(df_add(e, df_mul_f(rho, G.a)), G.icv);
+        const float r = rho.hi, Tf = Td.hi;
+        const float om = 1.0f - G.b * r;
+        const float iom = 1.0f / om;
+        const float iT = 1.0f / Tf;
+        const float p = r * G.R * Tf * iom - G.a * r * r;
+        if (!(r > 0.0f) || !(om > 0.0f) || !(Tf > 0.0f) || !(p > 0.0f)) raise_error(st, ES_ERR_INADMISSIBLE, id);
+        NF[M_RHO * P + id] = r;
+        NF[M_RHOL * P + id] = rho.lo;
+        NF[M_T * P + id] = Tf;
+        NF[M_TL * P + id] = Td.lo;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            NF[(M_V1 + c) * P + id] = v[c].hi;
+            NF[(M_V1L + c) * P + id] = v[c].lo;
+            NF[(M_VT1 + c) * P + id] = v[c].hi * iT;
+            NF[(M_RV1 + c) * P + id] = m[c].hi;
+        }
+        NF[M_IT * P + id] = iT;
+        NF[M_OM * P + id] = om;
+        NF[M_IOM * P + id] = iom;
+        NF[M_G * P + id] = G.R * iom - G.a * r * iT;
+        NF[M_RT * P + id] = r * iT;
+        NF[M_V2T * P + id] = 2.0f * ke.hi * iT;
+        NF[M_RP * P + id] = r / p;
     }
 }
 
@@ -907,7 +913,7 @@ static WenoF wenof(const Weno& w) {
 }
 
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s) {
-    k3_nodes_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)JU, (const float*)J, (float*)d->NF, st);
+    k3_nodes_f<<<d->grid, 256, 0, s>>>(d->g, gasf(d->gas), (const float*)JU, (const float*)J, (float*)d->NF, st);
     return 1;
 }
 
