@@ -347,9 +347,9 @@ __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double
 // Sweep k of the iteration.  Sweep k >= 1 reads buf[(pick + k - 1) % 2] and writes
 // buf[(pick + k) % 2]; sweep 0 reads `first` (x_n or the warm start) and writes buf[dst0].  Once
 // the iteration has converged (d->conv) the remaining sweeps return at once.  With `check`, the
-// grid-wide max change goes to red[slot]; if `judge`, the last block to finish compares it with eps.
+// grid-wide max change goes to red[slot]; if `decide`, the last block to finish compares it with eps.
 __global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
-                         int dst0, DevScalars* d, int check, int slot, int judge, double eps) {
+                         int dst0, DevScalars* d, int check, int slot, int decide, double eps) {
     if (d->conv) return;
     const double* xin;
     double* xout;
@@ -369,7 +369,7 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* first,
             __threadfence();
             const unsigned int ticket = atomicAdd(&d->done, 1u);
             if (ticket == gridDim.x - 1) {                 // every block's maximum is in
-                if (judge) {
+                if (decide) {
                     const double c = __longlong_as_double((long long)atomicAdd(&d->red[slot], 0ULL));
                     if (c < eps) d->conv = 1;
                     d->red[slot] = 0ULL;
