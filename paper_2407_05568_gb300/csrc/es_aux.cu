@@ -382,7 +382,7 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* first,
 }
 
 // The body of a graph while-loop over the sweeps with a tolerance: sweep k = d->sweeps (the
-// same buffers as k_jacobi), and the last block to finish judges the change, counts the sweep
+// same buffers as k_jacobi), and the last block to finish tests the change, counts the sweep
 // and sets the loop's condition: another sweep while not converged and fewer than mu sweeps.
 __global__ void k_jacobi_loop(GridParams g, const double* omega, const double* xn, double* xa, double* xb,
                               DevScalars* d, double eps, int mu, cudaGraphConditionalHandle h) {
