@@ -495,7 +495,7 @@ def direction_fluxes(sch, U_pad, n, xt, V_pad):
     # a plain jump within round-off of the terms that form W_i and W_{i+1}
     # (sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|)) is round-off of a zero jump: sign 0; for a
     # tangential wave the velocity's round-off follows the flow's velocity scale |v_t| + c, so its
-    # v_t entry counts as |v_t| + c (a zero tangential velocity is otherwise judged by its own noise)
+    # v_t entry counts as |v_t| + c (a zero tangential velocity is otherwise measured against its own noise)
     aTV = np.abs(TV[2]) + np.abs(TV[3])
     scale = np.einsum("ab...,a...->b...", np.abs(R), aTV)
     for m in range(2, d + 1):

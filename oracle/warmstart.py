@@ -2,7 +2,7 @@
 
 The Jacobi iteration of Sec. 4 solves the discretised mesh equation with the
 monitor omega frozen at the current mesh x^n.  A warm start x_s changes only
-where the iteration starts; this module states how a start is judged and
+where the iteration starts; this module states how a start is assessed and
 continued, and what features a network sees:
 
   * features: ln(omega) (omega after the filter passes), G/(1 + |G|) with the
