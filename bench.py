@@ -49,6 +49,8 @@ def parse():
                     help="skip the default matched-error comparison (1D sine 50..200, vortex 64^2..128^2, both forms)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="also run the precision-form sweep: 2D sine 1024^2 and the vortex 64^2..1024^2, both forms")
+    ap.add_argument("--mach-reflection", action="store_true",
+                    help="also run Example 5.4's Mach reflection (P1, D1) to its final time: MM, MM1, UM, FP64")
     ap.add_argument("--learned", action="store_true",
                     help="also train and evaluate the learned warm start (512^2, about 3 minutes)")
     ap.add_argument("--nn-inference", type=int, default=0,
@@ -494,6 +496,29 @@ def measure_precision_sweep(args, dev, cases=None):
     return {"runs": out, "matched_error": matched}
 
 
+# Table 5.3: the paper's CPU times (4 Xeon E5-2697A v4 cores) of Example 5.4, in seconds
+TABLE_5_3 = {"P1": {"MM": 233, "MM1": 199, "UM": 37, "UM600": 657}, "D1": {"MM": 240, "MM1": 217, "UM": 47, "UM600": 789}}
+
+
+def measure_mach(args, dev):
+    """Example 5.4's Mach reflection (one reading of its geometry, see workloads.mach_reflection), FP64:
+    MM, MM1 and UM on 200 x 100 and UM on 600 x 300, each advanced to its final time through es_steps;
+    time to solution beside the paper's CPU times (context: other hardware, and for P1 another final
+    time)."""
+    from paper_2407_05568_gb300 import workloads as wl
+    out = {}
+    for case in ("P1", "D1"):
+        rows = {}
+        for variant, (n1, n2) in (("MM", (200, 100)), ("MM1", (200, 100)), ("UM", (200, 100)), ("UM600", (600, 300))):
+            w = wl.mach_reflection(case, n1, n2, "UM" if variant == "UM600" else variant)
+            _, steps, ms, tile = run_to_end(w, "fp64", dev)
+            rows[variant] = {"grid": f"{n1}x{n2}", "steps": steps, "time_to_solution_ms": ms,
+                             "cell_updates_per_s": n1 * n2 * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None,
+                             "paper_cpu_s": TABLE_5_3[case][variant]}
+        out[case] = {"t_end": float(wl.mach_reflection(case, 8, 8, "UM")["t_end"]), "runs": rows}
+    return out
+
+
 def measure_learned(args, dev):
     """The learned warm start on the 2D vdW Riemann problem: snapshots of plain runs (Jacobi to
     max change < 0.02 cells, at most 300 sweeps), training, and the plain against the
@@ -601,6 +626,7 @@ def run_gpu(args):
     if sweep_res is None and not args.no_matched_error and rank == 0:
         quick = measure_precision_sweep(args, dev, QUICK_SWEEP)
     nn_res = measure_nn_inference(args.nn_inference, dev) if args.nn_inference > 0 and rank == 0 else None
+    mach_res = measure_mach(args, dev) if args.mach_reflection and rank == 0 else None
     if rank == 0:
         m = main_form
         line = {"metric": METRIC, "value": m["value"], "unit": "cell-updates/s", "n_gpus": world,
@@ -638,6 +664,8 @@ def run_gpu(args):
                                                "ideal-gas isentropic vortex 64^2/128^2 to t = 1, both forms")
         if nn_res is not None:
             line["nn_inference"] = nn_res
+        if mach_res is not None:
+            line["mach_reflection"] = mach_res
         if not args.no_cpu_baseline:
             sec, k = time_oracle(workload(args.n), 24)
             line["cpu_baseline"] = {"value": nodes * 3 * k / sec, "unit": "cell-updates/s", "cores": cpu_cores(),

@@ -43,6 +43,14 @@ def _pair_ok(s1, s2):
     Tm = 0.5 * (_recipe_temperature(s1[0], s1[-1]) + _recipe_temperature(s2[0], s2[-1]))
     return 4.0 * Tm - rm * (3.0 - rm) ** 2 > 0.0
 
+# Table 5.2 (Example 5.4, Mach reflection): gamma, rho_l, v1_l, v2_l, p_l, rho_r, v1_r, v2_r, p_r in the
+# paper's reduced units, and the incidence angle theta (degrees) of each case
+TABLE_5_2 = {
+    "P1": (1.4, 0.033, 5.016, 0.0, 3.001, 0.0156, 0.0, 0.0, 1.0),
+    "D1": (1.0125, 0.629, -0.135, 0.0, 0.983, 0.879, 0.0, 0.0, 1.09),
+}
+MACH_THETA = {"P1": 20.0, "D1": 30.0}
+
 
 def uniform_nodes(n, lo, hi, periodic):
     """Node coordinates and spacing: periodic -> n nodes on [lo, hi); else n nodes on [lo, hi]."""
@@ -161,6 +169,34 @@ def riemann_1d(name="RP1", n=100, moving=True, t_end=None, cfl=0.4):
                 moving=moving,
                 mesh=dict(monitor="vdw", alphas=alphas, kappa=2, filter_passes=5,
                           sweeps=10, eps=0.0))
+
+
+def mach_reflection(case="P1", n1=200, n2=100, variant="MM", t_end=None, cfl=0.4, foot=None):
+    """Example 5.4's Mach reflection on [0,1] x [0,0.5] as one reading of an underspecified setup: a planar
+    shock whose normal n = (cos theta, -sin theta) points right and down towards the wall y = 0.  Behind
+    it, (x - x_f) cos theta - y sin theta < 0, is Table 5.2's left state moving along n with the table's
+    v_1 as its normal velocity (times sqrt(8/3): the paper's reduced units to the general ones); ahead is
+    the right state at rest.  Wall at y = 0 (a mirrored end), outflow elsewhere.  variant: "MM" (monitor
+    with rho and the Laplacian of G, kappa = 1, alpha = (1200, 500)), "MM1" (alpha_2 = 0) or "UM" (fixed
+    mesh).  Default foot x_f and final time: D1 0.4 and the paper's t = 0.06 (0.0367 in general units);
+    P1 0.1 and 0.04, before the foot leaves the domain."""
+    gam, rl, vl, _, pl, rr, vr, _, pr = TABLE_5_2[case]
+    th = np.radians(MACH_THETA[case])
+    gas = dict(UNITS_A, cv=UNITS_A["R"] / (gam - 1.0))
+    x1, d1 = uniform_nodes(n1, 0.0, 1.0, False)
+    x2, d2 = uniform_nodes(n2, 0.0, 0.5, False)
+    X, Y = np.meshgrid(x1, x2)
+    xf = (0.1 if case == "P1" else 0.4) if foot is None else foot
+    behind = (X - xf) * np.cos(th) - Y * np.sin(th) < 0.0
+    vn = np.sqrt(8.0 / 3.0) * np.where(behind, vl, vr)
+    w = dict(gas=gas, dim=2, n=(n2, n1), dxi=(d1, d2), bc=("outflow", "symmetry_lo"), period=(1.0, 0.5),
+             x=np.stack([X, Y]), rho=np.where(behind, rl, rr), v=np.stack([vn * np.cos(th), -vn * np.sin(th)]),
+             p=np.where(behind, pl, pr), cfl=cfl, moving=variant != "UM",
+             t_end=t_end if t_end is not None else (0.04 if case == "P1" else 0.06 * np.sqrt(3.0 / 8.0)))
+    if variant != "UM":
+        w["mesh"] = dict(monitor="vdw", alphas=(1200.0, 500.0 if variant == "MM" else 0.0), kappa=1,
+                         filter_passes=5, sweeps=10, eps=0.0)
+    return w
 
 
 def mm1(w):
