@@ -361,6 +361,24 @@ def test_mixed_3d_mesh_redistribution_against_oracle(case, monitor, eps):
     assert np.abs(to_np(xdot) - xdot_o).max() <= 2e-5 * np.abs(xdot_o).max()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_run_host_3d_matches_device_path(prec):
+    """es_run_host on a 3D context (host buffers, copies inside) gives the device path's bits, both forms."""
+    from paper_2407_05568_gb300 import es
+    w = _moving(_mixed_case("wavy_periodic_smooth"), "smooth")
+    ctx, JU, J, xt = gpu_setup(w, precision=prec)
+    hJU, hJ, hx = JU.cpu().numpy().copy(), J.cpu().numpy().copy(), xt.cpu().numpy().copy()
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, 2, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    ctx2, _, _, _ = gpu_setup(w, precision=prec)
+    es.es_set_time(ctx2, 0.0)
+    es.es_run_host(ctx2, hJU, hJ, hx, 2, w["t_end"])
+    assert es.es_check(ctx2) == 0, es.es_last_error(ctx2)
+    assert np.array_equal(hJU, JU.cpu().numpy()) and np.array_equal(hJ, J.cpu().numpy())
+    assert np.array_equal(hx, xt.cpu().numpy())
+
+
 def test_mixed_3d_sine_to_final_time_against_fp64():
     """The 3D sine wave (Example 5.6 setup, fixed mesh) at 40^3 to t = 0.05: the mixed form stays within
     1e-5 (relative L1) of the FP64 path, whose error against the exact solution it matches."""
