@@ -20,8 +20,9 @@ Readings of points the paper leaves open (each listed in the design notes):
     dissipation are arithmetic means of the two neighbouring node values;
   * the rotation angle theta is taken with the quadrant of (n_1, n_2), i.e.
     cos(theta) = n_1/L, sin(theta) = n_2/L; in 3D theta = atan2(n_2, n_1)
-    (0 when n_1 = n_2 = 0) and phi = atan2(n_3, sqrt(n_1^2 + n_2^2)), so the
-    first row of T is n/L;
+    (0 when sqrt(n_1^2 + n_2^2) <= 1e-12 L, where (n_1, n_2) is the rounding of
+    metrics that vanish exactly) and phi = atan2(n_3, sqrt(n_1^2 + n_2^2)), so
+    the first row of T is n/L;
   * the sign switch Y compares [[W]]^WENO at face i+1/2 with the plain jump
     W_{i+1} - W_i at the same face; a plain jump no larger than sign_tol
     (1e-12) times the size of the terms that form it, sum_a |R_am|
@@ -318,13 +319,14 @@ def rotate(vec, c, s, inverse=False):
 
 def frame_3d(nf):
     """Rows of the momentum block of T in 3D (Sec. 3.3): with theta = atan2(n_2, n_1) and
-    phi = atan2(n_3, sqrt(n_1^2 + n_2^2)) (theta = 0 when n_1 = n_2 = 0),
+    phi = atan2(n_3, sqrt(n_1^2 + n_2^2)) (theta = 0 when sqrt(n_1^2 + n_2^2) <= 1e-12 |n|: at that
+    size (n_1, n_2) is the rounding of metrics that vanish exactly, and its direction is noise),
       e_n  = ( cos phi cos theta,  cos phi sin theta, sin phi) = n/L,
       e_t1 = (-sin theta,          cos theta,         0),
       e_t2 = (-sin phi cos theta, -sin phi sin theta, cos phi)."""
     L = np.sqrt(np.sum(nf**2, axis=0))
     r12 = np.sqrt(nf[0] ** 2 + nf[1] ** 2)
-    flat = r12 == 0.0
+    flat = r12 <= 1e-12 * L
     safe = np.where(flat, 1.0, r12)
     ct = np.where(flat, 1.0, nf[0] / safe)
     st = np.where(flat, 0.0, nf[1] / safe)

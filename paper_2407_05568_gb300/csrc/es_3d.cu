@@ -314,7 +314,8 @@ __device__ __forceinline__ void pair_flux3(const double* S, int NB, int l, int r
 }
 
 // -1/2 Lambda T^{-1} R Y [[W]]^WENO at the face between pencil nodes l and l+1 (Sec. 3.3,
-// eq. HOstable) with the 3D rotation: theta = atan2(n_2, n_1) (0 when n_1 = n_2 = 0),
+// eq. HOstable) with the 3D rotation: theta = atan2(n_2, n_1) (0 when |(n_1, n_2)| <= 1e-12 |n|, the
+// rounding of metrics that vanish exactly),
 // phi = atan2(n_3, sqrt(n_1^2 + n_2^2)), so the rows of T's momentum block are
 // e_n = n/L, e_t1 = (-sin theta, cos theta, 0), e_t2 = (-sin phi cos theta, -sin phi sin theta, cos phi);
 // R's tangential columns are (0, 0, 1, 0, v_t1) and (0, 0, 0, 1, v_t2), scaled by sqrt(rho T).
@@ -339,7 +340,7 @@ __device__ __forceinline__ void face_dissipation3(const double* S, int NB, int l
     const double L = sqrt(nx * nx + ny * ny + nz * nz);
     const double r12 = sqrt(nx * nx + ny * ny);
     double ct = 1.0, sn = 0.0;
-    if (r12 > 0.0) {
+    if (r12 > 1e-12 * L) {
         const double ir = rcp_nr(r12);
         ct = nx * ir;
         sn = ny * ir;

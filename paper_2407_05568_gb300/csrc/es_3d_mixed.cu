@@ -186,7 +186,7 @@ __device__ __forceinline__ void face_dissipation3_f(const float* S, int NB, int 
     const float L = sqrtf(nx * nx + ny * ny + nz * nz);
     const float r12 = sqrtf(nx * nx + ny * ny);
     float ct = 1.0f, sn = 0.0f;
-    if (r12 > 0.0f) {
+    if (r12 > 1e-12f * L) {                  // below: the rounding of metrics that vanish exactly
         const float ir = 1.0f / r12;
         ct = nx * ir;
         sn = ny * ir;

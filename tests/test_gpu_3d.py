@@ -379,6 +379,23 @@ def test_run_host_3d_matches_device_path(prec):
     assert np.array_equal(hx, xt.cpu().numpy())
 
 
+@pytest.mark.parametrize("periodic,prec", [(True, "fp64"), (False, "fp64"), (True, "mixed"), (False, "mixed")])
+def test_smallest_3d_mesh_against_oracle(periodic, prec):
+    """The smallest mesh a 3D context accepts (8 nodes in every direction: the 3-node halos and the
+    pencils' ghosts wrap or reflect across most of the mesh): one moving-mesh step against the oracle."""
+    from paper_2407_05568_gb300 import es
+    w = _moving(_box(8, 8, 8, periodic, amp=0.01 if periodic else 0.0, seed=21), "vdw")
+    sch, mc, JU_o, J_o, x_o = oracle_setup(w)
+    JU_o, J_o, x_o, t, _ = stepper.step(sch, mc, JU_o, J_o, x_o, 0.0, w["t_end"], w["cfl"])
+    ctx, JU, J, xt = gpu_setup(w, precision=prec)
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, 1, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    bound = 1e-12 if prec == "fp64" else 2e-6
+    assert rel_l1(to_np(JU), JU_o) < bound, rel_l1(to_np(JU), JU_o)
+    assert np.abs(to_np(xt) - x_o).max() < (1e-12 if prec == "fp64" else 1e-6)
+
+
 def test_mixed_3d_sine_to_final_time_against_fp64():
     """The 3D sine wave (Example 5.6 setup, fixed mesh) at 40^3 to t = 0.05: the mixed form stays within
     1e-5 (relative L1) of the FP64 path, whose error against the exact solution it matches."""

@@ -378,3 +378,39 @@ def test_sign_switch_ignores_velocity_noise_where_v_t_is_zero():
     dU, _ = op.rhs(sch, JU1, J1, x, np.zeros_like(x))
     dUn, _ = op.rhs(sch, JUn, J1, x, np.zeros_like(x))
     assert np.abs(dUn - dU).max() < 1e-12 * np.abs(dU).max()
+
+
+def test_frame_angle_ignores_rounding_of_vanishing_metrics():
+    """Reading 19: theta = 0 when |(n_1, n_2)| <= 1e-12 |n|.  On an outflow box whose boundary planes
+    stay Cartesian (the mesh velocity vanishes on the boundary nodes, as the mesh solve makes it) the
+    x_3-faces' (n_1, n_2) are the rounding of exact zeros; with theta taken from that rounding the
+    tangential frame, and through the per-field sign switch the dissipation, followed the noise (1e-5
+    relative changes of the right-hand side under 1-ulp changes of the mesh).  Now the operator is as
+    insensitive to such changes as on any other mesh."""
+    from oracle import operator as op
+    L, fr = op.frame_3d(np.array([[3e-15, 0.0], [-2e-15, 1e-10], [1.0, 1.0]]))
+    assert np.array_equal(fr[1][:, 0], [0.0, 1.0, 0.0])            # e_t1 with theta = 0
+    assert abs(fr[1][0, 1] + 1.0) < 1e-12                             # a 1e-10 tilt keeps its angle (pi/2)
+    X = [wl.uniform_nodes(10, 0.0, 1.0, False)[0]] * 3
+    Z, Y, Xg = np.meshgrid(X[2], X[1], X[0], indexing="ij")
+    rng = np.random.default_rng(21)
+    rho = 0.6 + 0.1 * rng.random(Xg.shape)
+    p = 1.0 + 0.1 * rng.random(Xg.shape)
+    v = 0.1 * rng.standard_normal((3,) + Xg.shape)
+    g = thermo.gas_units_a()
+    d = 1.0 / 9.0
+    sch = op.Scheme(gas=g, dim=3, bc=("outflow",) * 3, dxi=(d, d, d), period=(1.0, 1.0, 1.0))
+    x = np.stack([Xg, Y, Z])
+    tp = 2 * np.pi
+    xd = 0.05 * np.stack([np.sin(tp * (Xg + Y)), np.cos(tp * (Y - Z)), np.sin(tp * (Z + Xg))])
+    for ax in (1, 2, 3):
+        for e in (0, -1):
+            idx = [slice(None)] * 4
+            idx[ax] = e
+            xd[tuple(idx)] = 0.0
+    xs = x + 1e-3 * xd
+    J = op.node_jacobian(sch, xs)
+    JU = thermo.prim_to_cons(g, rho, v, p) * J
+    d0, _ = op.rhs(sch, JU, J, xs, xd)
+    d1, _ = op.rhs(sch, JU, J, xs * (1.0 + 2e-16 * rng.standard_normal(xs.shape)), xd)
+    assert np.abs(d1 - d0).sum() < 1e-12 * np.abs(d0).sum()
