@@ -178,7 +178,8 @@ def test_mesh_redistribution_parity_3d(case, monitor):
 
 
 @pytest.mark.parametrize("case,monitor,nsteps", [("shock_ragged", "vdw", 2), ("wavy_periodic_smooth", "smooth", 2),
-                                                 ("wavy_periodic_rough", None, 1), ("walls_rough", "vdw", 1)])
+                                                 ("wavy_periodic_rough", None, 1), ("walls_rough", "vdw", 1),
+                                                 ("outflow_rough", "vdw", 2)])
 def test_step_parity_3d(case, monitor, nsteps):
     """Full steps through es_steps (CFL, mesh redistribution, three stages; a CUDA graph)."""
     from paper_2407_05568_gb300 import es
