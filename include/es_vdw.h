@@ -155,8 +155,22 @@ int es_rk_stage(es_ctx* ctx, int stage, double dt,
                 const void* JUn, const void* Jn, const void* JUs, const void* Js,
                 const double* xn, const double* xdot, void* JU_out, void* J_out);
 
-/* Time step of eq. cfl from the current mesh with zero mesh velocity; writes the host double. */
-int es_cfl_dt(es_ctx* ctx, const void* JU, const void* J, const double* x, double* dt_host);
+/* Time step of eq. cfl (Sec. 5): CFL / max_i sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k), the
+ * spectral radius of the xi_k flux Jacobian with J xi_{k,t} = -xdot . n_k (eq. VCLCoeff).  xdot is the
+ * mesh velocity [dim][n...] (device, double) or NULL for a mesh at rest.  Synchronises the context's
+ * stream and writes the host double. */
+int es_cfl_dt(es_ctx* ctx, const void* JU, const void* J, const double* x, const double* xdot, double* dt_host);
+
+/* Entropy production check in FP64 (Sec. 2-3): the rate of the total entropy sum_i J_i eta(U_i) dV,
+ *   out_host[0] = dV sum_i (V_i . dJU_i - phi_i dJ_i),   out_host[1] = dV sum_i |V_i . dJU_i - phi_i dJ_i|,
+ * where (dJU, dJ) are right-hand sides of eq. semi_U / semi_J at the state (JU, J) (from es_rhs),
+ * eta = -rho s, V = eta'(U) the entropy variables, phi = p/T the potential and dV = prod_k dxi_k.  The
+ * EC scheme (dissipation = 0) conserves it on periodic data (eq. ECCondition_comp and the telescoping of
+ * the EC fluxes), so out_host[0] is round-off of out_host[1]; the ES flux of eq. HOstable only lowers it.
+ * Arrays have the state's precision and layout (the mixed form's (hi, lo) planes are read as their sum);
+ * the arithmetic is FP64 with a compensated sum in a fixed order, so repeated calls give the same bits.
+ * Synchronises the context's stream.  Errors: ES_ERR_ARG for a null pointer. */
+int es_entropy_rate(es_ctx* ctx, const void* JU, const void* J, const void* dJU, const void* dJ, double* out_host);
 
 /* Mesh redistribution of Sec. 4 for a step of size dt: monitor (with G) ->
  * filter passes -> Jacobi sweeps from xn -> limiter Delta_gamma -> mesh velocity
@@ -169,7 +183,11 @@ int es_mesh_redistribute(es_ctx* ctx, const void* JU, const void* J, const doubl
 
 /* Advance the caller's state (JU, J, x) in place by nsteps full steps
  * (Delta t from eq. cfl or dt_fixed, clipped to t_end; mesh redistribution when
- * moving; three RK stages; x += dt xdot).  The time t lives on the device:
+ * moving; three RK stages; x += dt xdot).  On a moving mesh without dt_fixed,
+ * eq. cfl's spectral radius holds the step's own mesh velocity (Sec. 4 defines
+ * xdot^n = Delta_gamma dx / Delta t_n): Delta t^(0) with the mesh at rest gives
+ * xdot, and the step is Delta t_n = min(Delta t^(0), eq. cfl with that xdot), so
+ * the mesh moves xdot Delta t_n, within Delta_gamma's bounds.  The time t lives on the device:
  * es_set_time / es_get_time move it.  Steps after t reaches t_end are no-ops.
  * Launches a CUDA graph per step once the first step has been captured. */
 int es_steps(es_ctx* ctx, void* JU, void* J, double* x, int nsteps, double t_end);

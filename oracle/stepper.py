@@ -5,8 +5,13 @@ Gottlieb, Shu & Tadmor (cited in Sec. 1 and Sec. 5) integrates (JU, J);
 Sec. 4 moves the mesh once per step with velocity xdot = Delta_gamma dx / Delta t_n.
 
 Readings of points the paper leaves open:
-  * eq. cfl needs the mesh velocity, which itself needs Delta t_n; Delta t_n is
-    taken from the current mesh with xdot = 0, and xdot follows from it;
+  * eq. cfl takes the spectral radius at t_n, which contains the mesh velocity
+    xdot^n = Delta_gamma dx / Delta t_n (Sec. 4), so the two define each other.
+    Delta t^(0) from the current mesh with xdot = 0 gives xdot; then
+    Delta t_n = min(Delta t^(0), CFL / max_i sum_k rho_{i,k}(xdot) / dxi_k) with
+    that xdot.  The mesh moves by xdot Delta t_n = Delta_gamma' dx with
+    Delta_gamma' = Delta_gamma Delta t_n / Delta t^(0) <= Delta_gamma, which still
+    meets the bounds that define Delta_gamma, so eq. cfl and those bounds both hold;
   * the mesh moves with constant xdot over the step; RK stage s evaluates the
     operator on x^(s) = x^n + c_s Delta t xdot with c = (0, 1, 1/2) (the
     stage times of SSP-RK3) and recomputes the metrics there, which keeps the
@@ -40,20 +45,21 @@ class MeshControl:
     eps: float = 0.0
 
 
-def cfl_dt(sch, JU, J, x, cfl):
-    """eq. cfl: Delta t = CFL / max_i sum_k rho_{i,k} / dxi_k with the spectral radius
-    rho_{i,k} = (|J xi_{k,t} + n_k . v| + L_k c) / J, taken here with xdot = 0."""
+def cfl_dt(sch, JU, J, x, cfl, xdot=None):
+    """eq. cfl: Delta t = CFL / max_i sum_k rho_{i,k} / dxi_k with the spectral radius of the
+    xi_k-direction flux Jacobian, rho_{i,k} = (|J xi_{k,t} + n_k . v| + L_k c) / J, where
+    J xi_{k,t} = -xdot . n_k (eq. VCLCoeff); xdot = None is a mesh at rest."""
     g = sch.gas
     U = JU / J
     rho, v, T, p = thermo.cons_to_prim(g, U)
     c = np.sqrt(thermo.sound_speed2(g, rho, T))
     tot = np.zeros_like(J)
-    zero = np.zeros_like(x)
+    xd = np.zeros_like(x) if xdot is None else xdot
     for k in range(sch.dim):
-        n, _ = direction_metrics(sch, x, zero, k, 0)
+        n, xt = direction_metrics(sch, x, xd, k, 0)
         L = np.sqrt(np.sum(n**2, axis=0))
         vn = np.sum(n * v, axis=0)
-        tot += (np.abs(vn) + L * c) / J / sch.dxi[k]
+        tot += (np.abs(xt + vn) + L * c) / J / sch.dxi[k]
     return cfl / float(np.max(tot))
 
 
@@ -93,6 +99,8 @@ def step(sch, mc, JU, J, x, t, t_end, cfl, dt_fixed=None):
     dt = min(dt, t_end - t)
     if mc.moving:
         xdot, sweeps, gam = redistribute(sch, mc, JU, J, x, dt)
+        if dt_fixed is None:
+            dt = min(dt, cfl_dt(sch, JU, J, x, cfl, xdot))
     else:
         xdot, sweeps, gam = np.zeros_like(x), 0, 0.0
     JU1, J1 = rk_stage(sch, 0, dt, JU, J, JU, J, x, xdot)

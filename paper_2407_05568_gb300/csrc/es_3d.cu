@@ -670,9 +670,11 @@ static cudaError_t dir_launch(const Dir3Params& P, int shape, cudaStream_t s) {
     }
 }
 
-// ================================================================ CFL (eq. cfl), zero mesh velocity
+// ================================================================ CFL (eq. cfl)
+// max_i sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k), J xi_{k,t} = -xdot . n_k (eq. VCLCoeff), from the
+// node fields and metrics of x^n; xdot = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
 __global__ void k3_cfl(Grid3 g, Gas G, const double* NF, const double* J, const double* NK0, const double* NK1,
-                       const double* NK2, DevScalars* d) {
+                       const double* NK2, const double* xdot, int slot, DevScalars* d) {
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     const size_t M[3] = {size_t(g.n[0] + 6) * g.n[1] * g.n[2], size_t(g.n[0]) * (g.n[1] + 6) * g.n[2],
                          size_t(g.n[0]) * g.n[1] * (g.n[2] + 6)};
@@ -685,19 +687,21 @@ __global__ void k3_cfl(Grid3 g, Gas G, const double* NF, const double* J, const 
         const double c2 = (1.0 + G.delta) * G.R * T * (iom * iom) - 2.0 * G.a * rho;
         const double c = sqrt(fmax(c2, 0.0));
         const double iJ = rcp_nr(J[id]);
+        const double xd[3] = {xdot ? xdot[id] : 0.0, xdot ? xdot[N + id] : 0.0, xdot ? xdot[2 * N + id] : 0.0};
         double tot = 0.0;
         for (int k = 0; k < 3; ++k) {
             const int m1 = g.n[0] + (k == 0 ? 6 : 0), m2 = g.n[1] + (k == 1 ? 6 : 0);
             const size_t mi = (size_t(i3 + (k == 2 ? 3 : 0)) * m2 + i2 + (k == 1 ? 3 : 0)) * m1 + i1 + (k == 0 ? 3 : 0);
             const double n0 = NK[k][mi], n1 = NK[k][M[k] + mi], n2 = NK[k][2 * M[k] + mi];
-            tot += (fabs(n0 * v[0] + n1 * v[1] + n2 * v[2]) + sqrt(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
+            const double xt = -(xd[0] * n0 + xd[1] * n1 + xd[2] * n2);
+            tot += (fabs(xt + (n0 * v[0] + n1 * v[1] + n2 * v[2])) + sqrt(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
                    g.inv_dxi[k];
         }
         if (!(c2 > 0.0)) tot = 1e300;
         mx = fmax(mx, tot);
     }
     mx = block_max(mx);
-    if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_CFL], mx);
+    if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], mx);
 }
 
 // ================================================================ init
@@ -994,11 +998,25 @@ int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* 
     int n = enqueue_metrics(d, x, nullptr, 0.0, nullptr, 0.0, s);
     if (d->mixed) {
         n += d3f_nodes(d, JU, J, &dv->status, s);
-        n += d3f_cfl(d, J, dv, s);
+        n += d3f_cfl(d, J, nullptr, RED_CFL, dv, s);
     } else {
         k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const double*)JU, (const double*)J, d->NF, &dv->status);
-        k3_cfl<<<d->grid, 256, 0, s>>>(d->g, d->gas, d->NF, (const double*)J, d->NK[0], d->NK[1], d->NK[2], dv);
+        k3_cfl<<<d->grid, 256, 0, s>>>(d->g, d->gas, d->NF, (const double*)J, d->NK[0], d->NK[1], d->NK[2], nullptr,
+                                       RED_CFL, dv);
         n += 2;
+    }
+    *err = cudaGetLastError();
+    return *err == cudaSuccess ? n : -1;
+}
+
+int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cudaStream_t s, cudaError_t* err) {
+    int n;
+    if (d->mixed) {
+        n = d3f_cfl(d, J, xdot, RED_CFL2, dv, s);
+    } else {
+        k3_cfl<<<d->grid, 256, 0, s>>>(d->g, d->gas, d->NF, (const double*)J, d->NK[0], d->NK[1], d->NK[2], xdot,
+                                       RED_CFL2, dv);
+        n = 1;
     }
     *err = cudaGetLastError();
     return *err == cudaSuccess ? n : -1;

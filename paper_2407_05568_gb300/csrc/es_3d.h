@@ -64,10 +64,12 @@ int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* 
            cudaError_t* err);
 int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
             cudaStream_t s, cudaError_t* err);
+// eq. cfl with the step's mesh velocity (into RED_CFL2), from the node fields and metrics d3_cfl left for x^n
+int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cudaStream_t s, cudaError_t* err);
 // the mixed form's kernels (es_3d_mixed.cu)
 cudaError_t d3f_prepare();
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s);
-int d3f_cfl(Ctx3* d, const void* J, DevScalars* dv, cudaStream_t s);
+int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s);
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);
 int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
 int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,

@@ -552,9 +552,10 @@ static cudaError_t launch_dir(const Dir3FParams& P, int shape, cudaStream_t s) {
     }
 }
 
-// CFL (eq. cfl) from the float node fields and the FP64 metrics, zero mesh velocity
+// CFL (eq. cfl) from the float node fields and the FP64 metrics: J xi_{k,t} = -xdot . n_k, xdot = nullptr
+// is a mesh at rest; the maximum goes to d->red[slot]
 __global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const double* NK0, const double* NK1,
-                         const double* NK2, DevScalars* d) {
+                         const double* NK2, const double* xdot, int slot, DevScalars* d) {
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     const size_t M[3] = {size_t(g.n[0] + 6) * g.n[1] * g.n[2], size_t(g.n[0]) * (g.n[1] + 6) * g.n[2],
                          size_t(g.n[0]) * g.n[1] * (g.n[2] + 6)};
@@ -568,19 +569,21 @@ __global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const
         const float c2 = (1.0f + delta) * R * T * (iom * iom) - 2.0f * a * rho;
         const float c = sqrtf(fmaxf(c2, 0.0f));
         const float iJ = 1.0f / J[id];
+        const float vr[3] = {v[0] - (xdot ? float(xdot[id]) : 0.0f), v[1] - (xdot ? float(xdot[N + id]) : 0.0f),
+                             v[2] - (xdot ? float(xdot[2 * N + id]) : 0.0f)};      // velocity relative to the mesh
         float tot = 0.0f;
         for (int k = 0; k < 3; ++k) {
             const int m1 = g.n[0] + (k == 0 ? 6 : 0), m2 = g.n[1] + (k == 1 ? 6 : 0);
             const size_t mi = (size_t(i3 + (k == 2 ? 3 : 0)) * m2 + i2 + (k == 1 ? 3 : 0)) * m1 + i1 + (k == 0 ? 3 : 0);
             const float n0 = float(NK[k][mi]), n1 = float(NK[k][M[k] + mi]), n2 = float(NK[k][2 * M[k] + mi]);
-            tot += (fabsf(n0 * v[0] + n1 * v[1] + n2 * v[2]) + sqrtf(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
+            tot += (fabsf(n0 * vr[0] + n1 * vr[1] + n2 * vr[2]) + sqrtf(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
                    float(g.inv_dxi[k]);
         }
         if (!(c2 > 0.0f)) tot = 3.0e38f;
         mx = fmaxf(mx, tot);
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(&d->red[RED_CFL], double(mx));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(&d->red[slot], double(mx));
 }
 
 // J (FP64, from the FP64 kernel) into double-float planes
@@ -917,9 +920,9 @@ int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_
     return 1;
 }
 
-int d3f_cfl(Ctx3* d, const void* J, DevScalars* dv, cudaStream_t s) {
+int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s) {
     k3_cfl_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)d->NF, (const float*)J, d->NK[0], d->NK[1],
-                                      d->NK[2], dv);
+                                      d->NK[2], xdot, slot, dv);
     return 1;
 }
 

@@ -342,8 +342,9 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
     return ES_OK;
 }
 
-void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x) {
-    launch_cfl(c->g, c->gas, JU, J, x, c->dev, c->mixed, c->grid1d, c->s_enq);
+void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot = nullptr,
+                 int slot = RED_CFL) {
+    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq);
     count(c);
 }
 
@@ -364,6 +365,12 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
         if (n < 0) return cuda_fail(c, e, "3D mesh kernels");
         count(c, n);
         xdot = c->xdot;
+        if (!(c->p.dt_fixed > 0.0)) {          // eq. cfl with the step's mesh velocity
+            n = d3_cfl_moving(c->d3, J, xdot, c->dev, s, &e);
+            if (n < 0) return cuda_fail(c, e, "3D time-step kernels");
+            k_dt_moving<<<1, 32, 0, s>>>(c->dev, c->p.cfl);
+            count(c, n + 1);
+        }
     }
     double* S1 = (double*)c->S1;
     double* S2 = (double*)c->S2;
@@ -408,7 +415,8 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     const bool f32 = mesh_on_fp32(c);
     if (f32) {      // the displacement kernel also resets the step's reductions (k_reset's work)
         k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
-        k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, c->dev);
+        k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, nullptr, RED_CFL,
+                                c->dev);
         count(c, 2);
     } else {
         k_reset<<<1, 32, 0, s>>>(c->dev);
@@ -427,6 +435,17 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
         int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true) : enqueue_mesh(c, JU, J, x, c->xdot);
         if (rc) return rc;
         xdot = c->xdot;
+        if (!(c->p.dt_fixed > 0.0)) {          // eq. cfl with the step's mesh velocity
+            if (f32) {
+                k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, c->fxd,
+                                        RED_CFL2, c->dev);
+                count(c);
+            } else {
+                enqueue_cfl(c, JU, J, x, c->xdot, RED_CFL2);
+            }
+            k_dt_moving<<<1, 32, 0, s>>>(c->dev, c->p.cfl);
+            count(c);
+        }
     }
     StageParams P = stage_params(c);
     P.dt_dev = &c->dev->dt;
@@ -758,29 +777,47 @@ int es_rk_stage(es_ctx* c, int stage, double dt, const void* JUn, const void* Jn
     return ES_OK;
 }
 
-int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, double* dt_host) {
+int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot, double* dt_host) {
     if (!c || !JU || !J || !x || !dt_host) return fail(c, ES_ERR_ARG, "null argument");
+    const int slot = xdot ? RED_CFL2 : RED_CFL;
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
     if (c->d3) {
         cudaError_t e;
-        const int n = d3_cfl(c->d3, (const double*)JU, (const double*)J, x, c->dev, c->stream, &e);
+        int n = d3_cfl(c->d3, (const double*)JU, (const double*)J, x, c->dev, c->stream, &e);
+        if (n >= 0 && xdot) n = d3_cfl_moving(c->d3, J, xdot, c->dev, c->stream, &e);
         if (n < 0) return cuda_fail(c, e, "3D time-step kernels");
         count(c, n);
     } else if (mesh_on_fp32(c)) {
-        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, nullptr, c->fdisp, c->fxd);
+        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, xdot, c->fdisp, c->fxd);
         k_cfl_f<<<c->grid1d, 256, 0, c->stream>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J,
-                                                   c->fdisp, c->dev);
+                                                   c->fdisp, xdot ? c->fxd : nullptr, slot, c->dev);
         count(c, 2);
     } else {
-        enqueue_cfl(c, JU, J, x);
+        enqueue_cfl(c, JU, J, x, xdot, slot);
     }
     CK(cudaGetLastError(), "k_cfl");
     CK(cudaMemcpyAsync(c->hpin, c->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream), "copy");
     CK(cudaStreamSynchronize(c->stream), "sync");
     double mx;
-    memcpy(&mx, &c->hpin->red[RED_CFL], sizeof(double));
+    memcpy(&mx, &c->hpin->red[slot], sizeof(double));
     *dt_host = c->p.cfl / mx;
+    return ES_OK;
+}
+
+int es_entropy_rate(es_ctx* c, const void* JU, const void* J, const void* dJU, const void* dJ, double* out_host) {
+    if (!c || !JU || !J || !dJU || !dJ || !out_host) return fail(c, ES_ERR_ARG, "null argument");
+    double vol = 1.0;
+    for (int k = 0; k < c->p.dim; ++k) vol *= c->p.dxi[k];
+    // t0 (per-block partial sums, 3 per block <= the mesh size) and t1 (the result) are mesh-solve scratch
+    launch_entropy_rate(int(c->N), c->p.dim, c->gas, JU, J, dJU, dJ, vol, c->t0, c->t1, c->mixed, c->grid1d,
+                        c->stream);
+    count(c, 2);
+    CK(cudaGetLastError(), "entropy kernels");
+    CK(cudaMemcpyAsync(c->hpin->last_change, c->t1, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    out_host[0] = c->hpin->last_change[0];
+    out_host[1] = c->hpin->last_change[1];
     return ES_OK;
 }
 

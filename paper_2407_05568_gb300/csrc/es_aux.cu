@@ -122,9 +122,11 @@ __global__ void k_reset(DevScalars* d) {
     if (threadIdx.x == 0 && blockIdx.x == 0) reset_scalars(d);
 }
 
-// eq. cfl: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), with zero mesh velocity
+// eq. cfl: max_i sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k) with J xi_{k,t} = -xdot . n_k
+// (eq. VCLCoeff); xdot = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
 template <class TS>
-__global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const double* x, DevScalars* d) {
+__global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const double* x, const double* xdot, int slot,
+                      DevScalars* d) {
     const int N = g.n1 * g.n2;
     double m = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
@@ -141,27 +143,35 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
         const double iom = rcp_nr(om);
         const double c2 = (1.0 + G.delta) * G.R * T * (iom * iom) - 2.0 * G.a * rho;
         const double c = sqrt(fmax(c2, 0.0));
+        const double xd1 = xdot != nullptr ? xdot[id] : 0.0;
         double tot;
         if (g.dim == 1) {
-            tot = (fabs(v1) + c) * iJ * g.inv_dxi[0];
+            tot = (fabs(-xd1 + v1) + c) * iJ * g.inv_dxi[0];
         } else {
+            const double xd2 = xdot != nullptr ? xdot[N + id] : 0.0;
             const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
             const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
             const double a1 = y2, b1 = -x2;          // J dxi_1/dx
             const double a2 = -y1, b2 = x1;          // J dxi_2/dx
-            tot = (fabs(a1 * v1 + b1 * v2) + sqrt(a1 * a1 + b1 * b1) * c) * iJ * g.inv_dxi[0] +
-                  (fabs(a2 * v1 + b2 * v2) + sqrt(a2 * a2 + b2 * b2) * c) * iJ * g.inv_dxi[1];
+            const double t1 = -(xd1 * a1 + xd2 * b1), t2 = -(xd1 * a2 + xd2 * b2);     // J xi_{k,t}
+            tot = (fabs(t1 + (a1 * v1 + b1 * v2)) + sqrt(a1 * a1 + b1 * b1) * c) * iJ * g.inv_dxi[0] +
+                  (fabs(t2 + (a2 * v1 + b2 * v2)) + sqrt(a2 * a2 + b2 * b2) * c) * iJ * g.inv_dxi[1];
         }
         if (!(c2 > 0.0)) tot = 1e300;
         m = fmax(m, tot);
     }
     m = block_reduce_max(m);
-    if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_CFL], m);
+    if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], m);
 }
 
 // Delta t = CFL / max (or the fixed step), clipped to t_end; 0 once t_end is reached
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed) {
     if (threadIdx.x == 0 && blockIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
+}
+
+// Delta t_n = min(Delta t^(0), CFL / the maximum with the step's mesh velocity)
+__global__ void k_dt_moving(DevScalars* d, double cfl) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) shrink_dt_for_mesh(d, cfl);
 }
 
 __global__ void k_set_dt(DevScalars* d, double dt) {
@@ -178,6 +188,86 @@ __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalar
         d->t += dt;
         d->last_dt = dt;
     }
+}
+
+// ------------------------------------------------------------ entropy production (FP64)
+// Knuth's error-free sum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum_d(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (s, e) += (s2, e2) for compensated sums
+__device__ __forceinline__ void add_comp(double& s, double& e, double s2, double e2) {
+    double t, err;
+    two_sum_d(s, s2, t, err);
+    s = t;
+    e += e2 + err;
+}
+
+// Per node the rate of J eta (eta = -rho s): V . d(JU)/dt - phi dJ/dt, with the entropy variables
+// V = ((e + p/rho)/T - s - |v|^2/(2T), v/T, -1/T) (Sec. 2, general units) and phi = p/T.  Each block
+// writes the compensated sum of its nodes' terms and the sum of their magnitudes to part[3 b ..]; the
+// grid-stride order and the tree below are fixed, so the result does not change from run to run.
+template <class TS>
+__global__ void k_entropy_terms(int N, int dim, Gas G, const TS* JU, const TS* J, const TS* dJU, const TS* dJ,
+                                double* part) {
+    __shared__ double sh[3][256];
+    const size_t P = size_t(dim + 2) * N;
+    double s = 0.0, e = 0.0, a = 0.0;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const double Jv = ld_state(J, N, id);
+        const double rho = ld_state(JU, P, id) / Jv;
+        double v[3] = {0.0, 0.0, 0.0}, v2 = 0.0;
+        for (int k = 0; k < dim; ++k) {
+            v[k] = ld_state(JU, P, size_t(1 + k) * N + id) / Jv / rho;
+            v2 += v[k] * v[k];
+        }
+        const double E = ld_state(JU, P, size_t(dim + 1) * N + id) / Jv;
+        const double T = (E / rho - 0.5 * v2 + G.a * rho) / G.cv;
+        const double om = 1.0 - G.b * rho;
+        const double sent = G.cv * log(T) + G.R * log(om / rho);
+        const double V0 = G.cv - sent - 2.0 * G.a * rho / T + G.R / om - 0.5 * v2 / T;
+        const double p = rho * G.R * T / om - G.a * rho * rho;
+        double term = V0 * ld_state(dJU, P, id);
+        for (int k = 0; k < dim; ++k) term += v[k] / T * ld_state(dJU, P, size_t(1 + k) * N + id);
+        term += -1.0 / T * ld_state(dJU, P, size_t(dim + 1) * N + id);
+        term -= p / T * ld_state(dJ, N, id);
+        add_comp(s, e, term, 0.0);
+        a += fabs(term);
+    }
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = e;
+    sh[2][threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double s1 = sh[0][threadIdx.x], e1 = sh[1][threadIdx.x];
+            add_comp(s1, e1, sh[0][threadIdx.x + w], sh[1][threadIdx.x + w]);
+            sh[0][threadIdx.x] = s1;
+            sh[1][threadIdx.x] = e1;
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = sh[0][0];
+        part[3 * blockIdx.x + 1] = sh[1][0];
+        part[3 * blockIdx.x + 2] = sh[2][0];
+    }
+}
+
+// the blocks' partial sums in block order; out = (vol sum, vol sum of magnitudes)
+__global__ void k_entropy_sum(int nb, const double* part, double vol, double* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0, e = 0.0, a = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        add_comp(s, e, part[3 * b], part[3 * b + 1]);
+        a += part[3 * b + 2];
+    }
+    out[0] = vol * (s + e);
+    out[1] = vol * a;
 }
 
 // ------------------------------------------------------------ monitor (Sec. 4)
@@ -542,10 +632,21 @@ void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, c
     else k_prim_to_cons<double><<<grid, 256, 0, s>>>(g, G, rho, v, p, (const double*)J, (double*)JU);
 }
 
-void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x, DevScalars* d,
-                bool f32, int grid, cudaStream_t s) {
-    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, d);
-    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, d);
+void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const void* J, const void* dJU,
+                         const void* dJ, double vol, double* part, double* out, bool f32, int grid, cudaStream_t s) {
+    if (f32)
+        k_entropy_terms<float><<<grid, 256, 0, s>>>(N, dim, G, (const float*)JU, (const float*)J, (const float*)dJU,
+                                                    (const float*)dJ, part);
+    else
+        k_entropy_terms<double><<<grid, 256, 0, s>>>(N, dim, G, (const double*)JU, (const double*)J,
+                                                     (const double*)dJU, (const double*)dJ, part);
+    k_entropy_sum<<<1, 32, 0, s>>>(grid, part, vol, out);
+}
+
+void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
+                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s) {
+    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d);
+    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d);
 }
 
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,

@@ -20,7 +20,8 @@ struct MonitorParams {
     double w0, w1, w2;   // weights of the three monitor terms
 };
 
-enum { RED_CFL = 0, RED_MON0 = 1, RED_MON1 = 2, RED_MON2 = 3, RED_GAMMA = 4, RED_JAC = 5, RED_JAC2 = 6 };
+// RED_CFL: eq. cfl's maximum with the mesh at rest; RED_CFL2: the same with the step's mesh velocity
+enum { RED_CFL = 0, RED_MON0 = 1, RED_MON1 = 2, RED_MON2 = 3, RED_GAMMA = 4, RED_JAC = 5, RED_JAC2 = 6, RED_CFL2 = 7 };
 
 // Device-resident scalars of a run.
 struct DevScalars {
@@ -55,16 +56,30 @@ __device__ __forceinline__ void set_dt_from_cfl(DevScalars* d, double cfl, doubl
     d->dt = dt;
 }
 
+// eq. cfl with the step's mesh velocity (maximum in RED_CFL2): Delta t_n = min(Delta t^(0), CFL / max).
+// The mesh velocity keeps its value, so the mesh moves Delta_gamma' dx with Delta_gamma' <= Delta_gamma.
+__device__ __forceinline__ void shrink_dt_for_mesh(DevScalars* d, double cfl) {
+    const double mx = __longlong_as_double((long long)d->red[RED_CFL2]);
+    const double dt = cfl / mx;
+    if (d->dt > 0.0 && dt < d->dt) d->dt = dt;
+}
+
 // kernels templated on the state type are launched through these (f32: float state)
 void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int grid, cudaStream_t s);
 void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
                          const void* J, void* JU, bool f32, int grid, cudaStream_t s);
-void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x, DevScalars* d,
-                bool f32, int grid, cudaStream_t s);
+// xdot (nullable): the mesh velocity of eq. VCLCoeff's J xi_t; slot: RED_CFL or RED_CFL2
+void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
+                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s);
+// total entropy rate sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt) vol in FP64 with a compensated, fixed-order
+// reduction: out[0] the rate, out[1] the sum of the magnitudes of its terms (device); part holds 3 grid doubles
+void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const void* J, const void* dJU,
+                         const void* dJ, double vol, double* part, double* out, bool f32, int grid, cudaStream_t s);
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,
                        bool f32, int grid, cudaStream_t s);
 __global__ void k_reset(DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
+__global__ void k_dt_moving(DevScalars* d, double cfl);
 __global__ void k_set_dt(DevScalars* d, double dt);
 __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
 // rst (nullable): also runs k_reset's work (the first kernel of a mixed-form step)

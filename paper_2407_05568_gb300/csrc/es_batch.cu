@@ -96,30 +96,39 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
         float* db = B.work + 8 * ntot + off;
         double t = B.tprob[p];
 
+        // node i's velocity, sound speed squared (rho, T for the monitor) and 1/J from the state
+        auto node = [&](int i, float& rho, float& v, float& T, float& c2, float& iJ) {
+            iJ = 1.0f / B.J[off + i];
+            rho = B.JU[off + i] * iJ;
+            v = B.JU[ntot + off + i] * iJ / rho;
+            const float E = B.JU[2 * ntot + off + i] * iJ;
+            T = (E / rho - 0.5f * v * v + G.a * rho) * G.icv;
+            const float om = 1.0f - G.b * rho;
+            c2 = (1.0f + G.delta) * G.R * T / (om * om) - 2.0f * G.a * rho;
+        };
         for (int step = 0; step < B.nsteps; ++step) {
-            // ---- time step, eq. cfl: dt = CFL / max (|v| + c) / (J dxi)
+            // ---- time step, eq. cfl with the mesh at rest: dt = CFL / max (|v| + c) / (J dxi)
             float m = 0.0f;
             for (int i = tid; i < L; i += BT) {
-                const float iJ = 1.0f / B.J[off + i];
-                const float rho = B.JU[off + i] * iJ;
-                const float v = B.JU[ntot + off + i] * iJ / rho;
-                const float E = B.JU[2 * ntot + off + i] * iJ;
-                const float T = (E / rho - 0.5f * v * v + G.a * rho) * G.icv;
-                const float om = 1.0f - G.b * rho;
-                const float c2 = (1.0f + G.delta) * G.R * T / (om * om) - 2.0f * G.a * rho;
+                float rho, v, T, c2, iJ;
+                node(i, rho, v, T, c2, iJ);
                 const float lam = (fabsf(v) + sqrtf(fmaxf(c2, 0.0f))) * iJ * idxi;
                 m = fmaxf(m, c2 > 0.0f ? lam : 3.0e38f);
-                rhoF[i] = rho;
-                // fundamental derivative G = nu^3 p_nunu|_s / (2 c^2)
-                GF[i] = ((1.0f + G.delta) * (2.0f + G.delta) * G.R * T / (om * om * om) - 6.0f * G.a * rho) /
-                        (2.0f * c2);
+                if (B.moving) {
+                    // monitor fields: rho and the fundamental derivative G in double-float arithmetic from the
+                    // (hi, lo) state planes (near the critical point p_nunu cancels to a small difference)
+                    const size_t q = off + i;
+                    const df mom[1] = {{B.JU[ntot + q], B.JU[4 * ntot + q]}};
+                    rho_G_df({B.JU[q], B.JU[3 * ntot + q]}, mom, 1, {B.JU[2 * ntot + q], B.JU[5 * ntot + q]},
+                             {B.J[q], B.J[ntot + q]}, B.gdf, &rhoF[i], &GF[i]);
+                }
             }
             m = block_max_f(m, red);
             double dt = double(B.cfl) / double(m);
             const double left = B.t_end - t;
             if (left <= 1e-14 * fmax(1.0, fabs(B.t_end))) break;
             if (dt > left) dt = left;
-            const float dtf = float(dt);
+            float dtf = float(dt);
 
             // ---- mesh redistribution (Sec. 4) on the displacement
             if (B.moving) {
@@ -179,7 +188,21 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
                 g = block_min_f(g, red);
                 const float fv = g / dtf;
                 for (int i = tid; i < L; i += BT) xd[i] = fv * (din[i] - d[i]);
-                __syncthreads();
+                // eq. cfl with this mesh velocity (J xi_t = -xdot): dt = min(dt, CFL / max (|v - xdot| + c) / (J dxi));
+                // xdot keeps its value, so the mesh moves less than Delta_gamma allows
+                float mv = 0.0f;
+                for (int i = tid; i < L; i += BT) {
+                    float rho, v, T, c2, iJ;
+                    node(i, rho, v, T, c2, iJ);
+                    const float lam = (fabsf(v - xd[i]) + sqrtf(fmaxf(c2, 0.0f))) * iJ * idxi;
+                    mv = fmaxf(mv, c2 > 0.0f ? lam : 3.0e38f);
+                }
+                mv = block_max_f(mv, red);
+                const double dtm = double(B.cfl) / double(mv);
+                if (dtm < dt) {
+                    dt = dtm;
+                    dtf = float(dt);
+                }
             }
 
             // ---- three fused RK stages, each a loop over BXC-node chunks
@@ -433,6 +456,7 @@ int es_batch_create(es_batch** out, const es_params* p, int nprob, const int* le
     B.tprob = b->tprob;
     B.queue = b->queue;
     B.cfl = float(p->cfl);
+    B.gdf = mixed::gas_df(p->a, p->b, p->R, p->cv);
     B.moving = p->moving;
     B.kappa = p->kappa;
     B.w0 = float(p->alpha[0]);

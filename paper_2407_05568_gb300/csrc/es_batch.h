@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "es_df.cuh"
 #include "es_internal.h"
 
 namespace es {
@@ -33,6 +34,7 @@ struct BatchParams {
     float w0, w1, w2;             // monitor weights
     int filter_passes, sweeps;
     StageParams tmpl;             // gas, WENO and the float constants of the stage kernel
+    mixed::GasDF gdf;             // gas constants as (hi, lo) pairs for the monitor's G
 };
 
 // CTA shapes (threads per CTA) of the batched kernel; the autotuner times each

@@ -95,8 +95,10 @@ __device__ __forceinline__ bool fixed_node_f(const GridParams& g, int i, int j) 
 
 }  // namespace
 
-// eq. cfl on the FP32 pipe: max_i sum_k (|n_k . v| + |n_k| c) / (J dxi_k), zero mesh velocity
-__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, DevScalars* d) {
+// eq. cfl on the FP32 pipe: max_i sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k) with
+// J xi_{k,t} = -xdot . n_k; vel = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
+__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
+                        int slot, DevScalars* d) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
     const float idx1 = float(g.inv_dxi[0]), idx2 = float(g.inv_dxi[1]);
@@ -113,10 +115,12 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
         const float iom = 1.0f / (1.0f - G.b * rho);
         const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
         const float c = sqrtf(fmaxf(c2, 0.0f));
+        const float xd1 = vel != nullptr ? vel[id] : 0.0f;
         float tot;
         if (g.dim == 1) {
-            tot = (fabsf(v1) + c) * iJ * idx1;
+            tot = (fabsf(v1 - xd1) + c) * iJ * idx1;
         } else {
+            const float xd2 = vel != nullptr ? vel[N + id] : 0.0f;
             float x1, x2, y1, y2;
             if (i >= 3 && i < g.n1 - 3 && j >= 3 && j < g.n2 - 3) {
                 // interior: the 24 displacement loads have no ghost rule and are issued together
@@ -141,35 +145,26 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
             }
             const float a1 = y2, b1 = -x2;        // J dxi_1/dx
             const float a2 = -y1, b2 = x1;        // J dxi_2/dx
-            tot = (fabsf(a1 * v1 + b1 * v2) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
-                  (fabsf(a2 * v1 + b2 * v2) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
+            tot = (fabsf(a1 * (v1 - xd1) + b1 * (v2 - xd2)) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
+                  (fabsf(a2 * (v1 - xd1) + b2 * (v2 - xd2)) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
         }
         if (!(c2 > 0.0f)) tot = 3.0e38f;
         m = fmaxf(m, tot);
     }
     m = block_max_f32(m);
-    if (threadIdx.x == 0) atomic_max_pos(&d->red[RED_CFL], double(m));
+    if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], double(m));
 }
 
-// density and G = nu^3 p_nunu|_s / (2 c^2) at the nodes, then the raw monitor terms need
-// the neighbours: two kernels (as in the FP64 path)
+// density and G = nu^3 p_nunu|_s / (2 c^2) at a node from the (hi, lo) state planes, G in double-float
+// arithmetic (near the critical point p_nunu is a difference of nearly equal terms: the EOS stays at
+// FP64-like accuracy there); the raw monitor terms need the neighbours
 __device__ __forceinline__ void mon_field_f(const GridParams& g, const GasF32& G, const float* JU, const float* J,
                                             int N, size_t P, int id, float* rho_out, float* G_out) {
-    const float iJ = 1.0f / ld2(J, N, id);
-    const float rho = ld2(JU, P, id) * iJ;
-    const float irho = 1.0f / rho;
-    float ke = 0.0f;
-    for (int k = 0; k < g.dim; ++k) {
-        const float v = ld2(JU, P, (1 + k) * N + id) * iJ * irho;
-        ke += v * v;
-    }
-    const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
-    const float T = (E * irho - 0.5f * ke + G.a * rho) * G.icv;
-    const float iom = 1.0f / (1.0f - G.b * rho);
-    const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
-    const float pnn3 = (1.0f + G.delta) * (2.0f + G.delta) * G.R * T * iom * iom * iom - 6.0f * G.a * rho;
-    *rho_out = rho;
-    *G_out = pnn3 / (2.0f * c2);
+    using mixed::df;
+    df mom[3];
+    for (int k = 0; k < g.dim; ++k) mom[k] = {JU[(1 + k) * N + id], JU[P + (1 + k) * N + id]};
+    const int ce = (g.dim + 1) * N + id;
+    mixed::rho_G_df({JU[id], JU[P + id]}, mom, g.dim, {JU[ce], JU[P + ce]}, {J[id], J[N + id]}, G.gdf, rho_out, G_out);
 }
 
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF) {

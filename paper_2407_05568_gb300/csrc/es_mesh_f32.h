@@ -3,12 +3,14 @@
 #include <cuda_runtime.h>
 
 #include "es_aux.h"
+#include "es_df.cuh"
 
 namespace es {
 
-// float copies of the gas constants
+// float copies of the gas constants, and the (hi, lo) pairs the monitor's G is evaluated with
 struct GasF32 {
     float a, b, R, cv, delta, icv;
+    mixed::GasDF gdf;
 };
 
 inline GasF32 gas_f32(const Gas& g) {
@@ -19,11 +21,14 @@ inline GasF32 gas_f32(const Gas& g) {
     f.cv = float(g.cv);
     f.delta = float(g.delta);
     f.icv = float(1.0 / g.cv);
+    f.gdf = mixed::gas_df(g.a, g.b, g.R, g.cv);
     return f;
 }
 
 // JU, J: the mixed form's (hi, lo) float planes; disp: the FP32 displacement [dim][N]
-__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, DevScalars* d);
+// vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity)
+__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
+                        int slot, DevScalars* d);
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
 __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
                         float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "es_device.cuh"
+#include "es_df.cuh"
 #include "es_internal.h"
 
 namespace es {
@@ -47,47 +48,6 @@ struct GasF {
 struct WenoF {
     float g1, g2, g3, g12, ig22, ig3, eps, sign_tol;
 };
-
-// ---- double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2
-struct df {
-    float hi, lo;
-};
-__device__ __forceinline__ df fast_two_sum(float a, float b) {   // |a| >= |b|
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ df df_add(df x, df y) {
-    df s = two_sum(x.hi, y.hi);
-    return fast_two_sum(s.hi, s.lo + x.lo + y.lo);
-}
-__device__ __forceinline__ df df_add_f(df x, float y) {
-    df s = two_sum(x.hi, y);
-    return fast_two_sum(s.hi, s.lo + x.lo);
-}
-__device__ __forceinline__ df df_mul(df x, df y) {
-    const float p = x.hi * y.hi;
-    const float e = fmaf(x.hi, y.hi, -p) + (x.hi * y.lo + x.lo * y.hi);
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ df df_mul_f(df x, float y) {
-    const float p = x.hi * y;
-    const float e = fmaf(x.hi, y, -p) + x.lo * y;
-    return fast_two_sum(p, e);
-}
-__device__ __forceinline__ df df_recip(df y) {
-    const float q1 = 1.0f / y.hi;
-    // r = 1 - q1 y, exactly enough: fma gives the low part of q1 y.hi
-    const float r = fmaf(-q1, y.hi, 1.0f) - q1 * y.lo;
-    return fast_two_sum(q1, r * q1);
-}
-__device__ __forceinline__ float df_diff(df a, df b) {            // (a - b) rounded to float
-    return (a.hi - b.hi) + (a.lo - b.lo);
-}
 
 // reciprocal logarithmic mean 1/{a}^ln from the relative jump f = (a_l - a_r)/(a_l + a_r):
 // [[ln a]] = ln((1 + f)/(1 - f)) = 2 artanh(f); series of artanh(f)/f for |f| < 0.05

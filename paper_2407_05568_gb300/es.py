@@ -59,8 +59,9 @@ def lib():
         L.es_prim_to_cons.argtypes = [vp, vp, vp, vp, vp, vp]
         L.es_rhs.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.es_rk_stage.argtypes = [vp, i, d, vp, vp, vp, vp, vp, vp, vp, vp]
-        L.es_cfl_dt.argtypes = [vp, vp, vp, vp, ctypes.POINTER(d)]
+        L.es_cfl_dt.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(d)]
         L.es_mesh_redistribute.argtypes = [vp, vp, vp, vp, d, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        L.es_entropy_rate.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(d)]
         L.es_steps.argtypes = [vp, vp, vp, vp, i, d]
         L.es_step.argtypes = [vp, vp, vp, vp, d, ctypes.POINTER(d), ctypes.POINTER(d)]
         L.es_set_time.argtypes = [vp, d]
@@ -111,7 +112,7 @@ def lib():
                      "es_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("es_create", "es_init_mesh", "es_prim_to_cons", "es_rhs", "es_rk_stage", "es_cfl_dt",
-                     "es_mesh_redistribute", "es_steps", "es_step", "es_set_time", "es_get_time", "es_run_host",
+                     "es_entropy_rate", "es_mesh_redistribute", "es_steps", "es_step", "es_set_time", "es_get_time", "es_run_host",
                      "es_check", "es_last_error"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -239,11 +240,20 @@ def es_rk_stage(ctx, stage, dt, JUn, Jn, JUs, Js, xn, xdot, JU_out, J_out):
                                 _ptr(xn, F64), _ptr(xdot, F64), _ptr(JU_out, S), _ptr(J_out, S)))
 
 
-def es_cfl_dt(ctx, JU, J, x):
+def es_cfl_dt(ctx, JU, J, x, xdot=None):
+    """eq. cfl's time step; xdot (the mesh velocity, or None for a mesh at rest) enters the spectral radius."""
     S = ctx.state_dtype
     dt = ctypes.c_double()
-    ctx._call(lib().es_cfl_dt(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(dt)))
+    ctx._call(lib().es_cfl_dt(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), _ptr(xdot, F64), ctypes.byref(dt)))
     return dt.value
+
+
+def es_entropy_rate(ctx, JU, J, dJU, dJ):
+    """FP64 entropy production check: (rate, sum of the magnitudes of its terms) of the total entropy."""
+    S = ctx.state_dtype
+    out = (ctypes.c_double * 2)()
+    ctx._call(lib().es_entropy_rate(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(dJU, S), _ptr(dJ, S), out))
+    return out[0], out[1]
 
 
 def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot):

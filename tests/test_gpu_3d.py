@@ -149,6 +149,24 @@ def test_cfl_parity_3d(case):
     assert abs(dt_g - dt_o) <= 1e-13 * dt_o
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cfl_with_mesh_velocity_3d(precision):
+    """eq. cfl with a mesh velocity in the spectral radius (|J xi_t + n . v| + |n| c), against the oracle."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = CASES["wavy_periodic_smooth"]()
+    X, Y, Z = w["x"]
+    tp = 2 * np.pi
+    xd = 0.8 * np.stack([np.sin(tp * (X + Y)), np.cos(tp * (Y - Z)), np.sin(tp * (Z + X))])
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision=precision)
+    dt_o = stepper.cfl_dt(sch, JU_o, J_o, x, w["cfl"], xd)
+    assert dt_o < 0.9 * stepper.cfl_dt(sch, JU_o, J_o, x, w["cfl"])          # the mesh velocity matters here
+    dt_g = es.es_cfl_dt(ctx, JU, J, xt, torch.tensor(xd, dtype=torch.float64, device="cuda"))
+    assert abs(dt_g - dt_o) <= (1e-13 if precision == "fp64" else 1e-5) * dt_o
+
+
 def _moving(w, monitor="vdw"):
     w = dict(w, moving=True)
     if monitor == "vdw":

@@ -141,6 +141,24 @@ def test_cfl_parity(case):
     assert abs(dt_g - dt_o) <= 1e-13 * dt_o
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["rp1d_ragged", "wavy_periodic"])
+def test_cfl_with_mesh_velocity(case, precision):
+    """eq. cfl with a mesh velocity in the spectral radius (|J xi_t + n . v| + |n| c, J xi_t = -xdot . n),
+    against the oracle; the step's second time-step pass uses this form."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = CASES[case]()
+    xd = 10.0 * _xdot(w) if case == "wavy_periodic" else 2.0 * np.sin(2 * np.pi * w["x"])
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision=precision)
+    dt_o = stepper.cfl_dt(sch, JU_o, J_o, x, w["cfl"], xd)
+    assert dt_o < 0.9 * stepper.cfl_dt(sch, JU_o, J_o, x, w["cfl"])
+    dt_g = es.es_cfl_dt(ctx, JU, J, xt, torch.tensor(np.ascontiguousarray(xd), dtype=torch.float64, device="cuda"))
+    assert abs(dt_g - dt_o) <= (1e-13 if precision == "fp64" else 1e-5) * dt_o
+
+
 @pytest.mark.parametrize("case", ["riemann2d_ragged", "rp1d_ragged"])
 def test_mesh_redistribution_parity(case):
     import torch

@@ -381,7 +381,7 @@ def test_sign_switch_ignores_velocity_noise_where_v_t_is_zero():
 
 
 def test_frame_angle_ignores_rounding_of_vanishing_metrics():
-    """Reading 19: theta = 0 when |(n_1, n_2)| <= 1e-12 |n|.  On an outflow box whose boundary planes
+    """The 3D face frame takes theta = 0 when |(n_1, n_2)| <= 1e-12 |n|.  On an outflow box whose boundary planes
     stay Cartesian (the mesh velocity vanishes on the boundary nodes, as the mesh solve makes it) the
     x_3-faces' (n_1, n_2) are the rounding of exact zeros; with theta taken from that rounding the
     tangential frame, and through the per-field sign switch the dissipation, followed the noise (1e-5
@@ -414,3 +414,28 @@ def test_frame_angle_ignores_rounding_of_vanishing_metrics():
     d0, _ = op.rhs(sch, JU, J, xs, xd)
     d1, _ = op.rhs(sch, JU, J, xs * (1.0 + 2e-16 * rng.standard_normal(xs.shape)), xd)
     assert np.abs(d1 - d0).sum() < 1e-12 * np.abs(d0).sum()
+
+
+def test_example_5_7_runs_to_its_final_time():
+    """Example 5.7 (Table 5.1's RP1 states inside and outside a sphere of radius 0.5; MM with Example 5.5's
+    monitor) at 12^3 on the moving mesh, with the paper's 3D CFL of 0.3: every node stays admissible after every
+    step up to the example's final time (t = 0.2 in the paper's reduced units), and, as in RP1, G < 0 appears
+    between the rarefaction and the shock.  Taking eq. cfl's spectral radius with the mesh at rest instead of with
+    the step's mesh velocity, the first step already left the admissible region."""
+    w = wl.spherical_shock_3d(12)
+    assert w["cfl"] == 0.3 and w["t_end"] == pytest.approx(0.2 * np.sqrt(3.0 / 8.0))
+    g = thermo.Gas(**w["gas"])
+    sch = op.Scheme(gas=g, dim=3, bc=tuple(w["bc"]), dxi=tuple(w["dxi"]), period=tuple(w["period"]))
+    mc = stepper.MeshControl(moving=True, **w["mesh"])
+    x = w["x"]
+    J = op.node_jacobian(sch, x)
+    JU = thermo.prim_to_cons(g, w["rho"], w["v"], w["p"]) * J
+    t, steps = 0.0, 0
+    while t < w["t_end"] * (1.0 - 1e-14):
+        JU, J, x, t, info = stepper.step(sch, mc, JU, J, x, t, w["t_end"], w["cfl"])
+        steps += 1
+        rho, v, T, p = thermo.cons_to_prim(g, JU / J)
+        assert thermo.admissible(g, rho, T).all(), steps
+    assert steps > 30
+    assert np.abs(x - w["x"]).max() > 0.1 * w["dxi"][0]                  # the mesh moved
+    assert thermo.fundamental_derivative(g, rho, T).min() < -0.1

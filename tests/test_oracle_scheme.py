@@ -297,6 +297,72 @@ def test_mm1_monitor_sees_the_density_only():
     assert np.allclose(om[right] ** 2 - 1.0, alphas[0], rtol=1e-12)
 
 
+def _periodic_grid(dim, n=16):
+    x1, d = wl.uniform_nodes(n, 0.0, 1.0, True)
+    if dim == 1:
+        return (x1,), (d,), ("periodic",)
+    X, Y = np.meshgrid(x1, x1)
+    return (X, Y), (d, d), ("periodic", "periodic")
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_vdw_monitor_closed_form(dim):
+    """eq. van der Waalsmonitor with kappa = 2 (delta_1 = rho, delta_2 = G) on periodic sines.  Second-order central
+    differences of sin(2 pi m xi) are cos(2 pi m xi) sin(2 pi m h)/h and -sin(2 pi m xi) 4 sin^2(pi m h)/h^2 exactly, so
+    every normalised term is a trigonometric polynomial whose constant factor cancels against its maximum (n = 16
+    puts nodes at the maxima).  With rho = 1 + 0.1 sin(4 pi xi_1) and G = 0.3 sum_k sin(2 pi xi_k):
+    omega^2 = 1 + a1 cos^2(4 pi xi_1) + a2 mean_k cos^2(2 pi xi_k) + a3 mean_k sin^2(2 pi xi_k).
+    The last term is |Delta_xi G|^2, the squared vector of second derivatives (Sec. 4); its gradient, or the term
+    without the square, gives another function."""
+    X, dxi, bc = _periodic_grid(dim)
+    rho = 1.0 + 0.1 * np.sin(4 * np.pi * X[0])
+    G = 0.3 * sum(np.sin(2 * np.pi * Xk) for Xk in X)
+    a = (1200.0, 3000.0, 5000.0)
+    om = mesh.monitor_vdw([rho, G], G, a, dim, bc, dxi)
+    c2 = sum(np.cos(2 * np.pi * Xk) ** 2 for Xk in X) / dim
+    s2 = sum(np.sin(2 * np.pi * Xk) ** 2 for Xk in X) / dim
+    expect = 1.0 + a[0] * np.cos(4 * np.pi * X[0]) ** 2 + a[1] * c2 + a[2] * s2
+    assert np.allclose(om**2, expect, rtol=1e-12, atol=0.0)
+    # kappa = 1 (Example 5.4's MM): the second weight goes to |Delta_xi G|^2
+    om1 = mesh.monitor_vdw([rho], G, (1200.0, 500.0), dim, bc, dxi)
+    assert np.allclose(om1**2, 1.0 + 1200.0 * np.cos(4 * np.pi * X[0]) ** 2 + 500.0 * s2, rtol=1e-12, atol=0.0)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_smooth_monitor_closed_form(dim):
+    """eq. van der Waalssinmonitor (Example 5.1): omega^2 = 1 + a1 |grad rho|/max + a2 |Delta_xi rho|/max with the
+    norms not squared.  For rho = 0.5 + 0.1 sum_k sin(2 pi xi_k) the exact difference quotients give
+    |grad rho|/max = sqrt(mean_k cos^2(2 pi xi_k)) and |Delta_xi rho|/max = sqrt(mean_k sin^2(2 pi xi_k))."""
+    X, dxi, bc = _periodic_grid(dim)
+    rho = 0.5 + 0.1 * sum(np.sin(2 * np.pi * Xk) for Xk in X)
+    om = mesh.monitor_smooth(rho, (20.0, 15.0), dim, bc, dxi)
+    c = np.sqrt(sum(np.cos(2 * np.pi * Xk) ** 2 for Xk in X) / dim)
+    s = np.sqrt(sum(np.sin(2 * np.pi * Xk) ** 2 for Xk in X) / dim)
+    assert np.allclose(om**2, 1.0 + 20.0 * c + 15.0 * s, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_sign_switch_dead_zone_leaves_real_jumps_alone(dim):
+    """The dead zone of the sign switch Y (a plain jump within sign_tol of the size of the terms that form it has
+    sign 0) only touches round-off-sized jumps: on rough random states, whose jumps are all far above 1e-12 of their
+    scale, the operator with sign_tol = 1e-12 equals the paper's plain sign rule (sign_tol = 0) bit for bit."""
+    if dim == 1:
+        w = wl.sine_1d(48)
+        shape = (48,)
+    else:
+        w = wl.sine_2d(20)
+        shape = (20, 20)
+    rho, v, p = wl.rough_state(shape, 17, dim)
+    g = thermo.Gas(**w["gas"])
+    out = []
+    for tol in (1e-12, 0.0):
+        sch = op.Scheme(gas=g, dim=dim, bc=w["bc"], dxi=w["dxi"], period=w["period"], sign_tol=tol)
+        J = op.node_jacobian(sch, w["x"])
+        JU = thermo.prim_to_cons(g, rho, v, p) * J
+        out.append(op.rhs(sch, JU, J, w["x"], np.zeros_like(w["x"])))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_uniform_monitor_fixed_point():
     """With omega = const the uniform mesh solves the discrete mesh equation (x unchanged)."""
     w = wl.riemann_2d(12, moving=True)
@@ -330,6 +396,32 @@ def test_limiter_keeps_order():
     # the bound is attained by some node
     moved = np.abs(gam * dx) / d
     assert moved.max() >= 0.5 - 1e-12 or gam == 1.0
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_cfl_on_a_translating_mesh(dim):
+    """eq. cfl with the spectral radius of the xi_k flux Jacobian, |J xi_{k,t} + n_k . v| + L_k c over J: on a
+    Cartesian mesh (n_k = e_k, J = 1) translating with constant velocity s (J xi_{k,t} = -s_k, eq. VCLCoeff), a
+    uniform state gives Delta t = CFL / sum_k (|v_k - s_k| + c) / dxi_k; at rest s = 0."""
+    n = (10, 12, 8)[:dim]
+    dxi = tuple(1.0 / m for m in n)
+    g = thermo.gas_units_a()
+    sch = op.Scheme(gas=g, dim=dim, bc=("periodic",) * dim, dxi=dxi, period=(1.0,) * dim)
+    axes = [np.arange(m) * h for m, h in zip(n, dxi)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]        # x_1 varies along the last axis
+    x = np.stack(grids)
+    shape = x.shape[1:]
+    v = np.array([0.4, -0.3, 0.25])[:dim]
+    s = np.array([0.9, 0.2, -0.6])[:dim]
+    rho, p = 0.7, 1.1
+    U = thermo.prim_to_cons(g, np.full(shape, rho), v.reshape((dim,) + (1,) * dim) * np.ones(shape), np.full(shape, p))
+    J = np.ones(shape)
+    c = np.sqrt(thermo.sound_speed2(g, rho, thermo.temperature(g, rho, p)))
+    xdot = s.reshape((dim,) + (1,) * dim) * np.ones(shape)
+    moving = 0.4 / sum((abs(v[k] - s[k]) + c) / dxi[k] for k in range(dim))
+    rest = 0.4 / sum((abs(v[k]) + c) / dxi[k] for k in range(dim))
+    assert stepper.cfl_dt(sch, U * J, J, x, 0.4, xdot) == pytest.approx(moving, rel=1e-13)
+    assert stepper.cfl_dt(sch, U * J, J, x, 0.4) == pytest.approx(rest, rel=1e-13)
 
 
 # ------------------------------------------------------------------ stepper
