@@ -1,0 +1,144 @@
+"""Example 5.2's Riemann problems (Table 5.1) on the GPU, through the C ABI, to the paper's final times.
+
+Every step: the oracle's run gives the state at each t_n.  The kernels take one full step (CFL, mesh
+redistribution, three RK stages) from that same state, and the result is compared with the oracle's next state.
+The FP64 form must agree to <= 1e-12 relative L1 in JU, J and x, on every one of the several hundred steps per
+problem, through the rarefaction shocks, the contact and the compressive shock.  The mixed form (FP32 bulk;
+double-float state, jumps and monitor G) is held to a per-step bar stated below.
+
+Free runs: both sides advance independently from t = 0 to the final time.  These discontinuous moving-mesh runs
+are sensitive to rounding.  The oracle itself, with its initial state perturbed by 1e-14 (relative), ends 1e-5 to
+1e-2 (relative L1) away from its own unperturbed run, depending on the problem and the perturbation.  The bar is
+therefore relative to that spread: the kernels' final state lies within 10 times the largest spread of three
+perturbed oracle runs.  On the fixed mesh (UM) the spread is ~1e-6.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import stepper
+from paper_2407_05568_gb300 import workloads as wl
+
+from sides import gpu_setup, oracle_setup, rel_l1, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_05568_gb300 import build
+    build.build()
+
+
+SIZES = {"MM": 100, "MM1": 100, "UM": 300}
+CASES = [("RP1", "MM"), ("RP2", "MM"), ("RP3", "MM"), ("RP1", "MM1"), ("RP1", "UM")]
+
+
+def _workload(name, variant):
+    w = wl.riemann_1d(name, n=SIZES[variant], moving=variant != "UM")
+    return wl.mm1(w) if variant == "MM1" else w
+
+
+@functools.lru_cache(maxsize=None)
+def _trajectory(name, variant):
+    """The oracle's states (JU, J, x, t) at every step from t = 0 to the final time."""
+    w = _workload(name, variant)
+    sch, mc, JU, J, x = oracle_setup(w)
+    t = 0.0
+    out = [(JU, J, x, t)]
+    while t < w["t_end"] * (1.0 - 1e-14):
+        JU, J, x, t, _ = stepper.step(sch, mc, JU, J, x, t, w["t_end"], w["cfl"])
+        out.append((JU, J, x, t))
+    return out
+
+
+@functools.lru_cache(maxsize=None)
+def _spread(name, variant):
+    """Largest final-time distance (relative L1 over JU, J, x) of three oracle runs whose initial JU is perturbed by
+    1e-14 (relative, seeded normal) from the unperturbed run."""
+    w = _workload(name, variant)
+    ref = _trajectory(name, variant)[-1]
+    worst = 0.0
+    for seed in (1, 2, 3):
+        sch, mc, JU, J, x = oracle_setup(w)
+        JU = JU * (1.0 + 1e-14 * np.random.default_rng(seed).standard_normal(JU.shape))
+        JU, J, x, _ = stepper.run(sch, mc, JU, J, x, w["t_end"], w["cfl"])
+        worst = max(worst, rel_l1(JU, ref[0]), rel_l1(J, ref[1]), rel_l1(x, ref[2]))
+    return worst
+
+
+def _load(JU_g, J_g, x_g, JU, J, x, mixed):
+    import torch
+    if mixed:
+        for arr, dst in ((JU, JU_g), (J, J_g)):
+            hi = arr.astype(np.float32)
+            lo = (arr - hi.astype(np.float64)).astype(np.float32)
+            dst[0].copy_(torch.from_numpy(hi))
+            dst[1].copy_(torch.from_numpy(lo))
+    else:
+        JU_g.copy_(torch.from_numpy(JU))
+        J_g.copy_(torch.from_numpy(J))
+    x_g.copy_(torch.from_numpy(x))
+
+
+def _every_step(name, variant, precision):
+    """Per-step relative L1 errors (JU, J, x) of the kernels' step from the oracle's state."""
+    from paper_2407_05568_gb300 import es
+    w = _workload(name, variant)
+    traj = _trajectory(name, variant)
+    ctx, JU, J, xt = gpu_setup(w, precision=precision)
+    errs = []
+    for k in range(len(traj) - 1):
+        _load(JU, J, xt, *traj[k][:3], precision == "mixed")
+        es.es_set_time(ctx, traj[k][3])
+        es.es_steps(ctx, JU, J, xt, 1, w["t_end"])
+        JU_n, J_n, x_n, t_n = traj[k + 1]
+        t_g, _ = es.es_get_time(ctx)
+        assert abs(t_g - t_n) <= (1e-13 if precision == "fp64" else 1e-4) * t_n, (k, t_g, t_n)
+        errs.append((rel_l1(to_np(JU), JU_n), rel_l1(to_np(J), J_n), rel_l1(to_np(xt), x_n)))
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    assert len(traj) > 200
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("name,variant", CASES)
+def test_fp64_every_step_of_the_run(name, variant):
+    e = _every_step(name, variant, "fp64")
+    assert e.max() < 1e-12, (int(np.argmax(e.max(axis=1))), e.max())
+
+
+@pytest.mark.parametrize("name,variant", CASES)
+def test_mixed_every_step_of_the_run(name, variant):
+    """The mixed form's step from the oracle's state.  Its mesh solve rounds the displacement to FP32, and near a
+    discontinuity a node's state follows its position, so the bar is 1e-5 relative L1 per step on the moving
+    meshes.  On the fixed mesh it is FP32 flux rounding, 1e-6."""
+    e = _every_step(name, variant, "mixed")
+    bar = 1e-6 if variant == "UM" else 1e-5
+    assert e.max() < bar, (int(np.argmax(e.max(axis=1))), e.max(axis=0))
+
+
+def _free_run(name, variant, precision):
+    from paper_2407_05568_gb300 import es
+    w = _workload(name, variant)
+    traj = _trajectory(name, variant)
+    ctx, JU, J, xt = gpu_setup(w, precision=precision)
+    es.es_set_time(ctx, 0.0)
+    es.es_steps(ctx, JU, J, xt, len(traj) + 50, w["t_end"])
+    assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+    t_g, _ = es.es_get_time(ctx)
+    assert t_g == pytest.approx(w["t_end"], rel=1e-12)
+    JU_o, J_o, x_o, _ = traj[-1]
+    return max(rel_l1(to_np(JU), JU_o), rel_l1(to_np(J), J_o), rel_l1(to_np(xt), x_o))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,variant", CASES)
+def test_free_run_to_final_time_within_the_oracles_own_spread(name, variant, precision):
+    err = _free_run(name, variant, precision)
+    spread = _spread(name, variant)
+    assert spread > 0.0
+    assert err < 10.0 * spread, (err, spread)
