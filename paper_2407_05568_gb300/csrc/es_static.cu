@@ -1,4 +1,4 @@
-// es_static.cu -- an SSP-RK3 step that allocates nothing.
+// es_static.cu -- an SSP-RK3 step that allocates nothing (after its first call on a device).
 //
 // Some callers cannot call cudaMalloc at all: a solver embedded in a host
 // application whose device memory is owned and budgeted by someone else, code
@@ -37,7 +37,8 @@ int g_prepared[MAX_DEVICES][3];            // stage kernel attributes set, per d
 
 // Device address of the scratch array on the current device (looked up once
 // per device with that device current), and the stage kernel's shared-memory
-// attribute for this dimension.
+// attribute for this dimension.  Under lazy module loading the symbol lookup is
+// also what loads this library's modules, and with them the array.
 int setup_current_device(int dim, double** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return ES_ERR_CUDA;
@@ -55,9 +56,12 @@ int setup_current_device(int dim, double** out) {
     return ES_OK;
 }
 
+// the parameter checks of es_create that apply to this call (1D/2D, FP64, periodic or outflow ends)
 bool params_ok(const es_params* p) {
     if (!p || (p->dim != 1 && p->dim != 2) || p->precision != ES_PREC_FP64) return false;
     if (p->n1 < 8 || (p->dim == 1 && p->n2 != 1) || (p->dim == 2 && p->n2 < 8)) return false;
+    if (p->n3 != 0 && p->n3 != 1) return false;
+    if (p->tile < 0 || p->tile > ES_NTILES) return false;
     if ((long long)p->n1 * p->n2 > ES_STATIC_MAX_NODES) return false;
     for (int k = 0; k < p->dim; ++k) {
         if (!(p->dxi[k] > 0.0)) return false;
@@ -66,7 +70,7 @@ bool params_ok(const es_params* p) {
     }
     if (!(p->R > 0.0) || !(p->cv > 0.0) || !(p->a >= 0.0) || !(p->b >= 0.0)) return false;
     if (!(p->weno_gamma[0] > 0.0) || !(p->weno_gamma[1] > 0.0) || !(p->weno_gamma[2] > 0.0)) return false;
-    if (!(p->weno_eps > 0.0) || !(p->sign_tol >= 0.0)) return false;
+    if (!(p->weno_eps > 0.0) || !(p->sign_tol >= 0.0) || p->sign_tol > 1e-2) return false;
     return true;
 }
 
@@ -118,6 +122,7 @@ extern "C" int es_rk3_step_static(const es_params* p, double dt, double* JU, dou
     P.weno.eps = p->weno_eps;
     P.weno.sign_tol = p->sign_tol;
     P.diss = p->dissipation;
+    P.tile = p->tile > 0 ? p->tile - 1 : 0;
     P.status = status;
     P.dt_host = dt;
     P.xn = x;

@@ -79,6 +79,38 @@ def test_static_step_matches_context_stages(case):
             assert np.abs(g - r).sum() / np.abs(r).sum() < 1e-12
 
 
+def test_static_step_allocates_nothing_after_its_first_call():
+    """After the first call on the device (its set-up), further calls leave the device's free memory unchanged,
+    on the default stream and on another stream, and give the same result on both."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = _problem("riemann2d")
+    dev = torch.device("cuda:0")
+    params = es.make_params(w)
+    ctx = es.es_create(params)
+    x = torch.tensor(w["x"], dtype=torch.float64, device=dev)
+    xdot = torch.tensor(w["xdot"], dtype=torch.float64, device=dev)
+    J = torch.empty(w["x"].shape[1:], dtype=torch.float64, device=dev)
+    es.es_init_mesh(ctx, x, J)
+    JU = torch.empty((w["dim"] + 2,) + w["x"].shape[1:], dtype=torch.float64, device=dev)
+    es.es_prim_to_cons(ctx, torch.tensor(w["rho"], device=dev), torch.tensor(w["v"], device=dev),
+                       torch.tensor(w["p"], device=dev), J, JU)
+    JU2, J2 = JU.clone(), J.clone()
+    side = torch.cuda.Stream()
+    dt = 0.2 * min(w["dxi"])
+    torch.cuda.synchronize()
+    assert es.es_rk3_step_static(params, dt, JU, J, x, xdot) == 0          # set-up call
+    free0, _ = torch.cuda.mem_get_info()
+    assert es.es_rk3_step_static(params, dt, JU, J, x, xdot) == 0
+    free1, _ = torch.cuda.mem_get_info()
+    assert es.es_rk3_step_static(params, dt, JU2, J2, x, xdot, stream=side) == 0
+    assert es.es_rk3_step_static(params, dt, JU2, J2, x, xdot, stream=side) == 0
+    free2, _ = torch.cuda.mem_get_info()
+    assert free0 == free1 == free2
+    assert torch.equal(JU, JU2) and torch.equal(J, J2)
+
+
 def test_static_step_rejects_large_meshes():
     from paper_2407_05568_gb300 import es
     w = wl.sine_2d(300)                          # 90000 nodes > 65536
