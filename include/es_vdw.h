@@ -92,7 +92,7 @@ typedef struct es_params {
     double period[3];       /* period of x_k along a periodic direction */
     int    bc[3];           /* ES_BC_* per direction */
     double weno_gamma[3];   /* MR-WENO5 linear weights (1-point, 3-point, 5-point), Sec. 5: (0.005, 0.045, 0.95) */
-    double weno_eps;        /* smoothness regulariser (paper silent; 1e-12) */
+    double weno_eps;        /* epsilon of the MR-WENO5 nonlinear weights (paper silent; 1e-6, Jiang and Shu's) */
     double sign_tol;        /* sign switch Y: a plain jump |W_{i+1} - W_i| no larger than sign_tol times
                                sum_a |R_am| (|(TV_i)_a| + |(TV_{i+1})_a|), the size of the terms forming
                                it, is round-off of a zero jump and has sign 0 (Y = 0): 1e-12 in
@@ -229,6 +229,14 @@ int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int
  * Divisors must be finite, normal and nonzero. */
 int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream);
 
+/* Measured arithmetic rates of the current GPU (the roofline denominators of the stage kernels, which the
+ * FP64 pipe bounds in the plain form and the FP32 pipe in the mixed and batched forms): a grid of SMs x 8
+ * CTAs x 256 threads, each with 8 independent chains of dependent FMAs, timed with CUDA events on `stream`,
+ * best of five launches after a warm-up; an FMA counts as two operations.  Writes TFLOP/s to the two host
+ * doubles; allocates and frees a small buffer; synchronises `stream`.  About 60 ms.  Errors: ES_ERR_ARG for
+ * null outputs, ES_ERR_CUDA. */
+int es_selftest_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
+
 /* Number of kernel launches the library has issued (graph launches count
  * their kernels), for launch accounting. */
 int64_t es_launch_count(es_ctx* ctx);
@@ -341,6 +349,12 @@ void es_batch_destroy(es_batch* b);
 int64_t es_batch_nodes(es_batch* b);
 /* Initial primitive state of every node (device arrays of ntot doubles). */
 int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const double* p);
+/* State of every problem from conservative values, as es_batch_get returns them (device arrays): JU [3][ntot],
+ * J [ntot] and x [ntot] (node coordinates, x_0 = 0 and x_{L-1} = 1 for outflow ends), and t [nprob] the time of
+ * each problem.  JU and J are split into the form's (hi, lo) float planes, x into the FP32 displacement from
+ * the uniform mesh; the mesh velocity restarts at zero (each step recomputes it).  Restarts a batch, or sets
+ * each problem to a given step of a reference run. */
+int es_batch_set_state(es_batch* b, const double* JU, const double* J, const double* x, const double* t);
 /* Advance every problem by nsteps full steps (each clipped to t_end). */
 int es_batch_steps(es_batch* b, int nsteps, double t_end);
 /* Autotuner of the CTA shape: runs one step of every shape the library has
@@ -374,9 +388,15 @@ int es_batch_last_error(es_batch* b, char* buf, int len);
  * ES_STATIC_MAX_NODES nodes are rejected with ES_ERR_ARG.  The call allocates
  * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  *
- * The first call on a device looks up the scratch array's device address and
- * sets the stage kernel's shared-memory attribute (with that device current);
- * make that first call before any stream capture.  Every call then clears the
+ * The first call on a device does that device's set-up, with it current: it
+ * looks up the scratch array's device address and sets the stage kernel's
+ * shared-memory attribute.  Under CUDA's lazy module loading (the default) that
+ * is also when the driver loads the library's modules, and with them reserves
+ * the scratch array, so the first call on each device can itself take device
+ * memory.  Make it during start-up, before the program stops allocating and
+ * before any stream capture (or set CUDA_MODULE_LOADING=EAGER so the modules
+ * and the array are loaded when the context is created).  es_params.tile picks
+ * the 2D stage tile as in es_create (0: the default shape).  Every call then clears the
  * status word, launches on `stream` and synchronises it to read the status
  * back: the return value is ES_OK, ES_ERR_ARG, ES_ERR_CUDA, or a device status
  * such as ES_ERR_INADMISSIBLE.  All calls share the one scratch array and it

@@ -57,7 +57,7 @@ class Scheme:
     dim: int = 1
     w: int = 3                                   # EC order 2w (eq. ECFlux_curv_2p)
     weno_gammas: tuple = (0.005, 0.045, 0.95)    # (1-pt, 3-pt, 5-pt) linear weights (Sec. 5)
-    weno_eps: float = 1e-12
+    weno_eps: float = 1e-6                       # epsilon of the nonlinear weights (paper silent)
     sign_tol: float = 1e-12                      # |[[W]]| below this relative size counts as 0 in Y
     dissipation: bool = True                     # False: the EC scheme alone
     bc: tuple = (PERIODIC,)                      # per direction xi_1, xi_2, xi_3

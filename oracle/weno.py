@@ -20,7 +20,15 @@ averages:
 
 Reading of the weights (the paper lists lambda_0..2 without naming the
 stencils): the dominant 0.95 goes to the 5-point stencil, 0.045 to the
-3-point and 0.005 to the 1-point stencil.  Parity of the nonlinear weights is
+3-point and 0.005 to the 1-point stencil.  eps = 1e-6 (Jiang and Shu's value;
+the paper gives none).  The acoustic components of W = R^T T V for a smooth
+entropy wave are flat at the face (R's face state makes R^T dV/dx vanish
+there), so W_{i+1} = W_i to second order and beta_1 falls to O(h^6) while
+beta_3 is O(h^4); with eps far below beta_3 the weights then drift to the
+1-point value and the reconstruction loses orders until the mesh is fine.
+With linear weights 1/3 each (Example 5.6) a 1e-12 eps left the 2D
+operator at order 2 to 3 up to 128^2; with 1e-6 it reaches fifth order from
+about 64^2.  Parity of the nonlinear weights is
 unpinned: the cited paper is not available; the pins are the linear limit,
 exactness on constants and the design order.
 """
@@ -108,7 +116,7 @@ _B2 = smoothness_matrix(_STENCILS[1])
 _B3 = smoothness_matrix(_STENCILS[2])
 
 
-def mr_weno5(w, gammas=(0.005, 0.045, 0.95), eps=1e-12):
+def mr_weno5(w, gammas=(0.005, 0.045, 0.95), eps=1e-6):
     """Reconstruct the value at x_{i+1/2} from w = (w_{i-2}, ..., w_{i+2}) (leading axis of length 5).
 
     gammas = (1-point, 3-point, 5-point) linear weights.

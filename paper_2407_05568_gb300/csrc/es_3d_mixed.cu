@@ -22,6 +22,8 @@ namespace mixed3 {
 using mixed::df;
 using mixed::df_add;
 using mixed::df_add_f;
+using mixed::df_diff;
+using mixed::df_second_diff;
 using mixed::df_mul;
 using mixed::df_mul_f;
 using mixed::df_recip;
@@ -654,6 +656,8 @@ __device__ __forceinline__ float warp_min_f(float v) {
 
 // the raw monitor terms of eq. van der Waalsmonitor (or the smooth-test monitor) from the
 // float density and G: central first and second differences along each direction
+// rhoF, GF: (hi, lo) float planes of the density and G (k_mon_fields_f); the differences of neighbours
+// are taken in double-float arithmetic and then rounded
 __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
                               float* t2, DevScalars* d) {
     const int N = g.n[0] * g.n[1] * g.n[2];
@@ -661,15 +665,16 @@ __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, cons
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         int ii[3];
         split3(g, id, ii);
-        const float r0 = rhoF[id], G0 = GF[id];
+        const df r0 = {rhoF[id], rhoF[N + id]}, G0 = {GF[id], GF[N + id]};
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float h = float(g.inv_dxi[k]);
             const int ip = nb3(g, id, ii[k], k, 1), im = nb3(g, id, ii[k], k, -1);
-            const float rp = rhoF[ip], rm = rhoF[im], Gp = GF[ip], Gm = GF[im];
-            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
-            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
+            const df rp = {rhoF[ip], rhoF[N + ip]}, rm = {rhoF[im], rhoF[N + im]};
+            const df Gp = {GF[ip], GF[N + ip]}, Gm = {GF[im], GF[N + im]};
+            const float a = df_diff(rp, rm) * 0.5f * h, b = df_diff(Gp, Gm) * 0.5f * h;
+            const float c = df_second_diff(Gp, G0, Gm) * h * h, e = df_second_diff(rp, r0, rm) * h * h;
             gr += a * a;
             gg += b * b;
             lg += c * c;

@@ -33,7 +33,7 @@ template <int BT>
 struct BatchShape {
     static constexpr int BXC = BT - 2;
     using TB = TileF<1, BXC, 1, BT>;
-    static constexpr int MIN_BLOCKS = BT >= 512 ? 1 : 512 / BT;
+    static constexpr int MIN_BLOCKS = BT >= 512 ? 1 : 768 / BT;     // 24 warps per SM (80 registers) below 512
 };
 
 __device__ __forceinline__ float block_max_f(float v, float* red) {
@@ -116,11 +116,17 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
                 m = fmaxf(m, c2 > 0.0f ? lam : 3.0e38f);
                 if (B.moving) {
                     // monitor fields: rho and the fundamental derivative G in double-float arithmetic from the
-                    // (hi, lo) state planes (near the critical point p_nunu cancels to a small difference)
+                    // (hi, lo) state planes (near the critical point p_nunu cancels to a small difference); the
+                    // low parts wait in om0 / om1 (free until omega is formed) for the monitor's differences
                     const size_t q = off + i;
                     const df mom[1] = {{B.JU[ntot + q], B.JU[4 * ntot + q]}};
-                    rho_G_df({B.JU[q], B.JU[3 * ntot + q]}, mom, 1, {B.JU[2 * ntot + q], B.JU[5 * ntot + q]},
-                             {B.J[q], B.J[ntot + q]}, B.gdf, &rhoF[i], &GF[i]);
+                    df r2, G2;
+                    rho_G_df2({B.JU[q], B.JU[3 * ntot + q]}, mom, 1, {B.JU[2 * ntot + q], B.JU[5 * ntot + q]},
+                              {B.J[q], B.J[ntot + q]}, B.gdf, &r2, &G2);
+                    rhoF[i] = r2.hi;
+                    om0[i] = r2.lo;
+                    GF[i] = G2.hi;
+                    om1[i] = G2.lo;
                 }
             }
             m = block_max_f(m, red);
@@ -134,10 +140,14 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
             if (B.moving) {
                 float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
                 for (int i = tid; i < L; i += BT) {
+                    // differences of neighbours from the double-float fields (block_max_f's barriers above
+                    // order the writes of the fields before these reads), then rounded
                     const int ip = clampi(i + 1, L), im = clampi(i - 1, L);
-                    const float gr = 0.5f * (rhoF[ip] - rhoF[im]) * idxi;
-                    const float gg = 0.5f * (GF[ip] - GF[im]) * idxi;
-                    const float lg = (GF[ip] - 2.0f * GF[i] + GF[im]) * idxi * idxi;
+                    const df rp = {rhoF[ip], om0[ip]}, rm = {rhoF[im], om0[im]};
+                    const df Gp = {GF[ip], om1[ip]}, G0 = {GF[i], om1[i]}, Gm = {GF[im], om1[im]};
+                    const float gr = 0.5f * df_diff(rp, rm) * idxi;
+                    const float gg = 0.5f * df_diff(Gp, Gm) * idxi;
+                    const float lg = df_second_diff(Gp, G0, Gm) * idxi * idxi;
                     const float a0 = gr * gr, a1 = B.kappa >= 2 ? gg * gg : 0.0f, a2 = lg * lg;
                     t0[i] = a0;
                     t1[i] = a1;
@@ -162,18 +172,35 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
                     __syncthreads();
                     float* tmp = om; om = ot; ot = tmp;
                 }
-                // Jacobi sweeps: x_i = (w+ x_{i+1} + w- x_{i-1})/(w+ + w-), with x = i dxi + d
-                const float* din = d;
-                float* dout = da;
-                for (int k = 0; k < B.sweeps; ++k) {
-                    for (int i = tid; i < L; i += BT) {
-                        if (i == 0 || i == L - 1) {
-                            dout[i] = din[i];
-                        } else {
-                            const float wp = 0.5f * (om[i] + om[i + 1]), wm = 0.5f * (om[i] + om[i - 1]);
-                            dout[i] = (wp * (dxi + din[i + 1]) + wm * (din[i - 1] - dxi)) / (wp + wm);
-                        }
+                // Jacobi sweeps x_i <- (w+ x_{i+1} + w- x_{i-1})/(w+ + w-), written for the change
+                // delta = x - x^n from the step's mesh: with a+- = w+-/(w+ + w-) and the constant part
+                // g_i = a+ (x^n_{i+1} - x^n_i) + a- (x^n_{i-1} - x^n_i), formed once per solve from the
+                // spacings (dxi + d_{i+1} - d_i),
+                //   delta_i <- g_i + a+ delta_{i+1} + a- delta_{i-1},  delta = 0 at the fixed ends.
+                // A sweep then rounds the small change, not the displacement d (up to a third of the
+                // domain), and the mesh velocity needs no difference of two displacements.
+                float* ap = t0;
+                float* gc = t1;
+                for (int i = tid; i < L; i += BT) {
+                    if (i == 0 || i == L - 1) {
+                        ap[i] = 0.0f;
+                        gc[i] = 0.0f;
+                    } else {
+                        const float wp = 0.5f * (om[i] + om[i + 1]), wm = 0.5f * (om[i] + om[i - 1]);
+                        const float a = wp / (wp + wm);
+                        ap[i] = a;
+                        gc[i] = a * (dxi + d[i + 1] - d[i]) - (1.0f - a) * (dxi + d[i] - d[i - 1]);
                     }
+                    da[i] = 0.0f;
+                }
+                __syncthreads();
+                const float* din = da;
+                float* dout = db;
+                for (int k = 0; k < B.sweeps; ++k) {
+                    for (int i = tid; i < L; i += BT)
+                        dout[i] = (i == 0 || i == L - 1)
+                                      ? 0.0f
+                                      : gc[i] + ap[i] * din[i + 1] + (1.0f - ap[i]) * din[i - 1];
                     __syncthreads();
                     din = dout;
                     dout = (dout == da) ? db : da;
@@ -181,13 +208,13 @@ __global__ void __launch_bounds__(BT, BatchShape<BT>::MIN_BLOCKS) batch_kernel(B
                 // limiter: each node moves at most half of its spacing towards its neighbour
                 float g = 1.0f;
                 for (int i = tid; i < L; i += BT) {
-                    const float del = din[i] - d[i];
+                    const float del = din[i];
                     if (del < 0.0f && i > 0) g = fminf(g, -(dxi + d[i] - d[i - 1]) / (2.0f * del));
                     else if (del > 0.0f && i < L - 1) g = fminf(g, (dxi + d[i + 1] - d[i]) / (2.0f * del));
                 }
                 g = block_min_f(g, red);
                 const float fv = g / dtf;
-                for (int i = tid; i < L; i += BT) xd[i] = fv * (din[i] - d[i]);
+                for (int i = tid; i < L; i += BT) xd[i] = fv * din[i];
                 // eq. cfl with this mesh velocity (J xi_t = -xdot): dt = min(dt, CFL / max (|v - xdot| + c) / (J dxi));
                 // xdot keeps its value, so the mesh moves less than Delta_gamma allows
                 float mv = 0.0f;
@@ -308,6 +335,31 @@ __global__ void k_batch_set(BatchParams B, Gas Gd, const double* rho, const doub
         B.xdot[id] = 0.0f;
     }
     if (threadIdx.x == 0) B.tprob[p] = 0.0;
+}
+
+// conservative state, mesh and time of every problem: (JU, J) into (hi, lo) planes, x into the displacement
+// from the uniform mesh, the mesh velocity cleared
+__global__ void k_batch_set_state(BatchParams B, const double* JU, const double* J, const double* x,
+                                  const double* t) {
+    const int p = blockIdx.x;
+    const int L = B.lengths[p];
+    const size_t off = size_t(B.offsets[p]);
+    const size_t n = B.ntot;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const size_t id = off + i;
+        for (int c = 0; c < 3; ++c) {
+            const double v = JU[c * n + id];
+            const float hi = float(v);
+            B.JU[c * n + id] = hi;
+            B.JU[3 * n + c * n + id] = float(v - double(hi));
+        }
+        const float jh = float(J[id]);
+        B.J[id] = jh;
+        B.J[n + id] = float(J[id] - double(jh));
+        B.disp[id] = float(x[id] - double(i) / double(L - 1));
+        B.xdot[id] = 0.0f;
+    }
+    if (threadIdx.x == 0) B.tprob[p] = t[p];
 }
 
 __global__ void k_batch_get(BatchParams B, double* JU, double* J, double* x, double* t) {
@@ -522,6 +574,13 @@ int es_batch_set_prim(es_batch* b, const double* rho, const double* v, const dou
     gas_reciprocals(Gd);
     k_batch_set<<<b->B.nprob, 256, 0, b->stream>>>(b->B, Gd, rho, v, pr);
     BCK(cudaGetLastError(), "k_batch_set");
+    return ES_OK;
+}
+
+int es_batch_set_state(es_batch* b, const double* JU, const double* J, const double* x, const double* t) {
+    if (!b || !JU || !J || !x || !t) return ES_ERR_ARG;
+    k_batch_set_state<<<b->B.nprob, 256, 0, b->stream>>>(b->B, JU, J, x, t);
+    BCK(cudaGetLastError(), "k_batch_set_state");
     return ES_OK;
 }
 

@@ -78,14 +78,15 @@ inline GasDF gas_df(double a, double b, double R, double cv) {
 }
 
 // Density and fundamental derivative G = nu^3 p_nunu|_s / (2 c^2) (Sec. 1) from a double-float state
-// (mass, momenta, energy and J as (hi, lo) pairs).  With nu = 1/rho,
+// (mass, momenta, energy and J as (hi, lo) pairs), as double-float values.  With nu = 1/rho,
 //   G = [(1 + delta)(2 + delta) R T / (1 - b rho)^3 - 6 a rho] / (2 c^2),
 //   c^2 = (1 + delta) R T / (1 - b rho)^2 - 2 a rho.
 // Near the critical point each bracket is a difference of nearly equal terms (p_nunu: about 16 - 16 =
-// -0.02), which FP32 leaves with errors of 1e-5 in G; in double-float both keep ~1e-12.  The results
-// are rounded to float.
-__device__ __forceinline__ void rho_G_df(df m0, const df* mom, int dim, df E, df J, const GasDF& G, float* rho_out,
-                                         float* G_out) {
+// -0.02), which FP32 leaves with errors of 1e-5 in G; in double-float both keep ~1e-12.  The monitor
+// differentiates both fields, and neighbouring values agree to many digits where the flow is smooth, so
+// its differences are formed from these pairs too (df_diff, df_second_diff) before rounding to float.
+__device__ __forceinline__ void rho_G_df2(df m0, const df* mom, int dim, df E, df J, const GasDF& G, df* rho_out,
+                                          df* G_out) {
     const df iJ = df_recip(J);
     const df rho = df_mul(m0, iJ);
     const df irho = df_recip(rho);
@@ -103,8 +104,22 @@ __device__ __forceinline__ void rho_G_df(df m0, const df* mom, int dim, df E, df
     const df ar = df_mul(rho, a);
     const df c2 = df_add(df_mul({G.k1.hi, G.k1.lo}, TA), df_mul_f(df_neg(ar), 2.0f));
     const df pnn = df_add(df_mul({G.k2.hi, G.k2.lo}, df_mul(TA, iom)), df_mul_f(df_neg(ar), 6.0f));
-    *rho_out = rho.hi + rho.lo;
-    *G_out = (pnn.hi + pnn.lo) / (2.0f * (c2.hi + c2.lo));
+    *rho_out = rho;
+    *G_out = df_mul(pnn, df_recip(df_mul_f(c2, 2.0f)));
+}
+
+// the same, rounded to float
+__device__ __forceinline__ void rho_G_df(df m0, const df* mom, int dim, df E, df J, const GasDF& G, float* rho_out,
+                                         float* G_out) {
+    df r, g;
+    rho_G_df2(m0, mom, dim, E, J, G, &r, &g);
+    *rho_out = r.hi + r.lo;
+    *G_out = g.hi + g.lo;
+}
+
+// a_{i+1} - 2 a_i + a_{i-1} of double-float values, rounded to float
+__device__ __forceinline__ float df_second_diff(df ap, df a0, df am) {
+    return df_diff(df_add(ap, am), df_mul_f(a0, 2.0f));
 }
 
 }  // namespace mixed

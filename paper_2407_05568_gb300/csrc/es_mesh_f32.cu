@@ -155,26 +155,35 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
     if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], double(m));
 }
 
-// density and G = nu^3 p_nunu|_s / (2 c^2) at a node from the (hi, lo) state planes, G in double-float
+// density and G = nu^3 p_nunu|_s / (2 c^2) at a node from the (hi, lo) state planes, in double-float
 // arithmetic (near the critical point p_nunu is a difference of nearly equal terms: the EOS stays at
-// FP64-like accuracy there); the raw monitor terms need the neighbours
-__device__ __forceinline__ void mon_field_f(const GridParams& g, const GasF32& G, const float* JU, const float* J,
-                                            int N, size_t P, int id, float* rho_out, float* G_out) {
+// FP64-like accuracy there); the monitor's differences of neighbours are formed from these pairs
+__device__ __forceinline__ void mon_field_df(const GridParams& g, const GasF32& G, const float* JU, const float* J,
+                                             int N, size_t P, int id, mixed::df* rho_out, mixed::df* G_out) {
     using mixed::df;
     df mom[3];
     for (int k = 0; k < g.dim; ++k) mom[k] = {JU[(1 + k) * N + id], JU[P + (1 + k) * N + id]};
     const int ce = (g.dim + 1) * N + id;
-    mixed::rho_G_df({JU[id], JU[P + id]}, mom, g.dim, {JU[ce], JU[P + ce]}, {J[id], J[N + id]}, G.gdf, rho_out, G_out);
+    mixed::rho_G_df2({JU[id], JU[P + id]}, mom, g.dim, {JU[ce], JU[P + ce]}, {J[id], J[N + id]}, G.gdf, rho_out,
+                     G_out);
 }
 
+// density and G of every node as (hi, lo) float planes: rhoF and GF hold 2 N floats each, the low parts
+// N floats after the high parts
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
-        mon_field_f(g, G, JU, J, N, P, id, rhoF + id, GF + id);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        mixed::df r, G0;
+        mon_field_df(g, G, JU, J, N, P, id, &r, &G0);
+        rhoF[id] = r.hi;
+        rhoF[N + id] = r.lo;
+        GF[id] = G0.hi;
+        GF[N + id] = G0.lo;
+    }
 }
 
-// k_mon_fields_f and k_mon_terms_f in one pass: the density and G of the +-1 neighbours are
+// the monitor terms in one pass: the density and G of the +-1 neighbours are
 // recomputed from their state (a few float operations against a launch and a round trip of two
 // fields).  With do_dt, thread 0 also sets the step's dt from the CFL maximum (k_dt's work:
 // the CFL kernel has finished when this one starts).
@@ -186,19 +195,19 @@ __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        float r0, G0;
-        mon_field_f(g, G, JU, J, N, P, id, &r0, &G0);
+        mixed::df r0, G0;
+        mon_field_df(g, G, JU, J, N, P, id, &r0, &G0);
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
         for (int k = 0; k < g.dim; ++k) {
             const int di = k == 0, dj = k == 1;
             const float h = float(g.inv_dxi[k]);
             const int sp = (g.dim == 2 ? state_index(j + dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i + di, g.n1, g.bc[0]);
             const int sm = (g.dim == 2 ? state_index(j - dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i - di, g.n1, g.bc[0]);
-            float rp, Gp, rm, Gm;
-            mon_field_f(g, G, JU, J, N, P, sp, &rp, &Gp);
-            mon_field_f(g, G, JU, J, N, P, sm, &rm, &Gm);
-            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
-            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
+            mixed::df rp, Gp, rm, Gm;
+            mon_field_df(g, G, JU, J, N, P, sp, &rp, &Gp);
+            mon_field_df(g, G, JU, J, N, P, sm, &rm, &Gm);
+            const float a = mixed::df_diff(rp, rm) * 0.5f * h, b = mixed::df_diff(Gp, Gm) * 0.5f * h;
+            const float c = mixed::df_second_diff(Gp, G0, Gm) * h * h, e = mixed::df_second_diff(rp, r0, rm) * h * h;
             gr += a * a;
             gg += b * b;
             lg += c * c;
@@ -231,52 +240,6 @@ __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
     }
 }
 
-__global__ void k_mon_terms_f(GridParams g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
-                              float* t2, DevScalars* d) {
-    const int N = g.n1 * g.n2;
-    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const int i = id % g.n1, j = id / g.n1;
-        float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
-        for (int k = 0; k < g.dim; ++k) {
-            const int di = k == 0, dj = k == 1;
-            const float h = float(g.inv_dxi[k]);
-            const float rp = field_at_f(g, rhoF, i + di, j + dj), rm = field_at_f(g, rhoF, i - di, j - dj);
-            const float Gp = field_at_f(g, GF, i + di, j + dj), Gm = field_at_f(g, GF, i - di, j - dj);
-            const float r0 = rhoF[id], G0 = GF[id];
-            const float a = (rp - rm) * 0.5f * h, b = (Gp - Gm) * 0.5f * h;
-            const float c = (Gp - 2.0f * G0 + Gm) * h * h, e = (rp - 2.0f * r0 + rm) * h * h;
-            gr += a * a;
-            gg += b * b;
-            lg += c * c;
-            lr += e * e;
-        }
-        float v0, v1, v2;
-        if (mp.kind == ES_MONITOR_SMOOTH) {
-            v0 = sqrtf(gr);
-            v1 = 0.0f;
-            v2 = sqrtf(lr);
-        } else {
-            v0 = gr;
-            v1 = mp.kappa >= 2 ? gg : 0.0f;
-            v2 = lg;
-        }
-        t0[id] = v0;
-        t1[id] = v1;
-        t2[id] = v2;
-        m0 = fmaxf(m0, v0);
-        m1 = fmaxf(m1, v1);
-        m2 = fmaxf(m2, v2);
-    }
-    m0 = block_max_f32(m0);
-    m1 = block_max_f32(m1);
-    m2 = block_max_f32(m2);
-    if (threadIdx.x == 0) {
-        atomic_max_pos(&d->red[RED_MON0], double(m0));
-        atomic_max_pos(&d->red[RED_MON1], double(m1));
-        atomic_max_pos(&d->red[RED_MON2], double(m2));
-    }
-}
 
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega) {

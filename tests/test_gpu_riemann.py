@@ -4,13 +4,14 @@ Every step: the oracle's run gives the state at each t_n.  The kernels take one 
 redistribution, three RK stages) from that same state, and the result is compared with the oracle's next state.
 The FP64 form must agree to <= 1e-12 relative L1 in JU, J and x, on every one of the several hundred steps per
 problem, through the rarefaction shocks, the contact and the compressive shock.  The mixed form (FP32 bulk;
-double-float state, jumps and monitor G) is held to a per-step bar stated below.
+double-float state, jumps and monitor fields) is held to a per-step bar stated below.
 
-Free runs: both sides advance independently from t = 0 to the final time.  These discontinuous moving-mesh runs
-are sensitive to rounding.  The oracle itself, with its initial state perturbed by 1e-14 (relative), ends 1e-5 to
-1e-2 (relative L1) away from its own unperturbed run, depending on the problem and the perturbation.  The bar is
-therefore relative to that spread: the kernels' final state lies within 10 times the largest spread of three
-perturbed oracle runs.  On the fixed mesh (UM) the spread is ~1e-6.
+Free runs: both sides advance independently from t = 0 to the final time, and the bar is what the problem does with
+errors of the form's own size.  The oracle is run three more times with its initial JU perturbed by a seeded
+relative amount: 1e-14 (FP64 rounding) for the FP64 form, 1e-7 (FP32 rounding, which the mixed form's bulk incurs
+every stage) for the mixed form.  The kernels' final state must lie within 10 times the largest distance of those
+perturbed runs from the unperturbed one.  On these discontinuous moving-mesh runs the 1e-7 spread is 1e-6 to 1e-2,
+so the mixed form cannot meet the 1e-5 final-time bar of smooth problems there; its per-step bar holds instead.
 """
 import functools
 
@@ -20,7 +21,7 @@ import pytest
 from oracle import stepper
 from paper_2407_05568_gb300 import workloads as wl
 
-from sides import gpu_setup, oracle_setup, rel_l1, to_np
+from sides import gpu_setup, oracle_setup, pool_map, rel_l1, riemann_perturbed_final, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -57,18 +58,12 @@ def _trajectory(name, variant):
 
 
 @functools.lru_cache(maxsize=None)
-def _spread(name, variant):
+def _spread(name, variant, size):
     """Largest final-time distance (relative L1 over JU, J, x) of three oracle runs whose initial JU is perturbed by
-    1e-14 (relative, seeded normal) from the unperturbed run."""
-    w = _workload(name, variant)
+    `size` (relative, seeded normal) from the unperturbed run."""
     ref = _trajectory(name, variant)[-1]
-    worst = 0.0
-    for seed in (1, 2, 3):
-        sch, mc, JU, J, x = oracle_setup(w)
-        JU = JU * (1.0 + 1e-14 * np.random.default_rng(seed).standard_normal(JU.shape))
-        JU, J, x, _ = stepper.run(sch, mc, JU, J, x, w["t_end"], w["cfl"])
-        worst = max(worst, rel_l1(JU, ref[0]), rel_l1(J, ref[1]), rel_l1(x, ref[2]))
-    return worst
+    finals = pool_map(riemann_perturbed_final, [(name, variant, SIZES[variant], size, seed) for seed in (1, 2, 3)])
+    return max(max(rel_l1(JU, ref[0]), rel_l1(J, ref[1]), rel_l1(x, ref[2])) for JU, J, x in finals)
 
 
 def _load(JU_g, J_g, x_g, JU, J, x, mixed):
@@ -139,6 +134,6 @@ def _free_run(name, variant, precision):
 @pytest.mark.parametrize("name,variant", CASES)
 def test_free_run_to_final_time_within_the_oracles_own_spread(name, variant, precision):
     err = _free_run(name, variant, precision)
-    spread = _spread(name, variant)
+    spread = _spread(name, variant, 1e-14 if precision == "fp64" else 1e-7)
     assert spread > 0.0
     assert err < 10.0 * spread, (err, spread)
