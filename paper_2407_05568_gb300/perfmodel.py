@@ -1,36 +1,27 @@
 """Algorithmic work per node and RK stage of the fused stage kernel, and the peaks it is compared to.
 
-Operation counts are taken from the formulas the kernel evaluates (es_stage.cu),
-counting one operation per +, -, *, /, sqrt and log and two per fused
-multiply-add.  They count each algorithmic quantity once per node (node data),
-three pairs per node and direction (the pair fluxes F(U_i, U_{i+m}), m = 1..3)
-and one face per node and direction; the halo recomputation of a tiled kernel
-is not algorithmic work and is not counted.
+The counts are the oracle's: oracle/opcount.py runs one RK stage of the oracle on arrays that tally every
+elementwise floating-point operation (+, -, *, /, square roots, logarithms and other transcendental functions one
+each, an FMA two, selections and comparisons none, contractions one multiply and one add per term), divides the
+pair fluxes' operations by their reuse (the oracle evaluates each pair once per face that uses it, the algorithm
+once), and takes the per-node coefficient of a fit over three mesh sizes, which removes the ghost nodes' work.
+tests/test_oracle_opcount.py recomputes them against the numbers below.
 
-Per node (2D):
-  node data      61   primitive state, 1/T, 1/(1 - b rho), four logarithms, entropy variables
-  metrics        34   two 6th-order differences per direction and J xi_t
-  pair flux     120   x 6 (3 per direction): means, three inverse log means
-                      (series branch 17, log branch 4; a typical mix), D, U~_1, F~_1,
-                      and the contraction with the face metrics
-  face flux    1470   x 2: the alpha-combination of six pairs (72), the face
-                      eigen-system (~110), six projections W = R^T T V (192),
-                      eight MR-WENO5 reconstructions (129 each = 1032),
-                      sign switch and back-projection (~50)
-  divergence     55   two directions and the Shu-Osher combination
-  total        3810
-Per node (1D): node 44, metrics 2, pair 75 x 3, face 1000 x 1, divergence 20 -> 1291.
+They exceed the count of the kernel's own formulas (1291 in 1D, 3810 in 2D: node data 61, metrics 34, 6 pairs x 120,
+2 faces x 1470, divergence and RK 55), which shares node data between the two directions, forms one rotation per
+node and evaluates the smoothness indicators from differences; the oracle's plain evaluation is the algorithm's
+work, the kernel's count is what it issues (plus halo recomputation).
 """
 
 COUNTS = {
-    2: dict(node=61, metrics=34, pair=120, pairs=6, face=1470, faces=2, rk=55),
-    1: dict(node=44, metrics=2, pair=75, pairs=3, face=1000, faces=1, rk=20),
+    2: dict(total=4837, pair=1212),
+    1: dict(total=1707, pair=480),
 }
+KERNEL_FORMULA_COUNTS = {2: 3810, 1: 1291}
 
 
 def flops_per_node_stage(dim):
-    c = COUNTS[dim]
-    return c["node"] + c["metrics"] + c["pair"] * c["pairs"] + c["face"] * c["faces"] + c["rk"]
+    return COUNTS[dim]["total"]
 
 
 def stage_flops(dim, nodes, precision="fp64"):

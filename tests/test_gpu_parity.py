@@ -416,3 +416,13 @@ def test_step_parity_jacobi_tolerance_graph_loop():
     assert solves == 2 and sw == sweeps_o and sw < 80
     assert rel_l1(to_np(JU), JU_o) < 2e-12
     assert rel_l1(to_np(xt), x_o) < 2e-12
+
+
+def test_measured_alu_peaks():
+    """The FMA-chain probe (the ALU roofline's denominators) reports rates of the right size for a GB300:
+    FP32 near 152 SMs x 128 lanes x 2 x clock (~80 TFLOP/s at 2.07 GHz), FP64 near 1 TFLOP/s."""
+    from paper_2407_05568_gb300 import es
+    f64, f32 = es.es_selftest_peaks()
+    assert 40.0 < f32 < 100.0, f32
+    assert 0.4 < f64 < 2.5, f64
+    assert f32 > 30.0 * f64
