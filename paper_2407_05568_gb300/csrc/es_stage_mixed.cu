@@ -34,8 +34,10 @@ namespace {
 
 using namespace mixed;
 
+// resident CTAs per SM the register allocation must allow: 5 x 160 or 4 x 192 threads (24 warps; 72 and 80
+// registers, no spills), 2 x 288, 1 x 544
 template <int DIM, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT, NT <= 192 ? 3 : (NT <= 320 ? 2 : 1)) stage_kernel_mixed(StageParams P) {
+__global__ void __launch_bounds__(NT, NT <= 160 ? 5 : (NT <= 192 ? 4 : (NT <= 320 ? 2 : 1))) stage_kernel_mixed(StageParams P) {
     extern __shared__ float smemf[];
     const int ntx = (P.n1 + BX - 1) / BX;
     const int i0 = (blockIdx.x % ntx) * BX;
