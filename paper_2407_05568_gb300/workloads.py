@@ -14,6 +14,7 @@ import numpy as np
 
 UNITS_A = dict(a=3.0, b=1.0 / 3.0, R=8.0 / 3.0, cv=(8.0 / 3.0) / 0.0125)
 IDEAL_14 = dict(a=0.0, b=0.0, R=1.0, cv=1.0 / 0.4)
+VORTEX_BOX = 20.0      # side of the periodic box of the isentropic vortex (see isentropic_vortex)
 
 # Table 5.1 (Example 5.2): (rho_l, v_l, p_l, rho_r, v_r, p_r)
 TABLE_5_1 = {
@@ -218,7 +219,7 @@ def mm1(w):
     return dict(w, mesh=m)
 
 
-def vortex_density(X, Y, t=0.0, eps_v=5.0, period=10.0, center=5.0):
+def vortex_density(X, Y, t=0.0, eps_v=5.0, period=VORTEX_BOX, center=0.5 * VORTEX_BOX):
     """Density of the isentropic vortex (gamma = 1.4) carried by the mean flow (1, 1) to time t:
     the initial field at (x - t, y - t), wrapped into the periodic box."""
     gam = 1.4
@@ -229,22 +230,26 @@ def vortex_density(X, Y, t=0.0, eps_v=5.0, period=10.0, center=5.0):
     return T ** (1.0 / (gam - 1.0))
 
 
-def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0):
-    """Ideal-gas (gamma = 1.4) isentropic vortex on [0,10]^2, periodic, mean flow (1, 1)
+def isentropic_vortex(n=64, t_end=1.0, cfl=0.4, eps_v=5.0, box=VORTEX_BOX):
+    """Ideal-gas (gamma = 1.4) isentropic vortex centred in the periodic box [0, box)^2, mean flow (1, 1)
     (Shu 1998): dT = -(gamma-1) eps^2 e^(1-r^2) / (8 gamma pi^2),
-    dv = eps/(2 pi) e^((1-r^2)/2) (-ybar, xbar), rho = T^(1/(gamma-1)), p = rho T."""
+    dv = eps/(2 pi) e^((1-r^2)/2) (-ybar, xbar), rho = T^(1/(gamma-1)), p = rho T.  The closed form is an
+    isolated vortex: in the usual box of side 10 its velocity perturbation is still e^-12 of its peak at the
+    edges, and that seam between periodic copies converges at first order, below the scheme's error only
+    down to about 1e-8; the default box of side 20 leaves e^-49.5 there."""
     gam = 1.4
-    x1, d = uniform_nodes(n, 0.0, 10.0, True)
+    c = 0.5 * box
+    x1, d = uniform_nodes(n, 0.0, box, True)
     X, Yc = np.meshgrid(x1, x1)
-    xb = X - 5.0
-    yb = Yc - 5.0
+    xb = X - c
+    yb = Yc - c
     r2 = xb**2 + yb**2
     T = 1.0 - (gam - 1.0) * eps_v**2 * np.exp(1.0 - r2) / (8.0 * gam * np.pi**2)
     rho = T ** (1.0 / (gam - 1.0))
     fac = eps_v / (2.0 * np.pi) * np.exp(0.5 * (1.0 - r2))
     v = np.stack([1.0 - fac * yb, 1.0 + fac * xb])
     return dict(gas=IDEAL_14, dim=2, n=(n, n), dxi=(d, d), bc=("periodic", "periodic"),
-                period=(10.0, 10.0), x=np.stack([X, Yc]), rho=rho, v=v, p=rho * T,
+                period=(box, box), x=np.stack([X, Yc]), rho=rho, v=v, p=rho * T,
                 t_end=t_end, cfl=cfl, moving=False)
 
 
