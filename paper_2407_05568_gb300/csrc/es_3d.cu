@@ -608,11 +608,29 @@ __global__ void __launch_bounds__(NT, W >= 16 ? 1 : (NT <= 96 ? 3 : 2)) k3_dir(D
         else { i1 = a; i2 = b; i3 = s; }
         const size_t id = idx3(g, i1, i2, i3);
         const int fm = line * (LB + 1) + pos;
+        // every global operand of the node is loaded before the first global store (a store may alias a later
+        // load as far as the compiler knows, which would serialise one round trip per component)
+        double rh[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        double un[6], us[6];
+        if (!P.first) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) rh[c] = P.RH[c * N + id];
+        }
+        const bool combine = P.last && P.mode != 1;
+        if (combine) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                un[c] = P.JUn[c * N + id];
+                us[c] = P.JUs[c * N + id];
+            }
+            un[5] = P.Jn[id];
+            us[5] = P.Js[id];
+        }
         double acc[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             acc[c] = -(FB[c * NFc + fm + 1] - FB[c * NFc + fm]) * inv;
-            if (!P.first) acc[c] += P.RH[c * N + id];
+            if (!P.first) acc[c] += rh[c];
         }
         if (!P.last) {
 #pragma unroll
@@ -623,9 +641,8 @@ __global__ void __launch_bounds__(NT, W >= 16 ? 1 : (NT <= 96 ? 3 : 2)) k3_dir(D
             P.Jo[id] = acc[5];
         } else {
 #pragma unroll
-            for (int c = 0; c < 5; ++c)
-                P.JUo[c * N + id] = P.ca * P.JUn[c * N + id] + P.cb * (P.JUs[c * N + id] + dt * acc[c]);
-            const double Jnew = P.ca * P.Jn[id] + P.cb * (P.Js[id] + dt * acc[5]);
+            for (int c = 0; c < 5; ++c) P.JUo[c * N + id] = P.ca * un[c] + P.cb * (us[c] + dt * acc[c]);
+            const double Jnew = P.ca * un[5] + P.cb * (us[5] + dt * acc[5]);
             P.Jo[id] = Jnew;
             if (!(Jnew > 0.0)) raise_error(P.status, ES_ERR_MESH, int(id));
         }

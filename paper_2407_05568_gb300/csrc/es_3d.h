@@ -39,6 +39,11 @@ struct Ctx3 {
     // mesh scratch (the context's buffers)
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1, *xa, *xb;
     float* gc;                // mixed form: the sweeps' constant term g [3][N]
+    // mixed form: tensor maps (CUtensorMap, 128 bytes) of the float node fields for the TMA-staged xi_2 and
+    // xi_3 pencils, per direction and pencil shape; state 0 = not built yet, 1 = built, -1 = plain loads
+    int no_tma;               // 1: plain loads only (tile D3_NSHAPES + k)
+    unsigned char tmap[2][4][128];
+    int tmap_state[2][4];
 };
 
 // arguments of one operator evaluation / RK stage
@@ -54,6 +59,7 @@ struct Stage3 {
 };
 
 constexpr int D3_NSHAPES = 4;
+static_assert(D3_NSHAPES == 4, "Ctx3::tmap holds one tensor map per direction and pencil shape");
 cudaError_t d3_alloc(Ctx3* d);
 void d3_free(Ctx3* d);
 cudaError_t d3_prepare();

@@ -8,7 +8,10 @@
 // as floats (with the low parts), and the metrics are the FP64 cross-form metrics of es_3d.cu
 // rounded to float at load.  The right-hand sides are accumulated over the
 // three directions in float and the Shu-Osher combination is done in double-float.
+#include <cuda.h>            // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <string.h>
 
 #include "es_3d.h"
 #include "es_device.cuh"
@@ -300,6 +303,7 @@ struct Dir3FParams {
     const double* xdot;       // nullable
     float* RH;                // accumulated right-hand sides [6][N] (float)
     int first, last;
+    int tma;                  // xi_2 / xi_3: node fields staged by TMA (persistent grid)
     int mode;
     float ca, cb, ca_lo, cb_lo;
     double dt_host;
@@ -318,14 +322,66 @@ struct PencilF {
     static constexpr int NF = W * (LB + 1);
     static constexpr int NJ = W * (LB + 5);
     static constexpr size_t SMEM = sizeof(float) * (size_t(MS_COUNT) * NB + 5 * NP + 6 * NF + 5 * NJ);
+    // TMA staging of the node fields of a xi_2 / xi_3 pencil: [MF_COUNT][LB + 6][W] floats, in 128-byte units
+    static constexpr int STG = (W * (LB + 6) * MF_COUNT + 31) / 32 * 32;
+    static constexpr size_t STG_BYTES = sizeof(float) * size_t(W) * (LB + 6) * MF_COUNT;
 };
 
+// ---------------------------------------------------------------- TMA staging
+// The xi_2 and xi_3 kernels run persistent: a CTA takes pencils p, p + gridDim.x, ... and, while it
+// computes one, the tensor-memory accelerator copies the next pencil's node fields (a box of W lines
+// along xi_1 x (LB + 6) nodes along xi_k x all MF_COUNT field planes, one cp.async.bulk.tensor) into
+// the staging buffer.  The box starts at xi_1 = a0, a multiple of W >= 4 floats (16 bytes), and the
+// field planes have a row pitch of n1 floats, a multiple of 4 (checked when the map is built); the
+// box may reach past the mesh along xi_k and xi_1, where the copy fills zeros: those nodes are the
+// ghosts and the clamped lines, which the fill phase takes by plain loads or from the clamped line.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bounded wait for the phase of the given parity; false when it did not complete in 2^20 polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// one thread: the copy of pencil (a0, b, s0) into stg, completing on bar
+template <int K, int LB>
+__device__ __forceinline__ void stage_pencil(float* stg, const CUtensorMap* map, unsigned long long* bar,
+                                             uint32_t bytes, int a0, int b, int s0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");    // the fill phase's reads of stg come first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    const int c1 = K == 1 ? s0 - 3 : b, c2 = K == 1 ? b : s0 - 3;
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(stg)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(a0), "r"(c1), "r"(c2), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <int K, int LB, int W, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k3_dir_f(Dir3FParams P) {
+__global__ void __launch_bounds__(NT, MINB) k3_dir_f(const __grid_constant__ Dir3FParams P,
+                                                     const __grid_constant__ CUtensorMap tmap) {
     using PC = PencilF<LB, W>;
     constexpr int LS = PC::LS, NB = PC::NB, NP = PC::NP, NFc = PC::NF, NJ = PC::NJ;
-    extern __shared__ float smf[];
-    float* S = smf;
+    extern __shared__ __align__(128) float smf[];
+    __shared__ __align__(8) unsigned long long bar;
+    const bool tma = K != 0 && P.tma;
+    float* STG = smf;
+    float* S = smf + (tma ? PC::STG : 0);
     float* PB = S + MS_COUNT * NB;
     float* FB = PB + 5 * NP;
     float* JB = FB + 6 * NFc;
@@ -336,12 +392,7 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(Dir3FParams P) {
     const int nB = K == 2 ? g.n[1] : g.n[2];
     const int nseg = (nk + LB - 1) / LB;
     const int ngA = (nA + W - 1) / W;
-    const int seg = blockIdx.x % nseg;
-    const int grp = blockIdx.x / nseg;
-    const int a0 = (grp % ngA) * W;
-    const int b = grp / ngA;
-    if (b >= nB) return;
-    const int s0 = seg * LB;
+    const int total = nseg * ngA * nB;
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     const double dtd = P.dt_dev ? *P.dt_dev : P.dt_host;
     if (P.mode == 0 && P.dt_dev && dtd == 0.0) return;   // finished run
@@ -349,187 +400,254 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(Dir3FParams P) {
     const int M1 = g.n[0] + (K == 0 ? 6 : 0), M2 = g.n[1] + (K == 1 ? 6 : 0), M3 = g.n[2] + (K == 2 ? 6 : 0);
     const size_t M = size_t(M1) * M2 * M3;
     const GasF& G = P.gas;
+    const uint32_t stg_bytes = uint32_t(PC::STG_BYTES);
+    if (tma) {
+        if (tid == 0) {
+            mbar_init(&bar);
+            if (int(blockIdx.x) < total) {
+                const int p = blockIdx.x, grp = p / nseg;
+                stage_pencil<K, LB>(STG, &tmap, &bar, stg_bytes, (grp % ngA) * W, grp / ngA, (p % nseg) * LB);
+            }
+        }
+        __syncthreads();
+    }
 
-    // ---- A: node fields and metrics of the pencils
-    for (int t = tid; t < W * (LB + 6); t += NT) {
-        int line, q;
-        if (K == 0) { line = t / (LB + 6); q = t % (LB + 6); }
-        else { q = t / W; line = t % W; }
-        int a = a0 + line;
-        if (a > nA - 1) a = nA - 1;
-        const int s = s0 + q - 3;
-        const int ss = state_index(s, nk, g.bc[K]);
-        int i1, i2, i3, j1, j2, j3;
-        if (K == 0) { i1 = ss; i2 = a; i3 = b; }
-        else if (K == 1) { i1 = a; i2 = ss; i3 = b; }
-        else { i1 = a; i2 = b; i3 = ss; }
-        const size_t id = idx3(g, i1, i2, i3);
-        const int bx = line * LS + q;
-        float v[MF_COUNT];                                   // all loads in flight before the stores
-#pragma unroll
-        for (int f = 0; f < MF_COUNT; ++f) v[f] = P.NF[f * N + id];
-#pragma unroll
-        for (int f = 0; f < MF_COUNT; ++f) S[f * NB + bx] = v[f];
-        int se = s + 3;
-        se = se < 0 ? 0 : (se > nk + 5 ? nk + 5 : se);
-        if (K == 0) { j1 = se; j2 = a; j3 = b; }
-        else if (K == 1) { j1 = a; j2 = se; j3 = b; }
-        else { j1 = a; j2 = b; j3 = se; }
-        const size_t mi = (size_t(j3) * M2 + j2) * M1 + j1;
-        const double nx = P.NK[mi], ny = P.NK[M + mi], nz = P.NK[2 * M + mi];
-        S[M_NX * NB + bx] = float(nx);
-        S[M_NY * NB + bx] = float(ny);
-        S[M_NZ * NB + bx] = float(nz);
-        double xt = 0.0;
-        if (P.xdot) {
-            double xd[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const GhostTerms tk = ghost_terms(s, nk, g.bc[K], c != K);
-                for (int u = 0; u < tk.nterm; ++u) {
-                    int k1 = i1, k2 = i2, k3 = i3;
-                    if (K == 0) k1 = tk.idx[u];
-                    else if (K == 1) k2 = tk.idx[u];
-                    else k3 = tk.idx[u];
-                    xd[c] += tk.w[u] * P.xdot[c * N + idx3(g, k1, k2, k3)];
+    int iter = 0;
+    for (int pen = blockIdx.x; pen < total; pen += tma ? int(gridDim.x) : total, ++iter) {   // plain: once
+        const int seg = pen % nseg;
+        const int grp = pen / nseg;
+        const int a0 = (grp % ngA) * W;
+        const int b = grp / ngA;
+        const int s0 = seg * LB;
+        if (tma) {
+            // every thread waits for the copy itself (the acquire makes it visible); the CTA leaves together if
+            // it did not arrive
+            const bool ok = mbar_wait(&bar, uint32_t(iter & 1));
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) {
+                    raise_error(P.status, ES_ERR_TIMEOUT, pen);
+                    mbar_wait(&bar, uint32_t(iter & 1));         // the copy in flight, once more with the limit
                 }
+                return;
             }
-            xt = -(xd[0] * nx + xd[1] * ny + xd[2] * nz);
         }
-        S[M_XT * NB + bx] = float(xt);
-    }
-    __syncthreads();
 
-    // ---- C: pair fluxes, and B: neighbour jumps V_{q+1} - V_q, q = 0 .. LB+4 (eq. jumpV)
-    for (int t = tid; t < NP; t += NT) {
-        const int line = t / PC::PL, kk = t % PC::PL;
-        int m, q;
-        if (kk < LB + 1) { m = 1; q = 2 + kk; }
-        else if (kk < 2 * LB + 3) { m = 2; q = 1 + (kk - LB - 1); }
-        else { m = 3; q = kk - 2 * LB - 3; }
-        const int l = line * LS + q, r = l + m;
-        const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + r]);
-        const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + r]);
-        const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + r]);
-        const float xt = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + r]);
-        float f[5];
-        pair_flux3_f(S, NB, l, r, nx, ny, nz, xt, G, f);
+        // ---- A: node fields and metrics of the pencils
+        for (int t = tid; t < W * (LB + 6); t += NT) {
+            int line, q;
+            if (K == 0) { line = t / (LB + 6); q = t % (LB + 6); }
+            else { q = t / W; line = t % W; }
+            int a = a0 + line;
+            if (a > nA - 1) a = nA - 1;
+            const int s = s0 + q - 3;
+            const int ss = state_index(s, nk, g.bc[K]);
+            int i1, i2, i3, j1, j2, j3;
+            if (K == 0) { i1 = ss; i2 = a; i3 = b; }
+            else if (K == 1) { i1 = a; i2 = ss; i3 = b; }
+            else { i1 = a; i2 = b; i3 = ss; }
+            const size_t id = idx3(g, i1, i2, i3);
+            const int bx = line * LS + q;
+            float v[MF_COUNT];                                   // all loads in flight before the stores
+            if (tma && s >= 0 && s < nk) {                       // the staged copy: line a - a0 of the box
 #pragma unroll
-        for (int c = 0; c < 5; ++c) PB[c * NP + t] = f[c];
-    }
-    if (P.diss) {
-        for (int t = tid; t < NJ; t += NT) {
-            const int line = t / (LB + 5), q = t % (LB + 5);
-            const int l = line * LS + q;
-            float dV[5];
-            entropy_jump3_f(S, NB, l, l + 1, G, dV);
+                for (int f = 0; f < MF_COUNT; ++f) v[f] = STG[(f * (LB + 6) + q) * W + (a - a0)];
+            } else {
 #pragma unroll
-            for (int c = 0; c < 5; ++c) JB[c * NJ + t] = dV[c];
-        }
-    }
-    __syncthreads();
-
-    // ---- D: face fluxes
-    for (int t = tid; t < NFc; t += NT) {
-        const int line = t / (LB + 1), f = t % (LB + 1);
-        const int q = 2 + f;
-        const int pbase = line * PC::PL;
-        const int base = line * LS;
-        float F[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        float FJ = 0.0f;
-#pragma unroll
-        for (int m = 1; m <= 3; ++m) {
-            const int off = m == 1 ? 0 : (m == 2 ? LB + 1 : 2 * LB + 3);
-            const float al = float(ec_alpha(m));
-            for (int s = 0; s < m; ++s) {
-                const int qq = q - s;
-                const int pi = pbase + off + (qq - (3 - m));
-#pragma unroll
-                for (int c = 0; c < 5; ++c) F[c] += al * PB[c * NP + pi];
-                FJ += al * 0.5f * (S[M_XT * NB + base + qq] + S[M_XT * NB + base + qq + m]);
+                for (int f = 0; f < MF_COUNT; ++f) v[f] = P.NF[f * N + id];
             }
+#pragma unroll
+            for (int f = 0; f < MF_COUNT; ++f) S[f * NB + bx] = v[f];
+            int se = s + 3;
+            se = se < 0 ? 0 : (se > nk + 5 ? nk + 5 : se);
+            if (K == 0) { j1 = se; j2 = a; j3 = b; }
+            else if (K == 1) { j1 = a; j2 = se; j3 = b; }
+            else { j1 = a; j2 = b; j3 = se; }
+            const size_t mi = (size_t(j3) * M2 + j2) * M1 + j1;
+            const double nx = P.NK[mi], ny = P.NK[M + mi], nz = P.NK[2 * M + mi];
+            S[M_NX * NB + bx] = float(nx);
+            S[M_NY * NB + bx] = float(ny);
+            S[M_NZ * NB + bx] = float(nz);
+            double xt = 0.0;
+            if (P.xdot) {
+                double xd[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const GhostTerms tk = ghost_terms(s, nk, g.bc[K], c != K);
+                    for (int u = 0; u < tk.nterm; ++u) {
+                        int k1 = i1, k2 = i2, k3 = i3;
+                        if (K == 0) k1 = tk.idx[u];
+                        else if (K == 1) k2 = tk.idx[u];
+                        else k3 = tk.idx[u];
+                        xd[c] += tk.w[u] * P.xdot[c * N + idx3(g, k1, k2, k3)];
+                    }
+                }
+                xt = -(xd[0] * nx + xd[1] * ny + xd[2] * nz);
+            }
+            S[M_XT * NB + bx] = float(xt);
+        }
+        __syncthreads();
+        if (tma && tid == 0 && pen + int(gridDim.x) < total) {    // the staging buffer is free: next pencil
+            const int p = pen + gridDim.x, gp = p / nseg;
+            stage_pencil<K, LB>(STG, &tmap, &bar, stg_bytes, (gp % ngA) * W, gp / ngA, (p % nseg) * LB);
+        }
+
+        // ---- C: pair fluxes, and B: neighbour jumps V_{q+1} - V_q, q = 0 .. LB+4 (eq. jumpV)
+        for (int t = tid; t < NP; t += NT) {
+            const int line = t / PC::PL, kk = t % PC::PL;
+            int m, q;
+            if (kk < LB + 1) { m = 1; q = 2 + kk; }
+            else if (kk < 2 * LB + 3) { m = 2; q = 1 + (kk - LB - 1); }
+            else { m = 3; q = kk - 2 * LB - 3; }
+            const int l = line * LS + q, r = l + m;
+            const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + r]);
+            const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + r]);
+            const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + r]);
+            const float xt = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + r]);
+            float f[5];
+            pair_flux3_f(S, NB, l, r, nx, ny, nz, xt, G, f);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) PB[c * NP + t] = f[c];
         }
         if (P.diss) {
-            const int l = base + q;
-            const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + l + 1]);
-            const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + l + 1]);
-            const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + l + 1]);
-            const float xtf = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + l + 1]);
-            float d[5];
-            face_dissipation3_f(S, NB, l, nx, ny, nz, xtf, G, P.weno, d, P.status, JB, NJ, line * (LB + 5) + q);
+            for (int t = tid; t < NJ; t += NT) {
+                const int line = t / (LB + 5), q = t % (LB + 5);
+                const int l = line * LS + q;
+                float dV[5];
+                entropy_jump3_f(S, NB, l, l + 1, G, dV);
 #pragma unroll
-            for (int c = 0; c < 5; ++c) F[c] += d[c];
-        }
-#pragma unroll
-        for (int c = 0; c < 5; ++c) FB[c * NFc + t] = F[c];
-        FB[5 * NFc + t] = FJ;
-    }
-    __syncthreads();
-
-    // ---- E: divergence, accumulated in float; the last direction writes double-float results
-    const float inv = float(g.inv_dxi[K]);
-    for (int t = tid; t < W * LB; t += NT) {
-        int line, pos;
-        if (K == 0) { line = t / LB; pos = t % LB; }
-        else { pos = t / W; line = t % W; }
-        const int a = a0 + line, s = s0 + pos;
-        if (a >= nA || s >= nk) continue;
-        int i1, i2, i3;
-        if (K == 0) { i1 = s; i2 = a; i3 = b; }
-        else if (K == 1) { i1 = a; i2 = s; i3 = b; }
-        else { i1 = a; i2 = b; i3 = s; }
-        const size_t id = idx3(g, i1, i2, i3);
-        const int fm = line * (LB + 1) + pos;
-        float acc[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            acc[c] = -(FB[c * NFc + fm + 1] - FB[c * NFc + fm]) * inv;
-            if (!P.first) acc[c] += P.RH[c * N + id];
-        }
-        if (!P.last) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) P.RH[c * N + id] = acc[c];
-        } else if (P.mode == 1) {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                P.JUo[c * N + id] = acc[c];
-                P.JUo[5 * N + c * N + id] = 0.0f;
+                for (int c = 0; c < 5; ++c) JB[c * NJ + t] = dV[c];
             }
-            P.Jo[id] = acc[5];
-            P.Jo[N + id] = 0.0f;
-        } else {
+        }
+        __syncthreads();
+
+        // ---- D: face fluxes
+        for (int t = tid; t < NFc; t += NT) {
+            const int line = t / (LB + 1), f = t % (LB + 1);
+            const int q = 2 + f;
+            const int pbase = line * PC::PL;
+            const int base = line * LS;
+            float F[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float FJ = 0.0f;
+#pragma unroll
+            for (int m = 1; m <= 3; ++m) {
+                const int off = m == 1 ? 0 : (m == 2 ? LB + 1 : 2 * LB + 3);
+                const float al = float(ec_alpha(m));
+                for (int s = 0; s < m; ++s) {
+                    const int qq = q - s;
+                    const int pi = pbase + off + (qq - (3 - m));
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) F[c] += al * PB[c * NP + pi];
+                    FJ += al * 0.5f * (S[M_XT * NB + base + qq] + S[M_XT * NB + base + qq + m]);
+                }
+            }
+            if (P.diss) {
+                const int l = base + q;
+                const float nx = 0.5f * (S[M_NX * NB + l] + S[M_NX * NB + l + 1]);
+                const float ny = 0.5f * (S[M_NY * NB + l] + S[M_NY * NB + l + 1]);
+                const float nz = 0.5f * (S[M_NZ * NB + l] + S[M_NZ * NB + l + 1]);
+                const float xtf = 0.5f * (S[M_XT * NB + l] + S[M_XT * NB + l + 1]);
+                float d[5];
+                face_dissipation3_f(S, NB, l, nx, ny, nz, xtf, G, P.weno, d, P.status, JB, NJ, line * (LB + 5) + q);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) F[c] += d[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 5; ++c) FB[c * NFc + t] = F[c];
+            FB[5 * NFc + t] = FJ;
+        }
+        __syncthreads();
+
+        // ---- E: divergence, accumulated in float; the last direction writes double-float results
+        const float inv = float(g.inv_dxi[K]);
+        for (int t = tid; t < W * LB; t += NT) {
+            int line, pos;
+            if (K == 0) { line = t / LB; pos = t % LB; }
+            else { pos = t / W; line = t % W; }
+            const int a = a0 + line, s = s0 + pos;
+            if (a >= nA || s >= nk) continue;
+            int i1, i2, i3;
+            if (K == 0) { i1 = s; i2 = a; i3 = b; }
+            else if (K == 1) { i1 = a; i2 = s; i3 = b; }
+            else { i1 = a; i2 = b; i3 = s; }
+            const size_t id = idx3(g, i1, i2, i3);
+            const int fm = line * (LB + 1) + pos;
+            // every global operand of this node is loaded before the first global store (as far as the
+            // compiler knows a store may alias a later load, which would serialise one round trip per component)
+            float rh[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float uh[6], ul[6], sh[6], sl[6];
+            if (!P.first) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) rh[c] = P.RH[c * N + id];
+            }
+            const bool combine = P.last && P.mode != 1;
+            if (combine) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const float* un = c < 5 ? P.JUn + c * N : P.Jn;
+                    const float* us = c < 5 ? P.JUs + c * N : P.Js;
+                    const size_t lo = c < 5 ? 5 * N : N;
+                    sh[c] = us[id];
+                    sl[c] = us[lo + id];
+                    uh[c] = P.ca != 0.0f ? un[id] : 0.0f;
+                    ul[c] = P.ca != 0.0f ? un[lo + id] : 0.0f;
+                }
+            }
+            float acc[6];
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
-                const float* un = c < 5 ? P.JUn + c * N : P.Jn;
-                const float* us = c < 5 ? P.JUs + c * N : P.Js;
-                float* uo = c < 5 ? P.JUo + c * N : P.Jo;
-                const size_t lo = c < 5 ? 5 * N : N;
-                const df Un = {un[id], un[lo + id]};
-                const df Us = {us[id], us[lo + id]};
-                const df inc = df_add_f(Us, dt * acc[c]);
-                df outv = df_mul(inc, {P.cb, P.cb_lo});
-                if (P.ca != 0.0f) outv = df_add(outv, df_mul(Un, {P.ca, P.ca_lo}));
-                uo[id] = outv.hi;
-                uo[lo + id] = outv.lo;
-                if (c == 5 && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(id));
+                acc[c] = -(FB[c * NFc + fm + 1] - FB[c * NFc + fm]) * inv;
+                if (!P.first) acc[c] += rh[c];
+            }
+            if (!P.last) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) P.RH[c * N + id] = acc[c];
+            } else if (P.mode == 1) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    P.JUo[c * N + id] = acc[c];
+                    P.JUo[5 * N + c * N + id] = 0.0f;
+                }
+                P.Jo[id] = acc[5];
+                P.Jo[N + id] = 0.0f;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    float* uo = c < 5 ? P.JUo + c * N : P.Jo;
+                    const size_t lo = c < 5 ? 5 * N : N;
+                    const df Un = {uh[c], ul[c]};
+                    const df Us = {sh[c], sl[c]};
+                    const df inc = df_add_f(Us, dt * acc[c]);
+                    df outv = df_mul(inc, {P.cb, P.cb_lo});
+                    if (P.ca != 0.0f) outv = df_add(outv, df_mul(Un, {P.ca, P.ca_lo}));
+                    uo[id] = outv.hi;
+                    uo[lo + id] = outv.lo;
+                    if (c == 5 && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(id));
+                }
             }
         }
+        __syncthreads();                                      // S, PB, FB and JB are refilled next
     }
 }
+
+int g_nsm = 0;                 // SMs of the device (the persistent grids), set by d3f_prepare
 
 template <int K, int LB, int W, int NT, int MINB>
 static cudaError_t prep_shape() {
-    return cudaFuncSetAttribute(k3_dir_f<K, LB, W, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(PencilF<LB, W>::SMEM));
+    const size_t smem = PencilF<LB, W>::SMEM + (K != 0 ? sizeof(float) * PencilF<LB, W>::STG : 0);
+    return cudaFuncSetAttribute(k3_dir_f<K, LB, W, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
 template <int K, int LB, int W, int NT, int MINB>
-static cudaError_t launch_shape(const Dir3FParams& P, cudaStream_t s) {
+static cudaError_t launch_shape(const Dir3FParams& P, const CUtensorMap& map, cudaStream_t s) {
     const Grid3& g = P.g;
     const int nA = K == 0 ? g.n[1] : g.n[0];
     const int nB = K == 2 ? g.n[1] : g.n[2];
     const long long blocks = (long long)((g.n[K] + LB - 1) / LB) * ((nA + W - 1) / W) * nB;
-    k3_dir_f<K, LB, W, NT, MINB><<<unsigned(blocks), NT, PencilF<LB, W>::SMEM, s>>>(P);
+    const bool tma = K != 0 && P.tma;
+    const long long resident = (long long)(g_nsm > 0 ? g_nsm : 1) * MINB;
+    const long long grid = tma && blocks > resident ? resident : blocks;
+    const size_t smem = PencilF<LB, W>::SMEM + (tma ? sizeof(float) * PencilF<LB, W>::STG : 0);
+    k3_dir_f<K, LB, W, NT, MINB><<<unsigned(grid), NT, smem, s>>>(P, map);
     return cudaGetLastError();
 }
 
@@ -545,13 +663,73 @@ static cudaError_t prep_dir() {
 }
 
 template <int K>
-static cudaError_t launch_dir(const Dir3FParams& P, int shape, cudaStream_t s) {
+static cudaError_t launch_dir(const Dir3FParams& P, const CUtensorMap& map, int shape, cudaStream_t s) {
     switch (shape) {
-        case 1: return launch_shape<K, 32, 8, 288, 2>(P, s);
-        case 2: return launch_shape<K, 16, 8, 160, 3>(P, s);
-        case 3: return launch_shape<K, 32, 4, 160, 3>(P, s);
-        default: return launch_shape<K, 16, 16, 288, 2>(P, s);
+        case 1: return launch_shape<K, 32, 8, 288, 2>(P, map, s);
+        case 2: return launch_shape<K, 16, 8, 160, 3>(P, map, s);
+        case 3: return launch_shape<K, 32, 4, 160, 3>(P, map, s);
+        default: return launch_shape<K, 16, 16, 288, 2>(P, map, s);
     }
+}
+
+// the driver's tensor-map encoder (fetched once; nullptr if the driver has none)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// the tensor map of the float node fields [MF_COUNT][n3][n2][n1] with the box of one xi_k pencil (k = 1, 2):
+// W nodes along xi_1, LB + 6 along xi_k, 1 along the third direction, all field planes.  Plain loads (false)
+// when n1 is not a multiple of 4 (TMA strides are multiples of 16 bytes) or the encoder refuses.
+template <int LB, int W>
+static bool build_tmap(Ctx3* d, int k, int shape) {
+    const Grid3& g = d->g;
+    if (g.n[0] % 4 != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    CUtensorMap m;
+    const cuuint64_t dims[4] = {cuuint64_t(g.n[0]), cuuint64_t(g.n[1]), cuuint64_t(g.n[2]), cuuint64_t(MF_COUNT)};
+    const cuuint64_t strides[3] = {cuuint64_t(g.n[0]) * 4, cuuint64_t(g.n[0]) * g.n[1] * 4, cuuint64_t(d->N) * 4};
+    const cuuint32_t box[4] = {cuuint32_t(W), cuuint32_t(k == 1 ? LB + 6 : 1), cuuint32_t(k == 2 ? LB + 6 : 1),
+                               cuuint32_t(MF_COUNT)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d->NF, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    static_assert(sizeof(CUtensorMap) == sizeof(d->tmap[0][0]), "tensor map size");
+    memcpy(d->tmap[k - 1][shape], &m, sizeof(m));
+    return true;
+}
+
+static bool tmap_for(Ctx3* d, int k, int shape, CUtensorMap* out) {
+    if (k == 0 || d->no_tma) return false;
+    int& st = d->tmap_state[k - 1][shape];
+    if (st == 0) {
+        bool ok;
+        switch (shape) {
+            case 1: ok = build_tmap<32, 8>(d, k, shape); break;
+            case 2: ok = build_tmap<16, 8>(d, k, shape); break;
+            case 3: ok = build_tmap<32, 4>(d, k, shape); break;
+            default: ok = build_tmap<16, 16>(d, k, shape); break;
+        }
+        st = ok ? 1 : -1;
+    }
+    if (st != 1) return false;
+    memcpy(out, d->tmap[k - 1][shape], sizeof(*out));
+    return true;
 }
 
 // CFL (eq. cfl) from the float node fields and the FP64 metrics: J xi_{k,t} = -xdot . n_k, xdot = nullptr
@@ -887,7 +1065,10 @@ __global__ void k3f_velocity(Grid3 g, const float* da, const float* db, DevScala
 using namespace mixed3;
 
 cudaError_t d3f_prepare() {
-    cudaError_t e = prep_dir<0>();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = prep_dir<0>();
     if (e == cudaSuccess) e = prep_dir<1>();
     if (e == cudaSuccess) e = prep_dir<2>();
     return e;
@@ -965,7 +1146,11 @@ int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cuda
         P.NK = d->NK[k];
         P.first = k == 0;
         P.last = k == 2;
-        e = k == 0 ? launch_dir<0>(P, d->shape, s) : (k == 1 ? launch_dir<1>(P, d->shape, s) : launch_dir<2>(P, d->shape, s));
+        CUtensorMap map;
+        memset(&map, 0, sizeof(map));
+        P.tma = tmap_for(d, k, d->shape, &map) ? 1 : 0;
+        e = k == 0 ? launch_dir<0>(P, map, d->shape, s)
+                   : (k == 1 ? launch_dir<1>(P, map, d->shape, s) : launch_dir<2>(P, map, d->shape, s));
         ++n;
     }
     *err = e;

@@ -294,7 +294,8 @@ bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
 
 // Sec. 4 on the FP32 pipe; c->fdisp must hold the displacement of x^n.  Writes c->fxd and xdot.
 // with_dt: the monitor kernel also sets the step's dt from the CFL maximum (k_dt's work).
-int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool with_dt) {
+// cfl_moving > 0: the velocity kernel also takes eq. cfl with the new mesh velocity and shrinks dt.
+int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool with_dt, double cfl_moving = 0.0) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const GasF32 gf = gas_f32(c->gas);
@@ -335,7 +336,8 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
         }
     }
     k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
-    k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot);
+    k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot, gf, (const float*)JU,
+                                 (const float*)J, cfl_moving);
     count(c, 2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels (FP32)");
@@ -432,17 +434,13 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
     if (c->p.moving) {
-        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true) : enqueue_mesh(c, JU, J, x, c->xdot);
+        // eq. cfl with the step's mesh velocity (the FP32 velocity kernel takes it in the same pass)
+        const double cfl_moving = c->p.dt_fixed > 0.0 ? 0.0 : c->p.cfl;
+        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true, cfl_moving) : enqueue_mesh(c, JU, J, x, c->xdot);
         if (rc) return rc;
         xdot = c->xdot;
-        if (!(c->p.dt_fixed > 0.0)) {          // eq. cfl with the step's mesh velocity
-            if (f32) {
-                k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, c->fxd,
-                                        RED_CFL2, c->dev);
-                count(c);
-            } else {
-                enqueue_cfl(c, JU, J, x, c->xdot, RED_CFL2);
-            }
+        if (!f32 && cfl_moving > 0.0) {
+            enqueue_cfl(c, JU, J, x, c->xdot, RED_CFL2);
             k_dt_moving<<<1, 32, 0, s>>>(c->dev, c->p.cfl);
             count(c);
         }
@@ -483,7 +481,8 @@ int check_params(const es_params* p) {
     if (p->dim == 1 && p->n2 != 1) return 0;
     if (p->dim >= 2 && p->n2 < 8) return 0;
     if (p->dim < 3 && p->n3 != 0 && p->n3 != 1) return 0;
-    if (p->dim == 3 && (p->n3 < 8 || p->tile > D3_NSHAPES)) return 0;
+    if (p->dim == 3 && (p->n3 < 8 || p->tile > (p->precision == ES_PREC_MIXED ? 2 * D3_NSHAPES : D3_NSHAPES)))
+        return 0;
     const long long n3 = p->dim == 3 ? p->n3 : 1;
     if ((long long)p->n1 * p->n2 * n3 > (1LL << 30)) return 0;
     for (int k = 0; k < p->dim; ++k) {
@@ -499,7 +498,7 @@ int check_params(const es_params* p) {
     if (!(p->sign_tol >= 0.0) || p->sign_tol > 1e-2) return 0;
     if (!(p->cfl > 0.0) && !(p->dt_fixed > 0.0)) return 0;
     if (p->precision != ES_PREC_FP64 && p->precision != ES_PREC_MIXED) return 0;
-    if (p->tile < 0 || p->tile > ES_NTILES) return 0;
+    if (p->tile < 0 || (p->dim < 3 && p->tile > ES_NTILES)) return 0;
     if (p->precision == ES_PREC_MIXED && p->dim < 3) {
         // the FP32 displacement (1D/2D) is periodic only when the period is n dxi
         const int nn[2] = {p->n1, p->n2};
@@ -647,7 +646,9 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;
         d->grid = c->grid1d;
-        d->shape = p->tile >= 1 && p->tile <= D3_NSHAPES ? p->tile - 1 : 0;   // tile 0: chosen by es_autotune
+        // tile 0: chosen by es_autotune; mixed tiles D3_NSHAPES + k: shape k with plain loads (no TMA staging)
+        d->shape = p->tile >= 1 ? (p->tile - 1) % D3_NSHAPES : 0;
+        d->no_tma = p->tile > D3_NSHAPES;
         d->rhoF = c->rhoF;
         d->GF = c->GF;
         d->t0 = c->t0;

@@ -56,12 +56,14 @@ __device__ __forceinline__ void set_dt_from_cfl(DevScalars* d, double cfl, doubl
     d->dt = dt;
 }
 
-// eq. cfl with the step's mesh velocity (maximum in RED_CFL2): Delta t_n = min(Delta t^(0), CFL / max).
+// eq. cfl with the step's mesh velocity (maximum mx): Delta t_n = min(Delta t^(0), CFL / mx).
 // The mesh velocity keeps its value, so the mesh moves Delta_gamma' dx with Delta_gamma' <= Delta_gamma.
-__device__ __forceinline__ void shrink_dt_for_mesh(DevScalars* d, double cfl) {
-    const double mx = __longlong_as_double((long long)d->red[RED_CFL2]);
+__device__ __forceinline__ void shrink_dt_to(DevScalars* d, double mx, double cfl) {
     const double dt = cfl / mx;
     if (d->dt > 0.0 && dt < d->dt) d->dt = dt;
+}
+__device__ __forceinline__ void shrink_dt_for_mesh(DevScalars* d, double cfl) {
+    shrink_dt_to(d, __longlong_as_double((long long)d->red[RED_CFL2]), cfl);
 }
 
 // kernels templated on the state type are launched through these (f32: float state)

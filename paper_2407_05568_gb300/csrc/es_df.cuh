@@ -91,9 +91,12 @@ __device__ __forceinline__ void rho_G_df2(df m0, const df* mom, int dim, df E, d
     const df rho = df_mul(m0, iJ);
     const df irho = df_recip(rho);
     df ke = {0.0f, 0.0f};
-    for (int k = 0; k < dim; ++k) {
-        const df v = df_mul(df_mul(mom[k], iJ), irho);
-        ke = df_add(ke, df_mul(v, v));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {                  // fixed bound: mom[] stays in registers
+        if (k < dim) {
+            const df v = df_mul(df_mul(mom[k], iJ), irho);
+            ke = df_add(ke, df_mul(v, v));
+        }
     }
     const df a = {G.a.hi, G.a.lo};
     const df e = df_add(df_mul(df_mul(E, iJ), irho), df_mul_f(df_neg(ke), 0.5f));

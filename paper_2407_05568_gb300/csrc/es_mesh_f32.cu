@@ -48,20 +48,58 @@ __device__ __forceinline__ float block_min_f32(float v) {
     return v;
 }
 
-// displacement at a node that may be a ghost: periodic wrap (d is periodic), outflow odd
-// reflection d_{-m} = 2 d_0 - d_m (the reflection of x, whose Cartesian part cancels)
+// a displacement ghost along one direction as at most two mesh nodes: periodic wrap (d is periodic),
+// outflow odd reflection d_{-m} = 2 d_0 - d_m (the reflection of x, whose Cartesian part cancels); the
+// mirror index is clamped to the mesh, as in ghost_terms.  Float weights (1, 2, -1, and their products,
+// are exact), so the boundary nodes cost no FP64 work.
+struct GhostF {
+    int i0, i1;
+    float w0, w1;
+    bool two;
+};
+
+__device__ __forceinline__ GhostF ghost_f(int i, int n, int bc) {
+    GhostF t;
+    t.two = false;
+    t.w0 = 1.0f;
+    t.w1 = 0.0f;
+    t.i1 = 0;
+    if (i >= 0 && i < n) {
+        t.i0 = i;
+    } else if (bc == ES_BC_PERIODIC) {
+        t.i0 = wrap_index(i, n);
+    } else {
+        int m = i < 0 ? -i : 2 * (n - 1) - i;
+        m = m < 0 ? 0 : (m > n - 1 ? n - 1 : m);
+        t.i0 = i < 0 ? 0 : n - 1;
+        t.i1 = m;
+        t.w0 = 2.0f;
+        t.w1 = -1.0f;
+        t.two = true;
+    }
+    return t;
+}
+
+// displacement at a node that may be a ghost
 __device__ __forceinline__ float disp_at(const GridParams& g, const float* d, int gi, int gj, int comp) {
     const size_t N = size_t(g.n1) * g.n2;
+    const float* dc = d + comp * N;
     if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))
-        return d[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
-    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0]);
-    GhostTerms tj;
-    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1]);
-    else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
-    float acc = 0.0f;
-    for (int a = 0; a < ti.nterm; ++a)
-        for (int c = 0; c < tj.nterm; ++c)
-            acc += float(ti.w[a] * tj.w[c]) * d[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
+        return dc[size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
+    const GhostF ti = ghost_f(gi, g.n1, g.bc[0]);
+    GhostF tj;
+    if (g.dim == 2) {
+        tj = ghost_f(gj, g.n2, g.bc[1]);
+    } else {
+        tj.i0 = 0; tj.i1 = 0; tj.w0 = 1.0f; tj.w1 = 0.0f; tj.two = false;
+    }
+    const size_t r0 = size_t(tj.i0) * g.n1, r1 = size_t(tj.i1) * g.n1;
+    float acc = (ti.w0 * tj.w0) * dc[r0 + ti.i0];             // the terms in ghost_terms' order
+    if (tj.two) acc += (ti.w0 * tj.w1) * dc[r1 + ti.i0];
+    if (ti.two) {
+        acc += (ti.w1 * tj.w0) * dc[r0 + ti.i1];
+        if (tj.two) acc += (ti.w1 * tj.w1) * dc[r1 + ti.i1];
+    }
     return acc;
 }
 
@@ -93,63 +131,72 @@ __device__ __forceinline__ bool fixed_node_f(const GridParams& g, int i, int j) 
     return f;
 }
 
-}  // namespace
-
-// eq. cfl on the FP32 pipe: max_i sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k) with
-// J xi_{k,t} = -xdot . n_k; vel = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
-__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
-                        int slot, DevScalars* d) {
+// the node term of eq. cfl on the FP32 pipe: sum_k (|J xi_{k,t} + n_k . v| + |n_k| c) / (J dxi_k) with
+// J xi_{k,t} = -xdot . n_k, at node id with mesh velocity (xd1, xd2); a node without a real sound speed
+// gives 3e38 (the time step then collapses and the admissibility check reports the state)
+__device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G, const float* JU, const float* J,
+                                            const float* disp, int id, float xd1, float xd2) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
     const float idx1 = float(g.inv_dxi[0]), idx2 = float(g.inv_dxi[1]);
+    const int i = id % g.n1, j = id / g.n1;
+    const float iJ = 1.0f / ld2(J, N, id);
+    const float rho = ld2(JU, P, id) * iJ;
+    const float irho = 1.0f / rho;
+    const float v1 = ld2(JU, P, N + id) * iJ * irho;
+    const float v2 = g.dim == 2 ? ld2(JU, P, 2 * N + id) * iJ * irho : 0.0f;
+    const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
+    const float T = (E * irho - 0.5f * (v1 * v1 + v2 * v2) + G.a * rho) * G.icv;
+    const float iom = 1.0f / (1.0f - G.b * rho);
+    const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
+    const float c = sqrtf(fmaxf(c2, 0.0f));
+    float tot;
+    if (g.dim == 1) {
+        tot = (fabsf(v1 - xd1) + c) * iJ * idx1;
+    } else {
+        float x1, x2, y1, y2;
+        if (i >= 3 && i < g.n1 - 3 && j >= 3 && j < g.n2 - 3) {
+            // interior: the 24 displacement loads have no ghost rule and are issued together
+            float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};      // d x/d xi_1, d x/d xi_2, d y/d xi_1, d y/d xi_2
+#pragma unroll
+            for (int m = 1; m <= 3; ++m) {
+                const float h = 0.5f * float(ec_alpha(m));
+                s[0] += h * (disp[id + m] - disp[id - m]);
+                s[1] += h * (disp[id + m * g.n1] - disp[id - m * g.n1]);
+                s[2] += h * (disp[N + id + m] - disp[N + id - m]);
+                s[3] += h * (disp[N + id + m * g.n1] - disp[N + id - m * g.n1]);
+            }
+            x1 = 1.0f + s[0] * idx1;
+            x2 = s[1] * idx2;
+            y1 = s[2] * idx1;
+            y2 = 1.0f + s[3] * idx2;
+        } else {
+            x1 = dx_dxi(g, disp, i, j, 0, 0, idx1);
+            x2 = dx_dxi(g, disp, i, j, 0, 1, idx2);
+            y1 = dx_dxi(g, disp, i, j, 1, 0, idx1);
+            y2 = dx_dxi(g, disp, i, j, 1, 1, idx2);
+        }
+        const float a1 = y2, b1 = -x2;        // J dxi_1/dx
+        const float a2 = -y1, b2 = x1;        // J dxi_2/dx
+        tot = (fabsf(a1 * (v1 - xd1) + b1 * (v2 - xd2)) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
+              (fabsf(a2 * (v1 - xd1) + b2 * (v2 - xd2)) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
+    }
+    if (!(c2 > 0.0f)) tot = 3.0e38f;
+    return tot;
+}
+
+}  // namespace
+
+// eq. cfl on the FP32 pipe: the maximum over the nodes of cfl_node_f goes to d->red[slot]; vel = nullptr
+// is a mesh at rest.
+__global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
+                        int slot, DevScalars* d) {
+    const int N = g.n1 * g.n2;
     float m = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const int i = id % g.n1, j = id / g.n1;
-        const float iJ = 1.0f / ld2(J, N, id);
-        const float rho = ld2(JU, P, id) * iJ;
-        const float irho = 1.0f / rho;
-        const float v1 = ld2(JU, P, N + id) * iJ * irho;
-        const float v2 = g.dim == 2 ? ld2(JU, P, 2 * N + id) * iJ * irho : 0.0f;
-        const float E = ld2(JU, P, (g.dim + 1) * N + id) * iJ;
-        const float T = (E * irho - 0.5f * (v1 * v1 + v2 * v2) + G.a * rho) * G.icv;
-        const float iom = 1.0f / (1.0f - G.b * rho);
-        const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
-        const float c = sqrtf(fmaxf(c2, 0.0f));
         const float xd1 = vel != nullptr ? vel[id] : 0.0f;
-        float tot;
-        if (g.dim == 1) {
-            tot = (fabsf(v1 - xd1) + c) * iJ * idx1;
-        } else {
-            const float xd2 = vel != nullptr ? vel[N + id] : 0.0f;
-            float x1, x2, y1, y2;
-            if (i >= 3 && i < g.n1 - 3 && j >= 3 && j < g.n2 - 3) {
-                // interior: the 24 displacement loads have no ghost rule and are issued together
-                float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};      // d x/d xi_1, d x/d xi_2, d y/d xi_1, d y/d xi_2
-#pragma unroll
-                for (int m = 1; m <= 3; ++m) {
-                    const float h = 0.5f * float(ec_alpha(m));
-                    s[0] += h * (disp[id + m] - disp[id - m]);
-                    s[1] += h * (disp[id + m * g.n1] - disp[id - m * g.n1]);
-                    s[2] += h * (disp[N + id + m] - disp[N + id - m]);
-                    s[3] += h * (disp[N + id + m * g.n1] - disp[N + id - m * g.n1]);
-                }
-                x1 = 1.0f + s[0] * idx1;
-                x2 = s[1] * idx2;
-                y1 = s[2] * idx1;
-                y2 = 1.0f + s[3] * idx2;
-            } else {
-                x1 = dx_dxi(g, disp, i, j, 0, 0, idx1);
-                x2 = dx_dxi(g, disp, i, j, 0, 1, idx2);
-                y1 = dx_dxi(g, disp, i, j, 1, 0, idx1);
-                y2 = dx_dxi(g, disp, i, j, 1, 1, idx2);
-            }
-            const float a1 = y2, b1 = -x2;        // J dxi_1/dx
-            const float a2 = -y1, b2 = x1;        // J dxi_2/dx
-            tot = (fabsf(a1 * (v1 - xd1) + b1 * (v2 - xd2)) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
-                  (fabsf(a2 * (v1 - xd1) + b2 * (v2 - xd2)) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
-        }
-        if (!(c2 > 0.0f)) tot = 3.0e38f;
-        m = fmaxf(m, tot);
+        const float xd2 = vel != nullptr && g.dim == 2 ? vel[N + id] : 0.0f;
+        m = fmaxf(m, cfl_node_f(g, G, JU, J, disp, id, xd1, xd2));
     }
     m = block_max_f32(m);
     if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], double(m));
@@ -161,8 +208,10 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
 __device__ __forceinline__ void mon_field_df(const GridParams& g, const GasF32& G, const float* JU, const float* J,
                                              int N, size_t P, int id, mixed::df* rho_out, mixed::df* G_out) {
     using mixed::df;
-    df mom[3];
-    for (int k = 0; k < g.dim; ++k) mom[k] = {JU[(1 + k) * N + id], JU[P + (1 + k) * N + id]};
+    df mom[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)                    // fixed bound: the array stays in registers
+        if (k < g.dim) mom[k] = {JU[(1 + k) * N + id], JU[P + (1 + k) * N + id]};
     const int ce = (g.dim + 1) * N + id;
     mixed::rho_G_df2({JU[id], JU[P + id]}, mom, g.dim, {JU[ce], JU[P + ce]}, {J[id], J[N + id]}, G.gdf, rho_out,
                      G_out);
@@ -198,7 +247,9 @@ __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
         mixed::df r0, G0;
         mon_field_df(g, G, JU, J, N, P, id, &r0, &G0);
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
-        for (int k = 0; k < g.dim; ++k) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {                  // fixed bound: no dynamic indexing of g
+            if (k >= g.dim) break;
             const int di = k == 0, dj = k == 1;
             const float h = float(g.inv_dxi[k]);
             const int sp = (g.dim == 2 ? state_index(j + dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i + di, g.n1, g.bc[0]);
@@ -284,6 +335,8 @@ __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, fl
     const float* xin = k == 0 ? d0 : ((k - 1) & 1 ? db : da);
     float* xout = (k & 1) ? db : da;
     float chg = 0.0f;
+    const float ih2k[2] = {float(g.inv_dxi[0] * g.inv_dxi[0]), float(g.inv_dxi[1] * g.inv_dxi[1])};
+    const float dxk[2] = {float(1.0 / g.inv_dxi[0]), float(1.0 / g.inv_dxi[1])};
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         if (fixed_node_f(g, i, j)) {
@@ -294,8 +347,8 @@ __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, fl
         float den = 0.0f, num0 = 0.0f, num1 = 0.0f;
         for (int kk = 0; kk < g.dim; ++kk) {
             const int di = kk == 0, dj = kk == 1;
-            const float ih2 = float(g.inv_dxi[kk] * g.inv_dxi[kk]);
-            const float dx = float(1.0 / g.inv_dxi[kk]);
+            const float ih2 = kk == 0 ? ih2k[0] : ih2k[1];
+            const float dx = kk == 0 ? dxk[0] : dxk[1];
             const float wp = 0.5f * (w0 + field_at_f(g, omega, i + di, j + dj)) * ih2;
             const float wm = 0.5f * (w0 + field_at_f(g, omega, i - di, j - dj)) * ih2;
             den += wp + wm;
@@ -343,12 +396,13 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
     float m = 1.0f;
+    const float hk[2] = {float(1.0 / g.inv_dxi[0]), float(1.0 / g.inv_dxi[1])};
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         for (int k = 0; k < g.dim; ++k) {
             const float dx = xit[k * N + id] - d0[k * N + id];
             const int di = k == 0, dj = k == 1;
-            const float h = float(1.0 / g.inv_dxi[k]);
+            const float h = k == 0 ? hk[0] : hk[1];
             if (dx < 0.0f) m = fminf(m, -(h + d0[k * N + id] - disp_at(g, d0, i - di, j - dj, k)) / (2.0f * dx));
             else if (dx > 0.0f) m = fminf(m, (h + disp_at(g, d0, i + di, j + dj, k) - d0[k * N + id]) / (2.0f * dx));
         }
@@ -357,23 +411,45 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
     if (threadIdx.x == 0) atomic_min_pos(&d->red[RED_GAMMA], double(m));
 }
 
-// xdot = Delta_gamma (x^[mu] - x^n) / dt: float (for the stage kernels) and double (the API's array)
+// xdot = Delta_gamma (x^[mu] - x^n) / dt: float (for the stage kernels) and double (the API's array).
+// cfl > 0 also takes eq. cfl with this mesh velocity at each node (k_cfl_f's RED_CFL2 pass, on the same
+// float velocity), and the last block to finish shrinks the step's dt to it (k_dt_moving's work).
 __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
-                             float* fxd, double* xdot) {
+                             float* fxd, double* xdot, GasF32 G, const float* JU, const float* J, double cfl) {
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
     const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
     const double dt = d->dt;
     const float f = dt > 0.0 ? float(gam / dt) : 0.0f;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x) {
-        const float v = f * (xit[id] - d0[id]);
-        fxd[id] = v;
-        xdot[id] = double(v);
+    float m = 0.0f;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        const float v1 = f * (xit[id] - d0[id]);
+        fxd[id] = v1;
+        xdot[id] = double(v1);
+        float v2 = 0.0f;
+        if (g.dim == 2) {
+            v2 = f * (xit[N + id] - d0[N + id]);
+            fxd[N + id] = v2;
+            xdot[N + id] = double(v2);
+        }
+        if (cfl > 0.0) m = fmaxf(m, cfl_node_f(g, G, JU, J, d0, id, v1, v2));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d->gamma = gam;
         d->sweeps_total += d->sweeps;
         d->solves += 1;
+    }
+    if (cfl > 0.0) {
+        m = block_max_f32(m);
+        if (threadIdx.x == 0) {
+            atomic_max_pos(&d->red[RED_CFL2], double(m));
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {          // every block's maximum is in: every block has read dt
+                shrink_dt_to(d, __longlong_as_double((long long)atomicAdd(&d->red[RED_CFL2], 0ULL)), cfl);
+                d->done = 0u;
+            }
+        }
     }
 }
 

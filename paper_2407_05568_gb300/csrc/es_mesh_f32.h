@@ -45,7 +45,8 @@ void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const flo
                          const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s);
 __global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
                                  DevScalars* dv);
+// cfl > 0: also eq. cfl with the new velocity into RED_CFL2, and dt = min(dt, cfl / that maximum)
 __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
-                             float* fxd, double* xdot);
+                             float* fxd, double* xdot, GasF32 G, const float* JU, const float* J, double cfl);
 
 }  // namespace es

@@ -585,17 +585,24 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
             // a_s U^n + b_s (U^s + dt L) in double-float (a_s, b_s are 0, 1, 3/4, 1/4, 1/3, 2/3)
             const float ca = P.fca, cb = P.fcb;
             const float ca_lo = P.fca_lo, cb_lo = P.fcb_lo;
+            // all operands loaded before the first store: as far as the compiler knows a store may alias a
+            // later load, which would serialise one round trip per component
+            df Un[NC + 1], Us[NC + 1];
 #pragma unroll
             for (int c = 0; c <= NC; ++c) {
                 const float* un = c < NC ? P.fJUn + c * N : P.fJn;
                 const float* us = c < NC ? P.fJUs + c * N : P.fJs;
+                const size_t lo = c < NC ? LO : P.fpsJ;
+                Us[c] = {us[idx], us[lo + idx]};
+                Un[c] = ca != 0.0f ? df{un[idx], un[lo + idx]} : df{0.0f, 0.0f};
+            }
+#pragma unroll
+            for (int c = 0; c <= NC; ++c) {
                 float* uo = c < NC ? P.fJUo + c * N : P.fJo;
                 const size_t lo = c < NC ? LO : P.fpsJ;
-                const df Un = {un[idx], un[lo + idx]};
-                const df Us = {us[idx], us[lo + idx]};
-                const df inc = df_add_f(Us, dt * acc[c]);
+                const df inc = df_add_f(Us[c], dt * acc[c]);
                 df outv = df_mul(inc, {cb, cb_lo});
-                if (ca != 0.0f) outv = df_add(outv, df_mul(Un, {ca, ca_lo}));
+                if (ca != 0.0f) outv = df_add(outv, df_mul(Un[c], {ca, ca_lo}));
                 uo[idx] = outv.hi;
                 uo[lo + idx] = outv.lo;
                 if (c == NC && !(outv.hi > 0.0f)) raise_error(P.status, ES_ERR_MESH, int(idx));

@@ -546,11 +546,19 @@ stage_kernel_fp64(StageParams P) {
             for (int c = 0; c < NC; ++c) P.JUo[c * N + idx] = acc[c];
             P.Jo[idx] = acc[NC];
         } else {
+            // all operands loaded before the first store (a store may alias a later load as far as the compiler
+            // knows, which would serialise one round trip per component)
+            double un[NC], us[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                P.JUo[c * N + idx] = P.ca * P.JUn[c * N + idx] + P.cb * (P.JUs[c * N + idx] + dt * acc[c]);
+            for (int c = 0; c < NC; ++c) {
+                un[c] = P.JUn[c * N + idx];
+                us[c] = P.JUs[c * N + idx];
+            }
             const double Jn = P.Jn[idx];
-            const double Jnew = P.ca * Jn + P.cb * (P.Js[idx] + dt * acc[NC]);
+            const double Js = P.Js[idx];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) P.JUo[c * N + idx] = P.ca * un[c] + P.cb * (us[c] + dt * acc[c]);
+            const double Jnew = P.ca * Jn + P.cb * (Js + dt * acc[NC]);
             P.Jo[idx] = Jnew;
             if (!(Jnew > 0.0)) raise_error(P.status, ES_ERR_MESH, int(idx));
         }
