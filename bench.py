@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-matched-error", action="store_true",
-                    help="skip the default matched-error comparison (1D sine 50..200, vortex 64^2..128^2, both forms)")
+                    help="skip the default matched-error comparison (1D sine 50..200, vortex 128^2..256^2, both forms)")
     ap.add_argument("--precision-sweep", action="store_true",
-                    help="also run the precision-form sweep: 2D sine 1024^2 and the vortex 64^2..1024^2, both forms")
+                    help="also run the precision-form sweep: 1D sine 50..1600, 2D sine 1024^2 and the vortex 128^2..2048^2, "
+                         "both forms")
     ap.add_argument("--mach-reflection", action="store_true",
                     help="also run Example 5.4's Mach reflection (P1, D1) to its final time: MM, MM1, UM, FP64")
     ap.add_argument("--learned", action="store_true",
@@ -58,10 +59,16 @@ def parse():
     ap.add_argument("--three-d", type=int, default=96,
                     help="also time the 3D FP64 path on the moving-mesh 3D sine wave at n^3 (0: skip)")
     ap.add_argument("--three-d-steps", type=int, default=5)
+    ap.add_argument("--large-n", type=int, default=1024,
+                    help="also time the mixed stage kernel on the n x n Riemann problem (0: skip)")
+    ap.add_argument("--mesh-n", type=int, default=4096,
+                    help="also time the mesh redistribution alone on an n x n mesh, both forms (0: skip)")
     ap.add_argument("--learned-n", type=int, default=512)
     ap.add_argument("--learned-seeds", type=int, default=20, help="plain runs; the last two are held out")
     ap.add_argument("--learned-steps", type=int, default=100)
     ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-tols", default="0.02,0.01,0.005,0.0025",
+                    help="Jacobi tolerances (cells) of the matched-accuracy comparison; the first is the training one")
     return ap.parse_args()
 
 
@@ -314,12 +321,85 @@ def measure_batch(args, dev, stream):
         raise RuntimeError("batched form: device status")
     ms = st.elapsed_time(en)
     cells = b.ntot * 3 * args.batch_steps
+    from paper_2407_05568_gb300 import perfmodel
+    _, f32 = measured_alu_peaks(es, stream)
+    achieved = cells * perfmodel.flops_per_node_stage(1) / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "batch_kernel", "achieved": achieved, "peak": f32, "unit": "TFLOP/s",
+            "frac": achieved / f32, "ops_per_node_stage": perfmodel.flops_per_node_stage(1),
+            "traffic": None, "launch_ms": ms,
+            "peak_source": "measured in this run: es_selftest_peaks, FMA chains on every SM, best of 5 launches "
+                           "(FP32); of measured"}
     return {"workload": f"{b.nprob} independent 1D vdW shock tubes, lengths U{{200..8000}} "
                         f"({b.ntot} nodes), moving mesh, one persistent launch per {args.batch_steps} steps",
             "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_launch": ms,
             "steps_per_launch": args.batch_steps, "nodes": b.ntot, "dtype": "f32",
             "autotune": {"threads_per_cta": bt, "probe_ms_128_256_512": probe_ms},
-            "l2": "state (2 GB) larger than L2"}
+            "roofline": roof, "l2": "state (2 GB) larger than L2"}
+
+
+def measure_large_stage(args, dev, stream):
+    """The mixed stage kernel alone on the n x n vdW Riemann problem (the 200 x 200 recipe at n x n): shape from
+    es_autotune, duration over 20 launches, against the measured FP32 rate."""
+    from paper_2407_05568_gb300 import es
+    n = args.large_n
+    ctx, JU, J, x = es.setup_workload(workload(n), "mixed", dev, stream=stream)
+    tile, tile_ms = es.es_autotune(ctx, JU, J, x)
+    roof = stage_roofline(es, ctx, JU, J, x, stream, workload(n), n * n, "mixed", tile)
+    roof["autotune_ms_per_shape"] = tile_ms
+    mb = (JU.numel() + J.numel()) * 4 * 2 / 1e6
+    return {"workload": f"2D vdW four-quadrant Riemann problem, {n}x{n} nodes, one RK stage (mixed form)",
+            "roofline": roof, "l2": f"state {mb:.0f} MB in and out per launch; bound by the FP32 pipe, no flush"}
+
+
+def measure_mesh(args, dev, stream):
+    """The mesh redistribution alone (es_mesh_redistribute: monitor with G, 5 filter passes, 5 Jacobi sweeps,
+    limiter, mesh velocity) on the n x n vdW Riemann problem, both forms, against the measured HBM copy rate with
+    the kernel sequence's compulsory bytes (perfmodel.mesh_bytes_per_node).  The state is larger than L2."""
+    import torch
+
+    from paper_2407_05568_gb300 import es, perfmodel
+    n = args.mesh_n
+    w = workload(n)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    source = "MEASURED_PEAKS.json hbm_gbs (STREAM-style copy); of measured"
+    if hbm is None:
+        hbm, source = 6800.0, "profiling recipe's fallback 6.8 TB/s; of fallback"
+    m = w.get("mesh", {})
+    passes, sweeps = m.get("filter_passes", 5), m.get("sweeps", 5)
+    out = {"workload": f"mesh redistribution of the 2D vdW Riemann problem, {n}x{n} nodes, {passes} filter passes, "
+                       f"{sweeps} Jacobi sweeps (es_mesh_redistribute)"}
+    for prec in ("mixed", "fp64"):
+        ctx, JU, J, x = es.setup_workload(w, prec, dev, stream=stream)
+        with torch.cuda.stream(stream):
+            xdot = torch.empty_like(x)
+        dt, reps = 1e-4, 10
+        for _ in range(3):
+            es.es_mesh_redistribute(ctx, JU, J, x, dt, xdot, stats=False)
+        st = torch.cuda.Event(enable_timing=True)
+        en = torch.cuda.Event(enable_timing=True)
+        launches0 = ctx.launches
+        st.record(stream)
+        for _ in range(reps):
+            es.es_mesh_redistribute(ctx, JU, J, x, dt, xdot, stats=False)
+        en.record(stream)
+        launches = (ctx.launches - launches0) // reps
+        en.synchronize()
+        if es.es_check(ctx):
+            raise RuntimeError(es.es_last_error(ctx))
+        ms = st.elapsed_time(en) / reps
+        bpn = perfmodel.mesh_bytes_per_node(prec, passes, sweeps)
+        achieved = bpn * n * n / (ms * 1e-3) / 1e9
+        out[prec] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "bytes_per_node": bpn, "ms_per_call": ms,
+                     "gpu_launches_per_call": int(launches), "peak_source": source}
+        del ctx, JU, J, x, xdot
+        torch.cuda.empty_cache()
+    return out
 
 
 def _three_d_form(w, precision, args, dev, stream):
@@ -444,20 +524,20 @@ def matched_error(rows, levels=(1e-4, 1e-5, 1e-6, 1e-7, 1e-8)):
 
 
 # the default line's matched-error comparison: the smallest grids of the two accuracy sweeps
-QUICK_SWEEP = [("sine1d", 50), ("sine1d", 100), ("sine1d", 200), ("vortex", 64), ("vortex", 128)]
+QUICK_SWEEP = [("sine1d", 50), ("sine1d", 100), ("sine1d", 200), ("vortex", 128), ("vortex", 256)]
 
 
 def measure_precision_sweep(args, dev, cases=None):
     """The precision form against the plain FP64 form: L1(rho) against the exact solution and
     against the FP64 run, throughput and time to solution, on the 1D sine wave (50 .. 1600 nodes,
     fixed mesh, dt = 0.4 dxi^(5/3), t = 0.1), the 2D sine wave (1024^2, t = 0.1) and the
-    ideal-gas isentropic vortex (64^2 .. 1024^2, t = 1); then, per sweep, the smallest grid of
+    ideal-gas isentropic vortex (128^2 .. 2048^2 on the box of side 20, t = 1); then, per sweep, the smallest grid of
     each form that meets each error level (matched error)."""
     from paper_2407_05568_gb300 import workloads as wl
     out = []
     if cases is None:
         cases = ([("sine1d", n) for n in (50, 100, 200, 400, 800, 1600)] + [("sine2d", 1024)]
-                 + [("vortex", n) for n in (64, 128, 256, 512, 1024)])
+                 + [("vortex", n) for n in (128, 256, 512, 1024, 2048)])
     for name, n in cases:
         dt_fixed = 0.0
         if name == "sine1d":
@@ -559,6 +639,25 @@ def measure_learned(args, dev):
         t_inf[name] = e0.elapsed_time(e1) / 20
     cmp = learned.compare_solves(net, test_seeds, n, args.learned_steps, eps, mu, device=dev)
     run = learned.compare_runs(net, test_seeds[0], n, args.learned_steps, eps, mu, device=dev)
+    # matched accuracy: both solves against the converged mesh of the same states, then full runs with the plain
+    # tolerance that gives the plain solve the warm solve's mean distance to it
+    tols = [float(t) for t in args.learned_tols.split(",")]
+    mres, ref_sw = learned.compare_matched(net, test_seeds, n, args.learned_steps, tols, mu, device=dev)
+    per_tol = {str(t): {k: float(v.mean()) for k, v in r.items()} | {"dist_plain_max_max": float(r["dist_plain_max"].max()),
+                                                                     "dist_warm_max_max": float(r["dist_warm_max"].max())}
+               for t, r in mres.items()}
+    matched = {"reference": f"Jacobi from x^n to a change below 1e-5 cells (at most 20000 sweeps; "
+                            f"mean {ref_sw.mean():.0f}, max {ref_sw.max()} sweeps)",
+               "per_tolerance": per_tol}
+    dw = float(mres[tols[0]]["dist_warm_mean"].mean())
+    at = learned.plain_at(mres, dw)
+    if at is not None:
+        tol_p, sw_p = at
+        matched["warm_at_training_tolerance"] = {"tolerance": tols[0], "dist_mean": dw,
+                                                 "sweeps_warm": float(mres[tols[0]]["sweeps_warm"].mean()),
+                                                 "plain_tolerance_at_same_dist": tol_p, "sweeps_plain_at_same_dist": sw_p}
+        matched["full_runs"] = learned.compare_runs(net, test_seeds[0], n, args.learned_steps, tol_p, mu,
+                                                    device=dev, eps_warm=tols[0])
     return {"workload": f"2D vdW Riemann problem {n}x{n}, moving mesh, Jacobi to max change < {eps} cells "
                         f"(at most {mu} sweeps); network 4 conv3x3 layers, 32 channels, bf16 weights",
             "snapshots": int(len(sw)), "train_seeds": f"{train_seeds[0]}..{train_seeds[-1]}",
@@ -572,7 +671,7 @@ def measure_learned(args, dev):
                             "warm_kept_frac": float(cmp["picked"].mean()),
                             "mesh_dev_cells_max": float(cmp["dev_cells"].max()),
                             "mesh_dev_cells_mean": float(cmp["dev_cells"].mean())},
-            "full_runs": run, "nn_inference_ms": t_inf}
+            "full_runs": run, "matched_accuracy": matched, "nn_inference_ms": t_inf}
 
 
 def measure_nn_inference(n, dev):
@@ -620,6 +719,8 @@ def run_gpu(args):
     if args.batch_problems > 0 and rank == 0:
         batched = measure_batch(args, dev, stream)
     three_d = measure_three_d(args, dev, stream) if args.three_d > 0 and rank == 0 else None
+    large = measure_large_stage(args, dev, stream) if args.large_n > 0 and rank == 0 else None
+    mesh_res = measure_mesh(args, dev, stream) if args.mesh_n > 0 and rank == 0 else None
     learned_res = measure_learned(args, dev) if args.learned and rank == 0 else None
     sweep_res = measure_precision_sweep(args, dev) if args.precision_sweep and rank == 0 else None
     quick = None
@@ -651,6 +752,10 @@ def run_gpu(args):
             line["batched"] = batched
         if three_d is not None:
             line["three_d"] = three_d
+        if large is not None:
+            line["chosen_large"] = large
+        if mesh_res is not None:
+            line["mesh"] = mesh_res
         if learned_res is not None:
             line["learned"] = learned_res
         if sweep_res is not None:
@@ -661,7 +766,7 @@ def run_gpu(args):
             # smallest grid of each form that reaches it and its time to solution (to t_end)
             line["matched_error"] = dict(quick["matched_error"],
                                          cases="1D sine 50/100/200 nodes to t = 0.1 (dt = 0.4 dxi^(5/3)), "
-                                               "ideal-gas isentropic vortex 64^2/128^2 to t = 1, both forms")
+                                               "ideal-gas isentropic vortex 128^2/256^2 (box of side 20) to t = 1, both forms")
         if nn_res is not None:
             line["nn_inference"] = nn_res
         if mach_res is not None:
@@ -683,17 +788,11 @@ def pin(a):
     return t.numpy()
 
 
-# Algorithmic FP64 operations per node and RK stage of the fused stage kernel
-# (+, -, *, / and sqrt/log each one operation; an FMA two), counted from the
-# formulas the kernel evaluates; derivation in the design notes.
-FLOPS_PER_NODE_STAGE_2D = None
-
-
 TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12), 5: (20, 10)},
          "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16), 5: (16, 8)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
 # kernel as it is now (a kernel changed since its capture has no entry); other sizes were not captured
-TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 3032064 + 0, "stage_kernel_mixed<2,16,8>": 2343680 + 0}
+TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 2393088 + 0}
 
 
 def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):

@@ -259,13 +259,15 @@ def es_entropy_rate(ctx, JU, J, dJU, dJ):
     return out[0], out[1]
 
 
-def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot):
+def es_mesh_redistribute(ctx, JU, J, xn, dt, xdot, stats=True):
+    """Sec. 4's redistribution from xn; returns (sweeps, Delta_gamma), or (None, None) with stats=False, which
+    leaves the call asynchronous on the context's stream."""
     S = ctx.state_dtype
     sw = ctypes.c_int()
     gam = ctypes.c_double()
     ctx._call(lib().es_mesh_redistribute(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(xn, F64), dt, _ptr(xdot, F64),
-                                         ctypes.byref(sw), ctypes.byref(gam)))
-    return sw.value, gam.value
+                                         ctypes.byref(sw) if stats else None, ctypes.byref(gam) if stats else None))
+    return (sw.value, gam.value) if stats else (None, None)
 
 
 def es_mesh_features(ctx, JU, J, x, feat):

@@ -242,15 +242,79 @@ def compare_solves(net, seeds, n, steps, eps_cells, mu_max, precision="fp64", de
     return {k: np.array(v) for k, v in out.items()}
 
 
+def compare_matched(net, seeds, n, steps, tols, mu_max, ref_tol=1e-5, ref_mu=20000, every=10, precision="fp64",
+                    device="cuda", guard_ratio=GUARD_RATIO):
+    """The plain and the warm-started solve measured against the converged mesh, along plain runs.
+
+    Every `every` steps of a plain run (Jacobi to tols[0] cells), the state's mesh equation is solved from x^n until
+    a sweep changes the mesh by less than ref_tol cells (at most ref_mu sweeps): x_ref.  Then, for each tolerance in
+    tols, the plain solve and the warm-started solve of that state: sweeps, and the max and mean over nodes and
+    components of |x - x_ref| / dxi.  Returns ({tol: {key: array over the sampled states}}, reference sweeps)."""
+    torch = _torch()
+    keys = ("sweeps_plain", "sweeps_warm", "picked", "dist_plain_max", "dist_plain_mean", "dist_warm_max",
+            "dist_warm_mean")
+    res = {t: {k: [] for k in keys} for t in tols}
+    ref_sweeps = []
+    for seed in seeds:
+        w = riemann_workload(n, seed, tols[0], mu_max)
+        dxi = w["dxi"][0]
+        ctx, JU, J, x = setup(w, precision, device)
+        solvers = {t: es.es_create(es.make_params(riemann_workload(n, seed, t, mu_max), precision=precision))
+                   for t in tols}
+        ref = es.es_create(es.make_params(riemann_workload(n, seed, ref_tol, ref_mu), precision=precision))
+        xr, xp, xw, xs = (torch.empty_like(x) for _ in range(4))
+        feat = torch.empty((1, 4, n, n), dtype=torch.float32, device=device)
+        for s in range(steps):
+            if s % every == 0:
+                sr, _ = es.es_mesh_solve(ref, JU, J, x, None, xr)
+                ref_sweeps.append(sr)
+                es.es_mesh_features(ctx, JU, J, x, feat[0])
+                o = net.infer(feat)
+                es.es_mesh_warm_start(ctx, x, o[0], xs)
+                for t, c in solvers.items():
+                    sp, _ = es.es_mesh_solve(c, JU, J, x, None, xp)
+                    sw, pk = es.es_mesh_solve(c, JU, J, x, xs, xw, guard_ratio=guard_ratio)
+                    r = res[t]
+                    r["sweeps_plain"].append(sp)
+                    r["sweeps_warm"].append(sw)
+                    r["picked"].append(pk)
+                    dp = (xp - xr).abs() / dxi
+                    dw = (xw - xr).abs() / dxi
+                    r["dist_plain_max"].append(float(dp.max().item()))
+                    r["dist_plain_mean"].append(float(dp.mean().item()))
+                    r["dist_warm_max"].append(float(dw.max().item()))
+                    r["dist_warm_mean"].append(float(dw.mean().item()))
+            es.es_steps(ctx, JU, J, x, 1, w["t_end"])
+        rc = es.es_check(ctx)
+        if rc != 0:
+            raise es.EsError(rc, es.es_last_error(ctx))
+    return {t: {k: np.array(v) for k, v in r.items()} for t, r in res.items()}, np.array(ref_sweeps)
+
+
+def plain_at(res, dist, key="mean"):
+    """(tolerance, sweeps) of the plain solve at a given mean (or max) distance to the converged mesh: log-log
+    interpolation of the plain solves' (distance, tolerance) and (distance, sweeps) over the tolerances; None
+    outside their range."""
+    pts = sorted((float(r[f"dist_plain_{key}"].mean()), t, float(r["sweeps_plain"].mean())) for t, r in res.items())
+    d = np.log([p[0] for p in pts])
+    x = np.log(dist)
+    if x < d[0] - 1e-12 or x > d[-1] + 1e-12:
+        return None
+    tol = float(np.exp(np.interp(x, d, np.log([p[1] for p in pts]))))
+    sweeps = float(np.exp(np.interp(x, d, np.log([p[2] for p in pts]))))
+    return tol, sweeps
+
+
 def compare_runs(net, seed, n, steps, eps_cells, mu_max, precision="fp64", device="cuda",
-                 guard_ratio=GUARD_RATIO):
-    """Two full runs from the same initial data, plain and warm-started; sweeps, time, and the
-    warm run's mesh and density against the plain run's after `steps` steps."""
+                 guard_ratio=GUARD_RATIO, eps_warm=None):
+    """Two full runs from the same initial data, plain (Jacobi to eps_cells) and warm-started (to eps_warm, default
+    eps_cells); sweeps, time, and the warm run's mesh and density against the plain run's after `steps` steps."""
     torch = _torch()
     res = {}
     states = {}
     for mode in ("plain", "warm"):
-        w = riemann_workload(n, seed, eps_cells, mu_max)
+        eps = eps_cells if mode == "plain" or eps_warm is None else eps_warm
+        w = riemann_workload(n, seed, eps, mu_max)
         ctx, JU, J, x = setup(w, precision, device)
         if mode == "warm":
             net.register(ctx, guard_ratio)
