@@ -266,8 +266,10 @@ int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* 
     return ES_OK;
 }
 
-// monitor -> filter -> [warm start] -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt
-int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot) {
+// monitor -> filter -> [warm start] -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt; cfl_moving > 0:
+// the velocity kernel also takes eq. cfl with the new velocity (from the terms the step's first CFL pass left in
+// c->S1 and c->S2) and shrinks dt
+int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot, double cfl_moving = 0.0) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const double* om = enqueue_monitor(c, JU, J);
@@ -280,7 +282,8 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
     int rc = enqueue_jacobi(c, om, xn, x_start, c->nn_ratio);
     if (rc) return rc;
     k_limiter<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev);
-    k_velocity<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev, xdot);
+    k_velocity<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev, xdot, (const double*)c->S1, (const double*)c->S2,
+                               cfl_moving);
     count(c, 2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels");
@@ -294,7 +297,8 @@ bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
 
 // Sec. 4 on the FP32 pipe; c->fdisp must hold the displacement of x^n.  Writes c->fxd and xdot.
 // with_dt: the monitor kernel also sets the step's dt from the CFL maximum (k_dt's work).
-// cfl_moving > 0: the velocity kernel also takes eq. cfl with the new mesh velocity and shrinks dt.
+// cfl_moving > 0: the velocity kernel also takes eq. cfl with the new mesh velocity (from the terms the step's
+// first CFL pass left in c->S1) and shrinks dt.
 int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool with_dt, double cfl_moving = 0.0) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
@@ -306,8 +310,9 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
     float* other = (float*)c->om1;
     float* da = (float*)c->xa;
     float* db = (float*)c->xb;
-    k_mon_f<<<G, B, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0, t1, t2, c->dev, with_dt ? 1 : 0,
-                            c->p.cfl, c->p.dt_fixed);
+    k_mon_f<<<mon_f_blocks(c->g), MON_TX * MON_TY, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0,
+                                                           t1, t2, c->dev, with_dt ? 1 : 0, c->p.cfl,
+                                                           c->p.dt_fixed);
     count(c);
     // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
     const bool fuse = c->p.dim == 2;
@@ -336,8 +341,7 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
         }
     }
     k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
-    k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot, gf, (const float*)JU,
-                                 (const float*)J, cfl_moving);
+    k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot, (const float*)c->S1, cfl_moving);
     count(c, 2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels (FP32)");
@@ -345,8 +349,8 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
 }
 
 void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot = nullptr,
-                 int slot = RED_CFL) {
-    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq);
+                 int slot = RED_CFL, double* t0 = nullptr, double* t1 = nullptr) {
+    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq, t0, t1);
     count(c);
 }
 
@@ -415,15 +419,18 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const bool f32 = mesh_on_fp32(c);
+    // eq. cfl with the step's mesh velocity: the first pass (mesh at rest) leaves its node terms in the stage
+    // buffers S1 (and S2), free until the first stage, and the velocity kernel takes the second pass from them
+    const double cfl_moving = c->p.moving && !(c->p.dt_fixed > 0.0) ? c->p.cfl : 0.0;
     if (f32) {      // the displacement kernel also resets the step's reductions (k_reset's work)
         k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
         k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, nullptr, RED_CFL,
-                                c->dev);
+                                c->dev, cfl_moving > 0.0 ? (float*)c->S1 : nullptr);
         count(c, 2);
     } else {
         k_reset<<<1, 32, 0, s>>>(c->dev);
         count(c);
-        enqueue_cfl(c, JU, J, x);
+        enqueue_cfl(c, JU, J, x, nullptr, RED_CFL, cfl_moving > 0.0 ? (double*)c->S1 : nullptr, (double*)c->S2);
     }
     const bool dt_in_mesh = f32 && c->p.moving;       // the FP32 monitor kernel sets dt
     if (!dt_in_mesh) {
@@ -434,16 +441,10 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
     if (c->p.moving) {
-        // eq. cfl with the step's mesh velocity (the FP32 velocity kernel takes it in the same pass)
-        const double cfl_moving = c->p.dt_fixed > 0.0 ? 0.0 : c->p.cfl;
-        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true, cfl_moving) : enqueue_mesh(c, JU, J, x, c->xdot);
+        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true, cfl_moving)
+                     : enqueue_mesh(c, JU, J, x, c->xdot, cfl_moving);
         if (rc) return rc;
         xdot = c->xdot;
-        if (!f32 && cfl_moving > 0.0) {
-            enqueue_cfl(c, JU, J, x, c->xdot, RED_CFL2);
-            k_dt_moving<<<1, 32, 0, s>>>(c->dev, c->p.cfl);
-            count(c);
-        }
     }
     StageParams P = stage_params(c);
     P.dt_dev = &c->dev->dt;

@@ -126,7 +126,7 @@ __global__ void k_reset(DevScalars* d) {
 // (eq. VCLCoeff); xdot = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
 template <class TS>
 __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const double* x, const double* xdot, int slot,
-                      DevScalars* d) {
+                      DevScalars* d, double* t0, double* t1) {
     const int N = g.n1 * g.n2;
     double m = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
@@ -145,19 +145,38 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
         const double c = sqrt(fmax(c2, 0.0));
         const double xd1 = xdot != nullptr ? xdot[id] : 0.0;
         double tot;
+        const bool ok = c2 > 0.0;
         if (g.dim == 1) {
             tot = (fabs(-xd1 + v1) + c) * iJ * g.inv_dxi[0];
+            if (t0) {
+                const double f = iJ * g.inv_dxi[0];
+                t0[id] = v1 * f;
+                t0[N + id] = f;
+                t0[2 * N + id] = ok ? c * f : 1e300;
+            }
         } else {
             const double xd2 = xdot != nullptr ? xdot[N + id] : 0.0;
             const double x1 = dcoord(g, x, i, j, 0, 0), x2 = dcoord(g, x, i, j, 0, 1);
             const double y1 = dcoord(g, x, i, j, 1, 0), y2 = dcoord(g, x, i, j, 1, 1);
             const double a1 = y2, b1 = -x2;          // J dxi_1/dx
             const double a2 = -y1, b2 = x1;          // J dxi_2/dx
-            const double t1 = -(xd1 * a1 + xd2 * b1), t2 = -(xd1 * a2 + xd2 * b2);     // J xi_{k,t}
-            tot = (fabs(t1 + (a1 * v1 + b1 * v2)) + sqrt(a1 * a1 + b1 * b1) * c) * iJ * g.inv_dxi[0] +
-                  (fabs(t2 + (a2 * v1 + b2 * v2)) + sqrt(a2 * a2 + b2 * b2) * c) * iJ * g.inv_dxi[1];
+            const double tx1 = -(xd1 * a1 + xd2 * b1), tx2 = -(xd1 * a2 + xd2 * b2);     // J xi_{k,t}
+            const double n1c = sqrt(a1 * a1 + b1 * b1) * c, n2c = sqrt(a2 * a2 + b2 * b2) * c;
+            tot = (fabs(tx1 + (a1 * v1 + b1 * v2)) + n1c) * iJ * g.inv_dxi[0] +
+                  (fabs(tx2 + (a2 * v1 + b2 * v2)) + n2c) * iJ * g.inv_dxi[1];
+            if (t0) {
+                const double f1 = iJ * g.inv_dxi[0], f2 = iJ * g.inv_dxi[1];
+                t0[id] = (a1 * v1 + b1 * v2) * f1;
+                t0[N + id] = a1 * f1;
+                t0[2 * N + id] = b1 * f1;
+                t0[3 * N + id] = ok ? n1c * f1 : 1e300;
+                t1[id] = (a2 * v1 + b2 * v2) * f2;
+                t1[N + id] = a2 * f2;
+                t1[2 * N + id] = b2 * f2;
+                t1[3 * N + id] = ok ? n2c * f2 : 0.0;
+            }
         }
-        if (!(c2 > 0.0)) tot = 1e300;
+        if (!ok) tot = 1e300;
         m = fmax(m, tot);
     }
     m = block_reduce_max(m);
@@ -544,14 +563,39 @@ __global__ void k_limiter(GridParams g, const double* xn, const double* xa, cons
 }
 
 __global__ void k_velocity(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d,
-                           double* xdot) {
+                           double* xdot, const double* t0, const double* t1, double cfl) {
     const int N = g.n1 * g.n2;
     const double* xit = jacobi_result(d, xn, xa, xb);
     const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
     const double dt = d->dt;
     const double f = dt > 0.0 ? gam / dt : 0.0;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
-        xdot[id] = f * (xit[id] - xn[id]);
+    if (cfl > 0.0) {
+        // per node: the velocity, then eq. cfl's term with it; the last block to finish shrinks dt
+        double m = 0.0;
+        for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+            const double v1 = f * (xit[id] - xn[id]);
+            xdot[id] = v1;
+            double v2 = 0.0;
+            if (g.dim == 2) {
+                v2 = f * (xit[N + id] - xn[N + id]);
+                xdot[N + id] = v2;
+            }
+            m = fmax(m, cfl_moving_term(t0, t1, size_t(N), size_t(id), g.dim, v1, v2));
+        }
+        m = block_reduce_max(m);
+        if (threadIdx.x == 0) {
+            atomic_max_pos(&d->red[RED_CFL2], m);
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {          // every block's maximum is in: every block has read dt
+                shrink_dt_to(d, __longlong_as_double((long long)atomicAdd(&d->red[RED_CFL2], 0ULL)), cfl);
+                d->done = 0u;
+            }
+        }
+    } else {
+        for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
+            xdot[id] = f * (xit[id] - xn[id]);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d->gamma = gam;
         d->sweeps_total += d->sweeps;
@@ -604,8 +648,8 @@ __global__ void k_warm_start(GridParams g, const double* xn, const float* out, d
 // Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)
 // and FP32 mesh velocity, once per step (the base is linear in the node index,
 // so delta_k of it is exactly dxi_k e_k)
-__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd,
-                           DevScalars* rst) {
+__global__ void k_mesh_f32(GridParams g, const double* __restrict__ x, const double* __restrict__ xdot,
+                           float* __restrict__ disp, float* __restrict__ fxd, DevScalars* rst) {
     const int N = g.n1 * g.n2;
     if (rst && blockIdx.x == 0 && threadIdx.x == 0) reset_scalars(rst);
     const double x00 = x[0];
@@ -616,7 +660,8 @@ __global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, fl
         const int i = id % g.n1, j = id / g.n1;
         disp[id] = float(x[id] - (x00 + i * dxi1));
         if (g.dim == 2) disp[N + id] = float(x[N + id] - (y00 + j * dxi2));
-        for (int k = 0; k < g.dim; ++k) fxd[k * N + id] = xdot ? float(xdot[k * N + id]) : 0.0f;
+        if (xdot)                           // fxd is read only where a velocity was given
+            for (int k = 0; k < g.dim; ++k) fxd[k * N + id] = float(xdot[k * N + id]);
     }
 }
 
@@ -644,9 +689,10 @@ void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const voi
 }
 
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
-                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s) {
-    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d);
-    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d);
+                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s, double* t0,
+                double* t1) {
+    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d, t0, t1);
+    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d, t0, t1);
 }
 
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,

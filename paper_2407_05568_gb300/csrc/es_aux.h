@@ -66,13 +66,26 @@ __device__ __forceinline__ void shrink_dt_for_mesh(DevScalars* d, double cfl) {
     shrink_dt_to(d, __longlong_as_double((long long)d->red[RED_CFL2]), cfl);
 }
 
+// eq. cfl's node term with a mesh velocity from the terms the mesh-at-rest pass stored: per direction k,
+// S_k = (n_k . v) f_k, P_k = n_k1 f_k, Q_k = n_k2 f_k, C_k = |n_k| c f_k with f_k = 1/(J dxi_k), fields
+// 0..3 (k = 1) in t0 and 4..7 (k = 2) in t1; in 1D S, P, C in t0.  C_k is HUGE at a node without a real
+// sound speed.  The term is sum_k |S_k - (xdot_1 P_k + xdot_2 Q_k)| + C_k.
+template <class T>
+__device__ __forceinline__ T cfl_moving_term(const T* t0, const T* t1, size_t N, size_t id, int dim, T xd1, T xd2) {
+    if (dim == 1) return fabs(t0[id] - xd1 * t0[N + id]) + t0[2 * N + id];
+    return fabs(t0[id] - (xd1 * t0[N + id] + xd2 * t0[2 * N + id])) + t0[3 * N + id] +
+           fabs(t1[id] - (xd1 * t1[N + id] + xd2 * t1[2 * N + id])) + t1[3 * N + id];
+}
+
 // kernels templated on the state type are launched through these (f32: float state)
 void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int grid, cudaStream_t s);
 void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
                          const void* J, void* JU, bool f32, int grid, cudaStream_t s);
-// xdot (nullable): the mesh velocity of eq. VCLCoeff's J xi_t; slot: RED_CFL or RED_CFL2
+// xdot (nullable): the mesh velocity of eq. VCLCoeff's J xi_t; slot: RED_CFL or RED_CFL2; t0, t1 (nullable):
+// also store the node terms cfl_moving_term reads (mesh at rest only)
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
-                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s);
+                const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s,
+                double* t0 = nullptr, double* t1 = nullptr);
 // total entropy rate sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt) vol in FP64 with a compensated, fixed-order
 // reduction: out[0] the rate, out[1] the sum of the magnitudes of its terms (device); part holds 3 grid doubles
 void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const void* J, const void* dJU,
@@ -85,8 +98,9 @@ __global__ void k_dt_moving(DevScalars* d, double cfl);
 __global__ void k_set_dt(DevScalars* d, double dt);
 __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
 // rst (nullable): also runs k_reset's work (the first kernel of a mixed-form step)
-__global__ void k_mesh_f32(GridParams g, const double* x, const double* xdot, float* disp, float* fxd,
-                           DevScalars* rst = nullptr);
+// fxd is written only when xdot is given (its readers take it only then)
+__global__ void k_mesh_f32(GridParams g, const double* __restrict__ x, const double* __restrict__ xdot,
+                           float* __restrict__ disp, float* __restrict__ fxd, DevScalars* rst = nullptr);
 __global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, const double* GF, double* t0,
                             double* t1, double* t2, DevScalars* d);
 __global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, const double* t1, const double* t2,
@@ -98,8 +112,10 @@ __global__ void k_jacobi_loop(GridParams g, const double* omega, const double* x
                               DevScalars* d, double eps, int mu, cudaGraphConditionalHandle h);
 __global__ void k_pick(DevScalars* d, int check, double eps, double ratio);
 __global__ void k_limiter(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d);
+// cfl > 0: also eq. cfl with the new velocity from the stored terms (t0, t1) into RED_CFL2, and the last block
+// shrinks dt to it
 __global__ void k_velocity(GridParams g, const double* xn, const double* xa, const double* xb, DevScalars* d,
-                           double* xdot);
+                           double* xdot, const double* t0 = nullptr, const double* t1 = nullptr, double cfl = 0.0);
 __global__ void k_jacobi_out(GridParams g, const double* xn, const double* xa, const double* xb,
                              const DevScalars* d, double* xout, float* disp);
 __global__ void k_features(GridParams g, const double* omega, const double* GF, const double* x, float* feat);

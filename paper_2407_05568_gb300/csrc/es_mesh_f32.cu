@@ -135,7 +135,8 @@ __device__ __forceinline__ bool fixed_node_f(const GridParams& g, int i, int j) 
 // J xi_{k,t} = -xdot . n_k, at node id with mesh velocity (xd1, xd2); a node without a real sound speed
 // gives 3e38 (the time step then collapses and the admissibility check reports the state)
 __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G, const float* JU, const float* J,
-                                            const float* disp, int id, float xd1, float xd2) {
+                                            const float* disp, int id, float xd1, float xd2, float* t0 = nullptr,
+                                            float* t1 = nullptr) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
     const float idx1 = float(g.inv_dxi[0]), idx2 = float(g.inv_dxi[1]);
@@ -150,9 +151,16 @@ __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G
     const float iom = 1.0f / (1.0f - G.b * rho);
     const float c2 = (1.0f + G.delta) * G.R * T * iom * iom - 2.0f * G.a * rho;
     const float c = sqrtf(fmaxf(c2, 0.0f));
+    const bool ok = c2 > 0.0f;
     float tot;
     if (g.dim == 1) {
         tot = (fabsf(v1 - xd1) + c) * iJ * idx1;
+        if (t0) {                                  // the terms of cfl_moving_term
+            const float f = iJ * idx1;
+            t0[id] = v1 * f;
+            t0[N + id] = f;
+            t0[2 * N + id] = ok ? c * f : 3.0e38f;
+        }
     } else {
         float x1, x2, y1, y2;
         if (i >= 3 && i < g.n1 - 3 && j >= 3 && j < g.n2 - 3) {
@@ -178,10 +186,22 @@ __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G
         }
         const float a1 = y2, b1 = -x2;        // J dxi_1/dx
         const float a2 = -y1, b2 = x1;        // J dxi_2/dx
-        tot = (fabsf(a1 * (v1 - xd1) + b1 * (v2 - xd2)) + sqrtf(a1 * a1 + b1 * b1) * c) * iJ * idx1 +
-              (fabsf(a2 * (v1 - xd1) + b2 * (v2 - xd2)) + sqrtf(a2 * a2 + b2 * b2) * c) * iJ * idx2;
+        const float n1c = sqrtf(a1 * a1 + b1 * b1) * c, n2c = sqrtf(a2 * a2 + b2 * b2) * c;
+        tot = (fabsf(a1 * (v1 - xd1) + b1 * (v2 - xd2)) + n1c) * iJ * idx1 +
+              (fabsf(a2 * (v1 - xd1) + b2 * (v2 - xd2)) + n2c) * iJ * idx2;
+        if (t0) {                                  // the terms of cfl_moving_term
+            const float f1 = iJ * idx1, f2 = iJ * idx2;
+            t0[id] = (a1 * v1 + b1 * v2) * f1;
+            t0[N + id] = a1 * f1;
+            t0[2 * N + id] = b1 * f1;
+            t0[3 * N + id] = ok ? n1c * f1 : 3.0e38f;
+            t1[id] = (a2 * v1 + b2 * v2) * f2;
+            t1[N + id] = a2 * f2;
+            t1[2 * N + id] = b2 * f2;
+            t1[3 * N + id] = ok ? n2c * f2 : 0.0f;
+        }
     }
-    if (!(c2 > 0.0f)) tot = 3.0e38f;
+    if (!ok) tot = 3.0e38f;
     return tot;
 }
 
@@ -190,13 +210,14 @@ __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G
 // eq. cfl on the FP32 pipe: the maximum over the nodes of cfl_node_f goes to d->red[slot]; vel = nullptr
 // is a mesh at rest.
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
-                        int slot, DevScalars* d) {
+                        int slot, DevScalars* d, float* terms) {
     const int N = g.n1 * g.n2;
+    float* t1 = terms ? terms + 4 * size_t(N) : nullptr;
     float m = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const float xd1 = vel != nullptr ? vel[id] : 0.0f;
         const float xd2 = vel != nullptr && g.dim == 2 ? vel[N + id] : 0.0f;
-        m = fmaxf(m, cfl_node_f(g, G, JU, J, disp, id, xd1, xd2));
+        m = fmaxf(m, cfl_node_f(g, G, JU, J, disp, id, xd1, xd2, terms, t1));
     }
     m = block_max_f32(m);
     if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], double(m));
@@ -232,36 +253,56 @@ __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const fl
     }
 }
 
-// the monitor terms in one pass: the density and G of the +-1 neighbours are
-// recomputed from their state (a few float operations against a launch and a round trip of two
-// fields).  With do_dt, thread 0 also sets the step's dt from the CFL maximum (k_dt's work:
-// the CFL kernel has finished when this one starts).
-__global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
-                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed) {
+// the monitor terms in one pass over MON_TX x MON_TY tiles (MON_TX x 1 in 1D): the density and G of the
+// tile's nodes and of a one-node halo (ghost rule of the state) are computed once each in double-float and kept
+// in shared memory, then every node forms its differences from them.  With do_dt, thread 0 also sets the step's
+// dt from the CFL maximum (k_dt's work: the CFL kernel has finished when this one starts).
+__global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
+                                                           MonitorParams mp, float* t0, float* t1, float* t2,
+                                                           DevScalars* d, int do_dt, double cfl, double dt_fixed) {
+    constexpr int CAP = (MON_TX + 2) * (MON_TY + 2);      // >= MON_TX * MON_TY + 2, the 1D tile with its halo
+    __shared__ float srh[CAP], srl[CAP], sgh[CAP], sgl[CAP];
     if (do_dt && blockIdx.x == 0 && threadIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
+    const int TW = g.dim == 2 ? MON_TX : MON_TX * MON_TY;  // tile width; 1D tiles are one row of all threads
+    const int HW = TW + 2;
+    const int ntx = (g.n1 + TW - 1) / TW;
+    const int i0 = (blockIdx.x % ntx) * TW;
+    const int j0 = g.dim == 2 ? (blockIdx.x / ntx) * MON_TY : 0;
+    const int hh = g.dim == 2 ? MON_TY + 2 : 1;
+    for (int t = threadIdx.x; t < HW * hh; t += blockDim.x) {
+        const int lx = t % HW, ly = t / HW;
+        const int gi = i0 - 1 + lx, gj = g.dim == 2 ? j0 - 1 + ly : 0;
+        const int sidx = (g.dim == 2 ? state_index(gj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(gi, g.n1, g.bc[0]);
+        mixed::df r, Gv;
+        mon_field_df(g, G, JU, J, N, P, sidx, &r, &Gv);
+        srh[t] = r.hi;
+        srl[t] = r.lo;
+        sgh[t] = Gv.hi;
+        sgl[t] = Gv.lo;
+    }
+    __syncthreads();
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
-        const int i = id % g.n1, j = id / g.n1;
-        mixed::df r0, G0;
-        mon_field_df(g, G, JU, J, N, P, id, &r0, &G0);
+    const int tx = threadIdx.x % TW, ty = threadIdx.x / TW;
+    const int i = i0 + tx, j = j0 + ty;
+    if (i < g.n1 && (g.dim == 1 || j < g.n2)) {
+        const int id = j * g.n1 + i;
+        const int c = (g.dim == 2 ? ty + 1 : 0) * HW + tx + 1;
+        const mixed::df r0 = {srh[c], srl[c]}, G0 = {sgh[c], sgl[c]};
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {                  // fixed bound: no dynamic indexing of g
+        for (int k = 0; k < 2; ++k) {
             if (k >= g.dim) break;
-            const int di = k == 0, dj = k == 1;
             const float h = float(g.inv_dxi[k]);
-            const int sp = (g.dim == 2 ? state_index(j + dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i + di, g.n1, g.bc[0]);
-            const int sm = (g.dim == 2 ? state_index(j - dj, g.n2, g.bc[1]) : 0) * g.n1 + state_index(i - di, g.n1, g.bc[0]);
-            mixed::df rp, Gp, rm, Gm;
-            mon_field_df(g, G, JU, J, N, P, sp, &rp, &Gp);
-            mon_field_df(g, G, JU, J, N, P, sm, &rm, &Gm);
+            const int off = k == 0 ? 1 : HW;
+            const mixed::df rp = {srh[c + off], srl[c + off]}, Gp = {sgh[c + off], sgl[c + off]};
+            const mixed::df rm = {srh[c - off], srl[c - off]}, Gm = {sgh[c - off], sgl[c - off]};
             const float a = mixed::df_diff(rp, rm) * 0.5f * h, b = mixed::df_diff(Gp, Gm) * 0.5f * h;
-            const float c = mixed::df_second_diff(Gp, G0, Gm) * h * h, e = mixed::df_second_diff(rp, r0, rm) * h * h;
+            const float cc = mixed::df_second_diff(Gp, G0, Gm) * h * h, e = mixed::df_second_diff(rp, r0, rm) * h * h;
             gr += a * a;
             gg += b * b;
-            lg += c * c;
+            lg += cc * cc;
             lr += e * e;
         }
         float v0, v1, v2;
@@ -277,9 +318,9 @@ __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
         t0[id] = v0;
         t1[id] = v1;
         t2[id] = v2;
-        m0 = fmaxf(m0, v0);
-        m1 = fmaxf(m1, v1);
-        m2 = fmaxf(m2, v2);
+        m0 = v0;
+        m1 = v1;
+        m2 = v2;
     }
     m0 = block_max_f32(m0);
     m1 = block_max_f32(m1);
@@ -289,6 +330,11 @@ __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
         atomic_max_pos(&d->red[RED_MON1], double(m1));
         atomic_max_pos(&d->red[RED_MON2], double(m2));
     }
+}
+
+int mon_f_blocks(const GridParams& g) {
+    if (g.dim == 1) return (g.n1 + MON_TX * MON_TY - 1) / (MON_TX * MON_TY);
+    return ((g.n1 + MON_TX - 1) / MON_TX) * ((g.n2 + MON_TY - 1) / MON_TY);
 }
 
 
@@ -397,6 +443,7 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
     const float* xit = jacobi_result_f(d, d0, da, db);
     float m = 1.0f;
     const float hk[2] = {float(1.0 / g.inv_dxi[0]), float(1.0 / g.inv_dxi[1])};
+#pragma unroll 4
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         for (int k = 0; k < g.dim; ++k) {
@@ -412,10 +459,11 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
 }
 
 // xdot = Delta_gamma (x^[mu] - x^n) / dt: float (for the stage kernels) and double (the API's array).
-// cfl > 0 also takes eq. cfl with this mesh velocity at each node (k_cfl_f's RED_CFL2 pass, on the same
-// float velocity), and the last block to finish shrinks the step's dt to it (k_dt_moving's work).
-__global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
-                             float* fxd, double* xdot, GasF32 G, const float* JU, const float* J, double cfl) {
+// cfl > 0 also takes eq. cfl with this mesh velocity at each node from the terms the mesh-at-rest CFL pass
+// stored (cfl_moving_term), and the last block to finish shrinks the step's dt to it (k_dt_moving's work).
+__global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const float* __restrict__ da,
+                             const float* __restrict__ db, DevScalars* d, float* __restrict__ fxd,
+                             double* __restrict__ xdot, const float* __restrict__ terms, double cfl) {
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
     const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
@@ -432,7 +480,7 @@ __global__ void k_velocity_f(GridParams g, const float* d0, const float* da, con
             fxd[N + id] = v2;
             xdot[N + id] = double(v2);
         }
-        if (cfl > 0.0) m = fmaxf(m, cfl_node_f(g, G, JU, J, d0, id, v1, v2));
+        if (cfl > 0.0) m = fmaxf(m, cfl_moving_term(terms, terms + 4 * size_t(N), size_t(N), size_t(id), g.dim, v1, v2));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d->gamma = gam;

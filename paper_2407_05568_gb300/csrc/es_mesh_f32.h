@@ -26,13 +26,18 @@ inline GasF32 gas_f32(const Gas& g) {
 }
 
 // JU, J: the mixed form's (hi, lo) float planes; disp: the FP32 displacement [dim][N]
-// vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity)
+// vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity);
+// terms (nullable, 8 N floats): also store the node terms of cfl_moving_term (fields 0..3, then 4..7 at 4 N)
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
-                        int slot, DevScalars* d);
+                        int slot, DevScalars* d, float* terms = nullptr);
 // rhoF, GF: 2 N floats each, (hi, lo) planes of the density and the fundamental derivative
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
+// monitor terms over MON_TX x MON_TY tiles (one row of MON_TX * MON_TY nodes in 1D); launch with
+// mon_f_blocks(g) blocks of MON_TX * MON_TY threads
+constexpr int MON_TX = 32, MON_TY = 8;
 __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
                         float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed);
+int mon_f_blocks(const GridParams& g);
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega);
 __global__ void k_filter_f(GridParams g, const float* in, float* out);
@@ -45,8 +50,10 @@ void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const flo
                          const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s);
 __global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
                                  DevScalars* dv);
-// cfl > 0: also eq. cfl with the new velocity into RED_CFL2, and dt = min(dt, cfl / that maximum)
-__global__ void k_velocity_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d,
-                             float* fxd, double* xdot, GasF32 G, const float* JU, const float* J, double cfl);
+// cfl > 0: also eq. cfl with the new velocity from k_cfl_f's stored terms into RED_CFL2, and
+// dt = min(dt, cfl / that maximum)
+__global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const float* __restrict__ da,
+                             const float* __restrict__ db, DevScalars* d, float* __restrict__ fxd,
+                             double* __restrict__ xdot, const float* __restrict__ terms, double cfl);
 
 }  // namespace es
