@@ -33,7 +33,7 @@ struct Ctx3 {
     size_t NKk[3];            // nodes of direction k's metric grid (3 ghosts along xi_k only)
     double* XE;               // stage coordinates on the extended grid [3][NE]
     double* D;                // cross-form products delta_l[x_p] x_q on the extended grid [9][NE] (k3_deriv)
-    double* NK[3];            // J dxi_k/dx_j on direction k's metric grid [3][NKk]
+    double* NK[3];            // J dxi_k/dx_j on direction k's metric grid [3][NKk] (mixed form: floats)
     double* NF;               // node fields of the stage state [F3_COUNT][N] (mixed: float fields)
     double* RH;               // right-hand sides accumulated over the directions [6][N] (mixed: float)
     // mesh scratch (the context's buffers)
@@ -74,6 +74,9 @@ int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xd
 int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cudaStream_t s, cudaError_t* err);
 // the mixed form's kernels (es_3d_mixed.cu)
 cudaError_t d3f_prepare();
+// the stage metrics of the mixed form (double-float arithmetic, float metrics in NK[k] as [3][NKk])
+int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const double* dt_dev, double dt_host,
+                cudaStream_t s);
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s);
 int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s);
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include "es_3d.h"
+#include "es_3d_grid.cuh"
 #include "es_device.cuh"
 #include "es_internal.h"
 #include "es_mesh_f32.h"
@@ -45,10 +46,6 @@ enum FieldM {
     MS_COUNT
 };
 static_assert(MF_COUNT <= 23, "the float node fields reuse the FP64 node-field buffer");
-
-__device__ __forceinline__ size_t idx3(const Grid3& g, int i1, int i2, int i3) {
-    return (size_t(i3) * g.n[1] + i2) * g.n[0] + i1;
-}
 
 // ---------------------------------------------------------------- node fields
 // From the double-float state (JU: hi plane [5][N] then lo plane; J: hi then lo) in double-float
@@ -299,7 +296,7 @@ struct Dir3FParams {
     WenoF weno;
     int diss;
     const float* NF;          // float node fields [MF_COUNT][N]
-    const double* NK;         // metrics of this direction [3][M]
+    const float* NK;          // metrics of this direction [3][M] (float, from k3f_metric)
     const double* xdot;       // nullable
     float* RH;                // accumulated right-hand sides [6][N] (float)
     int first, last;
@@ -463,10 +460,10 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(const __grid_constant__ Dir
             else if (K == 1) { j1 = a; j2 = se; j3 = b; }
             else { j1 = a; j2 = b; j3 = se; }
             const size_t mi = (size_t(j3) * M2 + j2) * M1 + j1;
-            const double nx = P.NK[mi], ny = P.NK[M + mi], nz = P.NK[2 * M + mi];
-            S[M_NX * NB + bx] = float(nx);
-            S[M_NY * NB + bx] = float(ny);
-            S[M_NZ * NB + bx] = float(nz);
+            const float nx = P.NK[mi], ny = P.NK[M + mi], nz = P.NK[2 * M + mi];
+            S[M_NX * NB + bx] = nx;
+            S[M_NY * NB + bx] = ny;
+            S[M_NZ * NB + bx] = nz;
             double xt = 0.0;
             if (P.xdot) {
                 double xd[3] = {0.0, 0.0, 0.0};
@@ -732,14 +729,118 @@ static bool tmap_for(Ctx3* d, int k, int shape, CUtensorMap* out) {
     return true;
 }
 
+// ---------------------------------------------------------------- metrics in double-float
+// The cross-form metrics of eq. SCLCoeff formed as the FP64 path forms them (k3_coords, k3_deriv, k3_metric:
+// stage coordinates on the mesh extended by 3 ghosts, the products delta_l[x_p] x_q once per node, and each
+// direction's metric from differences of those products), in double-float arithmetic on the FP32 pipe: the
+// stage coordinates are split into (hi, lo) floats once and every product and difference keeps a 48-bit
+// significand, so the metric is rounded once, to the float the direction kernels read.  On GB300 the FP64
+// version of these three kernels took more time than the float direction kernels.
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+
+// the coordinates of x_s = xn + cst dt xdot on the extended grid as (hi, lo) planes: XEh [3][NE], XEl [3][NE]
+__global__ void k3f_coords(Grid3 g, const double* xn, const double* xdot, double cst, const double* dt_dev,
+                           double dt_host, float* XEh, float* XEl) {
+    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
+    const unsigned E1 = g.n[0] + 6, E2 = g.n[1] + 6, E3 = g.n[2] + 6;
+    const size_t NE = size_t(E1) * E2 * E3;
+    const double cdt = cst * (dt_dev ? *dt_dev : dt_host);
+    for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
+        const unsigned eu = unsigned(e);                      // NE < 2^31 (es_create limits N to 2^30)
+        const int i1 = int(eu % E1) - 3, i2 = int((eu / E1) % E2) - 3, i3 = int(eu / (E1 * E2)) - 3;
+        const bool in = inside3(g, i1, i2, i3, 0);
+        const size_t id = in ? idx3(g, i1, i2, i3) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v;
+            if (in) v = xdot ? xn[c * N + id] + cdt * xdot[c * N + id] : xn[c * N + id];
+            else v = ghost_value3(g, xn + c * N, xdot ? xdot + c * N : nullptr, cdt, i1, i2, i3, c);
+            const float hi = float(v);
+            XEh[c * NE + e] = hi;
+            XEl[c * NE + e] = float(v - double(hi));
+        }
+    }
+}
+
+// D[3 l + j] = delta_l[x_p] x_q (p = (j + 1) % 3, q = (j + 2) % 3; delta_l undivided, 0 where the xi_l index is
+// not interior) as (hi, lo) planes Dh, Dl [9][NE]
+__global__ void k3f_deriv(Grid3 g, const float* XEh, const float* XEl, float* Dh, float* Dl) {
+    const unsigned E1 = g.n[0] + 6, E2 = g.n[1] + 6, E3 = g.n[2] + 6;
+    const size_t NE = size_t(E1) * E2 * E3;
+    const size_t st[3] = {1, size_t(E1), size_t(E1) * E2};
+    for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
+        const unsigned eu = unsigned(e);
+        const int ee[3] = {int(eu % E1), int((eu / E1) % E2), int(eu / (E1 * E2))};
+        const df x[3] = {{XEh[e], XEl[e]}, {XEh[NE + e], XEl[NE + e]}, {XEh[2 * NE + e], XEl[2 * NE + e]}};
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const bool ok = ee[l] >= 3 && ee[l] < g.n[l] + 3;
+            df dl[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                df acc = {0.0f, 0.0f};
+                if (ok) {
+#pragma unroll
+                    for (int m = 1; m <= 3; ++m) {
+                        const size_t up = p * NE + e + m * st[l], dn = p * NE + e - m * st[l];
+                        const df d = df_sub({XEh[up], XEl[up]}, {XEh[dn], XEl[dn]});
+                        acc = df_add(acc, df_mul_f(d, float(0.5 * ec_alpha(m))));
+                    }
+                }
+                dl[p] = acc;
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const df v = df_mul(dl[(j + 1) % 3], x[(j + 2) % 3]);
+                Dh[(3 * l + j) * NE + e] = v.hi;
+                Dl[(3 * l + j) * NE + e] = v.lo;
+            }
+        }
+    }
+}
+
+// J dxi_k/dx_j on direction k's grid (n_k + 6 nodes along xi_k, interior across), rounded to float [3][M]
+__global__ void k3f_metric(Grid3 g, int k, const float* Dh, const float* Dl, float* NKo) {
+    const unsigned E1 = g.n[0] + 6, E2 = g.n[1] + 6;
+    const size_t NE = size_t(E1) * E2 * (g.n[2] + 6);
+    unsigned m1 = g.n[0], m2 = g.n[1], m3 = g.n[2];
+    if (k == 0) m1 += 6;
+    else if (k == 1) m2 += 6;
+    else m3 += 6;
+    const size_t M = size_t(m1) * m2 * m3;
+    const int l = (k + 1) % 3, m = (k + 2) % 3;
+    const float scale = float(g.inv_dxi[l] * g.inv_dxi[m]);
+    const size_t stl = l == 0 ? 1 : (l == 1 ? size_t(E1) : size_t(E1) * E2);
+    const size_t stm = m == 0 ? 1 : (m == 1 ? size_t(E1) : size_t(E1) * E2);
+    for (size_t t = blockIdx.x * size_t(blockDim.x) + threadIdx.x; t < M; t += size_t(gridDim.x) * blockDim.x) {
+        const unsigned tu = unsigned(t);
+        const int a1 = int(tu % m1), a2 = int((tu / m1) % m2), a3 = int(tu / (m1 * m2));
+        const size_t e = eidx(g, a1 + (k == 0 ? 0 : 3), a2 + (k == 1 ? 0 : 3), a3 + (k == 2 ? 0 : 3));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const size_t ol = size_t(3 * l + j) * NE, om = size_t(3 * m + j) * NE;    // delta_l[x_p] x_q, delta_m[...]
+            df A = {0.0f, 0.0f}, B = {0.0f, 0.0f};
+#pragma unroll
+            for (int a = 1; a <= 3; ++a) {
+                const float h = float(0.5 * ec_alpha(a));
+                const size_t sm = a * stm, sl = a * stl;
+                A = df_add(A, df_mul_f(df_sub({Dh[ol + e + sm], Dl[ol + e + sm]}, {Dh[ol + e - sm], Dl[ol + e - sm]}), h));
+                B = df_add(B, df_mul_f(df_sub({Dh[om + e + sl], Dl[om + e + sl]}, {Dh[om + e - sl], Dl[om + e - sl]}), h));
+            }
+            const df diff = df_sub(A, B);
+            NKo[j * M + t] = (diff.hi + diff.lo) * scale;
+        }
+    }
+}
+
 // CFL (eq. cfl) from the float node fields and the FP64 metrics: J xi_{k,t} = -xdot . n_k, xdot = nullptr
 // is a mesh at rest; the maximum goes to d->red[slot]
-__global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const double* NK0, const double* NK1,
-                         const double* NK2, const double* xdot, int slot, DevScalars* d) {
+__global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const float* NK0, const float* NK1,
+                         const float* NK2, const double* xdot, int slot, DevScalars* d) {
     const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
     const size_t M[3] = {size_t(g.n[0] + 6) * g.n[1] * g.n[2], size_t(g.n[0]) * (g.n[1] + 6) * g.n[2],
                          size_t(g.n[0]) * g.n[1] * (g.n[2] + 6)};
-    const double* NK[3] = {NK0, NK1, NK2};
+    const float* NK[3] = {NK0, NK1, NK2};
     const float a = float(Gd.a), R = float(Gd.R), delta = float(Gd.delta);
     float mx = 0.0f;
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < N; id += size_t(gridDim.x) * blockDim.x) {
@@ -755,7 +856,7 @@ __global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const
         for (int k = 0; k < 3; ++k) {
             const int m1 = g.n[0] + (k == 0 ? 6 : 0), m2 = g.n[1] + (k == 1 ? 6 : 0);
             const size_t mi = (size_t(i3 + (k == 2 ? 3 : 0)) * m2 + i2 + (k == 1 ? 3 : 0)) * m1 + i1 + (k == 0 ? 3 : 0);
-            const float n0 = float(NK[k][mi]), n1 = float(NK[k][M[k] + mi]), n2 = float(NK[k][2 * M[k] + mi]);
+            const float n0 = NK[k][mi], n1 = NK[k][M[k] + mi], n2 = NK[k][2 * M[k] + mi];
             tot += (fabsf(n0 * vr[0] + n1 * vr[1] + n2 * vr[2]) + sqrtf(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
                    float(g.inv_dxi[k]);
         }
@@ -1101,14 +1202,26 @@ static WenoF wenof(const Weno& w) {
     return W;
 }
 
+int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const double* dt_dev, double dt_host,
+                cudaStream_t s) {
+    const int G = d->grid;
+    const size_t NE = d->NE;
+    float* XEh = (float*)d->XE;                   // [3][NE] doubles hold the (hi, lo) float planes
+    float* Dh = (float*)d->D;                     // [9][NE] likewise
+    k3f_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, XEh, XEh + 3 * NE);
+    k3f_deriv<<<G, 256, 0, s>>>(d->g, XEh, XEh + 3 * NE, Dh, Dh + 9 * NE);
+    for (int k = 0; k < 3; ++k) k3f_metric<<<G, 256, 0, s>>>(d->g, k, Dh, Dh + 9 * NE, (float*)d->NK[k]);
+    return 5;
+}
+
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s) {
     k3_nodes_f<<<d->grid, 256, 0, s>>>(d->g, gasf(d->gas), (const float*)JU, (const float*)J, (float*)d->NF, st);
     return 1;
 }
 
 int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s) {
-    k3_cfl_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)d->NF, (const float*)J, d->NK[0], d->NK[1],
-                                      d->NK[2], xdot, slot, dv);
+    k3_cfl_f<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const float*)d->NF, (const float*)J, (const float*)d->NK[0],
+                                      (const float*)d->NK[1], (const float*)d->NK[2], xdot, slot, dv);
     return 1;
 }
 
@@ -1143,7 +1256,7 @@ int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cuda
     cudaError_t e = cudaGetLastError();
     int n = 0;
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-        P.NK = d->NK[k];
+        P.NK = (const float*)d->NK[k];
         P.first = k == 0;
         P.last = k == 2;
         CUtensorMap map;
