@@ -559,7 +559,7 @@ def measure_precision_sweep(args, dev, cases=None):
         for prec in ("fp64", "mixed"):
             rho, steps, ms, tile = run_to_end(w, prec, dev, dt_fixed=dt_fixed)
             res[prec] = rho
-            bx, by = TILES[prec][tile] if w["dim"] == 2 else (254, 1)
+            bx, by, _ = TILES[prec][tile] if w["dim"] == 2 else (254, 1, 256)
             row[prec] = {"l1_vs_exact": float(np.abs(rho - exact).mean()), "steps": steps, "ms": ms,
                          "cell_updates_per_s": nodes * 3 * (steps - 1) / (ms * 1e-3) if ms > 0 else None,
                          "tile": f"{bx}x{by}"}
@@ -788,31 +788,19 @@ def pin(a):
     return t.numpy()
 
 
-TILES = {"fp64": {1: (32, 8), 2: (25, 11), 3: (16, 16), 4: (32, 12), 5: (20, 10)},
-         "mixed": {1: (32, 8), 2: (25, 6), 3: (20, 8), 4: (32, 16), 5: (16, 8)}}
+# (nodes along xi_1, along xi_2, threads) of each tile shape; the mixed 384- and 320-thread shapes give two lanes
+# to each face
+TILES = {"fp64": {1: (32, 8, 288), 2: (25, 11, 384), 3: (16, 16, 288), 4: (32, 12, 416), 5: (20, 10, 224)},
+         "mixed": {1: (20, 8, 384), 2: (25, 6, 192), 3: (20, 8, 192), 4: (16, 8, 320), 5: (16, 8, 160)}}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch at 200 x 200, from one ncu capture of each
 # kernel as it is now (a kernel changed since its capture has no entry); other sizes were not captured
-TRAFFIC_200 = {"stage_kernel_fp64<2,25,11>": 2393088 + 0}
+TRAFFIC_200 = {"stage_kernel_fp64<2,25,11,384>": 2393088 + 0}
 
 
 def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
-    """Average duration of the stage kernel (stage 2 form) over 20 launches on the bench stream."""
-    import torch
-    S1 = torch.empty_like(JU)
-    S1J = torch.empty_like(J)
-    xdot = torch.zeros_like(x)
-    dt = 1e-4
-    reps = 20
-    for _ in range(3):
-        es.es_rk_stage(ctx, 2, dt, JU, J, JU, J, x, xdot, S1, S1J)
-    st = torch.cuda.Event(enable_timing=True)
-    en = torch.cuda.Event(enable_timing=True)
-    st.record(stream)
-    for _ in range(reps):
-        es.es_rk_stage(ctx, 2, dt, JU, J, JU, J, x, xdot, S1, S1J)
-    en.record(stream)
-    en.synchronize()
-    ms = st.elapsed_time(en) / reps
+    """Mean device time of the stage kernel (stage 2 form) over 20 back-to-back launches, timed by the library
+    with CUDA events on the bench stream (es_time_stage: no host work between the launches)."""
+    ms = es.es_time_stage(ctx, JU, J, x, stage=2, dt=1e-4, reps=20)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -824,9 +812,9 @@ def stage_roofline(es, ctx, JU, J, x, stream, w, nodes, precision, tile):
     peak = f64 if precision == "fp64" else f32
     nominal = perfmodel.fp64_peak_tflops(peaks) if precision == "fp64" else perfmodel.fp32_peak_tflops(peaks)
     achieved = flops / (ms * 1e-3) / 1e12
-    bx, by = TILES[precision][tile]
-    kname = ("stage_kernel_fp64" if precision == "fp64" else "stage_kernel_mixed") + f"<2,{bx},{by}>"
-    return {"bound": "alu", "kernel": kname, "tile": f"{bx}x{by}",
+    bx, by, nt = TILES[precision][tile]
+    kname = ("stage_kernel_fp64" if precision == "fp64" else "stage_kernel_mixed") + f"<2,{bx},{by},{nt}>"
+    return {"bound": "alu", "kernel": kname, "tile": f"{bx}x{by}/{nt}",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": TRAFFIC_200.get(kname) if nodes == 200 * 200 else None, "launch_ms": ms,
             "flops_per_launch": flops,

@@ -22,7 +22,9 @@
  * Three dimensions (dim = 3)
  *   The operator, the SSP-RK3 stages and the mesh redistribution in their 3D form:
  *   the cross-form metrics of Sec. 3.2 (eq. SCLCoeff), the theta/phi rotation of
- *   Sec. 3.3 and the 27-point filter of Sec. 4.  ES_PREC_FP64 only.  es_create,
+ *   Sec. 3.3 and the 27-point filter of Sec. 4, in both precision forms (the mixed
+ *   form: FP32 direction kernels, double-float metrics and state; walls and symmetry
+ *   planes in ES_PREC_FP64 only).  es_create,
  *   es_init_mesh, es_prim_to_cons, es_rhs, es_rk_stage, es_cfl_dt,
  *   es_mesh_redistribute, es_steps, es_run_host, es_autotune (four pencil shapes) and the
  *   time and status calls accept a 3D context; es_mesh_features, es_mesh_solve,
@@ -110,10 +112,13 @@ typedef struct es_params {
     int    precision;       /* ES_PREC_* */
     int    tile;            /* stage tile shape: 0 = chosen by es_autotune (run by the first es_steps
                                if not called before); k = 1 .. ES_NTILES: shape k of the precision's
-                               2D table (FP64: 32x8, 25x11, 16x16, 32x12, 20x10 nodes; mixed: 32x8, 25x6,
-                               20x8, 32x16, 16x8); in 3D the direction kernels' pencils, FP64:
+                               2D table (FP64: 32x8, 25x11, 16x16, 32x12, 20x10 nodes; mixed: 20x8 with two
+                               lanes per face, 25x6, 20x8, 16x8 with two lanes per face, 16x8); in 3D the
+                               direction kernels' pencils, FP64:
                                1 = 16 nodes x 16 lines, 2 = 16 x 8, 3 = 16 x 4, 4 = 32 x 4; mixed:
-                               1 = 16 x 16, 2 = 32 x 8, 3 = 16 x 8, 4 = 32 x 4 */
+                               1 = 16 x 16, 2 = 32 x 8, 3 = 16 x 8, 4 = 32 x 4, and 5 .. 8 the same
+                               shapes with node-by-node loads instead of the TMA staging of the xi_2 and
+                               xi_3 pencils (which needs n1 a multiple of 4) */
 } es_params;
 
 #define ES_NTILES 5
@@ -221,6 +226,14 @@ int es_last_error(es_ctx* ctx, char* buf, int len);
  * (ES_NTILES of them in 2D; 4 in 3D, the pencil shapes of its direction kernels).  1D contexts have one shape (returns 1).
  * Synchronises. */
 int es_autotune(es_ctx* ctx, const void* JU, const void* J, const double* x, int* tile_host, double* ms_host);
+
+/* Device time of the fused stage kernel (Sec. 3 operator + one SSP-RK3 stage, the kernel es_rk_stage runs):
+ * `reps` launches of stage `stage` (1..3) with step dt on (JU, J) and the mesh x at rest, back to back on the
+ * context's stream between two CUDA events, written to the context's stage buffer; *ms_host = the mean time
+ * per launch.  The mixed form's displacement is formed once before the first event.  1D/2D contexts only
+ * (ES_ERR_ARG for 3D or reps < 1).  Synchronises the stream. */
+int es_time_stage(es_ctx* ctx, const void* JU, const void* J, const double* x, int stage, double dt, int reps,
+                  double* ms_host);
 
 /* Self-test of the library's FP64 quotient and reciprocal (the stage kernel divides with
  * them: a Newton-Raphson-refined hardware reciprocal and a Markstein quotient correction):

@@ -1177,6 +1177,41 @@ int es_autotune(es_ctx* c, const void* JU, const void* J, const double* x, int* 
     return ES_OK;
 }
 
+int es_time_stage(es_ctx* c, const void* JU, const void* J, const double* x, int stage, double dt, int reps,
+                  double* ms_host) {
+    if (!c || !JU || !J || !x || !ms_host || stage < 1 || stage > 3 || reps < 1 || !(dt > 0.0))
+        return fail(c, ES_ERR_ARG, "bad argument");
+    if (c->d3) return fail(c, ES_ERR_ARG, "es_time_stage: 1D/2D contexts only");
+    StageParams P = stage_params(c);
+    P.ca = RK_A[stage - 1];
+    P.cb = RK_B[stage - 1];
+    P.cst = RK_C[stage - 1];
+    P.dt_host = dt;
+    P.xn = x;
+    P.xdot = nullptr;
+    enqueue_mesh_f32(c, P, x, nullptr);
+    set_state(c, P, JU, J, JU, J, c->S1, c->S1J);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, e, "event");
+    }
+    e = launch_stage(c, P);                                  // loads the kernel before the timed launches
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->s_enq);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_stage(c, P);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->s_enq);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "es_time_stage");
+    *ms_host = double(ms) / reps;
+    return ES_OK;
+}
+
 int es_check(es_ctx* c) {
     if (!c) return ES_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream), "sync");

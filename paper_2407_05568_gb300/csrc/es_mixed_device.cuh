@@ -173,10 +173,16 @@ __device__ __forceinline__ void entropy_jump(const float* S, int NB, int i, int 
     dV[DIM + 1] = dT * S[G_IT * NB + i] * S[G_IT * NB + j];
 }
 
+// the face state of eq. HOstable's dissipation: log-mean density and pressure ratio, T, c, the rotation
+// (cos, sin) of the face normal of length L, normal / tangential velocity, and the scalings of R^T T
+struct FaceF {
+    float rho, c, cs, sn, L, vn, vt, H, mid, sA, sE, sT, Lam, Hm, Hp;
+};
+
 template <int DIM>
-__device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l, int step, float nx, float ny,
-                                                   float xtf, const GasF& G, const WenoF& Wc, float* out,
-                                                   DevStatus* st, const float* JB, int NJ, int jq) {
+__device__ __forceinline__ FaceF face_state_f(const float* S, int NB, int l, int step, float nx, float ny, float xtf,
+                                              const GasF& G, DevStatus* st) {
+    FaceF f;
     const int r = l + step;
     const float ilr = inv_log_mean_f(S[G_RHO * NB + l], S[G_RHO * NB + r]);
     const float rho = 1.0f / ilr;
@@ -206,13 +212,32 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
     }
     const float E = rho * (G.cv * T - G.a * rho) + 0.5f * rho * (vn * vn + vt * vt);
     const float H = (E + p) * ilr;
-    const float mid = H - c2 * om * G.idelta;
+    f.rho = rho;
+    f.c = c;
+    f.cs = cs;
+    f.sn = sn;
+    f.L = L;
+    f.vn = vn;
+    f.vt = vt;
+    f.H = H;
+    f.mid = H - c2 * om * G.idelta;
     const float ic2 = 1.0f / c2;
-    const float sA = sqrtf(0.5f * rho * T * ic2);
-    const float sE = sqrtf(G.R * G.delta * rho * T * T * ic2 / dcrit);
-    const float sT = sqrtf(rho * T);
-    const float Lam = fabsf(xtf + L * vn) + L * c;
-    const float Hm = H - vn * c, Hp = H + vn * c;
+    f.sA = sqrtf(0.5f * rho * T * ic2);
+    f.sE = sqrtf(G.R * G.delta * rho * T * T * ic2 / dcrit);
+    f.sT = sqrtf(rho * T);
+    f.Lam = fabsf(xtf + L * vn) + L * c;
+    f.Hm = H - vn * c;
+    f.Hp = H + vn * c;
+    return f;
+}
+
+template <int DIM>
+__device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l, int step, float nx, float ny,
+                                                   float xtf, const GasF& G, const WenoF& Wc, float* out,
+                                                   DevStatus* st, const float* JB, int NJ, int jq) {
+    const FaceF fs = face_state_f<DIM>(S, NB, l, step, nx, ny, xtf, G, st);
+    const float c = fs.c, cs = fs.cs, sn = fs.sn, vn = fs.vn, vt = fs.vt, mid = fs.mid;
+    const float sA = fs.sA, sE = fs.sE, sT = fs.sT, Lam = fs.Lam, Hm = fs.Hm, Hp = fs.Hp;
 
     // W_j - W_l = R^T T (V_j - V_l) at nodes l-2 .. l+3 (zero at l itself); V_j - V_l is the sum
     // of the neighbour jumps between them (JB[c][jq + q] = V_{q+1} - V_q along the line, the
@@ -315,6 +340,97 @@ __device__ __forceinline__ void face_dissipation_f(const float* S, int NB, int l
     }
 }
 
+// face_dissipation_f in 2D shared by the two lanes (2 p, 2 p + 1) of a warp: both form the face state, lane
+// half = 0 the characteristic components 0 and 1 (the acoustic wave u - c and the entropy wave), half = 1
+// components 2 and 3 (the shear wave and u + c), each its own reconstructions and sign switch, and the two
+// exchange their y values; every lane of the warp must call it (a lane without a face passes a valid one and
+// drops the result).  The same arithmetic per component as face_dissipation_f; twice the lanes per face.
+__device__ __forceinline__ void face_dissipation_split_f(const float* S, int NB, int l, int step, float nx, float ny,
+                                                         float xtf, const GasF& G, const WenoF& Wc, float* out,
+                                                         DevStatus* st, const float* JB, int NJ, int jq, int half) {
+    const FaceF fs = face_state_f<2>(S, NB, l, step, nx, ny, xtf, G, st);
+    const float c = fs.c, cs = fs.cs, sn = fs.sn, vn = fs.vn, vt = fs.vt, mid = fs.mid;
+    const float sA = fs.sA, sE = fs.sE, sT = fs.sT, Lam = fs.Lam, Hm = fs.Hm, Hp = fs.Hp;
+    const bool h0 = half == 0;
+    // rows of R^T T for this lane's components: a = 0 or 2, b = 1 or 3; component 2 is sT (V2 + vt V3), the
+    // others s (base + B V1 + D V3)
+    const float s_a = h0 ? sA : sT, B_a = h0 ? vn - c : 0.0f, D_a = h0 ? Hm : vt;
+    const float s_b = h0 ? sE : sA, B_b = h0 ? vn : vn + c, D_b = h0 ? mid : Hp;
+    float Wa[6], Wb[6];
+    float aTV[4];
+    Wa[2] = 0.0f;
+    Wb[2] = 0.0f;
+    float cum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float Vn[6][4];
+#pragma unroll
+    for (int o = 3; o < 6; ++o)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            cum[m] += JB[m * NJ + jq + (o - 3)];
+            Vn[o][m] = cum[m];
+        }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cum[m] = 0.0f;
+#pragma unroll
+    for (int o = 1; o >= 0; --o)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            cum[m] -= JB[m * NJ + jq + (o - 2)];
+            Vn[o][m] = cum[m];
+        }
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        if (o == 2) continue;
+        const float V0 = Vn[o][0];
+        const float V1 = cs * Vn[o][1] + sn * Vn[o][2], V2 = -sn * Vn[o][1] + cs * Vn[o][2], V3 = Vn[o][3];
+        const float base = V0 + vt * V2;
+        Wa[o] = s_a * ((h0 ? base : V2) + B_a * V1 + D_a * V3);
+        Wb[o] = s_b * (base + B_b * V1 + D_b * V3);
+        if (o == 3) {
+            aTV[0] = fabsf(V0);
+            aTV[1] = fabsf(V1);
+            aTV[2] = fabsf(V2);
+            aTV[3] = fabsf(V3);
+        }
+    }
+    const float avt = fabsf(vt);
+    const float scl_a = h0 ? sA * (aTV[0] + fabsf(vn - c) * aTV[1] + avt * aTV[2] + fabsf(Hm) * aTV[3])
+                           : sT * (aTV[2] + (avt + c) * aTV[3]);
+    const float scl_b = s_b * (aTV[0] + fabsf(B_b) * aTV[1] + avt * aTV[2] + fabsf(D_b) * aTV[3]);
+    float ya, yb;
+    {
+        const float wmin = mr_weno5_f(Wa[0], Wa[1], Wa[2], Wa[3], Wa[4], Wc);
+        const float wplu = mr_weno5_f(Wa[5], Wa[4], Wa[3], Wa[2], Wa[1], Wc);
+        const float jw = wplu - wmin;
+        float j = Wa[3];
+        if (fabsf(j) <= Wc.sign_tol * scl_a) j = 0.0f;
+        const bool keep = (jw > 0.0f && j > 0.0f) || (jw < 0.0f && j < 0.0f);
+        ya = keep ? jw : 0.0f;
+    }
+    {
+        const float wmin = mr_weno5_f(Wb[0], Wb[1], Wb[2], Wb[3], Wb[4], Wc);
+        const float wplu = mr_weno5_f(Wb[5], Wb[4], Wb[3], Wb[2], Wb[1], Wc);
+        const float jw = wplu - wmin;
+        float j = Wb[3];
+        if (fabsf(j) <= Wc.sign_tol * scl_b) j = 0.0f;
+        const bool keep = (jw > 0.0f && j > 0.0f) || (jw < 0.0f && j < 0.0f);
+        yb = keep ? jw : 0.0f;
+    }
+    const float oa = __shfl_xor_sync(0xffffffffu, ya, 1);
+    const float ob = __shfl_xor_sync(0xffffffffu, yb, 1);
+    const float y[4] = {h0 ? ya : oa, h0 ? yb : ob, h0 ? oa : ya, h0 ? ob : yb};
+    const float h = -0.5f * Lam;
+    const float y0 = sA * y[0], y1 = sE * y[1], y2 = sT * y[2], y3 = sA * y[3];
+    const float i0 = y0 + y1 + y3;
+    const float i1 = (vn - c) * y0 + vn * y1 + (vn + c) * y3;
+    const float i2 = vt * i0 + y2;
+    const float i3 = Hm * y0 + mid * y1 + vt * y2 + Hp * y3;
+    out[0] = h * i0;
+    out[1] = h * (cs * i1 - sn * i2);
+    out[2] = h * (sn * i1 + cs * i2);
+    out[3] = h * i3;
+}
+
 template <int DIM>
 __device__ __forceinline__ void load_node_f(float* S, int NB, int b, const StageParams& P, const GasF& G, int gi,
                                             int gj) {
@@ -408,9 +524,11 @@ __device__ __forceinline__ void stage_disp(const StageParams& P, int gi, int gj,
 // fluxes, face fluxes, divergence and the RK combination follow.  Called by the
 // tiled kernel (one tile per CTA) and by the batched kernel (a loop over the
 // chunks of one problem per CTA).
-template <int DIM, int BX, int BY, int NT>
+// SPLIT (2D): two lanes per face in the face phase (face_dissipation_split_f), for tiles with twice the threads
+template <int DIM, int BX, int BY, int NT, bool SPLIT = false>
 __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams& P, int i0, int j0, float dt,
                                                  const GasF& G, const WenoF& Wc) {
+    static_assert(!SPLIT || DIM == 2, "the split face phase is written for 2D");
     using TL = TileF<DIM, BX, BY, NT>;
     constexpr int GX = TL::GX, NB = TL::NB, NC = TL::NC;
     float* S = smemf;
@@ -480,9 +598,9 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
     for (int c = 0; c <= NC; ++c) acc[c] = 0.0f;
     const int tx = tid % BX, ty = tid / BX;
 
-    // both directions unrolled: line lengths and strides are constants, so the index
-    // divisions below compile to multiplications
-#pragma unroll
+    // one copy of the direction pipeline for both directions (unrolled, the kernel's code was twice the size
+    // and its warps stalled on instruction fetch); the line lengths and strides are then run-time values
+#pragma unroll 1
     for (int k = 0; k < DIM; ++k) {
         const int nlines = k == 0 ? (DIM == 2 ? BY : 1) : BX;
         const int LB = k == 0 ? BX : BY;
@@ -520,7 +638,15 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
             }
         }
         __syncthreads();
-        for (int t = tid; t < nlines * (LB + 1); t += NT) {
+        const int nfaces = nlines * (LB + 1);
+        const int lane = tid & 31;
+        // SPLIT: lanes (2 p, 2 p + 1) share face p; the trip count is uniform per warp (the halves exchange
+        // values), and a lane past the last face works on the last face and stores nothing
+        for (int ub = SPLIT ? tid - lane : tid; ub < (SPLIT ? 2 * nfaces : nfaces); ub += NT) {
+            const int u = SPLIT ? ub + lane : ub;
+            const bool active = !SPLIT || u < 2 * nfaces;
+            const int t = SPLIT ? (active ? (u >> 1) : nfaces - 1) : u;
+            const int half = SPLIT ? (u & 1) : 0;
             const int line = t / (LB + 1), f = t % (LB + 1);
             const int q = 2 + f;
             const int pbase = line * per_line;
@@ -547,14 +673,20 @@ __device__ __forceinline__ void stage_tile_mixed(float* smemf, const StageParams
                 const float ny = 0.5f * (S[fNy * NB + l] + S[fNy * NB + l + step]);
                 const float xtf = 0.5f * (S[fXT * NB + l] + S[fXT * NB + l + step]);
                 float d[NC];
-                face_dissipation_f<DIM>(S, NB, l, step, nx, ny, xtf, G, Wc, d, P.status, JB, TL::NJ,
-                                        line * (LB + 5) + q);
+                if constexpr (SPLIT)
+                    face_dissipation_split_f(S, NB, l, step, nx, ny, xtf, G, Wc, d, P.status, JB, TL::NJ,
+                                             line * (LB + 5) + q, half);
+                else
+                    face_dissipation_f<DIM>(S, NB, l, step, nx, ny, xtf, G, Wc, d, P.status, JB, TL::NJ,
+                                            line * (LB + 5) + q);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) F[c] += d[c];
             }
+            if (active && half == 0) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) FB[c * TL::NF + t] = F[c];
-            FB[NC * TL::NF + t] = FJ;
+                for (int c = 0; c < NC; ++c) FB[c * TL::NF + t] = F[c];
+                FB[NC * TL::NF + t] = FJ;
+            }
         }
         __syncthreads();
         if (tid < BX * (DIM == 2 ? BY : 1)) {

@@ -35,44 +35,45 @@ namespace {
 using namespace mixed;
 
 // resident CTAs per SM the register allocation must allow: 5 x 160 or 4 x 192 threads (24 warps; 72 and 80
-// registers, no spills), 2 x 288, 1 x 544
-template <int DIM, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT, NT <= 160 ? 5 : (NT <= 192 ? 4 : (NT <= 320 ? 2 : 1))) stage_kernel_mixed(StageParams P) {
+// registers, no spills), 2 x 320 or 384 (the two-lanes-per-face shapes), 1 x 544
+template <int DIM, int BX, int BY, int NT, bool SPLIT>
+__global__ void __launch_bounds__(NT, NT <= 160 ? 5 : (NT <= 192 ? 4 : (NT <= 384 ? 2 : 1)))
+    stage_kernel_mixed(StageParams P) {
     extern __shared__ float smemf[];
     const int ntx = (P.n1 + BX - 1) / BX;
     const int i0 = (blockIdx.x % ntx) * BX;
     const int j0 = DIM == 2 ? (blockIdx.x / ntx) * BY : 0;
     const double dtd = P.dt_dev ? *P.dt_dev : P.dt_host;
     if (P.mode == 0 && dtd == 0.0) return;               // finished run: leave the state untouched
-    stage_tile_mixed<DIM, BX, BY, NT>(smemf, P, i0, j0, float(dtd), gas_f(P), weno_f(P));
+    stage_tile_mixed<DIM, BX, BY, NT, SPLIT>(smemf, P, i0, j0, float(dtd), gas_f(P), weno_f(P));
 }
 
-template <int DIM, int BX, int BY, int NT>
+template <int DIM, int BX, int BY, int NT, bool SPLIT = false>
 cudaError_t prepare_tile_f() {
-    return cudaFuncSetAttribute(stage_kernel_mixed<DIM, BX, BY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(TileF<DIM, BX, BY, NT>::SMEM));
+    return cudaFuncSetAttribute(stage_kernel_mixed<DIM, BX, BY, NT, SPLIT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(TileF<DIM, BX, BY, NT>::SMEM));
 }
 
-template <int DIM, int BX, int BY, int NT>
+template <int DIM, int BX, int BY, int NT, bool SPLIT = false>
 cudaError_t launch_tile_f(const StageParams& P, cudaStream_t s) {
     const int ntx = (P.n1 + BX - 1) / BX;
     const int nty = DIM == 2 ? (P.n2 + BY - 1) / BY : 1;
-    stage_kernel_mixed<DIM, BX, BY, NT><<<ntx * nty, NT, TileF<DIM, BX, BY, NT>::SMEM, s>>>(P);
+    stage_kernel_mixed<DIM, BX, BY, NT, SPLIT><<<ntx * nty, NT, TileF<DIM, BX, BY, NT>::SMEM, s>>>(P);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// 2D shapes: 32 x 8 nodes with 288 threads, 25 x 6 with 192 (175 faces; 8 x 34 = 272 tiles fill
-// 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces), 32 x 16 with 544
-// (544 faces; less halo per node for large meshes, one CTA per SM), 16 x 8 with 160 (more CTAs
-// for small meshes)
+// 2D shapes: 20 x 8 nodes with 384 threads, two lanes per face (twice the warps of the 192-thread
+// shape: small meshes are latency bound), 25 x 6 with 192 (175 faces; 8 x 34 = 272 tiles fill
+// 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces), 16 x 8 with 320, two lanes
+// per face, and 16 x 8 with 160 (more CTAs for small meshes)
 cudaError_t stage_prepare_mixed(int dim) {
     if (dim == 1) return prepare_tile_f<1, 254, 1, 256>();
-    cudaError_t e = prepare_tile_f<2, 32, 8, 288>();
+    cudaError_t e = prepare_tile_f<2, 20, 8, 384, true>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 25, 6, 192>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 20, 8, 192>();
-    if (e == cudaSuccess) e = prepare_tile_f<2, 32, 16, 544>();
+    if (e == cudaSuccess) e = prepare_tile_f<2, 16, 8, 320, true>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 16, 8, 160>();
     return e;
 }
@@ -82,9 +83,9 @@ cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s) {
     switch (P.tile) {
         case 1: return launch_tile_f<2, 25, 6, 192>(P, s);
         case 2: return launch_tile_f<2, 20, 8, 192>(P, s);
-        case 3: return launch_tile_f<2, 32, 16, 544>(P, s);
+        case 3: return launch_tile_f<2, 16, 8, 320, true>(P, s);
         case 4: return launch_tile_f<2, 16, 8, 160>(P, s);
-        default: return launch_tile_f<2, 32, 8, 288>(P, s);
+        default: return launch_tile_f<2, 20, 8, 384, true>(P, s);
     }
 }
 

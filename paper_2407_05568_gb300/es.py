@@ -70,6 +70,7 @@ def lib():
         L.es_check.argtypes = [vp]
         L.es_last_error.argtypes = [vp, ctypes.c_char_p, i]
         L.es_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i), ctypes.POINTER(d)]
+        L.es_time_stage.argtypes = [vp, vp, vp, vp, i, d, i, ctypes.POINTER(d)]
         L.es_selftest_division.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
         L.es_selftest_division.restype = ctypes.c_int
         L.es_selftest_peaks.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), vp]
@@ -401,6 +402,15 @@ def es_autotune(ctx, JU, J, x):
     ms = (ctypes.c_double * 5)()
     ctx._call(lib().es_autotune(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), ctypes.byref(k), ms))
     return k.value, list(ms)
+
+
+def es_time_stage(ctx, JU, J, x, stage=2, dt=1e-4, reps=20):
+    """Mean device time (ms) of `reps` back-to-back launches of the fused stage kernel (1D/2D)."""
+    S = ctx.state_dtype
+    ms = ctypes.c_double()
+    ctx._call(lib().es_time_stage(ctx._h, _ptr(JU, S), _ptr(J, S), _ptr(x, F64), int(stage), float(dt), int(reps),
+                                  ctypes.byref(ms)))
+    return ms.value
 
 
 def es_selftest_division(a, b, q, r, stream=None):

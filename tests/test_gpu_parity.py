@@ -426,3 +426,21 @@ def test_measured_alu_peaks():
     assert 40.0 < f32 < 100.0, f32
     assert 0.4 < f64 < 2.5, f64
     assert f32 > 30.0 * f64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_time_stage(precision):
+    """es_time_stage times back-to-back launches of the stage kernel es_rk_stage runs: a positive time per
+    launch, no device error, and ES_ERR_ARG for bad arguments."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = wl.riemann_2d(64, seed=5)
+    ctx, JU, J, xt = gpu_setup(w, precision=precision)
+    ms = es.es_time_stage(ctx, JU, J, xt, stage=2, dt=1e-4, reps=5)
+    assert 0.0 < ms < 50.0, ms
+    assert es.es_check(ctx) == 0
+    with pytest.raises(es.EsError):
+        es.es_time_stage(ctx, JU, J, xt, stage=4)
+    with pytest.raises(es.EsError):
+        es.es_time_stage(ctx, JU, J, xt, reps=0)
