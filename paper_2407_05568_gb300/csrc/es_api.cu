@@ -296,10 +296,11 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
 bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
 
 // Sec. 4 on the FP32 pipe; c->fdisp must hold the displacement of x^n.  Writes c->fxd and xdot.
-// with_dt: the monitor kernel also sets the step's dt from the CFL maximum (k_dt's work).
+// with_dt: 1, the monitor kernel also sets the step's dt from the CFL maximum (k_dt's work); 2, it also takes
+// eq. cfl with the mesh at rest itself (k_cfl_f's work) and stores the moving pass's terms in c->S1.
 // cfl_moving > 0: the velocity kernel also takes eq. cfl with the new mesh velocity (from the terms the step's
-// first CFL pass left in c->S1) and shrinks dt.
-int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool with_dt, double cfl_moving = 0.0) {
+// first CFL pass left in c->S1) and shrinks dt.  In 2D the sweeps' tile kernel also forms Delta_gamma.
+int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int with_dt, double cfl_moving = 0.0) {
     const int B = 256, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const GasF32 gf = gas_f32(c->gas);
@@ -311,8 +312,8 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
     float* da = (float*)c->xa;
     float* db = (float*)c->xb;
     k_mon_f<<<mon_f_blocks(c->g), MON_TX * MON_TY, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0,
-                                                           t1, t2, c->dev, with_dt ? 1 : 0, c->p.cfl,
-                                                           c->p.dt_fixed);
+                                                           t1, t2, c->dev, with_dt, c->p.cfl, c->p.dt_fixed,
+                                                           c->fdisp, cfl_moving > 0.0 ? (float*)c->S1 : nullptr);
     count(c);
     // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
     const bool fuse = c->p.dim == 2;
@@ -331,18 +332,19 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, bool 
     }
     const int check = c->p.jacobi_eps > 0.0;
     const int mu = c->p.jacobi_sweeps;
-    if (fuse && !check && mu >= 1 && mu <= 8) {
-        k_jacobi_multi_f<<<tiles, 256, 0, s>>>(c->g, om, c->fdisp, ((mu - 1) & 1) ? db : da, mu, c->dev);
+    if (fuse && !check && mu >= 1 && mu <= 8) {              // the tile kernel also forms Delta_gamma
+        k_jacobi_multi_f<<<tiles, 256, 0, s>>>(c->g, om, c->fdisp, ((mu - 1) & 1) ? db : da, mu, c->dev, 1);
         count(c);
     } else {
         for (int k = 0; k < mu; ++k) {
             k_jacobi_f<<<G, B, 0, s>>>(c->g, om, c->fdisp, da, db, k, c->dev, check, c->p.jacobi_eps);
             count(c);
         }
+        k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
+        count(c);
     }
-    k_limiter_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev);
     k_velocity_f<<<G, B, 0, s>>>(c->g, c->fdisp, da, db, c->dev, c->fxd, xdot, (const float*)c->S1, cfl_moving);
-    count(c, 2);
+    count(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels (FP32)");
     return ES_OK;
@@ -424,15 +426,18 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     const double cfl_moving = c->p.moving && !(c->p.dt_fixed > 0.0) ? c->p.cfl : 0.0;
     if (f32) {      // the displacement kernel also resets the step's reductions (k_reset's work)
         k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
-        k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, nullptr, RED_CFL,
-                                c->dev, cfl_moving > 0.0 ? (float*)c->S1 : nullptr);
-        count(c, 2);
+        count(c);
+        if (!c->p.moving) {         // on a moving mesh the monitor kernel takes eq. cfl (with_dt = 2 below)
+            k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, nullptr,
+                                    RED_CFL, c->dev);
+            count(c);
+        }
     } else {
         k_reset<<<1, 32, 0, s>>>(c->dev);
         count(c);
         enqueue_cfl(c, JU, J, x, nullptr, RED_CFL, cfl_moving > 0.0 ? (double*)c->S1 : nullptr, (double*)c->S2);
     }
-    const bool dt_in_mesh = f32 && c->p.moving;       // the FP32 monitor kernel sets dt
+    const bool dt_in_mesh = f32 && c->p.moving;       // the FP32 monitor kernel takes eq. cfl and sets dt
     if (!dt_in_mesh) {
         k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
         count(c);
@@ -441,7 +446,7 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     if (e != cudaSuccess) return cuda_fail(c, e, "time-step kernels");
     const double* xdot = nullptr;
     if (c->p.moving) {
-        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, true, cfl_moving)
+        int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, 2, cfl_moving)
                      : enqueue_mesh(c, JU, J, x, c->xdot, cfl_moving);
         if (rc) return rc;
         xdot = c->xdot;
@@ -839,7 +844,7 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
     } else if (mesh_on_fp32(c)) {
         k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
         count(c);
-        rc = enqueue_mesh32(c, JU, J, xdot, false);
+        rc = enqueue_mesh32(c, JU, J, xdot, 0);
     } else {
         rc = enqueue_mesh(c, JU, J, xn, xdot);
     }

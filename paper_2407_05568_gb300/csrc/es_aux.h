@@ -47,13 +47,15 @@ __device__ __forceinline__ void reset_scalars(DevScalars* d) {
     d->done = 0u;
 }
 
-__device__ __forceinline__ void set_dt_from_cfl(DevScalars* d, double cfl, double dt_fixed) {
-    const double mx = __longlong_as_double((long long)d->red[RED_CFL]);
+__device__ __forceinline__ void set_dt_from_max(DevScalars* d, double mx, double cfl, double dt_fixed) {
     double dt = dt_fixed > 0.0 ? dt_fixed : cfl / mx;
     const double left = d->t_end - d->t;
     if (left <= 1e-14 * fmax(1.0, fabs(d->t_end))) dt = 0.0;
     else if (dt > left) dt = left;
     d->dt = dt;
+}
+__device__ __forceinline__ void set_dt_from_cfl(DevScalars* d, double cfl, double dt_fixed) {
+    set_dt_from_max(d, __longlong_as_double((long long)d->red[RED_CFL]), cfl, dt_fixed);
 }
 
 // eq. cfl with the step's mesh velocity (maximum mx): Delta t_n = min(Delta t^(0), CFL / mx).

@@ -259,10 +259,11 @@ __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const fl
 // dt from the CFL maximum (k_dt's work: the CFL kernel has finished when this one starts).
 __global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
                                                            MonitorParams mp, float* t0, float* t1, float* t2,
-                                                           DevScalars* d, int do_dt, double cfl, double dt_fixed) {
+                                                           DevScalars* d, int do_dt, double cfl, double dt_fixed,
+                                                           const float* disp, float* cfl_terms) {
     constexpr int CAP = (MON_TX + 2) * (MON_TY + 2);      // >= MON_TX * MON_TY + 2, the 1D tile with its halo
     __shared__ float srh[CAP], srl[CAP], sgh[CAP], sgl[CAP];
-    if (do_dt && blockIdx.x == 0 && threadIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
+    if (do_dt == 1 && blockIdx.x == 0 && threadIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
     const int TW = g.dim == 2 ? MON_TX : MON_TX * MON_TY;  // tile width; 1D tiles are one row of all threads
@@ -283,11 +284,15 @@ __global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 
         sgl[t] = Gv.lo;
     }
     __syncthreads();
-    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f;
+    float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, mc = 0.0f;
     const int tx = threadIdx.x % TW, ty = threadIdx.x / TW;
     const int i = i0 + tx, j = j0 + ty;
     if (i < g.n1 && (g.dim == 1 || j < g.n2)) {
         const int id = j * g.n1 + i;
+        // do_dt == 2: eq. cfl with the mesh at rest at this node (k_cfl_f's work), and its terms for the moving pass
+        if (do_dt == 2)
+            mc = cfl_node_f(g, G, JU, J, disp, id, 0.0f, 0.0f, cfl_terms,
+                            cfl_terms ? cfl_terms + 4 * size_t(N) : nullptr);
         const int c = (g.dim == 2 ? ty + 1 : 0) * HW + tx + 1;
         const mixed::df r0 = {srh[c], srl[c]}, G0 = {sgh[c], sgl[c]};
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
@@ -329,6 +334,18 @@ __global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 
         atomic_max_pos(&d->red[RED_MON0], double(m0));
         atomic_max_pos(&d->red[RED_MON1], double(m1));
         atomic_max_pos(&d->red[RED_MON2], double(m2));
+    }
+    if (do_dt == 2) {                                        // uniform: the step's dt once every node is in
+        mc = block_max_f32(mc);
+        if (threadIdx.x == 0) {
+            atomic_max_pos(&d->red[RED_CFL], double(mc));
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {
+                set_dt_from_max(d, __longlong_as_double((long long)atomicAdd(&d->red[RED_CFL], 0ULL)), cfl, dt_fixed);
+                d->done = 0u;
+            }
+        }
     }
 }
 
@@ -597,7 +614,7 @@ void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const flo
 }
 
 __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const float* omega, const float* d0,
-                                                        float* dout, int sweeps, DevScalars* dv) {
+                                                        float* dout, int sweeps, DevScalars* dv, int limit) {
     __shared__ float Wm[FT_W * FT_H];
     __shared__ float X[2][2][FT_W * FT_H];          // [buffer][component]
     const int h = sweeps, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
@@ -654,14 +671,31 @@ __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const floa
         b ^= 1;
     }
     const size_t N = size_t(g.n1) * g.n2;
+    float lim = 1.0f;                                        // limit: k_limiter_f's min over this tile's nodes
     for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
         const int ix = idx % FT_X, iy = idx / FT_X;
         const int gi = x0 + h + ix, gj = y0 + h + iy;
         if (gi < g.n1 && gj < g.n2) {
             const int s = (h + iy) * TW + h + ix;
-            dout[size_t(gj) * g.n1 + gi] = X[b][0][s];
-            dout[N + size_t(gj) * g.n1 + gi] = X[b][1][s];
+            const size_t id = size_t(gj) * g.n1 + gi;
+            dout[id] = X[b][0][s];
+            dout[N + id] = X[b][1][s];
+            if (limit) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float d0k = d0[k * N + id];
+                    const float dx = X[b][k][s] - d0k;
+                    const int di = k == 0, dj = k == 1;
+                    const float hk = k == 0 ? dxx : dxy;
+                    if (dx < 0.0f) lim = fminf(lim, -(hk + d0k - disp_at(g, d0, gi - di, gj - dj, k)) / (2.0f * dx));
+                    else if (dx > 0.0f) lim = fminf(lim, (hk + disp_at(g, d0, gi + di, gj + dj, k) - d0k) / (2.0f * dx));
+                }
+            }
         }
+    }
+    if (limit) {
+        lim = block_min_f32(lim);
+        if (threadIdx.x == 0) atomic_min_pos(&dv->red[RED_GAMMA], double(lim));
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&dv->sweeps, sweeps);
 }

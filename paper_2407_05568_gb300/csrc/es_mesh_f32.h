@@ -35,8 +35,12 @@ __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const fl
 // monitor terms over MON_TX x MON_TY tiles (one row of MON_TX * MON_TY nodes in 1D); launch with
 // mon_f_blocks(g) blocks of MON_TX * MON_TY threads
 constexpr int MON_TX = 32, MON_TY = 8;
+// do_dt: 0 no time step; 1 the step's dt from the CFL maximum an earlier kernel left (k_dt's work); 2 also eq. cfl
+// with the mesh at rest at every node (k_cfl_f's work on disp, its moving-pass terms to cfl_terms when non-null)
+// and dt set by the last block to finish
 __global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
-                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed);
+                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed,
+                        const float* disp = nullptr, float* cfl_terms = nullptr);
 int mon_f_blocks(const GridParams& g);
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega);
@@ -48,8 +52,9 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
 // omega and its low-pass filter passes fused per 32 x 16 tile (2D, 1 <= passes <= FT_HMAX = 8)
 void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const float* t0, const float* t1,
                          const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s);
+// limit: also Delta_gamma of the result over the tile's nodes into RED_GAMMA (k_limiter_f's work)
 __global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
-                                 DevScalars* dv);
+                                 DevScalars* dv, int limit);
 // cfl > 0: also eq. cfl with the new velocity from k_cfl_f's stored terms into RED_CFL2, and
 // dt = min(dt, cfl / that maximum)
 __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const float* __restrict__ da,
