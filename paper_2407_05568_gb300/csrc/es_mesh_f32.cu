@@ -210,14 +210,13 @@ __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G
 // eq. cfl on the FP32 pipe: the maximum over the nodes of cfl_node_f goes to d->red[slot]; vel = nullptr
 // is a mesh at rest.
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
-                        int slot, DevScalars* d, float* terms) {
+                        int slot, DevScalars* d) {
     const int N = g.n1 * g.n2;
-    float* t1 = terms ? terms + 4 * size_t(N) : nullptr;
     float m = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const float xd1 = vel != nullptr ? vel[id] : 0.0f;
         const float xd2 = vel != nullptr && g.dim == 2 ? vel[N + id] : 0.0f;
-        m = fmaxf(m, cfl_node_f(g, G, JU, J, disp, id, xd1, xd2, terms, t1));
+        m = fmaxf(m, cfl_node_f(g, G, JU, J, disp, id, xd1, xd2));
     }
     m = block_max_f32(m);
     if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], double(m));

@@ -26,10 +26,9 @@ inline GasF32 gas_f32(const Gas& g) {
 }
 
 // JU, J: the mixed form's (hi, lo) float planes; disp: the FP32 displacement [dim][N]
-// vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity);
-// terms (nullable, 8 N floats): also store the node terms of cfl_moving_term (fields 0..3, then 4..7 at 4 N)
+// vel (nullable): the float mesh velocity; slot: RED_CFL (mesh at rest) or RED_CFL2 (with the step's velocity)
 __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J, const float* disp, const float* vel,
-                        int slot, DevScalars* d, float* terms = nullptr);
+                        int slot, DevScalars* d);
 // rhoF, GF: 2 N floats each, (hi, lo) planes of the density and the fundamental derivative
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
 // monitor terms over MON_TX x MON_TY tiles (one row of MON_TX * MON_TY nodes in 1D); launch with
