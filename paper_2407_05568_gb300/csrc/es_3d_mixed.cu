@@ -986,42 +986,33 @@ __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, cons
     }
 }
 
-// omega_i <- sum_{j in {0,+-1}^3} (1/2)^(|j|_1 + 3) omega_{i+j} (Sec. 4's low-pass filter), one pass on 32 x 8 x 4
-// tiles: the tile and its one-node halo (ghosts by copy or wrap, per direction) are staged in shared memory once,
-// and every node sums its 27 neighbours there, rows along xi_1 first, then along xi_2, then xi_3
-constexpr int FT3X = 32, FT3Y = 8, FT3Z = 4;
-__global__ void __launch_bounds__(256) k3f_filter_tiled(Grid3 g, const float* in, float* out) {
-    constexpr int HX = FT3X + 2, HY = FT3Y + 2, HZ = FT3Z + 2;
-    __shared__ float T[HX * HY * HZ];
-    const int ntx = (g.n[0] + FT3X - 1) / FT3X, nty = (g.n[1] + FT3Y - 1) / FT3Y;
-    const int bx = blockIdx.x % ntx, by = (blockIdx.x / ntx) % nty, bz = blockIdx.x / (ntx * nty);
-    const int i0 = bx * FT3X - 1, j0 = by * FT3Y - 1, k0 = bz * FT3Z - 1;
-    for (int t = threadIdx.x; t < HX * HY * HZ; t += blockDim.x) {
-        const int lx = t % HX, ly = (t / HX) % HY, lz = t / (HX * HY);
-        const int si = state_index(i0 + lx, g.n[0], g.bc[0]);
-        const int sj = state_index(j0 + ly, g.n[1], g.bc[1]);
-        const int sk = state_index(k0 + lz, g.n[2], g.bc[2]);
-        T[t] = in[(size_t(sk) * g.n[1] + sj) * g.n[0] + si];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < FT3X * FT3Y * FT3Z; t += blockDim.x) {
-        const int lx = t % FT3X, ly = (t / FT3X) % FT3Y, lz = t / (FT3X * FT3Y);
-        const int i = i0 + 1 + lx, j = j0 + 1 + ly, k = k0 + 1 + lz;
-        if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
-        const int c = ((lz + 1) * HY + ly + 1) * HX + lx + 1;
+// omega_i <- sum_{j in {0,+-1}^3} (1/2)^(|j|_1 + 3) omega_{i+j} (Sec. 4's low-pass filter)
+__global__ void k3f_filter(Grid3 g, const float* in, float* out) {
+    const int N = g.n[0] * g.n[1] * g.n[2];
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
+        int ii[3];
+        split3(g, id, ii);
+        int o1[3], o2[3], o3[3];
+        o1[1] = o2[1] = o3[1] = 0;
+        o1[0] = nb3(g, id, ii[0], 0, -1) - id;
+        o1[2] = nb3(g, id, ii[0], 0, 1) - id;
+        o2[0] = nb3(g, id, ii[1], 1, -1) - id;
+        o2[2] = nb3(g, id, ii[1], 1, 1) - id;
+        o3[0] = nb3(g, id, ii[2], 2, -1) - id;
+        o3[2] = nb3(g, id, ii[2], 2, 1) - id;
         float s = 0.0f;
 #pragma unroll
         for (int d3 = 0; d3 < 3; ++d3) {
             float pl = 0.0f;
 #pragma unroll
             for (int d2 = 0; d2 < 3; ++d2) {
-                const int b = c + (d2 - 1) * HX + (d3 - 1) * HX * HY;
-                const float row = 0.25f * T[b - 1] + 0.5f * T[b] + 0.25f * T[b + 1];
+                const int b = id + o2[d2] + o3[d3];
+                const float row = 0.25f * in[b + o1[0]] + 0.5f * in[b] + 0.25f * in[b + o1[2]];
                 pl += (d2 == 1 ? 0.5f : 0.25f) * row;
             }
             s += (d3 == 1 ? 0.5f : 0.25f) * pl;
         }
-        out[(size_t(k) * g.n[1] + j) * g.n[0] + i] = s;
+        out[id] = s;
     }
 }
 
@@ -1304,9 +1295,8 @@ int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* x
     k3f_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, rho, Gf, t0, t1, t2, dv);
     k_mon_omega_f<<<G, 256, 0, s>>>(flat, d->mon, t0, t1, t2, dv, om);
     int n = 3;
-    const int ftiles = ((d->g.n[0] + FT3X - 1) / FT3X) * ((d->g.n[1] + FT3Y - 1) / FT3Y) * ((d->g.n[2] + FT3Z - 1) / FT3Z);
     for (int k = 0; k < d->filter_passes; ++k) {
-        k3f_filter_tiled<<<ftiles, 256, 0, s>>>(d->g, om, other);
+        k3f_filter<<<G, 256, 0, s>>>(d->g, om, other);
         ++n;
         float* t = om;
         om = other;
