@@ -1005,8 +1005,8 @@ int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cu
 }
 
 int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
-            cudaStream_t s, cudaError_t* err) {
-    if (d->mixed) return d3f_mesh(d, JU, J, xn, xdot, dv, s, err);       // FP32 pipe (es_3d_mixed.cu)
+            cudaStream_t s, cudaError_t* err, bool xe_current) {
+    if (d->mixed) return d3f_mesh(d, JU, J, xn, xdot, dv, s, err, xe_current);   // FP32 pipe (es_3d_mixed.cu)
     const int G = d->grid;
     // the elementwise kernels of the 1D/2D path see the 3D mesh as N nodes in a row
     GridParams flat;

@@ -68,8 +68,9 @@ int d3_init_J(const Ctx3* d, const double* x, void* J, cudaStream_t s, cudaError
 int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
 int d3_cfl(Ctx3* d, const void* JU, const void* J, const double* x, DevScalars* dv, cudaStream_t s,
            cudaError_t* err);
+// xe_current: the stage-metric coordinates of xn (d->XE) are current (the step's d3_cfl just formed them)
 int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
-            cudaStream_t s, cudaError_t* err);
+            cudaStream_t s, cudaError_t* err, bool xe_current = false);
 // eq. cfl with the step's mesh velocity (into RED_CFL2), from the node fields and metrics d3_cfl left for x^n
 int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cudaStream_t s, cudaError_t* err);
 // the mixed form's kernels (es_3d_mixed.cu)
@@ -82,6 +83,6 @@ int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);
 int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
 int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
-             cudaStream_t s, cudaError_t* err);
+             cudaStream_t s, cudaError_t* err, bool xe_current);
 
 }  // namespace es

@@ -881,8 +881,9 @@ __global__ void k3_split(const double* a, float* out, size_t n) {
 // On the FP32 pipe, with the Jacobi iteration written for the displacement delta = x - x^n from
 // the mesh at t^n.  omega is fixed during the sweeps, so x^[nu+1]_i = sum_nb a_nb x^[nu]_nb with
 // a_nb = w_nb / sum_nb w_nb becomes delta^[nu+1]_i = g_i + sum_nb a_nb delta^[nu]_nb, where
-// g_i = sum_nb a_nb (x^n_nb - x^n_i) is formed once per solve in FP64 from the FP64 mesh and
-// then rounded: the sweeps round only the displacement, which is small against the spacing.
+// g_i = sum_nb a_nb (x^n_nb - x^n_i) is formed once per solve in double-float from x^n on the
+// extended mesh (the stage metrics' coordinates, ghosts with the period shift) and then rounded:
+// the sweeps round only the displacement, which is small against the spacing.
 // The mixed form has periodic and outflow ends only; every node on an outflow end is fixed, so a
 // node that moves has its six neighbours in the mesh or across a periodic end, where delta wraps
 // (x shifts by the period, delta does not).
@@ -909,18 +910,6 @@ __device__ __forceinline__ bool fixed_node3(const Grid3& g, const int* ii) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) f = f || (g.bc[k] != ES_BC_PERIODIC && (ii[k] == 0 || ii[k] == g.n[k] - 1));
     return f;
-}
-
-// x^n_comp at the neighbour s = +-1 along k minus x^n_comp at the node (FP64), for a node that
-// moves: the neighbour is in the mesh or across a periodic end
-__device__ __forceinline__ double xn_step(const Grid3& g, const double* f, int id, int ik, int k, int s, int comp) {
-    const int n = g.n[k], j = ik + s;
-    const int st = stride3i(g, k);
-    if (j >= 0 && j < n) return f[id + s * st] - f[id];
-    const int r = j < 0 ? j + n : j - n;
-    double v = f[id + (r - ik) * st] - f[id];
-    if (comp == k) v += (j < 0 ? -1.0 : 1.0) * g.period[k];
-    return v;
 }
 
 __device__ __forceinline__ float warp_max_f(float v) {
@@ -1018,9 +1007,11 @@ __global__ void k3f_filter(Grid3 g, const float* in, float* out) {
 
 // the sweep coefficients of every node: a_nb for the six neighbours ([6][N], order -xi_1, +xi_1,
 // -xi_2, ...) and g ([3][N]); zero at fixed nodes
-__global__ void k3f_coeffs(Grid3 g, const float* om, const double* xn, float* A, float* Gc) {
+__global__ void k3f_coeffs(Grid3 g, const float* om, const float* XEh, const float* XEl, float* A, float* Gc) {
     const int N = g.n[0] * g.n[1] * g.n[2];
     const size_t P = size_t(N);
+    const size_t NE = size_t(g.n[0] + 6) * (g.n[1] + 6) * (g.n[2] + 6);
+    const size_t est[3] = {1, size_t(g.n[0] + 6), size_t(g.n[0] + 6) * (g.n[1] + 6)};
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         int ii[3];
         split3(g, id, ii);
@@ -1041,19 +1032,25 @@ __global__ void k3f_coeffs(Grid3 g, const float* om, const double* xn, float* A,
             den += w[2 * k] + w[2 * k + 1];
         }
         const float iden = 1.0f / den;
-        double gs[3] = {0.0, 0.0, 0.0};
+        // x^n_nb - x^n_i from the extended mesh (ghosts with the period shift), in double-float
+        const size_t e = eidx(g, ii[0] + 3, ii[1] + 3, ii[2] + 3);
+        df gs[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float am = w[2 * k] * iden, ap = w[2 * k + 1] * iden;
             A[(2 * k) * P + id] = am;
             A[(2 * k + 1) * P + id] = ap;
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                gs[c] += double(am) * xn_step(g, xn + size_t(c) * N, id, ii[k], k, -1, c) +
-                         double(ap) * xn_step(g, xn + size_t(c) * N, id, ii[k], k, 1, c);
+            for (int c = 0; c < 3; ++c) {
+                const size_t o = c * NE + e;
+                const df xi = {XEh[o], XEl[o]};
+                const df dm = df_sub({XEh[o - est[k]], XEl[o - est[k]]}, xi);
+                const df dp = df_sub({XEh[o + est[k]], XEl[o + est[k]]}, xi);
+                gs[c] = df_add(gs[c], df_add(df_mul_f(dm, am), df_mul_f(dp, ap)));
+            }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Gc[c * P + id] = float(gs[c]);
+        for (int c = 0; c < 3; ++c) Gc[c * P + id] = gs[c].hi + gs[c].lo;
     }
 }
 
@@ -1122,22 +1119,27 @@ __device__ __forceinline__ const float* sweep_result(const DevScalars* d, const 
 
 // Delta_gamma over all nodes and directions (Sec. 4): the spacing to the neighbour the node
 // moves towards, over twice its displacement along that direction
-__global__ void k3f_limiter(Grid3 g, const double* xn, const float* da, const float* db, DevScalars* d) {
+__global__ void k3f_limiter(Grid3 g, const float* XEh, const float* XEl, const float* da, const float* db,
+                            DevScalars* d) {
     const int N = g.n[0] * g.n[1] * g.n[2];
     const size_t P = size_t(N);
+    const size_t NE = size_t(g.n[0] + 6) * (g.n[1] + 6) * (g.n[2] + 6);
+    const size_t est[3] = {1, size_t(g.n[0] + 6), size_t(g.n[0] + 6) * (g.n[1] + 6)};
     const float* dl = sweep_result(d, da, db);
     float m = 1.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; dl && id < N; id += gridDim.x * blockDim.x) {
         int ii[3];
         split3(g, id, ii);
         if (fixed_node3(g, ii)) continue;
+        const size_t e = eidx(g, ii[0] + 3, ii[1] + 3, ii[2] + 3);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float dx = dl[k * P + id];
+            const size_t o = k * NE + e;                       // component k of x^n along direction k
             if (dx < 0.0f)
-                m = fminf(m, float(-xn_step(g, xn + size_t(k) * N, id, ii[k], k, -1, k)) / (-2.0f * dx));
+                m = fminf(m, df_diff({XEh[o], XEl[o]}, {XEh[o - est[k]], XEl[o - est[k]]}) / (-2.0f * dx));
             else if (dx > 0.0f)
-                m = fminf(m, float(xn_step(g, xn + size_t(k) * N, id, ii[k], k, 1, k)) / (2.0f * dx));
+                m = fminf(m, df_diff({XEh[o + est[k]], XEl[o + est[k]]}, {XEh[o], XEl[o]}) / (2.0f * dx));
         }
     }
     m = warp_min_f(m);
@@ -1271,8 +1273,17 @@ int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cuda
 }
 
 int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
-             cudaStream_t s, cudaError_t* err) {
+             cudaStream_t s, cudaError_t* err, bool xe_current) {
     const int G = d->grid;
+    int n = 0;
+    // the sweep coefficients and the limiter read x^n on the extended mesh as double-float planes, which the
+    // step's time-step pass has just formed for its metrics (xe_current); otherwise form them here
+    float* XEh = (float*)d->XE;
+    float* XEl = XEh + 3 * d->NE;
+    if (!xe_current) {
+        k3f_coords<<<G, 256, 0, s>>>(d->g, xn, nullptr, 0.0, nullptr, 0.0, XEh, XEl);
+        ++n;
+    }
     // the elementwise kernels of the 1D/2D mixed path see the 3D mesh as N nodes in a row
     GridParams flat;
     flat.dim = 3;
@@ -1294,7 +1305,7 @@ int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* x
     k_mon_fields_f<<<G, 256, 0, s>>>(flat, gas_f32(d->gas), (const float*)JU, (const float*)J, rho, Gf);
     k3f_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, rho, Gf, t0, t1, t2, dv);
     k_mon_omega_f<<<G, 256, 0, s>>>(flat, d->mon, t0, t1, t2, dv, om);
-    int n = 3;
+    n += 3;
     for (int k = 0; k < d->filter_passes; ++k) {
         k3f_filter<<<G, 256, 0, s>>>(d->g, om, other);
         ++n;
@@ -1302,14 +1313,14 @@ int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* x
         om = other;
         other = t;
     }
-    k3f_coeffs<<<G, 256, 0, s>>>(d->g, om, xn, A, d->gc);
+    k3f_coeffs<<<G, 256, 0, s>>>(d->g, om, XEh, XEl, A, d->gc);
     ++n;
     const int check = d->eps > 0.0;
     for (int k = 0; k < d->sweeps; ++k) {
         k3f_jacobi<<<G, 256, 0, s>>>(d->g, A, d->gc, da, db, k, dv, check, d->eps);
         ++n;
     }
-    k3f_limiter<<<G, 256, 0, s>>>(d->g, xn, da, db, dv);
+    k3f_limiter<<<G, 256, 0, s>>>(d->g, XEh, XEl, da, db, dv);
     k3f_velocity<<<G, 256, 0, s>>>(d->g, da, db, dv, xdot);
     n += 2;
     *err = cudaGetLastError();

@@ -369,7 +369,7 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
     count(c);
     const double* xdot = nullptr;
     if (c->p.moving) {
-        n = d3_mesh(c->d3, JU, J, x, c->xdot, c->dev, s, &e);
+        n = d3_mesh(c->d3, JU, J, x, c->xdot, c->dev, s, &e, true);     // d3_cfl formed x^n's metric coordinates
         if (n < 0) return cuda_fail(c, e, "3D mesh kernels");
         count(c, n);
         xdot = c->xdot;
