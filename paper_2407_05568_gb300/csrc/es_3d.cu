@@ -889,12 +889,13 @@ cudaError_t d3_alloc(Ctx3* d) {
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc((void**)&d->NK[k], sizeof(double) * 3 * d->NKk[k]);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->NF, sizeof(double) * F3_COUNT * d->N);
     if (e == cudaSuccess) e = cudaMalloc((void**)&d->RH, sizeof(double) * 6 * d->N);
+    if (e == cudaSuccess && d->mixed) e = cudaMalloc((void**)&d->XD, sizeof(float) * 3 * d->NE);
     return e;
 }
 
 void d3_free(Ctx3* d) {
     if (!d) return;
-    void* b[] = {d->XE, d->D, d->NK[0], d->NK[1], d->NK[2], d->NF, d->RH};
+    void* b[] = {d->XE, d->D, d->NK[0], d->NK[1], d->NK[2], d->NF, d->RH, d->XD};
     for (void* p : b)
         if (p) cudaFree(p);
 }
@@ -920,8 +921,8 @@ int d3_init_J(const Ctx3* d, const double* x, void* J, cudaStream_t s, cudaError
 
 // metrics of x_s = xn + cst dt xdot for the three directions
 static int enqueue_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const double* dt_dev,
-                           double dt_host, cudaStream_t s) {
-    if (d->mixed) return d3f_metrics(d, xn, xdot, cst, dt_dev, dt_host, s);
+                           double dt_host, cudaStream_t s, const Stage3* inc = nullptr) {
+    if (d->mixed) return d3f_metrics(d, xn, xdot, cst, dt_dev, dt_host, s, inc);
     const int G = d->grid;
     k3_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, d->XE);
     k3_deriv<<<G, 256, 0, s>>>(d->g, d->XE, d->D);
@@ -932,7 +933,7 @@ static int enqueue_metrics(Ctx3* d, const double* xn, const double* xdot, double
 int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err) {
     int n = 0;
     if (!a.reuse) {
-        n += enqueue_metrics(d, a.xn, a.xdot, a.cst, a.dt_dev, a.dt_host, s);
+        n += enqueue_metrics(d, a.xn, a.xdot, a.cst, a.dt_dev, a.dt_host, s, a.xe_incr ? &a : nullptr);
         if (d->mixed) n += d3f_nodes(d, a.JUs, a.Js, st, s);
         else {
             k3_nodes<<<d->grid, 256, 0, s>>>(d->g, d->gas, (const double*)a.JUs, (const double*)a.Js, d->NF, st);

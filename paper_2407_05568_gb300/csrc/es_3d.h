@@ -39,6 +39,7 @@ struct Ctx3 {
     // mesh scratch (the context's buffers)
     double *rhoF, *GF, *t0, *t1, *t2, *om0, *om1, *xa, *xb;
     float* gc;                // mixed form: the sweeps' constant term g [3][N]
+    float* XD;                // mixed form: the step's mesh velocity on the extended mesh [3][NE] (float)
     // mixed form: tensor maps (CUtensorMap, 128 bytes) of the float node fields for the TMA-staged xi_2 and
     // xi_3 pencils, per direction and pencil shape; state 0 = not built yet, 1 = built, -1 = plain loads
     int no_tma;               // 1: plain loads only (tile D3_NSHAPES + k)
@@ -56,6 +57,10 @@ struct Stage3 {
     const double* dt_dev;     // device dt (nullptr: dt_host)
     int mode;                 // 0: RK combination; 1: right-hand sides into (JUo, Jo)
     int reuse;                // the metrics and node fields of (xn, JUs, Js) are in the buffers
+    // mixed form, within a step: the metric coordinates (d->XE) hold x^n + xe_cst dt xdot, so the stage's are
+    // formed by adding (cst - xe_cst) dt xdot (xe_incr); form_xd: first form xdot on the extended mesh (d->XD)
+    int xe_incr, form_xd;
+    double xe_cst;
 };
 
 constexpr int D3_NSHAPES = 4;
@@ -77,7 +82,7 @@ int d3_cfl_moving(Ctx3* d, const void* J, const double* xdot, DevScalars* dv, cu
 cudaError_t d3f_prepare();
 // the stage metrics of the mixed form (double-float arithmetic, float metrics in NK[k] as [3][NKk])
 int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const double* dt_dev, double dt_host,
-                cudaStream_t s);
+                cudaStream_t s, const Stage3* inc = nullptr);
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s);
 int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s);
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);

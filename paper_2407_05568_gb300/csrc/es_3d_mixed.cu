@@ -762,6 +762,35 @@ __global__ void k3f_coords(Grid3 g, const double* xn, const double* xdot, double
     }
 }
 
+// the mesh velocity on the extended mesh as floats XD [3][NE]: the ghost rule of the coordinates without their
+// period shift (a ghost's coordinate is the ghost rule's combination of x^n + c dt xdot plus the shift, so its
+// velocity is the same combination of xdot)
+__global__ void k3f_xdot_ext(Grid3 g, const double* xdot, float* XD) {
+    const size_t N = size_t(g.n[0]) * g.n[1] * g.n[2];
+    const unsigned E1 = g.n[0] + 6, E2 = g.n[1] + 6, E3 = g.n[2] + 6;
+    const size_t NE = size_t(E1) * E2 * E3;
+    for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < NE; e += size_t(gridDim.x) * blockDim.x) {
+        const unsigned eu = unsigned(e);
+        const int i1 = int(eu % E1) - 3, i2 = int((eu / E1) % E2) - 3, i3 = int(eu / (E1 * E2)) - 3;
+        const bool in = inside3(g, i1, i2, i3, 0);
+        const size_t id = in ? idx3(g, i1, i2, i3) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            XD[c * NE + e] = float(in ? xdot[c * N + id] : ghost_value3(g, xdot + c * N, nullptr, 0.0, i1, i2, i3, -1));
+    }
+}
+
+// XE += f dt XD in double-float (f = the change of the stage-time fraction; dt from the device or the host)
+__global__ void k3f_coords_add(size_t NE, float* XEh, float* XEl, const float* XD, double f, const double* dt_dev,
+                               double dt_host) {
+    const float a = float(f * (dt_dev ? *dt_dev : dt_host));
+    for (size_t e = blockIdx.x * size_t(blockDim.x) + threadIdx.x; e < 3 * NE; e += size_t(gridDim.x) * blockDim.x) {
+        const df v = df_add_f({XEh[e], XEl[e]}, a * XD[e]);
+        XEh[e] = v.hi;
+        XEl[e] = v.lo;
+    }
+}
+
 // D[3 l + j] = delta_l[x_p] x_q (p = (j + 1) % 3, q = (j + 2) % 3; delta_l undivided, 0 where the xi_l index is
 // not interior) as (hi, lo) planes Dh, Dl [9][NE]
 __global__ void k3f_deriv(Grid3 g, const float* XEh, const float* XEl, float* Dh, float* Dl) {
@@ -1205,15 +1234,24 @@ static WenoF wenof(const Weno& w) {
 }
 
 int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const double* dt_dev, double dt_host,
-                cudaStream_t s) {
+                cudaStream_t s, const Stage3* inc) {
     const int G = d->grid;
     const size_t NE = d->NE;
     float* XEh = (float*)d->XE;                   // [3][NE] doubles hold the (hi, lo) float planes
     float* Dh = (float*)d->D;                     // [9][NE] likewise
-    k3f_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, XEh, XEh + 3 * NE);
+    int n = 4;
+    if (inc && xdot) {                            // within a step: move the coordinates the buffer holds
+        if (inc->form_xd) {
+            k3f_xdot_ext<<<G, 256, 0, s>>>(d->g, xdot, d->XD);
+            ++n;
+        }
+        k3f_coords_add<<<G, 256, 0, s>>>(NE, XEh, XEh + 3 * NE, d->XD, cst - inc->xe_cst, dt_dev, dt_host);
+    } else {
+        k3f_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, XEh, XEh + 3 * NE);
+    }
     k3f_deriv<<<G, 256, 0, s>>>(d->g, XEh, XEh + 3 * NE, Dh, Dh + 9 * NE);
     for (int k = 0; k < 3; ++k) k3f_metric<<<G, 256, 0, s>>>(d->g, k, Dh, Dh + 9 * NE, (float*)d->NK[k]);
-    return 5;
+    return n + 1;
 }
 
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s) {
