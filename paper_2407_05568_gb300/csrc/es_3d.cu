@@ -150,8 +150,10 @@ __global__ void k3_deriv(Grid3 g, const double* XE, double* D) {
     }
 }
 
-// J dxi_k/dx_j on direction k's grid (n_k + 6 nodes along xi_k, interior across)
-__global__ void k3_metric(Grid3 g, int k, const double* D, double* NKo) {
+// J dxi_k/dx_j on direction k's grid (n_k + 6 nodes along xi_k, interior across); the direction is a template
+// parameter (no run-time indexing of the grid's arrays)
+template <int k>
+__global__ void k3_metric(Grid3 g, const double* D, double* NKo) {
     const int E1 = g.n[0] + 6, E2 = g.n[1] + 6;
     const size_t NE = size_t(E1) * E2 * (g.n[2] + 6);
     int m1 = g.n[0], m2 = g.n[1], m3 = g.n[2];
@@ -926,7 +928,9 @@ static int enqueue_metrics(Ctx3* d, const double* xn, const double* xdot, double
     const int G = d->grid;
     k3_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, d->XE);
     k3_deriv<<<G, 256, 0, s>>>(d->g, d->XE, d->D);
-    for (int k = 0; k < 3; ++k) k3_metric<<<G, 256, 0, s>>>(d->g, k, d->D, d->NK[k]);
+    k3_metric<0><<<G, 256, 0, s>>>(d->g, d->D, d->NK[0]);
+    k3_metric<1><<<G, 256, 0, s>>>(d->g, d->D, d->NK[1]);
+    k3_metric<2><<<G, 256, 0, s>>>(d->g, d->D, d->NK[2]);
     return 5;
 }
 

@@ -829,7 +829,9 @@ __global__ void k3f_deriv(Grid3 g, const float* XEh, const float* XEl, float* Dh
 }
 
 // J dxi_k/dx_j on direction k's grid (n_k + 6 nodes along xi_k, interior across), rounded to float [3][M]
-__global__ void k3f_metric(Grid3 g, int k, const float* Dh, const float* Dl, float* NKo) {
+// (the direction is a template parameter: no run-time indexing of the grid's arrays)
+template <int k>
+__global__ void k3f_metric(Grid3 g, const float* Dh, const float* Dl, float* NKo) {
     const unsigned E1 = g.n[0] + 6, E2 = g.n[1] + 6;
     const size_t NE = size_t(E1) * E2 * (g.n[2] + 6);
     unsigned m1 = g.n[0], m2 = g.n[1], m3 = g.n[2];
@@ -1250,7 +1252,9 @@ int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const
         k3f_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, XEh, XEh + 3 * NE);
     }
     k3f_deriv<<<G, 256, 0, s>>>(d->g, XEh, XEh + 3 * NE, Dh, Dh + 9 * NE);
-    for (int k = 0; k < 3; ++k) k3f_metric<<<G, 256, 0, s>>>(d->g, k, Dh, Dh + 9 * NE, (float*)d->NK[k]);
+    k3f_metric<0><<<G, 256, 0, s>>>(d->g, Dh, Dh + 9 * NE, (float*)d->NK[0]);
+    k3f_metric<1><<<G, 256, 0, s>>>(d->g, Dh, Dh + 9 * NE, (float*)d->NK[1]);
+    k3f_metric<2><<<G, 256, 0, s>>>(d->g, Dh, Dh + 9 * NE, (float*)d->NK[2]);
     return n + 1;
 }
 
