@@ -242,6 +242,16 @@ int es_time_stage(es_ctx* ctx, const void* JU, const void* J, const double* x, i
  * Divisors must be finite, normal and nonzero. */
 int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream);
 
+/* Self-test of the mixed form's arithmetic building blocks, for device arrays of n values (test use):
+ * split[2i], split[2i+1] = x[i] as an unevaluated sum hi + lo of two floats taken apart from its bits
+ * (|x - hi - lo| < 2^-46 |x| for 2^-103 <= |x| < 2^127, hi the truncation of x); wide[i] = f[i] as a
+ * double assembled from its bits (exact, NaN payloads kept); mul[2i..2i+1] and add[2i..2i+1] = the
+ * double-float product and sum of (a[2i], a[2i+1]) and (b[2i], b[2i+1]) (the Sec. 3 state arithmetic of
+ * the mixed form).  Asynchronous on `stream`; ES_ERR_ARG for a null array or n <= 0, ES_ERR_CUDA if the
+ * launch fails. */
+int es_selftest_mixed_arith(const double* x, const float* f, const float* a, const float* b, int64_t n,
+                            float* split, double* wide, float* mul, float* add, void* stream);
+
 /* Measured arithmetic rates of the current GPU (the roofline denominators of the stage kernels, which the
  * FP64 pipe bounds in the plain form and the FP32 pipe in the mixed and batched forms): a grid of SMs x 8
  * CTAs x 256 threads, each with 8 independent chains of dependent FMAs, timed with CUDA events on `stream`,

@@ -1021,6 +1021,7 @@ int d3_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xd
     flat.bc[0] = flat.bc[1] = ES_BC_PERIODIC;
     flat.inv_dxi[0] = flat.inv_dxi[1] = 1.0;
     flat.period[0] = flat.period[1] = 0.0;
+    grid_floats(flat);
     int n = 0;
     launch_mon_fields(flat, d->gas, JU, J, d->rhoF, d->GF, false, G, s);
     k3_mon_terms<<<G, 256, 0, s>>>(d->g, d->mon, d->rhoF, d->GF, d->t0, d->t1, d->t2, dv);

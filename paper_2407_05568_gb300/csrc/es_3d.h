@@ -14,6 +14,7 @@ struct Grid3 {
     int bc[3];
     double inv_dxi[3];
     double period[3];
+    float finv[3], finv2[3];    // 1/dxi_k and 1/dxi_k^2 rounded once to float on the host (the FP32 kernels' copies)
 };
 
 // the context's 3D scratch (device) and settings

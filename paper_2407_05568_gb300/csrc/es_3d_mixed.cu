@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(const __grid_constant__ Dir
         __syncthreads();
 
         // ---- E: divergence, accumulated in float; the last direction writes double-float results
-        const float inv = float(g.inv_dxi[K]);
+        const float inv = g.finv[K];
         for (int t = tid; t < W * LB; t += NT) {
             int line, pos;
             if (K == 0) { line = t / LB; pos = t % LB; }
@@ -889,7 +889,7 @@ __global__ void k3_cfl_f(Grid3 g, Gas Gd, const float* NF, const float* J, const
             const size_t mi = (size_t(i3 + (k == 2 ? 3 : 0)) * m2 + i2 + (k == 1 ? 3 : 0)) * m1 + i1 + (k == 0 ? 3 : 0);
             const float n0 = NK[k][mi], n1 = NK[k][M[k] + mi], n2 = NK[k][2 * M[k] + mi];
             tot += (fabsf(n0 * vr[0] + n1 * vr[1] + n2 * vr[2]) + sqrtf(n0 * n0 + n1 * n1 + n2 * n2) * c) * iJ *
-                   float(g.inv_dxi[k]);
+                   g.finv[k];
         }
         if (!(c2 > 0.0f)) tot = 3.0e38f;
         mx = fmaxf(mx, tot);
@@ -968,7 +968,7 @@ __global__ void k3f_mon_terms(Grid3 g, MonitorParams mp, const float* rhoF, cons
         float gr = 0.0f, gg = 0.0f, lg = 0.0f, lr = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float h = float(g.inv_dxi[k]);
+            const float h = g.finv[k];
             const int ip = nb3(g, id, ii[k], k, 1), im = nb3(g, id, ii[k], k, -1);
             const df rp = {rhoF[ip], rhoF[N + ip]}, rm = {rhoF[im], rhoF[N + im]};
             const df Gp = {GF[ip], GF[N + ip]}, Gm = {GF[im], GF[N + im]};
@@ -1057,7 +1057,7 @@ __global__ void k3f_coeffs(Grid3 g, const float* om, const float* XEh, const flo
         float w[6], den = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float ih2 = float(g.inv_dxi[k] * g.inv_dxi[k]);
+            const float ih2 = g.finv2[k];
             w[2 * k] = 0.5f * (w0 + om[nb3(g, id, ii[k], k, -1)]) * ih2;
             w[2 * k + 1] = 0.5f * (w0 + om[nb3(g, id, ii[k], k, 1)]) * ih2;
             den += w[2 * k] + w[2 * k + 1];
@@ -1334,6 +1334,7 @@ int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* x
     flat.bc[0] = flat.bc[1] = ES_BC_PERIODIC;
     flat.inv_dxi[0] = flat.inv_dxi[1] = 1.0;
     flat.period[0] = flat.period[1] = 0.0;
+    grid_floats(flat);
     float* rho = (float*)d->rhoF;
     float* Gf = (float*)d->GF;
     float* t0 = (float*)d->t0;

@@ -317,7 +317,6 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int w
     count(c);
     // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
     const bool fuse = c->p.dim == 2;
-    const dim3 tiles((c->g.n1 + 31) / 32, (c->g.n2 + 15) / 16);
     if (fuse && c->p.filter_passes >= 1 && c->p.filter_passes <= 8) {
         launch_omega_filter(c->g, c->mon, t0, t1, t2, c->dev, c->p.filter_passes, om, s);
         count(c);
@@ -333,7 +332,7 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int w
     const int check = c->p.jacobi_eps > 0.0;
     const int mu = c->p.jacobi_sweeps;
     if (fuse && !check && mu >= 1 && mu <= 8) {              // the tile kernel also forms Delta_gamma
-        k_jacobi_multi_f<<<tiles, 256, 0, s>>>(c->g, om, c->fdisp, ((mu - 1) & 1) ? db : da, mu, c->dev, 1);
+        launch_jacobi_tiles(c->g, om, c->fdisp, ((mu - 1) & 1) ? db : da, mu, c->dev, 1, s);
         count(c);
     } else {
         for (int k = 0; k < mu; ++k) {
@@ -545,6 +544,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->g.bc[1] = p->dim == 2 ? p->bc[1] : ES_BC_PERIODIC;
     c->g.inv_dxi[0] = 1.0 / p->dxi[0];
     c->g.inv_dxi[1] = p->dim == 2 ? 1.0 / p->dxi[1] : 0.0;
+    grid_floats(c->g);
     c->g.period[0] = p->period[0];
     c->g.period[1] = p->period[1];
     c->gas.a = p->a;
@@ -580,6 +580,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         c->g.n2 = 1;
         c->g.bc[0] = c->g.bc[1] = ES_BC_PERIODIC;
         c->g.inv_dxi[0] = c->g.inv_dxi[1] = 1.0;
+        grid_floats(c->g);
     }
     c->N = size_t(c->g.n1) * c->g.n2;
     c->nc = p->dim + 2;
@@ -646,6 +647,8 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
             d->g.n[k] = nn[k];
             d->g.bc[k] = p->bc[k];
             d->g.inv_dxi[k] = 1.0 / p->dxi[k];
+            d->g.finv[k] = float(d->g.inv_dxi[k]);
+            d->g.finv2[k] = float(d->g.inv_dxi[k] * d->g.inv_dxi[k]);
             d->g.period[k] = p->period[k];
         }
         d->gas = c->gas;

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include "es_aux.h"
+#include "es_bits.cuh"
+#include "es_df.cuh"
 #include "es_device.cuh"
 
 namespace es {
@@ -648,18 +650,37 @@ __global__ void k_warm_start(GridParams g, const double* xn, const float* out, d
 // Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)
 // and FP32 mesh velocity, once per step (the base is linear in the node index,
 // so delta_k of it is exactly dxi_k e_k)
+// the float displacement x - (x_00 + i dxi_1) of one coordinate, in double-float arithmetic on the FP32 pipe:
+// x and x_00 split from their bits (es_bits.cuh), i dxi_1 an exact product plus i dxl, error-free sums; the
+// absolute error is about 2^-45 |x|, far below the float rounding of the displacement itself
+__device__ __forceinline__ float disp_f32(double x, float x0h, float x0l, int i, float dh, float dl) {
+    float xh, xl;
+    bits::split(x, xh, xl);
+    const float fi = bits::small_int(i);
+    const float ph = fi * dh;
+    const float pl = fmaf(fi, dl, fmaf(fi, dh, -ph));
+    // b = x_00 + i dxi as (bh, bl)
+    const float bh = x0h + ph;
+    const float bv = bh - x0h;
+    const float bl = ((x0h - (bh - bv)) + (ph - bv)) + (x0l + pl);
+    // x - b
+    const float sh = xh - bh;
+    const float sv = sh - xh;
+    const float se = (xh - (sh - sv)) + (-bh - sv);
+    return sh + (se + (xl - bl));
+}
+
 __global__ void k_mesh_f32(GridParams g, const double* __restrict__ x, const double* __restrict__ xdot,
                            float* __restrict__ disp, float* __restrict__ fxd, DevScalars* rst) {
     const int N = g.n1 * g.n2;
     if (rst && blockIdx.x == 0 && threadIdx.x == 0) reset_scalars(rst);
-    const double x00 = x[0];
-    const double y00 = g.dim == 2 ? x[N] : 0.0;
-    const double dxi1 = 1.0 / g.inv_dxi[0];
-    const double dxi2 = g.dim == 2 ? 1.0 / g.inv_dxi[1] : 0.0;
+    float x0h, x0l, y0h = 0.0f, y0l = 0.0f;
+    bits::split(x[0], x0h, x0l);
+    if (g.dim == 2) bits::split(x[N], y0h, y0l);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
-        disp[id] = float(x[id] - (x00 + i * dxi1));
-        if (g.dim == 2) disp[N + id] = float(x[N + id] - (y00 + j * dxi2));
+        disp[id] = disp_f32(x[id], x0h, x0l, i, g.dxh[0], g.dxl[0]);
+        if (g.dim == 2) disp[N + id] = disp_f32(x[N + id], y0h, y0l, j, g.dxh[1], g.dxl[1]);
         if (xdot)                           // fxd is read only where a velocity was given
             for (int k = 0; k < g.dim; ++k) fxd[k * N + id] = float(xdot[k * N + id]);
     }
@@ -711,6 +732,31 @@ __global__ void k_selftest_division(const double* a, const double* b, double* q,
     }
 }
 }  // namespace es
+
+namespace es {
+__global__ void k_selftest_mixed_arith(const double* x, const float* f, const float* a, const float* b, int64_t n,
+                                       float* split, double* wide, float* mul, float* add) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        bits::split(x[i], split[2 * i], split[2 * i + 1]);
+        wide[i] = bits::widen(f[i]);
+        const mixed::df u = {a[2 * i], a[2 * i + 1]}, v = {b[2 * i], b[2 * i + 1]};
+        const mixed::df p = mixed::df_mul(u, v), q = mixed::df_add(u, v);
+        mul[2 * i] = p.hi;
+        mul[2 * i + 1] = p.lo;
+        add[2 * i] = q.hi;
+        add[2 * i + 1] = q.lo;
+    }
+}
+}  // namespace es
+
+extern "C" int es_selftest_mixed_arith(const double* x, const float* f, const float* a, const float* b, int64_t n,
+                                       float* split, double* wide, float* mul, float* add, void* stream) {
+    if (!x || !f || !a || !b || !split || !wide || !mul || !add || n <= 0) return ES_ERR_ARG;
+    const int64_t blocks = (n + 255) / 256;
+    es::k_selftest_mixed_arith<<<int(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(
+        x, f, a, b, n, split, wide, mul, add);
+    return cudaGetLastError() == cudaSuccess ? ES_OK : ES_ERR_CUDA;
+}
 
 extern "C" int es_selftest_division(const double* a, const double* b, double* q, double* r, int64_t n, void* stream) {
     if (!a || !b || !q || !r || n <= 0) return ES_ERR_ARG;

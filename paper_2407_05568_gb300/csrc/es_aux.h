@@ -12,7 +12,24 @@ struct GridParams {
     int bc[2];
     double inv_dxi[2];
     double period[2];
+    // float copies formed on the host (grid_floats): 1/dxi_k, dxi_k and 1/dxi_k^2, each the double value rounded
+    // once; the FP32 kernels read these instead of converting (double conversions and divisions issue at 1/64 of
+    // the FP32 rate on this GPU)
+    float finv[2], fdx[2], finv2[2];
+    double dx[2];       // 1 / inv_dxi_k (host-formed, as the kernels formed it)
+    float dxh[2], dxl[2];   // dx_k as the unevaluated float sum dxh + dxl
 };
+
+inline void grid_floats(GridParams& g) {
+    for (int k = 0; k < 2; ++k) {
+        g.finv[k] = float(g.inv_dxi[k]);
+        g.fdx[k] = float(1.0 / g.inv_dxi[k]);
+        g.finv2[k] = float(g.inv_dxi[k] * g.inv_dxi[k]);
+        g.dx[k] = 1.0 / g.inv_dxi[k];
+        g.dxh[k] = float(g.dx[k]);
+        g.dxl[k] = float(g.dx[k] - double(g.dxh[k]));
+    }
+}
 
 struct MonitorParams {
     int kind;            // ES_MONITOR_*

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "es_aux.h"
+#include "es_bits.cuh"
 #include "es_device.cuh"
 #include "es_mesh_f32.h"
 
@@ -46,6 +47,26 @@ __device__ __forceinline__ float block_min_f32(float v) {
         for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     return v;
+}
+
+// The per-launch constants formed from device scalars are formed by lane 0 of each warp and broadcast: FP64
+// divisions and conversions issue at 1/64 of the FP32 rate on this GPU, once per warp instead of per thread.
+// The whole warp must call these.
+// omega's coefficients alpha_k / max_k of the three monitor terms (0 where a maximum is 0)
+__device__ __forceinline__ void mon_coeffs(const MonitorParams& mp, const DevScalars* d, float& c0, float& c1,
+                                           float& c2) {
+    float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
+    if ((threadIdx.x & 31) == 0) {
+        const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
+        const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
+        const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
+        v0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
+        v1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
+        v2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    }
+    c0 = __shfl_sync(0xffffffffu, v0, 0);
+    c1 = __shfl_sync(0xffffffffu, v1, 0);
+    c2 = __shfl_sync(0xffffffffu, v2, 0);
 }
 
 // a displacement ghost along one direction as at most two mesh nodes: periodic wrap (d is periodic),
@@ -139,7 +160,7 @@ __device__ __forceinline__ float cfl_node_f(const GridParams& g, const GasF32& G
                                             float* t1 = nullptr) {
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
-    const float idx1 = float(g.inv_dxi[0]), idx2 = float(g.inv_dxi[1]);
+    const float idx1 = g.finv[0], idx2 = g.finv[1];
     const int i = id % g.n1, j = id / g.n1;
     const float iJ = 1.0f / ld2(J, N, id);
     const float rho = ld2(JU, P, id) * iJ;
@@ -298,7 +319,7 @@ __global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (k >= g.dim) break;
-            const float h = float(g.inv_dxi[k]);
+            const float h = g.finv[k];
             const int off = k == 0 ? 1 : HW;
             const mixed::df rp = {srh[c + off], srl[c + off]}, Gp = {sgh[c + off], sgl[c + off]};
             const mixed::df rm = {srh[c - off], srl[c - off]}, Gm = {sgh[c - off], sgl[c - off]};
@@ -357,12 +378,8 @@ int mon_f_blocks(const GridParams& g) {
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega) {
     const int N = g.n1 * g.n2;
-    const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
-    const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
-    const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
-    const float c0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
-    const float c1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
-    const float c2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    float c0, c1, c2;
+    mon_coeffs(mp, d, c0, c1, c2);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
         omega[id] = sqrtf(1.0f + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
 }
@@ -397,8 +414,8 @@ __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, fl
     const float* xin = k == 0 ? d0 : ((k - 1) & 1 ? db : da);
     float* xout = (k & 1) ? db : da;
     float chg = 0.0f;
-    const float ih2k[2] = {float(g.inv_dxi[0] * g.inv_dxi[0]), float(g.inv_dxi[1] * g.inv_dxi[1])};
-    const float dxk[2] = {float(1.0 / g.inv_dxi[0]), float(1.0 / g.inv_dxi[1])};
+    const float ih2k[2] = {g.finv2[0], g.finv2[1]};
+    const float dxk[2] = {g.fdx[0], g.fdx[1]};
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         if (fixed_node_f(g, i, j)) {
@@ -458,7 +475,7 @@ __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, cons
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
     float m = 1.0f;
-    const float hk[2] = {float(1.0 / g.inv_dxi[0]), float(1.0 / g.inv_dxi[1])};
+    const float hk[2] = {g.fdx[0], g.fdx[1]};
 #pragma unroll 4
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
@@ -482,24 +499,28 @@ __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const f
                              double* __restrict__ xdot, const float* __restrict__ terms, double cfl) {
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
-    const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
-    const double dt = d->dt;
-    const float f = dt > 0.0 ? float(gam / dt) : 0.0f;
+    float fl = 0.0f;                    // Delta_gamma / dt (lane 0 of each warp, broadcast)
+    if ((threadIdx.x & 31) == 0) {
+        const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
+        const double dt = d->dt;
+        fl = dt > 0.0 ? float(gam / dt) : 0.0f;
+    }
+    const float f = __shfl_sync(0xffffffffu, fl, 0);
     float m = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const float v1 = f * (xit[id] - d0[id]);
         fxd[id] = v1;
-        xdot[id] = double(v1);
+        xdot[id] = bits::widen(v1);
         float v2 = 0.0f;
         if (g.dim == 2) {
             v2 = f * (xit[N + id] - d0[N + id]);
             fxd[N + id] = v2;
-            xdot[N + id] = double(v2);
+            xdot[N + id] = bits::widen(v2);
         }
         if (cfl > 0.0) m = fmaxf(m, cfl_moving_term(terms, terms + 4 * size_t(N), size_t(N), size_t(id), g.dim, v1, v2));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d->gamma = gam;
+        d->gamma = __longlong_as_double((long long)d->red[RED_GAMMA]);
         d->sweeps_total += d->sweeps;
         d->solves += 1;
     }
@@ -522,172 +543,316 @@ __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const f
 namespace es {
 
 // ---------------------------------------------------------------- fused passes (2D)
-// omega + s filter passes, and mu Jacobi sweeps without a tolerance, each in one launch: a CTA
-// owns a 32 x 16 tile and recomputes a halo of s (or mu) nodes in shared memory, so a pass
-// needs no grid-wide step.  Ghost nodes follow the unfused kernels: periodic halos hold the
-// wrapped nodes (and evolve with them); an outflow ghost of the filter is reset to its clamped
-// boundary node after every pass; outflow boundary nodes of the mesh do not move, so the sweeps
-// never read beyond them.  The arithmetic per node is that of k_mon_omega_f, k_filter_f and
-// k_jacobi_f, in the same order.
-constexpr int FT_X = 32, FT_Y = 16, FT_HMAX = 8;
-constexpr int FT_W = FT_X + 2 * FT_HMAX, FT_H = FT_Y + 2 * FT_HMAX;
+// omega with s filter passes, and mu Jacobi sweeps without a tolerance, each in one launch, on register
+// tiles.  A CTA owns a tile RT_W = 64 nodes wide and NW x RW tall, halo included; lane L of warp w keeps
+// columns 2L and 2L+1 of the warp's band of RW rows in registers.  A node's horizontal neighbours are in its
+// own lane or the adjacent one (one shuffle each), its vertical ones in the lane's registers, and the rows
+// just outside a band are the neighbouring warps' edge rows, exchanged through shared memory once per pass
+// (one barrier).  After p passes the p outermost columns and rows of the tile are stale, so a tile's output
+// is the tile less a band of h = s (or mu) nodes; periodic halos hold the wrapped nodes and evolve with them.
+// At an outflow end the filter reads the end node in place of its missing neighbour (the unfused kernels'
+// clamped index), and the sweeps leave the end nodes where they are, so neither reads beyond the mesh.  The
+// arithmetic per node is that of k_mon_omega_f, k_filter_f and k_jacobi_f, in the same order.
+constexpr int RT_W = 64, RT_HMAX = 8;
 
-// the (x, y) cell of a TW-wide tile one block stride further on (the strided loops below step
-// the cell without an integer division per iteration)
-__device__ __forceinline__ void next_cell(int& sx, int& sy, int2 sq, int TW) {
-    sx += sq.x;
-    sy += sq.y;
-    if (sx >= TW) {
-        sx -= TW;
-        ++sy;
-    }
+// the left neighbour of column 2L (lane L-1's column 2L+1) and the right neighbour of column 2L+1 (lane
+// L+1's column 2L); lanes 0 and 31 get their own value back: the tile's edge columns, never output
+__device__ __forceinline__ float from_left(float b) { return __shfl_up_sync(0xffffffffu, b, 1); }
+__device__ __forceinline__ float from_right(float a) { return __shfl_down_sync(0xffffffffu, a, 1); }
+
+// one 1/4 1/2 1/4 row of the filter, summed as k_filter_f sums it
+__device__ __forceinline__ float filter3(float l, float c, float r) {
+    float s = 0.0f;
+    s += 0.25f * l;
+    s += 0.5f * c;
+    s += 0.25f * r;
+    return s;
 }
 
-// (templated on the value type; the FP64 form keeps one pass per launch: in FP64 the halo
-// recomputation costs more than the launches it saves)
-template <class T>
-__global__ void __launch_bounds__(256) k_omega_filter_t(GridParams g, MonitorParams mp, const T* t0, const T* t1,
-                                                        const T* t2, const DevScalars* d, int passes, T* out) {
-    __shared__ T A[FT_W * FT_H], B[FT_W * FT_H];
-    const int h = passes, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
-    const int2 sq = make_int2(int(blockDim.x) % TW, int(blockDim.x) / TW);   // one stride in cells
-    const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
-    const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
-    const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
-    const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
-    const T c0 = M0 > 0.0 ? T(mp.w0 / M0) : T(0);
-    const T c1 = M1 > 0.0 ? T(mp.w1 / M1) : T(0);
-    const T c2 = M2 > 0.0 ? T(mp.w2 / M2) : T(0);
-    for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
-         idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
-        const int si = state_index(x0 + sx, g.n1, g.bc[0]), sj = state_index(y0 + sy, g.n2, g.bc[1]);
-        const int id = sj * g.n1 + si;
-        A[idx] = sqrt(T(1) + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
+// the filter's row sums at columns a = 2L and b = 2L+1; CX: outflow ends along xi_1, where the end node
+// stands in for its missing neighbour
+struct EndCols {
+    bool a_first, a_last, b_first, b_last;
+};
+
+template <bool CX>
+__device__ __forceinline__ void filter_row(float a, float b, const EndCols& e, float& ra, float& rb) {
+    float la = from_left(b), rgt_a = b, lb = a, rgt_b = from_right(a);
+    if (CX) {
+        if (e.a_first) la = a;
+        if (e.a_last) rgt_a = a;
+        if (e.b_first) lb = b;
+        if (e.b_last) rgt_b = b;
     }
-    __syncthreads();
-    T* cur = A;
-    T* nxt = B;
-    for (int p = 1; p <= h; ++p) {
-        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
-             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
-            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
-            T s = T(0);
-            for (int dj = -1; dj <= 1; ++dj) {
-                T row = T(0);
-                for (int di = -1; di <= 1; ++di) row += (di == 0 ? T(0.5) : T(0.25)) * cur[(sy + dj) * TW + sx + di];
-                s += (dj == 0 ? T(0.5) : T(0.25)) * row;
+    ra = filter3(la, a, rgt_a);
+    rb = filter3(lb, b, rgt_b);
+}
+
+// the passes of one warp's band (va, vb: columns 2L and 2L+1); CY: outflow ends along xi_2, yb: the band's
+// first mesh row
+template <int NW, int RW, bool CX, bool CY>
+__device__ __forceinline__ void filter_passes(float (&va)[RW], float (&vb)[RW], float (*edge)[NW][2][RT_W], int h,
+                                              int w, int lane, int yb, int n2, const EndCols& e) {
+    for (int p = 0; p < h; ++p) {
+        float(*E)[2][RT_W] = edge[p & 1];
+        *reinterpret_cast<float2*>(&E[w][0][2 * lane]) = make_float2(va[0], vb[0]);
+        *reinterpret_cast<float2*>(&E[w][1][2 * lane]) = make_float2(va[RW - 1], vb[RW - 1]);
+        __syncthreads();
+        // the rows above and below the band (the tile's first and last warps: their own edge rows, stale)
+        const float2 up = w > 0 ? *reinterpret_cast<const float2*>(&E[w - 1][1][2 * lane]) : make_float2(va[0], vb[0]);
+        const float2 dn = w < NW - 1 ? *reinterpret_cast<const float2*>(&E[w + 1][0][2 * lane])
+                                     : make_float2(va[RW - 1], vb[RW - 1]);
+        float ra[RW + 2], rb[RW + 2];
+        filter_row<CX>(up.x, up.y, e, ra[0], rb[0]);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) filter_row<CX>(va[r], vb[r], e, ra[r + 1], rb[r + 1]);
+        filter_row<CX>(dn.x, dn.y, e, ra[RW + 1], rb[RW + 1]);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            float ua = ra[r], ub = rb[r], da = ra[r + 2], db = rb[r + 2];
+            if (CY) {
+                if (yb + r == 0) {
+                    ua = ra[r + 1];
+                    ub = rb[r + 1];
+                }
+                if (yb + r == n2 - 1) {
+                    da = ra[r + 1];
+                    db = rb[r + 1];
+                }
             }
-            nxt[idx] = s;
+            va[r] = filter3(ua, ra[r + 1], da);
+            vb[r] = filter3(ub, rb[r + 1], db);
         }
-        __syncthreads();
-        // outflow ghosts take the new value of their clamped boundary node
-        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
-             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
-            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
-            const int gi = x0 + sx, gj = y0 + sy;
-            int cx = sx, cy = sy;
-            if (g.bc[0] == ES_BC_OUTFLOW) cx += (gi < 0 ? -gi : (gi >= g.n1 ? g.n1 - 1 - gi : 0));
-            if (g.bc[1] == ES_BC_OUTFLOW) cy += (gj < 0 ? -gj : (gj >= g.n2 ? g.n2 - 1 - gj : 0));
-            if (cx != sx || cy != sy) nxt[idx] = nxt[cy * TW + cx];
-        }
-        __syncthreads();
-        T* tmp = cur; cur = nxt; nxt = tmp;
-    }
-    for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
-        const int ix = idx % FT_X, iy = idx / FT_X;
-        const int gi = x0 + h + ix, gj = y0 + h + iy;
-        if (gi < g.n1 && gj < g.n2) out[gj * g.n1 + gi] = cur[(h + iy) * TW + h + ix];
     }
 }
 
-// launchers (the kernel template is instantiated here): 32 x 16 tiles, 256 threads
-template <class T>
-static void launch_omega_filter_t(const GridParams& g, const MonitorParams& mp, const T* t0, const T* t1,
-                                  const T* t2, const DevScalars* d, int passes, T* out, cudaStream_t s) {
-    const dim3 tiles((g.n1 + FT_X - 1) / FT_X, (g.n2 + FT_Y - 1) / FT_Y);
-    k_omega_filter_t<T><<<tiles, 256, 0, s>>>(g, mp, t0, t1, t2, d, passes, out);
+template <int NW, int RW>
+__global__ void __launch_bounds__(NW * 32) k_omega_filter_r(GridParams g, MonitorParams mp,
+                                                            const float* __restrict__ t0,
+                                                            const float* __restrict__ t1,
+                                                            const float* __restrict__ t2, const DevScalars* d,
+                                                            int h, float* __restrict__ out) {
+    __shared__ __align__(16) float edge[2][NW][2][RT_W];         // [pass parity][warp][first / last row][column]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int OX = RT_W - 2 * h, OY = NW * RW - 2 * h;
+    const int x0 = blockIdx.x * OX - h, y0 = blockIdx.y * OY - h;
+    const int xa = x0 + 2 * lane, yb = y0 + w * RW;
+    float c0, c1, c2;
+    mon_coeffs(mp, d, c0, c1, c2);
+    const int sa = state_index(xa, g.n1, g.bc[0]), sb = state_index(xa + 1, g.n1, g.bc[0]);
+    float va[RW], vb[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const size_t row = size_t(state_index(yb + r, g.n2, g.bc[1])) * g.n1;
+        va[r] = sqrtf(1.0f + c0 * t0[row + sa] + c1 * t1[row + sa] + c2 * t2[row + sa]);
+        vb[r] = sqrtf(1.0f + c0 * t0[row + sb] + c1 * t1[row + sb] + c2 * t2[row + sb]);
+    }
+    const EndCols e = {xa == 0, xa == g.n1 - 1, xa + 1 == 0, xa + 1 == g.n1 - 1};
+    // only tiles that reach an outflow end take the clamped reads
+    const bool cx = g.bc[0] == ES_BC_OUTFLOW && (x0 <= 0 || x0 + RT_W >= g.n1);
+    const bool cy = g.bc[1] == ES_BC_OUTFLOW && (y0 <= 0 || y0 + NW * RW >= g.n2);
+    if (cx) {
+        if (cy) filter_passes<NW, RW, true, true>(va, vb, edge, h, w, lane, yb, g.n2, e);
+        else filter_passes<NW, RW, true, false>(va, vb, edge, h, w, lane, yb, g.n2, e);
+    } else {
+        if (cy) filter_passes<NW, RW, false, true>(va, vb, edge, h, w, lane, yb, g.n2, e);
+        else filter_passes<NW, RW, false, false>(va, vb, edge, h, w, lane, yb, g.n2, e);
+    }
+    const bool ina = 2 * lane >= h && 2 * lane < h + OX && xa < g.n1;
+    const bool inb = 2 * lane + 1 >= h && 2 * lane + 1 < h + OX && xa + 1 < g.n1;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int tr = w * RW + r;
+        if (tr < h || tr >= h + OY || yb + r >= g.n2) continue;
+        float* o = out + size_t(yb + r) * g.n1;
+        if (ina) o[xa] = va[r];
+        if (inb) o[xa + 1] = vb[r];
+    }
 }
+
+// tiles NW x 4 rows tall: 64 rows (NW = 16) where the mesh gives at least four waves of them with per_sm
+// resident CTAs per SM, else 32 (more CTAs at a larger share of halo)
+constexpr int RT_RW = 4;
+
+template <int NW>
+static dim3 rt_grid(const GridParams& g, int h) {
+    return dim3((g.n1 + RT_W - 2 * h - 1) / (RT_W - 2 * h), (g.n2 + NW * RT_RW - 2 * h - 1) / (NW * RT_RW - 2 * h));
+}
+
+static bool rt_tall(const GridParams& g, int h, int per_sm) {
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || n < 1)
+            n = 1;
+        nsm = n;
+    }
+    const dim3 t = rt_grid<16>(g, h);
+    return size_t(t.x) * t.y >= size_t(4) * per_sm * nsm;
+}
+
 void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const float* t0, const float* t1,
                          const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s) {
-    launch_omega_filter_t(g, mp, t0, t1, t2, d, passes, out, s);
+    if (rt_tall(g, passes, 3))
+        k_omega_filter_r<16, RT_RW><<<rt_grid<16>(g, passes), 16 * 32, 0, s>>>(g, mp, t0, t1, t2, d, passes, out);
+    else
+        k_omega_filter_r<8, RT_RW><<<rt_grid<8>(g, passes), 8 * 32, 0, s>>>(g, mp, t0, t1, t2, d, passes, out);
 }
 
-__global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const float* omega, const float* d0,
-                                                        float* dout, int sweeps, DevScalars* dv, int limit) {
-    __shared__ float Wm[FT_W * FT_H];
-    __shared__ float X[2][2][FT_W * FT_H];          // [buffer][component]
-    const int h = sweeps, TW = FT_X + 2 * h, TH = FT_Y + 2 * h;
-    const int2 sq = make_int2(int(blockDim.x) % TW, int(blockDim.x) / TW);
-    const int x0 = blockIdx.x * FT_X - h, y0 = blockIdx.y * FT_Y - h;
-    for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
-         idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
-        const int gi = x0 + sx, gj = y0 + sy;
-        Wm[idx] = field_at_f(g, omega, gi, gj);
-        X[0][0][idx] = disp_at(g, d0, gi, gj, 0);
-        X[0][1][idx] = disp_at(g, d0, gi, gj, 1);
-    }
-    __syncthreads();
-    const float ih2x = float(g.inv_dxi[0] * g.inv_dxi[0]), ih2y = float(g.inv_dxi[1] * g.inv_dxi[1]);
-    const float dxx = float(1.0 / g.inv_dxi[0]), dxy = float(1.0 / g.inv_dxi[1]);
-    int b = 0;
-    for (int p = 1; p <= h; ++p) {
-        const float* c0 = X[b][0];
-        const float* c1 = X[b][1];
-        float* n0 = X[b ^ 1][0];
-        float* n1 = X[b ^ 1][1];
-        for (int idx = threadIdx.x, sx = idx % TW, sy = idx / TW; idx < TW * TH;
-             idx += blockDim.x, next_cell(sx, sy, sq, TW)) {
-            if (sx < p || sx >= TW - p || sy < p || sy >= TH - p) continue;
-            const int gi = x0 + sx, gj = y0 + sy;
-            const bool outside = (g.bc[0] == ES_BC_OUTFLOW && (gi < 0 || gi >= g.n1)) ||
-                                 (g.bc[1] == ES_BC_OUTFLOW && (gj < 0 || gj >= g.n2));
-            if (outside || fixed_node_f(g, gi, gj)) {
-                n0[idx] = c0[idx];
-                n1[idx] = c1[idx];
-                continue;
-            }
-            const float w0 = Wm[idx];
-            float den = 0.0f, num0 = 0.0f, num1 = 0.0f;
-            {   // direction 1
-                const float wp = 0.5f * (w0 + Wm[idx + 1]) * ih2x;
-                const float wm = 0.5f * (w0 + Wm[idx - 1]) * ih2x;
-                den += wp + wm;
-                num0 += wp * (c0[idx + 1] + dxx) + wm * (c0[idx - 1] - dxx);
-                num1 += wp * (c1[idx + 1] + 0.0f) + wm * (c1[idx - 1] - 0.0f);
-            }
-            {   // direction 2
-                const float wp = 0.5f * (w0 + Wm[idx + TW]) * ih2y;
-                const float wm = 0.5f * (w0 + Wm[idx - TW]) * ih2y;
-                den += wp + wm;
-                num0 += wp * (c0[idx + TW] + 0.0f) + wm * (c0[idx - TW] - 0.0f);
-                num1 += wp * (c1[idx + TW] + dxy) + wm * (c1[idx - TW] - dxy);
-            }
-            const float idn = 1.0f / den;
-            n0[idx] = num0 * idn;
-            n1[idx] = num1 * idn;
-        }
-        __syncthreads();
-        b ^= 1;
-    }
+// a node's sweep weights (constant over the sweeps), formed as k_jacobi_f forms them: the east face weight
+// 0.5 (w_0 + w_E) / dxi_1^2, the north one likewise with dxi_2, and the reciprocal of the four faces' sum.  A
+// node's west (south) face weight is its west (south) neighbour's east (north) one, the same float (the sum
+// w_0 + w_W is commutative), so each face is formed once.
+struct NodeW {
+    float px, py, idn;
+};
+
+__device__ __forceinline__ NodeW node_weights(float w0, float we, float ww, float wn, float ws, float ih2x,
+                                              float ih2y, float& mx, float& my) {
+    NodeW n;
+    float den = 0.0f;
+    n.px = 0.5f * (w0 + we) * ih2x;
+    mx = 0.5f * (w0 + ww) * ih2x;
+    den += n.px + mx;
+    n.py = 0.5f * (w0 + wn) * ih2y;
+    my = 0.5f * (w0 + ws) * ih2y;
+    den += n.py + my;
+    n.idn = 1.0f / den;
+    return n;
+}
+
+// one node's Jacobi update from its face weights (px, mx: east, west; py, my: north, south) and its
+// neighbours' displacements (e, w, n, s; 0 and 1 the components), in k_jacobi_f's order
+__device__ __forceinline__ void node_sweep(float px, float mx, float py, float my, float idn, float e0, float w0,
+                                           float n0, float s0, float e1, float w1, float n1, float s1, float dxx,
+                                           float dxy, float& o0, float& o1) {
+    float num0 = 0.0f, num1 = 0.0f;
+    num0 += px * (e0 + dxx) + mx * (w0 - dxx);
+    num1 += px * (e1 + 0.0f) + mx * (w1 - 0.0f);
+    num0 += py * (n0 + 0.0f) + my * (s0 - 0.0f);
+    num1 += py * (n1 + dxy) + my * (s1 - dxy);
+    o0 = num0 * idn;
+    o1 = num1 * idn;
+}
+
+template <int NW, int RW>
+__global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float* __restrict__ omega,
+                                                      const float* __restrict__ d0, float* __restrict__ dout, int h,
+                                                      DevScalars* dv, int limit) {
+    __shared__ __align__(16) float edge[2][NW][2][2][RT_W];      // [sweep parity][warp][first / last row][comp][col]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int OX = RT_W - 2 * h, OY = NW * RW - 2 * h;
+    const int x0 = blockIdx.x * OX - h, y0 = blockIdx.y * OY - h;
+    const int xa = x0 + 2 * lane, yb = y0 + w * RW;
+    const float ih2x = g.finv2[0], ih2y = g.finv2[1], dxx = g.fdx[0], dxy = g.fdx[1];
+    // periodic halos hold the wrapped nodes (the displacement is periodic); an outflow ghost holds its clamped
+    // node, which no moving node reads (the end nodes stay where they are)
+    const int sa = state_index(xa, g.n1, g.bc[0]), sb = state_index(xa + 1, g.n1, g.bc[0]);
     const size_t N = size_t(g.n1) * g.n2;
+    // the sweep weights from omega on the band and the rows above and below it
+    NodeW qa[RW], qb[RW];
+    float mxa[RW];                  // west face of column 2L (column 2L+1's west face is column 2L's east one)
+    float mya0, myb0;               // south faces of the band's first row (the others: the row below's north)
+    {
+        float Wa[RW + 2], Wb[RW + 2];
+#pragma unroll
+        for (int r = 0; r < RW + 2; ++r) {
+            const size_t row = size_t(state_index(yb + r - 1, g.n2, g.bc[1])) * g.n1;
+            Wa[r] = omega[row + sa];
+            Wb[r] = omega[row + sb];
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const float a = Wa[r + 1], b = Wb[r + 1];
+            float mx, mya, myb;
+            qa[r] = node_weights(a, b, from_left(b), Wa[r + 2], Wa[r], ih2x, ih2y, mxa[r], mya);
+            qb[r] = node_weights(b, from_right(a), a, Wb[r + 2], Wb[r], ih2x, ih2y, mx, myb);
+            if (r == 0) {
+                mya0 = mya;
+                myb0 = myb;
+            }
+        }
+    }
+    float a0[RW], b0[RW], a1[RW], b1[RW];                         // displacement components at columns 2L, 2L+1
+    unsigned int moves = 0u;                                      // bit 2r: column 2L of row r, 2r+1: column 2L+1
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int gy = yb + r;
+        const size_t row = size_t(state_index(gy, g.n2, g.bc[1])) * g.n1;
+        a0[r] = d0[row + sa];
+        a1[r] = d0[N + row + sa];
+        b0[r] = d0[row + sb];
+        b1[r] = d0[N + row + sb];
+        const bool out_y = g.bc[1] == ES_BC_OUTFLOW && (gy < 0 || gy >= g.n2);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int gx = xa + c;
+            const bool outside = out_y || (g.bc[0] == ES_BC_OUTFLOW && (gx < 0 || gx >= g.n1));
+            if (!(outside || fixed_node_f(g, gx, gy))) moves |= 1u << (2 * r + c);
+        }
+    }
+    for (int p = 0; p < h; ++p) {
+        float(*E)[2][2][RT_W] = edge[p & 1];
+        *reinterpret_cast<float2*>(&E[w][0][0][2 * lane]) = make_float2(a0[0], b0[0]);
+        *reinterpret_cast<float2*>(&E[w][0][1][2 * lane]) = make_float2(a1[0], b1[0]);
+        *reinterpret_cast<float2*>(&E[w][1][0][2 * lane]) = make_float2(a0[RW - 1], b0[RW - 1]);
+        *reinterpret_cast<float2*>(&E[w][1][1][2 * lane]) = make_float2(a1[RW - 1], b1[RW - 1]);
+        __syncthreads();
+        // rows above and below the band (the tile's first and last warps: their own edge rows, stale)
+        const float2 u0 = w > 0 ? *reinterpret_cast<const float2*>(&E[w - 1][1][0][2 * lane]) : make_float2(a0[0], b0[0]);
+        const float2 u1 = w > 0 ? *reinterpret_cast<const float2*>(&E[w - 1][1][1][2 * lane]) : make_float2(a1[0], b1[0]);
+        const float2 l0 = w < NW - 1 ? *reinterpret_cast<const float2*>(&E[w + 1][0][0][2 * lane])
+                                     : make_float2(a0[RW - 1], b0[RW - 1]);
+        const float2 l1 = w < NW - 1 ? *reinterpret_cast<const float2*>(&E[w + 1][0][1][2 * lane])
+                                     : make_float2(a1[RW - 1], b1[RW - 1]);
+        float sa0 = u0.x, sb0 = u0.y, sa1 = u1.x, sb1 = u1.y;     // the old values of the row below row r
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const float ta0 = r < RW - 1 ? a0[r + 1] : l0.x, tb0 = r < RW - 1 ? b0[r + 1] : l0.y;
+            const float ta1 = r < RW - 1 ? a1[r + 1] : l1.x, tb1 = r < RW - 1 ? b1[r + 1] : l1.y;
+            const float mya = r > 0 ? qa[r - 1].py : mya0, myb = r > 0 ? qb[r - 1].py : myb0;
+            float o0, o1, q0, q1;
+            node_sweep(qa[r].px, mxa[r], qa[r].py, mya, qa[r].idn, b0[r], from_left(b0[r]), ta0, sa0, b1[r],
+                       from_left(b1[r]), ta1, sa1, dxx, dxy, o0, o1);
+            node_sweep(qb[r].px, qa[r].px, qb[r].py, myb, qb[r].idn, from_right(a0[r]), a0[r], tb0, sb0,
+                       from_right(a1[r]), a1[r], tb1, sb1, dxx, dxy, q0, q1);
+            sa0 = a0[r];
+            sb0 = b0[r];
+            sa1 = a1[r];
+            sb1 = b1[r];
+            if ((moves >> (2 * r)) & 1u) {
+                a0[r] = o0;
+                a1[r] = o1;
+            }
+            if ((moves >> (2 * r + 1)) & 1u) {
+                b0[r] = q0;
+                b1[r] = q1;
+            }
+        }
+    }
     float lim = 1.0f;                                        // limit: k_limiter_f's min over this tile's nodes
-    for (int idx = threadIdx.x; idx < FT_X * FT_Y; idx += blockDim.x) {
-        const int ix = idx % FT_X, iy = idx / FT_X;
-        const int gi = x0 + h + ix, gj = y0 + h + iy;
-        if (gi < g.n1 && gj < g.n2) {
-            const int s = (h + iy) * TW + h + ix;
-            const size_t id = size_t(gj) * g.n1 + gi;
-            dout[id] = X[b][0][s];
-            dout[N + id] = X[b][1][s];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int tr = w * RW + r, gy = yb + r;
+        if (tr < h || tr >= h + OY || gy >= g.n2) continue;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int gx = xa + c;
+            if (2 * lane + c < h || 2 * lane + c >= h + OX || gx >= g.n1) continue;
+            const size_t id = size_t(gy) * g.n1 + gx;
+            const float v0 = c ? b0[r] : a0[r], v1 = c ? b1[r] : a1[r];
+            dout[id] = v0;
+            dout[N + id] = v1;
             if (limit) {
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const float d0k = d0[k * N + id];
-                    const float dx = X[b][k][s] - d0k;
+                    const float dx = (k ? v1 : v0) - d0k;
                     const int di = k == 0, dj = k == 1;
                     const float hk = k == 0 ? dxx : dxy;
-                    if (dx < 0.0f) lim = fminf(lim, -(hk + d0k - disp_at(g, d0, gi - di, gj - dj, k)) / (2.0f * dx));
-                    else if (dx > 0.0f) lim = fminf(lim, (hk + disp_at(g, d0, gi + di, gj + dj, k) - d0k) / (2.0f * dx));
+                    if (dx < 0.0f) lim = fminf(lim, -(hk + d0k - disp_at(g, d0, gx - di, gy - dj, k)) / (2.0f * dx));
+                    else if (dx > 0.0f) lim = fminf(lim, (hk + disp_at(g, d0, gx + di, gy + dj, k) - d0k) / (2.0f * dx));
                 }
             }
         }
@@ -696,7 +861,15 @@ __global__ void __launch_bounds__(256) k_jacobi_multi_f(GridParams g, const floa
         lim = block_min_f32(lim);
         if (threadIdx.x == 0) atomic_min_pos(&dv->red[RED_GAMMA], double(lim));
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&dv->sweeps, sweeps);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(&dv->sweeps, h);
+}
+
+void launch_jacobi_tiles(const GridParams& g, const float* omega, const float* d0, float* dout, int sweeps,
+                         DevScalars* dv, int limit, cudaStream_t s) {
+    if (rt_tall(g, sweeps, 1))
+        k_jacobi_r<16, RT_RW><<<rt_grid<16>(g, sweeps), 16 * 32, 0, s>>>(g, omega, d0, dout, sweeps, dv, limit);
+    else
+        k_jacobi_r<8, RT_RW><<<rt_grid<8>(g, sweeps), 8 * 32, 0, s>>>(g, omega, d0, dout, sweeps, dv, limit);
 }
 
 }  // namespace es

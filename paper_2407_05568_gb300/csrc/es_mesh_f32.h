@@ -47,13 +47,14 @@ __global__ void k_filter_f(GridParams g, const float* in, float* out);
 __global__ void k_jacobi_f(GridParams g, const float* omega, const float* d0, float* da, float* db, int k,
                            DevScalars* d, int check, double eps);
 __global__ void k_limiter_f(GridParams g, const float* d0, const float* da, const float* db, DevScalars* d);
-// fused 2D passes (32 x 16 tiles, halo = the pass count <= FT_HMAX = 8)
-// omega and its low-pass filter passes fused per 32 x 16 tile (2D, 1 <= passes <= FT_HMAX = 8)
+// fused 2D passes on register tiles 64 nodes wide (halo = the pass or sweep count, 1 .. 8)
+// omega and its low-pass filter passes in one launch
 void launch_omega_filter(const GridParams& g, const MonitorParams& mp, const float* t0, const float* t1,
                          const float* t2, const DevScalars* d, int passes, float* out, cudaStream_t s);
-// limit: also Delta_gamma of the result over the tile's nodes into RED_GAMMA (k_limiter_f's work)
-__global__ void k_jacobi_multi_f(GridParams g, const float* omega, const float* d0, float* dout, int sweeps,
-                                 DevScalars* dv, int limit);
+// sweeps Jacobi sweeps without a tolerance from d0 into dout in one launch; limit: also Delta_gamma of the
+// result into RED_GAMMA (k_limiter_f's work)
+void launch_jacobi_tiles(const GridParams& g, const float* omega, const float* d0, float* dout, int sweeps,
+                         DevScalars* dv, int limit, cudaStream_t s);
 // cfl > 0: also eq. cfl with the new velocity from k_cfl_f's stored terms into RED_CFL2, and
 // dt = min(dt, cfl / that maximum)
 __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const float* __restrict__ da,

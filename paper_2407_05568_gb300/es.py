@@ -73,6 +73,8 @@ def lib():
         L.es_time_stage.argtypes = [vp, vp, vp, vp, i, d, i, ctypes.POINTER(d)]
         L.es_selftest_division.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp]
         L.es_selftest_division.restype = ctypes.c_int
+        L.es_selftest_mixed_arith.argtypes = [vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp]
+        L.es_selftest_mixed_arith.restype = ctypes.c_int
         L.es_selftest_peaks.argtypes = [ctypes.POINTER(d), ctypes.POINTER(d), vp]
         L.es_selftest_peaks.restype = ctypes.c_int
         L.es_autotune.restype = ctypes.c_int
@@ -417,6 +419,21 @@ def es_selftest_division(a, b, q, r, stream=None):
     """q = a / b and r = 1 / b with the library's FP64 division (float64 device arrays)."""
     _nn_rc(lib().es_selftest_division(_ptr(a, F64), _ptr(b, F64), _ptr(q, F64), _ptr(r, F64), a.numel(),
                                       _stream_handle(stream)), "es_selftest_division")
+
+
+def es_selftest_mixed_arith(x, f, a, b, stream=None):
+    """Device self-test of the mixed form's building blocks (see es_vdw.h): x (float64, n), f (float32, n),
+    a and b (float32, 2n: double-float pairs).  Returns (split, wide, mul, add) as device tensors."""
+    import torch
+    n = x.numel()
+    split = torch.empty(2 * n, dtype=torch.float32, device=x.device)
+    wide = torch.empty(n, dtype=torch.float64, device=x.device)
+    mul = torch.empty(2 * n, dtype=torch.float32, device=x.device)
+    add = torch.empty(2 * n, dtype=torch.float32, device=x.device)
+    _nn_rc(lib().es_selftest_mixed_arith(_ptr(x, F64), _ptr(f, F32), _ptr(a, F32), _ptr(b, F32), n, _ptr(split, F32),
+                                         _ptr(wide, F64), _ptr(mul, F32), _ptr(add, F32), _stream_handle(stream)),
+           "es_selftest_mixed_arith")
+    return split, wide, mul, add
 
 
 def es_selftest_peaks(stream=None):

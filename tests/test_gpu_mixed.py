@@ -229,3 +229,56 @@ def test_mixed_riemann_2d_every_step():
         assert err < 1e-5, (k, err)
     assert es.es_check(ctx) == 0, es.es_last_error(ctx)
     assert worst > 0.0
+
+
+def test_mixed_arith_building_blocks():
+    """The bit-level float <-> double moves of the mixed form's elementwise kernels and its double-float
+    product and sum, against exact arithmetic (fractions): the split of a double is within 2^-46 of it
+    (relative) with hi its truncation; widening is exact for every float class (zeros, subnormals,
+    infinities, quiet NaNs with payload); the double-float product is within 2^-44 of the exact product of
+    its inputs, the sum within 2^-44 of |a| + |b| (the sum's bound allows cancellation)."""
+    from fractions import Fraction
+
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    rng = np.random.default_rng(7)
+    n = 3000
+    x = rng.standard_normal(n) * 10.0 ** rng.uniform(-30, 30, n)
+    x[:12] = [0.0, -0.0, 1.0, -1.5, 2.0 ** -103, -(2.0 ** -103), 2.0 ** 127 * 1.999, 1e-200, 1e-310, 3.0, 0.1, 1e3]
+    f = (rng.standard_normal(n) * 10.0 ** rng.uniform(-30, 30, n)).astype(np.float32)
+    special = np.array([0x00000001, 0x80000003, 0x007fffff, 0x00400000, 0x80000000, 0x00000000, 0x7f800000,
+                        0xff800000, 0x7fc00000, 0x7fc01234, 0x3f800000, 0x00012345], dtype=np.uint32)
+    f[:special.size] = special.view(np.float32)
+    hi = rng.uniform(-2, 2, (2, n)) * 10.0 ** rng.uniform(-3, 3, (2, n))
+    pairs = []
+    for h in hi:
+        h32 = h.astype(np.float32)
+        lo32 = (h32.astype(np.float64) * rng.uniform(-1, 1, n) * 2.0 ** -24).astype(np.float32)
+        pairs.append(np.stack([h32, lo32], axis=1).reshape(-1))
+    dev = lambda v: torch.tensor(v, device="cuda")
+    split, wide, mul, add = es.es_selftest_mixed_arith(dev(x), dev(f), dev(pairs[0]), dev(pairs[1]))
+    torch.cuda.synchronize()
+    split, wide, mul, add = (t.cpu().numpy() for t in (split, wide, mul, add))
+    sh, sl = split[0::2].astype(np.float64), split[1::2].astype(np.float64)
+    ax = np.abs(x)
+    inr = (ax >= 2.0 ** -103) & (ax < 2.0 ** 128)
+    assert inr.sum() > n // 2
+    assert np.all(np.abs(x[inr] - (sh[inr] + sl[inr])) <= 2.0 ** -46 * ax[inr])
+    assert np.all(np.abs(sh[inr]) <= ax[inr]) and np.all(np.sign(sh[inr]) == np.sign(x[inr]))
+    assert np.all(ax[inr] - np.abs(sh[inr]) < np.spacing(np.abs(split[0::2][inr])).astype(np.float64))
+    assert sh[0] == 0.0 and sl[0] == 0.0 and sh[1] == 0.0
+    ref = f.astype(np.float64)
+    nan = np.isnan(ref)
+    assert np.array_equal(wide[~nan].view(np.uint64), ref[~nan].view(np.uint64))
+    assert np.array_equal(wide[nan].view(np.uint64), ref[nan].view(np.uint64))   # quiet NaNs: payload kept
+    worst_mul = worst_add = 0.0
+    for i in range(n):
+        A = Fraction(float(pairs[0][2 * i])) + Fraction(float(pairs[0][2 * i + 1]))
+        B = Fraction(float(pairs[1][2 * i])) + Fraction(float(pairs[1][2 * i + 1]))
+        P = Fraction(float(mul[2 * i])) + Fraction(float(mul[2 * i + 1]))
+        S = Fraction(float(add[2 * i])) + Fraction(float(add[2 * i + 1]))
+        worst_mul = max(worst_mul, float(abs(P - A * B) / abs(A * B)))
+        worst_add = max(worst_add, float(abs(S - (A + B)) / (abs(A) + abs(B))))
+    assert worst_mul <= 2.0 ** -44, worst_mul
+    assert worst_add <= 2.0 ** -44, worst_add
