@@ -51,6 +51,7 @@ struct DevScalars {
     DevStatus status;
     double last_change[2];                     // first-sweep changes from x_n and from the warm start
     long long sweeps_total, solves, warm_kept; // cumulative mesh-solve counters
+    float mon_c[3];      // mixed form: omega's coefficients alpha_k / max_k as floats (k_mon_f's last block)
 };
 
 // the per-step reset of the reductions and counters (k_reset), and the time step from the CFL

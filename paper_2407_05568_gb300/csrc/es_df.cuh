@@ -87,19 +87,20 @@ inline GasDF gas_df(double a, double b, double R, double cv) {
 // its differences are formed from these pairs too (df_diff, df_second_diff) before rounding to float.
 __device__ __forceinline__ void rho_G_df2(df m0, const df* mom, int dim, df E, df J, const GasDF& G, df* rho_out,
                                           df* G_out) {
-    const df iJ = df_recip(J);
-    const df rho = df_mul(m0, iJ);
-    const df irho = df_recip(rho);
+    // rho = (J rho) / J; the velocity and the specific energy are quotients of conserved variables, in which J
+    // cancels: v = (J rho v) / (J rho), E / rho = (J E) / (J rho)
+    const df rho = df_mul(m0, df_recip(J));
+    const df im0 = df_recip(m0);
     df ke = {0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {                  // fixed bound: mom[] stays in registers
         if (k < dim) {
-            const df v = df_mul(df_mul(mom[k], iJ), irho);
+            const df v = df_mul(mom[k], im0);
             ke = df_add(ke, df_mul(v, v));
         }
     }
     const df a = {G.a.hi, G.a.lo};
-    const df e = df_add(df_mul(df_mul(E, iJ), irho), df_mul_f(df_neg(ke), 0.5f));
+    const df e = df_add(df_mul(E, im0), df_mul_f(df_neg(ke), 0.5f));
     const df T = df_mul(df_add(e, df_mul(rho, a)), {G.icv.hi, G.icv.lo});
     const df om = df_add_f(df_neg(df_mul(rho, {G.b.hi, G.b.lo})), 1.0f);
     const df iom = df_recip(om);

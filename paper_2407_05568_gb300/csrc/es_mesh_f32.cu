@@ -49,24 +49,15 @@ __device__ __forceinline__ float block_min_f32(float v) {
     return v;
 }
 
-// The per-launch constants formed from device scalars are formed by lane 0 of each warp and broadcast: FP64
-// divisions and conversions issue at 1/64 of the FP32 rate on this GPU, once per warp instead of per thread.
-// The whole warp must call these.
-// omega's coefficients alpha_k / max_k of the three monitor terms (0 where a maximum is 0)
-__device__ __forceinline__ void mon_coeffs(const MonitorParams& mp, const DevScalars* d, float& c0, float& c1,
-                                           float& c2) {
-    float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f;
-    if ((threadIdx.x & 31) == 0) {
-        const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
-        const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
-        const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
-        v0 = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
-        v1 = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
-        v2 = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
-    }
-    c0 = __shfl_sync(0xffffffffu, v0, 0);
-    c1 = __shfl_sync(0xffffffffu, v1, 0);
-    c2 = __shfl_sync(0xffffffffu, v2, 0);
+// omega's coefficients alpha_k / max_k of the three monitor terms (0 where a maximum is 0), as floats: k_mon_f's
+// last block forms them once (an FP64 division occupies the FP64 pipe, 1/64 of the FP32 rate on this GPU, for a
+// whole warp whatever its active lanes; formed per warp they bounded the filter kernel)
+__device__ __forceinline__ void set_mon_coeffs(DevScalars* d, const MonitorParams& mp) {
+    const double M[3] = {__longlong_as_double((long long)atomicAdd(&d->red[RED_MON0], 0ULL)),
+                         __longlong_as_double((long long)atomicAdd(&d->red[RED_MON1], 0ULL)),
+                         __longlong_as_double((long long)atomicAdd(&d->red[RED_MON2], 0ULL))};
+    const double w[3] = {mp.w0, mp.w1, mp.w2};
+    for (int k = 0; k < 3; ++k) d->mon_c[k] = M[k] > 0.0 ? float(w[k] / M[k]) : 0.0f;
 }
 
 // a displacement ghost along one direction as at most two mesh nodes: periodic wrap (d is periodic),
@@ -277,7 +268,7 @@ __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const fl
 // tile's nodes and of a one-node halo (ghost rule of the state) are computed once each in double-float and kept
 // in shared memory, then every node forms its differences from them.  With do_dt, thread 0 also sets the step's
 // dt from the CFL maximum (k_dt's work: the CFL kernel has finished when this one starts).
-__global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
+__global__ void __launch_bounds__(MON_TX * MON_TY, 4) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
                                                            MonitorParams mp, float* t0, float* t1, float* t2,
                                                            DevScalars* d, int do_dt, double cfl, double dt_fixed,
                                                            const float* disp, float* cfl_terms) {
@@ -350,21 +341,19 @@ __global__ void __launch_bounds__(MON_TX * MON_TY) k_mon_f(GridParams g, GasF32 
     m0 = block_max_f32(m0);
     m1 = block_max_f32(m1);
     m2 = block_max_f32(m2);
+    if (do_dt == 2) mc = block_max_f32(mc);                 // uniform
     if (threadIdx.x == 0) {
         atomic_max_pos(&d->red[RED_MON0], double(m0));
         atomic_max_pos(&d->red[RED_MON1], double(m1));
         atomic_max_pos(&d->red[RED_MON2], double(m2));
-    }
-    if (do_dt == 2) {                                        // uniform: the step's dt once every node is in
-        mc = block_max_f32(mc);
-        if (threadIdx.x == 0) {
-            atomic_max_pos(&d->red[RED_CFL], double(mc));
-            __threadfence();
-            const unsigned int ticket = atomicAdd(&d->done, 1u);
-            if (ticket == gridDim.x - 1) {
+        if (do_dt == 2) atomic_max_pos(&d->red[RED_CFL], double(mc));
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&d->done, 1u);
+        if (ticket == gridDim.x - 1) {                      // every block's maxima are in
+            set_mon_coeffs(d, mp);
+            if (do_dt == 2)                                 // the step's dt once every node is in
                 set_dt_from_max(d, __longlong_as_double((long long)atomicAdd(&d->red[RED_CFL], 0ULL)), cfl, dt_fixed);
-                d->done = 0u;
-            }
+            d->done = 0u;
         }
     }
 }
@@ -378,8 +367,18 @@ int mon_f_blocks(const GridParams& g) {
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega) {
     const int N = g.n1 * g.n2;
-    float c0, c1, c2;
-    mon_coeffs(mp, d, c0, c1, c2);
+    // the coefficients from the maxima once per block (the 3D form's terms kernel leaves no float copies)
+    __shared__ float cs[3];
+    if (threadIdx.x == 0) {
+        const double M0 = __longlong_as_double((long long)d->red[RED_MON0]);
+        const double M1 = __longlong_as_double((long long)d->red[RED_MON1]);
+        const double M2 = __longlong_as_double((long long)d->red[RED_MON2]);
+        cs[0] = M0 > 0.0 ? float(mp.w0 / M0) : 0.0f;
+        cs[1] = M1 > 0.0 ? float(mp.w1 / M1) : 0.0f;
+        cs[2] = M2 > 0.0 ? float(mp.w2 / M2) : 0.0f;
+    }
+    __syncthreads();
+    const float c0 = cs[0], c1 = cs[1], c2 = cs[2];
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x)
         omega[id] = sqrtf(1.0f + c0 * t0[id] + c1 * t1[id] + c2 * t2[id]);
 }
@@ -499,13 +498,15 @@ __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const f
                              double* __restrict__ xdot, const float* __restrict__ terms, double cfl) {
     const int N = g.n1 * g.n2;
     const float* xit = jacobi_result_f(d, d0, da, db);
-    float fl = 0.0f;                    // Delta_gamma / dt (lane 0 of each warp, broadcast)
-    if ((threadIdx.x & 31) == 0) {
+    __shared__ float fs;                // Delta_gamma / dt, formed once per block (FP64 division)
+    if (threadIdx.x == 0) {
         const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
         const double dt = d->dt;
-        fl = dt > 0.0 ? float(gam / dt) : 0.0f;
+        fs = dt > 0.0 ? float(gam / dt) : 0.0f;
     }
-    const float f = __shfl_sync(0xffffffffu, fl, 0);
+    __syncthreads();
+    const float f = fs;
+    const bool moving_cfl = cfl > 0.0;  // compared once, not per node (an FP64 comparison)
     float m = 0.0f;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const float v1 = f * (xit[id] - d0[id]);
@@ -517,7 +518,7 @@ __global__ void k_velocity_f(GridParams g, const float* __restrict__ d0, const f
             fxd[N + id] = v2;
             xdot[N + id] = bits::widen(v2);
         }
-        if (cfl > 0.0) m = fmaxf(m, cfl_moving_term(terms, terms + 4 * size_t(N), size_t(N), size_t(id), g.dim, v1, v2));
+        if (moving_cfl) m = fmaxf(m, cfl_moving_term(terms, terms + 4 * size_t(N), size_t(N), size_t(id), g.dim, v1, v2));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d->gamma = __longlong_as_double((long long)d->red[RED_GAMMA]);
@@ -553,7 +554,7 @@ namespace es {
 // At an outflow end the filter reads the end node in place of its missing neighbour (the unfused kernels'
 // clamped index), and the sweeps leave the end nodes where they are, so neither reads beyond the mesh.  The
 // arithmetic per node is that of k_mon_omega_f, k_filter_f and k_jacobi_f, in the same order.
-constexpr int RT_W = 64, RT_HMAX = 8;
+constexpr int RT_W = 64;           // halos up to 8 nodes (the callers pass 1 .. 8 passes or sweeps)
 
 // the left neighbour of column 2L (lane L-1's column 2L+1) and the right neighbour of column 2L+1 (lane
 // L+1's column 2L); lanes 0 and 31 get their own value back: the tile's edge columns, never output
@@ -637,8 +638,7 @@ __global__ void __launch_bounds__(NW * 32) k_omega_filter_r(GridParams g, Monito
     const int OX = RT_W - 2 * h, OY = NW * RW - 2 * h;
     const int x0 = blockIdx.x * OX - h, y0 = blockIdx.y * OY - h;
     const int xa = x0 + 2 * lane, yb = y0 + w * RW;
-    float c0, c1, c2;
-    mon_coeffs(mp, d, c0, c1, c2);
+    const float c0 = d->mon_c[0], c1 = d->mon_c[1], c2 = d->mon_c[2];
     const int sa = state_index(xa, g.n1, g.bc[0]), sb = state_index(xa + 1, g.n1, g.bc[0]);
     float va[RW], vb[RW];
 #pragma unroll
@@ -723,17 +723,26 @@ __device__ __forceinline__ NodeW node_weights(float w0, float we, float ww, floa
 }
 
 // one node's Jacobi update from its face weights (px, mx: east, west; py, my: north, south) and its
-// neighbours' displacements (e, w, n, s; 0 and 1 the components), in k_jacobi_f's order
+// neighbours' displacements (e, w, n, s; 0 and 1 the components), in k_jacobi_f's order (k_jacobi_f also adds
+// +-0 to the neighbours' components across the other direction, which changes no value)
 __device__ __forceinline__ void node_sweep(float px, float mx, float py, float my, float idn, float e0, float w0,
                                            float n0, float s0, float e1, float w1, float n1, float s1, float dxx,
                                            float dxy, float& o0, float& o1) {
-    float num0 = 0.0f, num1 = 0.0f;
-    num0 += px * (e0 + dxx) + mx * (w0 - dxx);
-    num1 += px * (e1 + 0.0f) + mx * (w1 - 0.0f);
-    num0 += py * (n0 + 0.0f) + my * (s0 - 0.0f);
+    float num0 = px * (e0 + dxx) + mx * (w0 - dxx);
+    float num1 = px * e1 + mx * w1;
+    num0 += py * n0 + my * s0;
     num1 += py * (n1 + dxy) + my * (s1 - dxy);
     o0 = num0 * idn;
     o1 = num1 * idn;
+}
+
+// Delta_gamma's bound at one node and direction (k_limiter_f's rule): d0 the node's starting displacement,
+// v its result, dm and dp the starting displacements of its neighbours before and after it, h the spacing
+__device__ __forceinline__ float limit_term(float lim, float v, float d0, float dm, float dp, float h) {
+    const float dx = v - d0;
+    if (dx < 0.0f) lim = fminf(lim, -(h + d0 - dm) / (2.0f * dx));
+    else if (dx > 0.0f) lim = fminf(lim, (h + dp - d0) / (2.0f * dx));
+    return lim;
 }
 
 template <int NW, int RW>
@@ -741,6 +750,7 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float*
                                                       const float* __restrict__ d0, float* __restrict__ dout, int h,
                                                       DevScalars* dv, int limit) {
     __shared__ __align__(16) float edge[2][NW][2][2][RT_W];      // [sweep parity][warp][first / last row][comp][col]
+    __shared__ __align__(16) float start1[NW][2][RT_W];          // the starting xi_2 component of those rows
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int OX = RT_W - 2 * h, OY = NW * RW - 2 * h;
     const int x0 = blockIdx.x * OX - h, y0 = blockIdx.y * OY - h;
@@ -775,15 +785,16 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float*
         }
     }
     float a0[RW], b0[RW], a1[RW], b1[RW];                         // displacement components at columns 2L, 2L+1
+    float sa0[RW], sb0[RW], sa1[RW], sb1[RW];                     // their starting values (the limiter's)
     unsigned int moves = 0u;                                      // bit 2r: column 2L of row r, 2r+1: column 2L+1
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
         const int gy = yb + r;
         const size_t row = size_t(state_index(gy, g.n2, g.bc[1])) * g.n1;
-        a0[r] = d0[row + sa];
-        a1[r] = d0[N + row + sa];
-        b0[r] = d0[row + sb];
-        b1[r] = d0[N + row + sb];
+        a0[r] = sa0[r] = d0[row + sa];
+        a1[r] = sa1[r] = d0[N + row + sa];
+        b0[r] = sb0[r] = d0[row + sb];
+        b1[r] = sb1[r] = d0[N + row + sb];
         const bool out_y = g.bc[1] == ES_BC_OUTFLOW && (gy < 0 || gy >= g.n2);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -791,6 +802,10 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float*
             const bool outside = out_y || (g.bc[0] == ES_BC_OUTFLOW && (gx < 0 || gx >= g.n1));
             if (!(outside || fixed_node_f(g, gx, gy))) moves |= 1u << (2 * r + c);
         }
+    }
+    if (limit) {
+        *reinterpret_cast<float2*>(&start1[w][0][2 * lane]) = make_float2(sa1[0], sb1[0]);
+        *reinterpret_cast<float2*>(&start1[w][1][2 * lane]) = make_float2(sa1[RW - 1], sb1[RW - 1]);
     }
     for (int p = 0; p < h; ++p) {
         float(*E)[2][2][RT_W] = edge[p & 1];
@@ -806,21 +821,21 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float*
                                      : make_float2(a0[RW - 1], b0[RW - 1]);
         const float2 l1 = w < NW - 1 ? *reinterpret_cast<const float2*>(&E[w + 1][0][1][2 * lane])
                                      : make_float2(a1[RW - 1], b1[RW - 1]);
-        float sa0 = u0.x, sb0 = u0.y, sa1 = u1.x, sb1 = u1.y;     // the old values of the row below row r
+        float pa0 = u0.x, pb0 = u0.y, pa1 = u1.x, pb1 = u1.y;     // the old values of the row below row r
 #pragma unroll
         for (int r = 0; r < RW; ++r) {
             const float ta0 = r < RW - 1 ? a0[r + 1] : l0.x, tb0 = r < RW - 1 ? b0[r + 1] : l0.y;
             const float ta1 = r < RW - 1 ? a1[r + 1] : l1.x, tb1 = r < RW - 1 ? b1[r + 1] : l1.y;
             const float mya = r > 0 ? qa[r - 1].py : mya0, myb = r > 0 ? qb[r - 1].py : myb0;
             float o0, o1, q0, q1;
-            node_sweep(qa[r].px, mxa[r], qa[r].py, mya, qa[r].idn, b0[r], from_left(b0[r]), ta0, sa0, b1[r],
-                       from_left(b1[r]), ta1, sa1, dxx, dxy, o0, o1);
-            node_sweep(qb[r].px, qa[r].px, qb[r].py, myb, qb[r].idn, from_right(a0[r]), a0[r], tb0, sb0,
-                       from_right(a1[r]), a1[r], tb1, sb1, dxx, dxy, q0, q1);
-            sa0 = a0[r];
-            sb0 = b0[r];
-            sa1 = a1[r];
-            sb1 = b1[r];
+            node_sweep(qa[r].px, mxa[r], qa[r].py, mya, qa[r].idn, b0[r], from_left(b0[r]), ta0, pa0, b1[r],
+                       from_left(b1[r]), ta1, pa1, dxx, dxy, o0, o1);
+            node_sweep(qb[r].px, qa[r].px, qb[r].py, myb, qb[r].idn, from_right(a0[r]), a0[r], tb0, pb0,
+                       from_right(a1[r]), a1[r], tb1, pb1, dxx, dxy, q0, q1);
+            pa0 = a0[r];
+            pb0 = b0[r];
+            pa1 = a1[r];
+            pb1 = b1[r];
             if ((moves >> (2 * r)) & 1u) {
                 a0[r] = o0;
                 a1[r] = o1;
@@ -831,29 +846,49 @@ __global__ void __launch_bounds__(NW * 32) k_jacobi_r(GridParams g, const float*
             }
         }
     }
+    // output, and Delta_gamma from the starting values in registers: the xi_1 neighbours by shuffle, the xi_2
+    // ones from the band or the neighbouring bands' edge rows (the tile's output nodes are at least one node
+    // inside the tile, so every neighbour they read is a tile node; at an outflow end the end nodes do not move
+    // and read none)
+    if (limit) __syncthreads();
     float lim = 1.0f;                                        // limit: k_limiter_f's min over this tile's nodes
+    const bool ina = 2 * lane >= h && 2 * lane < h + OX && xa < g.n1;
+    const bool inb = 2 * lane + 1 >= h && 2 * lane + 1 < h + OX && xa + 1 < g.n1;
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
+        const float wa = from_left(sb0[r]), eb = from_right(sa0[r]);     // every lane shuffles
         const int tr = w * RW + r, gy = yb + r;
         if (tr < h || tr >= h + OY || gy >= g.n2) continue;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int gx = xa + c;
-            if (2 * lane + c < h || 2 * lane + c >= h + OX || gx >= g.n1) continue;
-            const size_t id = size_t(gy) * g.n1 + gx;
-            const float v0 = c ? b0[r] : a0[r], v1 = c ? b1[r] : a1[r];
-            dout[id] = v0;
-            dout[N + id] = v1;
+        const size_t row = size_t(gy) * g.n1;
+        float sa1m, sb1m, sa1p, sb1p;                        // xi_2 neighbours' starting component 1
+        if (r > 0) {
+            sa1m = sa1[r - 1];
+            sb1m = sb1[r - 1];
+        } else {
+            sa1m = start1[w - 1][1][2 * lane];
+            sb1m = start1[w - 1][1][2 * lane + 1];
+        }
+        if (r < RW - 1) {
+            sa1p = sa1[r + 1];
+            sb1p = sb1[r + 1];
+        } else {
+            sa1p = start1[w + 1][0][2 * lane];
+            sb1p = start1[w + 1][0][2 * lane + 1];
+        }
+        if (ina) {
+            dout[row + xa] = a0[r];
+            dout[N + row + xa] = a1[r];
             if (limit) {
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const float d0k = d0[k * N + id];
-                    const float dx = (k ? v1 : v0) - d0k;
-                    const int di = k == 0, dj = k == 1;
-                    const float hk = k == 0 ? dxx : dxy;
-                    if (dx < 0.0f) lim = fminf(lim, -(hk + d0k - disp_at(g, d0, gx - di, gy - dj, k)) / (2.0f * dx));
-                    else if (dx > 0.0f) lim = fminf(lim, (hk + disp_at(g, d0, gx + di, gy + dj, k) - d0k) / (2.0f * dx));
-                }
+                lim = limit_term(lim, a0[r], sa0[r], wa, sb0[r], dxx);
+                lim = limit_term(lim, a1[r], sa1[r], sa1m, sa1p, dxy);
+            }
+        }
+        if (inb) {
+            dout[row + xa + 1] = b0[r];
+            dout[N + row + xa + 1] = b1[r];
+            if (limit) {
+                lim = limit_term(lim, b0[r], sb0[r], sa0[r], eb, dxx);
+                lim = limit_term(lim, b1[r], sb1[r], sb1m, sb1p, dxy);
             }
         }
     }
