@@ -934,8 +934,13 @@ static int enqueue_metrics(Ctx3* d, const double* xn, const double* xdot, double
     return 5;
 }
 
-int d3_stage(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err) {
+int d3_stage(Ctx3* d, const Stage3& a0, DevStatus* st, cudaStream_t s, cudaError_t* err) {
     int n = 0;
+    Stage3 a = a0;
+    if (d->mixed && a.xdot && !a.xd_ready) {       // the mixed kernels read xdot on the extended mesh as floats
+        n += d3f_form_xd(d, a.xdot, s);
+        a.xd_ready = 1;
+    }
     if (!a.reuse) {
         n += enqueue_metrics(d, a.xn, a.xdot, a.cst, a.dt_dev, a.dt_host, s, a.xe_incr ? &a : nullptr);
         if (d->mixed) n += d3f_nodes(d, a.JUs, a.Js, st, s);

@@ -59,8 +59,9 @@ struct Stage3 {
     int mode;                 // 0: RK combination; 1: right-hand sides into (JUo, Jo)
     int reuse;                // the metrics and node fields of (xn, JUs, Js) are in the buffers
     // mixed form, within a step: the metric coordinates (d->XE) hold x^n + xe_cst dt xdot, so the stage's are
-    // formed by adding (cst - xe_cst) dt xdot (xe_incr); form_xd: first form xdot on the extended mesh (d->XD)
-    int xe_incr, form_xd;
+    // formed by adding (cst - xe_cst) dt xdot (xe_incr); xd_ready: d->XD already holds xdot on the extended mesh
+    // (else the stage forms it first: the metrics' increments and the direction kernels read it)
+    int xe_incr, xd_ready;
     double xe_cst;
 };
 
@@ -88,6 +89,8 @@ int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_
 int d3f_cfl(Ctx3* d, const void* J, const double* xdot, int slot, DevScalars* dv, cudaStream_t s);
 int d3f_init_J(Ctx3* d, const double* Jd, void* J, cudaStream_t s);
 int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cudaError_t* err);
+// xdot on the extended mesh as floats into d->XD (the coordinates' ghost rule without the period shift)
+int d3f_form_xd(Ctx3* d, const double* xdot, cudaStream_t s);
 int d3f_mesh(Ctx3* d, const void* JU, const void* J, const double* xn, double* xdot, DevScalars* dv,
              cudaStream_t s, cudaError_t* err, bool xe_current);
 

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include "es_3d.h"
+#include "es_bits.cuh"
 #include "es_3d_grid.cuh"
 #include "es_device.cuh"
 #include "es_internal.h"
@@ -297,7 +298,7 @@ struct Dir3FParams {
     int diss;
     const float* NF;          // float node fields [MF_COUNT][N]
     const float* NK;          // metrics of this direction [3][M] (float, from k3f_metric)
-    const double* xdot;       // nullable
+    const float* XD;          // the mesh velocity on the extended mesh [3][NE] (nullable: mesh at rest)
     float* RH;                // accumulated right-hand sides [6][N] (float)
     int first, last;
     int tma;                  // xi_2 / xi_3: node fields staged by TMA (persistent grid)
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(const __grid_constant__ Dir
     const float dt = float(dtd);
     const int M1 = g.n[0] + (K == 0 ? 6 : 0), M2 = g.n[1] + (K == 1 ? 6 : 0), M3 = g.n[2] + (K == 2 ? 6 : 0);
     const size_t M = size_t(M1) * M2 * M3;
+    const int M1e = g.n[0] + 6, M2e = g.n[1] + 6, M3e = g.n[2] + 6;     // the extended mesh (3 ghosts each way)
     const GasF& G = P.gas;
     const uint32_t stg_bytes = uint32_t(PC::STG_BYTES);
     if (tma) {
@@ -464,23 +466,16 @@ __global__ void __launch_bounds__(NT, MINB) k3_dir_f(const __grid_constant__ Dir
             S[M_NX * NB + bx] = nx;
             S[M_NY * NB + bx] = ny;
             S[M_NZ * NB + bx] = nz;
-            double xt = 0.0;
-            if (P.xdot) {
-                double xd[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const GhostTerms tk = ghost_terms(s, nk, g.bc[K], c != K);
-                    for (int u = 0; u < tk.nterm; ++u) {
-                        int k1 = i1, k2 = i2, k3 = i3;
-                        if (K == 0) k1 = tk.idx[u];
-                        else if (K == 1) k2 = tk.idx[u];
-                        else k3 = tk.idx[u];
-                        xd[c] += tk.w[u] * P.xdot[c * N + idx3(g, k1, k2, k3)];
-                    }
-                }
-                xt = -(xd[0] * nx + xd[1] * ny + xd[2] * nz);
+            float xt = 0.0f;
+            if (P.XD) {     // J xi_{k,t} = -xdot . n_k, xdot from the extended mesh (its ghosts: the coordinates' rule)
+                const size_t NE = size_t(M1e) * M2e * M3e;
+                size_t e;
+                if (K == 0) e = (size_t(b + 3) * M2e + (a + 3)) * M1e + se;
+                else if (K == 1) e = (size_t(b + 3) * M2e + se) * M1e + (a + 3);
+                else e = (size_t(se) * M2e + (b + 3)) * M1e + (a + 3);
+                xt = -(P.XD[e] * nx + P.XD[NE + e] * ny + P.XD[2 * NE + e] * nz);
             }
-            S[M_XT * NB + bx] = float(xt);
+            S[M_XT * NB + bx] = xt;
         }
         __syncthreads();
         if (tma && tid == 0 && pen + int(gridDim.x) < total) {    // the staging buffer is free: next pencil
@@ -755,9 +750,10 @@ __global__ void k3f_coords(Grid3 g, const double* xn, const double* xdot, double
             double v;
             if (in) v = xdot ? xn[c * N + id] + cdt * xdot[c * N + id] : xn[c * N + id];
             else v = ghost_value3(g, xn + c * N, xdot ? xdot + c * N : nullptr, cdt, i1, i2, i3, c);
-            const float hi = float(v);
+            float hi, lo;
+            bits::split(v, hi, lo);                          // integer operations, not FP64 conversions
             XEh[c * NE + e] = hi;
-            XEl[c * NE + e] = float(v - double(hi));
+            XEl[c * NE + e] = lo;
         }
     }
 }
@@ -1182,13 +1178,19 @@ __global__ void k3f_velocity(Grid3 g, const float* da, const float* db, DevScala
     const int N = g.n[0] * g.n[1] * g.n[2];
     const size_t P = size_t(N);
     const float* dl = sweep_result(d, da, db);
-    const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
-    const double dt = d->dt;
-    const double f = dt > 0.0 ? gam / dt : 0.0;
+    // Delta_gamma / dt once per block (an FP64 division); the velocity in float, widened from its bits
+    __shared__ float fs;
+    if (threadIdx.x == 0) {
+        const double gam = __longlong_as_double((long long)d->red[RED_GAMMA]);
+        const double dt = d->dt;
+        fs = dt > 0.0 ? float(gam / dt) : 0.0f;
+    }
+    __syncthreads();
+    const float f = fs;
     for (size_t id = blockIdx.x * size_t(blockDim.x) + threadIdx.x; id < 3 * P; id += size_t(gridDim.x) * blockDim.x)
-        xdot[id] = dl ? f * double(dl[id]) : 0.0;
+        xdot[id] = dl ? bits::widen(f * dl[id]) : 0.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        d->gamma = gam;
+        d->gamma = __longlong_as_double((long long)d->red[RED_GAMMA]);
         d->sweeps_total += d->sweeps;
         d->solves += 1;
     }
@@ -1242,11 +1244,8 @@ int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const
     float* XEh = (float*)d->XE;                   // [3][NE] doubles hold the (hi, lo) float planes
     float* Dh = (float*)d->D;                     // [9][NE] likewise
     int n = 4;
-    if (inc && xdot) {                            // within a step: move the coordinates the buffer holds
-        if (inc->form_xd) {
-            k3f_xdot_ext<<<G, 256, 0, s>>>(d->g, xdot, d->XD);
-            ++n;
-        }
+    if (inc && xdot) {                            // within a step: move the coordinates the buffer holds (d->XD
+                                                  // holds xdot: d3_stage formed it)
         k3f_coords_add<<<G, 256, 0, s>>>(NE, XEh, XEh + 3 * NE, d->XD, cst - inc->xe_cst, dt_dev, dt_host);
     } else {
         k3f_coords<<<G, 256, 0, s>>>(d->g, xn, cst != 0.0 ? xdot : nullptr, cst, dt_dev, dt_host, XEh, XEh + 3 * NE);
@@ -1256,6 +1255,11 @@ int d3f_metrics(Ctx3* d, const double* xn, const double* xdot, double cst, const
     k3f_metric<1><<<G, 256, 0, s>>>(d->g, Dh, Dh + 9 * NE, (float*)d->NK[1]);
     k3f_metric<2><<<G, 256, 0, s>>>(d->g, Dh, Dh + 9 * NE, (float*)d->NK[2]);
     return n + 1;
+}
+
+int d3f_form_xd(Ctx3* d, const double* xdot, cudaStream_t s) {
+    k3f_xdot_ext<<<d->grid, 256, 0, s>>>(d->g, xdot, d->XD);
+    return 1;
 }
 
 int d3f_nodes(Ctx3* d, const void* JU, const void* J, DevStatus* st, cudaStream_t s) {
@@ -1281,7 +1285,7 @@ int d3f_directions(Ctx3* d, const Stage3& a, DevStatus* st, cudaStream_t s, cuda
     P.weno = wenof(d->weno);
     P.diss = d->diss;
     P.NF = (const float*)d->NF;
-    P.xdot = a.xdot;
+    P.XD = a.xdot ? d->XD : nullptr;          // d3_stage formed it from a.xdot
     P.RH = (float*)d->RH;
     P.mode = a.mode;
     P.ca = float(a.ca);

@@ -407,7 +407,7 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
         // mixed form: the metric coordinates hold x^n after the CFL pass and x^n + dt xdot after stage 2, so
         // stages 2 and 3 move them by (c_s - c_{s-1}) dt xdot
         a.xe_incr = st > 0;
-        a.form_xd = st == 1;
+        a.xd_ready = st > 0;               // stage 1 forms xdot on the extended mesh (mixed form)
         a.xe_cst = st > 0 ? RK_C[st - 1] : 0.0;
         n = d3_stage(c->d3, a, &c->dev->status, s, &e);
         if (n < 0) return cuda_fail(c, e, "3D stage kernels");
