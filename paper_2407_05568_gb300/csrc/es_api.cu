@@ -28,7 +28,8 @@ struct es_ctx {
     MonitorParams mon;
     size_t N;
     int nc;
-    int grid1d;
+    int grid1d;                       // blocks of the per-node grid-stride kernels
+    int block1d;                      // their threads per block (see es_create)
     int mixed;                        // ES_PREC_MIXED: float state
     int tile;                         // 2D stage tile shape (0-based); tuned: chosen by es_autotune or fixed
     int tuned;
@@ -126,7 +127,7 @@ void set_state(es_ctx* c, StageParams& P, const void* JUn, const void* Jn, const
 // mixed form: FP32 mesh displacement / velocity for the stage kernels
 void enqueue_mesh_f32(es_ctx* c, StageParams& P, const double* x, const double* xdot) {
     if (!c->mixed) return;
-    k_mesh_f32<<<c->grid1d, 256, 0, c->s_enq>>>(c->g, x, xdot, c->fdisp, c->fxd);
+    k_mesh_f32<<<c->grid1d, c->block1d, 0, c->s_enq>>>(c->g, x, xdot, c->fdisp, c->fxd);
     count(c);
     P.fdisp = c->fdisp;
     P.fxdot = xdot ? c->fxd : nullptr;
@@ -148,9 +149,9 @@ const double RK_C[3] = {0.0, 1.0, 0.5};
 
 // monitor -> filter passes (Sec. 4); returns the buffer holding the filtered omega
 const double* enqueue_monitor(es_ctx* c, const void* JU, const void* J) {
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
-    launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s);
+    launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s, B);
     k_mon_terms<<<G, B, 0, s>>>(c->g, c->mon, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->dev);
     k_mon_omega<<<G, B, 0, s>>>(c->g, c->mon, c->t0, c->t1, c->t2, c->dev, c->om0);
     count(c, 3);
@@ -166,7 +167,7 @@ const double* enqueue_monitor(es_ctx* c, const void* JU, const void* J) {
 
 // learned warm start x0 = x_n + dxi NN(features) into c->xw
 int enqueue_net(es_ctx* c, const double* om, const double* xn) {
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     k_features<<<G, B, 0, s>>>(c->g, om, c->GF, xn, c->feat);
     count(c);
@@ -224,7 +225,7 @@ int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
     if (cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
         return LOOP_BROKEN;
-    k_jacobi_loop<<<c->grid1d, 256, 0, c->body_stream>>>(c->g, om, xn, c->xa, c->xb, c->dev, c->p.jacobi_eps,
+    k_jacobi_loop<<<c->grid1d, c->block1d, 0, c->body_stream>>>(c->g, om, xn, c->xa, c->xb, c->dev, c->p.jacobi_eps,
                                                          c->p.jacobi_sweeps, h);
     const cudaError_t el = cudaGetLastError();
     count(c);
@@ -240,7 +241,7 @@ int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
 // Jacobi sweeps from x_n, or guarded from x_start (the first sweep runs from both starts
 // and the start whose sweep changes the mesh less is continued)
 int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio) {
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const int check = c->p.jacobi_eps > 0.0;
     const double eps = c->p.jacobi_eps;
@@ -270,7 +271,7 @@ int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* 
 // the velocity kernel also takes eq. cfl with the new velocity (from the terms the step's first CFL pass left in
 // c->S1 and c->S2) and shrinks dt
 int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot, double cfl_moving = 0.0) {
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const double* om = enqueue_monitor(c, JU, J);
     const double* x_start = nullptr;
@@ -301,7 +302,7 @@ bool mesh_on_fp32(const es_ctx* c) { return c->mixed && c->nn_layers == 0; }
 // cfl_moving > 0: the velocity kernel also takes eq. cfl with the new mesh velocity (from the terms the step's
 // first CFL pass left in c->S1) and shrinks dt.  In 2D the sweeps' tile kernel also forms Delta_gamma.
 int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int with_dt, double cfl_moving = 0.0) {
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const GasF32 gf = gas_f32(c->gas);
     float* t0 = (float*)c->t0;
@@ -351,7 +352,7 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int w
 
 void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot = nullptr,
                  int slot = RED_CFL, double* t0 = nullptr, double* t1 = nullptr) {
-    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq, t0, t1);
+    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq, t0, t1, c->block1d);
     count(c);
 }
 
@@ -413,7 +414,7 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
         if (n < 0) return cuda_fail(c, e, "3D stage kernels");
         count(c, n);
     }
-    k_advance<<<c->grid1d, 256, 0, s>>>(c->g, x, xdot, c->dev);
+    k_advance<<<c->grid1d, c->block1d, 0, s>>>(c->g, x, xdot, c->dev);
     count(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "advance kernel");
@@ -422,7 +423,7 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
 
 int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     if (c->p.dim == 3) return enqueue_step3(c, (double*)JU, (double*)J, x);
-    const int B = 256, G = c->grid1d;
+    const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const bool f32 = mesh_on_fp32(c);
     // eq. cfl with the step's mesh velocity: the first pass (mesh at rest) leaves its node terms in the stage
@@ -590,8 +591,20 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    const size_t blocks = (c->N + 255) / 256;
-    c->grid1d = (int)(blocks < size_t(nsm) * 8 ? blocks : size_t(nsm) * 8);
+    // The per-node kernels of a step (CFL, monitor, filter, sweeps, limiter, velocity, advance) take one node per
+    // thread on a small mesh, so their time is one thread's chain of dependent operations: there every CTA gets its
+    // own SM (blocks of ceil(N / SMs) threads, at most 512; with 256-thread blocks 200^2 gave 157 CTAs on 152 SMs
+    // and a few SMs ran two, doubling the launch).  Larger meshes take 256-thread blocks, at most 8 per SM.
+    const size_t per_sm = (c->N + size_t(nsm) - 1) / size_t(nsm);
+    if (per_sm <= 512) {
+        c->block1d = int((per_sm + 31) / 32 * 32);
+        if (c->block1d < 64) c->block1d = 64;
+        c->grid1d = int((c->N + size_t(c->block1d) - 1) / size_t(c->block1d));
+    } else {
+        const size_t blocks = (c->N + 255) / 256;
+        c->block1d = 256;
+        c->grid1d = (int)(blocks < size_t(nsm) * 8 ? blocks : size_t(nsm) * 8);
+    }
     if (c->grid1d < 1) c->grid1d = 1;
     const size_t B = sizeof(double) * c->N;
     int rc = ES_OK;
@@ -659,7 +672,8 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
         d->filter_passes = p->filter_passes;
         d->sweeps = p->jacobi_sweeps;
         d->eps = p->jacobi_eps;
-        d->grid = c->grid1d;
+        const size_t blocks = (c->N + 255) / 256;             // 256-thread grid-stride kernels
+        d->grid = (int)(blocks < size_t(nsm) * 8 ? blocks : size_t(nsm) * 8);
         // tile 0: chosen by es_autotune; mixed tiles D3_NSHAPES + k: shape k with plain loads (no TMA staging)
         d->shape = p->tile >= 1 ? (p->tile - 1) % D3_NSHAPES : 0;
         d->no_tma = p->tile > D3_NSHAPES;
@@ -804,8 +818,8 @@ int es_cfl_dt(es_ctx* c, const void* JU, const void* J, const double* x, const d
         if (n < 0) return cuda_fail(c, e, "3D time-step kernels");
         count(c, n);
     } else if (mesh_on_fp32(c)) {
-        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, x, xdot, c->fdisp, c->fxd);
-        k_cfl_f<<<c->grid1d, 256, 0, c->stream>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J,
+        k_mesh_f32<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, x, xdot, c->fdisp, c->fxd);
+        k_cfl_f<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J,
                                                    c->fdisp, xdot ? c->fxd : nullptr, slot, c->dev);
         count(c, 2);
     } else {
@@ -850,7 +864,7 @@ int es_mesh_redistribute(es_ctx* c, const void* JU, const void* J, const double*
         count(c, n);
         rc = ES_OK;
     } else if (mesh_on_fp32(c)) {
-        k_mesh_f32<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
+        k_mesh_f32<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, xn, nullptr, c->fdisp, c->fxd);
         count(c);
         rc = enqueue_mesh32(c, JU, J, xdot, 0);
     } else {
@@ -872,7 +886,7 @@ int es_mesh_features(es_ctx* c, const void* JU, const void* J, const double* x, 
     k_reset<<<1, 32, 0, c->stream>>>(c->dev);
     count(c);
     const double* om = enqueue_monitor(c, JU, J);
-    k_features<<<c->grid1d, 256, 0, c->stream>>>(c->g, om, c->GF, x, feat);
+    k_features<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, om, c->GF, x, feat);
     count(c);
     CK(cudaGetLastError(), "feature kernels");
     return ES_OK;
@@ -889,7 +903,7 @@ int es_mesh_solve(es_ctx* c, const void* JU, const void* J, const double* xn, co
     const double* om = enqueue_monitor(c, JU, J);
     const int rj = enqueue_jacobi(c, om, xn, x_start, guard_ratio);
     if (rj) return rj;
-    k_jacobi_out<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, c->xa, c->xb, c->dev, x_out, disp_out);
+    k_jacobi_out<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, xn, c->xa, c->xb, c->dev, x_out, disp_out);
     count(c);
     CK(cudaGetLastError(), "mesh kernels");
     if (sweeps_host || picked_host) {
@@ -905,7 +919,7 @@ int es_mesh_warm_start(es_ctx* c, const double* xn, const float* out, double* x_
     if (!c || !xn || !out || !x_start) return fail(c, ES_ERR_ARG, "null argument");
     if (c->p.dim != 2) return fail(c, ES_ERR_ARG, "the warm start is defined for 2D meshes");
     if (x_start == xn) return fail(c, ES_ERR_ARG, "x_start aliases xn");
-    k_warm_start<<<c->grid1d, 256, 0, c->stream>>>(c->g, xn, out, x_start);
+    k_warm_start<<<c->grid1d, c->block1d, 0, c->stream>>>(c->g, xn, out, x_start);
     count(c);
     CK(cudaGetLastError(), "k_warm_start");
     return ES_OK;

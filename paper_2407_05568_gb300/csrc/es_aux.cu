@@ -711,15 +711,15 @@ void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const voi
 
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
                 const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s, double* t0,
-                double* t1) {
-    if (f32) k_cfl<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d, t0, t1);
-    else k_cfl<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d, t0, t1);
+                double* t1, int block) {
+    if (f32) k_cfl<float><<<grid, block, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d, t0, t1);
+    else k_cfl<double><<<grid, block, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d, t0, t1);
 }
 
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,
-                       bool f32, int grid, cudaStream_t s) {
-    if (f32) k_mon_fields<float><<<grid, 256, 0, s>>>(g, G, (const float*)JU, (const float*)J, rhoF, GF);
-    else k_mon_fields<double><<<grid, 256, 0, s>>>(g, G, (const double*)JU, (const double*)J, rhoF, GF);
+                       bool f32, int grid, cudaStream_t s, int block) {
+    if (f32) k_mon_fields<float><<<grid, block, 0, s>>>(g, G, (const float*)JU, (const float*)J, rhoF, GF);
+    else k_mon_fields<double><<<grid, block, 0, s>>>(g, G, (const double*)JU, (const double*)J, rhoF, GF);
 }
 
 }  // namespace es

@@ -105,13 +105,13 @@ void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, c
 // also store the node terms cfl_moving_term reads (mesh at rest only)
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
                 const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s,
-                double* t0 = nullptr, double* t1 = nullptr);
+                double* t0 = nullptr, double* t1 = nullptr, int block = 256);
 // total entropy rate sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt) vol in FP64 with a compensated, fixed-order
 // reduction: out[0] the rate, out[1] the sum of the magnitudes of its terms (device); part holds 3 grid doubles
 void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const void* J, const void* dJU,
                          const void* dJ, double vol, double* part, double* out, bool f32, int grid, cudaStream_t s);
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,
-                       bool f32, int grid, cudaStream_t s);
+                       bool f32, int grid, cudaStream_t s, int block = 256);
 __global__ void k_reset(DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
 __global__ void k_dt_moving(DevScalars* d, double cfl);
