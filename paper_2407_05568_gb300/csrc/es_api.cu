@@ -30,6 +30,7 @@ struct es_ctx {
     int nc;
     int grid1d;                       // blocks of the per-node grid-stride kernels
     int block1d;                      // their threads per block (see es_create)
+    int nsm;                          // SMs of the device
     int mixed;                        // ES_PREC_MIXED: float state
     int tile;                         // 2D stage tile shape (0-based); tuned: chosen by es_autotune or fixed
     int tuned;
@@ -312,9 +313,8 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int w
     float* other = (float*)c->om1;
     float* da = (float*)c->xa;
     float* db = (float*)c->xb;
-    k_mon_f<<<mon_f_blocks(c->g), MON_TX * MON_TY, 0, s>>>(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0,
-                                                           t1, t2, c->dev, with_dt, c->p.cfl, c->p.dt_fixed,
-                                                           c->fdisp, cfl_moving > 0.0 ? (float*)c->S1 : nullptr);
+    launch_mon_f(c->g, gf, (const float*)JU, (const float*)J, c->mon, t0, t1, t2, c->dev, with_dt, c->p.cfl,
+                 c->p.dt_fixed, c->fdisp, cfl_moving > 0.0 ? (float*)c->S1 : nullptr, c->nsm, s);
     count(c);
     // 2D: omega with its filter passes, and the sweeps without a tolerance, fused per tile
     const bool fuse = c->p.dim == 2;
@@ -591,6 +591,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     c->esz = c->mixed ? 2 * sizeof(float) : sizeof(double);   // mixed: (hi, lo) float planes
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    c->nsm = nsm;
     // The per-node kernels of a step (CFL, monitor, filter, sweeps, limiter, velocity, advance) take one node per
     // thread on a small mesh, so their time is one thread's chain of dependent operations: there every CTA gets its
     // own SM (blocks of ceil(N / SMs) threads, at most 512; with 256-thread blocks 200^2 gave 157 CTAs on 152 SMs

@@ -264,25 +264,30 @@ __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const fl
     }
 }
 
-// the monitor terms in one pass over MON_TX x MON_TY tiles (MON_TX x 1 in 1D): the density and G of the
-// tile's nodes and of a one-node halo (ghost rule of the state) are computed once each in double-float and kept
-// in shared memory, then every node forms its differences from them.  With do_dt, thread 0 also sets the step's
-// dt from the CFL maximum (k_dt's work: the CFL kernel has finished when this one starts).
-__global__ void __launch_bounds__(MON_TX * MON_TY, 4) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
-                                                           MonitorParams mp, float* t0, float* t1, float* t2,
-                                                           DevScalars* d, int do_dt, double cfl, double dt_fixed,
-                                                           const float* disp, float* cfl_terms) {
-    constexpr int CAP = (MON_TX + 2) * (MON_TY + 2);      // >= MON_TX * MON_TY + 2, the 1D tile with its halo
+// the monitor terms in one pass over TX x TY tiles (TX TY x 1 in 1D): the density and G of the tile's nodes and
+// of a one-node halo (ghost rule of the state) are computed once each in double-float and kept in shared memory,
+// then every node forms its differences from them.  With do_dt, thread 0 also sets the step's dt from the CFL
+// maximum (k_dt's work: the CFL kernel has finished when this one starts).  MON_NT threads: 32 x 8 tiles take two
+// rounds of the EOS per thread (1.33 evaluations per node), 30 x 6 tiles one (the tile with its halo is one node
+// per thread, 1.42 evaluations per node): the first for throughput on large meshes, the second for latency on
+// small ones.
+template <int TX, int TY>
+__global__ void __launch_bounds__(MON_NT, 4) k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J,
+                                                     MonitorParams mp, float* t0, float* t1, float* t2, DevScalars* d,
+                                                     int do_dt, double cfl, double dt_fixed, const float* disp,
+                                                     float* cfl_terms) {
+    constexpr int CAP = (TX + 2) * (TY + 2);              // >= TX * TY + 2, the 1D tile with its halo
+    static_assert(TX * TY <= MON_NT && CAP >= TX * TY + 2, "tile");
     __shared__ float srh[CAP], srl[CAP], sgh[CAP], sgl[CAP];
     if (do_dt == 1 && blockIdx.x == 0 && threadIdx.x == 0) set_dt_from_cfl(d, cfl, dt_fixed);
     const int N = g.n1 * g.n2;
     const size_t P = size_t(g.dim + 2) * N;
-    const int TW = g.dim == 2 ? MON_TX : MON_TX * MON_TY;  // tile width; 1D tiles are one row of all threads
+    const int TW = g.dim == 2 ? TX : TX * TY;            // tile width; 1D tiles are one row
     const int HW = TW + 2;
     const int ntx = (g.n1 + TW - 1) / TW;
     const int i0 = (blockIdx.x % ntx) * TW;
-    const int j0 = g.dim == 2 ? (blockIdx.x / ntx) * MON_TY : 0;
-    const int hh = g.dim == 2 ? MON_TY + 2 : 1;
+    const int j0 = g.dim == 2 ? (blockIdx.x / ntx) * TY : 0;
+    const int hh = g.dim == 2 ? TY + 2 : 1;
     for (int t = threadIdx.x; t < HW * hh; t += blockDim.x) {
         const int lx = t % HW, ly = t / HW;
         const int gi = i0 - 1 + lx, gj = g.dim == 2 ? j0 - 1 + ly : 0;
@@ -298,7 +303,8 @@ __global__ void __launch_bounds__(MON_TX * MON_TY, 4) k_mon_f(GridParams g, GasF
     float m0 = 0.0f, m1 = 0.0f, m2 = 0.0f, mc = 0.0f;
     const int tx = threadIdx.x % TW, ty = threadIdx.x / TW;
     const int i = i0 + tx, j = j0 + ty;
-    if (i < g.n1 && (g.dim == 1 || j < g.n2)) {
+    const bool owner = threadIdx.x < TW * (g.dim == 2 ? TY : 1);   // the others formed halo values only
+    if (owner && i < g.n1 && (g.dim == 1 || j < g.n2)) {
         const int id = j * g.n1 + i;
         // do_dt == 2: eq. cfl with the mesh at rest at this node (k_cfl_f's work), and its terms for the moving pass
         if (do_dt == 2)
@@ -358,9 +364,21 @@ __global__ void __launch_bounds__(MON_TX * MON_TY, 4) k_mon_f(GridParams g, GasF
     }
 }
 
-int mon_f_blocks(const GridParams& g) {
-    if (g.dim == 1) return (g.n1 + MON_TX * MON_TY - 1) / (MON_TX * MON_TY);
-    return ((g.n1 + MON_TX - 1) / MON_TX) * ((g.n2 + MON_TY - 1) / MON_TY);
+template <int TX, int TY>
+static int mon_f_blocks(const GridParams& g) {
+    if (g.dim == 1) return (g.n1 + TX * TY - 1) / (TX * TY);
+    return ((g.n1 + TX - 1) / TX) * ((g.n2 + TY - 1) / TY);
+}
+
+void launch_mon_f(const GridParams& g, const GasF32& G, const float* JU, const float* J, const MonitorParams& mp,
+                  float* t0, float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed,
+                  const float* disp, float* cfl_terms, int nsm, cudaStream_t s) {
+    const int big = mon_f_blocks<32, 8>(g);
+    if (big >= 4 * nsm)         // four resident CTAs per SM: at least one full wave
+        k_mon_f<32, 8><<<big, MON_NT, 0, s>>>(g, G, JU, J, mp, t0, t1, t2, d, do_dt, cfl, dt_fixed, disp, cfl_terms);
+    else
+        k_mon_f<30, 6><<<mon_f_blocks<30, 6>(g), MON_NT, 0, s>>>(g, G, JU, J, mp, t0, t1, t2, d, do_dt, cfl, dt_fixed,
+                                                                   disp, cfl_terms);
 }
 
 

@@ -31,16 +31,14 @@ __global__ void k_cfl_f(GridParams g, GasF32 G, const float* JU, const float* J,
                         int slot, DevScalars* d);
 // rhoF, GF: 2 N floats each, (hi, lo) planes of the density and the fundamental derivative
 __global__ void k_mon_fields_f(GridParams g, GasF32 G, const float* JU, const float* J, float* rhoF, float* GF);
-// monitor terms over MON_TX x MON_TY tiles (one row of MON_TX * MON_TY nodes in 1D); launch with
-// mon_f_blocks(g) blocks of MON_TX * MON_TY threads
-constexpr int MON_TX = 32, MON_TY = 8;
+// monitor terms over tiles of MON_NT threads (k_mon_f, 32 x 8 or 30 x 6 nodes, chosen by the mesh size)
 // do_dt: 0 no time step; 1 the step's dt from the CFL maximum an earlier kernel left (k_dt's work); 2 also eq. cfl
 // with the mesh at rest at every node (k_cfl_f's work on disp, its moving-pass terms to cfl_terms when non-null)
-// and dt set by the last block to finish
-__global__ void k_mon_f(GridParams g, GasF32 G, const float* JU, const float* J, MonitorParams mp, float* t0,
-                        float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed,
-                        const float* disp = nullptr, float* cfl_terms = nullptr);
-int mon_f_blocks(const GridParams& g);
+// and dt set by the last block to finish; the last block also forms omega's coefficients (DevScalars::mon_c)
+constexpr int MON_NT = 256;
+void launch_mon_f(const GridParams& g, const GasF32& G, const float* JU, const float* J, const MonitorParams& mp,
+                  float* t0, float* t1, float* t2, DevScalars* d, int do_dt, double cfl, double dt_fixed,
+                  const float* disp, float* cfl_terms, int nsm, cudaStream_t s);
 __global__ void k_mon_omega_f(GridParams g, MonitorParams mp, const float* t0, const float* t1, const float* t2,
                               const DevScalars* d, float* omega);
 __global__ void k_filter_f(GridParams g, const float* in, float* out);
