@@ -241,7 +241,9 @@ int enqueue_sweep_loop(es_ctx* c, const double* om, const double* xn) {
 
 // Jacobi sweeps from x_n, or guarded from x_start (the first sweep runs from both starts
 // and the start whose sweep changes the mesh less is continued)
-int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio) {
+// *limited (nullable): set when the last sweep also formed Delta_gamma (sweeps without a tolerance)
+int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* x_start, double ratio,
+                   bool* limited = nullptr) {
     const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
     const int check = c->p.jacobi_eps > 0.0;
@@ -262,8 +264,10 @@ int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* 
         c->loop_failed = 1;
     }
     for (int k = k0; k < c->p.jacobi_sweeps; ++k) {
-        k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, k, 0, c->dev, check, RED_JAC, 1, eps);
+        const int lim = limited && !check && k == c->p.jacobi_sweeps - 1;
+        k_jacobi<<<G, B, 0, s>>>(c->g, om, xn, c->xa, c->xb, k, 0, c->dev, check, RED_JAC, 1, eps, lim);
         count(c);
+        if (lim) *limited = true;
     }
     return ES_OK;
 }
@@ -281,12 +285,16 @@ int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, dou
         if (rc) return rc;
         x_start = c->xw;
     }
-    int rc = enqueue_jacobi(c, om, xn, x_start, c->nn_ratio);
+    bool limited = false;
+    int rc = enqueue_jacobi(c, om, xn, x_start, c->nn_ratio, &limited);
     if (rc) return rc;
-    k_limiter<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev);
+    if (!limited) {
+        k_limiter<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev);
+        count(c);
+    }
     k_velocity<<<G, B, 0, s>>>(c->g, xn, c->xa, c->xb, c->dev, xdot, (const double*)c->S1, (const double*)c->S2,
                                cfl_moving);
-    count(c, 2);
+    count(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "mesh kernels");
     return ES_OK;

@@ -24,9 +24,11 @@ __device__ __forceinline__ double coord_at(const GridParams& g, const double* x,
     if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1], comp != 1);
     else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
     double acc = 0.0;
-    for (int a = 0; a < ti.nterm; ++a)
-        for (int c = 0; c < tj.nterm; ++c)
-            acc += ti.w[a] * tj.w[c] * x[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)              // fixed bounds: the terms stay in registers
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (a < ti.nterm && c < tj.nterm) acc += ti.w[a] * tj.w[c] * x[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
     if (comp == 0) acc += ti.q * g.period[0];
     if (comp == 1) acc += tj.q * g.period[1];
     return acc;
@@ -331,7 +333,9 @@ __global__ void k_mon_terms(GridParams g, MonitorParams mp, const double* rhoF, 
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         double gr = 0.0, gg = 0.0, lg = 0.0, lr = 0.0;
-        for (int k = 0; k < g.dim; ++k) {
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) {          // fixed bound: the spacings are indexed by constants
+            if (k >= g.dim) break;
             const int di = k == 0, dj = k == 1;
             const double h2 = g.inv_dxi[k];
             const double rp = field_at(g, rhoF, i + di, j + dj), rm = field_at(g, rhoF, i - di, j - dj);
@@ -428,30 +432,48 @@ __device__ __forceinline__ bool fixed_comp(const GridParams& g, int i, int j, in
 
 // One Jacobi sweep of sum_k [w_{k,+} (x_{i+e_k} - x_i) - w_{k,-} (x_i - x_{i-e_k})]/dxi_k^2 = 0
 // from xin into xout; returns this thread's max change
+// One sweep from xin into xout; CHG: returns the largest change; LIMIT: also min-accumulates into *lim the
+// limiter's bound Delta_gamma at every node from the result and x^n = xn (k_limiter's rule and arithmetic, so
+// the last sweep can take the limiter's work)
+template <bool CHG, bool LIMIT>
 __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double* omega, const double* xin,
-                                              double* xout) {
+                                              double* xout, const double* xn = nullptr, double* lim = nullptr) {
     const int N = g.n1 * g.n2;
-    double chg = 0.0;
+    double chg = 0.0, m = 1.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         const int i = id % g.n1, j = id / g.n1;
         const double w0 = omega[id];
         double den = 0.0, num[2] = {0.0, 0.0};
-        for (int kk = 0; kk < g.dim; ++kk) {
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {     // fixed bounds: num[] stays in registers
+            if (kk >= g.dim) break;
             const int di = kk == 0, dj = kk == 1;
             const double ih2 = g.inv_dxi[kk] * g.inv_dxi[kk];
             const double wp = 0.5 * (w0 + field_at(g, omega, i + di, j + dj)) * ih2;
             const double wm = 0.5 * (w0 + field_at(g, omega, i - di, j - dj)) * ih2;
             den += wp + wm;
-            for (int c = 0; c < g.dim; ++c)
-                num[c] += wp * coord_at(g, xin, i + di, j + dj, c) + wm * coord_at(g, xin, i - di, j - dj, c);
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                if (c < g.dim)
+                    num[c] += wp * coord_at(g, xin, i + di, j + dj, c) + wm * coord_at(g, xin, i - di, j - dj, c);
         }
         const double iden = rcp_nr(den);
-        for (int c = 0; c < g.dim; ++c) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c >= g.dim) break;
             const double xv = fixed_comp(g, i, j, c) ? xin[c * N + id] : num[c] * iden;
-            chg = fmax(chg, fabs(xv - xin[c * N + id]));
+            if (CHG) chg = fmax(chg, fabs(xv - xin[c * N + id]));
             xout[c * N + id] = xv;
+            if (LIMIT) {
+                const double x0 = xn[c * N + id];
+                const double dx = xv - x0;
+                const int di = c == 0, dj = c == 1;
+                if (dx < 0.0) m = fmin(m, div_nr(-(x0 - coord_at(g, xn, i - di, j - dj, c)), 2.0 * dx));
+                else if (dx > 0.0) m = fmin(m, div_nr(coord_at(g, xn, i + di, j + dj, c) - x0, 2.0 * dx));
+            }
         }
     }
+    if (LIMIT) *lim = m;
     return chg;
 }
 
@@ -460,7 +482,7 @@ __device__ __forceinline__ double jacobi_sweep(const GridParams& g, const double
 // the iteration has converged (d->conv) the remaining sweeps return at once.  With `check`, the
 // grid-wide max change goes to red[slot]; if `decide`, the last block to finish compares it with eps.
 __global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
-                         int dst0, DevScalars* d, int check, int slot, int decide, double eps) {
+                         int dst0, DevScalars* d, int check, int slot, int decide, double eps, int limit) {
     if (d->conv) return;
     const double* xin;
     double* xout;
@@ -472,7 +494,17 @@ __global__ void k_jacobi(GridParams g, const double* omega, const double* first,
         xin = src ? xb : xa;
         xout = src ? xa : xb;
     }
-    double chg = jacobi_sweep(g, omega, xin, xout);
+    double chg = 0.0;
+    if (check) {
+        chg = jacobi_sweep<true, false>(g, omega, xin, xout);
+    } else if (limit) {             // the last sweep without a tolerance: k_limiter's work (first is x^n)
+        double lim = 1.0;
+        jacobi_sweep<false, true>(g, omega, xin, xout, first, &lim);
+        lim = block_reduce_min(lim);
+        if (threadIdx.x == 0) atomic_min_pos(&d->red[RED_GAMMA], lim);
+    } else {
+        jacobi_sweep<false, false>(g, omega, xin, xout);
+    }
     if (check) {
         chg = block_reduce_max(chg);
         if (threadIdx.x == 0) {
@@ -512,7 +544,7 @@ __global__ void k_jacobi_loop(GridParams g, const double* omega, const double* x
         xin = src ? xb : xa;
         xout = src ? xa : xb;
     }
-    double chg = block_reduce_max(jacobi_sweep(g, omega, xin, xout));
+    double chg = block_reduce_max(jacobi_sweep<true, false>(g, omega, xin, xout));
     if (threadIdx.x == 0) {
         atomic_max_pos(&d->red[RED_JAC], chg);
         __threadfence();
@@ -614,7 +646,7 @@ __global__ void k_jacobi_out(GridParams g, const double* xn, const double* xa, c
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x) {
         const double v = xit[id];
         if (xout) xout[id] = v;
-        if (disp) disp[id] = float((v - xn[id]) * g.inv_dxi[id / N]);
+        if (disp) disp[id] = float((v - xn[id]) * (id < N ? g.inv_dxi[0] : g.inv_dxi[1]));
     }
 }
 

@@ -127,7 +127,7 @@ __global__ void k_mon_omega(GridParams g, MonitorParams mp, const double* t0, co
                             const DevScalars* d, double* omega);
 __global__ void k_filter(GridParams g, const double* in, double* out);
 __global__ void k_jacobi(GridParams g, const double* omega, const double* first, double* xa, double* xb, int k,
-                         int dst0, DevScalars* d, int check, int slot, int decide, double eps);
+                         int dst0, DevScalars* d, int check, int slot, int decide, double eps, int limit = 0);
 __global__ void k_jacobi_loop(GridParams g, const double* omega, const double* xn, double* xa, double* xb,
                               DevScalars* d, double eps, int mu, cudaGraphConditionalHandle h);
 __global__ void k_pick(DevScalars* d, int check, double eps, double ratio);
