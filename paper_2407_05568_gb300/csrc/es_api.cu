@@ -149,13 +149,17 @@ const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 const double RK_C[3] = {0.0, 1.0, 0.5};
 
 // monitor -> filter passes (Sec. 4); returns the buffer holding the filtered omega
-const double* enqueue_monitor(es_ctx* c, const void* JU, const void* J) {
+// fields_ready: the step's CFL kernel already wrote rho and G (c->rhoF, c->GF) for this state
+const double* enqueue_monitor(es_ctx* c, const void* JU, const void* J, bool fields_ready = false) {
     const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
-    launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s, B);
+    if (!fields_ready) {
+        launch_mon_fields(c->g, c->gas, JU, J, c->rhoF, c->GF, c->mixed, G, s, B);
+        count(c);
+    }
     k_mon_terms<<<G, B, 0, s>>>(c->g, c->mon, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->dev);
     k_mon_omega<<<G, B, 0, s>>>(c->g, c->mon, c->t0, c->t1, c->t2, c->dev, c->om0);
-    count(c, 3);
+    count(c, 2);
     double* om = c->om0;
     double* other = c->om1;
     for (int k = 0; k < c->p.filter_passes; ++k) {
@@ -275,10 +279,11 @@ int enqueue_jacobi(es_ctx* c, const double* om, const double* xn, const double* 
 // monitor -> filter -> [warm start] -> Jacobi -> limiter -> xdot, with dt already in c->dev->dt; cfl_moving > 0:
 // the velocity kernel also takes eq. cfl with the new velocity (from the terms the step's first CFL pass left in
 // c->S1 and c->S2) and shrinks dt
-int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot, double cfl_moving = 0.0) {
+int enqueue_mesh(es_ctx* c, const void* JU, const void* J, const double* xn, double* xdot, double cfl_moving = 0.0,
+                 bool fields_ready = false) {
     const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
-    const double* om = enqueue_monitor(c, JU, J);
+    const double* om = enqueue_monitor(c, JU, J, fields_ready);
     const double* x_start = nullptr;
     if (c->nn_layers > 0) {
         int rc = enqueue_net(c, om, xn);
@@ -358,9 +363,12 @@ int enqueue_mesh32(es_ctx* c, const void* JU, const void* J, double* xdot, int w
     return ES_OK;
 }
 
+// fields: also write the monitor's rho and G fields; set_dt: the kernel also sets the step's dt
 void enqueue_cfl(es_ctx* c, const void* JU, const void* J, const double* x, const double* xdot = nullptr,
-                 int slot = RED_CFL, double* t0 = nullptr, double* t1 = nullptr) {
-    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq, t0, t1, c->block1d);
+                 int slot = RED_CFL, double* t0 = nullptr, double* t1 = nullptr, bool fields = false,
+                 bool set_dt = false) {
+    launch_cfl(c->g, c->gas, JU, J, x, xdot, slot, c->dev, c->mixed, c->grid1d, c->s_enq, t0, t1, c->block1d,
+               fields ? c->rhoF : nullptr, fields ? c->GF : nullptr, set_dt ? 1 : 0, c->p.cfl, c->p.dt_fixed);
     count(c);
 }
 
@@ -448,10 +456,11 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     } else {
         k_reset<<<1, 32, 0, s>>>(c->dev);
         count(c);
-        enqueue_cfl(c, JU, J, x, nullptr, RED_CFL, cfl_moving > 0.0 ? (double*)c->S1 : nullptr, (double*)c->S2);
+        // the CFL kernel also writes the monitor's fields of this state and sets dt (k_mon_fields', k_dt's work)
+        enqueue_cfl(c, JU, J, x, nullptr, RED_CFL, cfl_moving > 0.0 ? (double*)c->S1 : nullptr, (double*)c->S2,
+                    c->p.moving, true);
     }
-    const bool dt_in_mesh = f32 && c->p.moving;       // the FP32 monitor kernel takes eq. cfl and sets dt
-    if (!dt_in_mesh) {
+    if (f32 && !c->p.moving) {      // on a moving mesh the FP32 monitor kernel sets dt, and k_cfl does in FP64
         k_dt<<<1, 32, 0, s>>>(c->dev, c->p.cfl, c->p.dt_fixed);
         count(c);
     }
@@ -460,7 +469,7 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     const double* xdot = nullptr;
     if (c->p.moving) {
         int rc = f32 ? enqueue_mesh32(c, JU, J, c->xdot, 2, cfl_moving)
-                     : enqueue_mesh(c, JU, J, x, c->xdot, cfl_moving);
+                     : enqueue_mesh(c, JU, J, x, c->xdot, cfl_moving, true);
         if (rc) return rc;
         xdot = c->xdot;
     }

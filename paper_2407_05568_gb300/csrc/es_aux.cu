@@ -130,7 +130,8 @@ __global__ void k_reset(DevScalars* d) {
 // (eq. VCLCoeff); xdot = nullptr is a mesh at rest.  The maximum goes to d->red[slot].
 template <class TS>
 __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const double* x, const double* xdot, int slot,
-                      DevScalars* d, double* t0, double* t1) {
+                      DevScalars* d, double* t0, double* t1, double* rhoF, double* GF, int set_dt, double cfl,
+                      double dt_fixed) {
     const int N = g.n1 * g.n2;
     double m = 0.0;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
@@ -146,6 +147,11 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
         const double om = 1.0 - G.b * rho;
         const double iom = rcp_nr(om);
         const double c2 = (1.0 + G.delta) * G.R * T * (iom * iom) - 2.0 * G.a * rho;
+        if (rhoF) {                     // the monitor's fields from the same node state (k_mon_fields' formulas)
+            const double pnn3 = (1.0 + G.delta) * (2.0 + G.delta) * G.R * T * (iom * iom * iom) - 6.0 * G.a * rho;
+            rhoF[id] = rho;
+            GF[id] = div_nr(pnn3, 2.0 * c2);
+        }
         const double c = sqrt(fmax(c2, 0.0));
         const double xd1 = xdot != nullptr ? xdot[id] : 0.0;
         double tot;
@@ -184,7 +190,17 @@ __global__ void k_cfl(GridParams g, Gas G, const TS* JU, const TS* J, const doub
         m = fmax(m, tot);
     }
     m = block_reduce_max(m);
-    if (threadIdx.x == 0) atomic_max_pos(&d->red[slot], m);
+    if (threadIdx.x == 0) {
+        atomic_max_pos(&d->red[slot], m);
+        if (set_dt) {                   // k_dt's work, by the last block to finish
+            __threadfence();
+            const unsigned int ticket = atomicAdd(&d->done, 1u);
+            if (ticket == gridDim.x - 1) {
+                set_dt_from_max(d, __longlong_as_double((long long)atomicAdd(&d->red[slot], 0ULL)), cfl, dt_fixed);
+                d->done = 0u;
+            }
+        }
+    }
 }
 
 // Delta t = CFL / max (or the fixed step), clipped to t_end; 0 once t_end is reached
@@ -743,9 +759,13 @@ void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const voi
 
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
                 const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s, double* t0,
-                double* t1, int block) {
-    if (f32) k_cfl<float><<<grid, block, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d, t0, t1);
-    else k_cfl<double><<<grid, block, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d, t0, t1);
+                double* t1, int block, double* rhoF, double* GF, int set_dt, double cfl, double dt_fixed) {
+    if (f32)
+        k_cfl<float><<<grid, block, 0, s>>>(g, G, (const float*)JU, (const float*)J, x, xdot, slot, d, t0, t1, rhoF, GF,
+                                            set_dt, cfl, dt_fixed);
+    else
+        k_cfl<double><<<grid, block, 0, s>>>(g, G, (const double*)JU, (const double*)J, x, xdot, slot, d, t0, t1, rhoF,
+                                             GF, set_dt, cfl, dt_fixed);
 }
 
 void launch_mon_fields(const GridParams& g, const Gas& G, const void* JU, const void* J, double* rhoF, double* GF,

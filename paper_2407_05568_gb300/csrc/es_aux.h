@@ -102,10 +102,12 @@ void launch_init_J(const GridParams& g, const double* x, void* J, bool f32, int 
 void launch_prim_to_cons(const GridParams& g, const Gas& G, const double* rho, const double* v, const double* p,
                          const void* J, void* JU, bool f32, int grid, cudaStream_t s);
 // xdot (nullable): the mesh velocity of eq. VCLCoeff's J xi_t; slot: RED_CFL or RED_CFL2; t0, t1 (nullable):
-// also store the node terms cfl_moving_term reads (mesh at rest only)
+// also store the node terms cfl_moving_term reads (mesh at rest only); rhoF, GF (nullable): also the monitor's
+// fields (k_mon_fields' work); set_dt: the last block also sets dt from the maximum (k_dt's work)
 void launch_cfl(const GridParams& g, const Gas& G, const void* JU, const void* J, const double* x,
                 const double* xdot, int slot, DevScalars* d, bool f32, int grid, cudaStream_t s,
-                double* t0 = nullptr, double* t1 = nullptr, int block = 256);
+                double* t0 = nullptr, double* t1 = nullptr, int block = 256, double* rhoF = nullptr,
+                double* GF = nullptr, int set_dt = 0, double cfl = 0.0, double dt_fixed = 0.0);
 // total entropy rate sum_i (V_i . d(JU)_i/dt - phi_i dJ_i/dt) vol in FP64 with a compensated, fixed-order
 // reduction: out[0] the rate, out[1] the sum of the magnitudes of its terms (device); part holds 3 grid doubles
 void launch_entropy_rate(int N, int dim, const Gas& G, const void* JU, const void* J, const void* dJU,
