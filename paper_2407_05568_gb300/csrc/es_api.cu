@@ -51,9 +51,10 @@ struct es_ctx {
     void *hJU, *hJ;                   // device copies for es_run_host
     double* hx;
     // graph cache
-    cudaGraphExec_t gexec;
+    cudaGraphExec_t gexec;            // the step graph (its first step in an es_steps call)
+    cudaGraphExec_t gexec2;           // the graph of the steps after it (1D/2D: no displacement or reset kernel)
     const void* gkey[3];
-    int graph_kernels;
+    int graph_kernels, graph_kernels2;
     int capturing;
     int capture_count;
     int loop_failed;                  // a graph while-loop could not be built (unrolled sweeps used)
@@ -61,6 +62,14 @@ struct es_ctx {
     Ctx3* d3;                         // the 3D path's scratch and settings (dim = 3)
     char msg[256];
 };
+
+// the cached step graphs (they hold the buffers, the tile shape and the warm-start network)
+static void drop_graphs(es_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gexec2) cudaGraphExecDestroy(c->gexec2);
+    c->gexec = c->gexec2 = nullptr;
+}
+
 
 namespace {
 
@@ -437,7 +446,9 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
     return ES_OK;
 }
 
-int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
+// first = false: a step that follows one of the same es_steps call, whose advance kernel has already formed the
+// mixed form's FP32 displacement of x and reset the reductions (no k_mesh_f32 or k_reset then; 1D/2D)
+int enqueue_step(es_ctx* c, void* JU, void* J, double* x, bool first = true) {
     if (c->p.dim == 3) return enqueue_step3(c, (double*)JU, (double*)J, x);
     const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
@@ -446,16 +457,20 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
     // buffers S1 (and S2), free until the first stage, and the velocity kernel takes the second pass from them
     const double cfl_moving = c->p.moving && !(c->p.dt_fixed > 0.0) ? c->p.cfl : 0.0;
     if (f32) {      // the displacement kernel also resets the step's reductions (k_reset's work)
-        k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
-        count(c);
+        if (first) {
+            k_mesh_f32<<<G, B, 0, s>>>(c->g, x, nullptr, c->fdisp, c->fxd, c->dev);
+            count(c);
+        }
         if (!c->p.moving) {         // on a moving mesh the monitor kernel takes eq. cfl (with_dt = 2 below)
             k_cfl_f<<<G, B, 0, s>>>(c->g, gas_f32(c->gas), (const float*)JU, (const float*)J, c->fdisp, nullptr,
                                     RED_CFL, c->dev);
             count(c);
         }
     } else {
-        k_reset<<<1, 32, 0, s>>>(c->dev);
-        count(c);
+        if (first) {
+            k_reset<<<1, 32, 0, s>>>(c->dev);
+            count(c);
+        }
         // the CFL kernel also writes the monitor's fields of this state and sets dt (k_mon_fields', k_dt's work)
         enqueue_cfl(c, JU, J, x, nullptr, RED_CFL, cfl_moving > 0.0 ? (double*)c->S1 : nullptr, (double*)c->S2,
                     c->p.moving, true);
@@ -495,7 +510,8 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x) {
         e = launch_stage(c, P);
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel");
     }
-    k_advance<<<G, B, 0, s>>>(c->g, x, xdot ? c->xdot : nullptr, c->dev);
+    // the next step's displacement (mixed form) and reductions, for a following step of the same call
+    k_advance<<<G, B, 0, s>>>(c->g, x, xdot ? c->xdot : nullptr, c->dev, f32 ? c->fdisp : nullptr, 1);
     count(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "advance kernel");
@@ -717,7 +733,7 @@ fail_out:
 
 void es_destroy(es_ctx* c) {
     if (!c) return;
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
     void* bufs[] = {c->S1, c->S2, c->S1J, c->S2J, c->rhoF, c->GF, c->t0, c->t1, c->t2, c->om0, c->om1,
@@ -947,10 +963,7 @@ int es_set_warm_start(es_ctx* c, const uint16_t* w_bf16, const float* bias, int 
                       double guard_ratio) {
     if (!c) return ES_ERR_ARG;
     CK(cudaStreamSynchronize(c->stream), "sync");
-    if (c->gexec) {                       // the step graph changes with the network
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);                        // the step graphs change with the network
     if (!w_bf16) {
         c->nn_layers = 0;
         return ES_OK;
@@ -1035,6 +1048,29 @@ int es_step(es_ctx* c, void* JU, void* J, double* x, double t_end, double* t_hos
     return es_get_time(c, t_host, dt_host);
 }
 
+// one step captured into an executable graph on the private capture stream
+static int capture_step(es_ctx* c, void* JU, void* J, double* x, bool first, cudaGraphExec_t* out, int* kernels) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->capturing = 1;
+    c->capture_count = 0;
+    c->s_enq = c->cap_stream;
+    int rc = enqueue_step(c, JU, J, x, first);
+    c->s_enq = c->stream;
+    c->capturing = 0;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (rc) {
+        if (e == cudaSuccess && graph) cudaGraphDestroy(graph);    // never instantiated
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    *kernels = c->capture_count;
+    return ES_OK;
+}
+
 int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) {
     if (!c || !JU || !J || !x || nsteps < 0) return fail(c, ES_ERR_ARG, "bad argument");
     if (nsteps == 0) return ES_OK;
@@ -1050,33 +1086,18 @@ int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) 
     }
     const void* key[3] = {JU, J, x};
     if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
-        if (c->gexec) {
-            cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
-        }
-        cudaGraph_t graph;
-        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        c->capturing = 1;
-        c->capture_count = 0;
-        c->s_enq = c->cap_stream;
-        int rc = enqueue_step(c, JU, J, x);
-        c->s_enq = c->stream;
-        c->capturing = 0;
-        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (rc) {
-            if (e == cudaSuccess && graph) cudaGraphDestroy(graph);    // never instantiated
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-        e = cudaGraphInstantiate(&c->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        drop_graphs(c);
+        int rc = capture_step(c, JU, J, x, true, &c->gexec, &c->graph_kernels);
+        if (rc) return rc;
         memcpy(c->gkey, key, sizeof(key));
-        c->graph_kernels = c->capture_count;
+    }
+    if (nsteps > 1 && !c->gexec2) {
+        int rc = capture_step(c, JU, J, x, false, &c->gexec2, &c->graph_kernels2);
+        if (rc) return rc;
     }
     for (int k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
-        c->launches += c->graph_kernels;
+        CK(cudaGraphLaunch(k == 0 ? c->gexec : c->gexec2, c->stream), "graph launch");
+        c->launches += k == 0 ? c->graph_kernels : c->graph_kernels2;
     }
     return ES_OK;
 }
@@ -1154,10 +1175,7 @@ static int autotune3(es_ctx* c, const void* JU, const void* J, const double* x, 
     }
     c->d3->shape = best;
     c->tuned = 1;
-    if (c->gexec) {                        // the step graph holds the old shape
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);                        // the step graphs hold the old shape
     if (tile_host) *tile_host = best + 1;
     return ES_OK;
 }
@@ -1214,10 +1232,7 @@ int es_autotune(es_ctx* c, const void* JU, const void* J, const double* x, int* 
     }
     c->tile = best;
     c->tuned = 1;
-    if (c->gexec) {                        // the step graph holds the old shape
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-    }
+    drop_graphs(c);                        // the step graphs hold the old shape
     if (tile_host) *tile_host = best + 1;
     return ES_OK;
 }

@@ -217,15 +217,49 @@ __global__ void k_set_dt(DevScalars* d, double dt) {
     if (threadIdx.x == 0 && blockIdx.x == 0) d->dt = dt;
 }
 
-__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d) {
+// the float displacement x - (x_00 + i dxi_1) of one coordinate, in double-float arithmetic on the FP32 pipe:
+// x and x_00 split from their bits (es_bits.cuh), i dxi_1 an exact product plus i dxl, error-free sums; the
+// absolute error is about 2^-45 |x|, far below the float rounding of the displacement itself
+__device__ __forceinline__ float disp_f32(double x, float x0h, float x0l, int i, float dh, float dl) {
+    float xh, xl;
+    bits::split(x, xh, xl);
+    const float fi = bits::small_int(i);
+    const float ph = fi * dh;
+    const float pl = fmaf(fi, dl, fmaf(fi, dh, -ph));
+    // b = x_00 + i dxi as (bh, bl)
+    const float bh = x0h + ph;
+    const float bv = bh - x0h;
+    const float bl = ((x0h - (bh - bv)) + (ph - bv)) + (x0l + pl);
+    // x - b
+    const float sh = xh - bh;
+    const float sv = sh - xh;
+    const float se = (xh - (sh - sv)) + (-bh - sv);
+    return sh + (se + (xl - bl));
+}
+
+__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d, float* fdisp, int reset) {
     const int N = g.n1 * g.n2;
     const double dt = d->dt;
-    if (xdot != nullptr && dt != 0.0)
+    const bool move = xdot != nullptr && dt != 0.0;
+    if (fdisp) {
+        float b0h, b0l, b1h = 0.0f, b1l = 0.0f;
+        bits::split(d->base[0], b0h, b0l);
+        if (g.dim == 2) bits::split(d->base[1], b1h, b1l);
+        for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x) {
+            const double v = move ? x[id] + dt * xdot[id] : x[id];
+            if (move) x[id] = v;
+            const int c = id < N ? 0 : 1, node = id - c * N;
+            const int i = node % g.n1, j = node / g.n1;
+            fdisp[id] = c == 0 ? disp_f32(v, b0h, b0l, i, g.dxh[0], g.dxl[0]) : disp_f32(v, b1h, b1l, j, g.dxh[1], g.dxl[1]);
+        }
+    } else if (move) {
         for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < g.dim * N; id += gridDim.x * blockDim.x)
             x[id] += dt * xdot[id];
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         d->t += dt;
         d->last_dt = dt;
+        if (reset) reset_scalars(d);
     }
 }
 
@@ -698,30 +732,14 @@ __global__ void k_warm_start(GridParams g, const double* xn, const float* out, d
 // Mixed form: FP32 displacement from the Cartesian base (x_00 + i dxi_1, y_00 + j dxi_2)
 // and FP32 mesh velocity, once per step (the base is linear in the node index,
 // so delta_k of it is exactly dxi_k e_k)
-// the float displacement x - (x_00 + i dxi_1) of one coordinate, in double-float arithmetic on the FP32 pipe:
-// x and x_00 split from their bits (es_bits.cuh), i dxi_1 an exact product plus i dxl, error-free sums; the
-// absolute error is about 2^-45 |x|, far below the float rounding of the displacement itself
-__device__ __forceinline__ float disp_f32(double x, float x0h, float x0l, int i, float dh, float dl) {
-    float xh, xl;
-    bits::split(x, xh, xl);
-    const float fi = bits::small_int(i);
-    const float ph = fi * dh;
-    const float pl = fmaf(fi, dl, fmaf(fi, dh, -ph));
-    // b = x_00 + i dxi as (bh, bl)
-    const float bh = x0h + ph;
-    const float bv = bh - x0h;
-    const float bl = ((x0h - (bh - bv)) + (ph - bv)) + (x0l + pl);
-    // x - b
-    const float sh = xh - bh;
-    const float sv = sh - xh;
-    const float se = (xh - (sh - sv)) + (-bh - sv);
-    return sh + (se + (xl - bl));
-}
-
 __global__ void k_mesh_f32(GridParams g, const double* __restrict__ x, const double* __restrict__ xdot,
                            float* __restrict__ disp, float* __restrict__ fxd, DevScalars* rst) {
     const int N = g.n1 * g.n2;
-    if (rst && blockIdx.x == 0 && threadIdx.x == 0) reset_scalars(rst);
+    if (rst && blockIdx.x == 0 && threadIdx.x == 0) {
+        reset_scalars(rst);
+        rst->base[0] = x[0];                     // the origin the step's displacement is measured from
+        rst->base[1] = g.dim == 2 ? x[N] : 0.0;
+    }
     float x0h, x0l, y0h = 0.0f, y0l = 0.0f;
     bits::split(x[0], x0h, x0l);
     if (g.dim == 2) bits::split(x[N], y0h, y0l);

@@ -52,6 +52,7 @@ struct DevScalars {
     double last_change[2];                     // first-sweep changes from x_n and from the warm start
     long long sweeps_total, solves, warm_kept; // cumulative mesh-solve counters
     float mon_c[3];      // mixed form: omega's coefficients alpha_k / max_k as floats (k_mon_f's last block)
+    double base[2];      // mixed form: the origin (x_00, y_00) the step's FP32 displacement is measured from
 };
 
 // the per-step reset of the reductions and counters (k_reset), and the time step from the CFL
@@ -118,7 +119,10 @@ __global__ void k_reset(DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
 __global__ void k_dt_moving(DevScalars* d, double cfl);
 __global__ void k_set_dt(DevScalars* d, double dt);
-__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d);
+// x += dt xdot and t += dt; fdisp (nullable): also the FP32 displacement of the new x from d->base (the next
+// step's, as k_mesh_f32 forms it); reset: also reset the next step's reductions (k_reset's work)
+__global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d, float* fdisp = nullptr,
+                          int reset = 0);
 // rst (nullable): also runs k_reset's work (the first kernel of a mixed-form step)
 // fxd is written only when xdot is given (its readers take it only then)
 __global__ void k_mesh_f32(GridParams g, const double* __restrict__ x, const double* __restrict__ xdot,

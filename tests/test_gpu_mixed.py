@@ -282,3 +282,29 @@ def test_mixed_arith_building_blocks():
         worst_add = max(worst_add, float(abs(S - (A + B)) / (abs(A) + abs(B))))
     assert worst_mul <= 2.0 ** -44, worst_mul
     assert worst_add <= 2.0 ** -44, worst_add
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_steps_in_one_call_match_single_steps(precision):
+    """es_steps(K) replays a first-step graph and then a continuation graph whose advance kernel formed the next
+    step's FP32 displacement and reset the reductions (no displacement or reset kernel at its start); on the
+    Riemann problem (outflow ends: the displacement's origin node does not move) it gives the same state, mesh
+    and time bit for bit as K calls of one step."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    w = wl.riemann_2d(48, seed=5)
+    out = []
+    for mode in ("one_call", "single_steps"):
+        ctx, JU, J, xt = gpu_setup(w, precision=precision)
+        if mode == "one_call":
+            es.es_steps(ctx, JU, J, xt, 4, w["t_end"])
+        else:
+            for _ in range(4):
+                es.es_steps(ctx, JU, J, xt, 1, w["t_end"])
+        torch.cuda.synchronize()
+        assert es.es_check(ctx) == 0, es.es_last_error(ctx)
+        out.append((to_np(JU), to_np(J), to_np(xt), es.es_get_time(ctx)))
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
+    assert out[0][3] == out[1][3]
