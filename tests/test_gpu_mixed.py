@@ -308,3 +308,31 @@ def test_steps_in_one_call_match_single_steps(precision):
     for a, b in zip(out[0][:3], out[1][:3]):
         assert np.array_equal(a, b)
     assert out[0][3] == out[1][3]
+
+
+@pytest.mark.parametrize("passes,sweeps", [(1, 1), (8, 8), (3, 2)])
+@pytest.mark.parametrize("case", ["riemann2d", "wavy_periodic"])
+def test_mixed_register_tiles_vs_oracle(case, passes, sweeps):
+    """The register-tiled filter and sweep kernels at the ends of their halo range (1 and 8 passes or sweeps: tiles
+    with 62 and 48 output columns) on outflow and periodic meshes whose sizes leave ragged tiles: the same sweeps,
+    Delta_gamma and mesh velocity as the FP64 oracle to FP32 rounding."""
+    import torch
+
+    from paper_2407_05568_gb300 import es
+    if case == "riemann2d":
+        w = wl.riemann_2d(70, seed=5)
+    else:
+        w = _wavy(52)
+        w["moving"] = True
+        w["rho"], w["v"], w["p"] = wl.rough_state(w["x"].shape[1:], 11, 2)
+    w["mesh"] = dict(monitor="vdw", alphas=(1200.0, 1200.0, 1200.0), kappa=2, filter_passes=passes, sweeps=sweeps,
+                     eps=0.0)
+    sch, mc, JU_o, J_o, x = oracle_setup(w)
+    ctx, JU, J, xt = gpu_setup(w, precision="mixed")
+    dt = 0.004
+    xdot_o, sw_o, gam_o = stepper.redistribute(sch, mc, JU_o, J_o, x, dt)
+    xdot = torch.empty_like(xt)
+    sw, gam = es.es_mesh_redistribute(ctx, JU, J, xt, dt, xdot)
+    assert sw == sw_o == sweeps
+    assert abs(gam - gam_o) <= 1e-5 * gam_o
+    assert np.abs(to_np(xdot) - xdot_o).max() <= 2e-5 * np.abs(xdot_o).max()
