@@ -31,6 +31,7 @@ struct es_ctx {
     int grid1d;                       // blocks of the per-node grid-stride kernels
     int block1d;                      // their threads per block (see es_create)
     int nsm;                          // SMs of the device
+    double t_end_dev;                 // the end time the device holds (NaN: unknown)
     int mixed;                        // ES_PREC_MIXED: float state
     int tile;                         // 2D stage tile shape (0-based); tuned: chosen by es_autotune or fixed
     int tuned;
@@ -625,6 +626,7 @@ int es_create(es_ctx** out, const es_params* p, void* stream) {
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     c->nsm = nsm;
+    c->t_end_dev = __builtin_nan("");
     // The per-node kernels of a step (CFL, monitor, filter, sweeps, limiter, velocity, advance) take one node per
     // thread on a small mesh, so their time is one thread's chain of dependent operations: there every CTA gets its
     // own SM (blocks of ceil(N / SMs) threads, at most 512; with 256-thread blocks 200^2 gave 157 CTAs on 152 SMs
@@ -1074,12 +1076,15 @@ static int capture_step(es_ctx* c, void* JU, void* J, double* x, bool first, cud
 int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) {
     if (!c || !JU || !J || !x || nsteps < 0) return fail(c, ES_ERR_ARG, "bad argument");
     if (nsteps == 0) return ES_OK;
-    // t_end lives on the device; write it with a tiny copy (ordered on the stream)
-    static_assert(offsetof(DevScalars, t_end) == 2 * sizeof(double), "layout");
-    c->hpin->t_end = t_end;
-    CK(cudaMemcpyAsync(&c->dev->t_end, &c->hpin->t_end, sizeof(double), cudaMemcpyHostToDevice, c->stream),
-       "copy t_end");
-    CK(cudaStreamSynchronize(c->stream), "sync");
+    // t_end lives on the device: a one-thread kernel writes it, ordered on the stream, when it changes (a copy from
+    // pinned host memory needed a synchronisation before the buffer could be reused, and that left the GPU idle
+    // between the caller's previous work and the steps)
+    if (!(c->t_end_dev == t_end)) {
+        k_set_t_end<<<1, 32, 0, c->stream>>>(c->dev, t_end);
+        count(c);
+        CK(cudaGetLastError(), "t_end kernel");
+        c->t_end_dev = t_end;
+    }
     if (!c->tuned) {
         int rc = es_autotune(c, JU, J, x, nullptr, nullptr);
         if (rc) return rc;

@@ -217,6 +217,10 @@ __global__ void k_set_dt(DevScalars* d, double dt) {
     if (threadIdx.x == 0 && blockIdx.x == 0) d->dt = dt;
 }
 
+__global__ void k_set_t_end(DevScalars* d, double t_end) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) d->t_end = t_end;
+}
+
 // the float displacement x - (x_00 + i dxi_1) of one coordinate, in double-float arithmetic on the FP32 pipe:
 // x and x_00 split from their bits (es_bits.cuh), i dxi_1 an exact product plus i dxl, error-free sums; the
 // absolute error is about 2^-45 |x|, far below the float rounding of the displacement itself

@@ -119,6 +119,7 @@ __global__ void k_reset(DevScalars* d);
 __global__ void k_dt(DevScalars* d, double cfl, double dt_fixed);
 __global__ void k_dt_moving(DevScalars* d, double cfl);
 __global__ void k_set_dt(DevScalars* d, double dt);
+__global__ void k_set_t_end(DevScalars* d, double t_end);
 // x += dt xdot and t += dt; fdisp (nullable): also the FP32 displacement of the new x from d->base (the next
 // step's, as k_mesh_f32 forms it); reset: also reset the next step's reductions (k_reset's work)
 __global__ void k_advance(GridParams g, double* x, const double* xdot, DevScalars* d, float* fdisp = nullptr,
