@@ -52,10 +52,12 @@ struct es_ctx {
     void *hJU, *hJ;                   // device copies for es_run_host
     double* hx;
     // graph cache
-    cudaGraphExec_t gexec;            // the step graph (its first step in an es_steps call)
-    cudaGraphExec_t gexec2;           // the graph of the steps after it (1D/2D: no displacement or reset kernel)
+    // the step graphs: [0] a call's only step, [1] the first of several (its advance kernel also forms the next
+    // step's displacement and resets the reductions), [2] the steps after it (1D/2D: without the displacement or
+    // reset kernel at their start)
+    cudaGraphExec_t gexec[3];
     const void* gkey[3];
-    int graph_kernels, graph_kernels2;
+    int graph_kernels[3];
     int capturing;
     int capture_count;
     int loop_failed;                  // a graph while-loop could not be built (unrolled sweeps used)
@@ -66,9 +68,10 @@ struct es_ctx {
 
 // the cached step graphs (they hold the buffers, the tile shape and the warm-start network)
 static void drop_graphs(es_ctx* c) {
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->gexec2) cudaGraphExecDestroy(c->gexec2);
-    c->gexec = c->gexec2 = nullptr;
+    for (int k = 0; k < 3; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        c->gexec[k] = nullptr;
+    }
 }
 
 
@@ -448,8 +451,9 @@ int enqueue_step3(es_ctx* c, double* JU, double* J, double* x) {
 }
 
 // first = false: a step that follows one of the same es_steps call, whose advance kernel has already formed the
-// mixed form's FP32 displacement of x and reset the reductions (no k_mesh_f32 or k_reset then; 1D/2D)
-int enqueue_step(es_ctx* c, void* JU, void* J, double* x, bool first = true) {
+// mixed form's FP32 displacement of x and reset the reductions (no k_mesh_f32 or k_reset then; 1D/2D); chain: a
+// step of the same call follows, so this step's advance kernel does that work
+int enqueue_step(es_ctx* c, void* JU, void* J, double* x, bool first = true, bool chain = false) {
     if (c->p.dim == 3) return enqueue_step3(c, (double*)JU, (double*)J, x);
     const int B = c->block1d, G = c->grid1d;
     cudaStream_t s = c->s_enq;
@@ -512,7 +516,7 @@ int enqueue_step(es_ctx* c, void* JU, void* J, double* x, bool first = true) {
         if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel");
     }
     // the next step's displacement (mixed form) and reductions, for a following step of the same call
-    k_advance<<<G, B, 0, s>>>(c->g, x, xdot ? c->xdot : nullptr, c->dev, f32 ? c->fdisp : nullptr, 1);
+    k_advance<<<G, B, 0, s>>>(c->g, x, xdot ? c->xdot : nullptr, c->dev, chain && f32 ? c->fdisp : nullptr, chain);
     count(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "advance kernel");
@@ -1051,13 +1055,14 @@ int es_step(es_ctx* c, void* JU, void* J, double* x, double t_end, double* t_hos
 }
 
 // one step captured into an executable graph on the private capture stream
-static int capture_step(es_ctx* c, void* JU, void* J, double* x, bool first, cudaGraphExec_t* out, int* kernels) {
+static int capture_step(es_ctx* c, void* JU, void* J, double* x, bool first, bool chain, cudaGraphExec_t* out,
+                        int* kernels) {
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     c->capturing = 1;
     c->capture_count = 0;
     c->s_enq = c->cap_stream;
-    int rc = enqueue_step(c, JU, J, x, first);
+    int rc = enqueue_step(c, JU, J, x, first, chain);
     c->s_enq = c->stream;
     c->capturing = 0;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
@@ -1090,19 +1095,21 @@ int es_steps(es_ctx* c, void* JU, void* J, double* x, int nsteps, double t_end) 
         if (rc) return rc;
     }
     const void* key[3] = {JU, J, x};
-    if (!c->gexec || memcmp(key, c->gkey, sizeof(key)) != 0) {
+    if (memcmp(key, c->gkey, sizeof(key)) != 0) {
         drop_graphs(c);
-        int rc = capture_step(c, JU, J, x, true, &c->gexec, &c->graph_kernels);
-        if (rc) return rc;
         memcpy(c->gkey, key, sizeof(key));
     }
-    if (nsteps > 1 && !c->gexec2) {
-        int rc = capture_step(c, JU, J, x, false, &c->gexec2, &c->graph_kernels2);
-        if (rc) return rc;
+    const int first = nsteps == 1 ? 0 : 1;
+    for (int k = first; k <= (nsteps == 1 ? 0 : 2); ++k) {
+        if (!c->gexec[k]) {
+            int rc = capture_step(c, JU, J, x, k < 2, k > 0, &c->gexec[k], &c->graph_kernels[k]);
+            if (rc) return rc;
+        }
     }
     for (int k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(k == 0 ? c->gexec : c->gexec2, c->stream), "graph launch");
-        c->launches += k == 0 ? c->graph_kernels : c->graph_kernels2;
+        const int g = k == 0 ? first : 2;
+        CK(cudaGraphLaunch(c->gexec[g], c->stream), "graph launch");
+        c->launches += c->graph_kernels[g];
     }
     return ES_OK;
 }
