@@ -66,14 +66,15 @@ cudaError_t launch_tile_f(const StageParams& P, cudaStream_t s) {
 
 // 2D shapes: 20 x 8 nodes with 384 threads, two lanes per face (twice the warps of the 192-thread
 // shape: small meshes are latency bound), 25 x 6 with 192 (175 faces; 8 x 34 = 272 tiles fill
-// 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces), 16 x 8 with 320, two lanes
-// per face, and 16 x 8 with 160 (more CTAs for small meshes)
+// 200 x 200 at two CTAs per SM in one wave), 20 x 8 with 192 (180 faces), 20 x 14 with 608, two lanes
+// per face (10 x 15 = 150 tiles: one CTA on each SM at 200 x 200, less halo per node), and 16 x 8 with 160
+// (more CTAs for small meshes)
 cudaError_t stage_prepare_mixed(int dim) {
     if (dim == 1) return prepare_tile_f<1, 254, 1, 256>();
     cudaError_t e = prepare_tile_f<2, 20, 8, 384, true>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 25, 6, 192>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 20, 8, 192>();
-    if (e == cudaSuccess) e = prepare_tile_f<2, 16, 8, 320, true>();
+    if (e == cudaSuccess) e = prepare_tile_f<2, 20, 14, 608, true>();
     if (e == cudaSuccess) e = prepare_tile_f<2, 16, 8, 160>();
     return e;
 }
@@ -83,7 +84,7 @@ cudaError_t launch_stage_mixed(const StageParams& P, cudaStream_t s) {
     switch (P.tile) {
         case 1: return launch_tile_f<2, 25, 6, 192>(P, s);
         case 2: return launch_tile_f<2, 20, 8, 192>(P, s);
-        case 3: return launch_tile_f<2, 16, 8, 320, true>(P, s);
+        case 3: return launch_tile_f<2, 20, 14, 608, true>(P, s);
         case 4: return launch_tile_f<2, 16, 8, 160>(P, s);
         default: return launch_tile_f<2, 20, 8, 384, true>(P, s);
     }
