@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tile", type=int, default=0,
+                    help="fixed stage-tile shape 1..5 of the main form (default 0: the autotuner chooses)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-chosen", action="store_true", help="skip the mixed-precision comparison run")
     ap.add_argument("--batch-problems", type=int, default=4096, help="batched-form problems (0: skip)")
@@ -219,7 +221,8 @@ def measure_form(args, precision, dev, stream, world):
     w = workload(args.n)
     nodes = args.n * args.n
     with torch.cuda.stream(stream):
-        ctx = es.es_create(es.make_params(w, precision=precision), stream)
+        tile = args.tile if precision == args.precision else 0
+        ctx = es.es_create(es.make_params(w, precision=precision, tile=tile), stream)
         x0 = torch.tensor(w["x"], dtype=torch.float64, device=dev)
         J0 = es.state_empty(ctx, w["x"].shape[1:], dev)
         es.es_init_mesh(ctx, x0, J0)
@@ -239,7 +242,10 @@ def measure_form(args, precision, dev, stream, world):
         es.es_set_time(ctx, 0.0)
 
     restart()
-    tile, tile_ms = es.es_autotune(ctx, JU, J, x)        # stage tile shape for this problem size
+    if tile:                                             # fixed by --tile
+        tile_ms = None
+    else:
+        tile, tile_ms = es.es_autotune(ctx, JU, J, x)    # stage tile shape for this problem size
     done = 0
     for _ in range(args.warmup):
         es.es_steps(ctx, JU, J, x, 1, w["t_end"])
