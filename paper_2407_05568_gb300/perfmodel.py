@@ -49,12 +49,12 @@ def mesh_bytes_per_node(precision, filter_passes, sweeps):
     the sequence reads its inputs once and writes its outputs once (neighbour reads served from cache).
 
     FP64 form, in 8-byte words: monitor fields (JU, J -> rho, G) 7, monitor terms (rho, G -> three terms) 5,
-    omega 4, each filter pass 2, each Jacobi sweep (omega, x -> x) 5, limiter (x^n, x^mu) 4, velocity
-    (x^n, x^mu -> xdot) 6.
+    omega 4, each filter pass 2, each Jacobi sweep (omega, x -> x) 5, the limiter inside the last sweep (x^n) 2,
+    velocity (x^n, x^mu -> xdot) 6.
     Mixed form, in bytes: the FP32 displacement from x (16 + 8), the fused monitor on the (hi, lo) state
     (40 + 12), omega and all filter passes in one tile kernel (12 + 4), all Jacobi sweeps and the limiter in
     one tile kernel (omega, d -> d: 4 + 8 + 8; the limiter reads the sweeps' own values), velocity (d, d^mu ->
     float and double xdot: 16 + 8 + 16)."""
     if precision == "fp64":
-        return 8 * (7 + 5 + 4 + 2 * filter_passes + 5 * sweeps + 4 + 6)
+        return 8 * (7 + 5 + 4 + 2 * filter_passes + 5 * sweeps + 2 + 6)
     return 24 + 52 + 16 + 20 + 40
