@@ -15,23 +15,34 @@
 namespace es {
 
 // ------------------------------------------------------------ helpers
-__device__ __forceinline__ double coord_at(const GridParams& g, const double* x, int gi, int gj, int comp) {
-    const size_t N = size_t(g.n1) * g.n2;
-    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))   // interior: a plain load
-        return x[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
-    const GhostTerms ti = ghost_terms(gi, g.n1, g.bc[0], comp != 0);
+// A ghost coordinate (the ghost rule: periodic wrap with the period shift, odd reflection at outflow ends, mirror
+// at walls).  Kept out of line: inlined at each of a kernel's neighbour reads it made the per-node kernels' code
+// long and branchy, and with one node per thread their warps stalled on instruction fetch (ncu: "no
+// instruction" the top stall of the sweep and CFL kernels); only boundary nodes call it.
+__device__ __noinline__ double coord_ghost(int n1, int n2, int dim, int bc0, int bc1, double per0, double per1,
+                                          const double* x, int gi, int gj, int comp) {
+    const size_t N = size_t(n1) * n2;
+    const GhostTerms ti = ghost_terms(gi, n1, bc0, comp != 0);
     GhostTerms tj;
-    if (g.dim == 2) tj = ghost_terms(gj, g.n2, g.bc[1], comp != 1);
+    if (dim == 2) tj = ghost_terms(gj, n2, bc1, comp != 1);
     else { tj.idx[0] = 0; tj.w[0] = 1.0; tj.nterm = 1; tj.q = 0; }
     double acc = 0.0;
 #pragma unroll
     for (int a = 0; a < 2; ++a)              // fixed bounds: the terms stay in registers
 #pragma unroll
         for (int c = 0; c < 2; ++c)
-            if (a < ti.nterm && c < tj.nterm) acc += ti.w[a] * tj.w[c] * x[comp * N + size_t(tj.idx[c]) * g.n1 + ti.idx[a]];
-    if (comp == 0) acc += ti.q * g.period[0];
-    if (comp == 1) acc += tj.q * g.period[1];
+            if (a < ti.nterm && c < tj.nterm) acc += ti.w[a] * tj.w[c] * x[comp * N + size_t(tj.idx[c]) * n1 + ti.idx[a]];
+    if (comp == 0) acc += ti.q * per0;
+    if (comp == 1) acc += tj.q * per1;
     return acc;
+}
+
+// (the grid's scalars go by value: a reference would put the kernel's parameter block in local memory)
+__device__ __forceinline__ double coord_at(const GridParams& g, const double* x, int gi, int gj, int comp) {
+    const size_t N = size_t(g.n1) * g.n2;
+    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))   // interior: a plain load
+        return x[comp * N + size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
+    return coord_ghost(g.n1, g.n2, g.dim, g.bc[0], g.bc[1], g.period[0], g.period[1], x, gi, gj, comp);
 }
 
 // 6th-order central difference delta_k of coordinate `comp` at node (i, j), divided by dxi_k

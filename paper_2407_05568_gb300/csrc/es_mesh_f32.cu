@@ -123,20 +123,17 @@ __device__ __forceinline__ GhostF ghost_f(int i, int n, int bc) {
     return t;
 }
 
-// displacement at a node that may be a ghost
-__device__ __forceinline__ float disp_at(const GridParams& g, const float* d, int gi, int gj, int comp) {
-    const size_t N = size_t(g.n1) * g.n2;
-    const float* dc = d + comp * N;
-    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))
-        return dc[size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
-    const GhostF ti = ghost_f(gi, g.n1, g.bc[0]);
+// displacement at a ghost node (out of line: inlined at every neighbour read it made the per-node kernels' code long
+// and branchy, and one-node-per-thread warps stall on instruction fetch; only boundary nodes call it)
+__device__ __noinline__ float disp_ghost(int n1, int n2, int dim, int bc0, int bc1, const float* dc, int gi, int gj) {
+    const GhostF ti = ghost_f(gi, n1, bc0);
     GhostF tj;
-    if (g.dim == 2) {
-        tj = ghost_f(gj, g.n2, g.bc[1]);
+    if (dim == 2) {
+        tj = ghost_f(gj, n2, bc1);
     } else {
         tj.i0 = 0; tj.i1 = 0; tj.w0 = 1.0f; tj.w1 = 0.0f; tj.two = false;
     }
-    const size_t r0 = size_t(tj.i0) * g.n1, r1 = size_t(tj.i1) * g.n1;
+    const size_t r0 = size_t(tj.i0) * n1, r1 = size_t(tj.i1) * n1;
     float acc = (ti.w0 * tj.w0) * dc[r0 + ti.i0];             // the terms in ghost_terms' order
     if (tj.two) acc += (ti.w0 * tj.w1) * dc[r1 + ti.i0];
     if (ti.two) {
@@ -144,6 +141,15 @@ __device__ __forceinline__ float disp_at(const GridParams& g, const float* d, in
         if (tj.two) acc += (ti.w1 * tj.w1) * dc[r1 + ti.i1];
     }
     return acc;
+}
+
+// displacement at a node that may be a ghost
+__device__ __forceinline__ float disp_at(const GridParams& g, const float* d, int gi, int gj, int comp) {
+    const size_t N = size_t(g.n1) * g.n2;
+    const float* dc = d + comp * N;
+    if (gi >= 0 && gi < g.n1 && (g.dim == 1 || (gj >= 0 && gj < g.n2)))
+        return dc[size_t(g.dim == 2 ? gj : 0) * g.n1 + gi];
+    return disp_ghost(g.n1, g.n2, g.dim, g.bc[0], g.bc[1], dc, gi, gj);
 }
 
 __device__ __forceinline__ float field_at_f(const GridParams& g, const float* f, int i, int j) {
